@@ -1,0 +1,207 @@
+/*
+ * asm2 -- two-level ("boundary conditioning") additive Schwarz preconditioned Krylov solver for
+ * fully implicit reservoir Jacobians with 3x3 blocks per cell, on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: H. Jackson, M. Taroni, D. K. Ponting, "A Two-Level Variant of Additive Schwarz
+ * Preconditioning for Use in Reservoir Simulation", arXiv:1401.7227.
+ *   - Linear problem r = b - A x = 0, A = -J (Section 2).
+ *   - Each subdomain i solves with A_i = R_i A R_i^T (Eq. 3.4), where R_i is the identity on the
+ *     subdomain's fine cells and coarsens the rest of the grid into near-field and far-field lumps
+ *     by plain summation (Eq. 4.1, Section 4, Appendix B).
+ *   - A_i is approximately inverted by a block ILU(0) whose dropped fill is moved to the diagonal
+ *     block of its column, so that E = B - A has zero column sums (Section 2; cf. Eq. A.7).
+ *   - B^{-1} r = sum_i P_i R_i^T A_i^{-1} R_i r: each cell takes the local solution of the
+ *     subdomain that owns it; the coarse parts are discarded (Eqs. 4.2-4.5).
+ *   - The Krylov accelerator is GMRES(m) or ORTHOMIN(k), right-preconditioned (Section 2).
+ *
+ * Conventions for every call:
+ *   - Cells are numbered z fastest: cell = k + nz * (i + nx * j) for grid position (i, j, k).
+ *   - Vectors hold 3 doubles per cell (cell-major); a matrix block is 9 doubles, row-major.
+ *   - Every call returns an asm_status; nothing throws across this boundary.
+ *   - A handle is used from one host thread at a time.  Device work is issued in order on the
+ *     CUDA stream given to asm_create (NULL = the legacy default stream); calls that take caller
+ *     buffers return after that work has completed.
+ *   - "on_device" says whether caller vector/matrix pointers are device memory (1) or host
+ *     memory (0).  Caller buffers stay owned by the caller.  The library copies everything given
+ *     to asm_set_* / asm_update_values into device memory it owns, freed by asm_destroy.
+ *   - Partition geometry (Section 4): the grid is split into px*py*pz boxes, part t of n cells
+ *     in a dimension being [n*t/p, n*(t+1)/p); subdomain s = tz + pz*(tx + px*ty).  Its fine
+ *     set is its box grown by `overlap` cells (clipped); near lumps are the c_near-sized boxes
+ *     aligned at 0 that meet the ring of width `near_width` around the fine set, minus the fine
+ *     set; far lumps are the far boxes (the partition boxes, or c_far-sized aligned boxes) minus
+ *     the fine set and the near lumps.  Empty lumps are dropped.  Local order: fine cells by cell
+ *     index, then near lumps, then far lumps, each by box index bz + nbz*(bx + nbx*by).
+ */
+#ifndef ASM2_H
+#define ASM2_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ASM_OK = 0,
+    ASM_ERR_INVALID_ARG = 1,   /* bad size, index, pointer or option; checked on the host */
+    ASM_ERR_PATTERN = 2,       /* block pattern not structurally symmetric / missing a diagonal */
+    ASM_ERR_ZERO_PIVOT = 3,    /* singular 3x3 pivot in a local factorisation */
+    ASM_ERR_NOT_CONVERGED = 4, /* max_iter reached; x holds the last iterate */
+    ASM_ERR_OOM = 5,           /* device (or host) allocation failed */
+    ASM_ERR_CUDA = 6,          /* a CUDA runtime call failed */
+    ASM_ERR_TIMEOUT = 7,       /* a bounded device wait expired */
+    ASM_ERR_STATE = 8          /* call out of order (e.g. solve before factor) */
+} asm_status;
+
+typedef enum {
+    ASM_PREC_FP64 = 0,  /* local factors stored and applied in FP64 */
+    ASM_PREC_FP32 = 1,  /* fine-cell factor rows stored and applied in FP32; lump rows FP64 */
+    ASM_PREC_FP16S = 2  /* fine-cell factor rows stored in FP16, applied in FP32; lump rows FP64 */
+} asm_precision;
+
+typedef enum { ASM_KRYLOV_GMRES = 0, ASM_KRYLOV_ORTHOMIN = 1 } asm_krylov;
+
+typedef enum {
+    ASM_LOCAL_BILU0_COLSUM = 0, /* block ILU(0) with column-sum compensation (default) */
+    ASM_LOCAL_BILU0 = 1         /* plain block ILU(0): dropped fill is discarded */
+} asm_local_solver;
+
+typedef enum {
+    ASM_FAR_NONE = 0,      /* no far field: cells outside fine set + near lumps are left out */
+    ASM_FAR_PARTITION = 1, /* far lumps = the partition boxes */
+    ASM_FAR_BOXES = 2      /* far lumps = aligned boxes of size c_far */
+} asm_far_mode;
+
+typedef struct {
+    int precision;    /* asm_precision */
+    int krylov;       /* asm_krylov */
+    int restart;      /* GMRES restart length m, or ORTHOMIN direction count k; 1..512 */
+    int local_solver; /* asm_local_solver */
+    int flexible;     /* GMRES update: 1 keeps Z_j = B^{-1} v_j and sets x += Z y; 0 sets
+                         x += B^{-1}(V y); -1 = automatic (0 for FP64, 1 otherwise) */
+    int device;       /* CUDA device ordinal */
+} asm_options;
+
+typedef struct {
+    int iterations;      /* preconditioned matrix-vector products */
+    int restarts;        /* completed GMRES cycles (true-residual evaluations) */
+    int converged;       /* 1 when ||b - A x||_2 <= rtol * ||b||_2, FP64 true residual */
+    int status;          /* asm_status of this system */
+    double rel_residual; /* final FP64 true relative residual */
+} asm_solve_info;
+
+typedef struct {
+    int n_cells;                 /* N */
+    int n_sub;                   /* subdomains K */
+    long long local_rows;        /* sum over subdomains of n_i (fine cells + lumps) */
+    int max_local_rows;          /* max n_i */
+    int max_levels;              /* max wavefront levels of a local factor */
+    long long local_blocks;      /* sum over subdomains of the local pattern size (blocks) */
+    long long factor_bytes;      /* factor-stream bytes read by one preconditioner apply */
+    long long apply_index_bytes; /* restriction/scatter list bytes read by one apply */
+    long long matrix_bytes;      /* values + column indices of A read by one SpMV */
+    long long alg_apply_bytes;   /* minimum bytes one apply must move: every off-diagonal factor
+                                    block (9 values + a 4-byte index) and every D^{-1} block at its
+                                    storage precision, plus r read and z written (48 N) */
+    double setup_ms;             /* host symbolic analysis time of the last asm_factor */
+    double factor_ms;            /* device assembly + factorisation time of the last asm_factor */
+} asm_stats;
+
+/* Device time of each part of the solver, accumulated while profiling is on (CUDA events on the
+ * handle's stream around each launch group), and the number of kernels launched. */
+typedef struct {
+    double apply_ms;        /* far-box sums + fused local solves (preconditioner apply) */
+    double spmv_ms;         /* SpMV (A z, and b - A x at restarts) */
+    double ortho_ms;        /* Gram-Schmidt / norms / Givens / vector updates */
+    double factor_ms;       /* assembly + factorisation + factor packing */
+    long long apply_launches;   /* preconditioner applies timed in apply_ms */
+    long long kernel_launches;  /* every kernel launched by the library (counted always) */
+} asm_profile_info;
+
+typedef struct asm_ctx* asm_handle;
+
+/* Defaults: FP64, GMRES, m = 30, column-sum ILU(0), automatic flexibility, device 0. */
+void asm_default_options(asm_options* opt);
+
+/* Text of a status code (static storage, never NULL). */
+const char* asm_error_string(int status);
+
+/* Create a handle.  opt NULL = defaults.  cuda_stream: a cudaStream_t of opt->device, or NULL.
+ * Errors: INVALID_ARG (bad option / device), CUDA. */
+int asm_create(asm_handle* h, const asm_options* opt, void* cuda_stream);
+
+/* Free every device and host resource of h (NULL is a no-op). */
+int asm_destroy(asm_handle h);
+
+/* Grid of the problem (Section 1: one cell = one 3x3 block row).  Must precede the matrix. */
+int asm_set_grid(asm_handle h, int nx, int ny, int nz);
+
+/* The matrix A (Section 2: A = -J) as BSR with 3x3 blocks: row_ptr[n_cells+1], col_idx[nnzb]
+ * (ascending within a row, diagonal present, pattern structurally symmetric), vals[nnzb*9]
+ * row-major blocks.  n_cells must equal nx*ny*nz.  The pattern is validated on the host
+ * (INVALID_ARG for bad indices, PATTERN for asymmetry or a missing diagonal); on_device applies
+ * to vals only (row_ptr/col_idx are always host arrays).  Invalidates any factorisation. */
+int asm_set_matrix_bsr(asm_handle h, int n_cells, int nnzb, const int* row_ptr, const int* col_idx,
+                       const double* vals, int on_device);
+
+/* New values for the same pattern (vals[nnzb*9]); keeps the symbolic analysis, so the next
+ * asm_factor only re-assembles and re-factors on the device (a new Newton iteration, Section 4:
+ * the coarsened matrices are rebuilt once per non-linear iteration). */
+int asm_update_values(asm_handle h, const double* vals, int on_device);
+
+/* Subdomain partition and coarsening (Section 4, Eq. 4.1, Figs. 2-3; geometry in the file
+ * header).  c_near[3]: near-box size (x, y, z), required when near_width > 0.  far_mode:
+ * asm_far_mode; c_far[3] is the far-box size for ASM_FAR_BOXES (else ignored, may be NULL).
+ * Errors: INVALID_ARG (p > n, negative widths, box sizes < 1). */
+int asm_set_partition_boxes(asm_handle h, int px, int py, int pz, int overlap, int near_width,
+                            const int* c_near, int far_mode, const int* c_far);
+
+/* Build B: host symbolic analysis (cached across asm_update_values), then on the device the
+ * local matrices A_i = R_i A R_i^T (Eq. 3.4, B.3) and their block ILU(0) (+ colsum, Section 2).
+ * Errors: STATE (no matrix/partition), ZERO_PIVOT (see asm_get_error_location), OOM, CUDA. */
+int asm_factor(asm_handle h);
+
+/* z = B^{-1} r = sum_i P_i R_i^T A_i^{-1} R_i r (Eqs. 4.2-4.5); r, z: 3N doubles. */
+int asm_apply_precond(asm_handle h, const double* r, double* z, int on_device);
+
+/* y = A x; x, y: 3N doubles. */
+int asm_spmv(asm_handle h, const double* x, double* y, int on_device);
+
+/* Solve A x = b to ||b - A x||_2 <= rtol ||b||_2 (FP64 true residual) with the Krylov method of
+ * the options, x0 = 0 (Section 2).  x receives the solution (or the last iterate with
+ * NOT_CONVERGED).  info may be NULL. */
+int asm_solve(asm_handle h, const double* b, double* x, double rtol, int max_iter, int on_device,
+              asm_solve_info* info);
+
+/* Solve n independent factored systems together: every Krylov step of all unfinished systems
+ * runs in the same kernel launches.  Handles must share device and stream and use GMRES.
+ * b[k], x[k] belong to hs[k]; infos[k] (may be NULL) receives its result.  Each system's
+ * arithmetic does not depend on the others in the batch.  Returns the worst status. */
+int asm_solve_batch(asm_handle* hs, int n, const double* const* b, double* const* x, double rtol,
+                    int max_iter, int on_device, asm_solve_info* infos);
+
+/* Sizes and timings of the current factorisation. */
+int asm_get_stats(asm_handle h, asm_stats* st);
+
+/* Profiling switch (0/1): when on, launch groups are bracketed by CUDA events. */
+int asm_set_profiling(asm_handle h, int enable);
+/* Accumulated profile since the last reset (counters keep running when profiling is off). */
+int asm_get_profile(asm_handle h, asm_profile_info* p);
+int asm_reset_profile(asm_handle h);
+
+/* After ZERO_PIVOT: the subdomain and local block row of the first singular pivot found. */
+int asm_get_error_location(asm_handle h, int* sub, int* row);
+
+/* Parity hooks (copies to caller HOST memory, in the local order of the file header):
+ * counts[3] = {fine cells, near lumps, far lumps}; map[N] = local row of each cell or -1;
+ * the local matrix A_s as BSR (row_ptr[n+1], col_idx[nnzb], vals[nnzb*9]); its factors in the
+ * same pattern (lu[nnzb*9]: L below, U above, D^{-1} on the diagonal; dpiv[n*9]: pivot blocks),
+ * as FP64 before any down-cast of the stored factors.  Any output pointer may be NULL. */
+int asm_get_local_info(asm_handle h, int s, int* n, int* nnzb, int* counts, int* n_levels);
+int asm_get_local_map(asm_handle h, int s, int* map);
+int asm_get_local_matrix(asm_handle h, int s, int* row_ptr, int* col_idx, double* vals);
+int asm_get_local_factors(asm_handle h, int s, double* lu, double* dpiv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

@@ -1,0 +1,337 @@
+"""Thin ctypes binding of ``libasm2.so`` (include/asm2.h).  Argument marshalling only: every step of
+the solver runs in the library's CUDA kernels.  Device buffers are torch CUDA tensors, host
+buffers numpy arrays; the stream is torch's current CUDA stream unless one is given.
+
+There is no fallback: if the library is missing or no CUDA device is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+ASM_OK = 0
+STATUS = {0: "ok", 1: "invalid argument", 2: "pattern", 3: "zero pivot", 4: "not converged", 5: "out of memory",
+          6: "cuda error", 7: "timeout", 8: "state"}
+PREC = {"fp64": 0, "fp32": 1, "fp16s": 2}
+FAR = {"none": 0, "partition": 1, "boxes": 2}
+
+#: every symbol include/asm2.h declares
+EXPORTS = [
+    "asm_default_options", "asm_error_string", "asm_create", "asm_destroy", "asm_set_grid", "asm_set_matrix_bsr",
+    "asm_update_values", "asm_set_partition_boxes", "asm_factor", "asm_apply_precond", "asm_spmv", "asm_solve",
+    "asm_solve_batch", "asm_get_stats", "asm_get_error_location", "asm_get_local_info", "asm_get_local_map",
+    "asm_get_local_matrix", "asm_get_local_factors", "asm_set_profiling", "asm_get_profile", "asm_reset_profile",
+]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("krylov", C.c_int), ("restart", C.c_int), ("local_solver", C.c_int),
+                ("flexible", C.c_int), ("device", C.c_int)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("restarts", C.c_int), ("converged", C.c_int), ("status", C.c_int),
+                ("rel_residual", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_cells", C.c_int), ("n_sub", C.c_int), ("local_rows", C.c_longlong), ("max_local_rows", C.c_int),
+                ("max_levels", C.c_int), ("local_blocks", C.c_longlong), ("factor_bytes", C.c_longlong),
+                ("apply_index_bytes", C.c_longlong), ("matrix_bytes", C.c_longlong), ("alg_apply_bytes", C.c_longlong),
+                ("setup_ms", C.c_double),
+                ("factor_ms", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Profile(C.Structure):
+    _fields_ = [("apply_ms", C.c_double), ("spmv_ms", C.c_double), ("ortho_ms", C.c_double), ("factor_ms", C.c_double),
+                ("apply_launches", C.c_longlong), ("kernel_launches", C.c_longlong)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ASMError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        super().__init__(f"asm2: {what}: {STATUS.get(status, status)} ({status})")
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libasm2.so (built by paper_1401_7227_gb300.build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"{path} is missing: run paper_1401_7227_gb300.build.build() first")
+        _build.build()
+    L = C.CDLL(path)
+    P, I, D = C.c_void_p, C.c_int, C.c_double
+    L.asm_default_options.argtypes = [C.POINTER(Options)]
+    L.asm_default_options.restype = None
+    L.asm_error_string.argtypes = [I]
+    L.asm_error_string.restype = C.c_char_p
+    L.asm_create.argtypes = [C.POINTER(P), C.POINTER(Options), P]
+    L.asm_destroy.argtypes = [P]
+    L.asm_set_grid.argtypes = [P, I, I, I]
+    L.asm_set_matrix_bsr.argtypes = [P, I, I, P, P, P, I]
+    L.asm_update_values.argtypes = [P, P, I]
+    L.asm_set_partition_boxes.argtypes = [P, I, I, I, I, I, P, I, P]
+    L.asm_factor.argtypes = [P]
+    L.asm_apply_precond.argtypes = [P, P, P, I]
+    L.asm_spmv.argtypes = [P, P, P, I]
+    L.asm_solve.argtypes = [P, P, P, D, I, I, C.POINTER(SolveInfo)]
+    L.asm_solve_batch.argtypes = [P, I, P, P, D, I, I, P]
+    L.asm_get_stats.argtypes = [P, C.POINTER(Stats)]
+    L.asm_get_error_location.argtypes = [P, C.POINTER(I), C.POINTER(I)]
+    L.asm_get_local_info.argtypes = [P, I, P, P, P, P]
+    L.asm_get_local_map.argtypes = [P, I, P]
+    L.asm_get_local_matrix.argtypes = [P, I, P, P, P]
+    L.asm_get_local_factors.argtypes = [P, I, P, P]
+    L.asm_set_profiling.argtypes = [P, I]
+    L.asm_get_profile.argtypes = [P, C.POINTER(Profile)]
+    L.asm_reset_profile.argtypes = [P]
+    for name in EXPORTS:
+        if name not in ("asm_default_options", "asm_error_string"):
+            getattr(L, name).restype = I
+    _lib = L
+    return L
+
+
+def _check(st: int, what: str):
+    if st != ASM_OK:
+        raise ASMError(st, what)
+
+
+def _host_ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _current_stream(device: int):
+    import torch
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+class Solver:
+    """One system: grid, BSR 3x3 matrix, partition, factorisation and solves."""
+
+    def __init__(self, precision: str = "fp64", restart: int = 30, local_solver: str = "colsum",
+                 flexible: int = -1, device: int = 0, stream: int | None = None, krylov: str = "gmres"):
+        L = load()
+        o = Options()
+        L.asm_default_options(C.byref(o))
+        o.precision = PREC[precision]
+        o.restart = restart
+        o.local_solver = {"colsum": 0, "plain": 1}[local_solver]
+        o.flexible = flexible
+        o.device = device
+        o.krylov = {"gmres": 0, "orthomin": 1}[krylov]
+        self.device = device
+        self.stream = stream if stream is not None else _current_stream(device)
+        h = C.c_void_p()
+        _check(L.asm_create(C.byref(h), C.byref(o), C.c_void_p(self.stream)), "create")
+        self._h = h
+        self.n_cells = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().asm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_grid(self, nx: int, ny: int, nz: int):
+        _check(load().asm_set_grid(self._h, nx, ny, nz), "set_grid")
+        self.n_cells = nx * ny * nz
+
+    def set_matrix(self, row_ptr, col_idx, vals):
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+        if _is_torch(vals) and vals.is_cuda:
+            v = vals.contiguous()
+            _check(load().asm_set_matrix_bsr(self._h, rp.shape[0] - 1, ci.shape[0], _host_ptr(rp), _host_ptr(ci),
+                                             C.c_void_p(v.data_ptr()), 1), "set_matrix")
+        else:
+            v = np.ascontiguousarray(vals, dtype=np.float64)
+            _check(load().asm_set_matrix_bsr(self._h, rp.shape[0] - 1, ci.shape[0], _host_ptr(rp), _host_ptr(ci),
+                                             _host_ptr(v), 0), "set_matrix")
+
+    def update_values(self, vals):
+        if _is_torch(vals) and vals.is_cuda:
+            v = vals.contiguous()
+            _check(load().asm_update_values(self._h, C.c_void_p(v.data_ptr()), 1), "update_values")
+        else:
+            v = np.ascontiguousarray(vals, dtype=np.float64)
+            _check(load().asm_update_values(self._h, _host_ptr(v), 0), "update_values")
+
+    def set_partition(self, px: int, py: int, pz: int, overlap: int = 1, near_width: int = 2,
+                      c_near=(2, 2, 2), far_mode: str | int = "partition", c_far=None):
+        fm = FAR[far_mode] if isinstance(far_mode, str) else int(far_mode)
+        cn = (C.c_int * 3)(*c_near)
+        cf = (C.c_int * 3)(*(c_far if c_far is not None else (1, 1, 1)))
+        _check(load().asm_set_partition_boxes(self._h, px, py, pz, overlap, near_width, cn, fm, cf), "set_partition")
+
+    def factor(self):
+        st = load().asm_factor(self._h)
+        if st == 3:
+            s, r = C.c_int(), C.c_int()
+            load().asm_get_error_location(self._h, C.byref(s), C.byref(r))
+            err = ASMError(st, f"factor (subdomain {s.value}, local row {r.value})")
+            err.where = (s.value, r.value)
+            raise err
+        _check(st, "factor")
+
+    def _vec_call(self, fn, x, what):
+        n3 = 3 * self.n_cells
+        if _is_torch(x) and x.is_cuda:
+            import torch
+            xi = x.contiguous().to(torch.float64)
+            out = torch.empty_like(xi)
+            _check(fn(self._h, C.c_void_p(xi.data_ptr()), C.c_void_p(out.data_ptr()), 1), what)
+            return out
+        xi = np.ascontiguousarray(x, dtype=np.float64)
+        if xi.shape[0] != n3:
+            raise ValueError(f"{what}: expected {n3} values")
+        out = np.empty_like(xi)
+        _check(fn(self._h, _host_ptr(xi), _host_ptr(out), 0), what)
+        return out
+
+    def apply(self, r):
+        """z = B^{-1} r (Eqs. 4.2-4.5)."""
+        return self._vec_call(load().asm_apply_precond, r, "apply_precond")
+
+    def spmv(self, x):
+        return self._vec_call(load().asm_spmv, x, "spmv")
+
+    def solve(self, b, rtol: float = 1e-8, max_iter: int = 1000, check: bool = False):
+        """x with ||b - A x|| <= rtol ||b||; returns (x, info dict)."""
+        info = SolveInfo()
+        if _is_torch(b) and b.is_cuda:
+            import torch
+            bi = b.contiguous().to(torch.float64)
+            x = torch.empty_like(bi)
+            st = load().asm_solve(self._h, C.c_void_p(bi.data_ptr()), C.c_void_p(x.data_ptr()), rtol, max_iter, 1,
+                                  C.byref(info))
+        else:
+            bi = np.ascontiguousarray(b, dtype=np.float64)
+            x = np.empty_like(bi)
+            st = load().asm_solve(self._h, _host_ptr(bi), _host_ptr(x), rtol, max_iter, 0, C.byref(info))
+        if st not in (ASM_OK, 4) or (check and st != ASM_OK):
+            raise ASMError(st, "solve")
+        return x, info.as_dict()
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(load().asm_get_stats(self._h, C.byref(s)), "stats")
+        return s.as_dict()
+
+    def set_profiling(self, on: bool = True):
+        _check(load().asm_set_profiling(self._h, 1 if on else 0), "set_profiling")
+
+    def profile(self) -> dict:
+        p = Profile()
+        _check(load().asm_get_profile(self._h, C.byref(p)), "profile")
+        return p.as_dict()
+
+    def reset_profile(self):
+        _check(load().asm_reset_profile(self._h), "reset_profile")
+
+    # parity hooks -----------------------------------------------------------------------------
+    def local_info(self, s: int):
+        n, nnz, lv = C.c_int(), C.c_int(), C.c_int()
+        cnt = (C.c_int * 3)()
+        _check(load().asm_get_local_info(self._h, s, C.byref(n), C.byref(nnz), cnt, C.byref(lv)), "local_info")
+        return {"n": n.value, "nnzb": nnz.value, "counts": tuple(cnt), "levels": lv.value}
+
+    def local_map(self, s: int) -> np.ndarray:
+        m = np.empty(self.n_cells, dtype=np.int32)
+        _check(load().asm_get_local_map(self._h, s, _host_ptr(m)), "local_map")
+        return m
+
+    def local_matrix(self, s: int):
+        inf = self.local_info(s)
+        rp = np.empty(inf["n"] + 1, dtype=np.int32)
+        ci = np.empty(inf["nnzb"], dtype=np.int32)
+        v = np.empty((inf["nnzb"], 3, 3))
+        _check(load().asm_get_local_matrix(self._h, s, _host_ptr(rp), _host_ptr(ci), _host_ptr(v)), "local_matrix")
+        return rp, ci, v
+
+    def local_factors(self, s: int):
+        inf = self.local_info(s)
+        lu = np.empty((inf["nnzb"], 3, 3))
+        dp = np.empty((inf["n"], 3, 3))
+        _check(load().asm_get_local_factors(self._h, s, _host_ptr(lu), _host_ptr(dp)), "local_factors")
+        return lu, dp
+
+
+def solve_batch(solvers, bs, rtol: float = 1e-8, max_iter: int = 1000):
+    """Solve several factored systems in the same launches; returns ([x], [info])."""
+    import torch
+    n = len(solvers)
+    hs = (C.c_void_p * n)(*[s.handle for s in solvers])
+    on_dev = all(_is_torch(b) and b.is_cuda for b in bs)
+    if on_dev:
+        bi = [b.contiguous().to(torch.float64) for b in bs]
+        xs = [torch.empty_like(b) for b in bi]
+        bp = (C.c_void_p * n)(*[b.data_ptr() for b in bi])
+        xp = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+    else:
+        bi = [np.ascontiguousarray(b, dtype=np.float64) for b in bs]
+        xs = [np.empty_like(b) for b in bi]
+        bp = (C.c_void_p * n)(*[b.ctypes.data for b in bi])
+        xp = (C.c_void_p * n)(*[x.ctypes.data for x in xs])
+    infos = (SolveInfo * n)()
+    st = load().asm_solve_batch(hs, n, bp, xp, rtol, max_iter, 1 if on_dev else 0, infos)
+    if st not in (ASM_OK, 4):
+        raise ASMError(st, "solve_batch")
+    return xs, [i.as_dict() for i in infos]
+
+
+@dataclass
+class Problem:
+    """Convenience: a Solver set up for a grid system and partition."""
+    solver: Solver
+    n_cells: int
+
+
+def setup(system, px, py, pz, overlap=1, near_width=2, c_near=(2, 2, 2), far_mode="partition", c_far=None,
+          precision="fp64", restart=30, local_solver="colsum", flexible=-1, device=0, factor=True) -> Solver:
+    """Solver for a paper_1401_7227_gb300.synth.GridSystem."""
+    s = Solver(precision=precision, restart=restart, local_solver=local_solver, flexible=flexible, device=device)
+    s.set_grid(system.nx, system.ny, system.nz)
+    s.set_matrix(system.row_ptr, system.col_idx, system.vals)
+    s.set_partition(px, py, pz, overlap, near_width, c_near, far_mode, c_far)
+    if factor:
+        s.factor()
+    return s

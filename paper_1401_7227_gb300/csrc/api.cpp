@@ -1,0 +1,980 @@
+// C-ABI of libasm2 (include/asm2.h): handle state, device memory, factorisation and the batched
+// GMRES driver.  All arithmetic of the method runs in the CUDA kernels; the host only moves
+// data, builds the symbolic structure and sequences launches.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "asm2.h"
+#include "asm2_internal.h"
+#include "symbolic.h"
+
+using namespace asm2;
+
+namespace {
+
+struct CudaFail {
+    int status;
+};
+
+inline void ck(cudaError_t e) {
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw CudaFail{e == cudaErrorMemoryAllocation ? ASM_ERR_OOM : ASM_ERR_CUDA};
+    }
+}
+
+struct DBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DBuf() = default;
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    ~DBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    void alloc(size_t b) {
+        release();
+        if (b == 0) b = 16;
+        ck(cudaMalloc(&p, b));
+        bytes = b;
+    }
+    void zero(cudaStream_t st) { ck(cudaMemsetAsync(p, 0, bytes, st)); }
+    template <class T>
+    T* as() const {
+        return static_cast<T*>(p);
+    }
+    template <class T>
+    void upload(const std::vector<T>& v, cudaStream_t st) {
+        alloc(v.size() * sizeof(T));
+        if (!v.empty()) ck(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    }
+};
+
+}  // namespace
+
+struct asm_ctx {
+    asm_options opt;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int prec = 0;
+    int flexible = 0;
+    // grid / matrix
+    int nx = 0, ny = 0, nz = 0, N = 0;
+    bool has_grid = false, has_matrix = false, has_partition = false;
+    Pattern pat;
+    int nnzb = 0;
+    DBuf d_ell_val, d_ell_col, d_ell_loc, d_stage;
+    // partition / symbolic
+    Geom geom;
+    std::unique_ptr<SysSym> sym;
+    bool sym_valid = false;
+    bool factored = false;
+    // device preconditioner data
+    DBuf d_bcell, d_cptr, d_cloc, d_cval, d_boxsum;
+    DBuf d_slot, d_dpiv, d_aptr, d_aloc, d_acs;
+    DBuf d_fp;  // factor program arrays (one allocation, see upload_factor_program)
+    DBuf d_stream, d_pk_off_f, d_pk_src_f, d_pk_off_c, d_pk_src_c;
+    DBuf d_lv, d_rlists, d_y;
+    DBuf d_factdesc, d_subdesc_single;
+    DBuf d_err;
+    std::vector<FactDesc> fact_desc;
+    std::vector<SubDesc> sub_desc;   // sys = 0
+    std::vector<BoxItem> box_items;  // sys = 0
+    std::vector<long long> slot_base, stream_base, row_base;
+    long long pk_nf = 0, pk_nc = 0, total_slots = 0;
+    // Krylov workspace
+    int ws_m = -1, ws_flex = -1;
+    long long n3p = 0;
+    int nchunk = 0;
+    DBuf d_ws, d_scal, d_ctl, d_partial;
+    SysTab tab{};
+    DBuf d_tab1, d_vec1, d_row1, d_box1;
+    int n_vec1 = 0, n_row1 = 0;
+    // profiling
+    bool profiling = false;
+    asm_profile_info prof{};
+    // diagnostics
+    int err_sub = -1, err_row = -1;
+    double setup_ms = 0, factor_ms = 0;
+    std::string last_error;
+};
+
+namespace {
+
+int guard(asm_ctx* h, const std::function<int()>& f) {
+    try {
+        if (h) ck(cudaSetDevice(h->device));
+        return f();
+    } catch (const CudaFail& e) {
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        return ASM_ERR_OOM;
+    }
+}
+
+void sync(asm_ctx* h) { ck(cudaStreamSynchronize(h->stream)); }
+
+// copy between caller memory (host or device) and device memory, in stream order
+void copy_in(asm_ctx* h, void* dst, const void* src, size_t bytes, int on_device) {
+    ck(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+}
+void copy_out(asm_ctx* h, void* dst, const void* src, size_t bytes, int on_device) {
+    ck(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+}
+
+void fill_ell(asm_ctx* h, const double* vals, int on_device) {
+    const size_t vb = (size_t)h->nnzb * 9 * sizeof(double);
+    const double* src = vals;
+    if (!on_device) {
+        if (h->d_stage.bytes < vb) h->d_stage.alloc(vb);
+        copy_in(h, h->d_stage.p, vals, vb, 0);
+        src = h->d_stage.as<double>();
+    }
+    launch_ell_fill(src, h->d_ell_loc.as<int>(), h->nnzb, h->d_ell_val.as<double>(), h->pat.rows_pad, 0, h->stream);
+    ck(cudaGetLastError());
+    if (!on_device) sync(h);
+}
+
+// Upload the symbolic structure and build the per-subdomain descriptors.
+void upload_symbolic(asm_ctx* h) {
+    SysSym& S = *h->sym;
+    cudaStream_t st = h->stream;
+    const int K = (int)S.subs.size();
+    h->slot_base.assign(K + 1, 0);
+    h->stream_base.assign(K + 1, 0);
+    h->row_base.assign(K + 1, 0);
+    std::vector<long long> aloc_base(K + 1, 0), fp_base(K + 1, 0), rl_base(K + 1, 0), lv_base(K + 1, 0);
+    long long npf = 0, npc = 0;
+    for (int s = 0; s < K; s++) {
+        const SubSym& o = S.subs[s];
+        h->slot_base[s + 1] = h->slot_base[s] + o.nslot;
+        h->stream_base[s + 1] = h->stream_base[s] + (long long)((o.stream.size() + 255) / 256 * 256);
+        h->row_base[s + 1] = h->row_base[s] + o.n;
+        aloc_base[s + 1] = aloc_base[s] + (long long)o.aloc.size();
+        // factor program ints: lv_pos0, diag_of_pos, row_of_pos, tgt_lv, tgt, pp, ls_lv, pair, ls
+        long long fpi = (long long)o.lv_pos0.size() + o.diag_of_pos.size() + o.row_of_pos.size() + o.tgt_lv.size() +
+                        o.tgt.size() + o.pp.size() + o.ls_lv.size();
+        fpi = (fpi + 1) / 2 * 2;
+        fpi += (long long)o.pair.size() + (long long)o.ls.size();
+        fp_base[s + 1] = fp_base[s] + fpi;
+        long long rli = (long long)o.rptr.size() + o.rsrc.size() + o.rbox.size() + o.own_pos.size() + o.own_cell.size();
+        rl_base[s + 1] = rl_base[s] + rli;
+        lv_base[s + 1] = lv_base[s] + o.nlev;
+        npf += (long long)o.pk_off_f.size();
+        npc += (long long)o.pk_off_c.size();
+    }
+    h->total_slots = h->slot_base[K];
+    if (h->total_slots >= (1LL << 31) / 9 || aloc_base[K] >= (1LL << 31)) throw CudaFail{ASM_ERR_INVALID_ARG};
+    h->d_slot.alloc((size_t)h->total_slots * 9 * sizeof(double));
+    h->d_dpiv.alloc((size_t)h->row_base[K] * 9 * sizeof(double));
+    h->d_y.alloc((size_t)h->row_base[K] * 3 * sizeof(double));
+    // assembly lists (global offsets)
+    {
+        std::vector<int> aptr;
+        aptr.reserve(h->total_slots + 1);
+        std::vector<int> acs;
+        acs.reserve(h->total_slots);
+        for (int s = 0; s < K; s++) {
+            const SubSym& o = S.subs[s];
+            for (int t = 0; t < o.nslot; t++) {
+                aptr.push_back((int)(aloc_base[s] + o.aptr[t]));
+                acs.push_back(o.acs[t]);
+            }
+        }
+        aptr.push_back((int)aloc_base[K]);
+        h->d_aptr.upload(aptr, st);
+        h->d_acs.upload(acs, st);
+        h->d_aloc.alloc((size_t)aloc_base[K] * 4);
+        for (int s = 0; s < K; s++)
+            if (!S.subs[s].aloc.empty())
+                ck(cudaMemcpyAsync(h->d_aloc.as<int>() + aloc_base[s], S.subs[s].aloc.data(), S.subs[s].aloc.size() * 4,
+                                   cudaMemcpyHostToDevice, st));
+        sync(h);
+    }
+    // factor program
+    h->d_fp.alloc((size_t)fp_base[K] * 4);
+    h->fact_desc.assign(K, FactDesc{});
+    {
+        std::vector<int> buf;
+        for (int s = 0; s < K; s++) {
+            const SubSym& o = S.subs[s];
+            buf.clear();
+            int* base = h->d_fp.as<int>() + fp_base[s];
+            FactDesc& fd = h->fact_desc[s];
+            fd.sys = 0;
+            fd.nlev = o.nlev;
+            fd.n = o.n;
+            fd.slot = h->d_slot.as<double>() + h->slot_base[s] * 9;
+            fd.dpiv = h->d_dpiv.as<double>() + h->row_base[s] * 9;
+            auto put = [&](const std::vector<int>& v) {
+                const int* p = base + buf.size();
+                buf.insert(buf.end(), v.begin(), v.end());
+                return p;
+            };
+            fd.lv_pos0 = put(o.lv_pos0);
+            fd.diag_of_pos = put(o.diag_of_pos);
+            fd.row_of_pos = put(o.row_of_pos);
+            fd.tgt_lv = put(o.tgt_lv);
+            fd.tgt = put(o.tgt);
+            fd.pp = put(o.pp);
+            fd.ls_lv = put(o.ls_lv);
+            if (buf.size() % 2) buf.push_back(0);
+            fd.pair = reinterpret_cast<const int2*>(put(o.pair));
+            fd.ls = reinterpret_cast<const int2*>(put(o.ls));
+            ck(cudaMemcpyAsync(base, buf.data(), buf.size() * 4, cudaMemcpyHostToDevice, st));
+            sync(h);
+        }
+        h->d_factdesc.upload(h->fact_desc, st);
+    }
+    // streams + pack lists + level tables + restriction lists
+    h->d_stream.alloc((size_t)h->stream_base[K]);
+    h->d_lv.alloc((size_t)std::max<long long>(1, lv_base[K]) * sizeof(LevelInfo));
+    h->d_rlists.alloc((size_t)std::max<long long>(1, rl_base[K]) * 4);
+    std::vector<long long> offf, offc;
+    std::vector<int> srcf, srcc;
+    offf.reserve(npf);
+    srcf.reserve(npf);
+    offc.reserve(npc);
+    srcc.reserve(npc);
+    h->sub_desc.assign(K, SubDesc{});
+    for (int s = 0; s < K; s++) {
+        const SubSym& o = S.subs[s];
+        if (!o.stream.empty())
+            ck(cudaMemcpyAsync(h->d_stream.as<unsigned char>() + h->stream_base[s], o.stream.data(), o.stream.size(),
+                               cudaMemcpyHostToDevice, st));
+        if (o.nlev)
+            ck(cudaMemcpyAsync(h->d_lv.as<LevelInfo>() + lv_base[s], o.lv.data(), o.lv.size() * sizeof(LevelInfo),
+                               cudaMemcpyHostToDevice, st));
+        for (size_t i = 0; i < o.pk_off_f.size(); i++) {
+            offf.push_back(h->stream_base[s] + o.pk_off_f[i]);
+            srcf.push_back((int)(h->slot_base[s] + o.pk_src_f[i]));
+        }
+        for (size_t i = 0; i < o.pk_off_c.size(); i++) {
+            offc.push_back(h->stream_base[s] + o.pk_off_c[i]);
+            srcc.push_back((int)(h->slot_base[s] + o.pk_src_c[i]));
+        }
+        std::vector<int> rl;
+        rl.reserve(rl_base[s + 1] - rl_base[s]);
+        int* base = h->d_rlists.as<int>() + rl_base[s];
+        SubDesc& sd = h->sub_desc[s];
+        auto put = [&](const std::vector<int>& v) {
+            const int* p = base + rl.size();
+            rl.insert(rl.end(), v.begin(), v.end());
+            return p;
+        };
+        sd.sys = 0;
+        sd.n = o.n;
+        sd.nlev = o.nlev;
+        sd.n_own = (int)o.own_pos.size();
+        sd.prec = S.prec;
+        sd.lv = h->d_lv.as<LevelInfo>() + lv_base[s];
+        sd.stream = h->d_stream.as<unsigned char>() + h->stream_base[s];
+        sd.y = h->d_y.as<double>() + h->row_base[s] * 3;
+        sd.rptr = put(o.rptr);
+        sd.rsrc = put(o.rsrc);
+        sd.rbox = put(o.rbox);
+        sd.own_pos = put(o.own_pos);
+        sd.own_cell = put(o.own_cell);
+        if (!rl.empty()) ck(cudaMemcpyAsync(base, rl.data(), rl.size() * 4, cudaMemcpyHostToDevice, st));
+        sync(h);
+    }
+    h->pk_nf = (long long)offf.size();
+    h->pk_nc = (long long)offc.size();
+    h->d_pk_off_f.upload(offf, st);
+    h->d_pk_src_f.upload(srcf, st);
+    h->d_pk_off_c.upload(offc, st);
+    h->d_pk_src_c.upload(srcc, st);
+    // far boxes and coarse matrix
+    if (S.g.far_mode != 0) {
+        h->d_bcell.upload(S.bcell, st);
+        h->d_cptr.upload(S.cptr, st);
+        h->d_cloc.upload(S.cloc, st);
+        h->d_cval.alloc((size_t)std::max(1, S.nC) * 9 * sizeof(double));
+        h->d_boxsum.alloc((size_t)std::max(1, S.nboxes) * 3 * sizeof(double));
+        h->box_items.clear();
+        for (int b = 0; b < S.nboxes; b++)
+            h->box_items.push_back(BoxItem{0, b, S.bptr[b], S.bptr[b + 1], h->d_bcell.as<int>()});
+    } else {
+        h->d_cval.alloc(16);
+        h->d_boxsum.alloc(16);
+        h->box_items.clear();
+    }
+    h->d_subdesc_single.upload(h->sub_desc, st);
+    h->d_err.alloc(sizeof(FactErr));
+    sync(h);
+}
+
+// Krylov workspace and the single-system tables
+void ensure_workspace(asm_ctx* h) {
+    const int m = std::max(1, h->opt.restart);
+    const int flex = h->flexible;
+    if (h->ws_m == m && h->ws_flex == flex && h->d_ws.p) return;
+    const long long n3 = 3LL * h->N;
+    h->n3p = (n3 + VEC_CHUNK - 1) / VEC_CHUNK * VEC_CHUNK;
+    h->nchunk = (int)(h->n3p / VEC_CHUNK);
+    const int nslots = VV0 + m + 1 + (flex ? m : 0);
+    h->d_ws.alloc((size_t)nslots * h->n3p * sizeof(double));
+    h->d_ws.zero(h->stream);
+    const ScalLayout SL = ScalLayout::make(m);
+    h->d_scal.alloc((size_t)SL.n * sizeof(double));
+    h->d_scal.zero(h->stream);
+    h->d_ctl.alloc(C_NCTL * sizeof(int));
+    h->d_ctl.zero(h->stream);
+    h->d_partial.alloc((size_t)2 * h->nchunk * sizeof(double));
+    h->ws_m = m;
+    h->ws_flex = flex;
+    SysTab& t = h->tab;
+    t.ws = h->d_ws.as<double>();
+    t.n3p = h->n3p;
+    t.n3 = (int)n3;
+    t.n_cells = h->N;
+    t.m = m;
+    t.flexible = flex;
+    t.nchunk = h->nchunk;
+    t.scal = h->d_scal.as<double>();
+    t.ctl = h->d_ctl.as<int>();
+    t.partial = h->d_partial.as<double>();
+    t.ell_val = h->d_ell_val.as<double>();
+    t.ell_col = h->d_ell_col.as<int>();
+    t.ell_w = h->pat.ell_w;
+    t.rows_pad = h->pat.rows_pad;
+    t.boxsum = h->d_boxsum.as<double>();
+    std::vector<SysTab> tabs{t};
+    h->d_tab1.upload(tabs, h->stream);
+    std::vector<VecItem> vi;
+    for (int c = 0; c < h->nchunk; c++) vi.push_back(VecItem{0, c});
+    h->d_vec1.upload(vi, h->stream);
+    h->n_vec1 = (int)vi.size();
+    std::vector<RowItem> ri;
+    for (int r = 0; r < h->N; r += 256) ri.push_back(RowItem{0, r});
+    h->d_row1.upload(ri, h->stream);
+    h->n_row1 = (int)ri.size();
+    h->d_box1.upload(h->box_items, h->stream);
+    sync(h);
+}
+
+void set_ctl(asm_ctx* h, int apply_in, int apply_out, int spmv_in, int spmv_out, int spmv_b) {
+    int c[C_NCTL];
+    std::memset(c, 0, sizeof(c));
+    c[C_PHASE] = PH_DONE;
+    c[C_APPLY_IN] = apply_in;
+    c[C_APPLY_OUT] = apply_out;
+    c[C_SPMV_IN] = spmv_in;
+    c[C_SPMV_OUT] = spmv_out;
+    c[C_SPMV_B] = spmv_b;
+    ck(cudaMemcpyAsync(h->d_ctl.p, c, sizeof(c), cudaMemcpyHostToDevice, h->stream));
+    sync(h);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// Batch driver: all systems advance together; each kernel reads each system's own state.
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+struct Batch {
+    std::vector<asm_ctx*> hs;
+    DBuf d_tab, d_vec, d_row, d_box, d_sub, d_gather;
+    int nvec = 0, nrow = 0, nbox = 0, nsub = 0, prec = 0;
+    std::vector<int> host_ctl;
+    int* pinned = nullptr;
+    ~Batch() {
+        if (pinned) cudaFreeHost(pinned);
+    }
+};
+
+void build_batch(Batch& B, cudaStream_t st) {
+    std::vector<SysTab> tabs;
+    std::vector<VecItem> vi;
+    std::vector<RowItem> ri;
+    std::vector<BoxItem> bi;
+    std::vector<SubDesc> sd;
+    for (int k = 0; k < (int)B.hs.size(); k++) {
+        asm_ctx* h = B.hs[k];
+        tabs.push_back(h->tab);
+        for (int c = 0; c < h->nchunk; c++) vi.push_back(VecItem{k, c});
+        for (int r = 0; r < h->N; r += 256) ri.push_back(RowItem{k, r});
+        for (BoxItem b : h->box_items) {
+            b.sys = k;
+            bi.push_back(b);
+        }
+        for (SubDesc s : h->sub_desc) {
+            s.sys = k;
+            sd.push_back(s);
+        }
+    }
+    B.d_tab.upload(tabs, st);
+    B.d_vec.upload(vi, st);
+    B.d_row.upload(ri, st);
+    B.d_box.upload(bi, st);
+    B.d_sub.upload(sd, st);
+    B.nvec = (int)vi.size();
+    B.nrow = (int)ri.size();
+    B.nbox = (int)bi.size();
+    B.nsub = (int)sd.size();
+    ck(cudaMallocHost((void**)&B.pinned, sizeof(int) * C_NCTL * B.hs.size()));
+}
+
+// events bracketing the launch groups of one step: [prep | apply | post | spmv | mgs+finish]
+struct StepEvents {
+    cudaEvent_t e[6] = {};
+    bool live = false;
+    void create() {
+        for (auto& x : e) ck(cudaEventCreate(&x));
+        live = true;
+    }
+    ~StepEvents() {
+        if (live)
+            for (auto& x : e) cudaEventDestroy(x);
+    }
+};
+
+void launch_step(Batch& B, int kmax, cudaStream_t st, StepEvents* ev) {
+    const SysTab* tab = B.d_tab.as<SysTab>();
+    const VecItem* vi = B.d_vec.as<VecItem>();
+    if (ev) ck(cudaEventRecord(ev->e[0], st));
+    launch_prep(tab, vi, B.nvec, st);
+    if (ev) ck(cudaEventRecord(ev->e[1], st));
+    launch_boxsum(tab, B.d_box.as<BoxItem>(), B.nbox, st);
+    launch_apply(tab, B.d_sub.as<SubDesc>(), B.nsub, B.prec, st);
+    if (ev) ck(cudaEventRecord(ev->e[2], st));
+    launch_post(tab, vi, B.nvec, st);
+    if (ev) ck(cudaEventRecord(ev->e[3], st));
+    launch_spmv(tab, B.d_row.as<RowItem>(), B.nrow, st);
+    if (ev) ck(cudaEventRecord(ev->e[4], st));
+    for (int k = 0; k <= kmax; k++) launch_mgs(tab, vi, B.nvec, k, st);
+    launch_finish(tab, vi, B.nvec, st);
+    if (ev) ck(cudaEventRecord(ev->e[5], st));
+    ck(cudaGetLastError());
+    const long long n = 7 + kmax + 1;
+    for (asm_ctx* h : B.hs) h->prof.kernel_launches += n;
+}
+
+float elapsed(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0;
+    ck(cudaEventElapsedTime(&ms, a, b));
+    return ms;
+}
+
+void read_ctl(Batch& B, cudaStream_t st) {
+    for (size_t k = 0; k < B.hs.size(); k++)
+        ck(cudaMemcpyAsync(B.pinned + k * C_NCTL, B.hs[k]->d_ctl.p, sizeof(int) * C_NCTL, cudaMemcpyDeviceToHost, st));
+    ck(cudaStreamSynchronize(st));
+}
+
+int run_gmres(std::vector<asm_ctx*>& hs, const double* const* b, double* const* x, double rtol, int max_iter,
+              int on_device, asm_solve_info* infos) {
+    cudaStream_t st = hs[0]->stream;
+    Batch B;
+    B.hs = hs;
+    B.prec = hs[0]->prec;
+    for (size_t k = 0; k < hs.size(); k++) {
+        asm_ctx* h = hs[k];
+        ensure_workspace(h);
+        const ScalLayout SL = ScalLayout::make(h->ws_m);
+        // b into slot VB, control words and tolerance
+        copy_in(h, h->d_ws.as<double>() + (long long)VB * h->n3p, b[k], sizeof(double) * 3 * (size_t)h->N, on_device);
+        int c[C_NCTL];
+        std::memset(c, 0, sizeof(c));
+        c[C_PHASE] = PH_INIT;
+        c[C_APPLY_IN] = -1;
+        c[C_SPMV_IN] = -1;
+        c[C_MAXIT] = max_iter;
+        c[C_STATUS] = ASM_ERR_NOT_CONVERGED;
+        ck(cudaMemcpyAsync(h->d_ctl.p, c, sizeof(c), cudaMemcpyHostToDevice, st));
+        double tol = rtol;
+        ck(cudaMemcpyAsync(h->d_scal.as<double>() + SL.tol, &tol, sizeof(double), cudaMemcpyHostToDevice, st));
+        ck(cudaStreamSynchronize(st));
+    }
+    build_batch(B, st);
+    {
+        // initial step: x = 0, r = b, beta = ||b||
+        const SysTab* tab = B.d_tab.as<SysTab>();
+        const VecItem* vi = B.d_vec.as<VecItem>();
+        launch_init(tab, vi, B.nvec, st);
+        launch_mgs(tab, vi, B.nvec, 0, st);
+        launch_finish(tab, vi, B.nvec, st);
+        ck(cudaGetLastError());
+        for (asm_ctx* h : hs) h->prof.kernel_launches += 3;
+    }
+    const bool prof = hs[0]->profiling;
+    StepEvents ev;
+    if (prof) ev.create();
+    bool pending = false;
+    int pending_applies = 0;
+    const int guard_steps = 4 * max_iter + 64;
+    for (int step = 0; step < guard_steps; step++) {
+        read_ctl(B, st);
+        if (pending) {
+            asm_profile_info& P = hs[0]->prof;
+            P.ortho_ms += elapsed(ev.e[0], ev.e[1]) + elapsed(ev.e[2], ev.e[3]) + elapsed(ev.e[4], ev.e[5]);
+            P.apply_ms += elapsed(ev.e[1], ev.e[2]);
+            P.spmv_ms += elapsed(ev.e[3], ev.e[4]);
+            P.apply_launches += pending_applies;
+            pending = false;
+        }
+        int kmax = -1;
+        bool any = false;
+        for (size_t k = 0; k < hs.size(); k++) {
+            const int* c = B.pinned + k * C_NCTL;
+            if (c[C_PHASE] == PH_DONE) continue;
+            any = true;
+            if (c[C_PHASE] == PH_ARNOLDI) kmax = std::max(kmax, c[C_J] + 1);
+            else kmax = std::max(kmax, 0);
+        }
+        if (!any) break;
+        pending_applies = 0;
+        for (size_t k = 0; k < hs.size(); k++) {
+            const int* c = B.pinned + k * C_NCTL;
+            if (c[C_APPLY_IN] >= 0 && c[C_PHASE] != PH_DONE) pending_applies++;
+        }
+        launch_step(B, kmax, st, prof ? &ev : nullptr);
+        pending = prof;
+    }
+    read_ctl(B, st);
+    int worst = ASM_OK;
+    for (size_t k = 0; k < hs.size(); k++) {
+        asm_ctx* h = hs[k];
+        const int* c = B.pinned + k * C_NCTL;
+        const ScalLayout SL = ScalLayout::make(h->ws_m);
+        double sc[2];
+        ck(cudaMemcpyAsync(sc, h->d_scal.as<double>() + SL.bnorm, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        copy_out(h, x[k], h->d_ws.as<double>() + (long long)VX * h->n3p, sizeof(double) * 3 * (size_t)h->N, on_device);
+        ck(cudaStreamSynchronize(st));
+        int status = c[C_PHASE] == PH_DONE ? c[C_STATUS] : ASM_ERR_NOT_CONVERGED;
+        if (infos) {
+            infos[k].iterations = c[C_ITERS];
+            infos[k].restarts = c[C_RESTARTS];
+            infos[k].converged = c[C_CONVERGED];
+            infos[k].status = status;
+            infos[k].rel_residual = sc[0] > 0 ? sc[1] / sc[0] : 0.0;
+        }
+        if (status != ASM_OK) worst = status;
+    }
+    return worst;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------------------------
+extern "C" {
+
+void asm_default_options(asm_options* opt) {
+    if (!opt) return;
+    opt->precision = ASM_PREC_FP64;
+    opt->krylov = ASM_KRYLOV_GMRES;
+    opt->restart = 30;
+    opt->local_solver = ASM_LOCAL_BILU0_COLSUM;
+    opt->flexible = -1;
+    opt->device = 0;
+}
+
+const char* asm_error_string(int s) {
+    switch (s) {
+        case ASM_OK: return "ok";
+        case ASM_ERR_INVALID_ARG: return "invalid argument";
+        case ASM_ERR_PATTERN: return "block pattern not structurally symmetric or missing a diagonal block";
+        case ASM_ERR_ZERO_PIVOT: return "singular 3x3 pivot in a local factorisation";
+        case ASM_ERR_NOT_CONVERGED: return "not converged within max_iter";
+        case ASM_ERR_OOM: return "out of memory";
+        case ASM_ERR_CUDA: return "CUDA runtime error";
+        case ASM_ERR_TIMEOUT: return "bounded device wait expired";
+        case ASM_ERR_STATE: return "call out of order";
+        default: return "unknown status";
+    }
+}
+
+int asm_create(asm_handle* out, const asm_options* opt, void* cuda_stream) {
+    if (!out) return ASM_ERR_INVALID_ARG;
+    *out = nullptr;
+    asm_options o;
+    asm_default_options(&o);
+    if (opt) o = *opt;
+    if (o.precision < 0 || o.precision > 2 || o.krylov < 0 || o.krylov > 1 || o.restart < 1 || o.restart > 512 ||
+        o.local_solver < 0 || o.local_solver > 1 || o.flexible < -1 || o.flexible > 1)
+        return ASM_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+        cudaGetLastError();
+        return ASM_ERR_CUDA;
+    }
+    if (o.device < 0 || o.device >= ndev) return ASM_ERR_INVALID_ARG;
+    asm_ctx* h = new (std::nothrow) asm_ctx();
+    if (!h) return ASM_ERR_OOM;
+    h->opt = o;
+    h->device = o.device;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->prec = o.precision;
+    h->flexible = o.flexible >= 0 ? o.flexible : (o.precision == ASM_PREC_FP64 ? 0 : 1);
+    int st = guard(h, [&] { return ASM_OK; });
+    if (st) {
+        delete h;
+        return st;
+    }
+    *out = h;
+    return ASM_OK;
+}
+
+int asm_destroy(asm_handle h) {
+    if (!h) return ASM_OK;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    delete h;
+    return ASM_OK;
+}
+
+int asm_set_grid(asm_handle h, int nx, int ny, int nz) {
+    if (!h || nx < 1 || ny < 1 || nz < 1 || (long long)nx * ny * nz > (1LL << 27)) return ASM_ERR_INVALID_ARG;
+    h->nx = nx;
+    h->ny = ny;
+    h->nz = nz;
+    h->N = nx * ny * nz;
+    h->has_grid = true;
+    h->has_matrix = false;
+    h->sym_valid = false;
+    h->factored = false;
+    return ASM_OK;
+}
+
+int asm_set_matrix_bsr(asm_handle h, int n_cells, int nnzb, const int* row_ptr, const int* col_idx,
+                       const double* vals, int on_device) {
+    if (!h || !row_ptr || !col_idx || !vals) return ASM_ERR_INVALID_ARG;
+    if (!h->has_grid) return ASM_ERR_STATE;
+    if (n_cells != h->N || nnzb < n_cells) return ASM_ERR_INVALID_ARG;
+    return guard(h, [&]() -> int {
+        Pattern P;
+        std::string e = build_pattern(n_cells, row_ptr, col_idx, nnzb, P);
+        if (!e.empty()) {
+            h->last_error = e;
+            return e.rfind("pattern", 0) == 0 ? ASM_ERR_PATTERN : ASM_ERR_INVALID_ARG;
+        }
+        h->pat = std::move(P);
+        h->nnzb = nnzb;
+        h->d_ell_val.alloc((size_t)h->pat.ell_w * 9 * h->pat.rows_pad * sizeof(double));
+        h->d_ell_val.zero(h->stream);
+        h->d_ell_col.upload(h->pat.ell_col, h->stream);
+        h->d_ell_loc.upload(h->pat.ell_loc, h->stream);
+        fill_ell(h, vals, on_device);
+        sync(h);
+        h->has_matrix = true;
+        h->sym_valid = false;
+        h->factored = false;
+        h->ws_m = -1;
+        return ASM_OK;
+    });
+}
+
+int asm_update_values(asm_handle h, const double* vals, int on_device) {
+    if (!h || !vals) return ASM_ERR_INVALID_ARG;
+    if (!h->has_matrix) return ASM_ERR_STATE;
+    return guard(h, [&]() -> int {
+        fill_ell(h, vals, on_device);
+        sync(h);
+        h->factored = false;
+        return ASM_OK;
+    });
+}
+
+int asm_set_partition_boxes(asm_handle h, int px, int py, int pz, int overlap, int near_width, const int* c_near,
+                            int far_mode, const int* c_far) {
+    if (!h) return ASM_ERR_INVALID_ARG;
+    if (!h->has_grid) return ASM_ERR_STATE;
+    if (px < 1 || py < 1 || pz < 1 || px > h->nx || py > h->ny || pz > h->nz || overlap < 0 || near_width < 0 ||
+        far_mode < 0 || far_mode > 2)
+        return ASM_ERR_INVALID_ARG;
+    Geom g;
+    g.nx = h->nx;
+    g.ny = h->ny;
+    g.nz = h->nz;
+    g.px = px;
+    g.py = py;
+    g.pz = pz;
+    g.ov = overlap;
+    g.nw = near_width;
+    if (near_width > 0) {
+        if (!c_near || c_near[0] < 1 || c_near[1] < 1 || c_near[2] < 1) return ASM_ERR_INVALID_ARG;
+        for (int d = 0; d < 3; d++) g.cn[d] = c_near[d];
+    }
+    g.far_mode = far_mode;
+    if (far_mode == ASM_FAR_BOXES) {
+        if (!c_far || c_far[0] < 1 || c_far[1] < 1 || c_far[2] < 1) return ASM_ERR_INVALID_ARG;
+        for (int d = 0; d < 3; d++) g.cf[d] = c_far[d];
+    }
+    h->geom = g;
+    h->has_partition = true;
+    h->sym_valid = false;
+    h->factored = false;
+    return ASM_OK;
+}
+
+int asm_factor(asm_handle h) {
+    if (!h) return ASM_ERR_INVALID_ARG;
+    if (!h->has_matrix || !h->has_partition) return ASM_ERR_STATE;
+    return guard(h, [&]() -> int {
+        h->err_sub = h->err_row = -1;
+        if (!h->sym_valid) {
+            auto t0 = std::chrono::steady_clock::now();
+            h->sym.reset(new SysSym());
+            std::string e = build_symbolic(h->geom, h->pat, h->prec, h->opt.local_solver == ASM_LOCAL_BILU0_COLSUM ? 1 : 0,
+                                           *h->sym, 0);
+            if (!e.empty()) {
+                h->last_error = e;
+                h->sym.reset();
+                return e.find("pattern") != std::string::npos ? ASM_ERR_PATTERN : ASM_ERR_INVALID_ARG;
+            }
+            upload_symbolic(h);
+            h->sym_valid = true;
+            h->ws_m = -1;
+            h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        }
+        SysSym& S = *h->sym;
+        cudaEvent_t e0, e1;
+        ck(cudaEventCreate(&e0));
+        ck(cudaEventCreate(&e1));
+        ck(cudaEventRecord(e0, h->stream));
+        if (S.g.far_mode != 0)
+            launch_coarse(h->d_cptr.as<int>(), h->d_cloc.as<int>(), h->d_ell_val.as<double>(), h->pat.rows_pad,
+                          h->d_cval.as<double>(), S.nC, h->stream);
+        launch_assemble(h->d_aptr.as<int>(), h->d_aloc.as<int>(), h->d_acs.as<int>(), h->d_ell_val.as<double>(),
+                        h->pat.rows_pad, h->d_cval.as<double>(), h->d_slot.as<double>(), h->total_slots, h->stream);
+        h->d_err.zero(h->stream);
+        launch_factor(h->d_factdesc.as<FactDesc>(), (int)S.subs.size(), h->d_err.as<FactErr>(), nullptr, h->stream);
+        launch_pack(h->d_pk_off_f.as<long long>(), h->d_pk_src_f.as<int>(), h->pk_nf, h->prec,
+                    h->d_stream.as<unsigned char>(), h->d_slot.as<double>(), h->stream);
+        launch_pack(h->d_pk_off_c.as<long long>(), h->d_pk_src_c.as<int>(), h->pk_nc, 0, h->d_stream.as<unsigned char>(),
+                    h->d_slot.as<double>(), h->stream);
+        ck(cudaGetLastError());
+        ck(cudaEventRecord(e1, h->stream));
+        FactErr fe;
+        ck(cudaMemcpyAsync(&fe, h->d_err.p, sizeof(fe), cudaMemcpyDeviceToHost, h->stream));
+        sync(h);
+        float ms = 0;
+        ck(cudaEventElapsedTime(&ms, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        h->factor_ms = ms;
+        h->prof.factor_ms += ms;
+        h->prof.kernel_launches += 5;
+        if (fe.flag) {
+            h->err_sub = fe.sub;
+            h->err_row = fe.row;
+            h->factored = false;
+            return ASM_ERR_ZERO_PIVOT;
+        }
+        h->factored = true;
+        return ASM_OK;
+    });
+}
+
+int asm_apply_precond(asm_handle h, const double* r, double* z, int on_device) {
+    if (!h || !r || !z) return ASM_ERR_INVALID_ARG;
+    if (!h->factored) return ASM_ERR_STATE;
+    return guard(h, [&]() -> int {
+        ensure_workspace(h);
+        const size_t bytes = sizeof(double) * 3 * (size_t)h->N;
+        double* in = h->d_ws.as<double>() + (long long)VU * h->n3p;
+        double* out = h->d_ws.as<double>() + (long long)VZ * h->n3p;
+        copy_in(h, in, r, bytes, on_device);
+        set_ctl(h, VU, VZ, -1, -1, -1);
+        launch_boxsum(h->d_tab1.as<SysTab>(), h->d_box1.as<BoxItem>(), (int)h->box_items.size(), h->stream);
+        launch_apply(h->d_tab1.as<SysTab>(), h->d_subdesc_single.as<SubDesc>(), (int)h->sub_desc.size(), h->prec,
+                     h->stream);
+        ck(cudaGetLastError());
+        h->prof.kernel_launches += 2;
+        copy_out(h, z, out, bytes, on_device);
+        sync(h);
+        return ASM_OK;
+    });
+}
+
+int asm_spmv(asm_handle h, const double* x, double* y, int on_device) {
+    if (!h || !x || !y) return ASM_ERR_INVALID_ARG;
+    if (!h->has_matrix) return ASM_ERR_STATE;
+    return guard(h, [&]() -> int {
+        if (!h->sym_valid) {
+            // SpMV needs only A; give it a workspace without a preconditioner
+            h->box_items.clear();
+            if (!h->d_boxsum.p) h->d_boxsum.alloc(16);
+        }
+        ensure_workspace(h);
+        const size_t bytes = sizeof(double) * 3 * (size_t)h->N;
+        double* in = h->d_ws.as<double>() + (long long)VU * h->n3p;
+        double* out = h->d_ws.as<double>() + (long long)VZ * h->n3p;
+        copy_in(h, in, x, bytes, on_device);
+        set_ctl(h, -1, -1, VU, VZ, -1);
+        launch_spmv(h->d_tab1.as<SysTab>(), h->d_row1.as<RowItem>(), h->n_row1, h->stream);
+        ck(cudaGetLastError());
+        h->prof.kernel_launches += 1;
+        copy_out(h, y, out, bytes, on_device);
+        sync(h);
+        return ASM_OK;
+    });
+}
+
+int asm_solve(asm_handle h, const double* b, double* x, double rtol, int max_iter, int on_device,
+              asm_solve_info* info) {
+    if (!h || !b || !x || !(rtol >= 0.0) || max_iter < 1) return ASM_ERR_INVALID_ARG;
+    if (!h->factored) return ASM_ERR_STATE;
+    if (h->opt.krylov != ASM_KRYLOV_GMRES) return ASM_ERR_INVALID_ARG;
+    return guard(h, [&]() -> int {
+        std::vector<asm_ctx*> hs{h};
+        const double* bs[1] = {b};
+        double* xs[1] = {x};
+        return run_gmres(hs, bs, xs, rtol, max_iter, on_device, info);
+    });
+}
+
+int asm_solve_batch(asm_handle* hs, int n, const double* const* b, double* const* x, double rtol, int max_iter,
+                    int on_device, asm_solve_info* infos) {
+    if (!hs || n < 1 || !b || !x || !(rtol >= 0.0) || max_iter < 1) return ASM_ERR_INVALID_ARG;
+    std::vector<asm_ctx*> v(hs, hs + n);
+    for (asm_ctx* h : v) {
+        if (!h) return ASM_ERR_INVALID_ARG;
+        if (!h->factored) return ASM_ERR_STATE;
+        if (h->device != v[0]->device || h->stream != v[0]->stream || h->prec != v[0]->prec ||
+            h->opt.krylov != ASM_KRYLOV_GMRES)
+            return ASM_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < n; i++)
+        for (int k = i + 1; k < n; k++)
+            if (v[i] == v[k]) return ASM_ERR_INVALID_ARG;
+    return guard(v[0], [&]() -> int { return run_gmres(v, b, x, rtol, max_iter, on_device, infos); });
+}
+
+int asm_get_stats(asm_handle h, asm_stats* st) {
+    if (!h || !st) return ASM_ERR_INVALID_ARG;
+    std::memset(st, 0, sizeof(*st));
+    st->n_cells = h->N;
+    st->matrix_bytes = (long long)h->nnzb * (72 + 4);
+    if (h->sym) {
+        const SysSym& S = *h->sym;
+        st->n_sub = (int)S.subs.size();
+        st->local_rows = S.total_rows;
+        st->max_local_rows = S.max_n;
+        st->max_levels = S.max_lev;
+        st->local_blocks = S.total_slots;
+        long long fb = 0, ib = 0;
+        for (const SubSym& o : S.subs) {
+            fb += (long long)o.stream.size() + (long long)o.lv.size() * sizeof(LevelInfo);
+            ib += o.apply_index_bytes;
+        }
+        st->factor_bytes = fb;
+        st->apply_index_bytes = ib;
+        const long long wf = S.prec == 0 ? 8 : (S.prec == 1 ? 4 : 2);
+        long long ab = 48LL * h->N;
+        for (const SubSym& o : S.subs)
+            for (int p = 0; p < o.n; p++) {
+                const long long w = p < o.nf ? wf : 8;
+                const long long ne = o.prp[p + 1] - o.prp[p] - 1;
+                ab += ne * (9 * w + 4) + 9 * w;
+            }
+        st->alg_apply_bytes = ab;
+    }
+    st->setup_ms = h->setup_ms;
+    st->factor_ms = h->factor_ms;
+    return ASM_OK;
+}
+
+int asm_set_profiling(asm_handle h, int enable) {
+    if (!h) return ASM_ERR_INVALID_ARG;
+    h->profiling = enable != 0;
+    return ASM_OK;
+}
+
+int asm_get_profile(asm_handle h, asm_profile_info* p) {
+    if (!h || !p) return ASM_ERR_INVALID_ARG;
+    *p = h->prof;
+    return ASM_OK;
+}
+
+int asm_reset_profile(asm_handle h) {
+    if (!h) return ASM_ERR_INVALID_ARG;
+    h->prof = asm_profile_info{};
+    return ASM_OK;
+}
+
+int asm_get_error_location(asm_handle h, int* sub, int* row) {
+    if (!h) return ASM_ERR_INVALID_ARG;
+    if (sub) *sub = h->err_sub;
+    if (row) *row = h->err_row;
+    return ASM_OK;
+}
+
+int asm_get_local_info(asm_handle h, int s, int* n, int* nnzb, int* counts, int* n_levels) {
+    if (!h || !h->sym_valid || s < 0 || s >= (int)h->sym->subs.size()) return ASM_ERR_INVALID_ARG;
+    const SubSym& o = h->sym->subs[s];
+    if (n) *n = o.n;
+    if (nnzb) *nnzb = o.nslot;
+    if (counts) {
+        counts[0] = o.nf;
+        counts[1] = o.nn;
+        counts[2] = o.nfar;
+    }
+    if (n_levels) *n_levels = o.nlev;
+    return ASM_OK;
+}
+
+int asm_get_local_map(asm_handle h, int s, int* map) {
+    if (!h || !map || !h->sym_valid || s < 0 || s >= (int)h->sym->subs.size()) return ASM_ERR_INVALID_ARG;
+    std::vector<int> m;
+    local_map(*h->sym, s, m);
+    std::memcpy(map, m.data(), m.size() * sizeof(int));
+    return ASM_OK;
+}
+
+int asm_get_local_matrix(asm_handle h, int s, int* row_ptr, int* col_idx, double* vals) {
+    if (!h || !h->sym_valid || s < 0 || s >= (int)h->sym->subs.size()) return ASM_ERR_INVALID_ARG;
+    const SubSym& o = h->sym->subs[s];
+    if (row_ptr) std::memcpy(row_ptr, o.prp.data(), o.prp.size() * sizeof(int));
+    if (col_idx) std::memcpy(col_idx, o.pci.data(), o.pci.size() * sizeof(int));
+    if (!vals) return ASM_OK;
+    return guard(h, [&]() -> int {
+        // re-assemble this subdomain's slots into a scratch buffer (the live slots hold factors)
+        DBuf tmp;
+        tmp.alloc((size_t)o.nslot * 9 * sizeof(double));
+        std::vector<int> aptr(o.aptr.begin(), o.aptr.end());
+        DBuf dap, dal, dac;
+        dap.upload(aptr, h->stream);
+        dal.upload(o.aloc, h->stream);
+        dac.upload(o.acs, h->stream);
+        if (h->sym->g.far_mode != 0)
+            launch_coarse(h->d_cptr.as<int>(), h->d_cloc.as<int>(), h->d_ell_val.as<double>(), h->pat.rows_pad,
+                          h->d_cval.as<double>(), h->sym->nC, h->stream);
+        launch_assemble(dap.as<int>(), dal.as<int>(), dac.as<int>(), h->d_ell_val.as<double>(), h->pat.rows_pad,
+                        h->d_cval.as<double>(), tmp.as<double>(), o.nslot, h->stream);
+        ck(cudaGetLastError());
+        ck(cudaMemcpyAsync(vals, tmp.p, (size_t)o.nslot * 9 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        sync(h);
+        return ASM_OK;
+    });
+}
+
+int asm_get_local_factors(asm_handle h, int s, double* lu, double* dpiv) {
+    if (!h || !h->sym_valid || s < 0 || s >= (int)h->sym->subs.size()) return ASM_ERR_INVALID_ARG;
+    if (!h->factored) return ASM_ERR_STATE;
+    const SubSym& o = h->sym->subs[s];
+    return guard(h, [&]() -> int {
+        if (lu)
+            ck(cudaMemcpyAsync(lu, h->d_slot.as<double>() + h->slot_base[s] * 9, (size_t)o.nslot * 9 * sizeof(double),
+                               cudaMemcpyDeviceToHost, h->stream));
+        if (dpiv)
+            ck(cudaMemcpyAsync(dpiv, h->d_dpiv.as<double>() + h->row_base[s] * 9, (size_t)o.n * 9 * sizeof(double),
+                               cudaMemcpyDeviceToHost, h->stream));
+        sync(h);
+        return ASM_OK;
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,180 @@
+// Internal declarations shared by the host runtime and the CUDA kernels of libasm2.
+//
+// Everything on the device is described by small tables of absolute pointers, so one kernel
+// launch can work on any mix of systems: a single solve is a batch of one system.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace asm2 {
+
+// ---------------------------------------------------------------------------------------------
+// Krylov workspace layout.  Each system owns one device block of vectors of n3p doubles
+// (n3 = 3 * n_cells rounded up to VEC_CHUNK), addressed by slot number.
+// ---------------------------------------------------------------------------------------------
+constexpr int VEC_CHUNK = 2048;   // elements per vector work item (256 threads x 8)
+constexpr int VEC_THREADS = 256;
+enum VecSlot { VX = 0, VB = 1, VR = 2, VW = 3, VZ = 4, VU = 5, VV0 = 6 };  // V_k = VV0 + k; Z_k after V
+
+// GMRES phases of one system
+enum Phase { PH_DONE = 0, PH_ARNOLDI = 1, PH_RESTART = 2, PH_INIT = 3 };
+
+// Per-system control words (device, int32), written by the state kernels.
+enum Ctl {
+    C_PHASE = 0,
+    C_J,          // Arnoldi index j of the step in progress
+    C_JEND,       // columns of H used by the pending update
+    C_ITERS,      // preconditioned mat-vecs so far
+    C_RESTARTS,
+    C_STATUS,     // asm_status of the system
+    C_CONVERGED,
+    C_APPLY_IN,   // vector slot fed to the preconditioner (-1: skip the apply)
+    C_APPLY_OUT,
+    C_SPMV_IN,    // vector slot of the SpMV input (-1: skip)
+    C_SPMV_OUT,
+    C_SPMV_B,     // slot of b for y = b - A x, or -1 for y = A x
+    C_MAXIT,
+    C_CNT_RED,    // arrival counter of the chunk reduction in flight
+    C_CNT_FIN,    // arrival counter of the finishing kernel
+    C_BREAKDOWN,
+    C_NCTL = 16
+};
+
+// Per-system scalars (device, double) at fixed offsets; H is (m+1) x m row-major.
+struct ScalLayout {
+    int bnorm, beta, tol, w0, hn, red0, red1, H, cs, sn, g, y, n;
+    __host__ __device__ static ScalLayout make(int m) {
+        ScalLayout L;
+        int o = 0;
+        L.bnorm = o++;
+        L.beta = o++;
+        L.tol = o++;
+        L.w0 = o++;
+        L.hn = o++;
+        L.red0 = o++;
+        L.red1 = o++;
+        L.H = o;
+        o += (m + 1) * m;
+        L.cs = o;
+        o += m;
+        L.sn = o;
+        o += m;
+        L.g = o;
+        o += m + 1;
+        L.y = o;
+        o += m;
+        L.n = o;
+        return L;
+    }
+};
+
+// Per-system table (device copy).  Pointers are absolute.
+struct SysTab {
+    double* ws;          // vector workspace base (slots of n3p doubles)
+    long long n3p;       // padded vector length
+    int n3;              // 3 * n_cells
+    int n_cells;
+    int m;               // GMRES restart length
+    int flexible;        // keep Z_k = B^{-1} V_k (slots after V)
+    int nchunk;          // vector work items of this system
+    double* scal;        // scalars (ScalLayout)
+    int* ctl;            // control words (Ctl)
+    double* partial;     // [2 * nchunk] chunk partial sums
+    // A in ELL form: slot w, element t of row r at ell_val[(w*9 + t) * rows_pad + r]
+    const double* ell_val;
+    const int* ell_col;  // [w * rows_pad + r]; padding slots point at r with zero values
+    int ell_w;
+    int rows_pad;
+    // preconditioner
+    double* boxsum;      // [n_boxes * 3] far-box sums of the apply input
+};
+
+// Work items
+struct VecItem {   // VEC_CHUNK elements [e0, e0 + VEC_CHUNK) of system sys; chunk index within system
+    int sys, chunk;
+};
+struct RowItem {   // rows [r0, r0 + 256) of system sys
+    int sys, r0;
+};
+struct BoxItem {   // far box `box` of system sys: cells bcell[b0 .. b1)
+    int sys, box, b0, b1;
+    const int* bcell;
+};
+
+// One wavefront level of a local factor.  Rows of the level have consecutive positions:
+// nf fine rows first, then nc lump rows.  Forward/backward segments are byte offsets into the
+// subdomain's factor stream; every array inside a segment starts on a 16-byte boundary.
+struct LevelInfo {
+    int pos0, nf, nc;
+    int eLf, eLc, eUf, eUc;
+    int pad_;
+    long long fwd_off, bwd_off;
+};
+
+// One subdomain work item of the preconditioner apply.
+struct SubDesc {
+    int sys;
+    int n;            // local rows
+    int nlev;
+    int n_own;
+    int prec;         // storage of the fine-row factors: 0 f64, 1 f32, 2 f16
+    int pad_;
+    const LevelInfo* lv;
+    const unsigned char* stream;
+    double* y;        // scratch local vector [n * 3], by position
+    const int* rptr;  // [n + 1] restriction sources by position
+    const int* rsrc;  // >= 0: + r[cell]; < 0: - r[~cell]
+    const int* rbox;  // [n] far box whose sum is added first, or -1
+    const int* own_pos;
+    const int* own_cell;
+};
+
+// One subdomain work item of the numeric factorisation (slot values in FP64).
+struct FactDesc {
+    int sys;
+    int nlev;
+    int n;
+    int pad_;
+    double* slot;           // [nslot * 9] assembled values, factored in place
+    double* dpiv;           // [n * 9] final pivot blocks, by local row
+    const int* lv_pos0;     // [nlev + 1] position ranges of the levels
+    const int* diag_of_pos; // [n] slot of the diagonal block of each position
+    const int* row_of_pos;  // [n]
+    const int* tgt_lv;      // [nlev + 1] ranges into tgt
+    const int* tgt;         // target slots finalised at each level
+    const int* pp;          // [ntgt + 1] pair ranges
+    const int2* pair;       // (L slot, U slot) to subtract, in the right-looking update order
+    const int* ls_lv;       // [nlev + 1] ranges into ls
+    const int2* ls;         // (L slot, diagonal slot of its column): L = A * D^{-1}
+};
+
+// Device error record of the factorisation (first singular pivot)
+struct FactErr {
+    int flag, sub, row, pad_;
+};
+
+// ---------------------------------------------------------------------------------------------
+// Kernel launchers (kernels.cu)
+// ---------------------------------------------------------------------------------------------
+void launch_assemble(const int* aptr, const int* aloc, const int* acs, const double* ell_val, int rows_pad,
+                     const double* cval, double* slot, long long nslot, cudaStream_t st);
+void launch_coarse(const int* cptr, const int* cloc, const double* ell_val, int rows_pad, double* cval, int nc,
+                   cudaStream_t st);
+void launch_factor(const FactDesc* fd, int nsub, FactErr* err, const int* sub_ids, cudaStream_t st);
+void launch_pack(const long long* off, const int* src, long long n, int prec, unsigned char* stream_base,
+                 const double* slot_base, cudaStream_t st);
+void launch_ell_fill(const double* bsr_vals, const int* ell_loc, long long nnzb, double* ell_val, int rows_pad,
+                     int on_device_layout, cudaStream_t st);
+
+void launch_boxsum(const SysTab* st_tab, const BoxItem* items, int nitems, cudaStream_t st);
+void launch_apply(const SysTab* st_tab, const SubDesc* subs, int nsub, int prec, cudaStream_t st);
+void launch_spmv(const SysTab* st_tab, const RowItem* items, int nitems, cudaStream_t st);
+
+void launch_init(const SysTab* tab, const VecItem* items, int nitems, cudaStream_t st);
+void launch_prep(const SysTab* tab, const VecItem* items, int nitems, cudaStream_t st);
+void launch_post(const SysTab* tab, const VecItem* items, int nitems, cudaStream_t st);
+void launch_mgs(const SysTab* tab, const VecItem* items, int nitems, int k, cudaStream_t st);
+void launch_finish(const SysTab* tab, const VecItem* items, int nitems, cudaStream_t st);
+
+}  // namespace asm2
