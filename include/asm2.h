@@ -181,6 +181,15 @@ int asm_solve_batch(asm_handle* hs, int n, const double* const* b, double* const
 /* Sizes and timings of the current factorisation. */
 int asm_get_stats(asm_handle h, asm_stats* st);
 
+/* Tuning switches of the kernels (none changes the arithmetic; results are bitwise the same):
+ *   ASM_TUNE_APPLY_SMEM  1 (default) keeps each subdomain's local vectors in shared memory when
+ *                        they fit, 0 keeps them in device memory;
+ *   ASM_TUNE_COOP_ORTHO  1 (default) runs the Gram-Schmidt step of a single-system solve in one
+ *                        cooperative launch, 0 in one launch per projection.
+ * Errors: INVALID_ARG for an unknown key or value. */
+typedef enum { ASM_TUNE_APPLY_SMEM = 0, ASM_TUNE_COOP_ORTHO = 1 } asm_tune_key;
+int asm_set_tuning(asm_handle h, int key, int value);
+
 /* Profiling switch (0/1): when on, launch groups are bracketed by CUDA events. */
 int asm_set_profiling(asm_handle h, int enable);
 /* Accumulated profile since the last reset (counters keep running when profiling is off). */

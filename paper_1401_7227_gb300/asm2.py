@@ -25,7 +25,7 @@ EXPORTS = [
     "asm_default_options", "asm_error_string", "asm_create", "asm_destroy", "asm_set_grid", "asm_set_matrix_bsr",
     "asm_update_values", "asm_set_partition_boxes", "asm_factor", "asm_apply_precond", "asm_spmv", "asm_solve",
     "asm_solve_batch", "asm_get_stats", "asm_get_error_location", "asm_get_local_info", "asm_get_local_map",
-    "asm_get_local_matrix", "asm_get_local_factors", "asm_set_profiling", "asm_get_profile", "asm_reset_profile",
+    "asm_get_local_matrix", "asm_get_local_factors", "asm_set_profiling", "asm_get_profile", "asm_reset_profile", "asm_set_tuning",
 ]
 
 
@@ -110,6 +110,7 @@ def load(build_if_missing: bool = False):
     L.asm_set_profiling.argtypes = [P, I]
     L.asm_get_profile.argtypes = [P, C.POINTER(Profile)]
     L.asm_reset_profile.argtypes = [P]
+    L.asm_set_tuning.argtypes = [P, I, I]
     for name in EXPORTS:
         if name not in ("asm_default_options", "asm_error_string"):
             getattr(L, name).restype = I
@@ -255,6 +256,12 @@ class Solver:
         s = Stats()
         _check(load().asm_get_stats(self._h, C.byref(s)), "stats")
         return s.as_dict()
+
+    def set_tuning(self, apply_smem: bool | None = None, coop_ortho: bool | None = None):
+        if apply_smem is not None:
+            _check(load().asm_set_tuning(self._h, 0, int(apply_smem)), "set_tuning")
+        if coop_ortho is not None:
+            _check(load().asm_set_tuning(self._h, 1, int(coop_ortho)), "set_tuning")
 
     def set_profiling(self, on: bool = True):
         _check(load().asm_set_profiling(self._h, 1 if on else 0), "set_profiling")

@@ -84,6 +84,7 @@ struct asm_ctx {
     DBuf d_fp;  // factor program arrays (one allocation, see upload_factor_program)
     DBuf d_stream, d_pk_off_f, d_pk_src_f, d_pk_off_c, d_pk_src_c;
     DBuf d_lv, d_rlists, d_y;
+    int apply_smem = 0;  // dynamic shared memory of the apply (0: local vectors in d_y)
     DBuf d_factdesc, d_subdesc_single;
     DBuf d_err;
     std::vector<FactDesc> fact_desc;
@@ -101,6 +102,8 @@ struct asm_ctx {
     int n_vec1 = 0, n_row1 = 0;
     // profiling
     bool profiling = false;
+    bool no_coop = false;  // per-kernel orthogonalisation path instead of the cooperative one
+    bool no_smem = false;  // local vectors of the apply in device memory
     asm_profile_info prof{};
     // diagnostics
     int err_sub = -1, err_row = -1;
@@ -166,7 +169,8 @@ void upload_symbolic(asm_ctx* h) {
         fpi = (fpi + 1) / 2 * 2;
         fpi += (long long)o.pair.size() + (long long)o.ls.size();
         fp_base[s + 1] = fp_base[s] + fpi;
-        long long rli = (long long)o.rptr.size() + o.rsrc.size() + o.rbox.size() + o.own_pos.size() + o.own_cell.size();
+        long long rli = (long long)o.fcell.size() + o.rptr.size() + o.rsrc.size() + o.rbox.size() + o.clong.size() +
+                        o.own_pos.size() + o.own_cell.size();
         rl_base[s + 1] = rl_base[s] + rli;
         lv_base[s + 1] = lv_base[s] + o.nlev;
         npf += (long long)o.pk_off_f.size();
@@ -246,6 +250,7 @@ void upload_symbolic(asm_ctx* h) {
     offc.reserve(npc);
     srcc.reserve(npc);
     h->sub_desc.assign(K, SubDesc{});
+    h->apply_smem = 0;
     for (int s = 0; s < K; s++) {
         const SubSym& o = S.subs[s];
         if (!o.stream.empty())
@@ -272,18 +277,22 @@ void upload_symbolic(asm_ctx* h) {
             return p;
         };
         sd.sys = 0;
-        sd.n = o.n;
+        sd.nf = o.nf;
+        sd.nc = o.n - o.nf;
         sd.nlev = o.nlev;
         sd.n_own = (int)o.own_pos.size();
-        sd.prec = S.prec;
+        sd.n_long = (int)o.clong.size();
         sd.lv = h->d_lv.as<LevelInfo>() + lv_base[s];
         sd.stream = h->d_stream.as<unsigned char>() + h->stream_base[s];
         sd.y = h->d_y.as<double>() + h->row_base[s] * 3;
+        sd.fcell = put(o.fcell);
         sd.rptr = put(o.rptr);
         sd.rsrc = put(o.rsrc);
         sd.rbox = put(o.rbox);
+        sd.clong = put(o.clong);
         sd.own_pos = put(o.own_pos);
         sd.own_cell = put(o.own_cell);
+        h->apply_smem = std::max<int>(h->apply_smem, (int)apply_smem_bytes(o.nf, o.n - o.nf, S.prec));
         if (!rl.empty()) ck(cudaMemcpyAsync(base, rl.data(), rl.size() * 4, cudaMemcpyHostToDevice, st));
         sync(h);
     }
@@ -308,6 +317,10 @@ void upload_symbolic(asm_ctx* h) {
         h->d_boxsum.alloc(16);
         h->box_items.clear();
     }
+    // local vectors in shared memory when they fit next to the kernel's static needs
+    int dev_smem = 0;
+    ck(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    if (h->apply_smem > dev_smem - 1024) h->apply_smem = 0;
     h->d_subdesc_single.upload(h->sub_desc, st);
     h->d_err.alloc(sizeof(FactErr));
     sync(h);
@@ -329,7 +342,7 @@ void ensure_workspace(asm_ctx* h) {
     h->d_scal.zero(h->stream);
     h->d_ctl.alloc(C_NCTL * sizeof(int));
     h->d_ctl.zero(h->stream);
-    h->d_partial.alloc((size_t)2 * h->nchunk * sizeof(double));
+    h->d_partial.alloc((size_t)4 * h->nchunk * sizeof(double));
     h->ws_m = m;
     h->ws_flex = flex;
     SysTab& t = h->tab;
@@ -385,7 +398,8 @@ namespace {
 struct Batch {
     std::vector<asm_ctx*> hs;
     DBuf d_tab, d_vec, d_row, d_box, d_sub, d_gather;
-    int nvec = 0, nrow = 0, nbox = 0, nsub = 0, prec = 0;
+    int nvec = 0, nrow = 0, nbox = 0, nsub = 0, prec = 0, smem = 0;
+    int coop_grid = 0;  // > 0: single system, orthogonalisation in one cooperative launch
     std::vector<int> host_ctl;
     int* pinned = nullptr;
     ~Batch() {
@@ -446,17 +460,23 @@ void launch_step(Batch& B, int kmax, cudaStream_t st, StepEvents* ev) {
     launch_prep(tab, vi, B.nvec, st);
     if (ev) ck(cudaEventRecord(ev->e[1], st));
     launch_boxsum(tab, B.d_box.as<BoxItem>(), B.nbox, st);
-    launch_apply(tab, B.d_sub.as<SubDesc>(), B.nsub, B.prec, st);
+    launch_apply(tab, B.d_sub.as<SubDesc>(), B.nsub, B.prec, B.smem, st);
     if (ev) ck(cudaEventRecord(ev->e[2], st));
     launch_post(tab, vi, B.nvec, st);
     if (ev) ck(cudaEventRecord(ev->e[3], st));
     launch_spmv(tab, B.d_row.as<RowItem>(), B.nrow, st);
     if (ev) ck(cudaEventRecord(ev->e[4], st));
-    for (int k = 0; k <= kmax; k++) launch_mgs(tab, vi, B.nvec, k, st);
-    launch_finish(tab, vi, B.nvec, st);
+    long long n = 5;
+    if (B.coop_grid > 0) {
+        ck(launch_ortho_coop(tab, B.hs[0]->d_partial.as<double>(), B.coop_grid, st));
+        n += 1;
+    } else {
+        for (int k = 0; k <= kmax; k++) launch_mgs(tab, vi, B.nvec, k, st);
+        launch_finish(tab, vi, B.nvec, st);
+        n += kmax + 2;
+    }
     if (ev) ck(cudaEventRecord(ev->e[5], st));
     ck(cudaGetLastError());
-    const long long n = 7 + kmax + 1;
     for (asm_ctx* h : B.hs) h->prof.kernel_launches += n;
 }
 
@@ -478,6 +498,13 @@ int run_gmres(std::vector<asm_ctx*>& hs, const double* const* b, double* const* 
     Batch B;
     B.hs = hs;
     B.prec = hs[0]->prec;
+    B.smem = 0;
+    bool all_smem = true;
+    for (asm_ctx* h : hs) {
+        B.smem = std::max(B.smem, h->apply_smem);
+        all_smem = all_smem && h->apply_smem > 0 && !h->no_smem;
+    }
+    if (!all_smem) B.smem = 0;
     for (size_t k = 0; k < hs.size(); k++) {
         asm_ctx* h = hs[k];
         ensure_workspace(h);
@@ -497,15 +524,20 @@ int run_gmres(std::vector<asm_ctx*>& hs, const double* const* b, double* const* 
         ck(cudaStreamSynchronize(st));
     }
     build_batch(B, st);
+    if (hs.size() == 1 && !hs[0]->no_coop) B.coop_grid = std::min(ortho_coop_grid(hs[0]->device), hs[0]->nchunk);
     {
         // initial step: x = 0, r = b, beta = ||b||
         const SysTab* tab = B.d_tab.as<SysTab>();
         const VecItem* vi = B.d_vec.as<VecItem>();
         launch_init(tab, vi, B.nvec, st);
-        launch_mgs(tab, vi, B.nvec, 0, st);
-        launch_finish(tab, vi, B.nvec, st);
+        if (B.coop_grid > 0) {
+            ck(launch_ortho_coop(tab, hs[0]->d_partial.as<double>(), B.coop_grid, st));
+        } else {
+            launch_mgs(tab, vi, B.nvec, 0, st);
+            launch_finish(tab, vi, B.nvec, st);
+        }
         ck(cudaGetLastError());
-        for (asm_ctx* h : hs) h->prof.kernel_launches += 3;
+        for (asm_ctx* h : hs) h->prof.kernel_launches += B.coop_grid > 0 ? 2 : 3;
     }
     const bool prof = hs[0]->profiling;
     StepEvents ev;
@@ -790,7 +822,7 @@ int asm_apply_precond(asm_handle h, const double* r, double* z, int on_device) {
         set_ctl(h, VU, VZ, -1, -1, -1);
         launch_boxsum(h->d_tab1.as<SysTab>(), h->d_box1.as<BoxItem>(), (int)h->box_items.size(), h->stream);
         launch_apply(h->d_tab1.as<SysTab>(), h->d_subdesc_single.as<SubDesc>(), (int)h->sub_desc.size(), h->prec,
-                     h->stream);
+                     h->no_smem ? 0 : h->apply_smem, h->stream);
         ck(cudaGetLastError());
         h->prof.kernel_launches += 2;
         copy_out(h, z, out, bytes, on_device);
@@ -884,6 +916,18 @@ int asm_get_stats(asm_handle h, asm_stats* st) {
     }
     st->setup_ms = h->setup_ms;
     st->factor_ms = h->factor_ms;
+    return ASM_OK;
+}
+
+int asm_set_tuning(asm_handle h, int key, int value) {
+    if (!h || value < 0 || value > 1) return ASM_ERR_INVALID_ARG;
+    if (key == ASM_TUNE_APPLY_SMEM) {
+        h->no_smem = value == 0;
+    } else if (key == ASM_TUNE_COOP_ORTHO) {
+        h->no_coop = value == 0;
+    } else {
+        return ASM_ERR_INVALID_ARG;
+    }
     return ASM_OK;
 }
 

@@ -102,31 +102,33 @@ struct BoxItem {   // far box `box` of system sys: cells bcell[b0 .. b1)
     const int* bcell;
 };
 
-// One wavefront level of a local factor.  Rows of the level have consecutive positions:
-// nf fine rows first, then nc lump rows.  Forward/backward segments are byte offsets into the
-// subdomain's factor stream; every array inside a segment starts on a 16-byte boundary.
+// One wavefront level of a local factor: its nf fine rows have fine indices f0 .. f0+nf-1 and
+// its nc lump rows lump indices c0 .. c0+nc-1.  Forward/backward segments are byte offsets into
+// the subdomain's factor stream; every array inside a segment starts on a 16-byte boundary.
+// A stored column is a fine index (>= 0) or ~lump index (< 0).
 struct LevelInfo {
-    int pos0, nf, nc;
+    int f0, nf, c0, nc;
     int eLf, eLc, eUf, eUc;
-    int pad_;
     long long fwd_off, bwd_off;
 };
 
 // One subdomain work item of the preconditioner apply.
 struct SubDesc {
     int sys;
-    int n;            // local rows
+    int nf;           // fine rows
+    int nc;           // lump rows
     int nlev;
     int n_own;
-    int prec;         // storage of the fine-row factors: 0 f64, 1 f32, 2 f16
-    int pad_;
+    int n_long;       // lump rows restricted by a whole warp
     const LevelInfo* lv;
     const unsigned char* stream;
-    double* y;        // scratch local vector [n * 3], by position
-    const int* rptr;  // [n + 1] restriction sources by position
+    double* y;        // global scratch for the local vectors when they do not fit in shared memory
+    const int* fcell; // [nf] cell of each fine row
+    const int* rptr;  // [nc + 1] restriction sources of the lump rows
     const int* rsrc;  // >= 0: + r[cell]; < 0: - r[~cell]
-    const int* rbox;  // [n] far box whose sum is added first, or -1
-    const int* own_pos;
+    const int* rbox;  // [nc] far box whose sum is added first, or -1
+    const int* clong; // [n_long] lump rows with long source lists
+    const int* own_pos;  // fine index of each owned cell
     const int* own_cell;
 };
 
@@ -168,7 +170,10 @@ void launch_ell_fill(const double* bsr_vals, const int* ell_loc, long long nnzb,
                      int on_device_layout, cudaStream_t st);
 
 void launch_boxsum(const SysTab* st_tab, const BoxItem* items, int nitems, cudaStream_t st);
-void launch_apply(const SysTab* st_tab, const SubDesc* subs, int nsub, int prec, cudaStream_t st);
+// smem_bytes: dynamic shared memory for the local vectors (0 = use the global scratch in SubDesc.y)
+void launch_apply(const SysTab* st_tab, const SubDesc* subs, int nsub, int prec, int smem_bytes, cudaStream_t st);
+// shared memory the local vectors of a subdomain need (nf fine rows, nc lump rows)
+size_t apply_smem_bytes(int nf, int nc, int prec);
 void launch_spmv(const SysTab* st_tab, const RowItem* items, int nitems, cudaStream_t st);
 
 void launch_init(const SysTab* tab, const VecItem* items, int nitems, cudaStream_t st);
@@ -176,5 +181,9 @@ void launch_prep(const SysTab* tab, const VecItem* items, int nitems, cudaStream
 void launch_post(const SysTab* tab, const VecItem* items, int nitems, cudaStream_t st);
 void launch_mgs(const SysTab* tab, const VecItem* items, int nitems, int k, cudaStream_t st);
 void launch_finish(const SysTab* tab, const VecItem* items, int nitems, cudaStream_t st);
+// Whole Gram-Schmidt + state step of a single system in one cooperative launch (grid <= the
+// co-resident limit from ortho_coop_grid); part2 holds 4 * nchunk doubles.
+int ortho_coop_grid(int device);
+cudaError_t launch_ortho_coop(const SysTab* tab, double* part2, int grid, cudaStream_t st);
 
 }  // namespace asm2

@@ -184,30 +184,30 @@ __global__ void __launch_bounds__(256) k_factor(const FactDesc* __restrict__ fds
     }
 }
 
-template <typename T>
-__device__ __forceinline__ T cvt(double v);
-template <>
-__device__ __forceinline__ double cvt<double>(double v) {
-    return v;
-}
-template <>
-__device__ __forceinline__ float cvt<float>(double v) {
-    return (float)v;
-}
-template <>
-__device__ __forceinline__ __half cvt<__half>(double v) {
-    return __double2half(v);
-}
-
+// One thread per 3x3 block.  FP16 blocks are stored as 9 halves of v * 2^-e followed by e (int16),
+// with e chosen so that the largest magnitude lands in [0.5, 1): U (~T) and D^{-1} (~1/T) then both
+// keep FP16's full relative precision instead of overflowing or underflowing.
 template <typename T>
 __global__ void k_pack(const long long* __restrict__ off, const int* __restrict__ src, long long n,
                        unsigned char* __restrict__ base, const double* __restrict__ slot) {
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n * 9) return;
-    long long i = t / 9;
-    int e = (int)(t - i * 9);
-    T* dst = reinterpret_cast<T*>(base + off[i]);
-    dst[e] = cvt<T>(slot[(long long)src[i] * 9 + e]);
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double* v = slot + (long long)src[i] * 9;
+    if constexpr (sizeof(T) == 2) {
+        double mx = 0.0;
+#pragma unroll
+        for (int e = 0; e < 9; e++) mx = fmax(mx, fabs(v[e]));
+        int ex = 0;
+        if (mx > 0.0) ex = ilogb(mx) + 1;
+        __half* dst = reinterpret_cast<__half*>(base + off[i]);
+#pragma unroll
+        for (int e = 0; e < 9; e++) dst[e] = __double2half(ldexp(v[e], -ex));
+        reinterpret_cast<short*>(dst)[9] = (short)ex;
+    } else {
+        T* dst = reinterpret_cast<T*>(base + off[i]);
+#pragma unroll
+        for (int e = 0; e < 9; e++) dst[e] = (T)v[e];
+    }
 }
 
 inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -240,7 +240,7 @@ void launch_factor(const FactDesc* fd, int nsub, FactErr* err, const int* sub_id
 void launch_pack(const long long* off, const int* src, long long n, int prec, unsigned char* stream_base,
                  const double* slot_base, cudaStream_t st) {
     if (n <= 0) return;
-    unsigned g = blocks_for(n * 9, 256);
+    unsigned g = blocks_for(n, 256);
     if (prec == 0)
         k_pack<double><<<g, 256, 0, st>>>(off, src, n, stream_base, slot_base);
     else if (prec == 1)

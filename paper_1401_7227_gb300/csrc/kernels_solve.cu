@@ -5,6 +5,8 @@
 // their solve share the same launches.
 #include <cuda_fp16.h>
 
+#include <cooperative_groups.h>
+
 #include "asm2_internal.h"
 
 namespace asm2 {
@@ -13,16 +15,32 @@ namespace {
 
 __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
+// Stored fine blocks: 9 FP32 values, or 9 FP16 values scaled by 2^-e followed by e (int16).
 template <typename T>
-__device__ __forceinline__ float ldf(const T* p);
+struct FineBlock;
 template <>
-__device__ __forceinline__ float ldf<float>(const float* p) {
-    return *p;
-}
+struct FineBlock<float> {
+    static constexpr int bytes = 36;
+    __device__ static __forceinline__ void load(const unsigned char* p, float* w) {
+        const float* f = reinterpret_cast<const float*>(p);
+#pragma unroll
+        for (int e = 0; e < 9; e++) w[e] = f[e];
+    }
+};
 template <>
-__device__ __forceinline__ float ldf<__half>(const __half* p) {
-    return __half2float(*p);
-}
+struct FineBlock<__half> {
+    static constexpr int bytes = 20;
+    __device__ static __forceinline__ void load(const unsigned char* p, float* w) {
+        const __half* h = reinterpret_cast<const __half*>(p);
+        const float sc = ldexpf(1.0f, reinterpret_cast<const short*>(p)[9]);
+#pragma unroll
+        for (int e = 0; e < 9; e++) w[e] = __half2float(h[e]) * sc;
+    }
+};
+template <>
+struct FineBlock<double> {
+    static constexpr int bytes = 72;
+};
 
 // ------------------------------------------------------------------------------------------
 // far-box sums of the apply input: boxsum[b] = sum over the cells of far box b
@@ -58,10 +76,45 @@ __global__ void __launch_bounds__(256) k_boxsum(const SysTab* __restrict__ tab, 
 
 // ------------------------------------------------------------------------------------------
 // fused local solve of one subdomain (one CTA): y = R_i r; y = L^{-1} y; y = U^{-1} y;
-// z[owned cells] = y[owned positions].  Levels are separated by CTA barriers.
+// z[owned cells] = y[owned fine rows] (Eqs. 4.2-4.5).  Fine rows and lump rows live in separate
+// local vectors (fine rows at the factor precision, lumps in FP64), in shared memory when they
+// fit.  Levels are separated by CTA barriers.  Fine rows (<= 6 blocks) take one thread each;
+// lump rows (up to ~70 blocks) take one warp each.
 // ------------------------------------------------------------------------------------------
 template <typename TF>
+struct Compute {
+    using T = float;  // fine rows of FP32/FP16 factors are applied in FP32
+};
+template <>
+struct Compute<double> {
+    using T = double;
+};
+
+template <typename TF>
+__device__ __forceinline__ void load_fine(const unsigned char* p, typename Compute<TF>::T* w) {
+    if constexpr (sizeof(TF) == 8) {
+        const double* d = reinterpret_cast<const double*>(p);
+#pragma unroll
+        for (int e = 0; e < 9; e++) w[e] = d[e];
+    } else {
+        FineBlock<TF>::load(p, w);
+    }
+}
+
+__device__ __forceinline__ void warp_sum3(double& a0, double& a1, double& a2) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    }
+}
+
+template <typename TF, bool SMEM>
 __global__ void __launch_bounds__(256) k_apply(const SysTab* __restrict__ tab, const SubDesc* __restrict__ subs) {
+    using TC = typename Compute<TF>::T;
+    constexpr int FB = FineBlock<TF>::bytes;
+    extern __shared__ __align__(16) double smem[];
     const SubDesc sd = subs[blockIdx.x];
     const SysTab& st = tab[sd.sys];
     const int in = st.ctl[C_APPLY_IN];
@@ -69,39 +122,67 @@ __global__ void __launch_bounds__(256) k_apply(const SysTab* __restrict__ tab, c
     const int out = st.ctl[C_APPLY_OUT];
     const double* __restrict__ r = st.ws + (long long)in * st.n3p;
     double* __restrict__ z = st.ws + (long long)out * st.n3p;
-    double* __restrict__ y = sd.y;
+    double* yc = SMEM ? smem : sd.y;
+    TC* yf = reinterpret_cast<TC*>(yc + 3 * sd.nc);
     const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
 
-    // restriction R_i r: fine rows copy, lumps sum (far lumps: box sum minus the near region)
-    for (int p = tid; p < sd.n; p += nt) {
+    // restriction R_i r
+    for (int f = tid; f < sd.nf; f += nt) {
+        const double* rc = r + 3LL * sd.fcell[f];
+        yf[3 * f] = (TC)rc[0];
+        yf[3 * f + 1] = (TC)rc[1];
+        yf[3 * f + 2] = (TC)rc[2];
+    }
+    for (int c = tid; c < sd.nc; c += nt) {
+        const int i0 = sd.rptr[c], i1 = sd.rptr[c + 1];
+        if (i1 - i0 > 16) continue;  // long lists: below, one warp per row
         double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-        const int b = sd.rbox[p];
+        const int b = sd.rbox[c];
         if (b >= 0) {
             a0 = st.boxsum[3 * b];
             a1 = st.boxsum[3 * b + 1];
             a2 = st.boxsum[3 * b + 2];
         }
-        for (int i = sd.rptr[p]; i < sd.rptr[p + 1]; i++) {
-            const int c = sd.rsrc[i];
-            if (c >= 0) {
-                const double* rc = r + 3LL * c;
-                a0 += rc[0];
-                a1 += rc[1];
-                a2 += rc[2];
-            } else {
-                const double* rc = r + 3LL * (~c);
-                a0 -= rc[0];
-                a1 -= rc[1];
-                a2 -= rc[2];
-            }
+        for (int i = i0; i < i1; i++) {
+            const int cell = sd.rsrc[i];
+            const double sg = cell >= 0 ? 1.0 : -1.0;
+            const double* rc = r + 3LL * (cell >= 0 ? cell : ~cell);
+            a0 += sg * rc[0];
+            a1 += sg * rc[1];
+            a2 += sg * rc[2];
         }
-        y[3 * p] = a0;
-        y[3 * p + 1] = a1;
-        y[3 * p + 2] = a2;
+        yc[3 * c] = a0;
+        yc[3 * c + 1] = a1;
+        yc[3 * c + 2] = a2;
+    }
+    for (int k = warp; k < sd.n_long; k += nwarp) {
+        const int c = sd.clong[k];
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        for (int i = sd.rptr[c] + lane; i < sd.rptr[c + 1]; i += 32) {
+            const int cell = sd.rsrc[i];
+            const double sg = cell >= 0 ? 1.0 : -1.0;
+            const double* rc = r + 3LL * (cell >= 0 ? cell : ~cell);
+            a0 += sg * rc[0];
+            a1 += sg * rc[1];
+            a2 += sg * rc[2];
+        }
+        warp_sum3(a0, a1, a2);
+        if (lane == 0) {
+            const int b = sd.rbox[c];
+            if (b >= 0) {
+                a0 += st.boxsum[3 * b];
+                a1 += st.boxsum[3 * b + 1];
+                a2 += st.boxsum[3 * b + 2];
+            }
+            yc[3 * c] = a0;
+            yc[3 * c + 1] = a1;
+            yc[3 * c + 2] = a2;
+        }
     }
     __syncthreads();
 
-    // forward sweep: y_p -= sum_k L_pk y_k, level by level
+    // forward sweep: y_p -= sum_k L_pk y_k
     for (int lv = 0; lv < sd.nlev; lv++) {
         const LevelInfo L = sd.lv[lv];
         const unsigned char* seg = sd.stream + L.fwd_off;
@@ -109,58 +190,56 @@ __global__ void __launch_bounds__(256) k_apply(const SysTab* __restrict__ tab, c
         size_t o = align16(4 * (size_t)(L.nf + 1));
         const int* fcol = reinterpret_cast<const int*>(seg + o);
         o += align16(4 * (size_t)L.eLf);
-        const TF* fval = reinterpret_cast<const TF*>(seg + o);
-        o += align16(sizeof(TF) * 9 * (size_t)L.eLf);
+        const unsigned char* fval = seg + o;
+        o += align16((size_t)FB * L.eLf);
         const int* cptr = reinterpret_cast<const int*>(seg + o);
         o += align16(4 * (size_t)(L.nc + 1));
         const int* ccol = reinterpret_cast<const int*>(seg + o);
         o += align16(4 * (size_t)L.eLc);
         const double* cval = reinterpret_cast<const double*>(seg + o);
-        for (int t = tid; t < L.nf + L.nc; t += nt) {
-            if (t < L.nf) {
-                const int pos = L.pos0 + t;
-                if constexpr (sizeof(TF) == 8) {
-                    double a0 = y[3 * pos], a1 = y[3 * pos + 1], a2 = y[3 * pos + 2];
-                    for (int e = fptr[t]; e < fptr[t + 1]; e++) {
-                        const double* v = reinterpret_cast<const double*>(fval) + 9LL * e;
-                        const int c = fcol[e];
-                        const double x0 = y[3 * c], x1 = y[3 * c + 1], x2 = y[3 * c + 2];
-                        a0 -= v[0] * x0 + v[1] * x1 + v[2] * x2;
-                        a1 -= v[3] * x0 + v[4] * x1 + v[5] * x2;
-                        a2 -= v[6] * x0 + v[7] * x1 + v[8] * x2;
-                    }
-                    y[3 * pos] = a0;
-                    y[3 * pos + 1] = a1;
-                    y[3 * pos + 2] = a2;
+        for (int t = tid; t < L.nf; t += nt) {
+            const int f = L.f0 + t;
+            TC a0 = yf[3 * f], a1 = yf[3 * f + 1], a2 = yf[3 * f + 2];
+            const int e0 = fptr[t], e1 = fptr[t + 1];
+#pragma unroll 3
+            for (int e = e0; e < e1; e++) {
+                TC v[9];
+                load_fine<TF>(fval + (size_t)FB * e, v);
+                const int c = fcol[e];
+                const TC x0 = yf[3 * c], x1 = yf[3 * c + 1], x2 = yf[3 * c + 2];
+                a0 -= v[0] * x0 + v[1] * x1 + v[2] * x2;
+                a1 -= v[3] * x0 + v[4] * x1 + v[5] * x2;
+                a2 -= v[6] * x0 + v[7] * x1 + v[8] * x2;
+            }
+            yf[3 * f] = a0;
+            yf[3 * f + 1] = a1;
+            yf[3 * f + 2] = a2;
+        }
+        for (int i = warp; i < L.nc; i += nwarp) {
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+            for (int e = cptr[i] + lane; e < cptr[i + 1]; e += 32) {
+                const double* v = cval + 9LL * e;
+                const int c = ccol[e];
+                double x0, x1, x2;
+                if (c >= 0) {
+                    x0 = yf[3 * c];
+                    x1 = yf[3 * c + 1];
+                    x2 = yf[3 * c + 2];
                 } else {
-                    float a0 = (float)y[3 * pos], a1 = (float)y[3 * pos + 1], a2 = (float)y[3 * pos + 2];
-                    for (int e = fptr[t]; e < fptr[t + 1]; e++) {
-                        const TF* v = fval + 9LL * e;
-                        const int c = fcol[e];
-                        const float x0 = (float)y[3 * c], x1 = (float)y[3 * c + 1], x2 = (float)y[3 * c + 2];
-                        a0 -= ldf(v) * x0 + ldf(v + 1) * x1 + ldf(v + 2) * x2;
-                        a1 -= ldf(v + 3) * x0 + ldf(v + 4) * x1 + ldf(v + 5) * x2;
-                        a2 -= ldf(v + 6) * x0 + ldf(v + 7) * x1 + ldf(v + 8) * x2;
-                    }
-                    y[3 * pos] = a0;
-                    y[3 * pos + 1] = a1;
-                    y[3 * pos + 2] = a2;
+                    x0 = yc[3 * ~c];
+                    x1 = yc[3 * ~c + 1];
+                    x2 = yc[3 * ~c + 2];
                 }
-            } else {
-                const int i = t - L.nf;
-                const int pos = L.pos0 + t;
-                double a0 = y[3 * pos], a1 = y[3 * pos + 1], a2 = y[3 * pos + 2];
-                for (int e = cptr[i]; e < cptr[i + 1]; e++) {
-                    const double* v = cval + 9LL * e;
-                    const int c = ccol[e];
-                    const double x0 = y[3 * c], x1 = y[3 * c + 1], x2 = y[3 * c + 2];
-                    a0 -= v[0] * x0 + v[1] * x1 + v[2] * x2;
-                    a1 -= v[3] * x0 + v[4] * x1 + v[5] * x2;
-                    a2 -= v[6] * x0 + v[7] * x1 + v[8] * x2;
-                }
-                y[3 * pos] = a0;
-                y[3 * pos + 1] = a1;
-                y[3 * pos + 2] = a2;
+                a0 += v[0] * x0 + v[1] * x1 + v[2] * x2;
+                a1 += v[3] * x0 + v[4] * x1 + v[5] * x2;
+                a2 += v[6] * x0 + v[7] * x1 + v[8] * x2;
+            }
+            warp_sum3(a0, a1, a2);
+            if (lane == 0) {
+                const int c = L.c0 + i;
+                yc[3 * c] -= a0;
+                yc[3 * c + 1] -= a1;
+                yc[3 * c + 2] -= a2;
             }
         }
         __syncthreads();
@@ -174,10 +253,10 @@ __global__ void __launch_bounds__(256) k_apply(const SysTab* __restrict__ tab, c
         size_t o = align16(4 * (size_t)(L.nf + 1));
         const int* fcol = reinterpret_cast<const int*>(seg + o);
         o += align16(4 * (size_t)L.eUf);
-        const TF* fval = reinterpret_cast<const TF*>(seg + o);
-        o += align16(sizeof(TF) * 9 * (size_t)L.eUf);
-        const TF* fdi = reinterpret_cast<const TF*>(seg + o);
-        o += align16(sizeof(TF) * 9 * (size_t)L.nf);
+        const unsigned char* fval = seg + o;
+        o += align16((size_t)FB * L.eUf);
+        const unsigned char* fdi = seg + o;
+        o += align16((size_t)FB * L.nf);
         const int* cptr = reinterpret_cast<const int*>(seg + o);
         o += align16(4 * (size_t)(L.nc + 1));
         const int* ccol = reinterpret_cast<const int*>(seg + o);
@@ -185,54 +264,63 @@ __global__ void __launch_bounds__(256) k_apply(const SysTab* __restrict__ tab, c
         const double* cval = reinterpret_cast<const double*>(seg + o);
         o += align16(8 * 9 * (size_t)L.eUc);
         const double* cdi = reinterpret_cast<const double*>(seg + o);
-        for (int t = tid; t < L.nf + L.nc; t += nt) {
-            if (t < L.nf) {
-                const int pos = L.pos0 + t;
-                if constexpr (sizeof(TF) == 8) {
-                    double a0 = y[3 * pos], a1 = y[3 * pos + 1], a2 = y[3 * pos + 2];
-                    for (int e = fptr[t]; e < fptr[t + 1]; e++) {
-                        const double* v = reinterpret_cast<const double*>(fval) + 9LL * e;
-                        const int c = fcol[e];
-                        const double x0 = y[3 * c], x1 = y[3 * c + 1], x2 = y[3 * c + 2];
-                        a0 -= v[0] * x0 + v[1] * x1 + v[2] * x2;
-                        a1 -= v[3] * x0 + v[4] * x1 + v[5] * x2;
-                        a2 -= v[6] * x0 + v[7] * x1 + v[8] * x2;
-                    }
-                    const double* d = reinterpret_cast<const double*>(fdi) + 9LL * t;
-                    y[3 * pos] = d[0] * a0 + d[1] * a1 + d[2] * a2;
-                    y[3 * pos + 1] = d[3] * a0 + d[4] * a1 + d[5] * a2;
-                    y[3 * pos + 2] = d[6] * a0 + d[7] * a1 + d[8] * a2;
+        // lump rows first within the level is not required: rows of one level are independent
+        for (int t = tid; t < L.nf; t += nt) {
+            const int f = L.f0 + t;
+            TC a0 = yf[3 * f], a1 = yf[3 * f + 1], a2 = yf[3 * f + 2];
+            const int e0 = fptr[t], e1 = fptr[t + 1];
+#pragma unroll 3
+            for (int e = e0; e < e1; e++) {
+                TC v[9];
+                load_fine<TF>(fval + (size_t)FB * e, v);
+                const int c = fcol[e];
+                TC x0, x1, x2;
+                if (c >= 0) {
+                    x0 = yf[3 * c];
+                    x1 = yf[3 * c + 1];
+                    x2 = yf[3 * c + 2];
                 } else {
-                    float a0 = (float)y[3 * pos], a1 = (float)y[3 * pos + 1], a2 = (float)y[3 * pos + 2];
-                    for (int e = fptr[t]; e < fptr[t + 1]; e++) {
-                        const TF* v = fval + 9LL * e;
-                        const int c = fcol[e];
-                        const float x0 = (float)y[3 * c], x1 = (float)y[3 * c + 1], x2 = (float)y[3 * c + 2];
-                        a0 -= ldf(v) * x0 + ldf(v + 1) * x1 + ldf(v + 2) * x2;
-                        a1 -= ldf(v + 3) * x0 + ldf(v + 4) * x1 + ldf(v + 5) * x2;
-                        a2 -= ldf(v + 6) * x0 + ldf(v + 7) * x1 + ldf(v + 8) * x2;
-                    }
-                    const TF* d = fdi + 9LL * t;
-                    y[3 * pos] = ldf(d) * a0 + ldf(d + 1) * a1 + ldf(d + 2) * a2;
-                    y[3 * pos + 1] = ldf(d + 3) * a0 + ldf(d + 4) * a1 + ldf(d + 5) * a2;
-                    y[3 * pos + 2] = ldf(d + 6) * a0 + ldf(d + 7) * a1 + ldf(d + 8) * a2;
+                    x0 = (TC)yc[3 * ~c];
+                    x1 = (TC)yc[3 * ~c + 1];
+                    x2 = (TC)yc[3 * ~c + 2];
                 }
-            } else {
-                const int i = t - L.nf;
-                const int pos = L.pos0 + t;
-                double a0 = y[3 * pos], a1 = y[3 * pos + 1], a2 = y[3 * pos + 2];
-                for (int e = cptr[i]; e < cptr[i + 1]; e++) {
-                    const double* v = cval + 9LL * e;
-                    const int c = ccol[e];
-                    const double x0 = y[3 * c], x1 = y[3 * c + 1], x2 = y[3 * c + 2];
-                    a0 -= v[0] * x0 + v[1] * x1 + v[2] * x2;
-                    a1 -= v[3] * x0 + v[4] * x1 + v[5] * x2;
-                    a2 -= v[6] * x0 + v[7] * x1 + v[8] * x2;
+                a0 -= v[0] * x0 + v[1] * x1 + v[2] * x2;
+                a1 -= v[3] * x0 + v[4] * x1 + v[5] * x2;
+                a2 -= v[6] * x0 + v[7] * x1 + v[8] * x2;
+            }
+            TC d[9];
+            load_fine<TF>(fdi + (size_t)FB * t, d);
+            yf[3 * f] = d[0] * a0 + d[1] * a1 + d[2] * a2;
+            yf[3 * f + 1] = d[3] * a0 + d[4] * a1 + d[5] * a2;
+            yf[3 * f + 2] = d[6] * a0 + d[7] * a1 + d[8] * a2;
+        }
+        for (int i = warp; i < L.nc; i += nwarp) {
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+            for (int e = cptr[i] + lane; e < cptr[i + 1]; e += 32) {
+                const double* v = cval + 9LL * e;
+                const int c = ccol[e];
+                double x0, x1, x2;
+                if (c >= 0) {
+                    x0 = yf[3 * c];
+                    x1 = yf[3 * c + 1];
+                    x2 = yf[3 * c + 2];
+                } else {
+                    x0 = yc[3 * ~c];
+                    x1 = yc[3 * ~c + 1];
+                    x2 = yc[3 * ~c + 2];
                 }
+                a0 += v[0] * x0 + v[1] * x1 + v[2] * x2;
+                a1 += v[3] * x0 + v[4] * x1 + v[5] * x2;
+                a2 += v[6] * x0 + v[7] * x1 + v[8] * x2;
+            }
+            warp_sum3(a0, a1, a2);
+            if (lane == 0) {
+                const int c = L.c0 + i;
+                const double b0 = yc[3 * c] - a0, b1 = yc[3 * c + 1] - a1, b2 = yc[3 * c + 2] - a2;
                 const double* d = cdi + 9LL * i;
-                y[3 * pos] = d[0] * a0 + d[1] * a1 + d[2] * a2;
-                y[3 * pos + 1] = d[3] * a0 + d[4] * a1 + d[5] * a2;
-                y[3 * pos + 2] = d[6] * a0 + d[7] * a1 + d[8] * a2;
+                yc[3 * c] = d[0] * b0 + d[1] * b1 + d[2] * b2;
+                yc[3 * c + 1] = d[3] * b0 + d[4] * b1 + d[5] * b2;
+                yc[3 * c + 2] = d[6] * b0 + d[7] * b1 + d[8] * b2;
             }
         }
         __syncthreads();
@@ -240,11 +328,11 @@ __global__ void __launch_bounds__(256) k_apply(const SysTab* __restrict__ tab, c
 
     // P_i R_i^T: owned cells take this subdomain's solution; the lumps are discarded
     for (int t = tid; t < sd.n_own; t += nt) {
-        const int p = sd.own_pos[t];
+        const int f = sd.own_pos[t];
         const long long c = 3LL * sd.own_cell[t];
-        z[c] = y[3 * p];
-        z[c + 1] = y[3 * p + 1];
-        z[c + 2] = y[3 * p + 2];
+        z[c] = yf[3 * f];
+        z[c + 1] = yf[3 * f + 1];
+        z[c + 2] = yf[3 * f + 2];
     }
 }
 
@@ -462,45 +550,10 @@ __device__ void set_slots(const SysTab& st, int ph, int j) {
     }
 }
 
-// End of a step: vector scaling (v_{j+1} = w / h_{j+1,j}, or v_0 = r / beta), then the last chunk
-// of each system applies the Givens rotations and moves its state machine.
-__global__ void __launch_bounds__(VEC_THREADS) k_finish(const SysTab* __restrict__ tab,
-                                                        const VecItem* __restrict__ items) {
-    const VecItem it = items[blockIdx.x];
-    const SysTab& st = tab[it.sys];
-    const int ph = st.ctl[C_PHASE];
-    if (ph == PH_DONE) return;
+// Givens rotation of column j and the GMRES state machine of one system (one thread).
+__device__ void step_state(const SysTab& st, int ph) {
     const ScalLayout SL = ScalLayout::make(st.m);
-    const long long e0 = (long long)it.chunk * VEC_CHUNK;
     const int m = st.m;
-    if (ph == PH_ARNOLDI) {
-        const int j = st.ctl[C_J];
-        const double hn = st.scal[SL.hn];
-        if (hn > 0.0) {
-            const double inv = 1.0 / hn;
-            const double* w = vec(st, VW);
-            double* v = vec(st, VV0 + j + 1);
-            for (int i = threadIdx.x; i < VEC_CHUNK; i += blockDim.x) v[e0 + i] = w[e0 + i] * inv;
-        }
-    } else {
-        const double beta = st.scal[SL.beta];
-        if (beta > 0.0) {
-            const double inv = 1.0 / beta;
-            const double* r = vec(st, VR);
-            double* v = vec(st, VV0);
-            for (int i = threadIdx.x; i < VEC_CHUNK; i += blockDim.x) v[e0 + i] = r[e0 + i] * inv;
-        }
-    }
-    __shared__ bool last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        last = atomicAdd(&st.ctl[C_CNT_FIN], 1) == st.nchunk - 1;
-    }
-    __syncthreads();
-    if (!last || threadIdx.x != 0) return;
-    __threadfence();
-    st.ctl[C_CNT_FIN] = 0;
     int* c = st.ctl;
     double* s = st.scal;
     double* H = s + SL.H;
@@ -577,20 +630,203 @@ __global__ void __launch_bounds__(VEC_THREADS) k_finish(const SysTab* __restrict
     }
 }
 
+
+// End of a step: vector scaling (v_{j+1} = w / h_{j+1,j}, or v_0 = r / beta), then the last chunk
+// of each system applies the Givens rotations and moves its state machine.
+__global__ void __launch_bounds__(VEC_THREADS) k_finish(const SysTab* __restrict__ tab,
+                                                        const VecItem* __restrict__ items) {
+    const VecItem it = items[blockIdx.x];
+    const SysTab& st = tab[it.sys];
+    const int ph = st.ctl[C_PHASE];
+    if (ph == PH_DONE) return;
+    const ScalLayout SL = ScalLayout::make(st.m);
+    const long long e0 = (long long)it.chunk * VEC_CHUNK;
+    if (ph == PH_ARNOLDI) {
+        const int j = st.ctl[C_J];
+        const double hn = st.scal[SL.hn];
+        if (hn > 0.0) {
+            const double inv = 1.0 / hn;
+            const double* w = vec(st, VW);
+            double* v = vec(st, VV0 + j + 1);
+            for (int i = threadIdx.x; i < VEC_CHUNK; i += blockDim.x) v[e0 + i] = w[e0 + i] * inv;
+        }
+    } else {
+        const double beta = st.scal[SL.beta];
+        if (beta > 0.0) {
+            const double inv = 1.0 / beta;
+            const double* r = vec(st, VR);
+            double* v = vec(st, VV0);
+            for (int i = threadIdx.x; i < VEC_CHUNK; i += blockDim.x) v[e0 + i] = r[e0 + i] * inv;
+        }
+    }
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&st.ctl[C_CNT_FIN], 1) == st.nchunk - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    st.ctl[C_CNT_FIN] = 0;
+    step_state(st, ph);
+}
+
+// The whole orthogonalisation of one step of one system in one cooperative launch: the same
+// chunk partials and the same ordered final sums as k_mgs/k_finish (so results are bitwise those of
+// the per-kernel path), with a grid-wide barrier per projection instead of a launch.  w stays in L2
+// between projections, so each basis vector is streamed from HBM about once.
+__device__ __forceinline__ void grid_total(const double* part, int nchunk, double& s0, double& s1) {
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nchunk; i += blockDim.x) {
+        a += __ldcg(&part[2 * i]);
+        b += __ldcg(&part[2 * i + 1]);
+    }
+    block_sum2(a, b);
+    __shared__ double bc[2];
+    if (threadIdx.x == 0) {
+        bc[0] = a;
+        bc[1] = b;
+    }
+    __syncthreads();
+    s0 = bc[0];
+    s1 = bc[1];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(VEC_THREADS) k_ortho_coop(const SysTab* __restrict__ tab, double* __restrict__ part2) {
+    namespace cg = cooperative_groups;
+    cg::grid_group grid = cg::this_grid();
+    const SysTab& st = tab[0];
+    const int ph = st.ctl[C_PHASE];
+    if (ph == PH_DONE) return;
+    const ScalLayout SL = ScalLayout::make(st.m);
+    const int m = st.m;
+    const int G = gridDim.x;
+    double* w = vec(st, VW);
+    if (ph == PH_ARNOLDI) {
+        const int j = st.ctl[C_J];
+        double hprev = 0.0, w0 = 0.0, hn = 0.0;
+        for (int k = 0; k <= j + 1; k++) {
+            double* part = part2 + (size_t)(k & 1) * 2 * st.nchunk;
+            const double* vprev = k >= 1 ? vec(st, VV0 + k - 1) : nullptr;
+            const double* vk = k <= j ? vec(st, VV0 + k) : nullptr;
+            for (int ch = blockIdx.x; ch < st.nchunk; ch += G) {
+                const long long e0 = (long long)ch * VEC_CHUNK;
+                double s0 = 0.0, s1 = 0.0;
+                if (k >= 1)
+                    for (int i = threadIdx.x; i < VEC_CHUNK; i += blockDim.x) w[e0 + i] -= hprev * vprev[e0 + i];
+                if (k <= j) {
+                    for (int i = threadIdx.x; i < VEC_CHUNK; i += blockDim.x) {
+                        const double a = w[e0 + i];
+                        s0 += a * vk[e0 + i];
+                        s1 += a * a;
+                    }
+                } else {
+                    for (int i = threadIdx.x; i < VEC_CHUNK; i += blockDim.x) {
+                        const double a = w[e0 + i];
+                        s0 += a * a;
+                    }
+                }
+                block_sum2(s0, s1);
+                if (threadIdx.x == 0) {
+                    part[2 * ch] = s0;
+                    part[2 * ch + 1] = s1;
+                }
+            }
+            grid.sync();
+            double t0, t1;
+            grid_total(part, st.nchunk, t0, t1);
+            if (k <= j) {
+                hprev = t0;
+                if (k == 0) w0 = sqrt(t1);
+                if (blockIdx.x == 0 && threadIdx.x == 0) st.scal[SL.H + k * m + j] = t0;
+            } else {
+                hn = sqrt(t0);
+            }
+        }
+        if (hn > 0.0) {
+            const double inv = 1.0 / hn;
+            double* v = vec(st, VV0 + j + 1);
+            for (int ch = blockIdx.x; ch < st.nchunk; ch += G) {
+                const long long e0 = (long long)ch * VEC_CHUNK;
+                for (int i = threadIdx.x; i < VEC_CHUNK; i += blockDim.x) v[e0 + i] = w[e0 + i] * inv;
+            }
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            st.scal[SL.w0] = w0;
+            st.scal[SL.hn] = hn;
+            st.scal[SL.H + (j + 1) * m + j] = hn;
+            step_state(st, ph);
+        }
+    } else {
+        const double* r = vec(st, VR);
+        for (int ch = blockIdx.x; ch < st.nchunk; ch += G) {
+            const long long e0 = (long long)ch * VEC_CHUNK;
+            double s0 = 0.0, s1 = 0.0;
+            for (int i = threadIdx.x; i < VEC_CHUNK; i += blockDim.x) {
+                const double a = r[e0 + i];
+                s0 += a * a;
+            }
+            block_sum2(s0, s1);
+            if (threadIdx.x == 0) {
+                part2[2 * ch] = s0;
+                part2[2 * ch + 1] = s1;
+            }
+        }
+        grid.sync();
+        double t0, t1;
+        grid_total(part2, st.nchunk, t0, t1);
+        const double beta = sqrt(t0);
+        if (beta > 0.0) {
+            const double inv = 1.0 / beta;
+            double* v = vec(st, VV0);
+            for (int ch = blockIdx.x; ch < st.nchunk; ch += G) {
+                const long long e0 = (long long)ch * VEC_CHUNK;
+                for (int i = threadIdx.x; i < VEC_CHUNK; i += blockDim.x) v[e0 + i] = r[e0 + i] * inv;
+            }
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            st.scal[SL.beta] = beta;
+            step_state(st, ph);
+        }
+    }
+}
+
 }  // namespace
 
 void launch_boxsum(const SysTab* tab, const BoxItem* items, int nitems, cudaStream_t st) {
     if (nitems > 0) k_boxsum<<<nitems, 256, 0, st>>>(tab, items);
 }
 
-void launch_apply(const SysTab* tab, const SubDesc* subs, int nsub, int prec, cudaStream_t st) {
+size_t apply_smem_bytes(int nf, int nc, int prec) {
+    return 24 * (size_t)nc + (prec == 0 ? 24 : 12) * (size_t)nf;
+}
+
+namespace {
+template <typename TF>
+void launch_apply_t(const SysTab* tab, const SubDesc* subs, int nsub, int smem, cudaStream_t st) {
+    if (smem > 0) {
+        static int configured = -1;
+        if (configured < smem) {
+            cudaFuncSetAttribute(k_apply<TF, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            configured = smem;
+        }
+        k_apply<TF, true><<<nsub, 256, smem, st>>>(tab, subs);
+    } else {
+        k_apply<TF, false><<<nsub, 256, 0, st>>>(tab, subs);
+    }
+}
+}  // namespace
+
+void launch_apply(const SysTab* tab, const SubDesc* subs, int nsub, int prec, int smem, cudaStream_t st) {
     if (nsub <= 0) return;
     if (prec == 0)
-        k_apply<double><<<nsub, 256, 0, st>>>(tab, subs);
+        launch_apply_t<double>(tab, subs, nsub, smem, st);
     else if (prec == 1)
-        k_apply<float><<<nsub, 256, 0, st>>>(tab, subs);
+        launch_apply_t<float>(tab, subs, nsub, smem, st);
     else
-        k_apply<__half><<<nsub, 256, 0, st>>>(tab, subs);
+        launch_apply_t<__half>(tab, subs, nsub, smem, st);
 }
 
 void launch_spmv(const SysTab* tab, const RowItem* items, int nitems, cudaStream_t st) {
@@ -609,6 +845,18 @@ void launch_post(const SysTab* tab, const VecItem* items, int nitems, cudaStream
 void launch_mgs(const SysTab* tab, const VecItem* items, int nitems, int k, cudaStream_t st) {
     if (nitems > 0) k_mgs<<<nitems, VEC_THREADS, 0, st>>>(tab, items, k);
 }
+int ortho_coop_grid(int device) {
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ortho_coop, VEC_THREADS, 0) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+    return per_sm * sms;
+}
+
+cudaError_t launch_ortho_coop(const SysTab* tab, double* part2, int grid, cudaStream_t st) {
+    void* args[] = {(void*)&tab, (void*)&part2};
+    return cudaLaunchCooperativeKernel((const void*)k_ortho_coop, dim3(grid), dim3(VEC_THREADS), args, 0, st);
+}
+
 void launch_finish(const SysTab* tab, const VecItem* items, int nitems, cudaStream_t st) {
     if (nitems > 0) k_finish<<<nitems, VEC_THREADS, 0, st>>>(tab, items);
 }

@@ -22,6 +22,8 @@ namespace asm2 {
 namespace {
 
 inline int split_lo(int n, int p, int t) { return (int)((long long)n * t / p); }
+// lump rows whose restriction list is longer than this are summed by a whole warp
+constexpr int kLongList = 16;
 inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 struct Box {
@@ -367,49 +369,76 @@ std::string build_sub(const Ctx& X, int s, SubSym& o) {
     o.diag_of_pos.assign(n, 0);
     for (int pos = 0; pos < n; pos++) o.diag_of_pos[pos] = o.pdiag[o.row_of_pos[pos]];
 
-    // restriction lists by position, owned-cell scatter
+    // fine and lump rows get separate index spaces (fine index / lump index, both in level order),
+    // so the apply can keep them in separate local vectors of their own precision
+    o.fidx_of_row.assign(n, -1);
+    o.cidx_of_row.assign(n, -1);
+    {
+        int nfi = 0, nci = 0;
+        for (int pos = 0; pos < n; pos++) {
+            const int p = o.row_of_pos[pos];
+            if (p < o.nf)
+                o.fidx_of_row[p] = nfi++;
+            else
+                o.cidx_of_row[p] = nci++;
+        }
+    }
+    // restriction: fine rows copy one cell; lump rows sum their cells (far lumps: box sum minus the
+    // near-region cells of the box)
+    o.fcell.assign(o.nf, 0);
+    for (int p = 0; p < o.nf; p++) o.fcell[o.fidx_of_row[p]] = rowcells[rowcells_ptr[p]];
+    const int nc = n - o.nf;
+    std::vector<int> row_of_c(nc);
+    for (int p = o.nf; p < n; p++) row_of_c[o.cidx_of_row[p]] = p;
     o.rptr.assign(1, 0);
     o.rsrc.clear();
-    o.rbox.assign(n, -1);
-    for (int pos = 0; pos < n; pos++) {
-        const int p = o.row_of_pos[pos];
+    o.rbox.assign(nc, -1);
+    o.clong.clear();
+    for (int c = 0; c < nc; c++) {
+        const int p = row_of_c[c];
         if (p < nN) {
             for (int t = rowcells_ptr[p]; t < rowcells_ptr[p + 1]; t++) o.rsrc.push_back(rowcells[t]);
         } else {
             const int J = far_box_of_row[p - nN];
-            o.rbox[pos] = J;
-            for (int c : corr[J]) o.rsrc.push_back(~c);
+            o.rbox[c] = J;
+            for (int cell : corr[J]) o.rsrc.push_back(~cell);
         }
         o.rptr.push_back((int)o.rsrc.size());
+        if (o.rptr[c + 1] - o.rptr[c] > kLongList) o.clong.push_back(c);
     }
     o.own_pos.clear();
     o.own_cell.clear();
     for (int y = own.lo[1]; y < own.hi[1]; y++)
         for (int x = own.lo[0]; x < own.hi[0]; x++)
             for (int z = own.lo[2]; z < own.hi[2]; z++) {
-                const int c = cell_of(g, x, y, z);
-                o.own_cell.push_back(c);
-                o.own_pos.push_back(o.pos_of_row[gmap[gidx(x, y, z)]]);
+                o.own_cell.push_back(cell_of(g, x, y, z));
+                o.own_pos.push_back(o.fidx_of_row[gmap[gidx(x, y, z)]]);
             }
-    o.apply_index_bytes = 4LL * ((long long)o.rptr.size() + (long long)o.rsrc.size() + n + 2LL * o.own_pos.size());
+    o.apply_index_bytes = 4LL * ((long long)o.fcell.size() + (long long)o.rptr.size() + (long long)o.rsrc.size() + nc +
+                                 (long long)o.clong.size() + 2LL * o.own_pos.size());
     o.cells_of_row_ptr = rowcells_ptr;
     o.cells_of_row = rowcells;
     for (int J : far_box_of_row) o.cells_of_row.push_back(-1 - J);  // far rows: -1 - box
 
     // factor streams: forward segments by level, then backward segments by reverse level
-    const size_t esz = X.prec == 0 ? 8 : (X.prec == 1 ? 4 : 2);
+    // bytes of one stored fine block: 9 FP64 / 9 FP32 / 9 FP16 + a 16-bit power-of-two exponent
+    const size_t fbb = X.prec == 0 ? 72 : (X.prec == 1 ? 36 : 20);
     o.lv.assign(nlev, LevelInfo{});
     size_t off = 0;
+    int f0 = 0, c0 = 0;
     for (int l = 0; l < nlev; l++) {
         LevelInfo& L = o.lv[l];
-        L.pos0 = o.lv_pos0[l];
+        L.f0 = f0;
+        L.c0 = c0;
         L.nf = cntf[l];
         L.nc = cntc[l];
+        f0 += L.nf;
+        c0 += L.nc;
         L.eLf = L.eLc = L.eUf = L.eUc = 0;
-        for (int pos = L.pos0; pos < L.pos0 + L.nf + L.nc; pos++) {
+        for (int pos = o.lv_pos0[l]; pos < o.lv_pos0[l + 1]; pos++) {
             const int p = o.row_of_pos[pos];
             const int nl = o.pdiag[p] - o.prp[p], nu = o.prp[p + 1] - o.pdiag[p] - 1;
-            if (pos < L.pos0 + L.nf) {
+            if (p < o.nf) {
                 L.eLf += nl;
                 L.eUf += nu;
             } else {
@@ -418,13 +447,13 @@ std::string build_sub(const Ctx& X, int s, SubSym& o) {
             }
         }
         L.fwd_off = (long long)off;
-        off += al16(4 * (size_t)(L.nf + 1)) + al16(4 * (size_t)L.eLf) + al16(esz * 9 * L.eLf) +
+        off += al16(4 * (size_t)(L.nf + 1)) + al16(4 * (size_t)L.eLf) + al16(fbb * L.eLf) +
                al16(4 * (size_t)(L.nc + 1)) + al16(4 * (size_t)L.eLc) + al16(72 * (size_t)L.eLc);
     }
     for (int l = nlev - 1; l >= 0; l--) {
         LevelInfo& L = o.lv[l];
         L.bwd_off = (long long)off;
-        off += al16(4 * (size_t)(L.nf + 1)) + al16(4 * (size_t)L.eUf) + al16(esz * 9 * L.eUf) + al16(esz * 9 * L.nf) +
+        off += al16(4 * (size_t)(L.nf + 1)) + al16(4 * (size_t)L.eUf) + al16(fbb * L.eUf) + al16(fbb * L.nf) +
                al16(4 * (size_t)(L.nc + 1)) + al16(4 * (size_t)L.eUc) + al16(72 * (size_t)L.eUc) + al16(72 * (size_t)L.nc);
     }
     o.stream.assign(off, 0);
@@ -432,7 +461,7 @@ std::string build_sub(const Ctx& X, int s, SubSym& o) {
     o.pk_off_c.clear();
     o.pk_src_f.clear();
     o.pk_src_c.clear();
-    auto put_rows = [&](size_t& w, int pos_b, int pos_e, bool lower, size_t vsz, bool with_dinv, bool fine_group) {
+    auto put_rows = [&](size_t& w, int pos_b, int pos_e, bool lower, size_t bb, bool with_dinv, bool fine_group) {
         int* ptr = reinterpret_cast<int*>(o.stream.data() + w);
         int ne = 0;
         ptr[0] = 0;
@@ -449,28 +478,30 @@ std::string build_sub(const Ctx& X, int s, SubSym& o) {
             const int p = o.row_of_pos[pos];
             const int tb = lower ? o.prp[p] : o.pdiag[p] + 1, te = lower ? o.pdiag[p] : o.prp[p + 1];
             for (int t = tb; t < te; t++, e++) {
-                col[e] = o.pos_of_row[o.pci[t]];
-                (fine_group ? o.pk_off_f : o.pk_off_c).push_back((long long)(vw + vsz * 9 * e));
+                const int q = o.pci[t];
+                col[e] = q < o.nf ? o.fidx_of_row[q] : ~o.cidx_of_row[q];
+                (fine_group ? o.pk_off_f : o.pk_off_c).push_back((long long)(vw + bb * e));
                 (fine_group ? o.pk_src_f : o.pk_src_c).push_back(t);
             }
         }
-        w = vw + al16(vsz * 9 * ne);
+        w = vw + al16(bb * ne);
         if (with_dinv) {
             for (int pos = pos_b; pos < pos_e; pos++) {
-                (fine_group ? o.pk_off_f : o.pk_off_c).push_back((long long)(w + vsz * 9 * (pos - pos_b)));
+                (fine_group ? o.pk_off_f : o.pk_off_c).push_back((long long)(w + bb * (pos - pos_b)));
                 (fine_group ? o.pk_src_f : o.pk_src_c).push_back(o.diag_of_pos[pos]);
             }
-            w += al16(vsz * 9 * (size_t)(pos_e - pos_b));
+            w += al16(bb * (size_t)(pos_e - pos_b));
         }
     };
     for (int l = 0; l < nlev; l++) {
         const LevelInfo& L = o.lv[l];
+        const int p0 = o.lv_pos0[l];
         size_t w = (size_t)L.fwd_off;
-        put_rows(w, L.pos0, L.pos0 + L.nf, true, esz, false, true);
-        put_rows(w, L.pos0 + L.nf, L.pos0 + L.nf + L.nc, true, 8, false, false);
+        put_rows(w, p0, p0 + L.nf, true, fbb, false, true);
+        put_rows(w, p0 + L.nf, p0 + L.nf + L.nc, true, 72, false, false);
         w = (size_t)L.bwd_off;
-        put_rows(w, L.pos0, L.pos0 + L.nf, false, esz, true, true);
-        put_rows(w, L.pos0 + L.nf, L.pos0 + L.nf + L.nc, false, 8, true, false);
+        put_rows(w, p0, p0 + L.nf, false, fbb, true, true);
+        put_rows(w, p0 + L.nf, p0 + L.nf + L.nc, false, 72, true, false);
     }
     return "";
 }

@@ -46,8 +46,11 @@ struct SubSym {
     std::vector<int> tgt_lv, tgt, pp, ls_lv, diag_of_pos;
     std::vector<int> pair;  // (L slot, U slot) interleaved
     std::vector<int> ls;    // (L slot, diag slot) interleaved
-    // restriction by position and owned-cell scatter
-    std::vector<int> rptr, rsrc, rbox, own_pos, own_cell;
+    // fine index / lump index of every local row (-1 in the other space)
+    std::vector<int> fidx_of_row, cidx_of_row;
+    // restriction: fcell by fine index; lump rows by lump index (rptr/rsrc/rbox), clong = lump
+    // rows with long lists; owned-cell scatter (own_pos = fine index)
+    std::vector<int> fcell, rptr, rsrc, rbox, clong, own_pos, own_cell;
     // factor stream
     std::vector<LevelInfo> lv;
     std::vector<unsigned char> stream;  // indices filled in, values zero

@@ -42,12 +42,14 @@ F_B = 40          # right-hand side
 #: nominal x transmissibility, k = 100 on a 100 x 100 x 2 cell: k * (dy * dz) / dx
 T_NOMINAL = 200.0
 #: pressure accumulation relative to the cell's transmissibility sum (sets the conditioning:
-#: cond(A) ~ 3e4 on the 10 x 10 x 5 grid, inside the 6.7e3 - 2.3e8 range of the paper's Table 1)
-EPS_P = 3.0e-4
+#: cond(A) ~ 1e4 on the 10 x 10 x 5 grid, inside the 6.7e3 - 2.3e8 range of the paper's Table 1)
+EPS_P = 1.0e-3
 #: saturation accumulation relative to the cell's transmissibility sum
-EPS_S = 0.2
+EPS_S = 0.5
 #: well index added to the diagonal of every perforated cell, relative to T_NOMINAL
 WELL = 1.0
+#: standard deviation of the within-layer (cell) part of ln k; sigma scales the layer part
+CELL_NOISE = 0.6
 
 
 def _mix(z: np.ndarray) -> np.ndarray:
@@ -124,10 +126,11 @@ def rhs(n_cells: int, seed: int) -> np.ndarray:
 
 
 def grid_jacobian(nx: int, ny: int, nz: int, seed: int, sigma: float = 1.0, b_seed: int | None = None,
-                  eps_p: float = EPS_P, eps_s: float = EPS_S) -> GridSystem:
+                  eps_p: float = EPS_P, eps_s: float = EPS_S, cell_noise: float | None = None) -> GridSystem:
     """Anisotropic black-oil-like Jacobian with a 7-point stencil of 3x3 blocks.
 
-    ln k_x = ln 100 + sigma * (0.8 g_layer + 0.6 g_cell), k_y = k_x, k_z = 0.1 k_x, cells
+    ln k_x = ln 100 + 0.8 sigma g_layer + CELL_NOISE g_cell (sigma sets the layer-to-layer
+    contrast of the layered field), k_y = k_x, k_z = 0.1 k_x, cells
     100 x 100 x 2, so T = harmonic-mean(k) * area / distance gives T_z / T_x ~ 250.
     Off-diagonal block (row cell c, neighbour n) = -T_cn * M, with
     M = [[lt, c01, c02], [w1, u*d11, u*d12], [w2, u*d21, u*d22]] and u = 1 when n is upstream of c
@@ -142,7 +145,8 @@ def grid_jacobian(nx: int, ny: int, nz: int, seed: int, sigma: float = 1.0, b_se
     c, i, j, k = cell_coords(nx, ny, nz)
     g_layer = normal(seed, F_GLAYER, np.arange(nz))
     g_cell = normal(seed, F_GCELL, c)
-    kx = 100.0 * np.exp(sigma * (0.8 * g_layer[k] + 0.6 * g_cell))
+    cn = CELL_NOISE if cell_noise is None else cell_noise
+    kx = 100.0 * np.exp(sigma * 0.8 * g_layer[k] + cn * g_cell)
     kz = 0.1 * kx
 
     fx = i / (nx - 1) if nx > 1 else np.zeros(n)

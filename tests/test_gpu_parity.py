@@ -105,7 +105,7 @@ def test_apply_mixed_precision_close_to_fp64():
     s = synth.grid_jacobian(g.nx, g.ny, g.nz, seed)
     pc = O.Precond(g, s.row_ptr, s.col_idx, s.vals)
     zo = pc.apply(s.b)
-    for prec, tol in (("fp32", 1e-5), ("fp16s", 5e-2)):
+    for prec, tol in (("fp32", 1e-5), ("fp16s", 1e-2)):
         z = gpu_solver(g, s, precision=prec).apply(s.b)
         assert rel(z, zo) <= tol, prec
 
@@ -264,3 +264,19 @@ def test_configuration_64x64x16_k64():
     x32, i32 = s32.solve(s.b, 1e-8, 2000)
     r = s.b - O.spmv(s.row_ptr, s.col_idx, s.vals, x32)
     assert i32["converged"] and np.linalg.norm(r) / np.linalg.norm(s.b) <= 1e-8
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16s"])
+def test_kernel_variants_are_bitwise_identical(prec):
+    """Shared-memory vs device-memory local vectors, cooperative vs per-projection Gram-Schmidt."""
+    g, seed = GEOMS["k32"]
+    s = synth.grid_jacobian(g.nx, g.ny, g.nz, seed)
+    sol = gpu_solver(g, s, precision=prec)
+    z1 = sol.apply(s.b)
+    x1, i1 = sol.solve(s.b, 1e-8, 2000)
+    sol.set_tuning(apply_smem=False, coop_ortho=False)
+    z2 = sol.apply(s.b)
+    x2, i2 = sol.solve(s.b, 1e-8, 2000)
+    np.testing.assert_array_equal(z1, z2)
+    np.testing.assert_array_equal(x1, x2)
+    assert i1 == i2
