@@ -83,7 +83,7 @@ struct asm_ctx {
     DBuf d_slot, d_dpiv, d_aptr, d_aloc, d_acs;
     DBuf d_fp;  // factor program arrays (one allocation, see upload_factor_program)
     DBuf d_stream, d_pk_off_f, d_pk_src_f, d_pk_off_c, d_pk_src_c;
-    DBuf d_lv, d_rlists, d_y;
+    DBuf d_lv, d_rlists, d_y, d_corr_cells, d_corr, d_dev_err;
     int apply_smem = 0;  // dynamic shared memory of the apply (0: local vectors in d_y)
     DBuf d_factdesc, d_subdesc_single;
     DBuf d_err;
@@ -169,9 +169,9 @@ void upload_symbolic(asm_ctx* h) {
         fpi = (fpi + 1) / 2 * 2;
         fpi += (long long)o.pair.size() + (long long)o.ls.size();
         fp_base[s + 1] = fp_base[s] + fpi;
-        long long rli = (long long)o.fcell.size() + o.rptr.size() + o.rsrc.size() + o.rbox.size() + o.clong.size() +
-                        o.own_pos.size() + o.own_cell.size();
-        rl_base[s + 1] = rl_base[s] + rli;
+        long long rli = (long long)o.fcell.size() + o.rptr.size() + o.rsrc.size() + o.rbox.size() + o.rcorr.size() +
+                        o.clong.size() + o.own_pos.size() + o.own_cell.size() + 2LL * o.chunk_off.size();
+        rl_base[s + 1] = rl_base[s] + (rli + 1) / 2 * 2;  // even: each block starts 8-byte aligned
         lv_base[s + 1] = lv_base[s] + o.nlev;
         npf += (long long)o.pk_off_f.size();
         npc += (long long)o.pk_off_c.size();
@@ -241,8 +241,10 @@ void upload_symbolic(asm_ctx* h) {
     }
     // streams + pack lists + level tables + restriction lists
     h->d_stream.alloc((size_t)h->stream_base[K]);
-    h->d_lv.alloc((size_t)std::max<long long>(1, lv_base[K]) * sizeof(LevelInfo));
-    h->d_rlists.alloc((size_t)std::max<long long>(1, rl_base[K]) * 4);
+    h->d_rlists.alloc((size_t)std::max<long long>(2, rl_base[K]) * 4);
+    std::vector<BoxItem> corr_items;
+    std::vector<int> corr_cells;
+    int corr_base = 0;
     std::vector<long long> offf, offc;
     std::vector<int> srcf, srcc;
     offf.reserve(npf);
@@ -255,9 +257,6 @@ void upload_symbolic(asm_ctx* h) {
         const SubSym& o = S.subs[s];
         if (!o.stream.empty())
             ck(cudaMemcpyAsync(h->d_stream.as<unsigned char>() + h->stream_base[s], o.stream.data(), o.stream.size(),
-                               cudaMemcpyHostToDevice, st));
-        if (o.nlev)
-            ck(cudaMemcpyAsync(h->d_lv.as<LevelInfo>() + lv_base[s], o.lv.data(), o.lv.size() * sizeof(LevelInfo),
                                cudaMemcpyHostToDevice, st));
         for (size_t i = 0; i < o.pk_off_f.size(); i++) {
             offf.push_back(h->stream_base[s] + o.pk_off_f[i]);
@@ -279,20 +278,36 @@ void upload_symbolic(asm_ctx* h) {
         sd.sys = 0;
         sd.nf = o.nf;
         sd.nc = o.n - o.nf;
-        sd.nlev = o.nlev;
+        sd.n_chunks = (int)o.chunk_off.size();
+        sd.n_fwd = o.n_fwd_chunks;
         sd.n_own = (int)o.own_pos.size();
         sd.n_long = (int)o.clong.size();
-        sd.lv = h->d_lv.as<LevelInfo>() + lv_base[s];
+        sd.corr0 = corr_base;
         sd.stream = h->d_stream.as<unsigned char>() + h->stream_base[s];
         sd.y = h->d_y.as<double>() + h->row_base[s] * 3;
+        {
+            // the chunk table goes first: base is 8-byte aligned, so the int2 entries are too
+            std::vector<int> ch;
+            for (size_t i = 0; i < o.chunk_off.size(); i++) {
+                ch.push_back((int)o.chunk_off[i]);
+                ch.push_back(o.chunk_bytes[i]);
+            }
+            sd.chunks = reinterpret_cast<const int2*>(put(ch));
+        }
         sd.fcell = put(o.fcell);
         sd.rptr = put(o.rptr);
         sd.rsrc = put(o.rsrc);
         sd.rbox = put(o.rbox);
+        sd.rcorr = put(o.rcorr);
         sd.clong = put(o.clong);
         sd.own_pos = put(o.own_pos);
         sd.own_cell = put(o.own_cell);
         h->apply_smem = std::max<int>(h->apply_smem, (int)apply_smem_bytes(o.nf, o.n - o.nf, S.prec));
+        for (size_t k = 0; k + 1 < o.corr_ptr.size(); k++)
+            corr_items.push_back(BoxItem{0, corr_base + (int)k, (int)corr_cells.size() + o.corr_ptr[k],
+                                         (int)corr_cells.size() + o.corr_ptr[k + 1], 1, 0, nullptr});
+        corr_cells.insert(corr_cells.end(), o.corr_cells.begin(), o.corr_cells.end());
+        corr_base += (int)o.corr_ptr.size() - 1;
         if (!rl.empty()) ck(cudaMemcpyAsync(base, rl.data(), rl.size() * 4, cudaMemcpyHostToDevice, st));
         sync(h);
     }
@@ -302,25 +317,30 @@ void upload_symbolic(asm_ctx* h) {
     h->d_pk_src_f.upload(srcf, st);
     h->d_pk_off_c.upload(offc, st);
     h->d_pk_src_c.upload(srcc, st);
-    // far boxes and coarse matrix
+    // far boxes, their near-region corrections, and the coarse matrix
+    h->box_items.clear();
     if (S.g.far_mode != 0) {
         h->d_bcell.upload(S.bcell, st);
         h->d_cptr.upload(S.cptr, st);
         h->d_cloc.upload(S.cloc, st);
         h->d_cval.alloc((size_t)std::max(1, S.nC) * 9 * sizeof(double));
         h->d_boxsum.alloc((size_t)std::max(1, S.nboxes) * 3 * sizeof(double));
-        h->box_items.clear();
         for (int b = 0; b < S.nboxes; b++)
-            h->box_items.push_back(BoxItem{0, b, S.bptr[b], S.bptr[b + 1], h->d_bcell.as<int>()});
+            h->box_items.push_back(BoxItem{0, b, S.bptr[b], S.bptr[b + 1], 0, 0, h->d_bcell.as<int>()});
     } else {
         h->d_cval.alloc(16);
         h->d_boxsum.alloc(16);
-        h->box_items.clear();
+    }
+    h->d_corr_cells.upload(corr_cells, st);
+    h->d_corr.alloc((size_t)std::max(1, corr_base) * 3 * sizeof(double));
+    for (BoxItem& it : corr_items) {
+        it.cells = h->d_corr_cells.as<int>();
+        h->box_items.push_back(it);
     }
     // local vectors in shared memory when they fit next to the kernel's static needs
     int dev_smem = 0;
     ck(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-    if (h->apply_smem > dev_smem - 1024) h->apply_smem = 0;
+    if ((size_t)h->apply_smem + apply_ring_bytes() > (size_t)dev_smem - 1024) h->apply_smem = 0;
     h->d_subdesc_single.upload(h->sub_desc, st);
     h->d_err.alloc(sizeof(FactErr));
     sync(h);
@@ -361,6 +381,12 @@ void ensure_workspace(asm_ctx* h) {
     t.ell_w = h->pat.ell_w;
     t.rows_pad = h->pat.rows_pad;
     t.boxsum = h->d_boxsum.as<double>();
+    t.corr = h->d_corr.p ? h->d_corr.as<double>() : h->d_boxsum.as<double>();
+    if (!h->d_dev_err.p) {
+        h->d_dev_err.alloc(16);
+        h->d_dev_err.zero(h->stream);
+    }
+    t.dev_err = h->d_dev_err.as<int>();
     std::vector<SysTab> tabs{t};
     h->d_tab1.upload(tabs, h->stream);
     std::vector<VecItem> vi;
@@ -373,6 +399,16 @@ void ensure_workspace(asm_ctx* h) {
     h->n_row1 = (int)ri.size();
     h->d_box1.upload(h->box_items, h->stream);
     sync(h);
+}
+
+// device status word: nonzero after a bounded wait of a kernel expired; read and clear
+bool take_dev_err(asm_ctx* h) {
+    if (!h->d_dev_err.p) return false;
+    int e = 0;
+    ck(cudaMemcpyAsync(&e, h->d_dev_err.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    sync(h);
+    if (e) h->d_dev_err.zero(h->stream);
+    return e != 0;
 }
 
 void set_ctl(asm_ctx* h, int apply_in, int apply_out, int spmv_in, int spmv_out, int spmv_b) {
@@ -575,6 +611,8 @@ int run_gmres(std::vector<asm_ctx*>& hs, const double* const* b, double* const* 
     }
     read_ctl(B, st);
     int worst = ASM_OK;
+    for (asm_ctx* h : hs)
+        if (take_dev_err(h)) worst = ASM_ERR_TIMEOUT;
     for (size_t k = 0; k < hs.size(); k++) {
         asm_ctx* h = hs[k];
         const int* c = B.pinned + k * C_NCTL;
@@ -591,7 +629,7 @@ int run_gmres(std::vector<asm_ctx*>& hs, const double* const* b, double* const* 
             infos[k].status = status;
             infos[k].rel_residual = sc[0] > 0 ? sc[1] / sc[0] : 0.0;
         }
-        if (status != ASM_OK) worst = status;
+        if (status != ASM_OK && worst != ASM_ERR_TIMEOUT) worst = status;
     }
     return worst;
 }
@@ -827,7 +865,7 @@ int asm_apply_precond(asm_handle h, const double* r, double* z, int on_device) {
         h->prof.kernel_launches += 2;
         copy_out(h, z, out, bytes, on_device);
         sync(h);
-        return ASM_OK;
+        return take_dev_err(h) ? ASM_ERR_TIMEOUT : ASM_OK;
     });
 }
 
@@ -899,7 +937,7 @@ int asm_get_stats(asm_handle h, asm_stats* st) {
         st->local_blocks = S.total_slots;
         long long fb = 0, ib = 0;
         for (const SubSym& o : S.subs) {
-            fb += (long long)o.stream.size() + (long long)o.lv.size() * sizeof(LevelInfo);
+            fb += (long long)o.stream.size();
             ib += o.apply_index_bytes;
         }
         st->factor_bytes = fb;

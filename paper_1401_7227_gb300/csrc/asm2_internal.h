@@ -14,6 +14,8 @@ namespace asm2 {
 // (n3 = 3 * n_cells rounded up to VEC_CHUNK), addressed by slot number.
 // ---------------------------------------------------------------------------------------------
 constexpr int VEC_CHUNK = 2048;   // elements per vector work item (256 threads x 8)
+constexpr int kStreamChunk = 16384;  // bytes of one factor-stream chunk / shared-memory ring slot
+constexpr int kStreamSlots = 4;      // ring slots of the apply (chunks in flight per CTA)
 constexpr int VEC_THREADS = 256;
 enum VecSlot { VX = 0, VB = 1, VR = 2, VW = 3, VZ = 4, VU = 5, VV0 = 6 };  // V_k = VV0 + k; Z_k after V
 
@@ -88,6 +90,8 @@ struct SysTab {
     int rows_pad;
     // preconditioner
     double* boxsum;      // [n_boxes * 3] far-box sums of the apply input
+    double* corr;        // [n_corr * 3] near-region sums subtracted from far-lump box sums
+    int* dev_err;        // device status word: nonzero after a bounded wait expired
 };
 
 // Work items
@@ -97,9 +101,10 @@ struct VecItem {   // VEC_CHUNK elements [e0, e0 + VEC_CHUNK) of system sys; chu
 struct RowItem {   // rows [r0, r0 + 256) of system sys
     int sys, r0;
 };
-struct BoxItem {   // far box `box` of system sys: cells bcell[b0 .. b1)
-    int sys, box, b0, b1;
-    const int* bcell;
+struct BoxItem {   // sum over cells[b0 .. b1) of the apply input into boxsum[out] (kind 0) or corr[out] (kind 1)
+    int sys, out, b0, b1;
+    int kind, pad_;
+    const int* cells;
 };
 
 // One wavefront level of a local factor: its nf fine rows have fine indices f0 .. f0+nf-1 and
@@ -117,16 +122,19 @@ struct SubDesc {
     int sys;
     int nf;           // fine rows
     int nc;           // lump rows
-    int nlev;
+    int n_chunks;     // factor-stream chunks (forward then backward)
+    int n_fwd;        // forward chunks
     int n_own;
     int n_long;       // lump rows restricted by a whole warp
-    const LevelInfo* lv;
-    const unsigned char* stream;
+    int corr0;        // first correction sum of this subdomain in SysTab::corr
+    const int2* chunks;          // (byte offset, bytes) of every chunk, consumption order
+    const unsigned char* stream; // 16-byte aligned
     double* y;        // global scratch for the local vectors when they do not fit in shared memory
     const int* fcell; // [nf] cell of each fine row
-    const int* rptr;  // [nc + 1] restriction sources of the lump rows
-    const int* rsrc;  // >= 0: + r[cell]; < 0: - r[~cell]
-    const int* rbox;  // [nc] far box whose sum is added first, or -1
+    const int* rptr;  // [nc + 1] cells summed into each near lump (far lumps: empty)
+    const int* rsrc;
+    const int* rbox;  // [nc] far box whose sum is the far lump's base, or -1
+    const int* rcorr; // [nc] correction sum subtracted from it (index from corr0), or -1
     const int* clong; // [n_long] lump rows with long source lists
     const int* own_pos;  // fine index of each owned cell
     const int* own_cell;
@@ -170,10 +178,12 @@ void launch_ell_fill(const double* bsr_vals, const int* ell_loc, long long nnzb,
                      int on_device_layout, cudaStream_t st);
 
 void launch_boxsum(const SysTab* st_tab, const BoxItem* items, int nitems, cudaStream_t st);
-// smem_bytes: dynamic shared memory for the local vectors (0 = use the global scratch in SubDesc.y)
-void launch_apply(const SysTab* st_tab, const SubDesc* subs, int nsub, int prec, int smem_bytes, cudaStream_t st);
-// shared memory the local vectors of a subdomain need (nf fine rows, nc lump rows)
+// ysmem: shared memory for the local vectors (0 = they stay in the global scratch SubDesc.y);
+// the ring of factor-stream slots is added on top
+void launch_apply(const SysTab* st_tab, const SubDesc* subs, int nsub, int prec, int ysmem, cudaStream_t st);
+// shared memory the local vectors of a subdomain need (nf fine rows, nc lump rows), and the ring
 size_t apply_smem_bytes(int nf, int nc, int prec);
+size_t apply_ring_bytes();
 void launch_spmv(const SysTab* st_tab, const RowItem* items, int nitems, cudaStream_t st);
 
 void launch_init(const SysTab* tab, const VecItem* items, int nitems, cudaStream_t st);

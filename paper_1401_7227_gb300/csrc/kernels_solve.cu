@@ -43,22 +43,24 @@ struct FineBlock<double> {
 };
 
 // ------------------------------------------------------------------------------------------
-// far-box sums of the apply input: boxsum[b] = sum over the cells of far box b
+// gather sums of the apply input: far-box sums (kind 0) and, per subdomain, the sums of the
+// near-region cells of each far box (kind 1); a far lump's restricted residual is their difference
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_boxsum(const SysTab* __restrict__ tab, const BoxItem* __restrict__ items) {
+__global__ void __launch_bounds__(128) k_sums(const SysTab* __restrict__ tab, const BoxItem* __restrict__ items) {
     const BoxItem it = items[blockIdx.x];
     const SysTab& st = tab[it.sys];
     const int in = st.ctl[C_APPLY_IN];
     if (in < 0) return;
     const double* r = st.ws + (long long)in * st.n3p;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+#pragma unroll 4
     for (int i = it.b0 + threadIdx.x; i < it.b1; i += blockDim.x) {
-        const long long c = (long long)it.bcell[i] * 3;
+        const long long c = (long long)it.cells[i] * 3;
         a0 += r[c];
         a1 += r[c + 1];
         a2 += r[c + 2];
     }
-    __shared__ double red[3][256];
+    __shared__ double red[3][128];
     red[0][threadIdx.x] = a0;
     red[1][threadIdx.x] = a1;
     red[2][threadIdx.x] = a2;
@@ -71,7 +73,8 @@ __global__ void __launch_bounds__(256) k_boxsum(const SysTab* __restrict__ tab, 
         }
         __syncthreads();
     }
-    if (threadIdx.x < 3) st.boxsum[(long long)it.box * 3 + threadIdx.x] = red[threadIdx.x][0];
+    double* out = it.kind == 0 ? st.boxsum : st.corr;
+    if (threadIdx.x < 3) out[(long long)it.out * 3 + threadIdx.x] = red[threadIdx.x][0];
 }
 
 // ------------------------------------------------------------------------------------------
@@ -110,11 +113,146 @@ __device__ __forceinline__ void warp_sum3(double& a0, double& a1, double& a2) {
     }
 }
 
-template <typename TF, bool SMEM>
-__global__ void __launch_bounds__(256) k_apply(const SysTab* __restrict__ tab, const SubDesc* __restrict__ subs) {
+// TMA bulk copies into a ring of shared-memory slots, completion tracked by mbarriers.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false once the iteration limit expired (the caller reports ASM_ERR_TIMEOUT).
+constexpr long long kWaitLimit = 1LL << 22;
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+    for (long long i = 0; i < kWaitLimit; i++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+constexpr int kRingBytes = kStreamSlots * kStreamChunk;
+constexpr int kRingHeader = 64;  // mbarriers
+
+// One chunk of the forward (lower = true) or backward sweep, read from shared memory.
+template <typename TF>
+__device__ __forceinline__ void sweep_chunk(const unsigned char* base, bool lower, typename Compute<TF>::T* yf,
+                                            double* yc) {
     using TC = typename Compute<TF>::T;
     constexpr int FB = FineBlock<TF>::bytes;
-    extern __shared__ __align__(16) double smem[];
+    const int* hdr = reinterpret_cast<const int*>(base);
+    const int f0 = hdr[0], nf = hdr[1], c0 = hdr[2], nc = hdr[3], ef = hdr[4], ec = hdr[5];
+    const unsigned char* p = base + 32;
+    const int* fptr = reinterpret_cast<const int*>(p);
+    p += align16(4 * (size_t)(nf + 1));
+    const int* fcol = reinterpret_cast<const int*>(p);
+    p += align16(4 * (size_t)ef);
+    const unsigned char* fval = p;
+    p += align16((size_t)FB * ef);
+    const unsigned char* fdi = p;
+    if (!lower) p += align16((size_t)FB * nf);
+    const int* cptr = reinterpret_cast<const int*>(p);
+    p += align16(4 * (size_t)(nc + 1));
+    const int* ccol = reinterpret_cast<const int*>(p);
+    p += align16(4 * (size_t)ec);
+    const double* cval = reinterpret_cast<const double*>(p);
+    p += align16(72 * (size_t)ec);
+    const double* cdi = reinterpret_cast<const double*>(p);
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
+    for (int t = tid; t < nf; t += nt) {
+        const int f = f0 + t;
+        TC a0 = yf[3 * f], a1 = yf[3 * f + 1], a2 = yf[3 * f + 2];
+        const int e0 = fptr[t], e1 = fptr[t + 1];
+        for (int e = e0; e < e1; e++) {
+            TC v[9];
+            load_fine<TF>(fval + (size_t)FB * e, v);
+            const int c = fcol[e];
+            TC x0, x1, x2;
+            if (c >= 0) {
+                x0 = yf[3 * c];
+                x1 = yf[3 * c + 1];
+                x2 = yf[3 * c + 2];
+            } else {
+                x0 = (TC)yc[3 * ~c];
+                x1 = (TC)yc[3 * ~c + 1];
+                x2 = (TC)yc[3 * ~c + 2];
+            }
+            a0 -= v[0] * x0 + v[1] * x1 + v[2] * x2;
+            a1 -= v[3] * x0 + v[4] * x1 + v[5] * x2;
+            a2 -= v[6] * x0 + v[7] * x1 + v[8] * x2;
+        }
+        if (lower) {
+            yf[3 * f] = a0;
+            yf[3 * f + 1] = a1;
+            yf[3 * f + 2] = a2;
+        } else {
+            TC d[9];
+            load_fine<TF>(fdi + (size_t)FB * t, d);
+            yf[3 * f] = d[0] * a0 + d[1] * a1 + d[2] * a2;
+            yf[3 * f + 1] = d[3] * a0 + d[4] * a1 + d[5] * a2;
+            yf[3 * f + 2] = d[6] * a0 + d[7] * a1 + d[8] * a2;
+        }
+    }
+    for (int i = warp; i < nc; i += nwarp) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        for (int e = cptr[i] + lane; e < cptr[i + 1]; e += 32) {
+            const double* v = cval + 9LL * e;
+            const int c = ccol[e];
+            double x0, x1, x2;
+            if (c >= 0) {
+                x0 = yf[3 * c];
+                x1 = yf[3 * c + 1];
+                x2 = yf[3 * c + 2];
+            } else {
+                x0 = yc[3 * ~c];
+                x1 = yc[3 * ~c + 1];
+                x2 = yc[3 * ~c + 2];
+            }
+            a0 += v[0] * x0 + v[1] * x1 + v[2] * x2;
+            a1 += v[3] * x0 + v[4] * x1 + v[5] * x2;
+            a2 += v[6] * x0 + v[7] * x1 + v[8] * x2;
+        }
+        warp_sum3(a0, a1, a2);
+        if (lane == 0) {
+            const int c = c0 + i;
+            const double b0 = yc[3 * c] - a0, b1 = yc[3 * c + 1] - a1, b2 = yc[3 * c + 2] - a2;
+            if (lower) {
+                yc[3 * c] = b0;
+                yc[3 * c + 1] = b1;
+                yc[3 * c + 2] = b2;
+            } else {
+                const double* d = cdi + 9LL * i;
+                yc[3 * c] = d[0] * b0 + d[1] * b1 + d[2] * b2;
+                yc[3 * c + 1] = d[3] * b0 + d[4] * b1 + d[5] * b2;
+                yc[3 * c + 2] = d[6] * b0 + d[7] * b1 + d[8] * b2;
+            }
+        }
+    }
+}
+
+// Fused local solve of one subdomain (one CTA): y = R_i r; y = L^{-1} y; y = U^{-1} y;
+// z[owned cells] = y[owned fine rows] (Eqs. 4.2-4.5).  Thread 0 streams the factor chunks
+// (front to back) into a ring of shared-memory slots with TMA bulk copies; all threads compute
+// from shared memory, one chunk at a time, with a CTA barrier after each chunk (which also orders
+// the wavefront levels).  Fine rows and lump rows live in separate local vectors (fine rows at the
+// factor precision, lumps in FP64), in shared memory when they fit.
+template <typename TF, bool SMEM_Y>
+__global__ void __launch_bounds__(256) k_apply(const SysTab* __restrict__ tab, const SubDesc* __restrict__ subs) {
+    using TC = typename Compute<TF>::T;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const SubDesc sd = subs[blockIdx.x];
     const SysTab& st = tab[sd.sys];
     const int in = st.ctl[C_APPLY_IN];
@@ -122,12 +260,27 @@ __global__ void __launch_bounds__(256) k_apply(const SysTab* __restrict__ tab, c
     const int out = st.ctl[C_APPLY_OUT];
     const double* __restrict__ r = st.ws + (long long)in * st.n3p;
     double* __restrict__ z = st.ws + (long long)out * st.n3p;
-    double* yc = SMEM ? smem : sd.y;
+    unsigned char* ring = smem_raw;
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + kRingBytes);
+    double* yc = SMEM_Y ? reinterpret_cast<double*>(smem_raw + kRingBytes + kRingHeader) : sd.y;
     TC* yf = reinterpret_cast<TC*>(yc + 3 * sd.nc);
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
 
-    // restriction R_i r
+    if (tid == 0) {
+        for (int k = 0; k < kStreamSlots; k++) mbar_init(&bar[k], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int k = 0; k < kStreamSlots && k < sd.n_chunks; k++) {
+            const int2 ch = sd.chunks[k];
+            mbar_expect_tx(&bar[k], (unsigned)ch.y);
+            bulk_load(ring + (size_t)k * kStreamChunk, sd.stream + ch.x, (unsigned)ch.y, &bar[k]);
+        }
+
+    // restriction R_i r (overlaps the first chunk copies)
+#pragma unroll 4
     for (int f = tid; f < sd.nf; f += nt) {
         const double* rc = r + 3LL * sd.fcell[f];
         yf[3 * f] = (TC)rc[0];
@@ -136,21 +289,26 @@ __global__ void __launch_bounds__(256) k_apply(const SysTab* __restrict__ tab, c
     }
     for (int c = tid; c < sd.nc; c += nt) {
         const int i0 = sd.rptr[c], i1 = sd.rptr[c + 1];
-        if (i1 - i0 > 16) continue;  // long lists: below, one warp per row
+        if (i1 - i0 > 16) continue;
         double a0 = 0.0, a1 = 0.0, a2 = 0.0;
         const int b = sd.rbox[c];
         if (b >= 0) {
             a0 = st.boxsum[3 * b];
             a1 = st.boxsum[3 * b + 1];
             a2 = st.boxsum[3 * b + 2];
+            const int k = sd.rcorr[c];
+            if (k >= 0) {
+                const double* q = st.corr + 3LL * (sd.corr0 + k);
+                a0 -= q[0];
+                a1 -= q[1];
+                a2 -= q[2];
+            }
         }
         for (int i = i0; i < i1; i++) {
-            const int cell = sd.rsrc[i];
-            const double sg = cell >= 0 ? 1.0 : -1.0;
-            const double* rc = r + 3LL * (cell >= 0 ? cell : ~cell);
-            a0 += sg * rc[0];
-            a1 += sg * rc[1];
-            a2 += sg * rc[2];
+            const double* rc = r + 3LL * sd.rsrc[i];
+            a0 += rc[0];
+            a1 += rc[1];
+            a2 += rc[2];
         }
         yc[3 * c] = a0;
         yc[3 * c + 1] = a1;
@@ -160,21 +318,13 @@ __global__ void __launch_bounds__(256) k_apply(const SysTab* __restrict__ tab, c
         const int c = sd.clong[k];
         double a0 = 0.0, a1 = 0.0, a2 = 0.0;
         for (int i = sd.rptr[c] + lane; i < sd.rptr[c + 1]; i += 32) {
-            const int cell = sd.rsrc[i];
-            const double sg = cell >= 0 ? 1.0 : -1.0;
-            const double* rc = r + 3LL * (cell >= 0 ? cell : ~cell);
-            a0 += sg * rc[0];
-            a1 += sg * rc[1];
-            a2 += sg * rc[2];
+            const double* rc = r + 3LL * sd.rsrc[i];
+            a0 += rc[0];
+            a1 += rc[1];
+            a2 += rc[2];
         }
         warp_sum3(a0, a1, a2);
         if (lane == 0) {
-            const int b = sd.rbox[c];
-            if (b >= 0) {
-                a0 += st.boxsum[3 * b];
-                a1 += st.boxsum[3 * b + 1];
-                a2 += st.boxsum[3 * b + 2];
-            }
             yc[3 * c] = a0;
             yc[3 * c + 1] = a1;
             yc[3 * c + 2] = a2;
@@ -182,148 +332,25 @@ __global__ void __launch_bounds__(256) k_apply(const SysTab* __restrict__ tab, c
     }
     __syncthreads();
 
-    // forward sweep: y_p -= sum_k L_pk y_k
-    for (int lv = 0; lv < sd.nlev; lv++) {
-        const LevelInfo L = sd.lv[lv];
-        const unsigned char* seg = sd.stream + L.fwd_off;
-        const int* fptr = reinterpret_cast<const int*>(seg);
-        size_t o = align16(4 * (size_t)(L.nf + 1));
-        const int* fcol = reinterpret_cast<const int*>(seg + o);
-        o += align16(4 * (size_t)L.eLf);
-        const unsigned char* fval = seg + o;
-        o += align16((size_t)FB * L.eLf);
-        const int* cptr = reinterpret_cast<const int*>(seg + o);
-        o += align16(4 * (size_t)(L.nc + 1));
-        const int* ccol = reinterpret_cast<const int*>(seg + o);
-        o += align16(4 * (size_t)L.eLc);
-        const double* cval = reinterpret_cast<const double*>(seg + o);
-        for (int t = tid; t < L.nf; t += nt) {
-            const int f = L.f0 + t;
-            TC a0 = yf[3 * f], a1 = yf[3 * f + 1], a2 = yf[3 * f + 2];
-            const int e0 = fptr[t], e1 = fptr[t + 1];
-#pragma unroll 3
-            for (int e = e0; e < e1; e++) {
-                TC v[9];
-                load_fine<TF>(fval + (size_t)FB * e, v);
-                const int c = fcol[e];
-                const TC x0 = yf[3 * c], x1 = yf[3 * c + 1], x2 = yf[3 * c + 2];
-                a0 -= v[0] * x0 + v[1] * x1 + v[2] * x2;
-                a1 -= v[3] * x0 + v[4] * x1 + v[5] * x2;
-                a2 -= v[6] * x0 + v[7] * x1 + v[8] * x2;
+    for (int ci = 0; ci < sd.n_chunks; ci++) {
+        const int slot = ci % kStreamSlots;
+        const bool ok = mbar_wait(&bar[slot], (unsigned)(ci / kStreamSlots) & 1u);
+        if (ok) sweep_chunk<TF>(ring + (size_t)slot * kStreamChunk, ci < sd.n_fwd, yf, yc);
+        if (__syncthreads_or(!ok)) {
+            // a copy did not land in time: report it, wait (bounded) for the copies still in
+            // flight into this CTA's shared memory, and leave
+            if (tid == 0) {
+                atomicExch(st.dev_err, 7);
+                const int last = min(sd.n_chunks, ci + kStreamSlots);
+                for (int k = ci; k < last; k++) mbar_wait(&bar[k % kStreamSlots], (unsigned)(k / kStreamSlots) & 1u);
             }
-            yf[3 * f] = a0;
-            yf[3 * f + 1] = a1;
-            yf[3 * f + 2] = a2;
+            return;
         }
-        for (int i = warp; i < L.nc; i += nwarp) {
-            double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-            for (int e = cptr[i] + lane; e < cptr[i + 1]; e += 32) {
-                const double* v = cval + 9LL * e;
-                const int c = ccol[e];
-                double x0, x1, x2;
-                if (c >= 0) {
-                    x0 = yf[3 * c];
-                    x1 = yf[3 * c + 1];
-                    x2 = yf[3 * c + 2];
-                } else {
-                    x0 = yc[3 * ~c];
-                    x1 = yc[3 * ~c + 1];
-                    x2 = yc[3 * ~c + 2];
-                }
-                a0 += v[0] * x0 + v[1] * x1 + v[2] * x2;
-                a1 += v[3] * x0 + v[4] * x1 + v[5] * x2;
-                a2 += v[6] * x0 + v[7] * x1 + v[8] * x2;
-            }
-            warp_sum3(a0, a1, a2);
-            if (lane == 0) {
-                const int c = L.c0 + i;
-                yc[3 * c] -= a0;
-                yc[3 * c + 1] -= a1;
-                yc[3 * c + 2] -= a2;
-            }
+        if (tid == 0 && ci + kStreamSlots < sd.n_chunks) {
+            const int2 ch = sd.chunks[ci + kStreamSlots];
+            mbar_expect_tx(&bar[slot], (unsigned)ch.y);
+            bulk_load(ring + (size_t)slot * kStreamChunk, sd.stream + ch.x, (unsigned)ch.y, &bar[slot]);
         }
-        __syncthreads();
-    }
-
-    // backward sweep: y_p = D_p^{-1} (y_p - sum_q U_pq y_q), levels in reverse
-    for (int lv = sd.nlev - 1; lv >= 0; lv--) {
-        const LevelInfo L = sd.lv[lv];
-        const unsigned char* seg = sd.stream + L.bwd_off;
-        const int* fptr = reinterpret_cast<const int*>(seg);
-        size_t o = align16(4 * (size_t)(L.nf + 1));
-        const int* fcol = reinterpret_cast<const int*>(seg + o);
-        o += align16(4 * (size_t)L.eUf);
-        const unsigned char* fval = seg + o;
-        o += align16((size_t)FB * L.eUf);
-        const unsigned char* fdi = seg + o;
-        o += align16((size_t)FB * L.nf);
-        const int* cptr = reinterpret_cast<const int*>(seg + o);
-        o += align16(4 * (size_t)(L.nc + 1));
-        const int* ccol = reinterpret_cast<const int*>(seg + o);
-        o += align16(4 * (size_t)L.eUc);
-        const double* cval = reinterpret_cast<const double*>(seg + o);
-        o += align16(8 * 9 * (size_t)L.eUc);
-        const double* cdi = reinterpret_cast<const double*>(seg + o);
-        // lump rows first within the level is not required: rows of one level are independent
-        for (int t = tid; t < L.nf; t += nt) {
-            const int f = L.f0 + t;
-            TC a0 = yf[3 * f], a1 = yf[3 * f + 1], a2 = yf[3 * f + 2];
-            const int e0 = fptr[t], e1 = fptr[t + 1];
-#pragma unroll 3
-            for (int e = e0; e < e1; e++) {
-                TC v[9];
-                load_fine<TF>(fval + (size_t)FB * e, v);
-                const int c = fcol[e];
-                TC x0, x1, x2;
-                if (c >= 0) {
-                    x0 = yf[3 * c];
-                    x1 = yf[3 * c + 1];
-                    x2 = yf[3 * c + 2];
-                } else {
-                    x0 = (TC)yc[3 * ~c];
-                    x1 = (TC)yc[3 * ~c + 1];
-                    x2 = (TC)yc[3 * ~c + 2];
-                }
-                a0 -= v[0] * x0 + v[1] * x1 + v[2] * x2;
-                a1 -= v[3] * x0 + v[4] * x1 + v[5] * x2;
-                a2 -= v[6] * x0 + v[7] * x1 + v[8] * x2;
-            }
-            TC d[9];
-            load_fine<TF>(fdi + (size_t)FB * t, d);
-            yf[3 * f] = d[0] * a0 + d[1] * a1 + d[2] * a2;
-            yf[3 * f + 1] = d[3] * a0 + d[4] * a1 + d[5] * a2;
-            yf[3 * f + 2] = d[6] * a0 + d[7] * a1 + d[8] * a2;
-        }
-        for (int i = warp; i < L.nc; i += nwarp) {
-            double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-            for (int e = cptr[i] + lane; e < cptr[i + 1]; e += 32) {
-                const double* v = cval + 9LL * e;
-                const int c = ccol[e];
-                double x0, x1, x2;
-                if (c >= 0) {
-                    x0 = yf[3 * c];
-                    x1 = yf[3 * c + 1];
-                    x2 = yf[3 * c + 2];
-                } else {
-                    x0 = yc[3 * ~c];
-                    x1 = yc[3 * ~c + 1];
-                    x2 = yc[3 * ~c + 2];
-                }
-                a0 += v[0] * x0 + v[1] * x1 + v[2] * x2;
-                a1 += v[3] * x0 + v[4] * x1 + v[5] * x2;
-                a2 += v[6] * x0 + v[7] * x1 + v[8] * x2;
-            }
-            warp_sum3(a0, a1, a2);
-            if (lane == 0) {
-                const int c = L.c0 + i;
-                const double b0 = yc[3 * c] - a0, b1 = yc[3 * c + 1] - a1, b2 = yc[3 * c + 2] - a2;
-                const double* d = cdi + 9LL * i;
-                yc[3 * c] = d[0] * b0 + d[1] * b1 + d[2] * b2;
-                yc[3 * c + 1] = d[3] * b0 + d[4] * b1 + d[5] * b2;
-                yc[3 * c + 2] = d[6] * b0 + d[7] * b1 + d[8] * b2;
-            }
-        }
-        __syncthreads();
     }
 
     // P_i R_i^T: owned cells take this subdomain's solution; the lumps are discarded
@@ -796,37 +823,43 @@ __global__ void __launch_bounds__(VEC_THREADS) k_ortho_coop(const SysTab* __rest
 }  // namespace
 
 void launch_boxsum(const SysTab* tab, const BoxItem* items, int nitems, cudaStream_t st) {
-    if (nitems > 0) k_boxsum<<<nitems, 256, 0, st>>>(tab, items);
+    if (nitems > 0) k_sums<<<nitems, 128, 0, st>>>(tab, items);
 }
 
 size_t apply_smem_bytes(int nf, int nc, int prec) {
     return 24 * (size_t)nc + (prec == 0 ? 24 : 12) * (size_t)nf;
 }
 
+size_t apply_ring_bytes() { return (size_t)kRingBytes + kRingHeader; }
+
 namespace {
-template <typename TF>
+template <typename TF, bool Y>
 void launch_apply_t(const SysTab* tab, const SubDesc* subs, int nsub, int smem, cudaStream_t st) {
-    if (smem > 0) {
-        static int configured = -1;
-        if (configured < smem) {
-            cudaFuncSetAttribute(k_apply<TF, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            configured = smem;
-        }
-        k_apply<TF, true><<<nsub, 256, smem, st>>>(tab, subs);
-    } else {
-        k_apply<TF, false><<<nsub, 256, 0, st>>>(tab, subs);
+    static int configured = -1;
+    if (configured < smem) {
+        cudaFuncSetAttribute(k_apply<TF, Y>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        configured = smem;
     }
+    k_apply<TF, Y><<<nsub, 256, smem, st>>>(tab, subs);
+}
+template <typename TF>
+void launch_apply_p(const SysTab* tab, const SubDesc* subs, int nsub, int ysmem, cudaStream_t st) {
+    const int ring = (int)apply_ring_bytes();
+    if (ysmem > 0)
+        launch_apply_t<TF, true>(tab, subs, nsub, ring + ysmem, st);
+    else
+        launch_apply_t<TF, false>(tab, subs, nsub, ring, st);
 }
 }  // namespace
 
-void launch_apply(const SysTab* tab, const SubDesc* subs, int nsub, int prec, int smem, cudaStream_t st) {
+void launch_apply(const SysTab* tab, const SubDesc* subs, int nsub, int prec, int ysmem, cudaStream_t st) {
     if (nsub <= 0) return;
     if (prec == 0)
-        launch_apply_t<double>(tab, subs, nsub, smem, st);
+        launch_apply_p<double>(tab, subs, nsub, ysmem, st);
     else if (prec == 1)
-        launch_apply_t<float>(tab, subs, nsub, smem, st);
+        launch_apply_p<float>(tab, subs, nsub, ysmem, st);
     else
-        launch_apply_t<__half>(tab, subs, nsub, smem, st);
+        launch_apply_p<__half>(tab, subs, nsub, ysmem, st);
 }
 
 void launch_spmv(const SysTab* tab, const RowItem* items, int nitems, cudaStream_t st) {

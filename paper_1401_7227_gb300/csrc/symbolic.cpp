@@ -24,6 +24,8 @@ namespace {
 inline int split_lo(int n, int p, int t) { return (int)((long long)n * t / p); }
 // lump rows whose restriction list is longer than this are summed by a whole warp
 constexpr int kLongList = 16;
+// largest factor-stream chunk (one shared-memory ring slot of the apply)
+constexpr int kChunkBytes = asm2::kStreamChunk;
 inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 struct Box {
@@ -390,10 +392,15 @@ std::string build_sub(const Ctx& X, int s, SubSym& o) {
     const int nc = n - o.nf;
     std::vector<int> row_of_c(nc);
     for (int p = o.nf; p < n; p++) row_of_c[o.cidx_of_row[p]] = p;
+    // near lumps: their cells; far lumps: box sum minus the sum of the box's near-region cells,
+    // the latter gathered by a separate pass over corr_cells
     o.rptr.assign(1, 0);
     o.rsrc.clear();
     o.rbox.assign(nc, -1);
+    o.rcorr.assign(nc, -1);
     o.clong.clear();
+    o.corr_ptr.assign(1, 0);
+    o.corr_cells.clear();
     for (int c = 0; c < nc; c++) {
         const int p = row_of_c[c];
         if (p < nN) {
@@ -401,7 +408,11 @@ std::string build_sub(const Ctx& X, int s, SubSym& o) {
         } else {
             const int J = far_box_of_row[p - nN];
             o.rbox[c] = J;
-            for (int cell : corr[J]) o.rsrc.push_back(~cell);
+            if (!corr[J].empty()) {
+                o.rcorr[c] = (int)o.corr_ptr.size() - 1;
+                o.corr_cells.insert(o.corr_cells.end(), corr[J].begin(), corr[J].end());
+                o.corr_ptr.push_back((int)o.corr_cells.size());
+            }
         }
         o.rptr.push_back((int)o.rsrc.size());
         if (o.rptr[c + 1] - o.rptr[c] > kLongList) o.clong.push_back(c);
@@ -414,68 +425,108 @@ std::string build_sub(const Ctx& X, int s, SubSym& o) {
                 o.own_cell.push_back(cell_of(g, x, y, z));
                 o.own_pos.push_back(o.fidx_of_row[gmap[gidx(x, y, z)]]);
             }
-    o.apply_index_bytes = 4LL * ((long long)o.fcell.size() + (long long)o.rptr.size() + (long long)o.rsrc.size() + nc +
-                                 (long long)o.clong.size() + 2LL * o.own_pos.size());
+    o.apply_index_bytes = 4LL * ((long long)o.fcell.size() + (long long)o.rptr.size() + (long long)o.rsrc.size() + 2LL * nc +
+                                 (long long)o.clong.size() + 2LL * o.own_pos.size() + (long long)o.corr_cells.size() +
+                                 (long long)o.corr_ptr.size());
     o.cells_of_row_ptr = rowcells_ptr;
     o.cells_of_row = rowcells;
     for (int J : far_box_of_row) o.cells_of_row.push_back(-1 - J);  // far rows: -1 - box
 
-    // factor streams: forward segments by level, then backward segments by reverse level
-    // bytes of one stored fine block: 9 FP64 / 9 FP32 / 9 FP16 + a 16-bit power-of-two exponent
-    const size_t fbb = X.prec == 0 ? 72 : (X.prec == 1 ? 36 : 20);
-    o.lv.assign(nlev, LevelInfo{});
-    size_t off = 0;
-    int f0 = 0, c0 = 0;
-    for (int l = 0; l < nlev; l++) {
-        LevelInfo& L = o.lv[l];
-        L.f0 = f0;
-        L.c0 = c0;
-        L.nf = cntf[l];
-        L.nc = cntc[l];
-        f0 += L.nf;
-        c0 += L.nc;
-        L.eLf = L.eLc = L.eUf = L.eUc = 0;
-        for (int pos = o.lv_pos0[l]; pos < o.lv_pos0[l + 1]; pos++) {
-            const int p = o.row_of_pos[pos];
-            const int nl = o.pdiag[p] - o.prp[p], nu = o.prp[p + 1] - o.pdiag[p] - 1;
-            if (p < o.nf) {
-                L.eLf += nl;
-                L.eUf += nu;
-            } else {
-                L.eLc += nl;
-                L.eUc += nu;
+    // Factor stream: self-contained chunks of at most kChunkBytes, each holding rows of one wavefront
+    // level (fine rows at the factor precision, lump rows in FP64): all forward chunks in level
+    // order, then all backward chunks in reverse level order -- the order the apply consumes them,
+    // so the stream is read front to back.  Chunk layout (every array 16-byte aligned):
+    //   header int[8] = {f0, nf, c0, nc, nef, nec, last_in_level, bytes}
+    //   fptr[nf+1] fcol[nef] fval[nef blocks] (fdinv[nf blocks]) cptr[nc+1] ccol[nec] cval[nec] (cdinv[nc])
+    // Columns: fine index (>= 0) or ~lump index.
+    const size_t fbb = X.prec == 0 ? 72 : (X.prec == 1 ? 36 : 20);  // FP64 / FP32 / FP16 + exponent
+    struct Piece {
+        int lv, pos_f, nf, pos_c, nc;
+        bool fwd, last;
+    };
+    std::vector<Piece> pieces;
+    auto nl = [&](int p) { return o.pdiag[p] - o.prp[p]; };
+    auto nu = [&](int p) { return o.prp[p + 1] - o.pdiag[p] - 1; };
+    auto chunk_bytes = [&](int nf_, int ef, int nc_, int ec, bool fwd) {
+        size_t b = 32 + al16(4 * (size_t)(nf_ + 1)) + al16(4 * (size_t)ef) + al16(fbb * ef) + al16(4 * (size_t)(nc_ + 1)) +
+                   al16(4 * (size_t)ec) + al16(72 * (size_t)ec);
+        if (!fwd) b += al16(fbb * nf_) + al16(72 * (size_t)nc_);
+        return b;
+    };
+    for (int pass = 0; pass < 2; pass++) {
+        const bool fwd = pass == 0;
+        for (int li = 0; li < nlev; li++) {
+            const int l = fwd ? li : nlev - 1 - li;
+            const int p0 = o.lv_pos0[l], pf_end = o.lv_pos0[l] + cntf[l], pc_end = o.lv_pos0[l + 1];
+            int pf = p0, pc = pf_end;
+            while (pf < pf_end || pc < pc_end) {
+                Piece pc_{l, pf, 0, pc, 0, fwd, false};
+                int ef = 0, ec = 0;
+                while (pf < pf_end) {
+                    const int p = o.row_of_pos[pf];
+                    const int e = fwd ? nl(p) : nu(p);
+                    if (chunk_bytes(pc_.nf + 1, ef + e, 0, 0, fwd) > (size_t)kChunkBytes - 256) break;
+                    ef += e;
+                    pc_.nf++;
+                    pf++;
+                }
+                if (pf == pf_end) {
+                    while (pc < pc_end) {
+                        const int p = o.row_of_pos[pc];
+                        const int e = fwd ? nl(p) : nu(p);
+                        if (chunk_bytes(pc_.nf, ef, pc_.nc + 1, ec + e, fwd) > (size_t)kChunkBytes) break;
+                        ec += e;
+                        pc_.nc++;
+                        pc++;
+                    }
+                }
+                if (pc_.nf == 0 && pc_.nc == 0) return "a single row does not fit in a stream chunk";
+                pc_.last = pf == pf_end && pc == pc_end;
+                pieces.push_back(pc_);
             }
         }
-        L.fwd_off = (long long)off;
-        off += al16(4 * (size_t)(L.nf + 1)) + al16(4 * (size_t)L.eLf) + al16(fbb * L.eLf) +
-               al16(4 * (size_t)(L.nc + 1)) + al16(4 * (size_t)L.eLc) + al16(72 * (size_t)L.eLc);
     }
-    for (int l = nlev - 1; l >= 0; l--) {
-        LevelInfo& L = o.lv[l];
-        L.bwd_off = (long long)off;
-        off += al16(4 * (size_t)(L.nf + 1)) + al16(4 * (size_t)L.eUf) + al16(fbb * L.eUf) + al16(fbb * L.nf) +
-               al16(4 * (size_t)(L.nc + 1)) + al16(4 * (size_t)L.eUc) + al16(72 * (size_t)L.eUc) + al16(72 * (size_t)L.nc);
+    // fine index / lump index of the first row of each position range
+    std::vector<int> fidx_pos(n + 1, 0), cidx_pos(n + 1, 0);
+    for (int pos = 0; pos < n; pos++) {
+        const int p = o.row_of_pos[pos];
+        fidx_pos[pos + 1] = fidx_pos[pos] + (p < o.nf ? 1 : 0);
+        cidx_pos[pos + 1] = cidx_pos[pos] + (p < o.nf ? 0 : 1);
     }
-    o.stream.assign(off, 0);
+    size_t total = 0;
+    o.chunk_off.clear();
+    o.chunk_bytes.clear();
+    o.n_fwd_chunks = 0;
+    for (const Piece& pc_ : pieces) {
+        int ef = 0, ec = 0;
+        for (int k = 0; k < pc_.nf; k++) ef += pc_.fwd ? nl(o.row_of_pos[pc_.pos_f + k]) : nu(o.row_of_pos[pc_.pos_f + k]);
+        for (int k = 0; k < pc_.nc; k++) ec += pc_.fwd ? nl(o.row_of_pos[pc_.pos_c + k]) : nu(o.row_of_pos[pc_.pos_c + k]);
+        const size_t bytes = chunk_bytes(pc_.nf, ef, pc_.nc, ec, pc_.fwd);
+        o.chunk_off.push_back((long long)total);
+        o.chunk_bytes.push_back((int)bytes);
+        if (pc_.fwd) o.n_fwd_chunks++;
+        total += bytes;
+    }
+    o.stream.assign(total, 0);
     o.pk_off_f.clear();
     o.pk_off_c.clear();
     o.pk_src_f.clear();
     o.pk_src_c.clear();
-    auto put_rows = [&](size_t& w, int pos_b, int pos_e, bool lower, size_t bb, bool with_dinv, bool fine_group) {
+    auto put_rows = [&](size_t& w, int pos_b, int cnt, bool lower, size_t bb, bool with_dinv, bool fine_group) {
         int* ptr = reinterpret_cast<int*>(o.stream.data() + w);
         int ne = 0;
         ptr[0] = 0;
-        for (int pos = pos_b; pos < pos_e; pos++) {
-            const int p = o.row_of_pos[pos];
-            ne += lower ? o.pdiag[p] - o.prp[p] : o.prp[p + 1] - o.pdiag[p] - 1;
-            ptr[pos - pos_b + 1] = ne;
+        for (int k = 0; k < cnt; k++) {
+            const int p = o.row_of_pos[pos_b + k];
+            ne += lower ? nl(p) : nu(p);
+            ptr[k + 1] = ne;
         }
-        w += al16(4 * (size_t)(pos_e - pos_b + 1));
+        w += al16(4 * (size_t)(cnt + 1));
         int* col = reinterpret_cast<int*>(o.stream.data() + w);
         size_t vw = w + al16(4 * (size_t)ne);
         int e = 0;
-        for (int pos = pos_b; pos < pos_e; pos++) {
-            const int p = o.row_of_pos[pos];
+        for (int k = 0; k < cnt; k++) {
+            const int p = o.row_of_pos[pos_b + k];
             const int tb = lower ? o.prp[p] : o.pdiag[p] + 1, te = lower ? o.pdiag[p] : o.prp[p + 1];
             for (int t = tb; t < te; t++, e++) {
                 const int q = o.pci[t];
@@ -486,23 +537,32 @@ std::string build_sub(const Ctx& X, int s, SubSym& o) {
         }
         w = vw + al16(bb * ne);
         if (with_dinv) {
-            for (int pos = pos_b; pos < pos_e; pos++) {
-                (fine_group ? o.pk_off_f : o.pk_off_c).push_back((long long)(w + bb * (pos - pos_b)));
-                (fine_group ? o.pk_src_f : o.pk_src_c).push_back(o.diag_of_pos[pos]);
+            for (int k = 0; k < cnt; k++) {
+                (fine_group ? o.pk_off_f : o.pk_off_c).push_back((long long)(w + bb * k));
+                (fine_group ? o.pk_src_f : o.pk_src_c).push_back(o.diag_of_pos[pos_b + k]);
             }
-            w += al16(bb * (size_t)(pos_e - pos_b));
+            w += al16(bb * (size_t)cnt);
         }
+        return ne;
     };
-    for (int l = 0; l < nlev; l++) {
-        const LevelInfo& L = o.lv[l];
-        const int p0 = o.lv_pos0[l];
-        size_t w = (size_t)L.fwd_off;
-        put_rows(w, p0, p0 + L.nf, true, fbb, false, true);
-        put_rows(w, p0 + L.nf, p0 + L.nf + L.nc, true, 72, false, false);
-        w = (size_t)L.bwd_off;
-        put_rows(w, p0, p0 + L.nf, false, fbb, true, true);
-        put_rows(w, p0 + L.nf, p0 + L.nf + L.nc, false, 72, true, false);
+    for (size_t i = 0; i < pieces.size(); i++) {
+        const Piece& pc_ = pieces[i];
+        size_t w = (size_t)o.chunk_off[i];
+        int* hdr = reinterpret_cast<int*>(o.stream.data() + w);
+        w += 32;
+        const int ef = put_rows(w, pc_.pos_f, pc_.nf, pc_.fwd, fbb, !pc_.fwd, true);
+        const int ec = put_rows(w, pc_.pos_c, pc_.nc, pc_.fwd, 72, !pc_.fwd, false);
+        hdr[0] = fidx_pos[pc_.pos_f];
+        hdr[1] = pc_.nf;
+        hdr[2] = cidx_pos[pc_.pos_c];
+        hdr[3] = pc_.nc;
+        hdr[4] = ef;
+        hdr[5] = ec;
+        hdr[6] = pc_.last ? 1 : 0;
+        hdr[7] = o.chunk_bytes[i];
+        if (w != (size_t)o.chunk_off[i] + (size_t)o.chunk_bytes[i]) return "stream chunk layout mismatch";
     }
+    o.lv.clear();
     return "";
 }
 

@@ -51,8 +51,15 @@ struct SubSym {
     // restriction: fcell by fine index; lump rows by lump index (rptr/rsrc/rbox), clong = lump
     // rows with long lists; owned-cell scatter (own_pos = fine index)
     std::vector<int> fcell, rptr, rsrc, rbox, clong, own_pos, own_cell;
-    // factor stream
+    // far lumps: rcorr = index of the lump's correction list (or -1); corr_ptr/corr_cells = the
+    // near-region cells of each far box, summed by a gather pass and subtracted from the box sum
+    std::vector<int> rcorr, corr_ptr, corr_cells;
+    // factor stream: chunks (byte offset, size) in consumption order; the first n_fwd_chunks
+    // belong to the forward sweep
     std::vector<LevelInfo> lv;
+    std::vector<long long> chunk_off;
+    std::vector<int> chunk_bytes;
+    int n_fwd_chunks = 0;
     std::vector<unsigned char> stream;  // indices filled in, values zero
     std::vector<long long> pk_off_f, pk_off_c;
     std::vector<int> pk_src_f, pk_src_c;
