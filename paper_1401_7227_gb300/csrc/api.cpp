@@ -362,7 +362,7 @@ void ensure_workspace(asm_ctx* h) {
     h->d_scal.zero(h->stream);
     h->d_ctl.alloc(C_NCTL * sizeof(int));
     h->d_ctl.zero(h->stream);
-    h->d_partial.alloc((size_t)4 * h->nchunk * sizeof(double));
+    h->d_partial.alloc((size_t)4 * std::max(h->nchunk, 4096) * sizeof(double));
     h->ws_m = m;
     h->ws_flex = flex;
     SysTab& t = h->tab;
@@ -560,7 +560,7 @@ int run_gmres(std::vector<asm_ctx*>& hs, const double* const* b, double* const* 
         ck(cudaStreamSynchronize(st));
     }
     build_batch(B, st);
-    if (hs.size() == 1 && !hs[0]->no_coop) B.coop_grid = std::min(ortho_coop_grid(hs[0]->device), hs[0]->nchunk);
+    if (hs.size() == 1 && !hs[0]->no_coop) B.coop_grid = ortho_coop_grid(hs[0]->device);
     {
         // initial step: x = 0, r = b, beta = ||b||
         const SysTab* tab = B.d_tab.as<SysTab>();

