@@ -207,12 +207,52 @@ __device__ __forceinline__ void sweep_chunk(const unsigned char* base, bool lowe
             yf[3 * f + 2] = d[6] * a0 + d[7] * a1 + d[8] * a2;
         }
     }
-    // lump rows: four lanes per row, eight rows per warp; FP64 throughput is scarce on this part,
-    // so the row sums use two shuffle rounds rather than a full warp tree
+    // Lump rows are FP64, and an FP64 warp instruction keeps an SM sub-partition's FP64 unit busy
+    // for ~64 cycles on this part, so no single warp may carry a long row serially: rows longer
+    // than kLongRow blocks take a whole warp (rows spread over the warps), the others four lanes
+    // each, eight rows per warp, summed with two shuffle rounds.
+    constexpr int kLongRow = 16;
+    for (int i = warp; i < nc; i += nwarp) {
+        const int e0 = cptr[i], e1 = cptr[i + 1];
+        if (e1 - e0 <= kLongRow) continue;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        for (int e = e0 + lane; e < e1; e += 32) {
+            const double* v = cval + 9LL * e;
+            const int c = ccol[e];
+            double x0, x1, x2;
+            if (c >= 0) {
+                x0 = yf[3 * c];
+                x1 = yf[3 * c + 1];
+                x2 = yf[3 * c + 2];
+            } else {
+                x0 = yc[3 * ~c];
+                x1 = yc[3 * ~c + 1];
+                x2 = yc[3 * ~c + 2];
+            }
+            a0 = fma(v[0], x0, fma(v[1], x1, fma(v[2], x2, a0)));
+            a1 = fma(v[3], x0, fma(v[4], x1, fma(v[5], x2, a1)));
+            a2 = fma(v[6], x0, fma(v[7], x1, fma(v[8], x2, a2)));
+        }
+        warp_sum3(a0, a1, a2);
+        if (lane == 0) {
+            const int c = c0 + i;
+            const double b0 = yc[3 * c] - a0, b1 = yc[3 * c + 1] - a1, b2 = yc[3 * c + 2] - a2;
+            if (lower) {
+                yc[3 * c] = b0;
+                yc[3 * c + 1] = b1;
+                yc[3 * c + 2] = b2;
+            } else {
+                const double* d = cdi + 9LL * i;
+                yc[3 * c] = d[0] * b0 + d[1] * b1 + d[2] * b2;
+                yc[3 * c + 1] = d[3] * b0 + d[4] * b1 + d[5] * b2;
+                yc[3 * c + 2] = d[6] * b0 + d[7] * b1 + d[8] * b2;
+            }
+        }
+    }
     const int q = lane >> 2, ql = lane & 3;
     for (int g = warp; g * 8 < nc; g += nwarp) {
         const int i = g * 8 + q;
-        const bool active = i < nc;
+        const bool active = i < nc && cptr[i + 1] - cptr[i] <= kLongRow;
         double a0 = 0.0, a1 = 0.0, a2 = 0.0;
         if (active)
             for (int e = cptr[i] + ql; e < cptr[i + 1]; e += 4) {
