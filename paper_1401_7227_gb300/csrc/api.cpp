@@ -85,6 +85,7 @@ struct asm_ctx {
     DBuf d_stream, d_pk_off_f, d_pk_src_f, d_pk_off_c, d_pk_src_c;
     DBuf d_lv, d_rlists, d_y, d_corr_cells, d_corr, d_dev_err;
     int apply_smem = 0;  // dynamic shared memory of the apply (0: local vectors in d_y)
+    int apply_slots = 3; // factor-stream ring slots of the apply
     DBuf d_factdesc, d_subdesc_single;
     DBuf d_err;
     std::vector<FactDesc> fact_desc;
@@ -340,7 +341,20 @@ void upload_symbolic(asm_ctx* h) {
     // local vectors in shared memory when they fit next to the kernel's static needs
     int dev_smem = 0;
     ck(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-    if ((size_t)h->apply_smem + apply_ring_bytes() > (size_t)dev_smem - 1024) h->apply_smem = 0;
+    // ring slots: as many as keep two CTAs per SM (shared memory per SM minus 1 KB per CTA),
+    // else 4 with one CTA per SM; local vectors in device memory when they cannot fit at all
+    int sm_smem = 0;
+    ck(cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device));
+    h->apply_slots = 4;
+    for (int sl = 4; sl >= 2; sl--)
+        if (2 * ((size_t)h->apply_smem + apply_ring_bytes(sl) + 1024) <= (size_t)sm_smem) {
+            h->apply_slots = sl;
+            break;
+        }
+    if ((size_t)h->apply_smem + apply_ring_bytes(h->apply_slots) > (size_t)dev_smem - 1024) {
+        h->apply_smem = 0;
+        h->apply_slots = 3;
+    }
     h->d_subdesc_single.upload(h->sub_desc, st);
     h->d_err.alloc(sizeof(FactErr));
     sync(h);
@@ -434,7 +448,7 @@ namespace {
 struct Batch {
     std::vector<asm_ctx*> hs;
     DBuf d_tab, d_vec, d_row, d_box, d_sub, d_gather;
-    int nvec = 0, nrow = 0, nbox = 0, nsub = 0, prec = 0, smem = 0;
+    int nvec = 0, nrow = 0, nbox = 0, nsub = 0, prec = 0, smem = 0, slots = 3;
     int coop_grid = 0;  // > 0: single system, orthogonalisation in one cooperative launch
     std::vector<int> host_ctl;
     int* pinned = nullptr;
@@ -496,7 +510,7 @@ void launch_step(Batch& B, int kmax, cudaStream_t st, StepEvents* ev) {
     launch_prep(tab, vi, B.nvec, st);
     if (ev) ck(cudaEventRecord(ev->e[1], st));
     launch_boxsum(tab, B.d_box.as<BoxItem>(), B.nbox, st);
-    launch_apply(tab, B.d_sub.as<SubDesc>(), B.nsub, B.prec, B.smem, st);
+    launch_apply(tab, B.d_sub.as<SubDesc>(), B.nsub, B.prec, B.smem, B.slots, st);
     if (ev) ck(cudaEventRecord(ev->e[2], st));
     launch_post(tab, vi, B.nvec, st);
     if (ev) ck(cudaEventRecord(ev->e[3], st));
@@ -541,6 +555,8 @@ int run_gmres(std::vector<asm_ctx*>& hs, const double* const* b, double* const* 
         all_smem = all_smem && h->apply_smem > 0 && !h->no_smem;
     }
     if (!all_smem) B.smem = 0;
+    B.slots = 4;
+    for (asm_ctx* h : hs) B.slots = std::min(B.slots, h->apply_slots);
     for (size_t k = 0; k < hs.size(); k++) {
         asm_ctx* h = hs[k];
         ensure_workspace(h);
@@ -860,7 +876,7 @@ int asm_apply_precond(asm_handle h, const double* r, double* z, int on_device) {
         set_ctl(h, VU, VZ, -1, -1, -1);
         launch_boxsum(h->d_tab1.as<SysTab>(), h->d_box1.as<BoxItem>(), (int)h->box_items.size(), h->stream);
         launch_apply(h->d_tab1.as<SysTab>(), h->d_subdesc_single.as<SubDesc>(), (int)h->sub_desc.size(), h->prec,
-                     h->no_smem ? 0 : h->apply_smem, h->stream);
+                     h->no_smem ? 0 : h->apply_smem, h->apply_slots, h->stream);
         ck(cudaGetLastError());
         h->prof.kernel_launches += 2;
         copy_out(h, z, out, bytes, on_device);

@@ -15,7 +15,7 @@ namespace asm2 {
 // ---------------------------------------------------------------------------------------------
 constexpr int VEC_CHUNK = 4096;   // elements per vector work item (256 threads x 16)
 constexpr int kStreamChunk = 8192;   // bytes of one factor-stream chunk / shared-memory ring slot
-constexpr int kStreamSlots = 3;      // ring slots of the apply (chunks in flight per CTA)
+constexpr int kStreamSlots = 3;      // default ring slots of the apply (chunks in flight per CTA)
 constexpr int VEC_THREADS = 256;
 enum VecSlot { VX = 0, VB = 1, VR = 2, VW = 3, VZ = 4, VU = 5, VV0 = 6 };  // V_k = VV0 + k; Z_k after V
 
@@ -180,10 +180,10 @@ void launch_ell_fill(const double* bsr_vals, const int* ell_loc, long long nnzb,
 void launch_boxsum(const SysTab* st_tab, const BoxItem* items, int nitems, cudaStream_t st);
 // ysmem: shared memory for the local vectors (0 = they stay in the global scratch SubDesc.y);
 // the ring of factor-stream slots is added on top
-void launch_apply(const SysTab* st_tab, const SubDesc* subs, int nsub, int prec, int ysmem, cudaStream_t st);
+void launch_apply(const SysTab* st_tab, const SubDesc* subs, int nsub, int prec, int ysmem, int slots, cudaStream_t st);
 // shared memory the local vectors of a subdomain need (nf fine rows, nc lump rows), and the ring
 size_t apply_smem_bytes(int nf, int nc, int prec);
-size_t apply_ring_bytes();
+size_t apply_ring_bytes(int slots);
 void launch_spmv(const SysTab* st_tab, const RowItem* items, int nitems, cudaStream_t st);
 
 void launch_init(const SysTab* tab, const VecItem* items, int nitems, cudaStream_t st);

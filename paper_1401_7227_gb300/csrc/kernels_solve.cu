@@ -145,13 +145,13 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
     return false;
 }
 
-constexpr int kRingBytes = kStreamSlots * kStreamChunk;
+constexpr int kMaxSlots = 4;  // ring slots of the apply: a launch argument, 2..kMaxSlots
 constexpr int kRingHeader = 64;  // mbarriers
 
 // One chunk of the forward (lower = true) or backward sweep, read from shared memory.
 template <typename TF>
 __device__ __forceinline__ void sweep_chunk(const unsigned char* base, bool lower, typename Compute<TF>::T* yf,
-                                            double* yc) {
+                                            double* yc, typename Compute<TF>::T* ycf) {
     using TC = typename Compute<TF>::T;
     constexpr int FB = FineBlock<TF>::bytes;
     const int* hdr = reinterpret_cast<const int*>(base);
@@ -173,27 +173,83 @@ __device__ __forceinline__ void sweep_chunk(const unsigned char* base, bool lowe
     p += align16(72 * (size_t)ec);
     const double* cdi = reinterpret_cast<const double*>(p);
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
+    if constexpr (sizeof(TC) == 8) {
+        // FP64 fine rows: three lanes per row (one per output component), ten rows per warp, so that
+        // each FP64 instruction carries three times the work of a thread-per-row loop
+        const int r = lane / 3, k = lane - 3 * (lane / 3);
+        for (int base = warp * 10; base < nf; base += nwarp * 10) {
+            const int t = base + r;
+            const bool on = lane < 30 && t < nf;
+            double acc = 0.0;
+            if (on) {
+                const int f = f0 + t;
+                acc = yf[3 * f + k];
+                for (int e = fptr[t]; e < fptr[t + 1]; e++) {
+                    const double* v = reinterpret_cast<const double*>(fval + (size_t)FB * e) + 3 * k;
+                    const int c = fcol[e];
+                    double x0, x1, x2;
+                    if (c >= 0) {
+                        x0 = yf[3 * c];
+                        x1 = yf[3 * c + 1];
+                        x2 = yf[3 * c + 2];
+                    } else {
+                        x0 = yc[3 * ~c];
+                        x1 = yc[3 * ~c + 1];
+                        x2 = yc[3 * ~c + 2];
+                    }
+                    acc -= fma(v[0], x0, fma(v[1], x1, v[2] * x2));
+                }
+            }
+            if (lower) {
+                if (on) yf[3 * (f0 + t) + k] = acc;
+            } else {
+                const int l0 = 3 * r;
+                const double b0 = __shfl_sync(0xffffffffu, acc, l0 < 32 ? l0 : 0);
+                const double b1 = __shfl_sync(0xffffffffu, acc, l0 + 1 < 32 ? l0 + 1 : 0);
+                const double b2 = __shfl_sync(0xffffffffu, acc, l0 + 2 < 32 ? l0 + 2 : 0);
+                if (on) {
+                    const double* d = reinterpret_cast<const double*>(fdi + (size_t)FB * t) + 3 * k;
+                    yf[3 * (f0 + t) + k] = fma(d[0], b0, fma(d[1], b1, d[2] * b2));
+                }
+            }
+        }
+    } else {
+    // fine rows: one thread each; the blocks and x of up to kUnroll entries are loaded before any
+    // arithmetic so that their shared-memory latencies overlap
+    constexpr int kUnroll = 6;
     for (int t = tid; t < nf; t += nt) {
         const int f = f0 + t;
         TC a0 = yf[3 * f], a1 = yf[3 * f + 1], a2 = yf[3 * f + 2];
         const int e0 = fptr[t], e1 = fptr[t + 1];
-        for (int e = e0; e < e1; e++) {
-            TC v[9];
-            load_fine<TF>(fval + (size_t)FB * e, v);
-            const int c = fcol[e];
-            TC x0, x1, x2;
-            if (c >= 0) {
-                x0 = yf[3 * c];
-                x1 = yf[3 * c + 1];
-                x2 = yf[3 * c + 2];
-            } else {
-                x0 = (TC)yc[3 * ~c];
-                x1 = (TC)yc[3 * ~c + 1];
-                x2 = (TC)yc[3 * ~c + 2];
+        for (int eb = e0; eb < e1; eb += kUnroll) {
+            TC xs[kUnroll][3];
+            int cs[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) cs[u] = eb + u < e1 ? fcol[eb + u] : f;
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                const int c = cs[u];
+                if (c >= 0) {
+                    xs[u][0] = yf[3 * c];
+                    xs[u][1] = yf[3 * c + 1];
+                    xs[u][2] = yf[3 * c + 2];
+                } else {
+                    const TC* src = ycf != nullptr ? ycf : reinterpret_cast<const TC*>(yc);
+                    xs[u][0] = src[3 * ~c];
+                    xs[u][1] = src[3 * ~c + 1];
+                    xs[u][2] = src[3 * ~c + 2];
+                }
             }
-            a0 -= v[0] * x0 + v[1] * x1 + v[2] * x2;
-            a1 -= v[3] * x0 + v[4] * x1 + v[5] * x2;
-            a2 -= v[6] * x0 + v[7] * x1 + v[8] * x2;
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                if (eb + u < e1) {
+                    TC v[9];
+                    load_fine<TF>(fval + (size_t)FB * (eb + u), v);
+                    a0 -= v[0] * xs[u][0] + v[1] * xs[u][1] + v[2] * xs[u][2];
+                    a1 -= v[3] * xs[u][0] + v[4] * xs[u][1] + v[5] * xs[u][2];
+                    a2 -= v[6] * xs[u][0] + v[7] * xs[u][1] + v[8] * xs[u][2];
+                }
+            }
         }
         if (lower) {
             yf[3 * f] = a0;
@@ -207,89 +263,96 @@ __device__ __forceinline__ void sweep_chunk(const unsigned char* base, bool lowe
             yf[3 * f + 2] = d[6] * a0 + d[7] * a1 + d[8] * a2;
         }
     }
+    }
     // Lump rows are FP64, and an FP64 warp instruction keeps an SM sub-partition's FP64 unit busy
-    // for ~64 cycles on this part, so no single warp may carry a long row serially: rows longer
-    // than kLongRow blocks take a whole warp (rows spread over the warps), the others four lanes
-    // each, eight rows per warp, summed with two shuffle rounds.
+    // for ~64 cycles whatever the number of active lanes, so lump work is packed into as few FP64
+    // instructions as the latency allows:
+    //  - short rows (<= kLongRow blocks): three lanes per row (one per output component, 3 FMAs per
+    //    block), ten rows per warp;
+    //  - long rows: one warp each, lane = 8 * k + s computing component k over the entries s, s+8,
+    //    ..., combined by three shuffle adds.
+    // Rows go to the warps from the last one (the first warps carry the fine rows of the chunk).
     constexpr int kLongRow = 16;
-    for (int i = warp; i < nc; i += nwarp) {
-        const int e0 = cptr[i], e1 = cptr[i + 1];
-        if (e1 - e0 <= kLongRow) continue;
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-        for (int e = e0 + lane; e < e1; e += 32) {
-            const double* v = cval + 9LL * e;
-            const int c = ccol[e];
-            double x0, x1, x2;
-            if (c >= 0) {
-                x0 = yf[3 * c];
-                x1 = yf[3 * c + 1];
-                x2 = yf[3 * c + 2];
-            } else {
-                x0 = yc[3 * ~c];
-                x1 = yc[3 * ~c + 1];
-                x2 = yc[3 * ~c + 2];
-            }
-            a0 = fma(v[0], x0, fma(v[1], x1, fma(v[2], x2, a0)));
-            a1 = fma(v[3], x0, fma(v[4], x1, fma(v[5], x2, a1)));
-            a2 = fma(v[6], x0, fma(v[7], x1, fma(v[8], x2, a2)));
-        }
-        warp_sum3(a0, a1, a2);
-        if (lane == 0) {
+    {
+        const int k = lane >> 3, sl = lane & 7;
+        const bool lane_on = lane < 24;
+        for (int i = nwarp - 1 - warp; i < nc; i += nwarp) {
+            if (cptr[i + 1] - cptr[i] <= kLongRow) continue;
+            double acc = 0.0;
+            if (lane_on)
+                for (int e = cptr[i] + sl; e < cptr[i + 1]; e += 8) {
+                    const double* v = cval + 9LL * e + 3 * k;
+                    const int c = ccol[e];
+                    double x0, x1, x2;
+                    if (c >= 0) {
+                        x0 = yf[3 * c];
+                        x1 = yf[3 * c + 1];
+                        x2 = yf[3 * c + 2];
+                    } else {
+                        x0 = yc[3 * ~c];
+                        x1 = yc[3 * ~c + 1];
+                        x2 = yc[3 * ~c + 2];
+                    }
+                    acc = fma(v[0], x0, fma(v[1], x1, fma(v[2], x2, acc)));
+                }
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
             const int c = c0 + i;
-            const double b0 = yc[3 * c] - a0, b1 = yc[3 * c + 1] - a1, b2 = yc[3 * c + 2] - a2;
+            double b = 0.0;
+            if (lane_on && sl == 0) b = yc[3 * c + k] - acc;
             if (lower) {
-                yc[3 * c] = b0;
-                yc[3 * c + 1] = b1;
-                yc[3 * c + 2] = b2;
+                if (lane_on && sl == 0) yc[3 * c + k] = b;
             } else {
-                const double* d = cdi + 9LL * i;
-                yc[3 * c] = d[0] * b0 + d[1] * b1 + d[2] * b2;
-                yc[3 * c + 1] = d[3] * b0 + d[4] * b1 + d[5] * b2;
-                yc[3 * c + 2] = d[6] * b0 + d[7] * b1 + d[8] * b2;
+                const double b0 = __shfl_sync(0xffffffffu, b, 0);
+                const double b1 = __shfl_sync(0xffffffffu, b, 8);
+                const double b2 = __shfl_sync(0xffffffffu, b, 16);
+                if (lane_on && sl == 0) {
+                    const double* d = cdi + 9LL * i + 3 * k;
+                    const double t = fma(d[0], b0, fma(d[1], b1, d[2] * b2));
+                    yc[3 * c + k] = t;
+                    if (ycf != nullptr) ycf[3 * c + k] = (TC)t;
+                }
             }
         }
     }
-    const int q = lane >> 2, ql = lane & 3;
-    for (int g = warp; g * 8 < nc; g += nwarp) {
-        const int i = g * 8 + q;
-        const bool active = i < nc && cptr[i + 1] - cptr[i] <= kLongRow;
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-        if (active)
-            for (int e = cptr[i] + ql; e < cptr[i + 1]; e += 4) {
-                const double* v = cval + 9LL * e;
-                const int c = ccol[e];
-                double x0, x1, x2;
-                if (c >= 0) {
-                    x0 = yf[3 * c];
-                    x1 = yf[3 * c + 1];
-                    x2 = yf[3 * c + 2];
-                } else {
-                    x0 = yc[3 * ~c];
-                    x1 = yc[3 * ~c + 1];
-                    x2 = yc[3 * ~c + 2];
+    {
+        const int r = lane / 3, k = lane - 3 * (lane / 3);
+        for (int base = (nwarp - 1 - warp) * 10; base < nc; base += nwarp * 10) {
+            const int i = base + r;
+            const bool on = lane < 30 && i < nc && cptr[i + 1] - cptr[i] <= kLongRow;
+            if (!__any_sync(0xffffffffu, on)) continue;
+            double acc = 0.0;
+            if (on)
+                for (int e = cptr[i]; e < cptr[i + 1]; e++) {
+                    const double* v = cval + 9LL * e + 3 * k;
+                    const int c = ccol[e];
+                    double x0, x1, x2;
+                    if (c >= 0) {
+                        x0 = yf[3 * c];
+                        x1 = yf[3 * c + 1];
+                        x2 = yf[3 * c + 2];
+                    } else {
+                        x0 = yc[3 * ~c];
+                        x1 = yc[3 * ~c + 1];
+                        x2 = yc[3 * ~c + 2];
+                    }
+                    acc = fma(v[0], x0, fma(v[1], x1, fma(v[2], x2, acc)));
                 }
-                a0 = fma(v[0], x0, fma(v[1], x1, fma(v[2], x2, a0)));
-                a1 = fma(v[3], x0, fma(v[4], x1, fma(v[5], x2, a1)));
-                a2 = fma(v[6], x0, fma(v[7], x1, fma(v[8], x2, a2)));
-            }
-#pragma unroll
-        for (int o = 1; o < 4; o <<= 1) {
-            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-        }
-        if (active && ql == 0) {
             const int c = c0 + i;
-            const double b0 = yc[3 * c] - a0, b1 = yc[3 * c + 1] - a1, b2 = yc[3 * c + 2] - a2;
+            const double b = on ? yc[3 * c + k] - acc : 0.0;
             if (lower) {
-                yc[3 * c] = b0;
-                yc[3 * c + 1] = b1;
-                yc[3 * c + 2] = b2;
+                if (on) yc[3 * c + k] = b;
             } else {
-                const double* d = cdi + 9LL * i;
-                yc[3 * c] = d[0] * b0 + d[1] * b1 + d[2] * b2;
-                yc[3 * c + 1] = d[3] * b0 + d[4] * b1 + d[5] * b2;
-                yc[3 * c + 2] = d[6] * b0 + d[7] * b1 + d[8] * b2;
+                const int l0 = 3 * r;
+                const double b0 = __shfl_sync(0xffffffffu, b, l0 < 32 ? l0 : 0);
+                const double b1 = __shfl_sync(0xffffffffu, b, l0 + 1 < 32 ? l0 + 1 : 0);
+                const double b2 = __shfl_sync(0xffffffffu, b, l0 + 2 < 32 ? l0 + 2 : 0);
+                if (on) {
+                    const double* d = cdi + 9LL * i + 3 * k;
+                    const double t = fma(d[0], b0, fma(d[1], b1, d[2] * b2));
+                    yc[3 * c + k] = t;
+                    if (ycf != nullptr) ycf[3 * c + k] = (TC)t;
+                }
             }
         }
     }
@@ -302,7 +365,8 @@ __device__ __forceinline__ void sweep_chunk(const unsigned char* base, bool lowe
 // the wavefront levels).  Fine rows and lump rows live in separate local vectors (fine rows at the
 // factor precision, lumps in FP64), in shared memory when they fit.
 template <typename TF, bool SMEM_Y>
-__global__ void __launch_bounds__(256) k_apply(const SysTab* __restrict__ tab, const SubDesc* __restrict__ subs) {
+__global__ void __launch_bounds__(256, 2) k_apply(const SysTab* __restrict__ tab, const SubDesc* __restrict__ subs,
+                                                   int slots) {
     using TC = typename Compute<TF>::T;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const SubDesc sd = subs[blockIdx.x];
@@ -313,19 +377,21 @@ __global__ void __launch_bounds__(256) k_apply(const SysTab* __restrict__ tab, c
     const double* __restrict__ r = st.ws + (long long)in * st.n3p;
     double* __restrict__ z = st.ws + (long long)out * st.n3p;
     unsigned char* ring = smem_raw;
-    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + kRingBytes);
-    double* yc = SMEM_Y ? reinterpret_cast<double*>(smem_raw + kRingBytes + kRingHeader) : sd.y;
+    const int ring_bytes = slots * kStreamChunk;
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + ring_bytes);
+    double* yc = SMEM_Y ? reinterpret_cast<double*>(smem_raw + ring_bytes + kRingHeader) : sd.y;
     TC* yf = reinterpret_cast<TC*>(yc + 3 * sd.nc);
+    TC* ycf = sizeof(TC) == 8 ? nullptr : yf + 3 * sd.nf;  // FP32 mirror of the lump values
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
 
     if (tid == 0) {
-        for (int k = 0; k < kStreamSlots; k++) mbar_init(&bar[k], 1);
+        for (int k = 0; k < slots; k++) mbar_init(&bar[k], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     if (tid == 0)
-        for (int k = 0; k < kStreamSlots && k < sd.n_chunks; k++) {
+        for (int k = 0; k < slots && k < sd.n_chunks; k++) {
             const int2 ch = sd.chunks[k];
             mbar_expect_tx(&bar[k], (unsigned)ch.y);
             bulk_load(ring + (size_t)k * kStreamChunk, sd.stream + ch.x, (unsigned)ch.y, &bar[k]);
@@ -356,6 +422,7 @@ __global__ void __launch_bounds__(256) k_apply(const SysTab* __restrict__ tab, c
                 a2 -= q[2];
             }
         }
+#pragma unroll 8
         for (int i = i0; i < i1; i++) {
             const double* rc = r + 3LL * sd.rsrc[i];
             a0 += rc[0];
@@ -385,21 +452,21 @@ __global__ void __launch_bounds__(256) k_apply(const SysTab* __restrict__ tab, c
     __syncthreads();
 
     for (int ci = 0; ci < sd.n_chunks; ci++) {
-        const int slot = ci % kStreamSlots;
-        const bool ok = mbar_wait(&bar[slot], (unsigned)(ci / kStreamSlots) & 1u);
-        if (ok) sweep_chunk<TF>(ring + (size_t)slot * kStreamChunk, ci < sd.n_fwd, yf, yc);
+        const int slot = ci % slots;
+        const bool ok = mbar_wait(&bar[slot], (unsigned)(ci / slots) & 1u);
+        if (ok) sweep_chunk<TF>(ring + (size_t)slot * kStreamChunk, ci < sd.n_fwd, yf, yc, ycf);
         if (__syncthreads_or(!ok)) {
             // a copy did not land in time: report it, wait (bounded) for the copies still in
             // flight into this CTA's shared memory, and leave
             if (tid == 0) {
                 atomicExch(st.dev_err, 7);
-                const int last = min(sd.n_chunks, ci + kStreamSlots);
-                for (int k = ci; k < last; k++) mbar_wait(&bar[k % kStreamSlots], (unsigned)(k / kStreamSlots) & 1u);
+                const int last = min(sd.n_chunks, ci + slots);
+                for (int k = ci; k < last; k++) mbar_wait(&bar[k % slots], (unsigned)(k / slots) & 1u);
             }
             return;
         }
-        if (tid == 0 && ci + kStreamSlots < sd.n_chunks) {
-            const int2 ch = sd.chunks[ci + kStreamSlots];
+        if (tid == 0 && ci + slots < sd.n_chunks) {
+            const int2 ch = sd.chunks[ci + slots];
             mbar_expect_tx(&bar[slot], (unsigned)ch.y);
             bulk_load(ring + (size_t)slot * kStreamChunk, sd.stream + ch.x, (unsigned)ch.y, &bar[slot]);
         }
@@ -874,39 +941,40 @@ void launch_boxsum(const SysTab* tab, const BoxItem* items, int nitems, cudaStre
 }
 
 size_t apply_smem_bytes(int nf, int nc, int prec) {
-    return 24 * (size_t)nc + (prec == 0 ? 24 : 12) * (size_t)nf;
+    return prec == 0 ? 24 * ((size_t)nc + nf) : 24 * (size_t)nc + 12 * ((size_t)nf + nc);
 }
 
-size_t apply_ring_bytes() { return (size_t)kRingBytes + kRingHeader; }
+size_t apply_ring_bytes(int slots) { return (size_t)slots * kStreamChunk + kRingHeader; }
 
 namespace {
 template <typename TF, bool Y>
-void launch_apply_t(const SysTab* tab, const SubDesc* subs, int nsub, int smem, cudaStream_t st) {
+void launch_apply_t(const SysTab* tab, const SubDesc* subs, int nsub, int smem, int slots, cudaStream_t st) {
     static int configured = -1;
     if (configured < smem) {
         cudaFuncSetAttribute(k_apply<TF, Y>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         configured = smem;
     }
-    k_apply<TF, Y><<<nsub, 256, smem, st>>>(tab, subs);
+    k_apply<TF, Y><<<nsub, 256, smem, st>>>(tab, subs, slots);
 }
 template <typename TF>
-void launch_apply_p(const SysTab* tab, const SubDesc* subs, int nsub, int ysmem, cudaStream_t st) {
-    const int ring = (int)apply_ring_bytes();
+void launch_apply_p(const SysTab* tab, const SubDesc* subs, int nsub, int ysmem, int slots, cudaStream_t st) {
+    const int ring = (int)apply_ring_bytes(slots);
     if (ysmem > 0)
-        launch_apply_t<TF, true>(tab, subs, nsub, ring + ysmem, st);
+        launch_apply_t<TF, true>(tab, subs, nsub, ring + ysmem, slots, st);
     else
-        launch_apply_t<TF, false>(tab, subs, nsub, ring, st);
+        launch_apply_t<TF, false>(tab, subs, nsub, ring, slots, st);
 }
 }  // namespace
 
-void launch_apply(const SysTab* tab, const SubDesc* subs, int nsub, int prec, int ysmem, cudaStream_t st) {
+void launch_apply(const SysTab* tab, const SubDesc* subs, int nsub, int prec, int ysmem, int slots, cudaStream_t st) {
     if (nsub <= 0) return;
+    slots = slots < 2 ? 2 : (slots > kMaxSlots ? kMaxSlots : slots);
     if (prec == 0)
-        launch_apply_p<double>(tab, subs, nsub, ysmem, st);
+        launch_apply_p<double>(tab, subs, nsub, ysmem, slots, st);
     else if (prec == 1)
-        launch_apply_p<float>(tab, subs, nsub, ysmem, st);
+        launch_apply_p<float>(tab, subs, nsub, ysmem, slots, st);
     else
-        launch_apply_p<__half>(tab, subs, nsub, ysmem, st);
+        launch_apply_p<__half>(tab, subs, nsub, ysmem, slots, st);
 }
 
 void launch_spmv(const SysTab* tab, const RowItem* items, int nitems, cudaStream_t st) {
