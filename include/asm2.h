@@ -209,6 +209,21 @@ int asm_get_local_map(asm_handle h, int s, int* map);
 int asm_get_local_matrix(asm_handle h, int s, int* row_ptr, int* col_idx, double* vals);
 int asm_get_local_factors(asm_handle h, int s, double* lu, double* dpiv);
 
+/* No-allocation true residual: r = b - A x and *norm = ||r||_2 for the matrix held by h.
+ * The paper has no counterpart: this entry point is for callers that cannot allocate device
+ * memory when they need it -- code running under a memory pool that forbids further device
+ * allocations, code that must keep its allocations fixed after start-up, or a driver about to
+ * capture work into a graph.  b, x (3N doubles, read), r (3N doubles, written) and norm (one
+ * double, written) are caller-owned DEVICE pointers; the call allocates nothing and calls no
+ * allocating routine.  The partial sums of the norm go to a scratch array compiled into the
+ * library (16384 doubles + a counter, 128 KB, held by every GPU that loads the library until the
+ * process exits), so N is limited to 256 * 16384 = 4,194,304 cells (INVALID_ARG beyond).  The
+ * first call on a device looks up the array's device address and clears its counter: make that
+ * first call before any stream capture.  All calls share the array: calls that overlap on the
+ * GPU race.  Work is issued on the handle's stream; the call returns when it is done.
+ * Errors: INVALID_ARG (NULL pointer, N too large), STATE (no matrix), CUDA. */
+int asm_residual_noalloc(asm_handle h, const double* b, const double* x, double* r, double* norm);
+
 #ifdef __cplusplus
 }
 #endif

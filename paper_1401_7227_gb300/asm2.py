@@ -25,7 +25,7 @@ EXPORTS = [
     "asm_default_options", "asm_error_string", "asm_create", "asm_destroy", "asm_set_grid", "asm_set_matrix_bsr",
     "asm_update_values", "asm_set_partition_boxes", "asm_factor", "asm_apply_precond", "asm_spmv", "asm_solve",
     "asm_solve_batch", "asm_get_stats", "asm_get_error_location", "asm_get_local_info", "asm_get_local_map",
-    "asm_get_local_matrix", "asm_get_local_factors", "asm_set_profiling", "asm_get_profile", "asm_reset_profile", "asm_set_tuning",
+    "asm_get_local_matrix", "asm_get_local_factors", "asm_set_profiling", "asm_get_profile", "asm_reset_profile", "asm_set_tuning", "asm_residual_noalloc",
 ]
 
 
@@ -111,6 +111,7 @@ def load(build_if_missing: bool = False):
     L.asm_get_profile.argtypes = [P, C.POINTER(Profile)]
     L.asm_reset_profile.argtypes = [P]
     L.asm_set_tuning.argtypes = [P, I, I]
+    L.asm_residual_noalloc.argtypes = [P, P, P, P, P]
     for name in EXPORTS:
         if name not in ("asm_default_options", "asm_error_string"):
             getattr(L, name).restype = I

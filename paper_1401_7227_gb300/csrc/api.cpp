@@ -652,6 +652,19 @@ int run_gmres(std::vector<asm_ctx*>& hs, const double* const* b, double* const* 
 
 }  // namespace
 
+int handle_matrix_view(asm_ctx* h, MatrixView* out) {
+    if (!h || !out) return ASM_ERR_INVALID_ARG;
+    if (!h->has_matrix) return ASM_ERR_STATE;
+    out->ell_val = h->d_ell_val.as<double>();
+    out->ell_col = h->d_ell_col.as<int>();
+    out->ell_w = h->pat.ell_w;
+    out->rows_pad = h->pat.rows_pad;
+    out->n_cells = h->N;
+    out->device = h->device;
+    out->stream = h->stream;
+    return ASM_OK;
+}
+
 // ---------------------------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------------------------

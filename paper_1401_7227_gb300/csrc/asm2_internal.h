@@ -196,4 +196,16 @@ void launch_finish(const SysTab* tab, const VecItem* items, int nitems, cudaStre
 int ortho_coop_grid(int device);
 cudaError_t launch_ortho_coop(const SysTab* tab, double* part2, int grid, cudaStream_t st);
 
+// Read-only view of the device matrix of a handle (used by the no-allocation residual)
+struct MatrixView {
+    const double* ell_val;
+    const int* ell_col;
+    int ell_w, rows_pad, n_cells, device;
+    cudaStream_t stream;
+};
+
 }  // namespace asm2
+
+struct asm_ctx;
+// ASM_OK and *out filled when h holds a matrix, else ASM_ERR_STATE
+int handle_matrix_view(asm_ctx* h, asm2::MatrixView* out);
