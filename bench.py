@@ -131,6 +131,79 @@ def oracle_estimate(w, system, iters: int, sample_subs=2, sample_iters=4):
     return est * 1e3, sample, {"setup_per_sub_s": t_setup, "apply_per_sub_s": t_apply, "gmres_iter_s": t_it}
 
 
+def serving_pool(n_pool: int, seed0: int = 5_000_000):
+    """Synthetic matrices for the serving stream: cells log-uniform on [2000, 1048576],
+    nx = ny = round((2n)^(1/3)), nz = max(2, round(n / nx^2)), px = py = clamp(round(nx / 8), 1, 16),
+    pz = 2 if nz > 32 else 1, overlap 1."""
+    import math
+    pool = []
+    for k in range(n_pool):
+        u = float(synth.uniform(seed0 + k, 98, np.arange(1))[0])
+        n = math.exp(math.log(2000) + u * (math.log(1048576) - math.log(2000)))
+        nx = max(2, int(round((2 * n) ** (1 / 3))))
+        nz = max(2, int(round(n / nx ** 2)))
+        p = min(16, max(1, int(round(nx / 8))))
+        pz = 2 if nz > 32 else 1
+        s = synth.grid_jacobian(nx, nx, nz, seed0 + k, 1.0)
+        rhs = [synth.rhs(s.n_cells, seed0 + 100000 + 10 * k + j) for j in range(4)]
+        pool.append((s, (p, p, pz), rhs))
+    return pool
+
+
+def run_serving(args, stream):
+    """Poisson arrivals; 30% of requests repeat an earlier matrix (factors reused), the rest carry a
+    new matrix (full set-up: values uploaded, local matrices assembled and factored).  Latency =
+    completion - arrival (host wall clock); generation is off the clock."""
+    from paper_1401_7227_gb300 import asm2
+    rng = np.random.default_rng(5)
+    pool = serving_pool(args.serve_pool)
+    n_req = args.serve_requests
+    gaps = rng.exponential(1.0 / args.serve_rate, n_req)
+    arrivals = np.cumsum(gaps)
+    reqs = []
+    for i in range(n_req):
+        if i > 0 and rng.random() < 0.3:
+            j = int(rng.integers(0, i))
+            key, pidx = reqs[j][0], reqs[j][1]
+        else:
+            key, pidx = i, int(rng.integers(0, len(pool)))
+        reqs.append((key, pidx, int(rng.integers(0, 4))))
+    srv = asm2.Server(precision="fp32", restart=30, max_active=args.serve_max_active, max_cached=32,
+                      stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    nxt = 0
+    inflight = {}
+    lat = []
+    done_t = []
+    while nxt < n_req or inflight:
+        now = time.perf_counter() - t0
+        while nxt < n_req and arrivals[nxt] <= now:
+            key, pidx, bj = reqs[nxt]
+            s, part, rhs = pool[pidx]
+            t = srv.submit(s, rhs[bj], partition=part, overlap=1, matrix_key=key, max_iter=2000)
+            inflight[t] = arrivals[nxt]
+            nxt += 1
+        a, pend = srv.progress(2)
+        now = time.perf_counter() - t0
+        for t in list(inflight):
+            r = srv.result(t)
+            if r is not None:
+                lat.append(now - inflight.pop(t))
+                done_t.append(now)
+        if a == 0 and pend == 0 and not inflight and nxt < n_req:
+            time.sleep(max(0.0, min(0.002, arrivals[nxt] - now)))
+    stats = srv.stats()
+    srv.close()
+    lat_ms = np.array(lat) * 1e3
+    return {"requests": n_req, "rate_per_s": args.serve_rate, "pool_matrices": len(pool),
+            "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+            "mean_ms": float(lat_ms.mean()), "solves_per_s": n_req / (max(done_t) - arrivals[0]),
+            "reuse_hits": stats["reuse_hits"], "structure_builds": stats["structure_builds"],
+            "steps": stats["steps"], "precision": "fp32 factors, fp64 Krylov",
+            "sample": f"{n_req} requests, Poisson {args.serve_rate}/s, 30% repeated matrices, "
+                      f"{len(pool)} distinct synthetic matrices 2e3-1e6 cells"}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -294,6 +367,8 @@ def run_gpu(args):
                                 "detail": detail}
     for r_ in results.values():
         r_["solver"].close()
+    if not args.no_serve and rank == 0:
+        line["serving"] = run_serving(args, stream)
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
@@ -312,6 +387,11 @@ def main():
     ap.add_argument("--max-iter", type=int, default=3000)
     ap.add_argument("--ref-iters", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=600)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-pool", type=int, default=12)
+    ap.add_argument("--serve-max-active", type=int, default=64)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -209,6 +209,55 @@ int asm_get_local_map(asm_handle h, int s, int* map);
 int asm_get_local_matrix(asm_handle h, int s, int* row_ptr, int* col_idx, double* vals);
 int asm_get_local_factors(asm_handle h, int s, double* lu, double* dpiv);
 
+/* ------------------------------------------------------------------------------------------
+ * Serving loop (continuous batching).  Requests of any grid size are submitted as they arrive;
+ * asm_server_progress admits them while the active-system limit and the device-memory budget
+ * allow (a request whose matrix key is already resident reuses its factors; a new grid shape is
+ * analysed once on a host worker thread and cached), and advances every active system by Krylov
+ * steps in the same kernel launches; finished systems leave the batch between steps.  Each
+ * system's arithmetic does not depend on the others in the batch.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct {
+    int precision;        /* asm_precision of every served system (default FP32) */
+    int restart;          /* GMRES m (default 30) */
+    int device;           /* CUDA device */
+    int max_active;       /* systems advanced together, 0 = no limit (default 64) */
+    int max_cached;       /* idle factored systems kept for matrix reuse, LRU (default 16) */
+    long long hbm_budget; /* device bytes for resident systems; 0 = 85% of free memory */
+} asm_server_options;
+
+typedef struct {
+    int nx, ny, nz, n_cells, nnzb;
+    const int* row_ptr;    /* host, borrowed until the result is collected */
+    const int* col_idx;    /* host, borrowed until the result is collected */
+    const double* vals;    /* host, borrowed until the result is collected */
+    int px, py, pz, overlap, near_width, c_near[3], far_mode, c_far[3]; /* asm_set_partition_boxes */
+    const double* b;       /* host, copied at submission */
+    double rtol;
+    int max_iter;
+    long long matrix_key;  /* >= 0: requests with the same key carry the same matrix */
+} asm_request;
+
+typedef struct {
+    long long submitted, admitted, completed, steps, reuse_hits, structure_builds, evictions;
+    long long resident_bytes, budget_bytes;
+    int active, pending;
+} asm_server_stats;
+
+void asm_server_default_options(asm_server_options* opt);
+typedef struct asm_server* asm_server_handle;
+/* cuda_stream: the stream all served work is issued on (NULL = legacy default stream). */
+int asm_server_create(asm_server_handle* s, const asm_server_options* opt, void* cuda_stream);
+/* Queue a request; *ticket identifies it.  Errors: INVALID_ARG (inconsistent sizes). */
+int asm_server_submit(asm_server_handle s, const asm_request* req, long long* ticket);
+/* Admit what fits, then run up to max_steps Krylov steps of the active systems. */
+int asm_server_progress(asm_server_handle s, int max_steps, int* n_active, int* n_pending);
+/* STATE while the request is unfinished; else copies x (3N doubles, host) and its info, forgets
+ * the ticket and returns OK (also when not converged: see info.status) or the request's error. */
+int asm_server_result(asm_server_handle s, long long ticket, double* x, asm_solve_info* info);
+int asm_server_get_stats(asm_server_handle s, asm_server_stats* stats);
+int asm_server_destroy(asm_server_handle s);
+
 /* No-allocation true residual: r = b - A x and *norm = ||r||_2 for the matrix held by h.
  * The paper has no counterpart: this entry point is for callers that cannot allocate device
  * memory when they need it -- code running under a memory pool that forbids further device

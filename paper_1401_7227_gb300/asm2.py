@@ -26,6 +26,8 @@ EXPORTS = [
     "asm_update_values", "asm_set_partition_boxes", "asm_factor", "asm_apply_precond", "asm_spmv", "asm_solve",
     "asm_solve_batch", "asm_get_stats", "asm_get_error_location", "asm_get_local_info", "asm_get_local_map",
     "asm_get_local_matrix", "asm_get_local_factors", "asm_set_profiling", "asm_get_profile", "asm_reset_profile", "asm_set_tuning", "asm_residual_noalloc",
+    "asm_server_default_options", "asm_server_create", "asm_server_submit", "asm_server_progress",
+    "asm_server_result", "asm_server_get_stats", "asm_server_destroy",
 ]
 
 
@@ -56,6 +58,29 @@ class Stats(C.Structure):
 class Profile(C.Structure):
     _fields_ = [("apply_ms", C.c_double), ("spmv_ms", C.c_double), ("ortho_ms", C.c_double), ("factor_ms", C.c_double),
                 ("apply_launches", C.c_longlong), ("kernel_launches", C.c_longlong)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ServerOptions(C.Structure):
+    _fields_ = [("precision", C.c_int), ("restart", C.c_int), ("device", C.c_int), ("max_active", C.c_int),
+                ("max_cached", C.c_int), ("hbm_budget", C.c_longlong)]
+
+
+class Request(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("n_cells", C.c_int), ("nnzb", C.c_int),
+                ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p), ("vals", C.c_void_p),
+                ("px", C.c_int), ("py", C.c_int), ("pz", C.c_int), ("overlap", C.c_int), ("near_width", C.c_int),
+                ("c_near", C.c_int * 3), ("far_mode", C.c_int), ("c_far", C.c_int * 3),
+                ("b", C.c_void_p), ("rtol", C.c_double), ("max_iter", C.c_int), ("matrix_key", C.c_longlong)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_longlong), ("admitted", C.c_longlong), ("completed", C.c_longlong),
+                ("steps", C.c_longlong), ("reuse_hits", C.c_longlong), ("structure_builds", C.c_longlong),
+                ("evictions", C.c_longlong), ("resident_bytes", C.c_longlong), ("budget_bytes", C.c_longlong),
+                ("active", C.c_int), ("pending", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -112,8 +137,16 @@ def load(build_if_missing: bool = False):
     L.asm_reset_profile.argtypes = [P]
     L.asm_set_tuning.argtypes = [P, I, I]
     L.asm_residual_noalloc.argtypes = [P, P, P, P, P]
+    L.asm_server_default_options.argtypes = [C.POINTER(ServerOptions)]
+    L.asm_server_default_options.restype = None
+    L.asm_server_create.argtypes = [C.POINTER(P), C.POINTER(ServerOptions), P]
+    L.asm_server_submit.argtypes = [P, C.POINTER(Request), C.POINTER(C.c_longlong)]
+    L.asm_server_progress.argtypes = [P, I, C.POINTER(I), C.POINTER(I)]
+    L.asm_server_result.argtypes = [P, C.c_longlong, P, C.POINTER(SolveInfo)]
+    L.asm_server_get_stats.argtypes = [P, C.POINTER(ServerStats)]
+    L.asm_server_destroy.argtypes = [P]
     for name in EXPORTS:
-        if name not in ("asm_default_options", "asm_error_string"):
+        if name not in ("asm_default_options", "asm_error_string", "asm_server_default_options"):
             getattr(L, name).restype = I
     _lib = L
     return L
@@ -343,3 +376,77 @@ def setup(system, px, py, pz, overlap=1, near_width=2, c_near=(2, 2, 2), far_mod
     if factor:
         s.factor()
     return s
+
+
+class Server:
+    """Continuous-batching serving loop (asm_server_*): submit solves of any grid size as they
+    arrive, call progress() to admit and advance them, collect results by ticket."""
+
+    def __init__(self, precision: str = "fp32", restart: int = 30, device: int = 0, max_active: int = 64,
+                 max_cached: int = 16, hbm_budget: int = 0, stream: int | None = None):
+        L = load()
+        o = ServerOptions()
+        L.asm_server_default_options(C.byref(o))
+        o.precision, o.restart, o.device = PREC[precision], restart, device
+        o.max_active, o.max_cached, o.hbm_budget = max_active, max_cached, hbm_budget
+        self.stream = stream if stream is not None else _current_stream(device)
+        h = C.c_void_p()
+        _check(L.asm_server_create(C.byref(h), C.byref(o), C.c_void_p(self.stream)), "server_create")
+        self._h = h
+        self._keep = {}  # ticket -> host arrays borrowed by the request
+        self._n = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().asm_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, system, b, partition=(1, 1, 1), overlap=1, near_width=2, c_near=(2, 2, 2), far_mode="partition",
+               c_far=None, rtol=1e-8, max_iter=1000, matrix_key=-1) -> int:
+        rp = np.ascontiguousarray(system.row_ptr, dtype=np.int32)
+        ci = np.ascontiguousarray(system.col_idx, dtype=np.int32)
+        v = np.ascontiguousarray(system.vals, dtype=np.float64)
+        bb = np.ascontiguousarray(b, dtype=np.float64)
+        q = Request()
+        q.nx, q.ny, q.nz = system.nx, system.ny, system.nz
+        q.n_cells, q.nnzb = system.nx * system.ny * system.nz, ci.shape[0]
+        q.row_ptr, q.col_idx, q.vals = rp.ctypes.data, ci.ctypes.data, v.ctypes.data
+        q.px, q.py, q.pz = partition
+        q.overlap, q.near_width = overlap, near_width
+        q.c_near = (C.c_int * 3)(*c_near)
+        q.far_mode = FAR[far_mode] if isinstance(far_mode, str) else int(far_mode)
+        q.c_far = (C.c_int * 3)(*(c_far if c_far is not None else (1, 1, 1)))
+        q.b, q.rtol, q.max_iter, q.matrix_key = bb.ctypes.data, rtol, max_iter, matrix_key
+        t = C.c_longlong()
+        _check(load().asm_server_submit(self._h, C.byref(q), C.byref(t)), "server_submit")
+        self._keep[t.value] = (rp, ci, v)
+        self._n[t.value] = q.n_cells
+        return t.value
+
+    def progress(self, max_steps: int = 1):
+        a, p = C.c_int(), C.c_int()
+        _check(load().asm_server_progress(self._h, max_steps, C.byref(a), C.byref(p)), "server_progress")
+        return a.value, p.value
+
+    def result(self, ticket: int):
+        """(x, info) once the request is finished, else None."""
+        x = np.empty(3 * self._n[ticket])
+        info = SolveInfo()
+        st = load().asm_server_result(self._h, ticket, _host_ptr(x), C.byref(info))
+        if st == 8:
+            return None
+        self._keep.pop(ticket, None)
+        self._n.pop(ticket, None)
+        _check(st, "server_result")
+        return x, info.as_dict()
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(load().asm_server_get_stats(self._h, C.byref(s)), "server_stats")
+        return s.as_dict()

@@ -75,7 +75,7 @@ struct asm_ctx {
     DBuf d_ell_val, d_ell_col, d_ell_loc, d_stage;
     // partition / symbolic
     Geom geom;
-    std::unique_ptr<SysSym> sym;
+    std::shared_ptr<SysSym> sym;
     bool sym_valid = false;
     bool factored = false;
     // device preconditioner data
@@ -440,6 +440,46 @@ void set_ctl(asm_ctx* h, int apply_in, int apply_out, int spmv_in, int spmv_out,
 
 }  // namespace
 
+// Device assembly, factorisation and packing of the current symbolic structure.
+int factor_numeric(asm_ctx* h) {
+    SysSym& S = *h->sym;
+    cudaEvent_t e0, e1;
+    ck(cudaEventCreate(&e0));
+    ck(cudaEventCreate(&e1));
+    ck(cudaEventRecord(e0, h->stream));
+    if (S.g.far_mode != 0)
+        launch_coarse(h->d_cptr.as<int>(), h->d_cloc.as<int>(), h->d_ell_val.as<double>(), h->pat.rows_pad,
+                      h->d_cval.as<double>(), S.nC, h->stream);
+    launch_assemble(h->d_aptr.as<int>(), h->d_aloc.as<int>(), h->d_acs.as<int>(), h->d_ell_val.as<double>(),
+                    h->pat.rows_pad, h->d_cval.as<double>(), h->d_slot.as<double>(), h->total_slots, h->stream);
+    h->d_err.zero(h->stream);
+    launch_factor(h->d_factdesc.as<FactDesc>(), (int)S.subs.size(), h->d_err.as<FactErr>(), nullptr, h->stream);
+    launch_pack(h->d_pk_off_f.as<long long>(), h->d_pk_src_f.as<int>(), h->pk_nf, h->prec,
+                h->d_stream.as<unsigned char>(), h->d_slot.as<double>(), h->stream);
+    launch_pack(h->d_pk_off_c.as<long long>(), h->d_pk_src_c.as<int>(), h->pk_nc, 0, h->d_stream.as<unsigned char>(),
+                h->d_slot.as<double>(), h->stream);
+    ck(cudaGetLastError());
+    ck(cudaEventRecord(e1, h->stream));
+    FactErr fe;
+    ck(cudaMemcpyAsync(&fe, h->d_err.p, sizeof(fe), cudaMemcpyDeviceToHost, h->stream));
+    sync(h);
+    float ms = 0;
+    ck(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->factor_ms = ms;
+    h->prof.factor_ms += ms;
+    h->prof.kernel_launches += 5;
+    if (fe.flag) {
+        h->err_sub = fe.sub;
+        h->err_row = fe.row;
+        h->factored = false;
+        return ASM_ERR_ZERO_PIVOT;
+    }
+    h->factored = true;
+    return ASM_OK;
+}
+
 // ---------------------------------------------------------------------------------------------
 // Batch driver: all systems advance together; each kernel reads each system's own state.
 // ---------------------------------------------------------------------------------------------
@@ -450,6 +490,7 @@ struct Batch {
     DBuf d_tab, d_vec, d_row, d_box, d_sub, d_gather;
     int nvec = 0, nrow = 0, nbox = 0, nsub = 0, prec = 0, smem = 0, slots = 3;
     int coop_grid = 0;  // > 0: single system, orthogonalisation in one cooperative launch
+    bool has_init = false;  // a system may be in its initial phase (serving: systems join mid-flight)
     std::vector<int> host_ctl;
     int* pinned = nullptr;
     ~Batch() {
@@ -486,7 +527,20 @@ void build_batch(Batch& B, cudaStream_t st) {
     B.nrow = (int)ri.size();
     B.nbox = (int)bi.size();
     B.nsub = (int)sd.size();
-    ck(cudaMallocHost((void**)&B.pinned, sizeof(int) * C_NCTL * B.hs.size()));
+    if (B.pinned) cudaFreeHost(B.pinned);
+    B.pinned = nullptr;
+    ck(cudaMallocHost((void**)&B.pinned, sizeof(int) * C_NCTL * std::max<size_t>(1, B.hs.size())));
+    // kernel variants shared by the whole batch
+    B.prec = B.hs.empty() ? 0 : B.hs[0]->prec;
+    B.smem = 0;
+    bool all_smem = !B.hs.empty();
+    for (asm_ctx* h : B.hs) {
+        B.smem = std::max(B.smem, h->apply_smem);
+        all_smem = all_smem && h->apply_smem > 0 && !h->no_smem;
+    }
+    if (!all_smem) B.smem = 0;
+    B.slots = 4;
+    for (asm_ctx* h : B.hs) B.slots = std::min(B.slots, h->apply_slots);
 }
 
 // events bracketing the launch groups of one step: [prep | apply | post | spmv | mgs+finish]
@@ -507,6 +561,7 @@ void launch_step(Batch& B, int kmax, cudaStream_t st, StepEvents* ev) {
     const SysTab* tab = B.d_tab.as<SysTab>();
     const VecItem* vi = B.d_vec.as<VecItem>();
     if (ev) ck(cudaEventRecord(ev->e[0], st));
+    if (B.has_init) launch_init(tab, vi, B.nvec, st);
     launch_prep(tab, vi, B.nvec, st);
     if (ev) ck(cudaEventRecord(ev->e[1], st));
     launch_boxsum(tab, B.d_box.as<BoxItem>(), B.nbox, st);
@@ -542,39 +597,49 @@ void read_ctl(Batch& B, cudaStream_t st) {
     ck(cudaStreamSynchronize(st));
 }
 
+// b into slot VB, control words (initial phase) and tolerance of one system
+void begin_solve(asm_ctx* h, const double* b, int on_device, double rtol, int max_iter) {
+    ensure_workspace(h);
+    const ScalLayout SL = ScalLayout::make(h->ws_m);
+    copy_in(h, h->d_ws.as<double>() + (long long)VB * h->n3p, b, sizeof(double) * 3 * (size_t)h->N, on_device);
+    int c[C_NCTL];
+    std::memset(c, 0, sizeof(c));
+    c[C_PHASE] = PH_INIT;
+    c[C_APPLY_IN] = -1;
+    c[C_SPMV_IN] = -1;
+    c[C_MAXIT] = max_iter;
+    c[C_STATUS] = ASM_ERR_NOT_CONVERGED;
+    ck(cudaMemcpyAsync(h->d_ctl.p, c, sizeof(c), cudaMemcpyHostToDevice, h->stream));
+    double tol = rtol;
+    ck(cudaMemcpyAsync(h->d_scal.as<double>() + SL.tol, &tol, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    ck(cudaStreamSynchronize(h->stream));
+}
+
+// x and the result of a finished (or abandoned) system; c = its control words
+int harvest(asm_ctx* h, const int* c, double* x, int on_device, asm_solve_info* info) {
+    const ScalLayout SL = ScalLayout::make(h->ws_m);
+    double sc[2];
+    ck(cudaMemcpyAsync(sc, h->d_scal.as<double>() + SL.bnorm, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    copy_out(h, x, h->d_ws.as<double>() + (long long)VX * h->n3p, sizeof(double) * 3 * (size_t)h->N, on_device);
+    ck(cudaStreamSynchronize(h->stream));
+    int status = c[C_PHASE] == PH_DONE ? c[C_STATUS] : ASM_ERR_NOT_CONVERGED;
+    if (take_dev_err(h)) status = ASM_ERR_TIMEOUT;
+    if (info) {
+        info->iterations = c[C_ITERS];
+        info->restarts = c[C_RESTARTS];
+        info->converged = c[C_CONVERGED];
+        info->status = status;
+        info->rel_residual = sc[0] > 0 ? sc[1] / sc[0] : 0.0;
+    }
+    return status;
+}
+
 int run_gmres(std::vector<asm_ctx*>& hs, const double* const* b, double* const* x, double rtol, int max_iter,
               int on_device, asm_solve_info* infos) {
     cudaStream_t st = hs[0]->stream;
     Batch B;
     B.hs = hs;
-    B.prec = hs[0]->prec;
-    B.smem = 0;
-    bool all_smem = true;
-    for (asm_ctx* h : hs) {
-        B.smem = std::max(B.smem, h->apply_smem);
-        all_smem = all_smem && h->apply_smem > 0 && !h->no_smem;
-    }
-    if (!all_smem) B.smem = 0;
-    B.slots = 4;
-    for (asm_ctx* h : hs) B.slots = std::min(B.slots, h->apply_slots);
-    for (size_t k = 0; k < hs.size(); k++) {
-        asm_ctx* h = hs[k];
-        ensure_workspace(h);
-        const ScalLayout SL = ScalLayout::make(h->ws_m);
-        // b into slot VB, control words and tolerance
-        copy_in(h, h->d_ws.as<double>() + (long long)VB * h->n3p, b[k], sizeof(double) * 3 * (size_t)h->N, on_device);
-        int c[C_NCTL];
-        std::memset(c, 0, sizeof(c));
-        c[C_PHASE] = PH_INIT;
-        c[C_APPLY_IN] = -1;
-        c[C_SPMV_IN] = -1;
-        c[C_MAXIT] = max_iter;
-        c[C_STATUS] = ASM_ERR_NOT_CONVERGED;
-        ck(cudaMemcpyAsync(h->d_ctl.p, c, sizeof(c), cudaMemcpyHostToDevice, st));
-        double tol = rtol;
-        ck(cudaMemcpyAsync(h->d_scal.as<double>() + SL.tol, &tol, sizeof(double), cudaMemcpyHostToDevice, st));
-        ck(cudaStreamSynchronize(st));
-    }
+    for (size_t k = 0; k < hs.size(); k++) begin_solve(hs[k], b[k], on_device, rtol, max_iter);
     build_batch(B, st);
     if (hs.size() == 1 && !hs[0]->no_coop) B.coop_grid = ortho_coop_grid(hs[0]->device);
     {
@@ -627,25 +692,12 @@ int run_gmres(std::vector<asm_ctx*>& hs, const double* const* b, double* const* 
     }
     read_ctl(B, st);
     int worst = ASM_OK;
-    for (asm_ctx* h : hs)
-        if (take_dev_err(h)) worst = ASM_ERR_TIMEOUT;
     for (size_t k = 0; k < hs.size(); k++) {
-        asm_ctx* h = hs[k];
-        const int* c = B.pinned + k * C_NCTL;
-        const ScalLayout SL = ScalLayout::make(h->ws_m);
-        double sc[2];
-        ck(cudaMemcpyAsync(sc, h->d_scal.as<double>() + SL.bnorm, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
-        copy_out(h, x[k], h->d_ws.as<double>() + (long long)VX * h->n3p, sizeof(double) * 3 * (size_t)h->N, on_device);
-        ck(cudaStreamSynchronize(st));
-        int status = c[C_PHASE] == PH_DONE ? c[C_STATUS] : ASM_ERR_NOT_CONVERGED;
-        if (infos) {
-            infos[k].iterations = c[C_ITERS];
-            infos[k].restarts = c[C_RESTARTS];
-            infos[k].converged = c[C_CONVERGED];
-            infos[k].status = status;
-            infos[k].rel_residual = sc[0] > 0 ? sc[1] / sc[0] : 0.0;
-        }
-        if (status != ASM_OK && worst != ASM_ERR_TIMEOUT) worst = status;
+        const int status = harvest(hs[k], B.pinned + k * C_NCTL, x[k], on_device, infos ? &infos[k] : nullptr);
+        if (status == ASM_ERR_TIMEOUT)
+            worst = ASM_ERR_TIMEOUT;
+        else if (status != ASM_OK && worst != ASM_ERR_TIMEOUT)
+            worst = status;
     }
     return worst;
 }
@@ -664,6 +716,298 @@ int handle_matrix_view(asm_ctx* h, MatrixView* out) {
     out->stream = h->stream;
     return ASM_OK;
 }
+
+
+// ---------------------------------------------------------------------------------------------
+// Serving loop: requests of any grid size join the running batch between Krylov steps
+// ---------------------------------------------------------------------------------------------
+#include <condition_variable>
+#include <deque>
+#include <list>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+
+namespace {
+
+size_t ctx_device_bytes(const asm_ctx* h) {
+    const DBuf* bufs[] = {&h->d_ell_val, &h->d_ell_col, &h->d_ell_loc, &h->d_stage, &h->d_bcell, &h->d_cptr, &h->d_cloc,
+                          &h->d_cval, &h->d_boxsum, &h->d_slot, &h->d_dpiv, &h->d_aptr, &h->d_aloc, &h->d_acs, &h->d_fp,
+                          &h->d_stream, &h->d_pk_off_f, &h->d_pk_src_f, &h->d_pk_off_c, &h->d_pk_src_c, &h->d_lv,
+                          &h->d_rlists, &h->d_y, &h->d_corr_cells, &h->d_corr, &h->d_dev_err, &h->d_factdesc,
+                          &h->d_subdesc_single, &h->d_err, &h->d_ws, &h->d_scal, &h->d_ctl, &h->d_partial, &h->d_tab1,
+                          &h->d_vec1, &h->d_row1, &h->d_box1};
+    size_t b = 0;
+    for (const DBuf* d : bufs) b += d->bytes;
+    return b;
+}
+
+// symbolic structure of one (grid, partition, pattern): built once on a worker thread
+struct SymEntry {
+    Pattern pat;
+    std::shared_ptr<SysSym> sym;
+    bool ready = false;
+    std::string err;
+};
+
+struct Req {
+    long long ticket = 0;
+    asm_request in{};
+    std::vector<double> b;
+    std::string skey;
+    asm_ctx* h = nullptr;
+    int state = 0;  // 0 pending, 1 active, 2 done
+    std::vector<double> x;
+    asm_solve_info info{};
+};
+
+unsigned long long fnv1a(const void* p, size_t n, unsigned long long h) {
+    const unsigned char* c = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; i++) {
+        h ^= c[i];
+        h *= 1099511628211ULL;
+    }
+    return h;
+}
+
+}  // namespace
+
+struct asm_server {
+    asm_server_options opt{};
+    cudaStream_t stream = nullptr;
+    size_t budget = 0, resident = 0;
+    long long next_ticket = 1;
+    std::deque<Req*> pending;
+    std::vector<Req*> active;
+    std::unordered_map<long long, Req*> by_ticket;
+    std::map<long long, asm_ctx*> idle;  // factored systems kept for matrix reuse
+    std::list<long long> lru;            // idle keys, least recently used first
+    std::map<long long, bool> key_busy;
+    Batch batch;
+    bool dirty = true;
+    // symbolic cache + worker
+    std::mutex mu;
+    std::condition_variable cv;
+    std::map<std::string, SymEntry> syms;
+    std::deque<std::pair<std::string, Req*>> jobs;
+    bool quit = false;
+    std::thread worker;
+    asm_server_stats st{};
+};
+
+namespace {
+
+void sym_worker(asm_server* S) {
+    for (;;) {
+        std::string key;
+        Req* r = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv.wait(lk, [&] { return S->quit || !S->jobs.empty(); });
+            if (S->quit) return;
+            key = S->jobs.front().first;
+            r = S->jobs.front().second;
+            S->jobs.pop_front();
+        }
+        SymEntry e;
+        const asm_request& q = r->in;
+        e.err = build_pattern(q.n_cells, q.row_ptr, q.col_idx, q.nnzb, e.pat);
+        if (e.err.empty()) {
+            Geom g;
+            g.nx = q.nx;
+            g.ny = q.ny;
+            g.nz = q.nz;
+            g.px = q.px;
+            g.py = q.py;
+            g.pz = q.pz;
+            g.ov = q.overlap;
+            g.nw = q.near_width;
+            for (int d = 0; d < 3; d++) {
+                g.cn[d] = q.near_width > 0 ? q.c_near[d] : 1;
+                g.cf[d] = q.far_mode == ASM_FAR_BOXES ? q.c_far[d] : 1;
+            }
+            g.far_mode = q.far_mode;
+            e.sym = std::make_shared<SysSym>();
+            e.err = build_symbolic(g, e.pat, S->opt.precision, 1, *e.sym, 0);
+        }
+        e.ready = true;
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->syms[key] = std::move(e);
+    }
+}
+
+std::string structure_key(const asm_request& q, int prec) {
+    unsigned long long hsh = 1469598103934665603ULL;
+    hsh = fnv1a(q.row_ptr, sizeof(int) * ((size_t)q.n_cells + 1), hsh);
+    hsh = fnv1a(q.col_idx, sizeof(int) * (size_t)q.nnzb, hsh);
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "%d,%d,%d|%d,%d,%d|%d,%d|%d,%d,%d|%d|%d,%d,%d|%d|%llx", q.nx, q.ny, q.nz, q.px, q.py,
+                  q.pz, q.overlap, q.near_width, q.c_near[0], q.c_near[1], q.c_near[2], q.far_mode, q.c_far[0],
+                  q.c_far[1], q.c_far[2], prec, hsh);
+    return buf;
+}
+
+void evict_idle(asm_server* S, size_t need) {
+    while (S->resident + need > S->budget && !S->lru.empty()) {
+        const long long key = S->lru.front();
+        S->lru.pop_front();
+        asm_ctx* h = S->idle[key];
+        S->idle.erase(key);
+        S->resident -= ctx_device_bytes(h);
+        asm_destroy(h);
+        S->st.evictions++;
+    }
+}
+
+// New system for a request whose structure is ready: matrix, shared symbolic, numeric factor.
+int build_ctx(asm_server* S, Req* r, const SymEntry& e, asm_ctx** out) {
+    asm_options o;
+    asm_default_options(&o);
+    o.precision = S->opt.precision;
+    o.restart = S->opt.restart;
+    o.device = S->opt.device;
+    asm_ctx* h = nullptr;
+    int st = asm_create(&h, &o, S->stream);
+    if (st) return st;
+    const asm_request& q = r->in;
+    st = guard(h, [&]() -> int {
+        asm_set_grid(h, q.nx, q.ny, q.nz);
+        h->pat = e.pat;
+        h->nnzb = q.nnzb;
+        h->d_ell_val.alloc((size_t)h->pat.ell_w * 9 * h->pat.rows_pad * sizeof(double));
+        h->d_ell_val.zero(h->stream);
+        h->d_ell_col.upload(h->pat.ell_col, h->stream);
+        h->d_ell_loc.upload(h->pat.ell_loc, h->stream);
+        fill_ell(h, q.vals, 0);
+        h->d_stage.release();
+        h->has_matrix = true;
+        const int cf[3] = {q.c_far[0], q.c_far[1], q.c_far[2]};
+        int s2 = asm_set_partition_boxes(h, q.px, q.py, q.pz, q.overlap, q.near_width, q.c_near, q.far_mode, cf);
+        if (s2) return s2;
+        h->sym = e.sym;
+        upload_symbolic(h);
+        h->sym_valid = true;
+        h->ws_m = -1;
+        return factor_numeric(h);
+    });
+    if (st) {
+        asm_destroy(h);
+        return st;
+    }
+    *out = h;
+    return ASM_OK;
+}
+
+void admit(asm_server* S) {
+    for (auto it = S->pending.begin(); it != S->pending.end();) {
+        Req* r = *it;
+        if (S->opt.max_active > 0 && (int)S->active.size() >= S->opt.max_active) break;
+        const long long key = r->in.matrix_key;
+        asm_ctx* h = nullptr;
+        bool fresh = false;  // a newly built system (a reused one is already counted as resident)
+        if (key >= 0 && S->key_busy[key]) {  // same matrix in flight: wait for it
+            ++it;
+            continue;
+        }
+        if (key >= 0 && S->idle.count(key)) {  // repeated matrix: factors already on the device
+            h = S->idle[key];
+            S->idle.erase(key);
+            S->lru.remove(key);
+            S->st.reuse_hits++;
+        } else {
+            if (r->skey.empty()) r->skey = structure_key(r->in, S->opt.precision);
+            SymEntry* e = nullptr;
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                auto f = S->syms.find(r->skey);
+                if (f == S->syms.end()) {
+                    S->syms[r->skey] = SymEntry();
+                    S->jobs.push_back({r->skey, r});
+                    S->cv.notify_one();
+                    S->st.structure_builds++;
+                } else if (f->second.ready) {
+                    e = &f->second;
+                }
+            }
+            if (!e) {  // structure being analysed on the worker thread
+                ++it;
+                continue;
+            }
+            if (!e->err.empty()) {
+                r->info.status = ASM_ERR_INVALID_ARG;
+                r->state = 2;
+                it = S->pending.erase(it);
+                continue;
+            }
+            const size_t need = (size_t)r->in.n_cells * 6144;  // ~6 KB per cell resident (FP32 factors, m = 30)
+            evict_idle(S, need);
+            if (S->resident + need > S->budget && !S->active.empty()) {
+                ++it;  // no memory now: wait for systems to finish
+                continue;
+            }
+            const int st = build_ctx(S, r, *e, &h);
+            if (st) {
+                r->info.status = st;
+                r->state = 2;
+                it = S->pending.erase(it);
+                continue;
+            }
+            fresh = true;
+        }
+        const int st = guard(h, [&]() -> int {
+            begin_solve(h, r->b.data(), 0, r->in.rtol, r->in.max_iter);
+            return ASM_OK;
+        });
+        if (st) {
+            r->info.status = st;
+            r->state = 2;
+            asm_destroy(h);
+            it = S->pending.erase(it);
+            continue;
+        }
+        r->h = h;
+        r->state = 1;
+        if (fresh) S->resident += ctx_device_bytes(h);
+        if (key >= 0) S->key_busy[key] = true;
+        S->active.push_back(r);
+        S->dirty = true;
+        it = S->pending.erase(it);
+        S->st.admitted++;
+    }
+}
+
+void retire(asm_server* S, Req* r, const int* c) {
+    asm_ctx* h = r->h;
+    r->x.resize(3 * (size_t)h->N);
+    guard(h, [&]() -> int {
+        harvest(h, c, r->x.data(), 0, &r->info);
+        return ASM_OK;
+    });
+    r->state = 2;
+    r->h = nullptr;
+    const long long key = r->in.matrix_key;
+    if (key >= 0) {
+        S->key_busy[key] = false;
+        if (S->opt.max_cached > 0) {
+            S->idle[key] = h;
+            S->lru.push_back(key);
+            while ((int)S->idle.size() > S->opt.max_cached) {
+                const long long k0 = S->lru.front();
+                S->lru.pop_front();
+                S->resident -= ctx_device_bytes(S->idle[k0]);
+                asm_destroy(S->idle[k0]);
+                S->idle.erase(k0);
+                S->st.evictions++;
+            }
+            return;
+        }
+    }
+    S->resident -= ctx_device_bytes(h);
+    asm_destroy(h);
+}
+
+}  // namespace
 
 // ---------------------------------------------------------------------------------------------
 // C ABI
@@ -825,7 +1169,7 @@ int asm_factor(asm_handle h) {
         h->err_sub = h->err_row = -1;
         if (!h->sym_valid) {
             auto t0 = std::chrono::steady_clock::now();
-            h->sym.reset(new SysSym());
+            h->sym = std::make_shared<SysSym>();
             std::string e = build_symbolic(h->geom, h->pat, h->prec, h->opt.local_solver == ASM_LOCAL_BILU0_COLSUM ? 1 : 0,
                                            *h->sym, 0);
             if (!e.empty()) {
@@ -838,42 +1182,7 @@ int asm_factor(asm_handle h) {
             h->ws_m = -1;
             h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         }
-        SysSym& S = *h->sym;
-        cudaEvent_t e0, e1;
-        ck(cudaEventCreate(&e0));
-        ck(cudaEventCreate(&e1));
-        ck(cudaEventRecord(e0, h->stream));
-        if (S.g.far_mode != 0)
-            launch_coarse(h->d_cptr.as<int>(), h->d_cloc.as<int>(), h->d_ell_val.as<double>(), h->pat.rows_pad,
-                          h->d_cval.as<double>(), S.nC, h->stream);
-        launch_assemble(h->d_aptr.as<int>(), h->d_aloc.as<int>(), h->d_acs.as<int>(), h->d_ell_val.as<double>(),
-                        h->pat.rows_pad, h->d_cval.as<double>(), h->d_slot.as<double>(), h->total_slots, h->stream);
-        h->d_err.zero(h->stream);
-        launch_factor(h->d_factdesc.as<FactDesc>(), (int)S.subs.size(), h->d_err.as<FactErr>(), nullptr, h->stream);
-        launch_pack(h->d_pk_off_f.as<long long>(), h->d_pk_src_f.as<int>(), h->pk_nf, h->prec,
-                    h->d_stream.as<unsigned char>(), h->d_slot.as<double>(), h->stream);
-        launch_pack(h->d_pk_off_c.as<long long>(), h->d_pk_src_c.as<int>(), h->pk_nc, 0, h->d_stream.as<unsigned char>(),
-                    h->d_slot.as<double>(), h->stream);
-        ck(cudaGetLastError());
-        ck(cudaEventRecord(e1, h->stream));
-        FactErr fe;
-        ck(cudaMemcpyAsync(&fe, h->d_err.p, sizeof(fe), cudaMemcpyDeviceToHost, h->stream));
-        sync(h);
-        float ms = 0;
-        ck(cudaEventElapsedTime(&ms, e0, e1));
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        h->factor_ms = ms;
-        h->prof.factor_ms += ms;
-        h->prof.kernel_launches += 5;
-        if (fe.flag) {
-            h->err_sub = fe.sub;
-            h->err_row = fe.row;
-            h->factored = false;
-            return ASM_ERR_ZERO_PIVOT;
-        }
-        h->factored = true;
-        return ASM_OK;
+        return factor_numeric(h);
     });
 }
 
@@ -1086,6 +1395,166 @@ int asm_get_local_factors(asm_handle h, int s, double* lu, double* dpiv) {
         sync(h);
         return ASM_OK;
     });
+}
+
+
+void asm_server_default_options(asm_server_options* o) {
+    if (!o) return;
+    o->precision = ASM_PREC_FP32;
+    o->restart = 30;
+    o->device = 0;
+    o->max_active = 64;
+    o->max_cached = 16;
+    o->hbm_budget = 0;
+}
+
+int asm_server_create(asm_server_handle* out, const asm_server_options* opt, void* cuda_stream) {
+    if (!out) return ASM_ERR_INVALID_ARG;
+    *out = nullptr;
+    asm_server_options o;
+    asm_server_default_options(&o);
+    if (opt) o = *opt;
+    if (o.precision < 0 || o.precision > 2 || o.restart < 1 || o.restart > 512 || o.max_active < 0 || o.max_cached < 0 ||
+        o.hbm_budget < 0)
+        return ASM_ERR_INVALID_ARG;
+    if (cudaSetDevice(o.device) != cudaSuccess) {
+        cudaGetLastError();
+        return ASM_ERR_INVALID_ARG;
+    }
+    asm_server* S = new (std::nothrow) asm_server();
+    if (!S) return ASM_ERR_OOM;
+    S->opt = o;
+    S->stream = static_cast<cudaStream_t>(cuda_stream);
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        cudaGetLastError();
+        delete S;
+        return ASM_ERR_CUDA;
+    }
+    S->budget = o.hbm_budget > 0 ? (size_t)o.hbm_budget : (size_t)(0.85 * (double)fr);
+    S->worker = std::thread(sym_worker, S);
+    *out = S;
+    return ASM_OK;
+}
+
+int asm_server_submit(asm_server_handle S, const asm_request* q, long long* ticket) {
+    if (!S || !q || !ticket || !q->b || !q->row_ptr || !q->col_idx || !q->vals) return ASM_ERR_INVALID_ARG;
+    if (q->nx < 1 || q->ny < 1 || q->nz < 1 || (long long)q->nx * q->ny * q->nz != q->n_cells || q->nnzb < q->n_cells ||
+        !(q->rtol >= 0.0) || q->max_iter < 1 || q->px < 1 || q->py < 1 || q->pz < 1 || q->px > q->nx ||
+        q->py > q->ny || q->pz > q->nz)
+        return ASM_ERR_INVALID_ARG;
+    Req* r = new (std::nothrow) Req();
+    if (!r) return ASM_ERR_OOM;
+    r->ticket = S->next_ticket++;
+    r->in = *q;
+    r->b.assign(q->b, q->b + 3 * (size_t)q->n_cells);
+    r->in.b = nullptr;
+    S->pending.push_back(r);
+    S->by_ticket[r->ticket] = r;
+    S->st.submitted++;
+    *ticket = r->ticket;
+    return ASM_OK;
+}
+
+int asm_server_progress(asm_server_handle S, int max_steps, int* n_active, int* n_pending) {
+    if (!S || max_steps < 0) return ASM_ERR_INVALID_ARG;
+    if (cudaSetDevice(S->opt.device) != cudaSuccess) {
+        cudaGetLastError();
+        return ASM_ERR_CUDA;
+    }
+    try {
+        admit(S);
+        for (int step = 0; step < max_steps && !S->active.empty(); step++) {
+            if (S->dirty) {
+                S->batch.hs.clear();
+                for (Req* r : S->active) S->batch.hs.push_back(r->h);
+                build_batch(S->batch, S->stream);
+                S->batch.has_init = true;
+                S->dirty = false;
+            }
+            read_ctl(S->batch, S->stream);
+            int kmax = -1;
+            std::vector<Req*> keep;
+            for (size_t k = 0; k < S->active.size(); k++) {
+                const int* c = S->batch.pinned + k * C_NCTL;
+                if (c[C_PHASE] == PH_DONE) {
+                    retire(S, S->active[k], c);
+                    S->st.completed++;
+                    S->dirty = true;
+                    continue;
+                }
+                keep.push_back(S->active[k]);
+                kmax = std::max(kmax, c[C_PHASE] == PH_ARNOLDI ? c[C_J] + 1 : 0);
+            }
+            if (S->dirty) {  // membership changed: retired systems leave, waiting ones join
+                S->active.swap(keep);
+                admit(S);
+                if (S->active.empty()) break;
+                S->batch.hs.clear();
+                for (Req* r : S->active) S->batch.hs.push_back(r->h);
+                build_batch(S->batch, S->stream);
+                S->batch.has_init = true;
+                S->dirty = false;
+                read_ctl(S->batch, S->stream);
+                kmax = -1;
+                for (size_t k = 0; k < S->active.size(); k++) {
+                    const int* c = S->batch.pinned + k * C_NCTL;
+                    if (c[C_PHASE] != PH_DONE) kmax = std::max(kmax, c[C_PHASE] == PH_ARNOLDI ? c[C_J] + 1 : 0);
+                }
+            }
+            launch_step(S->batch, kmax, S->stream, nullptr);
+            S->st.steps++;
+        }
+    } catch (const CudaFail& e) {
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        return ASM_ERR_OOM;
+    }
+    if (n_active) *n_active = (int)S->active.size();
+    if (n_pending) *n_pending = (int)S->pending.size();
+    S->st.resident_bytes = (long long)S->resident;
+    return ASM_OK;
+}
+
+int asm_server_result(asm_server_handle S, long long ticket, double* x, asm_solve_info* info) {
+    if (!S) return ASM_ERR_INVALID_ARG;
+    auto f = S->by_ticket.find(ticket);
+    if (f == S->by_ticket.end()) return ASM_ERR_INVALID_ARG;
+    Req* r = f->second;
+    if (r->state != 2) return ASM_ERR_STATE;
+    if (x && !r->x.empty()) std::memcpy(x, r->x.data(), r->x.size() * sizeof(double));
+    if (info) *info = r->info;
+    const int st = r->info.status;
+    S->by_ticket.erase(f);
+    delete r;
+    return st == ASM_OK || st == ASM_ERR_NOT_CONVERGED ? ASM_OK : st;
+}
+
+int asm_server_get_stats(asm_server_handle S, asm_server_stats* out) {
+    if (!S || !out) return ASM_ERR_INVALID_ARG;
+    S->st.resident_bytes = (long long)S->resident;
+    S->st.budget_bytes = (long long)S->budget;
+    S->st.active = (int)S->active.size();
+    S->st.pending = (int)S->pending.size();
+    *out = S->st;
+    return ASM_OK;
+}
+
+int asm_server_destroy(asm_server_handle S) {
+    if (!S) return ASM_OK;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->quit = true;
+    }
+    S->cv.notify_all();
+    if (S->worker.joinable()) S->worker.join();
+    cudaSetDevice(S->opt.device);
+    for (Req* r : S->active)
+        if (r->h) asm_destroy(r->h);
+    for (auto& kv : S->idle) asm_destroy(kv.second);
+    for (auto& kv : S->by_ticket) delete kv.second;
+    delete S;
+    return ASM_OK;
 }
 
 }  // extern "C"
