@@ -204,6 +204,43 @@ def run_serving(args, stream):
                       f"{len(pool)} distinct synthetic matrices 2e3-1e6 cells"}
 
 
+def run_profile_case(args):
+    """Small case for ncu captures: 128 x 128 x 32 (16 x 16 x 1 subdomains, overlap 2), three
+    preconditioner applies then one GMRES solve."""
+    import torch
+    from paper_1401_7227_gb300 import asm2
+    from paper_1401_7227_gb300 import build as lib_build
+    lib_build.build()
+    s = synth.grid_jacobian(128, 128, 32, 3, 2.0)
+    sol = asm2.Solver(precision=args.precision, restart=30)
+    sol.set_grid(128, 128, 32)
+    sol.set_matrix(s.row_ptr, s.col_idx, s.vals)
+    sol.set_partition(16, 16, 1, 2)
+    sol.factor()
+    b = torch.from_numpy(s.b).cuda()
+    for _ in range(3):
+        sol.apply(b)
+    torch.cuda.synchronize()
+    x, info = sol.solve(b, 1e-8, 400)
+    print(json.dumps({"profile_case": "grid128x128x32_k256", "info": info, "stats": sol.stats()}))
+    sol.close()
+    return 0
+
+
+def apply_traffic(alg_bytes: int):
+    """DRAM bytes per apply from the committed ncu record, scaled by algorithmic bytes; None when
+    the kernel source changed since the counters were taken."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "apply_traffic.json")))
+        src = open(os.path.join(ROOT, "paper_1401_7227_gb300", "csrc", "kernels_solve.cu"), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != rec["kernel_source_sha256_16"]:
+            return None
+        return int(rec["dram_bytes_per_launch"] * alg_bytes / rec["alg_bytes_per_launch"])
+    except Exception:
+        return None
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -354,7 +391,7 @@ def run_gpu(args):
                  "host_check_rel_residual": results["fp64"]["host_check_relres"]} if "fp64" in results else None,
         "breakdown_ms_per_solve": {k: prof[k] / args.steps for k in ("apply_ms", "spmv_ms", "ortho_ms", "factor_ms")},
         "roofline": {"bound": "hbm", "kernel": "precond apply (boxsum + fused local solves)", "achieved": achieved,
-                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": apply_traffic(alg_bytes),
                      "alg_bytes_per_launch": alg_bytes, "launch_ms": apply_ms, "peak_kind": peak_kind},
         "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(system.vals.nbytes + system.b.nbytes),
                 "d2h_bytes_per_step": int(system.b.nbytes)},
@@ -388,6 +425,7 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--profile-case", action="store_true", help="small case for ncu captures")
     ap.add_argument("--serve-requests", type=int, default=600)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-pool", type=int, default=12)
@@ -395,6 +433,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_case:
+        return run_profile_case(args)
     return run_gpu(args)
 
 
