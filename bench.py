@@ -99,6 +99,18 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, ws: int) -> float:
+    """The largest value of x over the ranks (the job's time is its slowest replica's)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------------------------------------
 # CPU oracle, bounded sample
 # ---------------------------------------------------------------------------------------------
@@ -325,11 +337,7 @@ def run_gpu(args):
                 infos.append(info)
             e1.record(stream)
             barrier()
-        ms = e0.elapsed_time(e1) / args.steps
-        if ws > 1:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, ws)
         prof = sol.profile()
         sol.set_profiling(False)
         st = sol.stats()
@@ -364,7 +372,7 @@ def run_gpu(args):
     for _ in range(args.steps):
         e2e_step()
     barrier()
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, ws)
 
     prof = main["prof"]
     st = main["stats"]

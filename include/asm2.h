@@ -167,12 +167,19 @@ int asm_spmv(asm_handle h, const double* x, double* y, int on_device);
 
 /* Solve A x = b to ||b - A x||_2 <= rtol ||b||_2 (FP64 true residual) with the Krylov method of
  * the options, x0 = 0 (Section 2).  x receives the solution (or the last iterate with
- * NOT_CONVERGED).  info may be NULL. */
+ * NOT_CONVERGED).  info may be NULL.
+ *   GMRES(m): restarted, modified Gram-Schmidt, Givens rotations; stops when the Arnoldi residual
+ *   estimate reaches rtol, then confirms on the true residual (a restart otherwise).
+ *   ORTHOMIN(k): p = B^{-1} r, q = A p, A-orthogonalised (newest first) against the k most
+ *   recent directions, x += alpha p, r -= alpha q with alpha = (r, q) / (q, q); stops when the
+ *   updated residual reaches rtol or max_iter steps have run, or on (q, q) = 0; the reported
+ *   status and rel_residual are those of the true residual at that point (no restart). */
 int asm_solve(asm_handle h, const double* b, double* x, double rtol, int max_iter, int on_device,
               asm_solve_info* info);
 
 /* Solve n independent factored systems together: every Krylov step of all unfinished systems
- * runs in the same kernel launches.  Handles must share device and stream and use GMRES.
+ * runs in the same kernel launches.  Handles must share device, stream, factor precision and
+ * Krylov method.
  * b[k], x[k] belong to hs[k]; infos[k] (may be NULL) receives its result.  Each system's
  * arithmetic does not depend on the others in the batch.  Returns the worst status. */
 int asm_solve_batch(asm_handle* hs, int n, const double* const* b, double* const* x, double rtol,

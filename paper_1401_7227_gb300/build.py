@@ -5,6 +5,7 @@ change (a content hash, not file times, so a copied tree rebuilds correctly).
 """
 from __future__ import annotations
 
+import fcntl
 import hashlib
 import os
 import shutil
@@ -50,14 +51,25 @@ def _run(cmd):
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every translation unit for sm_103a and link libasm2.so; returns its path."""
+    """Compile every translation unit for sm_103a and link libasm2.so; returns its path.  Processes
+    that build at the same time (one per rank) take turns on a lock file; the later ones find the
+    library up to date."""
+    os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build_locked(force, verbose)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(force: bool, verbose: bool) -> str:
     stamp_file = os.path.join(BUILD, "stamp")
     stamp = _stamp()
     if not force and os.path.exists(LIB) and os.path.exists(stamp_file):
         with open(stamp_file) as f:
             if f.read().strip() == stamp:
                 return LIB
-    os.makedirs(BUILD, exist_ok=True)
     cxx = shutil.which("g++") or "g++"
     jobs = []
     for s in CU_SOURCES:

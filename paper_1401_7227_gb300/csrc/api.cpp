@@ -90,6 +90,7 @@ struct asm_ctx {
     DBuf d_err;
     std::vector<FactDesc> fact_desc;
     std::vector<SubDesc> sub_desc;   // sys = 0
+    std::vector<double> sub_cost;    // estimated apply time of each subdomain (launch order)
     std::vector<BoxItem> box_items;  // sys = 0
     std::vector<long long> slot_base, stream_base, row_base;
     long long pk_nf = 0, pk_nc = 0, total_slots = 0;
@@ -146,6 +147,24 @@ void fill_ell(asm_ctx* h, const double* vals, int on_device) {
     launch_ell_fill(src, h->d_ell_loc.as<int>(), h->nnzb, h->d_ell_val.as<double>(), h->pat.rows_pad, 0, h->stream);
     ck(cudaGetLastError());
     if (!on_device) sync(h);
+}
+
+// Subdomain work items of several systems, most expensive first (the order of the CTAs of the
+// apply launch; every CTA writes only its own subdomain's owned rows, so the order does not
+// change any result)
+std::vector<SubDesc> longest_first(const std::vector<asm_ctx*>& hs) {
+    std::vector<std::pair<double, SubDesc>> v;
+    for (int k = 0; k < (int)hs.size(); k++)
+        for (size_t i = 0; i < hs[k]->sub_desc.size(); i++) {
+            SubDesc d = hs[k]->sub_desc[i];
+            d.sys = k;
+            v.emplace_back(i < hs[k]->sub_cost.size() ? hs[k]->sub_cost[i] : 0.0, d);
+        }
+    std::stable_sort(v.begin(), v.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    std::vector<SubDesc> out;
+    out.reserve(v.size());
+    for (auto& e : v) out.push_back(e.second);
+    return out;
 }
 
 // Upload the symbolic structure and build the per-subdomain descriptors.
@@ -253,6 +272,7 @@ void upload_symbolic(asm_ctx* h) {
     offc.reserve(npc);
     srcc.reserve(npc);
     h->sub_desc.assign(K, SubDesc{});
+    h->sub_cost.assign(K, 0.0);
     h->apply_smem = 0;
     for (int s = 0; s < K; s++) {
         const SubSym& o = S.subs[s];
@@ -281,6 +301,12 @@ void upload_symbolic(asm_ctx* h) {
         sd.nc = o.n - o.nf;
         sd.n_chunks = (int)o.chunk_off.size();
         sd.n_fwd = o.n_fwd_chunks;
+        // a chunk costs about one barrier-bounded step; lump-only chunks (FP64 rows) about 2.3
+        for (size_t i = 0; i < o.chunk_off.size(); i++) {
+            int hdr_nf = 0;
+            std::memcpy(&hdr_nf, o.stream.data() + o.chunk_off[i] + 4, sizeof(int));
+            h->sub_cost[s] += hdr_nf == 0 ? 2.3 : 1.0;
+        }
         sd.n_own = (int)o.own_pos.size();
         sd.n_long = (int)o.clong.size();
         sd.corr0 = corr_base;
@@ -355,7 +381,8 @@ void upload_symbolic(asm_ctx* h) {
         h->apply_smem = 0;
         h->apply_slots = 3;
     }
-    h->d_subdesc_single.upload(h->sub_desc, st);
+    // most expensive subdomains first: the CTAs of the last wave are then the short ones
+    h->d_subdesc_single.upload(longest_first({h}), st);
     h->d_err.alloc(sizeof(FactErr));
     sync(h);
 }
@@ -363,12 +390,14 @@ void upload_symbolic(asm_ctx* h) {
 // Krylov workspace and the single-system tables
 void ensure_workspace(asm_ctx* h) {
     const int m = std::max(1, h->opt.restart);
-    const int flex = h->flexible;
+    const bool om = h->opt.krylov == ASM_KRYLOV_ORTHOMIN;
+    const int flex = om ? 2 : h->flexible;  // ORTHOMIN keeps its own slot layout
     if (h->ws_m == m && h->ws_flex == flex && h->d_ws.p) return;
     const long long n3 = 3LL * h->N;
     h->n3p = (n3 + VEC_CHUNK - 1) / VEC_CHUNK * VEC_CHUNK;
     h->nchunk = (int)(h->n3p / VEC_CHUNK);
-    const int nslots = VV0 + m + 1 + (flex ? m : 0);
+    // GMRES: V_0..V_m (+ Z_0..Z_{m-1} when flexible); ORTHOMIN: P_0..P_k, Q_0..Q_k
+    const int nslots = om ? VV0 + 2 * (m + 1) : VV0 + m + 1 + (flex ? m : 0);
     h->d_ws.alloc((size_t)nslots * h->n3p * sizeof(double));
     h->d_ws.zero(h->stream);
     const ScalLayout SL = ScalLayout::make(m);
@@ -385,7 +414,8 @@ void ensure_workspace(asm_ctx* h) {
     t.n3 = (int)n3;
     t.n_cells = h->N;
     t.m = m;
-    t.flexible = flex;
+    t.flexible = om ? 0 : flex;
+    t.krylov = om ? 1 : 0;
     t.nchunk = h->nchunk;
     t.scal = h->d_scal.as<double>();
     t.ctl = h->d_ctl.as<int>();
@@ -513,11 +543,8 @@ void build_batch(Batch& B, cudaStream_t st) {
             b.sys = k;
             bi.push_back(b);
         }
-        for (SubDesc s : h->sub_desc) {
-            s.sys = k;
-            sd.push_back(s);
-        }
     }
+    sd = longest_first(B.hs);
     B.d_tab.upload(tabs, st);
     B.d_vec.upload(vi, st);
     B.d_row.upload(ri, st);
@@ -585,6 +612,29 @@ void launch_step(Batch& B, int kmax, cudaStream_t st, StepEvents* ev) {
     for (asm_ctx* h : B.hs) h->prof.kernel_launches += n;
 }
 
+// One ORTHOMIN step of every system: [apply | mat-vec | projections 0..kmax + update], with the
+// events at the same places as a GMRES step (the prep and post groups are empty)
+void launch_step_om(Batch& B, int kmax, cudaStream_t st, StepEvents* ev) {
+    const SysTab* tab = B.d_tab.as<SysTab>();
+    const VecItem* vi = B.d_vec.as<VecItem>();
+    if (ev) ck(cudaEventRecord(ev->e[0], st));
+    if (B.has_init) launch_init(tab, vi, B.nvec, st);
+    if (ev) ck(cudaEventRecord(ev->e[1], st));
+    launch_boxsum(tab, B.d_box.as<BoxItem>(), B.nbox, st);
+    launch_apply(tab, B.d_sub.as<SubDesc>(), B.nsub, B.prec, B.smem, B.slots, st);
+    if (ev) {
+        ck(cudaEventRecord(ev->e[2], st));
+        ck(cudaEventRecord(ev->e[3], st));
+    }
+    launch_spmv(tab, B.d_row.as<RowItem>(), B.nrow, st);
+    if (ev) ck(cudaEventRecord(ev->e[4], st));
+    for (int l = 0; l <= kmax; l++) launch_om(tab, vi, B.nvec, l, st);
+    launch_om_update(tab, vi, B.nvec, st);
+    if (ev) ck(cudaEventRecord(ev->e[5], st));
+    ck(cudaGetLastError());
+    for (asm_ctx* h : B.hs) h->prof.kernel_launches += 4 + kmax + 1;
+}
+
 float elapsed(cudaEvent_t a, cudaEvent_t b) {
     float ms = 0;
     ck(cudaEventElapsedTime(&ms, a, b));
@@ -634,27 +684,31 @@ int harvest(asm_ctx* h, const int* c, double* x, int on_device, asm_solve_info* 
     return status;
 }
 
-int run_gmres(std::vector<asm_ctx*>& hs, const double* const* b, double* const* x, double rtol, int max_iter,
+// GMRES(m) or ORTHOMIN(k) (every system of the batch uses the same method)
+int run_krylov(std::vector<asm_ctx*>& hs, const double* const* b, double* const* x, double rtol, int max_iter,
               int on_device, asm_solve_info* infos) {
     cudaStream_t st = hs[0]->stream;
     Batch B;
     B.hs = hs;
     for (size_t k = 0; k < hs.size(); k++) begin_solve(hs[k], b[k], on_device, rtol, max_iter);
     build_batch(B, st);
-    if (hs.size() == 1 && !hs[0]->no_coop) B.coop_grid = ortho_coop_grid(hs[0]->device);
+    const bool om = hs[0]->opt.krylov == ASM_KRYLOV_ORTHOMIN;
+    if (hs.size() == 1 && !hs[0]->no_coop && !om) B.coop_grid = ortho_coop_grid(hs[0]->device);
     {
         // initial step: x = 0, r = b, beta = ||b||
         const SysTab* tab = B.d_tab.as<SysTab>();
         const VecItem* vi = B.d_vec.as<VecItem>();
         launch_init(tab, vi, B.nvec, st);
-        if (B.coop_grid > 0) {
+        if (om) {
+            launch_om(tab, vi, B.nvec, 0, st);
+        } else if (B.coop_grid > 0) {
             ck(launch_ortho_coop(tab, hs[0]->d_partial.as<double>(), B.coop_grid, st));
         } else {
             launch_mgs(tab, vi, B.nvec, 0, st);
             launch_finish(tab, vi, B.nvec, st);
         }
         ck(cudaGetLastError());
-        for (asm_ctx* h : hs) h->prof.kernel_launches += B.coop_grid > 0 ? 2 : 3;
+        for (asm_ctx* h : hs) h->prof.kernel_launches += (B.coop_grid > 0 || om) ? 2 : 3;
     }
     const bool prof = hs[0]->profiling;
     StepEvents ev;
@@ -679,6 +733,7 @@ int run_gmres(std::vector<asm_ctx*>& hs, const double* const* b, double* const* 
             if (c[C_PHASE] == PH_DONE) continue;
             any = true;
             if (c[C_PHASE] == PH_ARNOLDI) kmax = std::max(kmax, c[C_J] + 1);
+            else if (c[C_PHASE] == PH_OM) kmax = std::max(kmax, c[C_OM_STORED]);
             else kmax = std::max(kmax, 0);
         }
         if (!any) break;
@@ -687,7 +742,10 @@ int run_gmres(std::vector<asm_ctx*>& hs, const double* const* b, double* const* 
             const int* c = B.pinned + k * C_NCTL;
             if (c[C_APPLY_IN] >= 0 && c[C_PHASE] != PH_DONE) pending_applies++;
         }
-        launch_step(B, kmax, st, prof ? &ev : nullptr);
+        if (om)
+            launch_step_om(B, kmax, st, prof ? &ev : nullptr);
+        else
+            launch_step(B, kmax, st, prof ? &ev : nullptr);
         pending = prof;
     }
     read_ctl(B, st);
@@ -1235,12 +1293,11 @@ int asm_solve(asm_handle h, const double* b, double* x, double rtol, int max_ite
               asm_solve_info* info) {
     if (!h || !b || !x || !(rtol >= 0.0) || max_iter < 1) return ASM_ERR_INVALID_ARG;
     if (!h->factored) return ASM_ERR_STATE;
-    if (h->opt.krylov != ASM_KRYLOV_GMRES) return ASM_ERR_INVALID_ARG;
     return guard(h, [&]() -> int {
         std::vector<asm_ctx*> hs{h};
         const double* bs[1] = {b};
         double* xs[1] = {x};
-        return run_gmres(hs, bs, xs, rtol, max_iter, on_device, info);
+        return run_krylov(hs, bs, xs, rtol, max_iter, on_device, info);
     });
 }
 
@@ -1252,13 +1309,13 @@ int asm_solve_batch(asm_handle* hs, int n, const double* const* b, double* const
         if (!h) return ASM_ERR_INVALID_ARG;
         if (!h->factored) return ASM_ERR_STATE;
         if (h->device != v[0]->device || h->stream != v[0]->stream || h->prec != v[0]->prec ||
-            h->opt.krylov != ASM_KRYLOV_GMRES)
+            h->opt.krylov != v[0]->opt.krylov)
             return ASM_ERR_INVALID_ARG;
     }
     for (int i = 0; i < n; i++)
         for (int k = i + 1; k < n; k++)
             if (v[i] == v[k]) return ASM_ERR_INVALID_ARG;
-    return guard(v[0], [&]() -> int { return run_gmres(v, b, x, rtol, max_iter, on_device, infos); });
+    return guard(v[0], [&]() -> int { return run_krylov(v, b, x, rtol, max_iter, on_device, infos); });
 }
 
 int asm_get_stats(asm_handle h, asm_stats* st) {

@@ -16,11 +16,15 @@ namespace asm2 {
 constexpr int VEC_CHUNK = 4096;   // elements per vector work item (256 threads x 16)
 constexpr int kStreamChunk = 8192;   // bytes of one factor-stream chunk / shared-memory ring slot
 constexpr int kStreamSlots = 3;      // default ring slots of the apply (chunks in flight per CTA)
+constexpr int kLongLumpRow = 16;     // lump rows with more stored blocks are swept by a whole warp
+// Chunk header word 6: bit 0 = last chunk of its wavefront level; bits 8..11 = log2 of the entry
+// slots S of the short lump rows (each such row takes 3 S lanes: 3 output components x S slots).
 constexpr int VEC_THREADS = 256;
 enum VecSlot { VX = 0, VB = 1, VR = 2, VW = 3, VZ = 4, VU = 5, VV0 = 6 };  // V_k = VV0 + k; Z_k after V
 
 // GMRES phases of one system
-enum Phase { PH_DONE = 0, PH_ARNOLDI = 1, PH_RESTART = 2, PH_INIT = 3 };
+enum Phase { PH_DONE = 0, PH_ARNOLDI = 1, PH_RESTART = 2, PH_INIT = 3, PH_OM = 4, PH_OM_FINAL = 5 };
+// PH_OM: one ORTHOMIN direction (apply, mat-vec, projections, update); PH_OM_FINAL: true residual.
 
 // Per-system control words (device, int32), written by the state kernels.
 enum Ctl {
@@ -40,12 +44,14 @@ enum Ctl {
     C_CNT_RED,    // arrival counter of the chunk reduction in flight
     C_CNT_FIN,    // arrival counter of the finishing kernel
     C_BREAKDOWN,
-    C_NCTL = 16
+    C_OM_STORED,  // ORTHOMIN: directions held (at most k)
+    C_OM_SLOT,    // ORTHOMIN: ring slot of the direction in progress (0 .. k)
+    C_NCTL = 20
 };
 
 // Per-system scalars (device, double) at fixed offsets; H is (m+1) x m row-major.
 struct ScalLayout {
-    int bnorm, beta, tol, w0, hn, red0, red1, H, cs, sn, g, y, n;
+    int bnorm, beta, tol, w0, hn, red0, red1, H, cs, sn, g, y, om_qq, om_beta, om_alpha, n;
     __host__ __device__ static ScalLayout make(int m) {
         ScalLayout L;
         int o = 0;
@@ -66,6 +72,11 @@ struct ScalLayout {
         o += m + 1;
         L.y = o;
         o += m;
+        L.om_qq = o;  // ORTHOMIN: (q_s, q_s) of every ring slot
+        o += m + 1;
+        L.om_beta = o;  // ORTHOMIN: projection coefficients of the step in progress
+        o += m;
+        L.om_alpha = o++;
         L.n = o;
         return L;
     }
@@ -77,8 +88,9 @@ struct SysTab {
     long long n3p;       // padded vector length
     int n3;              // 3 * n_cells
     int n_cells;
-    int m;               // GMRES restart length
+    int m;               // GMRES restart length, or ORTHOMIN direction count k
     int flexible;        // keep Z_k = B^{-1} V_k (slots after V)
+    int krylov;          // asm_krylov: 0 GMRES (slots V_k, Z_k), 1 ORTHOMIN (slots P_s, then Q_s)
     int nchunk;          // vector work items of this system
     double* scal;        // scalars (ScalLayout)
     int* ctl;            // control words (Ctl)
@@ -191,6 +203,10 @@ void launch_prep(const SysTab* tab, const VecItem* items, int nitems, cudaStream
 void launch_post(const SysTab* tab, const VecItem* items, int nitems, cudaStream_t st);
 void launch_mgs(const SysTab* tab, const VecItem* items, int nitems, int k, cudaStream_t st);
 void launch_finish(const SysTab* tab, const VecItem* items, int nitems, cudaStream_t st);
+// ORTHOMIN(k): projection pass l of the direction in progress (l = 0 also reduces ||r|| of
+// initial systems and ||b - A x|| of finishing ones), then x += alpha p, r -= alpha q.
+void launch_om(const SysTab* tab, const VecItem* items, int nitems, int l, cudaStream_t st);
+void launch_om_update(const SysTab* tab, const VecItem* items, int nitems, cudaStream_t st);
 // Whole Gram-Schmidt + state step of a single system in one cooperative launch (grid <= the
 // co-resident limit from ortho_coop_grid); part2 holds 4 * nchunk doubles.
 int ortho_coop_grid(int device);

@@ -156,6 +156,7 @@ __device__ __forceinline__ void sweep_chunk(const unsigned char* base, bool lowe
     constexpr int FB = FineBlock<TF>::bytes;
     const int* hdr = reinterpret_cast<const int*>(base);
     const int f0 = hdr[0], nf = hdr[1], c0 = hdr[2], nc = hdr[3], ef = hdr[4], ec = hdr[5];
+    const int lump_lg = (hdr[6] >> 8) & 15;
     const unsigned char* p = base + 32;
     const int* fptr = reinterpret_cast<const int*>(p);
     p += align16(4 * (size_t)(nf + 1));
@@ -267,12 +268,13 @@ __device__ __forceinline__ void sweep_chunk(const unsigned char* base, bool lowe
     // Lump rows are FP64, and an FP64 warp instruction keeps an SM sub-partition's FP64 unit busy
     // for ~64 cycles whatever the number of active lanes, so lump work is packed into as few FP64
     // instructions as the latency allows:
-    //  - short rows (<= kLongRow blocks): three lanes per row (one per output component, 3 FMAs per
-    //    block), ten rows per warp;
+    //  - short rows (<= kLongLumpRow blocks): 3 S lanes per row, lane = 3 s + k computing output
+    //    component k over the entries s, s + S, ..., combined by log2(S) shuffle adds; 32 / (3 S)
+    //    rows per warp.  S (1, 2, 4 or 8) is chosen per chunk by the host (header word 6);
     //  - long rows: one warp each, lane = 8 * k + s computing component k over the entries s, s+8,
     //    ..., combined by three shuffle adds.
     // Rows go to the warps from the last one (the first warps carry the fine rows of the chunk).
-    constexpr int kLongRow = 16;
+    constexpr int kLongRow = kLongLumpRow;
     {
         const int k = lane >> 3, sl = lane & 7;
         const bool lane_on = lane < 24;
@@ -316,14 +318,15 @@ __device__ __forceinline__ void sweep_chunk(const unsigned char* base, bool lowe
         }
     }
     {
-        const int r = lane / 3, k = lane - 3 * (lane / 3);
-        for (int base = (nwarp - 1 - warp) * 10; base < nc; base += nwarp * 10) {
+        const int S = 1 << lump_lg, lpr = 3 * S, rpw = 32 / lpr;
+        const int r = lane / lpr, within = lane - r * lpr, sl = within / 3, k = within - 3 * sl;
+        for (int base = (nwarp - 1 - warp) * rpw; base < nc; base += nwarp * rpw) {
             const int i = base + r;
-            const bool on = lane < 30 && i < nc && cptr[i + 1] - cptr[i] <= kLongRow;
+            const bool on = r < rpw && i < nc && cptr[i + 1] - cptr[i] <= kLongRow;
             if (!__any_sync(0xffffffffu, on)) continue;
             double acc = 0.0;
             if (on)
-                for (int e = cptr[i]; e < cptr[i + 1]; e++) {
+                for (int e = cptr[i] + sl; e < cptr[i + 1]; e += S) {
                     const double* v = cval + 9LL * e + 3 * k;
                     const int c = ccol[e];
                     double x0, x1, x2;
@@ -338,16 +341,19 @@ __device__ __forceinline__ void sweep_chunk(const unsigned char* base, bool lowe
                     }
                     acc = fma(v[0], x0, fma(v[1], x1, fma(v[2], x2, acc)));
                 }
+            // slot 0 of each (row, component) collects the row's sum: sources stay inside the row
+            for (int o = 3; o < lpr; o <<= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+            const bool head = on && sl == 0;
             const int c = c0 + i;
-            const double b = on ? yc[3 * c + k] - acc : 0.0;
+            const double b = head ? yc[3 * c + k] - acc : 0.0;
             if (lower) {
-                if (on) yc[3 * c + k] = b;
+                if (head) yc[3 * c + k] = b;
             } else {
-                const int l0 = 3 * r;
+                const int l0 = r * lpr;
                 const double b0 = __shfl_sync(0xffffffffu, b, l0 < 32 ? l0 : 0);
                 const double b1 = __shfl_sync(0xffffffffu, b, l0 + 1 < 32 ? l0 + 1 : 0);
                 const double b2 = __shfl_sync(0xffffffffu, b, l0 + 2 < 32 ? l0 + 2 : 0);
-                if (on) {
+                if (head) {
                     const double* d = cdi + 9LL * i + 3 * k;
                     const double t = fma(d[0], b0, fma(d[1], b1, d[2] * b2));
                     yc[3 * c + k] = t;
@@ -451,6 +457,10 @@ __global__ void __launch_bounds__(256, 2) k_apply(const SysTab* __restrict__ tab
     }
     __syncthreads();
 
+    // descriptor of the next chunk to stream, loaded one chunk ahead so that thread 0 does not
+    // wait on a global load between the barrier and the copy it issues
+    int2 next_ch = make_int2(0, 0);
+    if (tid == 0 && slots < sd.n_chunks) next_ch = sd.chunks[slots];
     for (int ci = 0; ci < sd.n_chunks; ci++) {
         const int slot = ci % slots;
         const bool ok = mbar_wait(&bar[slot], (unsigned)(ci / slots) & 1u);
@@ -466,9 +476,9 @@ __global__ void __launch_bounds__(256, 2) k_apply(const SysTab* __restrict__ tab
             return;
         }
         if (tid == 0 && ci + slots < sd.n_chunks) {
-            const int2 ch = sd.chunks[ci + slots];
-            mbar_expect_tx(&bar[slot], (unsigned)ch.y);
-            bulk_load(ring + (size_t)slot * kStreamChunk, sd.stream + ch.x, (unsigned)ch.y, &bar[slot]);
+            mbar_expect_tx(&bar[slot], (unsigned)next_ch.y);
+            bulk_load(ring + (size_t)slot * kStreamChunk, sd.stream + next_ch.x, (unsigned)next_ch.y, &bar[slot]);
+            if (ci + slots + 1 < sd.n_chunks) next_ch = sd.chunks[ci + slots + 1];
         }
     }
 
@@ -626,6 +636,7 @@ __global__ void __launch_bounds__(VEC_THREADS) k_mgs(const SysTab* __restrict__ 
                                                      int k) {
     const VecItem it = items[blockIdx.x];
     const SysTab& st = tab[it.sys];
+    if (st.krylov != 0) return;
     const int ph = st.ctl[C_PHASE];
     const long long e0 = (long long)it.chunk * VEC_CHUNK;
     const ScalLayout SL = ScalLayout::make(st.m);
@@ -783,7 +794,7 @@ __global__ void __launch_bounds__(VEC_THREADS) k_finish(const SysTab* __restrict
     const VecItem it = items[blockIdx.x];
     const SysTab& st = tab[it.sys];
     const int ph = st.ctl[C_PHASE];
-    if (ph == PH_DONE) return;
+    if (ph == PH_DONE || st.krylov != 0) return;
     const ScalLayout SL = ScalLayout::make(st.m);
     const long long e0 = (long long)it.chunk * VEC_CHUNK;
     if (ph == PH_ARNOLDI) {
@@ -815,6 +826,166 @@ __global__ void __launch_bounds__(VEC_THREADS) k_finish(const SysTab* __restrict
     __threadfence();
     st.ctl[C_CNT_FIN] = 0;
     step_state(st, ph);
+}
+
+// ------------------------------------------------------------------------------------------
+// ORTHOMIN(k) (Section 2): the new direction p = B^{-1} r, q = A p is A-orthogonalised against the
+// k most recent directions (newest first, each projection on the q already updated), then
+// alpha = (r, q) / (q, q), x += alpha p, r -= alpha q.  The directions sit in a ring of k + 1
+// slots: P_s = VV0 + s, Q_s = VV0 + k + 1 + s.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ int om_p(const SysTab& st, int s) { return VV0 + s; }
+__device__ __forceinline__ int om_q(const SysTab& st, int s) { return VV0 + st.m + 1 + s; }
+
+__device__ void om_set_slots(const SysTab& st, int ph) {
+    int* c = st.ctl;
+    if (ph == PH_OM) {
+        const int s = c[C_OM_SLOT];
+        c[C_APPLY_IN] = VR;
+        c[C_APPLY_OUT] = om_p(st, s);
+        c[C_SPMV_IN] = om_p(st, s);
+        c[C_SPMV_OUT] = om_q(st, s);
+        c[C_SPMV_B] = -1;
+    } else if (ph == PH_OM_FINAL) {
+        c[C_APPLY_IN] = -1;
+        c[C_SPMV_IN] = VX;
+        c[C_SPMV_OUT] = VW;
+        c[C_SPMV_B] = VB;
+    } else {
+        c[C_APPLY_IN] = -1;
+        c[C_SPMV_IN] = -1;
+    }
+}
+
+// ORTHOMIN state machine of one system (one thread).  nrm = ||r|| (initial and after an update)
+// or ||b - A x|| (final).
+__device__ void om_state(const SysTab& st, int ph, double nrm) {
+    const ScalLayout SL = ScalLayout::make(st.m);
+    int* c = st.ctl;
+    double* s = st.scal;
+    int next = PH_OM;
+    if (ph == PH_INIT) {
+        s[SL.bnorm] = nrm;
+        s[SL.beta] = nrm;
+        if (nrm == 0.0) {
+            c[C_CONVERGED] = 1;
+            c[C_STATUS] = 0;
+            next = PH_DONE;
+        } else {
+            c[C_OM_STORED] = 0;
+            c[C_OM_SLOT] = 0;
+        }
+    } else if (ph == PH_OM) {
+        c[C_ITERS] += 1;
+        if (c[C_OM_STORED] < st.m) c[C_OM_STORED] += 1;
+        if (nrm <= s[SL.tol] * s[SL.bnorm] || c[C_ITERS] >= c[C_MAXIT])
+            next = PH_OM_FINAL;
+        else
+            c[C_OM_SLOT] = (c[C_OM_SLOT] + 1) % (st.m + 1);
+    } else {  // PH_OM_FINAL
+        s[SL.beta] = nrm;
+        const bool conv = nrm <= s[SL.tol] * s[SL.bnorm];
+        c[C_CONVERGED] = conv ? 1 : 0;
+        c[C_STATUS] = conv ? 0 : 4;  // ASM_ERR_NOT_CONVERGED
+        next = PH_DONE;
+    }
+    c[C_PHASE] = next;
+    om_set_slots(st, next);
+}
+
+// Pass l of a direction step: l >= 1 first applies projection l (p -= beta_l P_os, q -= beta_l Q_os,
+// os = the l-th most recent stored direction); then either the next coefficient
+// beta_{l+1} = (q, Q_os') / (Q_os', Q_os') or, after the last projection, (q, q) and (r, q).
+__global__ void __launch_bounds__(VEC_THREADS) k_om(const SysTab* __restrict__ tab, const VecItem* __restrict__ items,
+                                                    int l) {
+    const VecItem it = items[blockIdx.x];
+    const SysTab& st = tab[it.sys];
+    if (st.krylov != 1) return;
+    const int ph = st.ctl[C_PHASE];
+    const long long e0 = (long long)it.chunk * VEC_CHUNK;
+    const ScalLayout SL = ScalLayout::make(st.m);
+    double s0 = 0.0, s1 = 0.0;
+    if (ph == PH_OM) {
+        const int stored = st.ctl[C_OM_STORED];
+        if (l > stored) return;
+        const int K1 = st.m + 1, slot = st.ctl[C_OM_SLOT];
+        double* p = vec(st, om_p(st, slot));
+        double* q = vec(st, om_q(st, slot));
+        if (l >= 1) {
+            const int os = (slot - l + K1) % K1;
+            const double beta = st.scal[SL.om_beta + l - 1];
+            const double* po = vec(st, om_p(st, os));
+            const double* qo = vec(st, om_q(st, os));
+            for (int i = threadIdx.x; i < VEC_CHUNK; i += blockDim.x) {
+                p[e0 + i] -= beta * po[e0 + i];
+                q[e0 + i] -= beta * qo[e0 + i];
+            }
+        }
+        if (l < stored) {
+            const double* qo = vec(st, om_q(st, (slot - l - 1 + K1) % K1));
+            for (int i = threadIdx.x; i < VEC_CHUNK; i += blockDim.x) s0 += q[e0 + i] * qo[e0 + i];
+        } else {
+            const double* r = vec(st, VR);
+            for (int i = threadIdx.x; i < VEC_CHUNK; i += blockDim.x) {
+                const double a = q[e0 + i];
+                s0 += a * a;
+                s1 += r[e0 + i] * a;
+            }
+        }
+        if (!finish_reduction(st, it.chunk, s0, s1)) return;
+        if (threadIdx.x == 0) {
+            if (l < stored) {
+                const int on = (slot - l - 1 + K1) % K1;
+                st.scal[SL.om_beta + l] = s0 / st.scal[SL.om_qq + on];
+            } else {
+                st.scal[SL.om_qq + slot] = s0;
+                st.scal[SL.om_alpha] = s0 != 0.0 ? s1 / s0 : 0.0;
+            }
+        }
+    } else if (ph == PH_INIT || ph == PH_OM_FINAL) {
+        if (l != 0) return;
+        const double* r = vec(st, ph == PH_INIT ? VR : VW);
+        for (int i = threadIdx.x; i < VEC_CHUNK; i += blockDim.x) {
+            const double a = r[e0 + i];
+            s0 += a * a;
+        }
+        if (!finish_reduction(st, it.chunk, s0, s1)) return;
+        if (threadIdx.x == 0) om_state(st, ph, sqrt(s0));
+    }
+}
+
+// x += alpha p, r -= alpha q and ||r||; a direction with (q, q) = 0 ends the iteration instead.
+__global__ void __launch_bounds__(VEC_THREADS) k_om_update(const SysTab* __restrict__ tab,
+                                                           const VecItem* __restrict__ items) {
+    const VecItem it = items[blockIdx.x];
+    const SysTab& st = tab[it.sys];
+    if (st.krylov != 1 || st.ctl[C_PHASE] != PH_OM) return;
+    const ScalLayout SL = ScalLayout::make(st.m);
+    const int slot = st.ctl[C_OM_SLOT];
+    const bool dead = st.scal[SL.om_qq + slot] == 0.0;
+    const long long e0 = (long long)it.chunk * VEC_CHUNK;
+    double s0 = 0.0, s1 = 0.0;
+    if (!dead) {
+        const double alpha = st.scal[SL.om_alpha];
+        const double* p = vec(st, om_p(st, slot));
+        const double* q = vec(st, om_q(st, slot));
+        double* x = vec(st, VX);
+        double* r = vec(st, VR);
+        for (int i = threadIdx.x; i < VEC_CHUNK; i += blockDim.x) {
+            x[e0 + i] += alpha * p[e0 + i];
+            const double a = r[e0 + i] - alpha * q[e0 + i];
+            r[e0 + i] = a;
+            s0 += a * a;
+        }
+    }
+    if (!finish_reduction(st, it.chunk, s0, s1)) return;
+    if (threadIdx.x != 0) return;
+    if (dead) {
+        st.ctl[C_PHASE] = PH_OM_FINAL;
+        om_set_slots(st, PH_OM_FINAL);
+    } else {
+        om_state(st, PH_OM, sqrt(s0));
+    }
 }
 
 // The whole orthogonalisation of one step of one system in one cooperative launch: modified
@@ -1004,6 +1175,13 @@ int ortho_coop_grid(int device) {
 cudaError_t launch_ortho_coop(const SysTab* tab, double* part2, int grid, cudaStream_t st) {
     void* args[] = {(void*)&tab, (void*)&part2};
     return cudaLaunchCooperativeKernel((const void*)k_ortho_coop, dim3(grid), dim3(VEC_THREADS), args, 0, st);
+}
+
+void launch_om(const SysTab* tab, const VecItem* items, int nitems, int l, cudaStream_t st) {
+    if (nitems > 0) k_om<<<nitems, VEC_THREADS, 0, st>>>(tab, items, l);
+}
+void launch_om_update(const SysTab* tab, const VecItem* items, int nitems, cudaStream_t st) {
+    if (nitems > 0) k_om_update<<<nitems, VEC_THREADS, 0, st>>>(tab, items);
 }
 
 void launch_finish(const SysTab* tab, const VecItem* items, int nitems, cudaStream_t st) {

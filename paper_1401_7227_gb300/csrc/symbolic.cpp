@@ -442,7 +442,8 @@ std::string build_sub(const Ctx& X, int s, SubSym& o) {
     // level (fine rows at the factor precision, lump rows in FP64): all forward chunks in level
     // order, then all backward chunks in reverse level order -- the order the apply consumes them,
     // so the stream is read front to back.  Chunk layout (every array 16-byte aligned):
-    //   header int[8] = {f0, nf, c0, nc, nef, nec, last_in_level, bytes}
+    //   header int[8] = {f0, nf, c0, nc, nef, nec, flags, bytes}; flags: bit 0 = last chunk of
+    //   the level, bits 8..11 = log2 of the short lump rows' entry slots
     //   fptr[nf+1] fcol[nef] fval[nef blocks] (fdinv[nf blocks]) cptr[nc+1] ccol[nec] cval[nec] (cdinv[nc])
     // Columns: fine index (>= 0) or ~lump index.
     const size_t fbb = X.prec == 0 ? 72 : (X.prec == 1 ? 36 : 20);  // FP64 / FP32 / FP16 + exponent
@@ -551,6 +552,34 @@ std::string build_sub(const Ctx& X, int s, SubSym& o) {
         }
         return ne;
     };
+    // Entry slots of the short lump rows of a chunk.  A row split over S slots costs
+    // 3 ceil(len / S) FMAs plus log2(S) shuffle-adds per lane, and 32 / (3 S) rows share a warp;
+    // groups of rows go to warps 7, 6, ..., so groups g and g + 4 share an SM sub-partition, whose
+    // FP64 pipe issues one warp instruction at a time.  S minimises the FP64 instructions of the
+    // busiest sub-partition (the sweep is latency-bound: these instructions are its critical path).
+    auto lump_slots_log2 = [&](const Piece& pc_) {
+        int rows = 0, len = 0;
+        for (int k = 0; k < pc_.nc; k++) {
+            const int p = o.row_of_pos[pc_.pos_c + k];
+            const int e = pc_.fwd ? nl(p) : nu(p);
+            if (e <= asm2::kLongLumpRow) {
+                rows++;
+                len = std::max(len, e);
+            }
+        }
+        int best = 0;
+        long long best_cost = -1;
+        for (int lg = 0; lg <= 3; lg++) {
+            const int S = 1 << lg, rpw = 32 / (3 * S);
+            const long long groups = (rows + rpw - 1) / rpw, per_smsp = (groups + 3) / 4;
+            const long long cost = per_smsp * (3LL * ((len + S - 1) / S) + lg);
+            if (best_cost < 0 || cost < best_cost) {
+                best_cost = cost;
+                best = lg;
+            }
+        }
+        return best;
+    };
     for (size_t i = 0; i < pieces.size(); i++) {
         const Piece& pc_ = pieces[i];
         size_t w = (size_t)o.chunk_off[i];
@@ -564,7 +593,7 @@ std::string build_sub(const Ctx& X, int s, SubSym& o) {
         hdr[3] = pc_.nc;
         hdr[4] = ef;
         hdr[5] = ec;
-        hdr[6] = pc_.last ? 1 : 0;
+        hdr[6] = (pc_.last ? 1 : 0) | (lump_slots_log2(pc_) << 8);
         hdr[7] = o.chunk_bytes[i];
         if (w != (size_t)o.chunk_off[i] + (size_t)o.chunk_bytes[i]) return "stream chunk layout mismatch";
     }

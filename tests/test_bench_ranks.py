@@ -1,0 +1,64 @@
+"""Host logic of the benchmark's multi-rank launch (one process per GPU, replicas of the solve),
+run here as two gloo ranks on the CPU: the rank environment, the max-over-ranks timing, and the
+reference arm doing its work on rank 0 only."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+WORKER = r"""
+import json, os, sys
+sys.path.insert(0, os.environ["REPO_ROOT"])
+import torch.distributed as dist
+import bench
+ws, rank, local = bench.dist_env()
+dist.init_process_group("gloo", rank=rank, world_size=ws)
+t = bench.max_over_ranks(10.0 + 5.0 * rank, ws)
+dist.barrier()
+print(json.dumps({"rank": rank, "ws": ws, "local": local, "max": t}))
+dist.destroy_process_group()
+"""
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _env(rank, ws, port):
+    env = dict(os.environ)
+    env.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws),
+               LOCAL_RANK=str(rank), REPO_ROOT=ROOT)
+    return env
+
+
+def test_max_over_ranks_with_two_gloo_ranks():
+    port = _free_port()
+    procs = [subprocess.Popen([sys.executable, "-c", WORKER], env=_env(r, 2, port), stdout=subprocess.PIPE,
+                              stderr=subprocess.PIPE, text=True) for r in range(2)]
+    outs = []
+    for p in procs:
+        out, err = p.communicate(timeout=120)
+        assert p.returncode == 0, err
+        outs.append(json.loads(out.strip().splitlines()[-1]))
+    assert sorted(o["rank"] for o in outs) == [0, 1]
+    for o in outs:
+        assert o["ws"] == 2 and o["local"] == o["rank"]
+        assert o["max"] == 15.0  # every rank reports the slowest replica
+
+
+def test_single_rank_needs_no_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(3.5, 1) == 3.5
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    # a non-zero rank of the reference arm exits 0 at once and prints nothing
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], env=_env(1, 2, _free_port()), capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == ""
