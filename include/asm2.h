@@ -154,6 +154,21 @@ int asm_update_values(asm_handle h, const double* vals, int on_device);
 int asm_set_partition_boxes(asm_handle h, int px, int py, int pz, int overlap, int near_width,
                             const int* c_near, int far_mode, const int* c_far);
 
+/* Classical coarse-grid corrections, the methods the paper compares its boundary conditioning
+ * with (Section 3, Fig. 6), added to the preconditioner set by asm_set_partition_boxes (B_AS):
+ *   ASM_COARSE_TWO_LEVEL  B^{-1} = B_AS^{-1} + R_C^T A_C^{-1} R_C                      (Eq. 3.5)
+ *   ASM_COARSE_TWO_STAGE  B^{-1} = B_AS^{-1} + R_C^T A_C^{-1} R_C (I - A B_AS^{-1})    (Eqs. 3.7-3.8)
+ * R_C sums the 3-vectors of the cells of each coarse box, R_C^T copies a box's value to each of
+ * its cells, and A_C = R_C A R_C^T (Eq. 3.6) is inverted exactly at asm_factor (Gauss-Jordan
+ * elimination with partial pivoting, FP64, on the device).  c_box: the coarse box size (x, y, z)
+ * in cells, boxes aligned at 0 and numbered bz + nbz*(bx + nbx*by); NULL or {0,0,0} takes the
+ * partition boxes (box = subdomain).  At most 1024 coarse boxes.  ASM_COARSE_NONE removes the
+ * correction.  Invalidates the factorisation.  Errors: INVALID_ARG (mode, box size, too many
+ * boxes), STATE (no grid or partition yet); a singular A_C makes asm_factor return ZERO_PIVOT
+ * with error location (-1, coarse block row).  The serving loop does not take these options. */
+typedef enum { ASM_COARSE_NONE = 0, ASM_COARSE_TWO_LEVEL = 1, ASM_COARSE_TWO_STAGE = 2 } asm_coarse_mode;
+int asm_set_coarse_correction(asm_handle h, int mode, const int* c_box);
+
 /* Build B: host symbolic analysis (cached across asm_update_values), then on the device the
  * local matrices A_i = R_i A R_i^T (Eq. 3.4, B.3) and their block ILU(0) (+ colsum, Section 2).
  * Errors: STATE (no matrix/partition), ZERO_PIVOT (see asm_get_error_location), OOM, CUDA. */

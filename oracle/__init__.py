@@ -89,6 +89,9 @@ def lib():
         L.orc_gmres.argtypes = [C.c_int, P, P, P, P, P, P, C.c_int, C.c_double, C.c_int,
                                 C.POINTER(_Info), P]
         L.orc_orthomin.argtypes = L.orc_gmres.argtypes
+        L.orc_pc_set_coarse.argtypes = [P, P, P, P, C.c_int, P, C.POINTER(C.c_int)]
+        L.orc_pc_coarse_nb.argtypes = [P]
+        L.orc_pc_coarse_matrix.argtypes = [P, P, P]
         _lib = L
     return _lib
 
@@ -180,12 +183,19 @@ class OracleError(RuntimeError):
         self.where = where
 
 
+NO_COARSE, TWO_LEVEL, TWO_STAGE = 0, 1, 2
+
+
 class Precond:
     """B^{-1} = sum_s P_s R_s^T A_s^{-1} R_s with A_s = R_s A R_s^T (Eqs. 3.4, 4.1-4.5).
 
-    ``only`` builds a single subdomain (sampled checks on large grids)."""
+    ``only`` builds a single subdomain (sampled checks on large grids).  ``coarse`` adds the
+    classical coarse-grid correction the paper compares with (Section 3): TWO_LEVEL (Eq. 3.5) or
+    TWO_STAGE (Eqs. 3.7-3.8), on the partition boxes (``cbox`` None) or aligned boxes of ``cbox``
+    cells."""
 
-    def __init__(self, g: Geometry, row_ptr, col_idx, vals, solver: int = BILU0_COLSUM, only: int = -1):
+    def __init__(self, g: Geometry, row_ptr, col_idx, vals, solver: int = BILU0_COLSUM, only: int = -1,
+                 coarse: int = NO_COARSE, cbox=None):
         self.g = g
         self.solver = solver
         self.only = only
@@ -197,6 +207,14 @@ class Precond:
                                       only, C.byref(st), _p(loc))
         if not self._h:
             raise OracleError(st.value, tuple(int(x) for x in loc))
+        self.coarse = coarse
+        if coarse != NO_COARSE:
+            cb = None if cbox is None else np.asarray(cbox, dtype=np.int32)
+            bad = C.c_int(-1)
+            st = lib().orc_pc_set_coarse(self._h, _p(self._rp), _p(self._ci), _p(self._v), coarse,
+                                         None if cb is None else _p(cb), C.byref(bad))
+            if st != 0:
+                raise OracleError(st, ("coarse", bad.value))
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -249,6 +267,14 @@ class Precond:
         out = np.empty_like(rhs)
         lib().orc_pc_local_solve(self._h, s, _p(rhs), _p(out))
         return out
+
+    def coarse_matrix(self):
+        """(A_C as a dense (3 nb, 3 nb) array, coarse box of every cell)."""
+        nb = lib().orc_pc_coarse_nb(self._h)
+        ac = np.empty((3 * nb, 3 * nb))
+        box = np.empty(self.g.n_cells, dtype=np.int32)
+        lib().orc_pc_coarse_matrix(self._h, _p(ac), _p(box))
+        return ac, box
 
     def apply(self, r, z=None) -> np.ndarray:
         r = _f64(r)

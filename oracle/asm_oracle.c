@@ -1,8 +1,9 @@
 /*
  * Plain, slow, single-threaded FP64 CPU oracle of the two-level ("boundary conditioning")
  * additive Schwarz preconditioner of Jackson, Taroni & Ponting (arXiv:1401.7227), with block
- * ILU(0) + column-sum compensation as the local solver, and of the GMRES and ORTHOMIN
- * accelerators it is used in.
+ * ILU(0) + column-sum compensation as the local solver, of the classical two-level and
+ * two-stage coarse-grid corrections it is compared with (Section 3), and of the GMRES and
+ * ORTHOMIN accelerators it is used in.
  *
  * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's CPU-baseline leg
  * may load this file.  It shares no code with the CUDA library and must stay readable against the
@@ -456,18 +457,19 @@ typedef struct {
     int* piv;
 } dense_lu_t;
 
-static int dense_lu_factor(const bsr_t* m, dense_lu_t* d, int* bad_row) {
-    const int n3 = 3 * m->n;
+static int dense_alloc(dense_lu_t* d, int n3) {
     d->n3 = n3;
     d->a = (double*)calloc((size_t)n3 * n3 + 1, sizeof(double));
     d->piv = (int*)malloc(sizeof(int) * (size_t)(n3 > 0 ? n3 : 1));
-    if (!d->a || !d->piv) return ORC_ERR_NOMEM;
+    return (!d->a || !d->piv) ? ORC_ERR_NOMEM : ORC_OK;
+}
+
+/* Gaussian elimination with partial pivoting (whole rows swapped) of the filled d->a, in place:
+ * unit-lower multipliers below the diagonal, U on and above it.  *bad_row = block row of a zero
+ * pivot. */
+static int dense_factor(dense_lu_t* d, int* bad_row) {
+    const int n3 = d->n3;
     double* a = d->a;
-    for (int p = 0; p < m->n; p++)
-        for (int t = m->rp[p]; t < m->rp[p + 1]; t++)
-            for (int r = 0; r < 3; r++)
-                for (int s = 0; s < 3; s++)
-                    a[(size_t)(3 * p + r) * n3 + 3 * m->ci[t] + s] = m->v[9 * (size_t)t + 3 * r + s];
     for (int c = 0; c < n3; c++) {
         int pr = c;
         for (int r = c + 1; r < n3; r++)
@@ -491,6 +493,18 @@ static int dense_lu_factor(const bsr_t* m, dense_lu_t* d, int* bad_row) {
         }
     }
     return 0;
+}
+
+static int dense_lu_factor(const bsr_t* m, dense_lu_t* d, int* bad_row) {
+    const int n3 = 3 * m->n;
+    if (dense_alloc(d, n3)) return ORC_ERR_NOMEM;
+    double* a = d->a;
+    for (int p = 0; p < m->n; p++)
+        for (int t = m->rp[p]; t < m->rp[p + 1]; t++)
+            for (int r = 0; r < 3; r++)
+                for (int s = 0; s < 3; s++)
+                    a[(size_t)(3 * p + r) * n3 + 3 * m->ci[t] + s] = m->v[9 * (size_t)t + 3 * r + s];
+    return dense_factor(d, bad_row);
 }
 
 static void dense_lu_solve(const dense_lu_t* d, const double* rhs, double* x) {
@@ -528,12 +542,26 @@ typedef struct {
     dense_lu_t dlu; /* solver 2 */
 } orc_sub;
 
+/* Classical coarse-grid correction (Section 3, Eqs. 3.5-3.8): R_C sums the 3-vectors of each coarse
+ * box's cells, R_C^T copies a box's value to each of its cells, A_C = R_C A R_C^T (Eq. 3.6) is
+ * solved exactly (dense LU with partial pivoting). */
+typedef struct {
+    int mode;       /* 0 none, 1 two-level (Eq. 3.5), 2 two-stage (Eqs. 3.7-3.8) */
+    int nb;         /* coarse boxes */
+    int* box;       /* [N] coarse box of each cell */
+    dense_lu_t lu;  /* of A_C, 3 nb unknowns */
+    double* ac;     /* A_C before factorisation (3 nb x 3 nb, row-major), for inspection */
+    const int *rp, *ci; /* A (caller-owned, kept alive by the caller) for the two-stage residual */
+    const double* v;
+} orc_coarse;
+
 typedef struct {
     orc_geom g;
     int N, K, solver;
     int* owner;
     orc_sub* sub;
     int only; /* -1: all subdomains built; else the one subdomain that was built */
+    orc_coarse cc;
 } orc_pc;
 
 static void sub_free(orc_sub* s) {
@@ -548,6 +576,10 @@ static void sub_free(orc_sub* s) {
 
 void orc_pc_destroy(orc_pc* pc) {
     if (!pc) return;
+    free(pc->cc.box);
+    free(pc->cc.lu.a);
+    free(pc->cc.lu.piv);
+    free(pc->cc.ac);
     if (pc->sub)
         for (int s = 0; s < pc->K; s++) sub_free(&pc->sub[s]);
     free(pc->sub);
@@ -668,6 +700,100 @@ void orc_pc_restrict(const orc_pc* pc, int s, const double* r, double* rl) {
     }
 }
 
+/* Coarse boxes and A_C = R_C A R_C^T of the classical correction.  mode 1: two-level (Eq. 3.5),
+ * 2: two-stage (Eqs. 3.7-3.8), 0: none.  cbox = NULL or {0,0,0}: the coarse boxes are the
+ * partition boxes (box = owning subdomain); else aligned boxes of cbox cells, numbered
+ * bz + nbz*(bx + nbx*by) like cells.  A (rp, ci, v) must outlive the preconditioner.  Returns
+ * ORC_OK, ORC_ERR_ARG, ORC_ERR_NOMEM, or ORC_ERR_PIVOT with *bad_box = the coarse block row. */
+int orc_pc_set_coarse(orc_pc* pc, const int* rp, const int* ci, const double* v, int mode, const int* cbox,
+                      int* bad_box) {
+    if (mode < 0 || mode > 2) return ORC_ERR_ARG;
+    free(pc->cc.box);
+    free(pc->cc.lu.a);
+    free(pc->cc.lu.piv);
+    free(pc->cc.ac);
+    memset(&pc->cc, 0, sizeof(pc->cc));
+    if (mode == 0) return ORC_OK;
+    const orc_geom* g = &pc->g;
+    const int N = pc->N;
+    orc_coarse* cc = &pc->cc;
+    cc->box = (int*)malloc(sizeof(int) * (size_t)N);
+    if (!cc->box) return ORC_ERR_NOMEM;
+    const int partition = cbox == NULL || (cbox[0] == 0 && cbox[1] == 0 && cbox[2] == 0);
+    if (partition) {
+        cc->nb = pc->K;
+        memcpy(cc->box, pc->owner, sizeof(int) * (size_t)N);
+    } else {
+        if (cbox[0] < 1 || cbox[1] < 1 || cbox[2] < 1) return ORC_ERR_ARG;
+        const int nbx = (g->nx + cbox[0] - 1) / cbox[0], nby = (g->ny + cbox[1] - 1) / cbox[1],
+                  nbz = (g->nz + cbox[2] - 1) / cbox[2];
+        cc->nb = nbx * nby * nbz;
+        for (int j = 0; j < g->ny; j++)
+            for (int i = 0; i < g->nx; i++)
+                for (int k = 0; k < g->nz; k++)
+                    cc->box[k + g->nz * (i + g->nx * j)] = k / cbox[2] + nbz * (i / cbox[0] + nbx * (j / cbox[1]));
+    }
+    const int n3 = 3 * cc->nb;
+    if (dense_alloc(&cc->lu, n3)) return ORC_ERR_NOMEM;
+    /* A_C(I, J) = sum of the blocks A(a, b) over cells a in box I and b in box J */
+    for (int a = 0; a < N; a++)
+        for (int e = rp[a]; e < rp[a + 1]; e++) {
+            const int I = cc->box[a], J = cc->box[ci[e]];
+            for (int r = 0; r < 3; r++)
+                for (int s = 0; s < 3; s++)
+                    cc->lu.a[(size_t)(3 * I + r) * n3 + 3 * J + s] += v[9 * (size_t)e + 3 * r + s];
+        }
+    cc->ac = (double*)malloc(sizeof(double) * ((size_t)n3 * n3 + 1));
+    if (!cc->ac) return ORC_ERR_NOMEM;
+    memcpy(cc->ac, cc->lu.a, sizeof(double) * (size_t)n3 * n3);
+    int bad = -1;
+    const int st = dense_factor(&cc->lu, &bad);
+    if (st) {
+        if (bad_box) *bad_box = bad;
+        return st;
+    }
+    cc->mode = mode;
+    cc->rp = rp;
+    cc->ci = ci;
+    cc->v = v;
+    return ORC_OK;
+}
+
+int orc_pc_coarse_nb(const orc_pc* pc) { return pc->cc.nb; }
+
+/* A_C (3 nb x 3 nb, row-major) and the coarse box of every cell */
+void orc_pc_coarse_matrix(const orc_pc* pc, double* ac, int* box) {
+    const int n3 = 3 * pc->cc.nb;
+    if (ac) memcpy(ac, pc->cc.ac, sizeof(double) * (size_t)n3 * n3);
+    if (box) memcpy(box, pc->cc.box, sizeof(int) * (size_t)pc->N);
+}
+
+void orc_spmv(int N, const int* rp, const int* ci, const double* v, const double* x, double* y);
+
+/* z += R_C^T A_C^{-1} R_C r (two-level, Eq. 3.5) or z += R_C^T A_C^{-1} R_C (r - A z) (two-stage,
+ * Eq. 3.7 with z = B_AS^{-1} r on entry) */
+static void coarse_correct(const orc_pc* pc, const double* r, double* z) {
+    const orc_coarse* cc = &pc->cc;
+    const int N = pc->N, n3 = 3 * cc->nb;
+    double* w = (double*)malloc(sizeof(double) * 3 * (size_t)N);
+    double* rc = (double*)calloc((size_t)n3 + 1, sizeof(double));
+    double* yc = (double*)malloc(sizeof(double) * ((size_t)n3 + 1));
+    if (cc->mode == 2) {
+        orc_spmv(N, cc->rp, cc->ci, cc->v, z, w);
+        for (int i = 0; i < 3 * N; i++) w[i] = r[i] - w[i];
+    } else {
+        memcpy(w, r, sizeof(double) * 3 * (size_t)N);
+    }
+    for (int a = 0; a < N; a++)
+        for (int c = 0; c < 3; c++) rc[3 * cc->box[a] + c] += w[3 * a + c];
+    dense_lu_solve(&cc->lu, rc, yc);
+    for (int a = 0; a < N; a++)
+        for (int c = 0; c < 3; c++) z[3 * a + c] += yc[3 * cc->box[a] + c];
+    free(w);
+    free(rc);
+    free(yc);
+}
+
 /* z = sum_s P_s R_s^T A_s^{-1} R_s r: each cell takes its owner's local solution (Eq. 4.2; the
  * off-processor coarse solution is discarded, Section 4).  With a single-subdomain build
  * (only >= 0), only that subdomain's owned rows of z are written. */
@@ -686,6 +812,7 @@ void orc_pc_apply(const orc_pc* pc, const double* r, double* z) {
         free(rl);
         free(zl);
     }
+    if (pc->cc.mode != 0) coarse_correct(pc, r, z);
 }
 
 /* ------------------------------------------------------------------------------------------ */

@@ -19,11 +19,12 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "pattern", 3: "zero pivot", 4: "not
           6: "cuda error", 7: "timeout", 8: "state"}
 PREC = {"fp64": 0, "fp32": 1, "fp16s": 2}
 FAR = {"none": 0, "partition": 1, "boxes": 2}
+COARSE = {"none": 0, "two-level": 1, "two-stage": 2}
 
 #: every symbol include/asm2.h declares
 EXPORTS = [
     "asm_default_options", "asm_error_string", "asm_create", "asm_destroy", "asm_set_grid", "asm_set_matrix_bsr",
-    "asm_update_values", "asm_set_partition_boxes", "asm_factor", "asm_apply_precond", "asm_spmv", "asm_solve",
+    "asm_update_values", "asm_set_partition_boxes", "asm_set_coarse_correction", "asm_factor", "asm_apply_precond", "asm_spmv", "asm_solve",
     "asm_solve_batch", "asm_get_stats", "asm_get_error_location", "asm_get_local_info", "asm_get_local_map",
     "asm_get_local_matrix", "asm_get_local_factors", "asm_set_profiling", "asm_get_profile", "asm_reset_profile", "asm_set_tuning", "asm_residual_noalloc",
     "asm_server_default_options", "asm_server_create", "asm_server_submit", "asm_server_progress",
@@ -236,6 +237,14 @@ class Solver:
         cn = (C.c_int * 3)(*c_near)
         cf = (C.c_int * 3)(*(c_far if c_far is not None else (1, 1, 1)))
         _check(load().asm_set_partition_boxes(self._h, px, py, pz, overlap, near_width, cn, fm, cf), "set_partition")
+
+    def set_coarse(self, mode: str | int = "two-level", c_box=None):
+        """Classical coarse-grid correction (Section 3): "none", "two-level" (Eq. 3.5) or
+        "two-stage" (Eqs. 3.7-3.8), on the partition boxes (c_box None) or aligned boxes of c_box
+        cells.  Takes effect at the next factor()."""
+        m = COARSE[mode] if isinstance(mode, str) else int(mode)
+        cb = None if c_box is None else (C.c_int * 3)(*c_box)
+        _check(load().asm_set_coarse_correction(self._h, m, cb), "set_coarse")
 
     def factor(self):
         st = load().asm_factor(self._h)

@@ -107,6 +107,15 @@ struct asm_ctx {
     bool no_coop = false;  // per-kernel orthogonalisation path instead of the cooperative one
     bool no_smem = false;  // local vectors of the apply in device memory
     asm_profile_info prof{};
+    // classical coarse-grid correction (Eqs. 3.5-3.8)
+    int coarse_mode = 0;
+    int coarse_c[3] = {0, 0, 0};  // {0,0,0}: partition boxes
+    bool coarse_valid = false;    // coarse structure built for the current grid, partition, pattern
+    int cnb = 0, cnkeys = 0, cpart_cap = 0;
+    DBuf d_cbox, d_ccells, d_ckptr, d_ckloc, d_ckeys, d_cblk, d_caug, d_cprow, d_cfcol, d_cpart, d_cerr, d_crc, d_cyc,
+        d_cw, d_cbox_items1, d_cgrow1;
+    std::vector<BoxItem> cbox_items;   // sys = 0: cells of each coarse box
+    std::vector<RowItem> cgrow_items;  // sys = 0: 8 rows of A_C^{-1} each
     // diagnostics
     int err_sub = -1, err_row = -1;
     double setup_ms = 0, factor_ms = 0;
@@ -431,6 +440,14 @@ void ensure_workspace(asm_ctx* h) {
         h->d_dev_err.zero(h->stream);
     }
     t.dev_err = h->d_dev_err.as<int>();
+    const bool coarse = h->coarse_mode != 0 && h->coarse_valid;
+    t.cmode = coarse ? h->coarse_mode : 0;
+    t.cnb = coarse ? h->cnb : 0;
+    t.cbox = coarse ? h->d_cbox.as<int>() : nullptr;
+    t.caug = coarse ? h->d_caug.as<double>() : nullptr;
+    t.crc = coarse ? h->d_crc.as<double>() : nullptr;
+    t.cyc = coarse ? h->d_cyc.as<double>() : nullptr;
+    t.cw = coarse && h->coarse_mode == 2 ? h->d_cw.as<double>() : nullptr;
     std::vector<SysTab> tabs{t};
     h->d_tab1.upload(tabs, h->stream);
     std::vector<VecItem> vi;
@@ -442,6 +459,10 @@ void ensure_workspace(asm_ctx* h) {
     h->d_row1.upload(ri, h->stream);
     h->n_row1 = (int)ri.size();
     h->d_box1.upload(h->box_items, h->stream);
+    if (coarse) {
+        h->d_cbox_items1.upload(h->cbox_items, h->stream);
+        h->d_cgrow1.upload(h->cgrow_items, h->stream);
+    }
     sync(h);
 }
 
@@ -469,6 +490,111 @@ void set_ctl(asm_ctx* h, int apply_in, int apply_out, int spmv_in, int spmv_out,
 }
 
 }  // namespace
+
+// Coarse boxes of the classical correction for the current grid and partition: cell -> box, the
+// cells of each box, and the box pairs of A's blocks (with their ELL locations) for A_C.
+int coarse_box_count(const asm_ctx* h, const int* c) {
+    if (c[0] == 0) return h->geom.px * h->geom.py * h->geom.pz;
+    return ((h->nx + c[0] - 1) / c[0]) * ((h->ny + c[1] - 1) / c[1]) * ((h->nz + c[2] - 1) / c[2]);
+}
+
+void coarse_build(asm_ctx* h) {
+    const Geom& g = h->geom;
+    const int N = h->N;
+    const int* c = h->coarse_c;
+    const int nb = coarse_box_count(h, c);
+    std::vector<int> box(N);
+    auto part = [](int n, int p, int x) {  // part t of n cells is [n t / p, n (t + 1) / p)
+        int t = (int)(((long long)x * p) / n);
+        while (t + 1 < p && (long long)n * (t + 1) / p <= x) t++;
+        while (t > 0 && (long long)n * t / p > x) t--;
+        return t;
+    };
+    const int nbx = c[0] ? (h->nx + c[0] - 1) / c[0] : 0, nbz = c[0] ? (h->nz + c[2] - 1) / c[2] : 0;
+    for (int y = 0; y < h->ny; y++)
+        for (int x = 0; x < h->nx; x++)
+            for (int z = 0; z < h->nz; z++) {
+                const int cell = z + h->nz * (x + h->nx * y);
+                box[cell] = c[0] == 0 ? part(h->nz, g.pz, z) + g.pz * (part(h->nx, g.px, x) + g.px * part(h->ny, g.py, y))
+                                      : z / c[2] + nbz * (x / c[0] + nbx * (y / c[1]));
+            }
+    std::vector<int> bptr(nb + 1, 0), cells(N);
+    for (int a = 0; a < N; a++) bptr[box[a] + 1]++;
+    for (int b = 0; b < nb; b++) bptr[b + 1] += bptr[b];
+    {
+        std::vector<int> fill(bptr.begin(), bptr.end() - 1);
+        for (int a = 0; a < N; a++) cells[fill[box[a]]++] = a;
+    }
+    std::vector<std::pair<long long, int>> kv;
+    kv.reserve(h->pat.ci.size());
+    for (int a = 0; a < N; a++)
+        for (int e = h->pat.rp[a]; e < h->pat.rp[a + 1]; e++)
+            kv.push_back({(long long)box[a] * nb + box[h->pat.ci[e]], h->pat.ell_loc[e]});
+    std::sort(kv.begin(), kv.end());
+    std::vector<int> kptr, kloc(kv.size());
+    std::vector<long long> keys;
+    for (size_t i = 0; i < kv.size(); i++) {
+        if (i == 0 || kv[i].first != kv[i - 1].first) {
+            kptr.push_back((int)i);
+            keys.push_back(kv[i].first);
+        }
+        kloc[i] = kv[i].second;
+    }
+    kptr.push_back((int)kv.size());
+    cudaStream_t st = h->stream;
+    h->cnb = nb;
+    h->cnkeys = (int)keys.size();
+    h->d_cbox.upload(box, st);
+    h->d_ccells.upload(cells, st);
+    h->d_ckptr.upload(kptr, st);
+    h->d_ckloc.upload(kloc, st);
+    h->d_ckeys.upload(keys, st);
+    const long long n = 3LL * nb;
+    h->d_cblk.alloc((size_t)std::max(1, h->cnkeys) * 9 * sizeof(double));
+    h->d_caug.alloc((size_t)(n * 2 * n) * sizeof(double));
+    h->d_cprow.alloc((size_t)(2 * n) * sizeof(double));
+    h->d_cfcol.alloc((size_t)n * sizeof(double));
+    int sms = 0;
+    ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    h->cpart_cap = 4 * std::max(1, sms);
+    h->d_cpart.alloc((size_t)2 * h->cpart_cap * sizeof(double));
+    h->d_cerr.alloc(sizeof(int));
+    h->d_crc.alloc((size_t)n * sizeof(double));
+    h->d_cyc.alloc((size_t)n * sizeof(double));
+    if (h->coarse_mode == 2)
+        h->d_cw.alloc((size_t)3 * N * sizeof(double));
+    else
+        h->d_cw.release();
+    h->cbox_items.clear();
+    for (int b = 0; b < nb; b++)
+        h->cbox_items.push_back(BoxItem{0, b, bptr[b], bptr[b + 1], 0, 0, h->d_ccells.as<int>()});
+    h->cgrow_items.clear();
+    for (long long r0 = 0; r0 < n; r0 += 8) h->cgrow_items.push_back(RowItem{0, (int)r0});
+    sync(h);
+    h->coarse_valid = true;
+    h->ws_m = -1;  // the system table takes the new coarse buffers
+}
+
+// A_C = R_C A R_C^T from the current values, inverted in place; ZERO_PIVOT for a singular A_C
+int coarse_numeric(asm_ctx* h) {
+    launch_coarse(h->d_ckptr.as<int>(), h->d_ckloc.as<int>(), h->d_ell_val.as<double>(), h->pat.rows_pad,
+                  h->d_cblk.as<double>(), h->cnkeys, h->stream);
+    h->d_cerr.zero(h->stream);
+    ck(launch_coarse_invert(h->d_ckeys.as<long long>(), h->d_cblk.as<double>(), h->cnkeys, h->cnb,
+                            h->d_caug.as<double>(), h->d_cprow.as<double>(), h->d_cfcol.as<double>(),
+                            h->d_cpart.as<double>(), h->cpart_cap, h->d_cerr.as<int>(), h->device, h->stream));
+    ck(cudaGetLastError());
+    int err = 0;
+    ck(cudaMemcpyAsync(&err, h->d_cerr.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    sync(h);
+    h->prof.kernel_launches += 4;
+    if (err != 0) {
+        h->err_sub = -1;
+        h->err_row = (err - 1) / 3;
+        return ASM_ERR_ZERO_PIVOT;
+    }
+    return ASM_OK;
+}
 
 // Device assembly, factorisation and packing of the current symbolic structure.
 int factor_numeric(asm_ctx* h) {
@@ -506,6 +632,14 @@ int factor_numeric(asm_ctx* h) {
         h->factored = false;
         return ASM_ERR_ZERO_PIVOT;
     }
+    if (h->coarse_mode != 0) {
+        if (!h->coarse_valid) coarse_build(h);
+        const int cs = coarse_numeric(h);
+        if (cs != ASM_OK) {
+            h->factored = false;
+            return cs;
+        }
+    }
     h->factored = true;
     return ASM_OK;
 }
@@ -519,6 +653,9 @@ struct Batch {
     std::vector<asm_ctx*> hs;
     DBuf d_tab, d_vec, d_row, d_box, d_sub, d_gather;
     int nvec = 0, nrow = 0, nbox = 0, nsub = 0, prec = 0, smem = 0, slots = 3;
+    DBuf d_cbox, d_cgrow;   // coarse-correction work items of the systems that have one
+    int ncbox = 0, ncgrow = 0;
+    bool two_stage = false;
     int coop_grid = 0;  // > 0: single system, orthogonalisation in one cooperative launch
     bool has_init = false;  // a system may be in its initial phase (serving: systems join mid-flight)
     std::vector<int> host_ctl;
@@ -545,6 +682,26 @@ void build_batch(Batch& B, cudaStream_t st) {
         }
     }
     sd = longest_first(B.hs);
+    std::vector<BoxItem> cb;
+    std::vector<RowItem> cg;
+    B.two_stage = false;
+    for (int k = 0; k < (int)B.hs.size(); k++) {
+        asm_ctx* h = B.hs[k];
+        if (h->coarse_mode == 0 || !h->coarse_valid) continue;
+        for (BoxItem b : h->cbox_items) {
+            b.sys = k;
+            cb.push_back(b);
+        }
+        for (RowItem r : h->cgrow_items) {
+            r.sys = k;
+            cg.push_back(r);
+        }
+        B.two_stage = B.two_stage || h->coarse_mode == 2;
+    }
+    B.d_cbox.upload(cb, st);
+    B.d_cgrow.upload(cg, st);
+    B.ncbox = (int)cb.size();
+    B.ncgrow = (int)cg.size();
     B.d_tab.upload(tabs, st);
     B.d_vec.upload(vi, st);
     B.d_row.upload(ri, st);
@@ -593,6 +750,8 @@ void launch_step(Batch& B, int kmax, cudaStream_t st, StepEvents* ev) {
     if (ev) ck(cudaEventRecord(ev->e[1], st));
     launch_boxsum(tab, B.d_box.as<BoxItem>(), B.nbox, st);
     launch_apply(tab, B.d_sub.as<SubDesc>(), B.nsub, B.prec, B.smem, B.slots, st);
+    launch_coarse_apply(tab, B.d_row.as<RowItem>(), B.nrow, B.d_cbox.as<BoxItem>(), B.ncbox, B.d_cgrow.as<RowItem>(),
+                        B.ncgrow, vi, B.nvec, B.two_stage, st);
     if (ev) ck(cudaEventRecord(ev->e[2], st));
     launch_post(tab, vi, B.nvec, st);
     if (ev) ck(cudaEventRecord(ev->e[3], st));
@@ -622,6 +781,8 @@ void launch_step_om(Batch& B, int kmax, cudaStream_t st, StepEvents* ev) {
     if (ev) ck(cudaEventRecord(ev->e[1], st));
     launch_boxsum(tab, B.d_box.as<BoxItem>(), B.nbox, st);
     launch_apply(tab, B.d_sub.as<SubDesc>(), B.nsub, B.prec, B.smem, B.slots, st);
+    launch_coarse_apply(tab, B.d_row.as<RowItem>(), B.nrow, B.d_cbox.as<BoxItem>(), B.ncbox, B.d_cgrow.as<RowItem>(),
+                        B.ncgrow, vi, B.nvec, B.two_stage, st);
     if (ev) {
         ck(cudaEventRecord(ev->e[2], st));
         ck(cudaEventRecord(ev->e[3], st));
@@ -1220,6 +1381,26 @@ int asm_set_partition_boxes(asm_handle h, int px, int py, int pz, int overlap, i
     return ASM_OK;
 }
 
+int asm_set_coarse_correction(asm_handle h, int mode, const int* c_box) {
+    if (!h) return ASM_ERR_INVALID_ARG;
+    if (mode < ASM_COARSE_NONE || mode > ASM_COARSE_TWO_STAGE) return ASM_ERR_INVALID_ARG;
+    int c[3] = {0, 0, 0};
+    if (c_box && (c_box[0] != 0 || c_box[1] != 0 || c_box[2] != 0)) {
+        if (c_box[0] < 1 || c_box[1] < 1 || c_box[2] < 1) return ASM_ERR_INVALID_ARG;
+        for (int d = 0; d < 3; d++) c[d] = c_box[d];
+    }
+    if (mode != ASM_COARSE_NONE) {
+        if (!h->has_grid || (c[0] == 0 && !h->has_partition)) return ASM_ERR_STATE;
+        if (coarse_box_count(h, c) > 1024) return ASM_ERR_INVALID_ARG;
+    }
+    h->coarse_mode = mode;
+    for (int d = 0; d < 3; d++) h->coarse_c[d] = c[d];
+    h->coarse_valid = false;
+    h->factored = false;
+    h->ws_m = -1;
+    return ASM_OK;
+}
+
 int asm_factor(asm_handle h) {
     if (!h) return ASM_ERR_INVALID_ARG;
     if (!h->has_matrix || !h->has_partition) return ASM_ERR_STATE;
@@ -1237,6 +1418,7 @@ int asm_factor(asm_handle h) {
             }
             upload_symbolic(h);
             h->sym_valid = true;
+            h->coarse_valid = false;
             h->ws_m = -1;
             h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         }
@@ -1257,6 +1439,11 @@ int asm_apply_precond(asm_handle h, const double* r, double* z, int on_device) {
         launch_boxsum(h->d_tab1.as<SysTab>(), h->d_box1.as<BoxItem>(), (int)h->box_items.size(), h->stream);
         launch_apply(h->d_tab1.as<SysTab>(), h->d_subdesc_single.as<SubDesc>(), (int)h->sub_desc.size(), h->prec,
                      h->no_smem ? 0 : h->apply_smem, h->apply_slots, h->stream);
+        if (h->tab.cmode != 0)
+            launch_coarse_apply(h->d_tab1.as<SysTab>(), h->d_row1.as<RowItem>(), h->n_row1,
+                                h->d_cbox_items1.as<BoxItem>(), (int)h->cbox_items.size(), h->d_cgrow1.as<RowItem>(),
+                                (int)h->cgrow_items.size(), h->d_vec1.as<VecItem>(), h->n_vec1, h->tab.cmode == 2,
+                                h->stream);
         ck(cudaGetLastError());
         h->prof.kernel_launches += 2;
         copy_out(h, z, out, bytes, on_device);

@@ -104,6 +104,14 @@ struct SysTab {
     double* boxsum;      // [n_boxes * 3] far-box sums of the apply input
     double* corr;        // [n_corr * 3] near-region sums subtracted from far-lump box sums
     int* dev_err;        // device status word: nonzero after a bounded wait expired
+    // classical coarse-grid correction (0 none, 1 two-level, 2 two-stage; Eqs. 3.5-3.8)
+    int cmode;
+    int cnb;             // coarse boxes
+    const int* cbox;     // [n_cells] coarse box of each cell
+    const double* caug;  // [3 cnb][6 cnb]: the right half holds A_C^{-1}
+    double* crc;         // [3 cnb] R_C x
+    double* cyc;         // [3 cnb] A_C^{-1} R_C x
+    double* cw;          // [3 n_cells] two-stage residual r - A z
 };
 
 // Work items
@@ -207,6 +215,15 @@ void launch_finish(const SysTab* tab, const VecItem* items, int nitems, cudaStre
 // initial systems and ||b - A x|| of finishing ones), then x += alpha p, r -= alpha q.
 void launch_om(const SysTab* tab, const VecItem* items, int nitems, int l, cudaStream_t st);
 void launch_om_update(const SysTab* tab, const VecItem* items, int nitems, cudaStream_t st);
+// Coarse-grid correction: [A_C | I] from the box-pair blocks, then in-place Gauss-Jordan (one
+// cooperative launch; *err = 1 + column of a zero pivot); and the per-apply kernels
+// (two-stage residual, R_C, A_C^{-1} product, R_C^T added to the apply output).
+cudaError_t launch_coarse_invert(const long long* keys, const double* blocks, int nkeys, int nb, double* aug,
+                                 double* prow, double* fcol, double* part, int part_cap, int* err, int device,
+                                 cudaStream_t st);
+void launch_coarse_apply(const SysTab* tab, const RowItem* rows, int nrows, const BoxItem* boxes, int nboxes,
+                         const RowItem* grows, int ngrows, const VecItem* vecs, int nvecs, bool two_stage,
+                         cudaStream_t st);
 // Whole Gram-Schmidt + state step of a single system in one cooperative launch (grid <= the
 // co-resident limit from ortho_coop_grid); part2 holds 4 * nchunk doubles.
 int ortho_coop_grid(int device);
