@@ -61,7 +61,11 @@ typedef enum { ASM_KRYLOV_GMRES = 0, ASM_KRYLOV_ORTHOMIN = 1 } asm_krylov;
 
 typedef enum {
     ASM_LOCAL_BILU0_COLSUM = 0, /* block ILU(0) with column-sum compensation (default) */
-    ASM_LOCAL_BILU0 = 1         /* plain block ILU(0): dropped fill is discarded */
+    ASM_LOCAL_BILU0 = 1,        /* plain block ILU(0): dropped fill is discarded */
+    ASM_LOCAL_EXACT = 2         /* exact local solves A_i^{-1} (Section 5: the paper's own setting,
+                                   Gaussian elimination): every A_i is inverted at asm_factor by
+                                   Gauss-Jordan elimination with partial pivoting (FP64 only; at most
+                                   4096 local block rows; (3 n_i)^2 * 16 bytes of device memory each) */
 } asm_local_solver;
 
 typedef enum {

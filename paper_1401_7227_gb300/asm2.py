@@ -181,7 +181,7 @@ class Solver:
         L.asm_default_options(C.byref(o))
         o.precision = PREC[precision]
         o.restart = restart
-        o.local_solver = {"colsum": 0, "plain": 1}[local_solver]
+        o.local_solver = {"colsum": 0, "plain": 1, "exact": 2}[local_solver]
         o.flexible = flexible
         o.device = device
         o.krylov = {"gmres": 0, "orthomin": 1}[krylov]

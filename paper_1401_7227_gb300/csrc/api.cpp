@@ -107,13 +107,18 @@ struct asm_ctx {
     bool no_coop = false;  // per-kernel orthogonalisation path instead of the cooperative one
     bool no_smem = false;  // local vectors of the apply in device memory
     asm_profile_info prof{};
+    // exact local solves (local_solver = ASM_LOCAL_EXACT): [A_i | I] inverted in place per subdomain
+    DBuf d_daug, d_dprow, d_dfcol, d_dmats, d_dinit, d_doff, d_dmat_of_slot, d_dpart, d_derr, d_ditems1;
+    std::vector<long long> daug_base;            // offset of each subdomain's augmented matrix
+    std::vector<std::vector<int>> drow_of_q;     // local row of each dense block row (error location)
+    int n_dinit = 0, n_ditems1 = 0, dpart_cap = 0, dmax3 = 0;
     // classical coarse-grid correction (Eqs. 3.5-3.8)
     int coarse_mode = 0;
     int coarse_c[3] = {0, 0, 0};  // {0,0,0}: partition boxes
     bool coarse_valid = false;    // coarse structure built for the current grid, partition, pattern
     int cnb = 0, cnkeys = 0, cpart_cap = 0;
     DBuf d_cbox, d_ccells, d_ckptr, d_ckloc, d_ckeys, d_cblk, d_caug, d_cprow, d_cfcol, d_cpart, d_cerr, d_crc, d_cyc,
-        d_cw, d_cbox_items1, d_cgrow1;
+        d_cw, d_cbox_items1, d_cgrow1, d_cmat;
     std::vector<BoxItem> cbox_items;   // sys = 0: cells of each coarse box
     std::vector<RowItem> cgrow_items;  // sys = 0: 8 rows of A_C^{-1} each
     // diagnostics
@@ -158,6 +163,14 @@ void fill_ell(asm_ctx* h, const double* vals, int on_device) {
     if (!on_device) sync(h);
 }
 
+// Exact-local-solve work items of an ordered subdomain list: (item index, first of 8 owned rows)
+std::vector<int2> dense_items(const std::vector<SubDesc>& sd) {
+    std::vector<int2> it;
+    for (int i = 0; i < (int)sd.size(); i++)
+        for (int q = 0; q < 3 * sd[i].n_own; q += 8) it.push_back(make_int2(i, q));
+    return it;
+}
+
 // Subdomain work items of several systems, most expensive first (the order of the CTAs of the
 // apply launch; every CTA writes only its own subdomain's owned rows, so the order does not
 // change any result)
@@ -177,6 +190,73 @@ std::vector<SubDesc> longest_first(const std::vector<asm_ctx*>& hs) {
 }
 
 // Upload the symbolic structure and build the per-subdomain descriptors.
+// Exact local solves: per subdomain an augmented [A_i | I] (3n x 6n) in fine-index-then-lump-index
+// order, the scatter offsets of the assembled slots into it, and the Gauss-Jordan descriptors.
+void upload_dense(asm_ctx* h, cudaStream_t st) {
+    const SysSym& S = *h->sym;
+    const int K = (int)S.subs.size();
+    h->daug_base.assign(K + 1, 0);
+    h->drow_of_q.assign(K, {});
+    std::vector<long long> pbase(K + 1, 0), fbase(K + 1, 0);
+    int nmax3 = 0;
+    for (int s = 0; s < K; s++) {
+        const SubSym& o = S.subs[s];
+        if (o.n > 4096) throw CudaFail{ASM_ERR_INVALID_ARG};
+        const long long n3 = 3LL * o.n;
+        h->daug_base[s + 1] = h->daug_base[s] + n3 * 2 * n3;
+        pbase[s + 1] = pbase[s] + 2 * n3;
+        fbase[s + 1] = fbase[s] + n3;
+        nmax3 = std::max(nmax3, (int)n3);
+    }
+    h->dmax3 = nmax3;
+    h->d_daug.alloc((size_t)h->daug_base[K] * sizeof(double));
+    h->d_dprow.alloc((size_t)pbase[K] * sizeof(double));
+    h->d_dfcol.alloc((size_t)fbase[K] * sizeof(double));
+    std::vector<GJMat> mats(K);
+    std::vector<int2> init;
+    std::vector<long long> off;
+    std::vector<int> mat_of_slot;
+    off.reserve(h->total_slots);
+    mat_of_slot.reserve(h->total_slots);
+    for (int s = 0; s < K; s++) {
+        const SubSym& o = S.subs[s];
+        const int n3 = 3 * o.n;
+        mats[s] = GJMat{h->d_daug.as<double>() + h->daug_base[s], n3, h->d_dprow.as<double>() + pbase[s],
+                        h->d_dfcol.as<double>() + fbase[s]};
+        for (int r = 0; r < n3; r++) init.push_back(make_int2(s, r));
+        std::vector<int> q(o.n);
+        h->drow_of_q[s].assign(o.n, 0);
+        for (int p = 0; p < o.n; p++) {
+            q[p] = p < o.nf ? o.fidx_of_row[p] : o.nf + o.cidx_of_row[p];
+            h->drow_of_q[s][q[p]] = p;
+        }
+        // offset of the slot's (0,0) element within its own augmented matrix (row stride 2 n3); the
+        // scatter adds rows 0..2 and columns 0..2, all inside the left half
+        for (int p = 0; p < o.n; p++)
+            for (int t = o.prp[p]; t < o.prp[p + 1]; t++) {
+                const long long o0 = 3LL * q[p] * 2 * n3 + 3LL * q[o.pci[t]];
+                if (q[p] < 0 || q[p] >= o.n || q[o.pci[t]] < 0 || q[o.pci[t]] >= o.n ||
+                    o0 + 2LL * 2 * n3 + 2 >= (long long)n3 * 2 * n3)
+                    throw CudaFail{ASM_ERR_INVALID_ARG};
+                off.push_back(o0);
+                mat_of_slot.push_back(s);
+            }
+        h->sub_desc[s].dinv = h->d_daug.as<double>() + h->daug_base[s];
+    }
+    if ((long long)off.size() != h->total_slots) throw CudaFail{ASM_ERR_INVALID_ARG};
+    h->d_dmats.upload(mats, st);
+    h->d_dinit.upload(init, st);
+    h->n_dinit = (int)init.size();
+    h->d_doff.upload(off, st);
+    h->d_dmat_of_slot.upload(mat_of_slot, st);
+    int sms = 0;
+    ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    h->dpart_cap = 4 * std::max(1, sms);
+    h->d_dpart.alloc((size_t)2 * h->dpart_cap * sizeof(double));
+    h->d_derr.alloc((size_t)std::max(1, K) * sizeof(int));
+    sync(h);
+}
+
 void upload_symbolic(asm_ctx* h) {
     SysSym& S = *h->sym;
     cudaStream_t st = h->stream;
@@ -347,6 +427,7 @@ void upload_symbolic(asm_ctx* h) {
         if (!rl.empty()) ck(cudaMemcpyAsync(base, rl.data(), rl.size() * 4, cudaMemcpyHostToDevice, st));
         sync(h);
     }
+    if (h->opt.local_solver == ASM_LOCAL_EXACT) upload_dense(h, st);
     h->pk_nf = (long long)offf.size();
     h->pk_nc = (long long)offc.size();
     h->d_pk_off_f.upload(offf, st);
@@ -391,7 +472,13 @@ void upload_symbolic(asm_ctx* h) {
         h->apply_slots = 3;
     }
     // most expensive subdomains first: the CTAs of the last wave are then the short ones
-    h->d_subdesc_single.upload(longest_first({h}), st);
+    {
+        const std::vector<SubDesc> ordered = longest_first({h});
+        h->d_subdesc_single.upload(ordered, st);
+        const std::vector<int2> di = dense_items(ordered);
+        h->d_ditems1.upload(di, st);
+        h->n_ditems1 = (int)di.size();
+    }
     h->d_err.alloc(sizeof(FactErr));
     sync(h);
 }
@@ -559,6 +646,10 @@ void coarse_build(asm_ctx* h) {
     h->cpart_cap = 4 * std::max(1, sms);
     h->d_cpart.alloc((size_t)2 * h->cpart_cap * sizeof(double));
     h->d_cerr.alloc(sizeof(int));
+    {
+        std::vector<GJMat> m{GJMat{h->d_caug.as<double>(), (int)n, h->d_cprow.as<double>(), h->d_cfcol.as<double>()}};
+        h->d_cmat.upload(m, st);
+    }
     h->d_crc.alloc((size_t)n * sizeof(double));
     h->d_cyc.alloc((size_t)n * sizeof(double));
     if (h->coarse_mode == 2)
@@ -581,8 +672,8 @@ int coarse_numeric(asm_ctx* h) {
                   h->d_cblk.as<double>(), h->cnkeys, h->stream);
     h->d_cerr.zero(h->stream);
     ck(launch_coarse_invert(h->d_ckeys.as<long long>(), h->d_cblk.as<double>(), h->cnkeys, h->cnb,
-                            h->d_caug.as<double>(), h->d_cprow.as<double>(), h->d_cfcol.as<double>(),
-                            h->d_cpart.as<double>(), h->cpart_cap, h->d_cerr.as<int>(), h->device, h->stream));
+                            h->d_caug.as<double>(), h->d_cmat.as<GJMat>(), h->d_cpart.as<double>(), h->cpart_cap,
+                            h->d_cerr.as<int>(), h->device, h->stream));
     ck(cudaGetLastError());
     int err = 0;
     ck(cudaMemcpyAsync(&err, h->d_cerr.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -609,16 +700,39 @@ int factor_numeric(asm_ctx* h) {
     launch_assemble(h->d_aptr.as<int>(), h->d_aloc.as<int>(), h->d_acs.as<int>(), h->d_ell_val.as<double>(),
                     h->pat.rows_pad, h->d_cval.as<double>(), h->d_slot.as<double>(), h->total_slots, h->stream);
     h->d_err.zero(h->stream);
-    launch_factor(h->d_factdesc.as<FactDesc>(), (int)S.subs.size(), h->d_err.as<FactErr>(), nullptr, h->stream);
-    launch_pack(h->d_pk_off_f.as<long long>(), h->d_pk_src_f.as<int>(), h->pk_nf, h->prec,
-                h->d_stream.as<unsigned char>(), h->d_slot.as<double>(), h->stream);
-    launch_pack(h->d_pk_off_c.as<long long>(), h->d_pk_src_c.as<int>(), h->pk_nc, 0, h->d_stream.as<unsigned char>(),
-                h->d_slot.as<double>(), h->stream);
+    const bool exact = h->opt.local_solver == ASM_LOCAL_EXACT;
+    if (exact) {
+        const int K = (int)S.subs.size();
+        launch_gj_init(h->d_dmats.as<GJMat>(), h->d_dinit.as<int2>(), h->n_dinit, h->stream);
+        launch_dense_scatter(h->d_slot.as<double>(), h->d_doff.as<long long>(), h->d_dmat_of_slot.as<int>(),
+                             h->d_dmats.as<GJMat>(), h->total_slots, h->stream);
+        h->d_derr.zero(h->stream);
+        ck(launch_gj_run(h->d_dmats.as<GJMat>(), K, h->dmax3, h->d_dpart.as<double>(), h->dpart_cap,
+                         h->d_derr.as<int>(), h->device, h->stream));
+    } else {
+        launch_factor(h->d_factdesc.as<FactDesc>(), (int)S.subs.size(), h->d_err.as<FactErr>(), nullptr, h->stream);
+        launch_pack(h->d_pk_off_f.as<long long>(), h->d_pk_src_f.as<int>(), h->pk_nf, h->prec,
+                    h->d_stream.as<unsigned char>(), h->d_slot.as<double>(), h->stream);
+        launch_pack(h->d_pk_off_c.as<long long>(), h->d_pk_src_c.as<int>(), h->pk_nc, 0,
+                    h->d_stream.as<unsigned char>(), h->d_slot.as<double>(), h->stream);
+    }
     ck(cudaGetLastError());
     ck(cudaEventRecord(e1, h->stream));
     FactErr fe;
     ck(cudaMemcpyAsync(&fe, h->d_err.p, sizeof(fe), cudaMemcpyDeviceToHost, h->stream));
+    std::vector<int> derr;
+    if (exact) {
+        derr.assign(S.subs.size(), 0);
+        ck(cudaMemcpyAsync(derr.data(), h->d_derr.p, derr.size() * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    }
     sync(h);
+    for (size_t s = 0; s < derr.size(); s++)
+        if (derr[s] != 0) {  // the first singular local matrix, its local block row
+            fe.flag = 1;
+            fe.sub = (int)s;
+            fe.row = h->drow_of_q[s][(derr[s] - 1) / 3];
+            break;
+        }
     float ms = 0;
     ck(cudaEventElapsedTime(&ms, e0, e1));
     cudaEventDestroy(e0);
@@ -653,6 +767,9 @@ struct Batch {
     std::vector<asm_ctx*> hs;
     DBuf d_tab, d_vec, d_row, d_box, d_sub, d_gather;
     int nvec = 0, nrow = 0, nbox = 0, nsub = 0, prec = 0, smem = 0, slots = 3;
+    DBuf d_dense;           // exact local solves: (subdomain item, first owned row of 8)
+    int ndense = 0;
+    bool exact = false;     // every system of the batch has exact local solves
     DBuf d_cbox, d_cgrow;   // coarse-correction work items of the systems that have one
     int ncbox = 0, ncgrow = 0;
     bool two_stage = false;
@@ -682,6 +799,12 @@ void build_batch(Batch& B, cudaStream_t st) {
         }
     }
     sd = longest_first(B.hs);
+    B.exact = !B.hs.empty() && B.hs[0]->opt.local_solver == ASM_LOCAL_EXACT;
+    if (B.exact) {
+        const std::vector<int2> di = dense_items(sd);
+        B.d_dense.upload(di, st);
+        B.ndense = (int)di.size();
+    }
     std::vector<BoxItem> cb;
     std::vector<RowItem> cg;
     B.two_stage = false;
@@ -741,6 +864,16 @@ struct StepEvents {
     }
 };
 
+// the local solves of one apply: fused ILU sweeps, or R_i r and the owned rows of A_i^{-1} R_i r
+void launch_local_solves(Batch& B, const SysTab* tab, cudaStream_t st) {
+    if (B.exact) {
+        launch_dense_restrict(tab, B.d_sub.as<SubDesc>(), B.nsub, st);
+        launch_dense_apply(tab, B.d_sub.as<SubDesc>(), B.d_dense.as<int2>(), B.ndense, st);
+    } else {
+        launch_apply(tab, B.d_sub.as<SubDesc>(), B.nsub, B.prec, B.smem, B.slots, st);
+    }
+}
+
 void launch_step(Batch& B, int kmax, cudaStream_t st, StepEvents* ev) {
     const SysTab* tab = B.d_tab.as<SysTab>();
     const VecItem* vi = B.d_vec.as<VecItem>();
@@ -749,7 +882,7 @@ void launch_step(Batch& B, int kmax, cudaStream_t st, StepEvents* ev) {
     launch_prep(tab, vi, B.nvec, st);
     if (ev) ck(cudaEventRecord(ev->e[1], st));
     launch_boxsum(tab, B.d_box.as<BoxItem>(), B.nbox, st);
-    launch_apply(tab, B.d_sub.as<SubDesc>(), B.nsub, B.prec, B.smem, B.slots, st);
+    launch_local_solves(B, tab, st);
     launch_coarse_apply(tab, B.d_row.as<RowItem>(), B.nrow, B.d_cbox.as<BoxItem>(), B.ncbox, B.d_cgrow.as<RowItem>(),
                         B.ncgrow, vi, B.nvec, B.two_stage, st);
     if (ev) ck(cudaEventRecord(ev->e[2], st));
@@ -780,7 +913,7 @@ void launch_step_om(Batch& B, int kmax, cudaStream_t st, StepEvents* ev) {
     if (B.has_init) launch_init(tab, vi, B.nvec, st);
     if (ev) ck(cudaEventRecord(ev->e[1], st));
     launch_boxsum(tab, B.d_box.as<BoxItem>(), B.nbox, st);
-    launch_apply(tab, B.d_sub.as<SubDesc>(), B.nsub, B.prec, B.smem, B.slots, st);
+    launch_local_solves(B, tab, st);
     launch_coarse_apply(tab, B.d_row.as<RowItem>(), B.nrow, B.d_cbox.as<BoxItem>(), B.ncbox, B.d_cgrow.as<RowItem>(),
                         B.ncgrow, vi, B.nvec, B.two_stage, st);
     if (ev) {
@@ -1265,7 +1398,8 @@ int asm_create(asm_handle* out, const asm_options* opt, void* cuda_stream) {
     asm_default_options(&o);
     if (opt) o = *opt;
     if (o.precision < 0 || o.precision > 2 || o.krylov < 0 || o.krylov > 1 || o.restart < 1 || o.restart > 512 ||
-        o.local_solver < 0 || o.local_solver > 1 || o.flexible < -1 || o.flexible > 1)
+        o.local_solver < 0 || o.local_solver > 2 || o.flexible < -1 || o.flexible > 1 ||
+        (o.local_solver == ASM_LOCAL_EXACT && o.precision != ASM_PREC_FP64))
         return ASM_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
@@ -1437,8 +1571,15 @@ int asm_apply_precond(asm_handle h, const double* r, double* z, int on_device) {
         copy_in(h, in, r, bytes, on_device);
         set_ctl(h, VU, VZ, -1, -1, -1);
         launch_boxsum(h->d_tab1.as<SysTab>(), h->d_box1.as<BoxItem>(), (int)h->box_items.size(), h->stream);
-        launch_apply(h->d_tab1.as<SysTab>(), h->d_subdesc_single.as<SubDesc>(), (int)h->sub_desc.size(), h->prec,
-                     h->no_smem ? 0 : h->apply_smem, h->apply_slots, h->stream);
+        if (h->opt.local_solver == ASM_LOCAL_EXACT) {
+            launch_dense_restrict(h->d_tab1.as<SysTab>(), h->d_subdesc_single.as<SubDesc>(), (int)h->sub_desc.size(),
+                                  h->stream);
+            launch_dense_apply(h->d_tab1.as<SysTab>(), h->d_subdesc_single.as<SubDesc>(), h->d_ditems1.as<int2>(),
+                               h->n_ditems1, h->stream);
+        } else {
+            launch_apply(h->d_tab1.as<SysTab>(), h->d_subdesc_single.as<SubDesc>(), (int)h->sub_desc.size(), h->prec,
+                         h->no_smem ? 0 : h->apply_smem, h->apply_slots, h->stream);
+        }
         if (h->tab.cmode != 0)
             launch_coarse_apply(h->d_tab1.as<SysTab>(), h->d_row1.as<RowItem>(), h->n_row1,
                                 h->d_cbox_items1.as<BoxItem>(), (int)h->cbox_items.size(), h->d_cgrow1.as<RowItem>(),
@@ -1496,7 +1637,8 @@ int asm_solve_batch(asm_handle* hs, int n, const double* const* b, double* const
         if (!h) return ASM_ERR_INVALID_ARG;
         if (!h->factored) return ASM_ERR_STATE;
         if (h->device != v[0]->device || h->stream != v[0]->stream || h->prec != v[0]->prec ||
-            h->opt.krylov != v[0]->opt.krylov)
+            h->opt.krylov != v[0]->opt.krylov ||
+            (h->opt.local_solver == ASM_LOCAL_EXACT) != (v[0]->opt.local_solver == ASM_LOCAL_EXACT))
             return ASM_ERR_INVALID_ARG;
     }
     for (int i = 0; i < n; i++)
@@ -1627,6 +1769,7 @@ int asm_get_local_matrix(asm_handle h, int s, int* row_ptr, int* col_idx, double
 
 int asm_get_local_factors(asm_handle h, int s, double* lu, double* dpiv) {
     if (!h || !h->sym_valid || s < 0 || s >= (int)h->sym->subs.size()) return ASM_ERR_INVALID_ARG;
+    if (h->opt.local_solver == ASM_LOCAL_EXACT) return ASM_ERR_INVALID_ARG;  // no ILU factors
     if (!h->factored) return ASM_ERR_STATE;
     const SubSym& o = h->sym->subs[s];
     return guard(h, [&]() -> int {

@@ -147,6 +147,7 @@ struct SubDesc {
     int n_own;
     int n_long;       // lump rows restricted by a whole warp
     int corr0;        // first correction sum of this subdomain in SysTab::corr
+    const double* dinv;          // exact local solves: [A_i | A_i^{-1}] (3n x 6n), fine then lump order
     const int2* chunks;          // (byte offset, bytes) of every chunk, consumption order
     const unsigned char* stream; // 16-byte aligned
     double* y;        // global scratch for the local vectors when they do not fit in shared memory
@@ -213,14 +214,32 @@ void launch_mgs(const SysTab* tab, const VecItem* items, int nitems, int k, cuda
 void launch_finish(const SysTab* tab, const VecItem* items, int nitems, cudaStream_t st);
 // ORTHOMIN(k): projection pass l of the direction in progress (l = 0 also reduces ||r|| of
 // initial systems and ||b - A x|| of finishing ones), then x += alpha p, r -= alpha q.
+// Dense matrices inverted in place by Gauss-Jordan elimination with partial pivoting: aug = [A | I]
+// (n x 2n, row-major), prow / fcol scratch of 2n / n doubles.
+struct GJMat {
+    double* aug;
+    int n;
+    double* prow;
+    double* fcol;
+};
+void launch_gj_init(const GJMat* mats, const int2* rows, int nrows, cudaStream_t st);
+// one cooperative launch; err[m] = 1 + pivot column of a singular matrix m (else untouched)
+cudaError_t launch_gj_run(const GJMat* mats, int nmat, int nmax, double* part, int part_cap, int* err, int device,
+                          cudaStream_t st);
+void launch_dense_scatter(const double* slot, const long long* off, const int* mat_of_slot, const GJMat* mats,
+                          long long nslot, cudaStream_t st);
+// exact local solves: R_i r (one CTA per subdomain), then the owned rows of A_i^{-1} R_i r
+// (items: (subdomain work item, first of 8 owned rows)) written to the apply output
+void launch_dense_restrict(const SysTab* tab, const SubDesc* subs, int nsub, cudaStream_t st);
+void launch_dense_apply(const SysTab* tab, const SubDesc* subs, const int2* items, int nitems, cudaStream_t st);
 void launch_om(const SysTab* tab, const VecItem* items, int nitems, int l, cudaStream_t st);
 void launch_om_update(const SysTab* tab, const VecItem* items, int nitems, cudaStream_t st);
 // Coarse-grid correction: [A_C | I] from the box-pair blocks, then in-place Gauss-Jordan (one
 // cooperative launch; *err = 1 + column of a zero pivot); and the per-apply kernels
 // (two-stage residual, R_C, A_C^{-1} product, R_C^T added to the apply output).
+struct GJMat;
 cudaError_t launch_coarse_invert(const long long* keys, const double* blocks, int nkeys, int nb, double* aug,
-                                 double* prow, double* fcol, double* part, int part_cap, int* err, int device,
-                                 cudaStream_t st);
+                                 const GJMat* mat, double* part, int part_cap, int* err, int device, cudaStream_t st);
 void launch_coarse_apply(const SysTab* tab, const RowItem* rows, int nrows, const BoxItem* boxes, int nboxes,
                          const RowItem* grows, int ngrows, const VecItem* vecs, int nvecs, bool two_stage,
                          cudaStream_t st);

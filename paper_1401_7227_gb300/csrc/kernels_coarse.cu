@@ -4,9 +4,8 @@
 //   two-stage:  z = B_AS^{-1} r + R_C^T A_C^{-1} R_C (r - A B_AS^{-1} r)     (Eqs. 3.7-3.8)
 // R_C sums the 3-vectors of each coarse box's cells, R_C^T copies a box's value to its cells and
 // A_C = R_C A R_C^T (Eq. 3.6).  A_C is small (3 unknowns per coarse box), so it is inverted once
-// per factorisation (Gauss-Jordan elimination with partial pivoting, FP64) and applied as a
-// dense matrix-vector product.
-#include <cooperative_groups.h>
+// per factorisation (Gauss-Jordan elimination with partial pivoting, FP64, kernels_dense.cu) and
+// applied as a dense matrix-vector product.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,108 +34,6 @@ __global__ void k_coarse_scatter(const long long* __restrict__ keys, const doubl
     const long long I = keys[q] / nb, J = keys[q] - (keys[q] / nb) * nb;
     const long long n = 3LL * nb;
     aug[(3 * I + e / 3) * 2 * n + 3 * J + e % 3] = blocks[9 * q + e];
-}
-
-// Gauss-Jordan elimination with partial pivoting on [A_C | I], in place, one cooperative launch:
-// per pivot column k, (A) each CTA finds the largest |a(i,k)|, i >= k, of its rows; (B) every CTA
-// reduces those in the same order (ties: lowest row), and the pivot row scaled by 1/pivot and the
-// column multipliers are saved; (C) every row is updated (rows k and p exchanged on the way).
-// The right half then holds A_C^{-1}.  A zero pivot column sets *err = 1 + k and stops.
-__global__ void __launch_bounds__(256) k_coarse_gj(double* __restrict__ aug, int n, double* __restrict__ prow,
-                                                   double* __restrict__ fcol, double* __restrict__ part,
-                                                   int* __restrict__ err) {
-    namespace cg = cooperative_groups;
-    cg::grid_group grid = cg::this_grid();
-    const long long W = 2LL * n;
-    const int G = gridDim.x;
-    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long gstride = (long long)G * blockDim.x;
-    __shared__ double sval[256];
-    __shared__ int sidx[256];
-    __shared__ int piv_row;
-    __shared__ double piv_val;
-    for (int k = 0; k < n; k++) {
-        // (A) partial pivot search over rows k .. n-1
-        double best = -1.0;
-        int bi = n;
-        for (long long i = k + gtid; i < n; i += gstride) {
-            const double a = fabs(aug[i * W + k]);
-            if (a > best) {
-                best = a;
-                bi = (int)i;
-            }
-        }
-        sval[threadIdx.x] = best;
-        sidx[threadIdx.x] = bi;
-        __syncthreads();
-        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-            if ((int)threadIdx.x < s) {
-                const double o = sval[threadIdx.x + s];
-                const int oi = sidx[threadIdx.x + s];
-                if (o > sval[threadIdx.x] || (o == sval[threadIdx.x] && oi < sidx[threadIdx.x])) {
-                    sval[threadIdx.x] = o;
-                    sidx[threadIdx.x] = oi;
-                }
-            }
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            part[2 * blockIdx.x] = sval[0];
-            part[2 * blockIdx.x + 1] = (double)sidx[0];
-        }
-        grid.sync();
-        // (B) every CTA reduces the partials in the same order
-        if (threadIdx.x == 0) {
-            double b = -1.0;
-            int p = n;
-            for (int c = 0; c < G; c++) {
-                const double v = __ldcg(&part[2 * c]);
-                const int vi = (int)__ldcg(&part[2 * c + 1]);
-                if (v > b || (v == b && vi < p)) {
-                    b = v;
-                    p = vi;
-                }
-            }
-            piv_row = p;
-            piv_val = (p < n) ? __ldcg(&aug[(long long)p * W + k]) : 0.0;
-        }
-        __syncthreads();
-        const int p = piv_row;
-        const double pv = piv_val;
-        if (p >= n || pv == 0.0) {
-            if (gtid == 0) *err = 1 + k;
-            return;  // every CTA takes this branch: the partials are the same for all
-        }
-        const double inv = 1.0 / pv;
-        for (long long j = gtid; j < W; j += gstride) prow[j] = aug[(long long)p * W + j] * inv;
-        for (long long i = gtid; i < n; i += gstride) {
-            // multiplier of row i after rows k and p are exchanged
-            const long long src = (i == k) ? p : (i == p ? k : i);
-            fcol[i] = (i == k) ? 0.0 : aug[src * W + k];
-        }
-        grid.sync();
-        // (C) row k <- scaled pivot row; row p <- old row k minus its multiple; others in place
-        const long long total = (long long)n * W;
-        for (long long t = gtid; t < total; t += gstride) {
-            const long long i = t / W, j = t - i * W;
-            if (i == p && p != k) continue;  // handled together with row k
-            const double pj = prow[j];
-            if (i == k) {
-                if (p != k) {
-                    const double old_k = aug[(long long)k * W + j];
-                    aug[(long long)p * W + j] = (j == k) ? 0.0 : old_k - fcol[p] * pj;
-                }
-                aug[(long long)k * W + j] = pj;
-            } else {
-                const double f = fcol[i];
-                if (j == k)
-                    aug[i * W + j] = 0.0;
-                else if (f != 0.0 && pj != 0.0)
-                    aug[i * W + j] -= f * pj;
-            }
-        }
-        grid.sync();
-    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -234,20 +131,12 @@ __global__ void __launch_bounds__(VEC_THREADS) k_coarse_prolong(const SysTab* __
 }  // namespace
 
 cudaError_t launch_coarse_invert(const long long* keys, const double* blocks, int nkeys, int nb, double* aug,
-                                 double* prow, double* fcol, double* part, int part_cap, int* err, int device,
-                                 cudaStream_t st) {
+                                 const GJMat* mat, double* part, int part_cap, int* err, int device, cudaStream_t st) {
     const long long n = 3LL * nb;
     const long long tot = n * 2 * n;
     k_coarse_init<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, aug);
     if (nkeys > 0) k_coarse_scatter<<<(unsigned)((9LL * nkeys + 255) / 256), 256, 0, st>>>(keys, blocks, nkeys, nb, aug);
-    int per_sm = 0, sms = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_gj, 256, 0);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    int grid = std::min(std::max(1, per_sm), 2) * std::max(1, sms);
-    grid = std::min(grid, part_cap);
-    int ni = (int)n;
-    void* args[] = {(void*)&aug, (void*)&ni, (void*)&prow, (void*)&fcol, (void*)&part, (void*)&err};
-    return cudaLaunchCooperativeKernel((const void*)k_coarse_gj, dim3(grid), dim3(256), args, 0, st);
+    return launch_gj_run(mat, 1, (int)n, part, part_cap, err, device, st);
 }
 
 void launch_coarse_apply(const SysTab* tab, const RowItem* rows, int nrows, const BoxItem* boxes, int nboxes,

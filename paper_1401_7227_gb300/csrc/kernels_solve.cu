@@ -364,46 +364,14 @@ __device__ __forceinline__ void sweep_chunk(const unsigned char* base, bool lowe
     }
 }
 
-// Fused local solve of one subdomain (one CTA): y = R_i r; y = L^{-1} y; y = U^{-1} y;
-// z[owned cells] = y[owned fine rows] (Eqs. 4.2-4.5).  Thread 0 streams the factor chunks
-// (front to back) into a ring of shared-memory slots with TMA bulk copies; all threads compute
-// from shared memory, one chunk at a time, with a CTA barrier after each chunk (which also orders
-// the wavefront levels).  Fine rows and lump rows live in separate local vectors (fine rows at the
-// factor precision, lumps in FP64), in shared memory when they fit.
-template <typename TF, bool SMEM_Y>
-__global__ void __launch_bounds__(256, 2) k_apply(const SysTab* __restrict__ tab, const SubDesc* __restrict__ subs,
-                                                   int slots) {
-    using TC = typename Compute<TF>::T;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    const SubDesc sd = subs[blockIdx.x];
-    const SysTab& st = tab[sd.sys];
-    const int in = st.ctl[C_APPLY_IN];
-    if (in < 0) return;
-    const int out = st.ctl[C_APPLY_OUT];
-    const double* __restrict__ r = st.ws + (long long)in * st.n3p;
-    double* __restrict__ z = st.ws + (long long)out * st.n3p;
-    unsigned char* ring = smem_raw;
-    const int ring_bytes = slots * kStreamChunk;
-    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + ring_bytes);
-    double* yc = SMEM_Y ? reinterpret_cast<double*>(smem_raw + ring_bytes + kRingHeader) : sd.y;
-    TC* yf = reinterpret_cast<TC*>(yc + 3 * sd.nc);
-    TC* ycf = sizeof(TC) == 8 ? nullptr : yf + 3 * sd.nf;  // FP32 mirror of the lump values
+// R_i r (Eqs. 4.1, B.2): fine entries copied from their cells (as TC), lump entries summed over
+// the lump's cells in FP64 -- far lumps as the far box's sum minus its near-region cells, long
+// lists by a whole warp.  The caller synchronises the CTA afterwards.
+template <typename TC>
+__device__ __forceinline__ void restrict_local(const SysTab& st, const SubDesc& sd, const double* __restrict__ r,
+                                               TC* yf, double* yc) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
-
-    if (tid == 0) {
-        for (int k = 0; k < slots; k++) mbar_init(&bar[k], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    if (tid == 0)
-        for (int k = 0; k < slots && k < sd.n_chunks; k++) {
-            const int2 ch = sd.chunks[k];
-            mbar_expect_tx(&bar[k], (unsigned)ch.y);
-            bulk_load(ring + (size_t)k * kStreamChunk, sd.stream + ch.x, (unsigned)ch.y, &bar[k]);
-        }
-
-    // restriction R_i r (overlaps the first chunk copies)
 #pragma unroll 4
     for (int f = tid; f < sd.nf; f += nt) {
         const double* rc = r + 3LL * sd.fcell[f];
@@ -455,6 +423,49 @@ __global__ void __launch_bounds__(256, 2) k_apply(const SysTab* __restrict__ tab
             yc[3 * c + 2] = a2;
         }
     }
+}
+
+// Fused local solve of one subdomain (one CTA): y = R_i r; y = L^{-1} y; y = U^{-1} y;
+// z[owned cells] = y[owned fine rows] (Eqs. 4.2-4.5).  Thread 0 streams the factor chunks
+// (front to back) into a ring of shared-memory slots with TMA bulk copies; all threads compute
+// from shared memory, one chunk at a time, with a CTA barrier after each chunk (which also orders
+// the wavefront levels).  Fine rows and lump rows live in separate local vectors (fine rows at the
+// factor precision, lumps in FP64), in shared memory when they fit.
+template <typename TF, bool SMEM_Y>
+__global__ void __launch_bounds__(256, 2) k_apply(const SysTab* __restrict__ tab, const SubDesc* __restrict__ subs,
+                                                   int slots) {
+    using TC = typename Compute<TF>::T;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const SubDesc sd = subs[blockIdx.x];
+    const SysTab& st = tab[sd.sys];
+    const int in = st.ctl[C_APPLY_IN];
+    if (in < 0) return;
+    const int out = st.ctl[C_APPLY_OUT];
+    const double* __restrict__ r = st.ws + (long long)in * st.n3p;
+    double* __restrict__ z = st.ws + (long long)out * st.n3p;
+    unsigned char* ring = smem_raw;
+    const int ring_bytes = slots * kStreamChunk;
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + ring_bytes);
+    double* yc = SMEM_Y ? reinterpret_cast<double*>(smem_raw + ring_bytes + kRingHeader) : sd.y;
+    TC* yf = reinterpret_cast<TC*>(yc + 3 * sd.nc);
+    TC* ycf = sizeof(TC) == 8 ? nullptr : yf + 3 * sd.nf;  // FP32 mirror of the lump values
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
+
+    if (tid == 0) {
+        for (int k = 0; k < slots; k++) mbar_init(&bar[k], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int k = 0; k < slots && k < sd.n_chunks; k++) {
+            const int2 ch = sd.chunks[k];
+            mbar_expect_tx(&bar[k], (unsigned)ch.y);
+            bulk_load(ring + (size_t)k * kStreamChunk, sd.stream + ch.x, (unsigned)ch.y, &bar[k]);
+        }
+
+    // restriction R_i r (overlaps the first chunk copies)
+    restrict_local<TC>(st, sd, r, yf, yc);
     __syncthreads();
 
     // descriptor of the next chunk to stream, loaded one chunk ahead so that thread 0 does not
@@ -490,6 +501,16 @@ __global__ void __launch_bounds__(256, 2) k_apply(const SysTab* __restrict__ tab
         z[c + 1] = yf[3 * f + 1];
         z[c + 2] = yf[3 * f + 2];
     }
+}
+
+// Exact local solves: R_i r into the subdomain's FP64 local vector, fine indices then lump indices
+// (the order of the dense A_i^{-1}); one CTA per subdomain
+__global__ void __launch_bounds__(256) k_dense_restrict(const SysTab* __restrict__ tab, const SubDesc* __restrict__ subs) {
+    const SubDesc& sd = subs[blockIdx.x];
+    const SysTab& st = tab[sd.sys];
+    const int in = st.ctl[C_APPLY_IN];
+    if (in < 0) return;
+    restrict_local<double>(st, sd, st.ws + (long long)in * st.n3p, sd.y, sd.y + 3 * sd.nf);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1146,6 +1167,10 @@ void launch_apply(const SysTab* tab, const SubDesc* subs, int nsub, int prec, in
         launch_apply_p<float>(tab, subs, nsub, ysmem, slots, st);
     else
         launch_apply_p<__half>(tab, subs, nsub, ysmem, slots, st);
+}
+
+void launch_dense_restrict(const SysTab* tab, const SubDesc* subs, int nsub, cudaStream_t st) {
+    if (nsub > 0) k_dense_restrict<<<nsub, 256, 0, st>>>(tab, subs);
 }
 
 void launch_spmv(const SysTab* tab, const RowItem* items, int nitems, cudaStream_t st) {
