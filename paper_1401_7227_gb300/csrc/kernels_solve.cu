@@ -372,12 +372,29 @@ __device__ __forceinline__ void restrict_local(const SysTab& st, const SubDesc& 
                                                TC* yf, double* yc) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
-#pragma unroll 4
-    for (int f = tid; f < sd.nf; f += nt) {
-        const double* rc = r + 3LL * sd.fcell[f];
-        yf[3 * f] = (TC)rc[0];
-        yf[3 * f + 1] = (TC)rc[1];
-        yf[3 * f + 2] = (TC)rc[2];
+    // fine cells in batches of kB rows per thread: all cell indices, then all values, are in flight
+    // together (two dependent global-load round trips per batch instead of per row)
+    constexpr int kB = 4;
+    for (int f0 = tid; f0 < sd.nf; f0 += kB * nt) {
+        int cell[kB];
+#pragma unroll
+        for (int u = 0; u < kB; u++) cell[u] = f0 + u * nt < sd.nf ? sd.fcell[f0 + u * nt] : -1;
+        double v[kB][3];
+#pragma unroll
+        for (int u = 0; u < kB; u++) {
+            const double* rc = r + 3LL * (cell[u] >= 0 ? cell[u] : 0);
+            v[u][0] = rc[0];
+            v[u][1] = rc[1];
+            v[u][2] = rc[2];
+        }
+#pragma unroll
+        for (int u = 0; u < kB; u++)
+            if (cell[u] >= 0) {
+                const int f = f0 + u * nt;
+                yf[3 * f] = (TC)v[u][0];
+                yf[3 * f + 1] = (TC)v[u][1];
+                yf[3 * f + 2] = (TC)v[u][2];
+            }
     }
     for (int c = tid; c < sd.nc; c += nt) {
         const int i0 = sd.rptr[c], i1 = sd.rptr[c + 1];
