@@ -162,15 +162,14 @@ def serving_pool(n_pool: int, seed0: int = 5_000_000):
     return pool
 
 
-def run_serving(args, stream):
-    """Poisson arrivals; 30% of requests repeat an earlier matrix (factors reused), the rest carry a
-    new matrix (full set-up: values uploaded, local matrices assembled and factored).  Latency =
-    completion - arrival (host wall clock); generation is off the clock."""
+def serve_stream(pool, n_req: int, rate: float, precision: str, max_active: int, stream, seed: int = 5):
+    """One Poisson stream through the serving loop.  30% of requests repeat an earlier matrix
+    (factors reused), the rest carry a new matrix (full set-up: values uploaded, local matrices
+    assembled and factored).  Latency = completion - arrival (host wall clock); generation is off
+    the clock."""
     from paper_1401_7227_gb300 import asm2
-    rng = np.random.default_rng(5)
-    pool = serving_pool(args.serve_pool)
-    n_req = args.serve_requests
-    gaps = rng.exponential(1.0 / args.serve_rate, n_req)
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, n_req)
     arrivals = np.cumsum(gaps)
     reqs = []
     for i in range(n_req):
@@ -180,7 +179,7 @@ def run_serving(args, stream):
         else:
             key, pidx = i, int(rng.integers(0, len(pool)))
         reqs.append((key, pidx, int(rng.integers(0, 4))))
-    srv = asm2.Server(precision="fp32", restart=30, max_active=args.serve_max_active, max_cached=32,
+    srv = asm2.Server(precision=precision, restart=30, max_active=max_active, max_cached=32,
                       stream=stream.cuda_stream)
     t0 = time.perf_counter()
     nxt = 0
@@ -207,13 +206,30 @@ def run_serving(args, stream):
     stats = srv.stats()
     srv.close()
     lat_ms = np.array(lat) * 1e3
-    return {"requests": n_req, "rate_per_s": args.serve_rate, "pool_matrices": len(pool),
-            "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
-            "mean_ms": float(lat_ms.mean()), "solves_per_s": n_req / (max(done_t) - arrivals[0]),
-            "reuse_hits": stats["reuse_hits"], "structure_builds": stats["structure_builds"],
-            "steps": stats["steps"], "precision": "fp32 factors, fp64 Krylov",
-            "sample": f"{n_req} requests, Poisson {args.serve_rate}/s, 30% repeated matrices, "
-                      f"{len(pool)} distinct synthetic matrices 2e3-1e6 cells"}
+    span = max(done_t) - arrivals[0]
+    return {"requests": n_req, "offered_per_s": rate, "p50_ms": float(np.percentile(lat_ms, 50)),
+            "p99_ms": float(np.percentile(lat_ms, 99)), "mean_ms": float(lat_ms.mean()),
+            "solves_per_s": n_req / span, "reuse_hits": stats["reuse_hits"],
+            "structure_builds": stats["structure_builds"], "steps": stats["steps"]}
+
+
+def run_serving(args, stream):
+    """The serving stream at the offered rate (200/s) with the FP32 and the FP64 preconditioner.
+    One GB300 cannot keep up with that rate on this stream (it needs ~6x the solves/s measured), so
+    the offered-rate run measures capacity (solves/s under overload) and its latencies mostly
+    measure queueing; a second run at 70% of the measured capacity gives p50/p99 at a sustainable
+    load."""
+    pool = serving_pool(args.serve_pool)
+    out = {"sample": f"Poisson arrivals, 30% repeated matrices (factors reused), {len(pool)} distinct "
+                     f"synthetic matrices of 2e3-1e6 cells, overlap 1, GMRES(30) to 1e-8",
+           "contract_rate_per_s": args.serve_rate}
+    for prec in ("fp32", "fp64"):
+        over = serve_stream(pool, args.serve_requests, args.serve_rate, prec, args.serve_max_active, stream)
+        cap = over["solves_per_s"]
+        sus = serve_stream(pool, max(20, args.serve_requests // 2), 0.7 * cap, prec, args.serve_max_active, stream,
+                           seed=6)
+        out[prec] = {"offered_rate": over, "capacity_solves_per_s": cap, "at_70pct_capacity": sus}
+    return out
 
 
 def run_profile_case(args):
@@ -237,6 +253,23 @@ def run_profile_case(args):
     print(json.dumps({"profile_case": "grid128x128x32_k256", "info": info, "stats": sol.stats()}))
     sol.close()
     return 0
+
+
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64 (no measured figure for it is given)
+
+
+def spmv_roofline(res, system, steps: int):
+    """The SpMV is bound by the FP64 pipe on this GPU (18 flops per 3x3 block against ~76 bytes):
+    achieved TFLOP/s of one launch against the nominal FP64 rate.  Launches per solve: one per
+    Arnoldi step and one per restart (true residual)."""
+    info = res["info"]
+    launches = info["iterations"] + info["restarts"] + 1
+    ms = res["prof"]["spmv_ms"] / steps / launches
+    flops = 18.0 * system.col_idx.size
+    ach = flops / (ms * 1e-3) / 1e12
+    return {"kernel": "k_spmv", "bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / FP64_NOMINAL_TFLOPS, "peak_kind": "nominal FP64", "launch_ms": ms,
+            "hbm_frac": (76.0 * system.col_idx.size + 48.0 * system.n_cells) / (ms * 1e-3) / 1e9 / peaks()[0]}
 
 
 def apply_traffic(alg_bytes: int):
@@ -401,6 +434,7 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "kernel": "precond apply (boxsum + fused local solves)", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": apply_traffic(alg_bytes),
                      "alg_bytes_per_launch": alg_bytes, "launch_ms": apply_ms, "peak_kind": peak_kind},
+        "rooflines_other": [spmv_roofline(main, system, args.steps)],
         "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(system.vals.nbytes + system.b.nbytes),
                 "d2h_bytes_per_step": int(system.b.nbytes)},
         "gpu_launches": int(launches),
@@ -434,7 +468,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--profile-case", action="store_true", help="small case for ncu captures")
-    ap.add_argument("--serve-requests", type=int, default=600)
+    ap.add_argument("--serve-requests", type=int, default=240)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-pool", type=int, default=12)
     ap.add_argument("--serve-max-active", type=int, default=64)
