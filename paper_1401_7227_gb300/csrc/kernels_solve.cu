@@ -1050,6 +1050,7 @@ __device__ __forceinline__ void grid_total(const double* part, int G, double& s0
 }
 
 __global__ void __launch_bounds__(VEC_THREADS) k_ortho_coop(const SysTab* __restrict__ tab, double* __restrict__ part2) {
+    constexpr int kU = 4;
     namespace cg = cooperative_groups;
     cg::grid_group grid = cg::this_grid();
     const SysTab& st = tab[0];
@@ -1068,29 +1069,51 @@ __global__ void __launch_bounds__(VEC_THREADS) k_ortho_coop(const SysTab* __rest
         for (int k = 0; k <= j + 1; k++) {
             double* part = part2 + (size_t)(k & 1) * 2 * G;
             double s0 = 0.0, s1 = 0.0;
+            // kU elements per thread per iteration, loaded before any arithmetic, with kU partial
+            // sums: keeps enough loads in flight per warp to cover the memory latency
+            double p0[kU], p1[kU];
+#pragma unroll
+            for (int u = 0; u < kU; u++) p0[u] = p1[u] = 0.0;
             if (k == 0) {
                 const double* vk = vec(st, VV0);
-                for (long long e = e_begin; e < n; e += stride) {
-                    const double a = w[e];
-                    s0 = fma(a, vk[e], s0);
-                    s1 = fma(a, a, s1);
-                }
-            } else if (k <= j) {
-                const double* vp = vec(st, VV0 + k - 1);
-                const double* vk = vec(st, VV0 + k);
-                for (long long e = e_begin; e < n; e += stride) {
-                    const double a = fma(-hprev, vp[e], w[e]);
-                    w[e] = a;
-                    s0 = fma(a, vk[e], s0);
+                for (long long e0 = e_begin; e0 < n; e0 += kU * stride) {
+                    double a[kU], b[kU];
+#pragma unroll
+                    for (int u = 0; u < kU; u++) {
+                        const long long e = e0 + u * stride;
+                        a[u] = e < n ? w[e] : 0.0;
+                        b[u] = e < n ? vk[e] : 0.0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kU; u++) {
+                        p0[u] = fma(a[u], b[u], p0[u]);
+                        p1[u] = fma(a[u], a[u], p1[u]);
+                    }
                 }
             } else {
                 const double* vp = vec(st, VV0 + k - 1);
-                for (long long e = e_begin; e < n; e += stride) {
-                    const double a = fma(-hprev, vp[e], w[e]);
-                    w[e] = a;
-                    s0 = fma(a, a, s0);
+                const double* vk = k <= j ? vec(st, VV0 + k) : nullptr;
+                for (long long e0 = e_begin; e0 < n; e0 += kU * stride) {
+                    double a[kU], b[kU], c[kU];
+#pragma unroll
+                    for (int u = 0; u < kU; u++) {
+                        const long long e = e0 + u * stride;
+                        const bool in = e < n;
+                        a[u] = in ? w[e] : 0.0;
+                        b[u] = in ? vp[e] : 0.0;
+                        c[u] = in && vk ? vk[e] : 0.0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kU; u++) {
+                        const long long e = e0 + u * stride;
+                        const double x = fma(-hprev, b[u], a[u]);
+                        if (e < n) w[e] = x;
+                        p0[u] = fma(x, vk ? c[u] : x, p0[u]);
+                    }
                 }
             }
+            s0 = (p0[0] + p0[1]) + (p0[2] + p0[3]);
+            s1 = (p1[0] + p1[1]) + (p1[2] + p1[3]);
             block_sum2(s0, s1);
             if (threadIdx.x == 0) {
                 part[2 * blockIdx.x] = s0;
@@ -1110,7 +1133,14 @@ __global__ void __launch_bounds__(VEC_THREADS) k_ortho_coop(const SysTab* __rest
         if (hn > 0.0) {
             const double inv = 1.0 / hn;
             double* v = vec(st, VV0 + j + 1);
-            for (long long e = e_begin; e < n; e += stride) v[e] = w[e] * inv;
+            for (long long e0 = e_begin; e0 < n; e0 += kU * stride) {
+                double a[kU];
+#pragma unroll
+                for (int u = 0; u < kU; u++) a[u] = e0 + u * stride < n ? w[e0 + u * stride] : 0.0;
+#pragma unroll
+                for (int u = 0; u < kU; u++)
+                    if (e0 + u * stride < n) v[e0 + u * stride] = a[u] * inv;
+            }
         }
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             st.scal[SL.w0] = w0;
