@@ -145,7 +145,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
     return false;
 }
 
-constexpr int kMaxSlots = 4;  // ring slots of the apply: a launch argument, 2..kMaxSlots
+constexpr int kMaxSlots = 4;  // ring slots of the apply: a template argument, 2..kMaxSlots
 constexpr int kRingHeader = 64;  // mbarriers
 
 // One chunk of the forward (lower = true) or backward sweep, read from shared memory.
@@ -217,7 +217,7 @@ __device__ __forceinline__ void sweep_chunk(const unsigned char* base, bool lowe
     } else {
     // fine rows: one thread each; the blocks and x of up to kUnroll entries are loaded before any
     // arithmetic so that their shared-memory latencies overlap
-    constexpr int kUnroll = 6;
+    constexpr int kUnroll = 4;
     for (int t = tid; t < nf; t += nt) {
         const int f = f0 + t;
         TC a0 = yf[3 * f], a1 = yf[3 * f + 1], a2 = yf[3 * f + 2];
@@ -448,9 +448,8 @@ __device__ __forceinline__ void restrict_local(const SysTab& st, const SubDesc& 
 // from shared memory, one chunk at a time, with a CTA barrier after each chunk (which also orders
 // the wavefront levels).  Fine rows and lump rows live in separate local vectors (fine rows at the
 // factor precision, lumps in FP64), in shared memory when they fit.
-template <typename TF, bool SMEM_Y>
-__global__ void __launch_bounds__(256, 2) k_apply(const SysTab* __restrict__ tab, const SubDesc* __restrict__ subs,
-                                                   int slots) {
+template <typename TF, bool SMEM_Y, int SLOTS>
+__global__ void __launch_bounds__(256, 2) k_apply(const SysTab* __restrict__ tab, const SubDesc* __restrict__ subs) {
     using TC = typename Compute<TF>::T;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const SubDesc sd = subs[blockIdx.x];
@@ -461,7 +460,7 @@ __global__ void __launch_bounds__(256, 2) k_apply(const SysTab* __restrict__ tab
     const double* __restrict__ r = st.ws + (long long)in * st.n3p;
     double* __restrict__ z = st.ws + (long long)out * st.n3p;
     unsigned char* ring = smem_raw;
-    const int ring_bytes = slots * kStreamChunk;
+    constexpr int ring_bytes = SLOTS * kStreamChunk;
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + ring_bytes);
     double* yc = SMEM_Y ? reinterpret_cast<double*>(smem_raw + ring_bytes + kRingHeader) : sd.y;
     TC* yf = reinterpret_cast<TC*>(yc + 3 * sd.nc);
@@ -470,12 +469,12 @@ __global__ void __launch_bounds__(256, 2) k_apply(const SysTab* __restrict__ tab
     const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
 
     if (tid == 0) {
-        for (int k = 0; k < slots; k++) mbar_init(&bar[k], 1);
+        for (int k = 0; k < SLOTS; k++) mbar_init(&bar[k], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     if (tid == 0)
-        for (int k = 0; k < slots && k < sd.n_chunks; k++) {
+        for (int k = 0; k < SLOTS && k < sd.n_chunks; k++) {
             const int2 ch = sd.chunks[k];
             mbar_expect_tx(&bar[k], (unsigned)ch.y);
             bulk_load(ring + (size_t)k * kStreamChunk, sd.stream + ch.x, (unsigned)ch.y, &bar[k]);
@@ -485,28 +484,38 @@ __global__ void __launch_bounds__(256, 2) k_apply(const SysTab* __restrict__ tab
     restrict_local<TC>(st, sd, r, yf, yc);
     __syncthreads();
 
-    // descriptor of the next chunk to stream, loaded one chunk ahead so that thread 0 does not
-    // wait on a global load between the barrier and the copy it issues
+    // The copy that refills a slot is issued by lane 0 of a warp without rows in the chunk just
+    // finished (fine rows fill warps from the first, lump rows from the last), so the next chunk's
+    // rows are not held up behind it.  Both candidate issuers keep the next chunk's descriptor,
+    // loaded one chunk ahead.
+    const bool issuer_fine = lane == 0 && warp == nwarp - 1, issuer_lump = tid == 0;
     int2 next_ch = make_int2(0, 0);
-    if (tid == 0 && slots < sd.n_chunks) next_ch = sd.chunks[slots];
+    if ((issuer_fine || issuer_lump) && SLOTS < sd.n_chunks) next_ch = sd.chunks[SLOTS];
     for (int ci = 0; ci < sd.n_chunks; ci++) {
-        const int slot = ci % slots;
-        const bool ok = mbar_wait(&bar[slot], (unsigned)(ci / slots) & 1u);
-        if (ok) sweep_chunk<TF>(ring + (size_t)slot * kStreamChunk, ci < sd.n_fwd, yf, yc, ycf);
+        const int slot = ci % SLOTS;
+        const bool ok = mbar_wait(&bar[slot], (unsigned)(ci / SLOTS) & 1u);
+        bool fine_chunk = false;
+        if (ok) {
+            const unsigned char* chunk = ring + (size_t)slot * kStreamChunk;
+            fine_chunk = reinterpret_cast<const int*>(chunk)[1] > 0;
+            sweep_chunk<TF>(chunk, ci < sd.n_fwd, yf, yc, ycf);
+        }
         if (__syncthreads_or(!ok)) {
             // a copy did not land in time: report it, wait (bounded) for the copies still in
             // flight into this CTA's shared memory, and leave
             if (tid == 0) {
                 atomicExch(st.dev_err, 7);
-                const int last = min(sd.n_chunks, ci + slots);
-                for (int k = ci; k < last; k++) mbar_wait(&bar[k % slots], (unsigned)(k / slots) & 1u);
+                const int last = min(sd.n_chunks, ci + SLOTS);
+                for (int k = ci; k < last; k++) mbar_wait(&bar[k % SLOTS], (unsigned)(k / SLOTS) & 1u);
             }
             return;
         }
-        if (tid == 0 && ci + slots < sd.n_chunks) {
-            mbar_expect_tx(&bar[slot], (unsigned)next_ch.y);
-            bulk_load(ring + (size_t)slot * kStreamChunk, sd.stream + next_ch.x, (unsigned)next_ch.y, &bar[slot]);
-            if (ci + slots + 1 < sd.n_chunks) next_ch = sd.chunks[ci + slots + 1];
+        if (ci + SLOTS < sd.n_chunks) {
+            if (fine_chunk ? issuer_fine : issuer_lump) {
+                mbar_expect_tx(&bar[slot], (unsigned)next_ch.y);
+                bulk_load(ring + (size_t)slot * kStreamChunk, sd.stream + next_ch.x, (unsigned)next_ch.y, &bar[slot]);
+            }
+            if ((issuer_fine || issuer_lump) && ci + SLOTS + 1 < sd.n_chunks) next_ch = sd.chunks[ci + SLOTS + 1];
         }
     }
 
@@ -1186,22 +1195,31 @@ size_t apply_smem_bytes(int nf, int nc, int prec) {
 size_t apply_ring_bytes(int slots) { return (size_t)slots * kStreamChunk + kRingHeader; }
 
 namespace {
-template <typename TF, bool Y>
-void launch_apply_t(const SysTab* tab, const SubDesc* subs, int nsub, int smem, int slots, cudaStream_t st) {
+template <typename TF, bool Y, int SLOTS>
+void launch_apply_t(const SysTab* tab, const SubDesc* subs, int nsub, int smem, cudaStream_t st) {
     static int configured = -1;
     if (configured < smem) {
-        cudaFuncSetAttribute(k_apply<TF, Y>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_apply<TF, Y, SLOTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         configured = smem;
     }
-    k_apply<TF, Y><<<nsub, 256, smem, st>>>(tab, subs, slots);
+    k_apply<TF, Y, SLOTS><<<nsub, 256, smem, st>>>(tab, subs);
+}
+template <typename TF, bool Y>
+void launch_apply_s(const SysTab* tab, const SubDesc* subs, int nsub, int smem, int slots, cudaStream_t st) {
+    if (slots == 2)
+        launch_apply_t<TF, Y, 2>(tab, subs, nsub, smem, st);
+    else if (slots == 3)
+        launch_apply_t<TF, Y, 3>(tab, subs, nsub, smem, st);
+    else
+        launch_apply_t<TF, Y, 4>(tab, subs, nsub, smem, st);
 }
 template <typename TF>
 void launch_apply_p(const SysTab* tab, const SubDesc* subs, int nsub, int ysmem, int slots, cudaStream_t st) {
     const int ring = (int)apply_ring_bytes(slots);
     if (ysmem > 0)
-        launch_apply_t<TF, true>(tab, subs, nsub, ring + ysmem, slots, st);
+        launch_apply_s<TF, true>(tab, subs, nsub, ring + ysmem, slots, st);
     else
-        launch_apply_t<TF, false>(tab, subs, nsub, ring, slots, st);
+        launch_apply_s<TF, false>(tab, subs, nsub, ring, slots, st);
 }
 }  // namespace
 
