@@ -208,8 +208,10 @@ int asm_solve_batch(asm_handle* hs, int n, const double* const* b, double* const
 int asm_get_stats(asm_handle h, asm_stats* st);
 
 /* Tuning switches of the kernels (none changes the arithmetic; results are bitwise the same):
- *   ASM_TUNE_APPLY_SMEM  1 (default) keeps each subdomain's local vectors in shared memory when
- *                        they fit, 0 keeps them in device memory;
+ *   ASM_TUNE_APPLY_SMEM  1 (default): each subdomain's local vectors live in shared memory
+ *                        (256-thread CTAs, two per SM) when every subdomain CTA of the launch then
+ *                        runs at once, else in device memory (128-thread CTAs, four per SM); 0 keeps
+ *                        them in device memory;
  *   ASM_TUNE_COOP_ORTHO  1 (default) runs the Gram-Schmidt step of a single-system solve in one
  *                        cooperative launch, 0 in one launch per projection.
  * Errors: INVALID_ARG for an unknown key or value. */

@@ -86,6 +86,7 @@ struct asm_ctx {
     DBuf d_lv, d_rlists, d_y, d_corr_cells, d_corr, d_dev_err;
     int apply_smem = 0;  // dynamic shared memory of the apply (0: local vectors in d_y)
     int apply_slots = 3; // factor-stream ring slots of the apply
+    int sm_smem = 0, n_sms = 1;  // shared memory per SM and SM count of the device
     DBuf d_factdesc, d_subdesc_single;
     DBuf d_err;
     std::vector<FactDesc> fact_desc;
@@ -93,6 +94,7 @@ struct asm_ctx {
     std::vector<double> sub_cost;    // estimated apply time of each subdomain (launch order)
     std::vector<BoxItem> box_items;  // sys = 0
     std::vector<long long> slot_base, stream_base, row_base;
+    std::vector<long long> y_base;  // doubles: each subdomain's local vectors when not in shared memory
     long long pk_nf = 0, pk_nc = 0, total_slots = 0;
     // Krylov workspace
     int ws_m = -1, ws_flex = -1;
@@ -289,7 +291,15 @@ void upload_symbolic(asm_ctx* h) {
     if (h->total_slots >= (1LL << 31) / 9 || aloc_base[K] >= (1LL << 31)) throw CudaFail{ASM_ERR_INVALID_ARG};
     h->d_slot.alloc((size_t)h->total_slots * 9 * sizeof(double));
     h->d_dpiv.alloc((size_t)h->row_base[K] * 9 * sizeof(double));
-    h->d_y.alloc((size_t)h->row_base[K] * 3 * sizeof(double));
+    // local vectors of the apply in device memory: the same layout as in shared memory
+    // (FP64 lumps, fine rows at the factor precision, an FP32 lump mirror), 16-byte aligned
+    h->y_base.assign(K + 1, 0);
+    for (int s = 0; s < K; s++) {
+        const SubSym& o = S.subs[s];
+        const long long bytes = std::max<long long>((long long)apply_smem_bytes(o.nf, o.n - o.nf, S.prec), 24LL * o.n);
+        h->y_base[s + 1] = h->y_base[s] + (bytes + 15) / 16 * 2;
+    }
+    h->d_y.alloc((size_t)h->y_base[K] * sizeof(double));
     // assembly lists (global offsets)
     {
         std::vector<int> aptr;
@@ -400,7 +410,7 @@ void upload_symbolic(asm_ctx* h) {
         sd.n_long = (int)o.clong.size();
         sd.corr0 = corr_base;
         sd.stream = h->d_stream.as<unsigned char>() + h->stream_base[s];
-        sd.y = h->d_y.as<double>() + h->row_base[s] * 3;
+        sd.y = h->d_y.as<double>() + h->y_base[s];
         {
             // the chunk table goes first: base is 8-byte aligned, so the int2 entries are too
             std::vector<int> ch;
@@ -461,6 +471,8 @@ void upload_symbolic(asm_ctx* h) {
     // else 4 with one CTA per SM; local vectors in device memory when they cannot fit at all
     int sm_smem = 0;
     ck(cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device));
+    h->sm_smem = sm_smem;
+    ck(cudaDeviceGetAttribute(&h->n_sms, cudaDevAttrMultiProcessorCount, h->device));
     h->apply_slots = 4;
     for (int sl = 4; sl >= 2; sl--)
         if (2 * ((size_t)h->apply_smem + apply_ring_bytes(sl) + 1024) <= (size_t)sm_smem) {
@@ -848,6 +860,7 @@ void build_batch(Batch& B, cudaStream_t st) {
     if (!all_smem) B.smem = 0;
     B.slots = 4;
     for (asm_ctx* h : B.hs) B.slots = std::min(B.slots, h->apply_slots);
+    if (!B.hs.empty()) B.smem = apply_local_vectors(B.nsub, B.smem, B.slots, B.hs[0]->sm_smem, B.hs[0]->n_sms);
 }
 
 // events bracketing the launch groups of one step: [prep | apply | post | spmv | mgs+finish]
@@ -1577,8 +1590,10 @@ int asm_apply_precond(asm_handle h, const double* r, double* z, int on_device) {
             launch_dense_apply(h->d_tab1.as<SysTab>(), h->d_subdesc_single.as<SubDesc>(), h->d_ditems1.as<int2>(),
                                h->n_ditems1, h->stream);
         } else {
-            launch_apply(h->d_tab1.as<SysTab>(), h->d_subdesc_single.as<SubDesc>(), (int)h->sub_desc.size(), h->prec,
-                         h->no_smem ? 0 : h->apply_smem, h->apply_slots, h->stream);
+            const int nsub = (int)h->sub_desc.size();
+            launch_apply(h->d_tab1.as<SysTab>(), h->d_subdesc_single.as<SubDesc>(), nsub, h->prec,
+                         h->no_smem ? 0 : apply_local_vectors(nsub, h->apply_smem, h->apply_slots, h->sm_smem, h->n_sms),
+                         h->apply_slots, h->stream);
         }
         if (h->tab.cmode != 0)
             launch_coarse_apply(h->d_tab1.as<SysTab>(), h->d_row1.as<RowItem>(), h->n_row1,

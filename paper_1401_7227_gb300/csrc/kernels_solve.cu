@@ -449,7 +449,7 @@ __device__ __forceinline__ void restrict_local(const SysTab& st, const SubDesc& 
 // the wavefront levels).  Fine rows and lump rows live in separate local vectors (fine rows at the
 // factor precision, lumps in FP64), in shared memory when they fit.
 template <typename TF, bool SMEM_Y, int SLOTS>
-__global__ void __launch_bounds__(256, 2) k_apply(const SysTab* __restrict__ tab, const SubDesc* __restrict__ subs) {
+__global__ void __launch_bounds__(SMEM_Y ? 256 : kApplyThreadsDev, SMEM_Y ? 2 : 4) k_apply(const SysTab* __restrict__ tab, const SubDesc* __restrict__ subs) {
     using TC = typename Compute<TF>::T;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const SubDesc sd = subs[blockIdx.x];
@@ -1194,6 +1194,13 @@ size_t apply_smem_bytes(int nf, int nc, int prec) {
 
 size_t apply_ring_bytes(int slots) { return (size_t)slots * kStreamChunk + kRingHeader; }
 
+int apply_local_vectors(int nsub, int ysmem, int slots, int sm_smem, int sms) {
+    if (ysmem <= 0) return 0;
+    const long long per_cta = (long long)ysmem + (long long)apply_ring_bytes(slots) + 1024;
+    const long long fit = std::min<long long>(2, sm_smem / per_cta);  // 256-thread CTAs: two per SM at most
+    return (long long)nsub <= fit * sms ? ysmem : 0;
+}
+
 namespace {
 template <typename TF, bool Y, int SLOTS>
 void launch_apply_t(const SysTab* tab, const SubDesc* subs, int nsub, int smem, cudaStream_t st) {
@@ -1202,7 +1209,7 @@ void launch_apply_t(const SysTab* tab, const SubDesc* subs, int nsub, int smem, 
         cudaFuncSetAttribute(k_apply<TF, Y, SLOTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         configured = smem;
     }
-    k_apply<TF, Y, SLOTS><<<nsub, 256, smem, st>>>(tab, subs);
+    k_apply<TF, Y, SLOTS><<<nsub, Y ? 256 : kApplyThreadsDev, smem, st>>>(tab, subs);
 }
 template <typename TF, bool Y>
 void launch_apply_s(const SysTab* tab, const SubDesc* subs, int nsub, int smem, int slots, cudaStream_t st) {

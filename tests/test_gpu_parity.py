@@ -287,3 +287,19 @@ def test_kernel_variants(prec):
     x3, i3 = sol.solve(s.b, 1e-8, 2000)
     assert i1 == i2 and i3["iterations"] == i1["iterations"]
     assert rel(x3, x1) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16s"])
+def test_device_memory_local_vectors_with_more_lumps_than_fine_rows(prec):
+    """Subdomains of 4 cells with ~60 far lumps each: the device-memory local vectors (lumps in
+    FP64, fine rows and the lump mirror at the factor precision) must not spill into the next
+    subdomain's; the result equals the shared-memory variant bit for bit."""
+    g = O.Geometry(8, 8, 4, 8, 8, 1, ov=0, near_width=2)
+    s = synth.grid_jacobian(g.nx, g.ny, g.nz, 9)
+    pc = O.Precond(g, s.row_ptr, s.col_idx, s.vals)
+    assert max(pc.sub_n(k) - pc.sub_counts(k)[0] for k in range(g.n_sub)) > 4 * pc.sub_counts(0)[0]
+    sol = gpu_solver(g, s, precision=prec)
+    z1 = sol.apply(s.b)
+    sol.set_tuning(apply_smem=False)
+    np.testing.assert_array_equal(z1, sol.apply(s.b))
+    assert rel(z1, pc.apply(s.b)) <= (1e-5 if prec == "fp32" else 1e-2)
