@@ -208,10 +208,13 @@ int asm_solve_batch(asm_handle* hs, int n, const double* const* b, double* const
 int asm_get_stats(asm_handle h, asm_stats* st);
 
 /* Tuning switches of the kernels (none changes the arithmetic; results are bitwise the same):
- *   ASM_TUNE_APPLY_SMEM  1 (default): each subdomain's local vectors live in shared memory
- *                        (256-thread CTAs, two per SM) when every subdomain CTA of the launch then
- *                        runs at once, else in device memory (128-thread CTAs, four per SM); 0 keeps
- *                        them in device memory;
+ *   ASM_TUNE_APPLY_SMEM  where the apply keeps each subdomain's local vectors.  1 (default):
+ *                        all in shared memory (256-thread CTAs, two per SM) when every subdomain CTA
+ *                        of the launch then runs at once; else the lump vector in shared memory and
+ *                        the fine-row vector in device memory (128-thread CTAs, four per SM) when
+ *                        that fits; else all in device memory (128-thread CTAs).  0: all in device
+ *                        memory; 2: lumps in shared memory; 3: all in shared memory (2 and 3 fall
+ *                        back to device memory when they do not fit);
  *   ASM_TUNE_COOP_ORTHO  1 (default) runs the Gram-Schmidt step of a single-system solve in one
  *                        cooperative launch, 0 in one launch per projection.
  * Errors: INVALID_ARG for an unknown key or value. */

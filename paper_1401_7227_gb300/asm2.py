@@ -300,9 +300,13 @@ class Solver:
         _check(load().asm_get_stats(self._h, C.byref(s)), "stats")
         return s.as_dict()
 
-    def set_tuning(self, apply_smem: bool | None = None, coop_ortho: bool | None = None):
+    def set_tuning(self, apply_smem: bool | str | None = None, coop_ortho: bool | None = None):
+        """apply_smem: True / "auto" (default placement), False / "device", "lumps" (lump vector in
+        shared memory), "shared" (all local vectors in shared memory); see ASM_TUNE_APPLY_SMEM."""
         if apply_smem is not None:
-            _check(load().asm_set_tuning(self._h, 0, int(apply_smem)), "set_tuning")
+            v = {"device": 0, "auto": 1, "lumps": 2, "shared": 3}[apply_smem] if isinstance(apply_smem, str) \
+                else int(apply_smem)
+            _check(load().asm_set_tuning(self._h, 0, v), "set_tuning")
         if coop_ortho is not None:
             _check(load().asm_set_tuning(self._h, 1, int(coop_ortho)), "set_tuning")
 

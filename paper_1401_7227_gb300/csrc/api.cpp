@@ -84,7 +84,8 @@ struct asm_ctx {
     DBuf d_fp;  // factor program arrays (one allocation, see upload_factor_program)
     DBuf d_stream, d_pk_off_f, d_pk_src_f, d_pk_off_c, d_pk_src_c;
     DBuf d_lv, d_rlists, d_y, d_corr_cells, d_corr, d_dev_err;
-    int apply_smem = 0;  // dynamic shared memory of the apply (0: local vectors in d_y)
+    int apply_smem = 0;       // shared memory for all local vectors of the largest subdomain (0: none)
+    int apply_lump_smem = 0;  // shared memory for its lump vector and the FP32 mirror
     int apply_slots = 3; // factor-stream ring slots of the apply
     int sm_smem = 0, n_sms = 1;  // shared memory per SM and SM count of the device
     DBuf d_factdesc, d_subdesc_single;
@@ -107,7 +108,7 @@ struct asm_ctx {
     // profiling
     bool profiling = false;
     bool no_coop = false;  // per-kernel orthogonalisation path instead of the cooperative one
-    bool no_smem = false;  // local vectors of the apply in device memory
+    int apply_place = 0;  // 0 automatic, else ApplyY + 1 (asm_set_tuning ASM_TUNE_APPLY_SMEM)
     asm_profile_info prof{};
     // exact local solves (local_solver = ASM_LOCAL_EXACT): [A_i | I] inverted in place per subdomain
     DBuf d_daug, d_dprow, d_dfcol, d_dmats, d_dinit, d_doff, d_dmat_of_slot, d_dpart, d_derr, d_ditems1;
@@ -373,6 +374,7 @@ void upload_symbolic(asm_ctx* h) {
     h->sub_desc.assign(K, SubDesc{});
     h->sub_cost.assign(K, 0.0);
     h->apply_smem = 0;
+    h->apply_lump_smem = 0;
     for (int s = 0; s < K; s++) {
         const SubSym& o = S.subs[s];
         if (!o.stream.empty())
@@ -429,6 +431,7 @@ void upload_symbolic(asm_ctx* h) {
         sd.own_pos = put(o.own_pos);
         sd.own_cell = put(o.own_cell);
         h->apply_smem = std::max<int>(h->apply_smem, (int)apply_smem_bytes(o.nf, o.n - o.nf, S.prec));
+        h->apply_lump_smem = std::max<int>(h->apply_lump_smem, (int)apply_lump_bytes(o.n - o.nf, S.prec));
         for (size_t k = 0; k + 1 < o.corr_ptr.size(); k++)
             corr_items.push_back(BoxItem{0, corr_base + (int)k, (int)corr_cells.size() + o.corr_ptr[k],
                                          (int)corr_cells.size() + o.corr_ptr[k + 1], 1, 0, nullptr});
@@ -778,7 +781,8 @@ namespace {
 struct Batch {
     std::vector<asm_ctx*> hs;
     DBuf d_tab, d_vec, d_row, d_box, d_sub, d_gather;
-    int nvec = 0, nrow = 0, nbox = 0, nsub = 0, prec = 0, smem = 0, slots = 3;
+    int nvec = 0, nrow = 0, nbox = 0, nsub = 0, prec = 0, slots = 3;
+    ApplyConfig apply{Y_DEVICE, 0};
     DBuf d_dense;           // exact local solves: (subdomain item, first owned row of 8)
     int ndense = 0;
     bool exact = false;     // every system of the batch has exact local solves
@@ -851,16 +855,19 @@ void build_batch(Batch& B, cudaStream_t st) {
     ck(cudaMallocHost((void**)&B.pinned, sizeof(int) * C_NCTL * std::max<size_t>(1, B.hs.size())));
     // kernel variants shared by the whole batch
     B.prec = B.hs.empty() ? 0 : B.hs[0]->prec;
-    B.smem = 0;
-    bool all_smem = !B.hs.empty();
+    int all_bytes = 0, lump_bytes = 0;
+    bool all_ok = !B.hs.empty();
     for (asm_ctx* h : B.hs) {
-        B.smem = std::max(B.smem, h->apply_smem);
-        all_smem = all_smem && h->apply_smem > 0 && !h->no_smem;
+        all_bytes = std::max(all_bytes, h->apply_smem);
+        lump_bytes = std::max(lump_bytes, h->apply_lump_smem);
+        all_ok = all_ok && h->apply_smem > 0;
     }
-    if (!all_smem) B.smem = 0;
+    if (!all_ok) all_bytes = 0;
     B.slots = 4;
     for (asm_ctx* h : B.hs) B.slots = std::min(B.slots, h->apply_slots);
-    if (!B.hs.empty()) B.smem = apply_local_vectors(B.nsub, B.smem, B.slots, B.hs[0]->sm_smem, B.hs[0]->n_sms);
+    if (!B.hs.empty())
+        B.apply = apply_local_vectors(B.nsub, all_bytes, lump_bytes, B.slots, B.hs[0]->sm_smem, B.hs[0]->n_sms,
+                                      B.hs[0]->apply_place);
 }
 
 // events bracketing the launch groups of one step: [prep | apply | post | spmv | mgs+finish]
@@ -883,7 +890,7 @@ void launch_local_solves(Batch& B, const SysTab* tab, cudaStream_t st) {
         launch_dense_restrict(tab, B.d_sub.as<SubDesc>(), B.nsub, st);
         launch_dense_apply(tab, B.d_sub.as<SubDesc>(), B.d_dense.as<int2>(), B.ndense, st);
     } else {
-        launch_apply(tab, B.d_sub.as<SubDesc>(), B.nsub, B.prec, B.smem, B.slots, st);
+        launch_apply(tab, B.d_sub.as<SubDesc>(), B.nsub, B.prec, B.apply, B.slots, st);
     }
 }
 
@@ -1592,7 +1599,8 @@ int asm_apply_precond(asm_handle h, const double* r, double* z, int on_device) {
         } else {
             const int nsub = (int)h->sub_desc.size();
             launch_apply(h->d_tab1.as<SysTab>(), h->d_subdesc_single.as<SubDesc>(), nsub, h->prec,
-                         h->no_smem ? 0 : apply_local_vectors(nsub, h->apply_smem, h->apply_slots, h->sm_smem, h->n_sms),
+                         apply_local_vectors(nsub, h->apply_smem, h->apply_lump_smem, h->apply_slots, h->sm_smem,
+                                             h->n_sms, h->apply_place),
                          h->apply_slots, h->stream);
         }
         if (h->tab.cmode != 0)
@@ -1697,10 +1705,13 @@ int asm_get_stats(asm_handle h, asm_stats* st) {
 }
 
 int asm_set_tuning(asm_handle h, int key, int value) {
-    if (!h || value < 0 || value > 1) return ASM_ERR_INVALID_ARG;
+    if (!h || value < 0) return ASM_ERR_INVALID_ARG;
     if (key == ASM_TUNE_APPLY_SMEM) {
-        h->no_smem = value == 0;
+        if (value > 3) return ASM_ERR_INVALID_ARG;
+        static const int place[4] = {Y_DEVICE + 1, 0, Y_LUMPS + 1, Y_SMEM + 1};
+        h->apply_place = place[value];
     } else if (key == ASM_TUNE_COOP_ORTHO) {
+        if (value > 1) return ASM_ERR_INVALID_ARG;
         h->no_coop = value == 0;
     } else {
         return ASM_ERR_INVALID_ARG;

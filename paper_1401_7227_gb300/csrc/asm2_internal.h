@@ -17,10 +17,17 @@ constexpr int VEC_CHUNK = 4096;   // elements per vector work item (256 threads 
 constexpr int kStreamChunk = 8192;   // bytes of one factor-stream chunk / shared-memory ring slot
 constexpr int kStreamSlots = 3;      // default ring slots of the apply (chunks in flight per CTA)
 constexpr int kLongLumpRow = 16;     // lump rows with more stored blocks are swept by a whole warp
-// The apply runs one CTA per subdomain.  With its local vectors in shared memory a CTA has 256
-// threads and two fit on an SM; with them in device memory (L1/L2) a CTA has 128 threads and four
-// fit, which wins once a launch has more subdomains than the shared-memory variant runs at once.
+// The apply runs one CTA per subdomain.  With all its local vectors in shared memory a CTA has 256
+// threads and two fit on an SM; with the fine-row vector in device memory (L1/L2) a CTA has 128
+// threads and four fit, which wins once a launch has more subdomains than the shared-memory variant
+// runs at once.  The lump vector (FP64) and its FP32 mirror then stay in shared memory when four
+// CTAs' worth fit, else they go to device memory too.
 constexpr int kApplyThreadsDev = 128;
+enum ApplyY { Y_SMEM = 0, Y_LUMPS = 1, Y_DEVICE = 2 };  // where the apply's local vectors live
+struct ApplyConfig {
+    int ymode;  // ApplyY
+    int smem;   // dynamic shared memory of the vectors (bytes)
+};
 // Chunk header word 6: bit 0 = last chunk of its wavefront level; bits 8..11 = log2 of the entry
 // slots S of the short lump rows (each such row takes 3 S lanes: 3 output components x S slots).
 constexpr int VEC_THREADS = 256;
@@ -205,13 +212,16 @@ void launch_ell_fill(const double* bsr_vals, const int* ell_loc, long long nnzb,
 void launch_boxsum(const SysTab* st_tab, const BoxItem* items, int nitems, cudaStream_t st);
 // ysmem: shared memory for the local vectors (0 = they stay in the global scratch SubDesc.y);
 // the ring of factor-stream slots is added on top
-void launch_apply(const SysTab* st_tab, const SubDesc* subs, int nsub, int prec, int ysmem, int slots, cudaStream_t st);
+void launch_apply(const SysTab* st_tab, const SubDesc* subs, int nsub, int prec, ApplyConfig cfg, int slots,
+                  cudaStream_t st);
 // shared memory the local vectors of a subdomain need (nf fine rows, nc lump rows), and the ring
-size_t apply_smem_bytes(int nf, int nc, int prec);
-// Local vectors of one apply launch: in shared memory (returns the dynamic shared memory of the
-// vectors, ysmem > 0) while all nsub CTAs run at once at the shared-memory occupancy, else in device
-// memory (returns 0).  ysmem is the largest subdomain's need, sm_smem the shared memory of an SM.
-int apply_local_vectors(int nsub, int ysmem, int slots, int sm_smem, int sms);
+size_t apply_smem_bytes(int nf, int nc, int prec);  // all local vectors of one subdomain
+size_t apply_lump_bytes(int nc, int prec);          // its lump vector and the FP32 mirror
+// Placement of one apply launch's local vectors.  all_bytes / lump_bytes: the largest subdomain's
+// needs (0: not available); force: 0 automatic (all in shared memory while the launch's nsub CTAs
+// run at once at that occupancy, else lumps in shared memory when four CTAs fit, else device
+// memory), Y_SMEM + 1 / Y_LUMPS + 1 / Y_DEVICE + 1 to ask for one placement (taken when it fits).
+ApplyConfig apply_local_vectors(int nsub, int all_bytes, int lump_bytes, int slots, int sm_smem, int sms, int force);
 size_t apply_ring_bytes(int slots);
 void launch_spmv(const SysTab* st_tab, const RowItem* items, int nitems, cudaStream_t st);
 

@@ -448,8 +448,9 @@ __device__ __forceinline__ void restrict_local(const SysTab& st, const SubDesc& 
 // from shared memory, one chunk at a time, with a CTA barrier after each chunk (which also orders
 // the wavefront levels).  Fine rows and lump rows live in separate local vectors (fine rows at the
 // factor precision, lumps in FP64), in shared memory when they fit.
-template <typename TF, bool SMEM_Y, int SLOTS>
-__global__ void __launch_bounds__(SMEM_Y ? 256 : kApplyThreadsDev, SMEM_Y ? 2 : 4) k_apply(const SysTab* __restrict__ tab, const SubDesc* __restrict__ subs) {
+template <typename TF, int YM, int SLOTS>
+__global__ void __launch_bounds__(YM == Y_SMEM ? 256 : kApplyThreadsDev, YM == Y_SMEM ? 2 : 4)
+    k_apply(const SysTab* __restrict__ tab, const SubDesc* __restrict__ subs) {
     using TC = typename Compute<TF>::T;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const SubDesc sd = subs[blockIdx.x];
@@ -462,9 +463,14 @@ __global__ void __launch_bounds__(SMEM_Y ? 256 : kApplyThreadsDev, SMEM_Y ? 2 : 
     unsigned char* ring = smem_raw;
     constexpr int ring_bytes = SLOTS * kStreamChunk;
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + ring_bytes);
-    double* yc = SMEM_Y ? reinterpret_cast<double*>(smem_raw + ring_bytes + kRingHeader) : sd.y;
-    TC* yf = reinterpret_cast<TC*>(yc + 3 * sd.nc);
-    TC* ycf = sizeof(TC) == 8 ? nullptr : yf + 3 * sd.nf;  // FP32 mirror of the lump values
+    // local vectors: lumps (FP64), fine rows (factor precision), FP32 mirror of the lumps; laid out
+    // [yc | yf | ycf] in shared or device memory, or [yc | ycf] in shared memory with yf in device
+    // memory (Y_LUMPS; the device slice keeps the same offsets)
+    double* ysm = reinterpret_cast<double*>(smem_raw + ring_bytes + kRingHeader);
+    double* yc = YM == Y_DEVICE ? sd.y : ysm;
+    TC* yf = YM == Y_LUMPS ? reinterpret_cast<TC*>(sd.y + 3 * sd.nc) : reinterpret_cast<TC*>(yc + 3 * sd.nc);
+    TC* ycf = sizeof(TC) == 8 ? nullptr
+                              : (YM == Y_LUMPS ? reinterpret_cast<TC*>(yc + 3 * sd.nc) : yf + 3 * sd.nf);
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
 
@@ -1194,51 +1200,61 @@ size_t apply_smem_bytes(int nf, int nc, int prec) {
 
 size_t apply_ring_bytes(int slots) { return (size_t)slots * kStreamChunk + kRingHeader; }
 
-int apply_local_vectors(int nsub, int ysmem, int slots, int sm_smem, int sms) {
-    if (ysmem <= 0) return 0;
-    const long long per_cta = (long long)ysmem + (long long)apply_ring_bytes(slots) + 1024;
-    const long long fit = std::min<long long>(2, sm_smem / per_cta);  // 256-thread CTAs: two per SM at most
-    return (long long)nsub <= fit * sms ? ysmem : 0;
+size_t apply_lump_bytes(int nc, int prec) { return prec == 0 ? 24 * (size_t)nc : 36 * (size_t)nc; }
+
+ApplyConfig apply_local_vectors(int nsub, int all_bytes, int lump_bytes, int slots, int sm_smem, int sms, int force) {
+    const long long ring = (long long)apply_ring_bytes(slots) + 1024;
+    const long long fit_all = all_bytes > 0 ? std::min<long long>(2, sm_smem / (all_bytes + ring)) : 0;
+    const bool lumps_fit = lump_bytes > 0 && 4 * (lump_bytes + ring) <= sm_smem;
+    if (force == Y_SMEM + 1) return fit_all >= 1 ? ApplyConfig{Y_SMEM, all_bytes} : ApplyConfig{Y_DEVICE, 0};
+    if (force == Y_LUMPS + 1) return lumps_fit ? ApplyConfig{Y_LUMPS, lump_bytes} : ApplyConfig{Y_DEVICE, 0};
+    if (force == Y_DEVICE + 1) return ApplyConfig{Y_DEVICE, 0};
+    if (fit_all >= 1 && (long long)nsub <= fit_all * sms) return ApplyConfig{Y_SMEM, all_bytes};
+    if (lumps_fit) return ApplyConfig{Y_LUMPS, lump_bytes};
+    return ApplyConfig{Y_DEVICE, 0};
 }
 
 namespace {
-template <typename TF, bool Y, int SLOTS>
+template <typename TF, int YM, int SLOTS>
 void launch_apply_t(const SysTab* tab, const SubDesc* subs, int nsub, int smem, cudaStream_t st) {
     static int configured = -1;
     if (configured < smem) {
-        cudaFuncSetAttribute(k_apply<TF, Y, SLOTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_apply<TF, YM, SLOTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         configured = smem;
     }
-    k_apply<TF, Y, SLOTS><<<nsub, Y ? 256 : kApplyThreadsDev, smem, st>>>(tab, subs);
+    k_apply<TF, YM, SLOTS><<<nsub, YM == Y_SMEM ? 256 : kApplyThreadsDev, smem, st>>>(tab, subs);
 }
-template <typename TF, bool Y>
+template <typename TF, int YM>
 void launch_apply_s(const SysTab* tab, const SubDesc* subs, int nsub, int smem, int slots, cudaStream_t st) {
     if (slots == 2)
-        launch_apply_t<TF, Y, 2>(tab, subs, nsub, smem, st);
+        launch_apply_t<TF, YM, 2>(tab, subs, nsub, smem, st);
     else if (slots == 3)
-        launch_apply_t<TF, Y, 3>(tab, subs, nsub, smem, st);
+        launch_apply_t<TF, YM, 3>(tab, subs, nsub, smem, st);
     else
-        launch_apply_t<TF, Y, 4>(tab, subs, nsub, smem, st);
+        launch_apply_t<TF, YM, 4>(tab, subs, nsub, smem, st);
 }
 template <typename TF>
-void launch_apply_p(const SysTab* tab, const SubDesc* subs, int nsub, int ysmem, int slots, cudaStream_t st) {
+void launch_apply_p(const SysTab* tab, const SubDesc* subs, int nsub, ApplyConfig cfg, int slots, cudaStream_t st) {
     const int ring = (int)apply_ring_bytes(slots);
-    if (ysmem > 0)
-        launch_apply_s<TF, true>(tab, subs, nsub, ring + ysmem, slots, st);
+    if (cfg.ymode == Y_SMEM)
+        launch_apply_s<TF, Y_SMEM>(tab, subs, nsub, ring + cfg.smem, slots, st);
+    else if (cfg.ymode == Y_LUMPS)
+        launch_apply_s<TF, Y_LUMPS>(tab, subs, nsub, ring + cfg.smem, slots, st);
     else
-        launch_apply_s<TF, false>(tab, subs, nsub, ring, slots, st);
+        launch_apply_s<TF, Y_DEVICE>(tab, subs, nsub, ring, slots, st);
 }
 }  // namespace
 
-void launch_apply(const SysTab* tab, const SubDesc* subs, int nsub, int prec, int ysmem, int slots, cudaStream_t st) {
+void launch_apply(const SysTab* tab, const SubDesc* subs, int nsub, int prec, ApplyConfig cfg, int slots,
+                  cudaStream_t st) {
     if (nsub <= 0) return;
     slots = slots < 2 ? 2 : (slots > kMaxSlots ? kMaxSlots : slots);
     if (prec == 0)
-        launch_apply_p<double>(tab, subs, nsub, ysmem, slots, st);
+        launch_apply_p<double>(tab, subs, nsub, cfg, slots, st);
     else if (prec == 1)
-        launch_apply_p<float>(tab, subs, nsub, ysmem, slots, st);
+        launch_apply_p<float>(tab, subs, nsub, cfg, slots, st);
     else
-        launch_apply_p<__half>(tab, subs, nsub, ysmem, slots, st);
+        launch_apply_p<__half>(tab, subs, nsub, cfg, slots, st);
 }
 
 void launch_dense_restrict(const SysTab* tab, const SubDesc* subs, int nsub, cudaStream_t st) {

@@ -303,3 +303,24 @@ def test_device_memory_local_vectors_with_more_lumps_than_fine_rows(prec):
     sol.set_tuning(apply_smem=False)
     np.testing.assert_array_equal(z1, sol.apply(s.b))
     assert rel(z1, pc.apply(s.b)) <= (1e-5 if prec == "fp32" else 1e-2)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_local_vector_placements_agree(prec):
+    """512 subdomains (more than one wave of the shared-memory variant, so the automatic choice is
+    lumps in shared memory): every placement of the apply's local vectors gives the same bits, and
+    the FP64 apply matches the oracle."""
+    g = O.Geometry(32, 32, 4, 16, 16, 2, ov=1)
+    s = synth.grid_jacobian(g.nx, g.ny, g.nz, 12)
+    sol = gpu_solver(g, s, precision=prec)
+    z = sol.apply(s.b)
+    for place in ("device", "lumps", "shared", "auto"):
+        sol.set_tuning(apply_smem=place)
+        np.testing.assert_array_equal(z, sol.apply(s.b))
+    if prec == "fp64":
+        assert rel(z, O.Precond(g, s.row_ptr, s.col_idx, s.vals).apply(s.b)) <= 1e-12
+    x1, i1 = sol.solve(s.b, 1e-8, 2000)
+    sol.set_tuning(apply_smem="device")
+    x2, i2 = sol.solve(s.b, 1e-8, 2000)
+    assert i1 == i2
+    np.testing.assert_array_equal(x1, x2)
