@@ -782,7 +782,7 @@ struct Batch {
     std::vector<asm_ctx*> hs;
     DBuf d_tab, d_vec, d_row, d_box, d_sub, d_gather;
     int nvec = 0, nrow = 0, nbox = 0, nsub = 0, prec = 0, slots = 3;
-    ApplyConfig apply{Y_DEVICE, 0};
+    ApplyConfig apply{Y_DEVICE, 0, 2};
     DBuf d_dense;           // exact local solves: (subdomain item, first owned row of 8)
     int ndense = 0;
     bool exact = false;     // every system of the batch has exact local solves
@@ -890,7 +890,7 @@ void launch_local_solves(Batch& B, const SysTab* tab, cudaStream_t st) {
         launch_dense_restrict(tab, B.d_sub.as<SubDesc>(), B.nsub, st);
         launch_dense_apply(tab, B.d_sub.as<SubDesc>(), B.d_dense.as<int2>(), B.ndense, st);
     } else {
-        launch_apply(tab, B.d_sub.as<SubDesc>(), B.nsub, B.prec, B.apply, B.slots, st);
+        launch_apply(tab, B.d_sub.as<SubDesc>(), B.nsub, B.prec, B.apply, st);
     }
 }
 
@@ -1601,7 +1601,7 @@ int asm_apply_precond(asm_handle h, const double* r, double* z, int on_device) {
             launch_apply(h->d_tab1.as<SysTab>(), h->d_subdesc_single.as<SubDesc>(), nsub, h->prec,
                          apply_local_vectors(nsub, h->apply_smem, h->apply_lump_smem, h->apply_slots, h->sm_smem,
                                              h->n_sms, h->apply_place),
-                         h->apply_slots, h->stream);
+                         h->stream);
         }
         if (h->tab.cmode != 0)
             launch_coarse_apply(h->d_tab1.as<SysTab>(), h->d_row1.as<RowItem>(), h->n_row1,

@@ -27,6 +27,7 @@ enum ApplyY { Y_SMEM = 0, Y_LUMPS = 1, Y_DEVICE = 2 };  // where the apply's loc
 struct ApplyConfig {
     int ymode;  // ApplyY
     int smem;   // dynamic shared memory of the vectors (bytes)
+    int slots;  // factor-stream ring slots (2 for the 128-thread variants: deeper rings gain nothing)
 };
 // Chunk header word 6: bit 0 = last chunk of its wavefront level; bits 8..11 = log2 of the entry
 // slots S of the short lump rows (each such row takes 3 S lanes: 3 output components x S slots).
@@ -212,16 +213,17 @@ void launch_ell_fill(const double* bsr_vals, const int* ell_loc, long long nnzb,
 void launch_boxsum(const SysTab* st_tab, const BoxItem* items, int nitems, cudaStream_t st);
 // ysmem: shared memory for the local vectors (0 = they stay in the global scratch SubDesc.y);
 // the ring of factor-stream slots is added on top
-void launch_apply(const SysTab* st_tab, const SubDesc* subs, int nsub, int prec, ApplyConfig cfg, int slots,
-                  cudaStream_t st);
+void launch_apply(const SysTab* st_tab, const SubDesc* subs, int nsub, int prec, ApplyConfig cfg, cudaStream_t st);
 // shared memory the local vectors of a subdomain need (nf fine rows, nc lump rows), and the ring
 size_t apply_smem_bytes(int nf, int nc, int prec);  // all local vectors of one subdomain
 size_t apply_lump_bytes(int nc, int prec);          // its lump vector and the FP32 mirror
 // Placement of one apply launch's local vectors.  all_bytes / lump_bytes: the largest subdomain's
-// needs (0: not available); force: 0 automatic (all in shared memory while the launch's nsub CTAs
-// run at once at that occupancy, else lumps in shared memory when four CTAs fit, else device
-// memory), Y_SMEM + 1 / Y_LUMPS + 1 / Y_DEVICE + 1 to ask for one placement (taken when it fits).
-ApplyConfig apply_local_vectors(int nsub, int all_bytes, int lump_bytes, int slots, int sm_smem, int sms, int force);
+// needs (0: not available); smem_slots: ring slots of the all-shared-memory variant; force: 0
+// automatic (all in shared memory while the launch's nsub CTAs run at once at that occupancy, else
+// lumps in shared memory when four CTAs fit, else device memory), Y_SMEM + 1 / Y_LUMPS + 1 /
+// Y_DEVICE + 1 to ask for one placement (taken when it fits).
+ApplyConfig apply_local_vectors(int nsub, int all_bytes, int lump_bytes, int smem_slots, int sm_smem, int sms,
+                                int force);
 size_t apply_ring_bytes(int slots);
 void launch_spmv(const SysTab* st_tab, const RowItem* items, int nitems, cudaStream_t st);
 

@@ -1202,16 +1202,17 @@ size_t apply_ring_bytes(int slots) { return (size_t)slots * kStreamChunk + kRing
 
 size_t apply_lump_bytes(int nc, int prec) { return prec == 0 ? 24 * (size_t)nc : 36 * (size_t)nc; }
 
-ApplyConfig apply_local_vectors(int nsub, int all_bytes, int lump_bytes, int slots, int sm_smem, int sms, int force) {
-    const long long ring = (long long)apply_ring_bytes(slots) + 1024;
-    const long long fit_all = all_bytes > 0 ? std::min<long long>(2, sm_smem / (all_bytes + ring)) : 0;
-    const bool lumps_fit = lump_bytes > 0 && 4 * (lump_bytes + ring) <= sm_smem;
-    if (force == Y_SMEM + 1) return fit_all >= 1 ? ApplyConfig{Y_SMEM, all_bytes} : ApplyConfig{Y_DEVICE, 0};
-    if (force == Y_LUMPS + 1) return lumps_fit ? ApplyConfig{Y_LUMPS, lump_bytes} : ApplyConfig{Y_DEVICE, 0};
-    if (force == Y_DEVICE + 1) return ApplyConfig{Y_DEVICE, 0};
-    if (fit_all >= 1 && (long long)nsub <= fit_all * sms) return ApplyConfig{Y_SMEM, all_bytes};
-    if (lumps_fit) return ApplyConfig{Y_LUMPS, lump_bytes};
-    return ApplyConfig{Y_DEVICE, 0};
+ApplyConfig apply_local_vectors(int nsub, int all_bytes, int lump_bytes, int smem_slots, int sm_smem, int sms,
+                                int force) {
+    const long long ring_all = (long long)apply_ring_bytes(smem_slots) + 1024, ring2 = (long long)apply_ring_bytes(2) + 1024;
+    const long long fit_all = all_bytes > 0 ? std::min<long long>(2, sm_smem / (all_bytes + ring_all)) : 0;
+    const bool lumps_fit = lump_bytes > 0 && 4 * (lump_bytes + ring2) <= sm_smem;
+    const ApplyConfig all{Y_SMEM, all_bytes, smem_slots}, lumps{Y_LUMPS, lump_bytes, 2}, dev{Y_DEVICE, 0, 2};
+    if (force == Y_SMEM + 1) return fit_all >= 1 ? all : dev;
+    if (force == Y_LUMPS + 1) return lumps_fit ? lumps : dev;
+    if (force == Y_DEVICE + 1) return dev;
+    if (fit_all >= 1 && (long long)nsub <= fit_all * sms) return all;
+    return lumps_fit ? lumps : dev;
 }
 
 namespace {
@@ -1245,10 +1246,9 @@ void launch_apply_p(const SysTab* tab, const SubDesc* subs, int nsub, ApplyConfi
 }
 }  // namespace
 
-void launch_apply(const SysTab* tab, const SubDesc* subs, int nsub, int prec, ApplyConfig cfg, int slots,
-                  cudaStream_t st) {
+void launch_apply(const SysTab* tab, const SubDesc* subs, int nsub, int prec, ApplyConfig cfg, cudaStream_t st) {
     if (nsub <= 0) return;
-    slots = slots < 2 ? 2 : (slots > kMaxSlots ? kMaxSlots : slots);
+    const int slots = cfg.slots < 2 ? 2 : (cfg.slots > kMaxSlots ? kMaxSlots : cfg.slots);
     if (prec == 0)
         launch_apply_p<double>(tab, subs, nsub, cfg, slots, st);
     else if (prec == 1)
