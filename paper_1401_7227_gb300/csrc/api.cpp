@@ -72,7 +72,8 @@ struct asm_ctx {
     bool has_grid = false, has_matrix = false, has_partition = false;
     Pattern pat;
     int nnzb = 0;
-    DBuf d_ell_val, d_ell_col, d_ell_loc, d_stage;
+    DBuf d_ell_val, d_ell_col, d_ell_loc, d_bsr_rp;
+    DBuf d_bsr_val;  // A's values as 3x3 blocks in BSR order (assembly reads whole blocks from here)
     // partition / symbolic
     Geom geom;
     std::shared_ptr<SysSym> sym;
@@ -80,7 +81,8 @@ struct asm_ctx {
     bool factored = false;
     // device preconditioner data
     DBuf d_bcell, d_cptr, d_cloc, d_cval, d_boxsum;
-    DBuf d_slot, d_dpiv, d_aptr, d_aloc, d_acs;
+    DBuf d_slot, d_dpiv, d_aptr, d_aloc, d_acs, d_along;
+    int n_along = 0;  // slots whose assembly lists are summed by a warp each
     DBuf d_fp;  // factor program arrays (one allocation, see upload_factor_program)
     DBuf d_stream, d_pk_off_f, d_pk_src_f, d_pk_off_c, d_pk_src_c;
     DBuf d_lv, d_rlists, d_y, d_corr_cells, d_corr, d_dev_err;
@@ -155,15 +157,27 @@ void copy_out(asm_ctx* h, void* dst, const void* src, size_t bytes, int on_devic
 
 void fill_ell(asm_ctx* h, const double* vals, int on_device) {
     const size_t vb = (size_t)h->nnzb * 9 * sizeof(double);
-    const double* src = vals;
-    if (!on_device) {
-        if (h->d_stage.bytes < vb) h->d_stage.alloc(vb);
-        copy_in(h, h->d_stage.p, vals, vb, 0);
-        src = h->d_stage.as<double>();
-    }
-    launch_ell_fill(src, h->d_ell_loc.as<int>(), h->nnzb, h->d_ell_val.as<double>(), h->pat.rows_pad, 0, h->stream);
+    if (h->d_bsr_val.bytes < vb) h->d_bsr_val.alloc(vb);
+    copy_in(h, h->d_bsr_val.p, vals, vb, on_device);
+    launch_ell_fill(h->d_bsr_val.as<double>(), h->d_bsr_rp.as<int>(), h->N, h->pat.ell_w, h->d_ell_val.as<double>(),
+                    h->pat.rows_pad, h->stream);
     ck(cudaGetLastError());
     if (!on_device) sync(h);
+}
+
+// BSR block index of an ELL location w * rows_pad + r (slot w of row r holds block rp[r] + w); the
+// sign encoding of subtracted blocks (~) is kept
+int bsr_of_loc(const Pattern& P, int loc) {
+    const bool neg = loc < 0;
+    const int L = neg ? ~loc : loc;
+    const int w = L / P.rows_pad, r = L - w * P.rows_pad;
+    const int e = P.rp[r] + w;
+    return neg ? ~e : e;
+}
+std::vector<int> bsr_of_locs(const Pattern& P, const std::vector<int>& locs) {
+    std::vector<int> out(locs.size());
+    for (size_t i = 0; i < locs.size(); i++) out[i] = bsr_of_loc(P, locs[i]);
+    return out;
 }
 
 // Exact-local-solve work items of an ordered subdomain list: (item index, first of 8 owned rows)
@@ -305,23 +319,28 @@ void upload_symbolic(asm_ctx* h) {
     {
         std::vector<int> aptr;
         aptr.reserve(h->total_slots + 1);
-        std::vector<int> acs;
+        std::vector<int> acs, along;
         acs.reserve(h->total_slots);
         for (int s = 0; s < K; s++) {
             const SubSym& o = S.subs[s];
             for (int t = 0; t < o.nslot; t++) {
                 aptr.push_back((int)(aloc_base[s] + o.aptr[t]));
                 acs.push_back(o.acs[t]);
+                if (o.aptr[t + 1] - o.aptr[t] >= kLongAssembly) along.push_back((int)(h->slot_base[s] + t));
             }
         }
         aptr.push_back((int)aloc_base[K]);
         h->d_aptr.upload(aptr, st);
         h->d_acs.upload(acs, st);
+        h->d_along.upload(along, st);
+        h->n_along = (int)along.size();
         h->d_aloc.alloc((size_t)aloc_base[K] * 4);
         for (int s = 0; s < K; s++)
-            if (!S.subs[s].aloc.empty())
-                ck(cudaMemcpyAsync(h->d_aloc.as<int>() + aloc_base[s], S.subs[s].aloc.data(), S.subs[s].aloc.size() * 4,
-                                   cudaMemcpyHostToDevice, st));
+            if (!S.subs[s].aloc.empty()) {
+                const std::vector<int> a = bsr_of_locs(h->pat, S.subs[s].aloc);
+                ck(cudaMemcpyAsync(h->d_aloc.as<int>() + aloc_base[s], a.data(), a.size() * 4, cudaMemcpyHostToDevice,
+                                   st));
+            }
         sync(h);
     }
     // factor program
@@ -452,7 +471,7 @@ void upload_symbolic(asm_ctx* h) {
     if (S.g.far_mode != 0) {
         h->d_bcell.upload(S.bcell, st);
         h->d_cptr.upload(S.cptr, st);
-        h->d_cloc.upload(S.cloc, st);
+        h->d_cloc.upload(bsr_of_locs(h->pat, S.cloc), st);
         h->d_cval.alloc((size_t)std::max(1, S.nC) * 9 * sizeof(double));
         h->d_boxsum.alloc((size_t)std::max(1, S.nboxes) * 3 * sizeof(double));
         for (int b = 0; b < S.nboxes; b++)
@@ -631,7 +650,7 @@ void coarse_build(asm_ctx* h) {
     kv.reserve(h->pat.ci.size());
     for (int a = 0; a < N; a++)
         for (int e = h->pat.rp[a]; e < h->pat.rp[a + 1]; e++)
-            kv.push_back({(long long)box[a] * nb + box[h->pat.ci[e]], h->pat.ell_loc[e]});
+            kv.push_back({(long long)box[a] * nb + box[h->pat.ci[e]], e});
     std::sort(kv.begin(), kv.end());
     std::vector<int> kptr, kloc(kv.size());
     std::vector<long long> keys;
@@ -683,7 +702,7 @@ void coarse_build(asm_ctx* h) {
 
 // A_C = R_C A R_C^T from the current values, inverted in place; ZERO_PIVOT for a singular A_C
 int coarse_numeric(asm_ctx* h) {
-    launch_coarse(h->d_ckptr.as<int>(), h->d_ckloc.as<int>(), h->d_ell_val.as<double>(), h->pat.rows_pad,
+    launch_coarse(h->d_ckptr.as<int>(), h->d_ckloc.as<int>(), h->d_bsr_val.as<double>(),
                   h->d_cblk.as<double>(), h->cnkeys, h->stream);
     h->d_cerr.zero(h->stream);
     ck(launch_coarse_invert(h->d_ckeys.as<long long>(), h->d_cblk.as<double>(), h->cnkeys, h->cnb,
@@ -710,10 +729,11 @@ int factor_numeric(asm_ctx* h) {
     ck(cudaEventCreate(&e1));
     ck(cudaEventRecord(e0, h->stream));
     if (S.g.far_mode != 0)
-        launch_coarse(h->d_cptr.as<int>(), h->d_cloc.as<int>(), h->d_ell_val.as<double>(), h->pat.rows_pad,
+        launch_coarse(h->d_cptr.as<int>(), h->d_cloc.as<int>(), h->d_bsr_val.as<double>(),
                       h->d_cval.as<double>(), S.nC, h->stream);
-    launch_assemble(h->d_aptr.as<int>(), h->d_aloc.as<int>(), h->d_acs.as<int>(), h->d_ell_val.as<double>(),
-                    h->pat.rows_pad, h->d_cval.as<double>(), h->d_slot.as<double>(), h->total_slots, h->stream);
+    launch_assemble(h->d_aptr.as<int>(), h->d_aloc.as<int>(), h->d_acs.as<int>(), h->d_bsr_val.as<double>(),
+                    h->d_cval.as<double>(), h->d_slot.as<double>(), h->total_slots, h->stream, h->d_along.as<int>(),
+                    h->n_along);
     h->d_err.zero(h->stream);
     const bool exact = h->opt.local_solver == ASM_LOCAL_EXACT;
     if (exact) {
@@ -1104,7 +1124,7 @@ int handle_matrix_view(asm_ctx* h, MatrixView* out) {
 namespace {
 
 size_t ctx_device_bytes(const asm_ctx* h) {
-    const DBuf* bufs[] = {&h->d_ell_val, &h->d_ell_col, &h->d_ell_loc, &h->d_stage, &h->d_bcell, &h->d_cptr, &h->d_cloc,
+    const DBuf* bufs[] = {&h->d_ell_val, &h->d_ell_col, &h->d_ell_loc, &h->d_bsr_val, &h->d_bcell, &h->d_cptr, &h->d_cloc,
                           &h->d_cval, &h->d_boxsum, &h->d_slot, &h->d_dpiv, &h->d_aptr, &h->d_aloc, &h->d_acs, &h->d_fp,
                           &h->d_stream, &h->d_pk_off_f, &h->d_pk_src_f, &h->d_pk_off_c, &h->d_pk_src_c, &h->d_lv,
                           &h->d_rlists, &h->d_y, &h->d_corr_cells, &h->d_corr, &h->d_dev_err, &h->d_factdesc,
@@ -1251,8 +1271,8 @@ int build_ctx(asm_server* S, Req* r, const SymEntry& e, asm_ctx** out) {
         h->d_ell_val.zero(h->stream);
         h->d_ell_col.upload(h->pat.ell_col, h->stream);
         h->d_ell_loc.upload(h->pat.ell_loc, h->stream);
+        h->d_bsr_rp.upload(h->pat.rp, h->stream);
         fill_ell(h, q.vals, 0);
-        h->d_stage.release();
         h->has_matrix = true;
         const int cf[3] = {q.c_far[0], q.c_far[1], q.c_far[2]};
         int s2 = asm_set_partition_boxes(h, q.px, q.py, q.pz, q.overlap, q.near_width, q.c_near, q.far_mode, cf);
@@ -1482,6 +1502,7 @@ int asm_set_matrix_bsr(asm_handle h, int n_cells, int nnzb, const int* row_ptr, 
         h->d_ell_val.zero(h->stream);
         h->d_ell_col.upload(h->pat.ell_col, h->stream);
         h->d_ell_loc.upload(h->pat.ell_loc, h->stream);
+        h->d_bsr_rp.upload(h->pat.rp, h->stream);
         fill_ell(h, vals, on_device);
         sync(h);
         h->has_matrix = true;
@@ -1779,12 +1800,12 @@ int asm_get_local_matrix(asm_handle h, int s, int* row_ptr, int* col_idx, double
         std::vector<int> aptr(o.aptr.begin(), o.aptr.end());
         DBuf dap, dal, dac;
         dap.upload(aptr, h->stream);
-        dal.upload(o.aloc, h->stream);
+        dal.upload(bsr_of_locs(h->pat, o.aloc), h->stream);
         dac.upload(o.acs, h->stream);
         if (h->sym->g.far_mode != 0)
-            launch_coarse(h->d_cptr.as<int>(), h->d_cloc.as<int>(), h->d_ell_val.as<double>(), h->pat.rows_pad,
+            launch_coarse(h->d_cptr.as<int>(), h->d_cloc.as<int>(), h->d_bsr_val.as<double>(),
                           h->d_cval.as<double>(), h->sym->nC, h->stream);
-        launch_assemble(dap.as<int>(), dal.as<int>(), dac.as<int>(), h->d_ell_val.as<double>(), h->pat.rows_pad,
+        launch_assemble(dap.as<int>(), dal.as<int>(), dac.as<int>(), h->d_bsr_val.as<double>(),
                         h->d_cval.as<double>(), tmp.as<double>(), o.nslot, h->stream);
         ck(cudaGetLastError());
         ck(cudaMemcpyAsync(vals, tmp.p, (size_t)o.nslot * 9 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));

@@ -200,15 +200,18 @@ struct FactErr {
 // ---------------------------------------------------------------------------------------------
 // Kernel launchers (kernels.cu)
 // ---------------------------------------------------------------------------------------------
-void launch_assemble(const int* aptr, const int* aloc, const int* acs, const double* ell_val, int rows_pad,
-                     const double* cval, double* slot, long long nslot, cudaStream_t st);
-void launch_coarse(const int* cptr, const int* cloc, const double* ell_val, int rows_pad, double* cval, int nc,
-                   cudaStream_t st);
+// slot values of the local matrices from the array-of-blocks copy of A (lists of BSR block indices,
+// ~index for a subtracted block); slots whose lists hold kLongAssembly or more blocks are
+// summed by a warp each (long_slots, nlong; null: every slot by the per-element kernel)
+constexpr int kLongAssembly = 32;
+void launch_assemble(const int* aptr, const int* aloc, const int* acs, const double* bsr_val, const double* cval,
+                     double* slot, long long nslot, cudaStream_t st, const int* long_slots = nullptr, int nlong = 0);
+void launch_coarse(const int* cptr, const int* cloc, const double* bsr_val, double* cval, int nc, cudaStream_t st);
 void launch_factor(const FactDesc* fd, int nsub, FactErr* err, const int* sub_ids, cudaStream_t st);
 void launch_pack(const long long* off, const int* src, long long n, int prec, unsigned char* stream_base,
                  const double* slot_base, cudaStream_t st);
-void launch_ell_fill(const double* bsr_vals, const int* ell_loc, long long nnzb, double* ell_val, int rows_pad,
-                     int on_device_layout, cudaStream_t st);
+void launch_ell_fill(const double* bsr_vals, const int* row_ptr, int n, int ell_w, double* ell_val, int rows_pad,
+                     cudaStream_t st);
 
 void launch_boxsum(const SysTab* st_tab, const BoxItem* items, int nitems, cudaStream_t st);
 // ysmem: shared memory for the local vectors (0 = they stay in the global scratch SubDesc.y);

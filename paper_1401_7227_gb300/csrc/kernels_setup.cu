@@ -9,26 +9,29 @@ namespace asm2 {
 
 namespace {
 
-__device__ __forceinline__ double ell_at(const double* ell_val, int rows_pad, int loc, int e) {
-    const int w = loc / rows_pad, r = loc - w * rows_pad;
-    return ell_val[((long long)w * 9 + e) * rows_pad + r];
-}
 
-// BSR block e -> ELL slot loc = w * rows_pad + r
-__global__ void k_ell_fill(const double* __restrict__ bsr, const int* __restrict__ loc, long long nnzb,
+// ELL slot w of row r <- BSR block rp[r] + w (the w-th stored block of the row).  Threads run over
+// (w, r) with r fastest, so the nine element planes are written with unit stride across a warp;
+// each thread reads its block's 72 contiguous bytes.  Padding slots keep their zeros.
+__global__ void k_ell_fill(const double* __restrict__ bsr, const int* __restrict__ rp, int n, int ell_w,
                            double* __restrict__ ell, int rows_pad) {
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nnzb * 9) return;
-    long long e = t / 9;
-    int k = (int)(t - e * 9);
-    int L = loc[e];
-    int w = L / rows_pad, r = L - w * rows_pad;
-    ell[((long long)w * 9 + k) * rows_pad + r] = bsr[t];
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)ell_w * n) return;
+    const int w = (int)(t / n), r = (int)(t - (long long)w * n);
+    const int e = rp[r] + w;
+    if (e >= rp[r + 1]) return;
+    const double* b = bsr + 9LL * e;
+    double v[9];
+#pragma unroll
+    for (int k = 0; k < 9; k++) v[k] = b[k];
+#pragma unroll
+    for (int k = 0; k < 9; k++) ell[((long long)w * 9 + k) * rows_pad + r] = v[k];
 }
 
-// C[J, J'] = sum of the blocks of A coupling far box J to far box J' (one CTA per C block)
+// C[J, J'] = sum of the blocks of A coupling far box J to far box J' (one CTA per C block); block
+// lists hold BSR block indices into the array-of-blocks copy of A
 __global__ void k_coarse(const int* __restrict__ cptr, const int* __restrict__ cloc,
-                         const double* __restrict__ ell, int rows_pad, double* __restrict__ cval) {
+                         const double* __restrict__ bsr, double* __restrict__ cval) {
     const int c = blockIdx.x;
     double acc[9];
 #pragma unroll
@@ -36,7 +39,7 @@ __global__ void k_coarse(const int* __restrict__ cptr, const int* __restrict__ c
     for (int i = cptr[c] + threadIdx.x; i < cptr[c + 1]; i += blockDim.x) {
         const int L = cloc[i];
 #pragma unroll
-        for (int e = 0; e < 9; e++) acc[e] += ell_at(ell, rows_pad, L, e);
+        for (int e = 0; e < 9; e++) acc[e] += bsr[9LL * L + e];
     }
     __shared__ double red[9][256];
 #pragma unroll
@@ -53,23 +56,68 @@ __global__ void k_coarse(const int* __restrict__ cptr, const int* __restrict__ c
 
 // slot value = C block (far-far pairs) + signed sum of A blocks from the slot's list
 __global__ void k_assemble(const int* __restrict__ aptr, const int* __restrict__ aloc, const int* __restrict__ acs,
-                           const double* __restrict__ ell, int rows_pad, const double* __restrict__ cval,
-                           double* __restrict__ slot, long long nslot) {
+                           const double* __restrict__ bsr, const double* __restrict__ cval,
+                           double* __restrict__ slot, long long nslot, int long_min) {
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nslot * 9) return;
     long long s = t / 9;
     int e = (int)(t - s * 9);
+    const int i0 = aptr[s], i1 = aptr[s + 1];
+    if (i1 - i0 >= long_min) return;  // a whole warp sums this one (k_assemble_long)
     double acc = 0.0;
     int c = acs[s];
     if (c >= 0) acc = cval[(long long)c * 9 + e];
-    for (int i = aptr[s]; i < aptr[s + 1]; i++) {
+    for (int i = i0; i < i1; i++) {
         int L = aloc[i];
         if (L >= 0)
-            acc += ell_at(ell, rows_pad, L, e);
+            acc += bsr[9LL * L + e];
         else
-            acc -= ell_at(ell, rows_pad, ~L, e);
+            acc -= bsr[9LL * ~L + e];
     }
     slot[t] = acc;
+}
+
+// Slots with long lists (far-lump blocks: the box-pair block minus thousands of near-region
+// couplings): one warp per slot, lanes over the list four entries at a time with the loads issued
+// first, nine partial sums per lane combined by shuffles
+__global__ void __launch_bounds__(256) k_assemble_long(const int* __restrict__ aptr, const int* __restrict__ aloc,
+                                                       const int* __restrict__ acs, const double* __restrict__ bsr,
+                                                       const double* __restrict__ cval,
+                                                       double* __restrict__ slot, const int* __restrict__ long_slots,
+                                                       int nlong) {
+    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (w >= nlong) return;
+    const int s = long_slots[w];
+    const int i0 = aptr[s], i1 = aptr[s + 1];
+    double acc[9];
+#pragma unroll
+    for (int e = 0; e < 9; e++) acc[e] = 0.0;
+    constexpr int kU = 4;
+    for (int b = i0 + lane; b < i1; b += 32 * kU) {
+        int L[kU];
+#pragma unroll
+        for (int u = 0; u < kU; u++) L[u] = b + 32 * u < i1 ? aloc[b + 32 * u] : 0x7fffffff;
+#pragma unroll
+        for (int u = 0; u < kU; u++) {
+            if (L[u] == 0x7fffffff) continue;
+            const int loc = L[u] >= 0 ? L[u] : ~L[u];
+            const double sg = L[u] >= 0 ? 1.0 : -1.0;
+#pragma unroll
+            for (int e = 0; e < 9; e++) acc[e] = fma(sg, bsr[9LL * loc + e], acc[e]);
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 9; e++)
+        for (int o = 16; o > 0; o >>= 1) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
+    if (lane < 9) {
+        double v = 0.0;
+#pragma unroll
+        for (int e = 0; e < 9; e++)
+            if (e == lane) v = acc[e];
+        const int c = acs[s];
+        if (c >= 0) v += cval[(long long)c * 9 + lane];
+        slot[(long long)s * 9 + lane] = v;
+    }
 }
 
 // 3x3 inverse by Gauss-Jordan elimination with partial pivoting; false on a zero pivot.
@@ -94,8 +142,9 @@ __device__ bool inverse3(const double* a, double* inv) {
                 m[c][k] = m[p][k];
                 m[p][k] = t;
             }
-        const double d = m[c][c];
-        for (int k = 0; k < 6; k++) m[c][k] /= d;
+        // one reciprocal per pivot column: FP64 division expands to many FP64-pipe instructions
+        const double id = 1.0 / m[c][c];
+        for (int k = 0; k < 6; k++) m[c][k] *= id;
         for (int r = 0; r < 3; r++) {
             if (r == c) continue;
             const double f = m[r][c];
@@ -118,30 +167,43 @@ __global__ void __launch_bounds__(256) k_factor(const FactDesc* __restrict__ fds
                                                 FactErr* err) {
     const FactDesc fd = fds[ids ? ids[blockIdx.x] : blockIdx.x];
     double* slot = fd.slot;
+    // nine lanes per 3x3 result (lane = 3 r + c within a group), three groups per warp: each FP64
+    // instruction then serves three targets instead of one thread's nine elements
+    const int lane = threadIdx.x & 31, grp = lane / 9, e9 = lane - 9 * grp, er = e9 / 3, ec = e9 - 3 * er;
+    const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const bool lane_on = grp < 3;
     for (int lv = 0; lv < fd.nlev; lv++) {
-        for (int t = fd.tgt_lv[lv] + threadIdx.x; t < fd.tgt_lv[lv + 1]; t += blockDim.x) {
+        for (int t0 = fd.tgt_lv[lv] + 3 * warp; t0 < fd.tgt_lv[lv + 1]; t0 += 3 * nwarp) {
+            const int t = t0 + grp;
+            if (!lane_on || t >= fd.tgt_lv[lv + 1]) continue;
             double* s = slot + (long long)fd.tgt[t] * 9;
-            double acc[9];
+            double acc = s[e9];
+            // kP pairs at a time: their indices, then their blocks, are loaded before any arithmetic
+            // (the pairs are subtracted in the same order as one at a time)
+            constexpr int kP = 4;
+            const int q1 = fd.pp[t + 1];
+            for (int q0 = fd.pp[t]; q0 < q1; q0 += kP) {
+                int2 pr[kP];
 #pragma unroll
-            for (int e = 0; e < 9; e++) acc[e] = s[e];
-            for (int q = fd.pp[t]; q < fd.pp[t + 1]; q++) {
-                const int2 pr = fd.pair[q];
-                const double* L = slot + (long long)pr.x * 9;
-                const double* U = slot + (long long)pr.y * 9;
-                double l[9], u[9];
+                for (int u = 0; u < kP; u++) pr[u] = q0 + u < q1 ? fd.pair[q0 + u] : make_int2(-1, -1);
+                double l[kP][3], uu[kP][3];
 #pragma unroll
-                for (int e = 0; e < 9; e++) {
-                    l[e] = L[e];
-                    u[e] = U[e];
+                for (int u = 0; u < kP; u++) {
+                    const bool on = pr[u].x >= 0;
+                    const double* L = slot + (long long)(on ? pr[u].x : 0) * 9 + 3 * er;
+                    const double* U = slot + (long long)(on ? pr[u].y : 0) * 9 + ec;
+                    l[u][0] = L[0];
+                    l[u][1] = L[1];
+                    l[u][2] = L[2];
+                    uu[u][0] = U[0];
+                    uu[u][1] = U[3];
+                    uu[u][2] = U[6];
                 }
 #pragma unroll
-                for (int r = 0; r < 3; r++)
-#pragma unroll
-                    for (int c = 0; c < 3; c++)
-                        acc[3 * r + c] -= l[3 * r] * u[c] + l[3 * r + 1] * u[3 + c] + l[3 * r + 2] * u[6 + c];
+                for (int u = 0; u < kP; u++)
+                    if (pr[u].x >= 0) acc -= l[u][0] * uu[u][0] + l[u][1] * uu[u][1] + l[u][2] * uu[u][2];
             }
-#pragma unroll
-            for (int e = 0; e < 9; e++) s[e] = acc[e];
+            s[e9] = acc;
         }
         __syncthreads();
         for (int p = fd.lv_pos0[lv] + threadIdx.x; p < fd.lv_pos0[lv + 1]; p += blockDim.x) {
@@ -164,21 +226,19 @@ __global__ void __launch_bounds__(256) k_factor(const FactDesc* __restrict__ fds
             for (int e = 0; e < 9; e++) d[e] = Di[e];
         }
         __syncthreads();
-        for (int t = fd.ls_lv[lv] + threadIdx.x; t < fd.ls_lv[lv + 1]; t += blockDim.x) {
-            const int2 q = fd.ls[t];
-            double* L = slot + (long long)q.x * 9;
-            const double* Di = slot + (long long)q.y * 9;
-            double a[9], di[9];
-#pragma unroll
-            for (int e = 0; e < 9; e++) {
-                a[e] = L[e];
-                di[e] = Di[e];
+        for (int t0 = fd.ls_lv[lv] + 3 * warp; t0 < fd.ls_lv[lv + 1]; t0 += 3 * nwarp) {
+            const int t = t0 + grp;
+            double v = 0.0;
+            int2 q = make_int2(0, 0);
+            const bool on = lane_on && t < fd.ls_lv[lv + 1];
+            if (on) {
+                q = fd.ls[t];
+                const double* A = slot + (long long)q.x * 9 + 3 * er;
+                const double* Di = slot + (long long)q.y * 9 + ec;
+                v = A[0] * Di[0] + A[1] * Di[3] + A[2] * Di[6];
             }
-#pragma unroll
-            for (int r = 0; r < 3; r++)
-#pragma unroll
-                for (int c = 0; c < 3; c++)
-                    L[3 * r + c] = a[3 * r] * di[c] + a[3 * r + 1] * di[3 + c] + a[3 * r + 2] * di[6 + c];
+            __syncwarp();  // every lane of the group has read its row of L before any writes
+            if (on) slot[(long long)q.x * 9 + e9] = v;
         }
         __syncthreads();
     }
@@ -214,22 +274,28 @@ inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1)
 
 }  // namespace
 
-void launch_ell_fill(const double* bsr_vals, const int* ell_loc, long long nnzb, double* ell_val, int rows_pad,
-                     int, cudaStream_t st) {
-    if (nnzb <= 0) return;
-    k_ell_fill<<<blocks_for(nnzb * 9, 256), 256, 0, st>>>(bsr_vals, ell_loc, nnzb, ell_val, rows_pad);
+void launch_ell_fill(const double* bsr_vals, const int* row_ptr, int n, int ell_w, double* ell_val, int rows_pad,
+                     cudaStream_t st) {
+    if (n <= 0 || ell_w <= 0) return;
+    k_ell_fill<<<blocks_for((long long)ell_w * n, 256), 256, 0, st>>>(bsr_vals, row_ptr, n, ell_w, ell_val, rows_pad);
 }
 
-void launch_coarse(const int* cptr, const int* cloc, const double* ell_val, int rows_pad, double* cval, int nc,
+void launch_coarse(const int* cptr, const int* cloc, const double* bsr_val, double* cval, int nc,
                    cudaStream_t st) {
     if (nc <= 0) return;
-    k_coarse<<<nc, 256, 0, st>>>(cptr, cloc, ell_val, rows_pad, cval);
+    k_coarse<<<nc, 256, 0, st>>>(cptr, cloc, bsr_val, cval);
 }
 
-void launch_assemble(const int* aptr, const int* aloc, const int* acs, const double* ell_val, int rows_pad,
-                     const double* cval, double* slot, long long nslot, cudaStream_t st) {
+void launch_assemble(const int* aptr, const int* aloc, const int* acs, const double* bsr_val,
+                     const double* cval, double* slot, long long nslot, cudaStream_t st, const int* long_slots,
+                     int nlong) {
     if (nslot <= 0) return;
-    k_assemble<<<blocks_for(nslot * 9, 256), 256, 0, st>>>(aptr, aloc, acs, ell_val, rows_pad, cval, slot, nslot);
+    const int long_min = long_slots ? kLongAssembly : 0x7fffffff;
+    k_assemble<<<blocks_for(nslot * 9, 256), 256, 0, st>>>(aptr, aloc, acs, bsr_val, cval, slot, nslot,
+                                                           long_min);
+    if (long_slots && nlong > 0)
+        k_assemble_long<<<(nlong + 7) / 8, 256, 0, st>>>(aptr, aloc, acs, bsr_val, cval, slot, long_slots,
+                                                         nlong);
 }
 
 void launch_factor(const FactDesc* fd, int nsub, FactErr* err, const int* sub_ids, cudaStream_t st) {
