@@ -218,7 +218,16 @@ int asm_get_stats(asm_handle h, asm_stats* st);
  *   ASM_TUNE_COOP_ORTHO  1 (default) runs the Gram-Schmidt step of a single-system solve in one
  *                        cooperative launch, 0 in one launch per projection.
  * Errors: INVALID_ARG for an unknown key or value. */
-typedef enum { ASM_TUNE_APPLY_SMEM = 0, ASM_TUNE_COOP_ORTHO = 1 } asm_tune_key;
+typedef enum {
+    ASM_TUNE_APPLY_SMEM = 0,
+    ASM_TUNE_COOP_ORTHO = 1,
+    ASM_TUNE_AUTOTUNE = 2, /* 1 (default): a solve's first apply steps try every placement of the
+                              local vectors that fits (a warm-up round, then a timed round) and
+                              keep the fastest; remembered per handle for single-system solves.
+                              Placements give bitwise equal results.  0: the placement rule only. */
+    ASM_TUNE_GRAPHS = 3    /* 1 (default): batched solves replay each Krylov step as a captured
+                              CUDA graph (one per projection count); 0: plain launches */
+} asm_tune_key;
 int asm_set_tuning(asm_handle h, int key, int value);
 
 /* Profiling switch (0/1): when on, launch groups are bracketed by CUDA events. */

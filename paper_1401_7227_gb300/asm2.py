@@ -300,9 +300,16 @@ class Solver:
         _check(load().asm_get_stats(self._h, C.byref(s)), "stats")
         return s.as_dict()
 
-    def set_tuning(self, apply_smem: bool | str | None = None, coop_ortho: bool | None = None):
+    def set_tuning(self, apply_smem: bool | str | None = None, coop_ortho: bool | None = None,
+                   autotune: bool | None = None, graphs: bool | None = None):
         """apply_smem: True / "auto" (default placement), False / "device", "lumps" (lump vector in
-        shared memory), "shared" (all local vectors in shared memory); see ASM_TUNE_APPLY_SMEM."""
+        shared memory), "shared" (all local vectors in shared memory); see ASM_TUNE_APPLY_SMEM.
+        autotune: the online placement tuner (ASM_TUNE_AUTOTUNE); graphs: CUDA graphs for batched
+        solves (ASM_TUNE_GRAPHS)."""
+        if autotune is not None:
+            _check(load().asm_set_tuning(self._h, 2, int(autotune)), "set_tuning")
+        if graphs is not None:
+            _check(load().asm_set_tuning(self._h, 3, int(graphs)), "set_tuning")
         if apply_smem is not None:
             v = {"device": 0, "auto": 1, "lumps": 2, "shared": 3}[apply_smem] if isinstance(apply_smem, str) \
                 else int(apply_smem)

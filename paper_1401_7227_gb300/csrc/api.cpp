@@ -6,7 +6,9 @@
 #include <cstdio>
 #include <cstring>
 #include <functional>
+#include <map>
 #include <memory>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -111,6 +113,9 @@ struct asm_ctx {
     bool profiling = false;
     bool no_coop = false;  // per-kernel orthogonalisation path instead of the cooperative one
     int apply_place = 0;  // 0 automatic, else ApplyY + 1 (asm_set_tuning ASM_TUNE_APPLY_SMEM)
+    bool no_autotune = false;  // asm_set_tuning ASM_TUNE_AUTOTUNE = 0
+    bool no_graphs = false;    // asm_set_tuning ASM_TUNE_GRAPHS = 0
+    int tuned_ymode = -1;      // placement the online tuner chose for single-system solves (-1: none)
     asm_profile_info prof{};
     // exact local solves (local_solver = ASM_LOCAL_EXACT): [A_i | I] inverted in place per subdomain
     DBuf d_daug, d_dprow, d_dfcol, d_dmats, d_dinit, d_doff, d_dmat_of_slot, d_dpart, d_derr, d_ditems1;
@@ -394,6 +399,7 @@ void upload_symbolic(asm_ctx* h) {
     h->sub_cost.assign(K, 0.0);
     h->apply_smem = 0;
     h->apply_lump_smem = 0;
+    h->tuned_ymode = -1;
     for (int s = 0; s < K; s++) {
         const SubSym& o = S.subs[s];
         if (!o.stream.empty())
@@ -803,6 +809,7 @@ struct Batch {
     DBuf d_tab, d_vec, d_row, d_box, d_sub, d_gather;
     int nvec = 0, nrow = 0, nbox = 0, nsub = 0, prec = 0, slots = 3;
     ApplyConfig apply{Y_DEVICE, 0, 2};
+    int all_bytes = 0, lump_bytes = 0;  // largest subdomain's shared-memory needs (placements)
     DBuf d_dense;           // exact local solves: (subdomain item, first owned row of 8)
     int ndense = 0;
     bool exact = false;     // every system of the batch has exact local solves
@@ -883,6 +890,8 @@ void build_batch(Batch& B, cudaStream_t st) {
         all_ok = all_ok && h->apply_smem > 0;
     }
     if (!all_ok) all_bytes = 0;
+    B.all_bytes = all_bytes;
+    B.lump_bytes = lump_bytes;
     B.slots = 4;
     for (asm_ctx* h : B.hs) B.slots = std::min(B.slots, h->apply_slots);
     if (!B.hs.empty())
@@ -903,6 +912,22 @@ struct StepEvents {
             for (auto& x : e) cudaEventDestroy(x);
     }
 };
+
+// The placements of the apply's local vectors that fit this batch, for the online tuner (one entry
+// when a placement was asked for).  Every placement gives the same bits, so the tuner may try them
+// on the solve's own first steps.
+std::vector<ApplyConfig> apply_candidates(const Batch& B) {
+    std::vector<ApplyConfig> c;
+    if (B.hs.empty() || B.exact) return c;
+    const asm_ctx* h = B.hs[0];
+    if (h->apply_place != 0) return {B.apply};
+    for (int force : {Y_SMEM + 1, Y_LUMPS + 1, Y_DEVICE + 1}) {
+        const ApplyConfig a =
+            apply_local_vectors(B.nsub, B.all_bytes, B.lump_bytes, B.slots, h->sm_smem, h->n_sms, force);
+        if (a.ymode == force - 1) c.push_back(a);
+    }
+    return c;
+}
 
 // the local solves of one apply: fused ILU sweeps, or R_i r and the owned rows of A_i^{-1} R_i r
 void launch_local_solves(Batch& B, const SysTab* tab, cudaStream_t st) {
@@ -1045,8 +1070,33 @@ int run_krylov(std::vector<asm_ctx*>& hs, const double* const* b, double* const*
         for (asm_ctx* h : hs) h->prof.kernel_launches += (B.coop_grid > 0 || om) ? 2 : 3;
     }
     const bool prof = hs[0]->profiling;
+    // online tuner: the first apply steps try each placement of the local vectors (one round to
+    // warm up, one timed); the fastest is kept (and remembered for this handle's next solves)
+    std::vector<ApplyConfig> cand;
+    if (!hs[0]->no_autotune) cand = apply_candidates(B);
+    int tune_total = cand.size() > 1 ? 2 * (int)cand.size() : 0;
+    if (hs.size() == 1 && hs[0]->tuned_ymode >= 0)
+        for (const ApplyConfig& a : cand)
+            if (a.ymode == hs[0]->tuned_ymode) {
+                B.apply = a;
+                tune_total = 0;
+            }
+    std::vector<float> tune_ms(cand.size(), 0.0f);
+    int tune_next = 0, tune_at = -1;
     StepEvents ev;
-    if (prof) ev.create();
+    if (prof || tune_total > 0) ev.create();
+    // CUDA graphs for batches: the launch sequence of a step depends only on the number of
+    // projections, so each is captured once (after one plain run) and replayed
+    bool graphs_ok = hs.size() > 1 && B.coop_grid == 0 && !prof && st != nullptr && !hs[0]->no_graphs;
+    std::map<int, cudaGraphExec_t> graphs;
+    std::map<int, long long> graph_launches;
+    std::set<int> seen;
+    auto plain_step = [&](int kmax, StepEvents* e) {
+        if (om)
+            launch_step_om(B, kmax, st, e);
+        else
+            launch_step(B, kmax, st, e);
+    };
     bool pending = false;
     int pending_applies = 0;
     const int guard_steps = 4 * max_iter + 64;
@@ -1059,6 +1109,17 @@ int run_krylov(std::vector<asm_ctx*>& hs, const double* const* b, double* const*
             P.spmv_ms += elapsed(ev.e[3], ev.e[4]);
             P.apply_launches += pending_applies;
             pending = false;
+        }
+        if (tune_at >= 0) {
+            if (tune_at >= (int)cand.size()) tune_ms[tune_at - cand.size()] = elapsed(ev.e[1], ev.e[2]);
+            tune_at = -1;
+            if (tune_next == tune_total) {
+                int best = 0;
+                for (size_t k = 1; k < cand.size(); k++)
+                    if (tune_ms[k] < tune_ms[best]) best = (int)k;
+                B.apply = cand[best];
+                if (hs.size() == 1) hs[0]->tuned_ymode = B.apply.ymode;
+            }
         }
         int kmax = -1;
         bool any = false;
@@ -1076,12 +1137,52 @@ int run_krylov(std::vector<asm_ctx*>& hs, const double* const* b, double* const*
             const int* c = B.pinned + k * C_NCTL;
             if (c[C_APPLY_IN] >= 0 && c[C_PHASE] != PH_DONE) pending_applies++;
         }
-        if (om)
-            launch_step_om(B, kmax, st, prof ? &ev : nullptr);
-        else
-            launch_step(B, kmax, st, prof ? &ev : nullptr);
-        pending = prof;
+        if (tune_next < tune_total && pending_applies > 0) {
+            B.apply = cand[tune_next % cand.size()];
+            tune_at = tune_next++;
+            plain_step(kmax, &ev);
+            pending = prof;
+        } else if (graphs_ok && tune_next >= tune_total) {
+            auto it = graphs.find(kmax);
+            if (it == graphs.end() && seen.count(kmax)) {
+                // capture this step's launch sequence (its kernels were all launched once before)
+                const long long before = hs[0]->prof.kernel_launches;
+                cudaGraph_t g = nullptr;
+                cudaGraphExec_t ex = nullptr;
+                bool okc = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+                if (okc) {
+                    try {
+                        plain_step(kmax, nullptr);
+                    } catch (const CudaFail&) {
+                        okc = false;
+                    }
+                    okc = cudaStreamEndCapture(st, &g) == cudaSuccess && okc;
+                }
+                if (okc) okc = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+                if (g) cudaGraphDestroy(g);
+                for (asm_ctx* h : hs) h->prof.kernel_launches -= hs[0]->prof.kernel_launches - before;
+                if (okc) {
+                    it = graphs.emplace(kmax, ex).first;
+                    graph_launches[kmax] = hs[0]->prof.kernel_launches - before;
+                } else {
+                    cudaGetLastError();
+                    if (ex) cudaGraphExecDestroy(ex);
+                    graphs_ok = false;
+                }
+            }
+            if (it != graphs.end()) {
+                ck(cudaGraphLaunch(it->second, st));
+                for (asm_ctx* h : hs) h->prof.kernel_launches += graph_launches[kmax];
+            } else {
+                plain_step(kmax, nullptr);
+                seen.insert(kmax);
+            }
+        } else {
+            plain_step(kmax, prof ? &ev : nullptr);
+            pending = prof;
+        }
     }
+    for (auto& g : graphs) cudaGraphExecDestroy(g.second);
     read_ctl(B, st);
     int worst = ASM_OK;
     for (size_t k = 0; k < hs.size(); k++) {
@@ -1731,6 +1832,14 @@ int asm_set_tuning(asm_handle h, int key, int value) {
         if (value > 3) return ASM_ERR_INVALID_ARG;
         static const int place[4] = {Y_DEVICE + 1, 0, Y_LUMPS + 1, Y_SMEM + 1};
         h->apply_place = place[value];
+        h->tuned_ymode = -1;
+    } else if (key == ASM_TUNE_AUTOTUNE) {
+        if (value > 1) return ASM_ERR_INVALID_ARG;
+        h->no_autotune = value == 0;
+        h->tuned_ymode = -1;
+    } else if (key == ASM_TUNE_GRAPHS) {
+        if (value > 1) return ASM_ERR_INVALID_ARG;
+        h->no_graphs = value == 0;
     } else if (key == ASM_TUNE_COOP_ORTHO) {
         if (value > 1) return ASM_ERR_INVALID_ARG;
         h->no_coop = value == 0;

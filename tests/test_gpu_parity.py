@@ -324,3 +324,32 @@ def test_local_vector_placements_agree(prec):
     x2, i2 = sol.solve(s.b, 1e-8, 2000)
     assert i1 == i2
     np.testing.assert_array_equal(x1, x2)
+
+
+def test_graphs_and_online_tuner_leave_results_unchanged():
+    """Batched steps replayed as CUDA graphs and the online placement tuner change no bit of any
+    result; a handle's second solve (with the tuner's remembered choice) repeats its first."""
+    cases = [GEOMS["cfg1"], GEOMS["ragged"], GEOMS["k32"], (O.Geometry(32, 32, 4, 16, 16, 2, ov=1), 12)]
+    systems = [synth.grid_jacobian(g.nx, g.ny, g.nz, seed) for g, seed in cases]
+
+    def batch(**tuning):
+        solvers = []
+        for (g, _), s in zip(cases, systems):
+            sol = gpu_solver(g, s, precision="fp32")
+            sol.set_tuning(**tuning)
+            solvers.append(sol)
+        return asm2.solve_batch(solvers, [s.b for s in systems], 1e-8, 2000)
+
+    ref_x, ref_i = batch(graphs=False, autotune=False)
+    for tuning in ({"graphs": True, "autotune": False}, {"graphs": False, "autotune": True}, {}):
+        xs, infos = batch(**tuning)
+        for a, b_ in zip(xs, ref_x):
+            np.testing.assert_array_equal(a, b_)
+        assert infos == ref_i
+    g, seed = cases[3]
+    s = systems[3]
+    sol = gpu_solver(g, s, precision="fp32")
+    x1, i1 = sol.solve(s.b, 1e-8, 2000)
+    x2, i2 = sol.solve(s.b, 1e-8, 2000)
+    np.testing.assert_array_equal(x1, x2)
+    assert i1 == i2
