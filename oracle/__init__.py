@@ -32,6 +32,8 @@ _LIB_PATH = os.path.join(_BUILD, "liborc.so")
 BILU0_COLSUM = 0
 BILU0 = 1
 DENSE_LU = 2
+NF_COLSUM = 3  # nested factorisation with column-sum compensation (Appendix A, Eq. A.7)
+NF = 4         # nested factorisation, G = D - L1 G^{-1} U1 only (Eq. A.6)
 
 OK, ERR_ARG, ERR_PIVOT, ERR_PATTERN, ERR_NOMEM = 0, -1, -2, -3, -4
 
@@ -92,6 +94,7 @@ def lib():
         L.orc_pc_set_coarse.argtypes = [P, P, P, P, C.c_int, P, C.POINTER(C.c_int)]
         L.orc_pc_coarse_nb.argtypes = [P]
         L.orc_pc_coarse_matrix.argtypes = [P, P, P]
+        L.orc_pc_sub_nf.argtypes = [P, C.c_int, P, P]
         _lib = L
     return _lib
 
@@ -267,6 +270,15 @@ class Precond:
         out = np.empty_like(rhs)
         lib().orc_pc_local_solve(self._h, s, _p(rhs), _p(out))
         return out
+
+    def sub_nf(self, s: int):
+        """Nested factorisation of subdomain s: ((bx, by, bz), G blocks (n, 3, 3)); local cell
+        p = z + bz (x + bx y)."""
+        dims = np.zeros(3, dtype=np.int32)
+        G = np.empty((self.sub_n(s), 3, 3))
+        if lib().orc_pc_sub_nf(self._h, s, _p(dims), _p(G)) != 0:
+            raise ValueError("no nested factorisation for this local solver")
+        return tuple(int(x) for x in dims), G
 
     def coarse_matrix(self):
         """(A_C as a dense (3 nb, 3 nb) array, coarse box of every cell)."""

@@ -1,7 +1,8 @@
 /*
  * Plain, slow, single-threaded FP64 CPU oracle of the two-level ("boundary conditioning")
  * additive Schwarz preconditioner of Jackson, Taroni & Ponting (arXiv:1401.7227), with block
- * ILU(0) + column-sum compensation as the local solver, of the classical two-level and
+ * ILU(0) + column-sum compensation as the local solver (or exact dense LU, or the nested
+ * factorisation of Appendix A on local problems without lumps), of the classical two-level and
  * two-stage coarse-grid corrections it is compared with (Section 3), and of the GMRES and
  * ORTHOMIN accelerators it is used in.
  *
@@ -374,7 +375,7 @@ static int assemble_local(int N, const int* rp, const int* ci, const double* v, 
 /* Local solvers                                                                               */
 /* ------------------------------------------------------------------------------------------ */
 
-enum { ORC_BILU0_COLSUM = 0, ORC_BILU0 = 1, ORC_DENSE_LU = 2 };
+enum { ORC_BILU0_COLSUM = 0, ORC_BILU0 = 1, ORC_DENSE_LU = 2, ORC_NF_COLSUM = 3, ORC_NF = 4 };
 
 /* Right-looking block ILU(0) (Section 2: ILU with zero fill on the 3x3 block structure, the
  * diagonal blocks inverted directly), in place on m.  With colsum != 0, every fill block that
@@ -529,6 +530,264 @@ static void dense_lu_solve(const dense_lu_t* d, const double* rhs, double* x) {
     }
 }
 
+
+/* ------------------------------------------------------------------------------------------ */
+/* Nested factorisation (Appendix A) of a local matrix on a box of bx * by * bz cells           */
+/* ------------------------------------------------------------------------------------------ */
+/* Local cell p = z + bz*(x + bx*y) (the local order of a box without lumps).  The hepta-banded
+ * A = D + L1 + U1 + L2 + U2 + L3 + U3 (Eq. A.1) is held per cell: D[p] = A(p,p), L1[p] = A(p,p-1),
+ * U1[p] = A(p,p+1), L2[p] = A(p,p-bz), U2[p] = A(p,p+bz), L3[p] = A(p,p-S), U3[p] = A(p,p+S),
+ * S = bz*bx (zero blocks where a neighbour is missing).  The preconditioner (Eqs. A.2-A.4) is
+ *   B = (P + L3)(I + P^{-1} U3),  P = (T + L2)(I + T^{-1} U2),  T = (G + L1)(I + G^{-1} U1)
+ * with G block diagonal: G = D - L1 G^{-1} U1 (Eq. A.6), and with colsum (Eq. A.7) also minus the
+ * block column sums of L2 T^{-1} U2 and of L3 P^{-1} U3.  T is block diagonal over the lines of a
+ * plane (each line a block tridiagonal factor), P block diagonal over the planes. */
+typedef struct {
+    int bx, by, bz, n;
+    double *D, *L1, *U1, *L2, *U2, *L3, *U3, *G, *Gi; /* [n*9] each */
+} nf_t;
+
+static void nf_free(nf_t* f) {
+    free(f->D);
+    free(f->L1);
+    free(f->U1);
+    free(f->L2);
+    free(f->U2);
+    free(f->L3);
+    free(f->U3);
+    free(f->G);
+    free(f->Gi);
+    memset(f, 0, sizeof(*f));
+}
+
+static void sub3(double* a, const double* b) { /* a -= b */
+    for (int e = 0; e < 9; e++) a[e] -= b[e];
+}
+static void mulv3_sub(double* y, const double* a, const double* x) { /* y -= a x (3-vectors) */
+    double t[3];
+    mulv3(a, x, t);
+    for (int r = 0; r < 3; r++) y[r] -= t[r];
+}
+
+/* T^{-1} b on the line starting at cell q0 (b, out: 3-vectors of the line's bz cells) */
+static void nf_line_solve(const nf_t* f, int q0, const double* b, double* out) {
+    const int bz = f->bz;
+    double* s = (double*)malloc(sizeof(double) * 3 * (size_t)bz);
+    for (int q = 0; q < bz; q++) { /* (G + L1) s = b */
+        double t[3] = {b[3 * q], b[3 * q + 1], b[3 * q + 2]};
+        if (q > 0) mulv3_sub(t, f->L1 + 9 * (size_t)(q0 + q), s + 3 * (q - 1));
+        mulv3(f->Gi + 9 * (size_t)(q0 + q), t, s + 3 * q);
+    }
+    for (int q = bz - 1; q >= 0; q--) { /* (I + G^{-1} U1) out = s */
+        double t[3] = {s[3 * q], s[3 * q + 1], s[3 * q + 2]};
+        if (q < bz - 1) {
+            double u[3], w[3];
+            mulv3(f->U1 + 9 * (size_t)(q0 + q), out + 3 * (q + 1), u);
+            mulv3(f->Gi + 9 * (size_t)(q0 + q), u, w);
+            for (int r = 0; r < 3; r++) t[r] -= w[r];
+        }
+        for (int r = 0; r < 3; r++) out[3 * q + r] = t[r];
+    }
+    free(s);
+}
+
+/* W = u T^{-1} for a row of 3x3 blocks u over the line starting at q0 (W T = u) */
+static void nf_line_solve_row(const nf_t* f, int q0, const double* u, double* W) {
+    const int bz = f->bz;
+    double* v = (double*)malloc(sizeof(double) * 9 * (size_t)bz);
+    double t[9], t2[9];
+    for (int q = 0; q < bz; q++) { /* v (I + G^{-1} U1) = u */
+        memcpy(v + 9 * q, u + 9 * q, sizeof(double) * 9);
+        if (q > 0) {
+            mul3(v + 9 * (q - 1), f->Gi + 9 * (size_t)(q0 + q - 1), t);
+            mul3(t, f->U1 + 9 * (size_t)(q0 + q - 1), t2);
+            sub3(v + 9 * q, t2);
+        }
+    }
+    for (int q = bz - 1; q >= 0; q--) { /* W (G + L1) = v */
+        memcpy(t, v + 9 * q, sizeof(double) * 9);
+        if (q < bz - 1) {
+            mul3(W + 9 * (q + 1), f->L1 + 9 * (size_t)(q0 + q + 1), t2);
+            sub3(t, t2);
+        }
+        mul3(t, f->Gi + 9 * (size_t)(q0 + q), W + 9 * q);
+    }
+    free(v);
+}
+
+/* P^{-1} b on the plane starting at cell c0 (3-vectors of its S cells) */
+static void nf_plane_solve(const nf_t* f, int c0, const double* b, double* out) {
+    const int bz = f->bz, bx = f->bx, S = bz * bx;
+    double* z = (double*)malloc(sizeof(double) * 3 * (size_t)S);
+    double* t = (double*)malloc(sizeof(double) * 3 * (size_t)bz);
+    double* w = (double*)malloc(sizeof(double) * 3 * (size_t)bz);
+    for (int l = 0; l < bx; l++) { /* (T + L2) z = b */
+        for (int q = 0; q < bz; q++) {
+            const int c = l * bz + q;
+            for (int r = 0; r < 3; r++) t[3 * q + r] = b[3 * c + r];
+            if (l > 0) mulv3_sub(t + 3 * q, f->L2 + 9 * (size_t)(c0 + c), z + 3 * (c - bz));
+        }
+        nf_line_solve(f, c0 + l * bz, t, z + 3 * l * bz);
+    }
+    for (int l = bx - 1; l >= 0; l--) { /* (I + T^{-1} U2) out = z */
+        if (l == bx - 1) {
+            memcpy(out + 3 * l * bz, z + 3 * l * bz, sizeof(double) * 3 * (size_t)bz);
+            continue;
+        }
+        for (int q = 0; q < bz; q++) {
+            const int c = l * bz + q;
+            mulv3(f->U2 + 9 * (size_t)(c0 + c), out + 3 * (c + bz), t + 3 * q);
+        }
+        nf_line_solve(f, c0 + l * bz, t, w);
+        for (int i = 0; i < 3 * bz; i++) out[3 * l * bz + i] = z[3 * l * bz + i] - w[i];
+    }
+    free(z);
+    free(t);
+    free(w);
+}
+
+/* W = u P^{-1} for a row of 3x3 blocks u over the plane starting at c0 (W P = u) */
+static void nf_plane_solve_row(const nf_t* f, int c0, const double* u, double* W) {
+    const int bz = f->bz, bx = f->bx, S = bz * bx;
+    double* v = (double*)malloc(sizeof(double) * 9 * (size_t)S);
+    double* x = (double*)malloc(sizeof(double) * 9 * (size_t)bz);
+    double* y = (double*)malloc(sizeof(double) * 9 * (size_t)bz);
+    double t[9];
+    for (int l = 0; l < bx; l++) { /* v (I + T^{-1} U2) = u: v_l = u_l - (v_{l-1} T^{-1}) U2 */
+        memcpy(v + 9 * (size_t)l * bz, u + 9 * (size_t)l * bz, sizeof(double) * 9 * (size_t)bz);
+        if (l > 0) {
+            nf_line_solve_row(f, c0 + (l - 1) * bz, v + 9 * (size_t)(l - 1) * bz, x);
+            for (int q = 0; q < bz; q++) {
+                mul3(x + 9 * q, f->U2 + 9 * (size_t)(c0 + (l - 1) * bz + q), t);
+                sub3(v + 9 * ((size_t)l * bz + q), t);
+            }
+        }
+    }
+    for (int l = bx - 1; l >= 0; l--) { /* W (T + L2) = v: W_l = (v_l - W_{l+1} L2) T^{-1} */
+        memcpy(y, v + 9 * (size_t)l * bz, sizeof(double) * 9 * (size_t)bz);
+        if (l < bx - 1)
+            for (int q = 0; q < bz; q++) {
+                mul3(W + 9 * ((size_t)(l + 1) * bz + q), f->L2 + 9 * (size_t)(c0 + (l + 1) * bz + q), t);
+                sub3(y + 9 * q, t);
+            }
+        nf_line_solve_row(f, c0 + l * bz, y, W + 9 * (size_t)l * bz);
+    }
+    free(v);
+    free(x);
+    free(y);
+}
+
+/* Factor: the G blocks, plane by plane, line by line, cell by cell (Eqs. A.6 / A.7). */
+static int nf_factor(nf_t* f, int colsum, int* bad_row) {
+    const int bz = f->bz, bx = f->bx, by = f->by, S = bz * bx;
+    double* cs = (double*)calloc(9 * (size_t)S, sizeof(double)); /* colsum terms of one line/plane */
+    double* u = (double*)malloc(sizeof(double) * 9 * (size_t)S);
+    double* W = (double*)malloc(sizeof(double) * 9 * (size_t)S);
+    double t[9], t2[9];
+    for (int j = 0; j < by; j++) {
+        const int c0 = j * S;
+        /* colsum(L3 P^{-1} U3) on plane j: W3 = u3 P_{j-1}^{-1}, u3[c'] = L3[c'+S]; term[c] = W3[c-S] U3[c-S] */
+        double* cs3 = (double*)calloc(9 * (size_t)S, sizeof(double));
+        if (colsum && j > 0) {
+            for (int c = 0; c < S; c++) memcpy(u + 9 * c, f->L3 + 9 * (size_t)(c0 + c), sizeof(double) * 9);
+            nf_plane_solve_row(f, c0 - S, u, W);
+            for (int c = 0; c < S; c++) mul3(W + 9 * c, f->U3 + 9 * (size_t)(c0 - S + c), cs3 + 9 * c);
+        }
+        for (int l = 0; l < bx; l++) {
+            const int q0 = c0 + l * bz;
+            /* colsum(L2 T^{-1} U2) on line l: W2 = u2 T_{l-1}^{-1}, u2[q'] = L2[q'+bz]; term[q] = W2[q-bz] U2[q-bz] */
+            memset(cs, 0, sizeof(double) * 9 * (size_t)bz);
+            if (colsum && l > 0) {
+                for (int q = 0; q < bz; q++) memcpy(u + 9 * q, f->L2 + 9 * (size_t)(q0 + q), sizeof(double) * 9);
+                nf_line_solve_row(f, q0 - bz, u, W);
+                for (int q = 0; q < bz; q++) mul3(W + 9 * q, f->U2 + 9 * (size_t)(q0 - bz + q), cs + 9 * q);
+            }
+            for (int q = 0; q < bz; q++) {
+                const int p = q0 + q;
+                double* G = f->G + 9 * (size_t)p;
+                memcpy(G, f->D + 9 * (size_t)p, sizeof(double) * 9);
+                if (q > 0) { /* - L1 G^{-1} U1 */
+                    mul3(f->L1 + 9 * (size_t)p, f->Gi + 9 * (size_t)(p - 1), t);
+                    mul3(t, f->U1 + 9 * (size_t)(p - 1), t2);
+                    sub3(G, t2);
+                }
+                sub3(G, cs + 9 * q);
+                sub3(G, cs3 + 9 * (size_t)(l * bz + q));
+                if (inv3(G, f->Gi + 9 * (size_t)p)) {
+                    *bad_row = p;
+                    free(cs3);
+                    free(cs);
+                    free(u);
+                    free(W);
+                    return ORC_ERR_PIVOT;
+                }
+            }
+        }
+        free(cs3);
+    }
+    free(cs);
+    free(u);
+    free(W);
+    return ORC_OK;
+}
+
+/* B^{-1} r: (P + L3) y = r plane by plane, then (I + P^{-1} U3) x = y */
+static void nf_solve(const nf_t* f, const double* r, double* x) {
+    const int S = f->bz * f->bx, by = f->by;
+    double* y = (double*)malloc(sizeof(double) * 3 * (size_t)f->n);
+    double* t = (double*)malloc(sizeof(double) * 3 * (size_t)S);
+    double* w = (double*)malloc(sizeof(double) * 3 * (size_t)S);
+    for (int j = 0; j < by; j++) {
+        for (int c = 0; c < S; c++) {
+            for (int k = 0; k < 3; k++) t[3 * c + k] = r[3 * ((size_t)j * S + c) + k];
+            if (j > 0) mulv3_sub(t + 3 * c, f->L3 + 9 * ((size_t)j * S + c), y + 3 * ((size_t)(j - 1) * S + c));
+        }
+        nf_plane_solve(f, j * S, t, y + 3 * (size_t)j * S);
+    }
+    for (int j = by - 1; j >= 0; j--) {
+        if (j == by - 1) {
+            memcpy(x + 3 * (size_t)j * S, y + 3 * (size_t)j * S, sizeof(double) * 3 * (size_t)S);
+            continue;
+        }
+        for (int c = 0; c < S; c++) mulv3(f->U3 + 9 * ((size_t)j * S + c), x + 3 * ((size_t)(j + 1) * S + c), t + 3 * c);
+        nf_plane_solve(f, j * S, t, w);
+        for (int i = 0; i < 3 * S; i++) x[3 * (size_t)j * S + i] = y[3 * (size_t)j * S + i] - w[i];
+    }
+    free(y);
+    free(t);
+    free(w);
+}
+
+/* Bands of a box's local matrix; ORC_ERR_PATTERN if A_s has a block outside the seven bands. */
+static int nf_setup(const bsr_t* A, int bx, int by, int bz, nf_t* f) {
+    f->bx = bx;
+    f->by = by;
+    f->bz = bz;
+    f->n = bx * by * bz;
+    if (f->n != A->n) return ORC_ERR_ARG;
+    double** band[7] = {&f->D, &f->L1, &f->U1, &f->L2, &f->U2, &f->L3, &f->U3};
+    for (int k = 0; k < 7; k++) {
+        *band[k] = (double*)calloc(9 * (size_t)f->n + 1, sizeof(double));
+        if (!*band[k]) return ORC_ERR_NOMEM;
+    }
+    f->G = (double*)calloc(9 * (size_t)f->n + 1, sizeof(double));
+    f->Gi = (double*)calloc(9 * (size_t)f->n + 1, sizeof(double));
+    if (!f->G || !f->Gi) return ORC_ERR_NOMEM;
+    const int S = bz * bx;
+    for (int p = 0; p < f->n; p++)
+        for (int e = A->rp[p]; e < A->rp[p + 1]; e++) {
+            const int d = A->ci[e] - p;
+            double* dst = d == 0 ? f->D : d == -1 ? f->L1 : d == 1 ? f->U1 : d == -bz ? f->L2 : d == bz ? f->U2
+                        : d == -S ? f->L3 : d == S ? f->U3 : NULL;
+            /* a -1/+1 or -bz/+bz offset that wraps to another line/plane is not a band entry */
+            if (dst && (d == -1 || d == 1) && (A->ci[e] / bz != p / bz)) dst = NULL;
+            if (dst && (d == -bz || d == bz) && (A->ci[e] / S != p / S)) dst = NULL;
+            if (!dst) return ORC_ERR_PATTERN;
+            memcpy(dst + 9 * (size_t)p, A->v + 9 * (size_t)e, sizeof(double) * 9);
+        }
+    return ORC_OK;
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* The preconditioner B^{-1} = sum_s P_s R_s^T A_s^{-1} R_s (Eqs. 4.2-4.3, 4.5)               */
 /* ------------------------------------------------------------------------------------------ */
@@ -540,6 +799,7 @@ typedef struct {
     bsr_t LU;       /* ILU factors (solver 0/1) */
     double* dpiv;   /* final pivot blocks (solver 0/1) */
     dense_lu_t dlu; /* solver 2 */
+    nf_t nf;        /* solvers 3/4 */
 } orc_sub;
 
 /* Classical coarse-grid correction (Section 3, Eqs. 3.5-3.8): R_C sums the 3-vectors of each coarse
@@ -571,6 +831,7 @@ static void sub_free(orc_sub* s) {
     free(s->dpiv);
     free(s->dlu.a);
     free(s->dlu.piv);
+    nf_free(&s->nf);
     memset(s, 0, sizeof(*s));
 }
 
@@ -608,7 +869,7 @@ static int bsr_copy(const bsr_t* a, bsr_t* b) {
 orc_pc* orc_pc_create(const orc_geom* g, const int* rp, const int* ci, const double* v, int solver,
                       int only, int* status, int* err_loc) {
     *status = ORC_ERR_ARG;
-    if (!geom_ok(g) || solver < 0 || solver > 2) return NULL;
+    if (!geom_ok(g) || solver < 0 || solver > 4) return NULL;
     orc_pc* pc = (orc_pc*)calloc(1, sizeof(orc_pc));
     pc->g = *g;
     pc->N = g->nx * g->ny * g->nz;
@@ -636,6 +897,15 @@ orc_pc* orc_pc_create(const orc_geom* g, const int* rp, const int* ci, const dou
         int bad = -1;
         if (solver == ORC_DENSE_LU) {
             st = dense_lu_factor(&S->A, &S->dlu, &bad);
+        } else if (solver == ORC_NF_COLSUM || solver == ORC_NF) {
+            /* nested factorisation needs a box without lumps (Appendix A: hepta-banded matrix) */
+            if (S->counts[1] != 0 || S->counts[2] != 0) {
+                st = ORC_ERR_ARG;
+            } else {
+                const box3 F = grow_clip(g, owned_box(g, s), g->ov);
+                st = nf_setup(&S->A, F.hi[0] - F.lo[0], F.hi[1] - F.lo[1], F.hi[2] - F.lo[2], &S->nf);
+                if (!st) st = nf_factor(&S->nf, solver == ORC_NF_COLSUM, &bad);
+            }
         } else {
             st = bsr_copy(&S->A, &S->LU);
             S->dpiv = (double*)malloc(sizeof(double) * 9 * (size_t)(n > 0 ? n : 1));
@@ -673,9 +943,20 @@ void orc_pc_sub_matrix(const orc_pc* pc, int s, int* rp, int* ci, double* v) {
 /* ILU factors in A_s's pattern: L below, U above, D^{-1} on the diagonal; and the pivots D */
 int orc_pc_sub_factors(const orc_pc* pc, int s, double* lu, double* dpiv) {
     const orc_sub* S = &pc->sub[s];
-    if (pc->solver == ORC_DENSE_LU) return ORC_ERR_ARG;
+    if (pc->solver >= ORC_DENSE_LU) return ORC_ERR_ARG;
     memcpy(lu, S->LU.v, sizeof(double) * 9 * (size_t)S->LU.nnz);
     if (dpiv) memcpy(dpiv, S->dpiv, sizeof(double) * 9 * (size_t)S->LU.n);
+    return ORC_OK;
+}
+
+/* Nested factorisation of subdomain s: box dims {bx, by, bz} and the G blocks [n*9] */
+int orc_pc_sub_nf(const orc_pc* pc, int s, int* dims, double* G) {
+    const orc_sub* S = &pc->sub[s];
+    if (pc->solver != ORC_NF_COLSUM && pc->solver != ORC_NF) return ORC_ERR_ARG;
+    dims[0] = S->nf.bx;
+    dims[1] = S->nf.by;
+    dims[2] = S->nf.bz;
+    if (G) memcpy(G, S->nf.G, sizeof(double) * 9 * (size_t)S->nf.n);
     return ORC_OK;
 }
 
@@ -684,6 +965,8 @@ void orc_pc_local_solve(const orc_pc* pc, int s, const double* rhs, double* sol)
     const orc_sub* S = &pc->sub[s];
     if (pc->solver == ORC_DENSE_LU)
         dense_lu_solve(&S->dlu, rhs, sol);
+    else if (pc->solver == ORC_NF_COLSUM || pc->solver == ORC_NF)
+        nf_solve(&S->nf, rhs, sol);
     else
         bilu0_solve(&S->LU, rhs, sol);
 }
