@@ -66,6 +66,15 @@ typedef enum {
                                    Gaussian elimination): every A_i is inverted at asm_factor by
                                    Gauss-Jordan elimination with partial pivoting (FP64 only; at most
                                    4096 local block rows; (3 n_i)^2 * 16 bytes of device memory each) */
+    ,
+    ASM_LOCAL_NF_COLSUM = 3,    /* nested factorisation with column-sum compensation (Appendix A,
+                                   Eqs. A.2-A.4 and A.7): for local problems without lumps only
+                                   (near_width 0 and ASM_FAR_NONE), whose A_i is hepta-banded on the
+                                   box of the fine set, ordered z fastest, then x, then y; FP64 only.
+                                   asm_factor returns ASM_ERR_INVALID_ARG when a local problem has lumps
+                                   and ASM_ERR_PATTERN when an A_i has a block off the seven bands */
+    ASM_LOCAL_NF = 4            /* nested factorisation without compensation: G = D - L1 G^{-1} U1
+                                   (Eq. A.6); same conditions */
 } asm_local_solver;
 
 typedef enum {
@@ -243,7 +252,9 @@ int asm_get_error_location(asm_handle h, int* sub, int* row);
  * counts[3] = {fine cells, near lumps, far lumps}; map[N] = local row of each cell or -1;
  * the local matrix A_s as BSR (row_ptr[n+1], col_idx[nnzb], vals[nnzb*9]); its factors in the
  * same pattern (lu[nnzb*9]: L below, U above, D^{-1} on the diagonal; dpiv[n*9]: pivot blocks),
- * as FP64 before any down-cast of the stored factors.  Any output pointer may be NULL. */
+ * as FP64 before any down-cast of the stored factors.  Any output pointer may be NULL.  With
+ * nested factorisation dpiv receives the diagonal blocks G of Eqs. A.6-A.7 by local row and lu
+ * must be NULL; with exact local solves asm_get_local_factors returns ASM_ERR_INVALID_ARG. */
 int asm_get_local_info(asm_handle h, int s, int* n, int* nnzb, int* counts, int* n_levels);
 int asm_get_local_map(asm_handle h, int s, int* map);
 int asm_get_local_matrix(asm_handle h, int s, int* row_ptr, int* col_idx, double* vals);

@@ -171,6 +171,11 @@ def _current_stream(device: int):
     return torch.cuda.current_stream(device).cuda_stream
 
 
+# local solvers: block ILU(0) with / without column-sum compensation, exact (Gauss-Jordan), and
+# nested factorisation (Appendix A) with / without column-sum compensation (boxes without lumps)
+LOCAL = {"colsum": 0, "plain": 1, "exact": 2, "nf_colsum": 3, "nf": 4}
+
+
 class Solver:
     """One system: grid, BSR 3x3 matrix, partition, factorisation and solves."""
 
@@ -181,7 +186,7 @@ class Solver:
         L.asm_default_options(C.byref(o))
         o.precision = PREC[precision]
         o.restart = restart
-        o.local_solver = {"colsum": 0, "plain": 1, "exact": 2}[local_solver]
+        o.local_solver = LOCAL[local_solver]
         o.flexible = flexible
         o.device = device
         o.krylov = {"gmres": 0, "orthomin": 1}[krylov]
@@ -347,6 +352,13 @@ class Solver:
         v = np.empty((inf["nnzb"], 3, 3))
         _check(load().asm_get_local_matrix(self._h, s, _host_ptr(rp), _host_ptr(ci), _host_ptr(v)), "local_matrix")
         return rp, ci, v
+
+    def nf_diagonal(self, s: int):
+        """Nested factorisation: the diagonal blocks G (Eqs. A.6-A.7) of subdomain s, by local row."""
+        inf = self.local_info(s)
+        g = np.empty((inf["n"], 3, 3))
+        _check(load().asm_get_local_factors(self._h, s, None, _host_ptr(g)), "nf_diagonal")
+        return g
 
     def local_factors(self, s: int):
         inf = self.local_info(s)

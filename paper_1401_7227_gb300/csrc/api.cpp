@@ -122,6 +122,11 @@ struct asm_ctx {
     std::vector<long long> daug_base;            // offset of each subdomain's augmented matrix
     std::vector<std::vector<int>> drow_of_q;     // local row of each dense block row (error location)
     int n_dinit = 0, n_ditems1 = 0, dpart_cap = 0, dmax3 = 0;
+    // nested factorisation (ASM_LOCAL_NF_COLSUM / ASM_LOCAL_NF): band tables, G, G^{-1}, scratch
+    DBuf d_nfint, d_nfval, d_nfdesc1;
+    std::vector<NFDesc> nf_desc;                   // sys = 0
+    std::vector<std::vector<int>> nf_row_of_cell;  // local row of each box cell (error location)
+    std::vector<long long> nf_g_off;               // offset of each subdomain's G in d_nfval
     // classical coarse-grid correction (Eqs. 3.5-3.8)
     int coarse_mode = 0;
     int coarse_c[3] = {0, 0, 0};  // {0,0,0}: partition boxes
@@ -138,6 +143,10 @@ struct asm_ctx {
 };
 
 namespace {
+
+bool is_nf(const asm_ctx* h) {
+    return h->opt.local_solver == ASM_LOCAL_NF_COLSUM || h->opt.local_solver == ASM_LOCAL_NF;
+}
 
 int guard(asm_ctx* h, const std::function<int()>& f) {
     try {
@@ -276,6 +285,122 @@ void upload_dense(asm_ctx* h, cudaStream_t st) {
     h->dpart_cap = 4 * std::max(1, sms);
     h->d_dpart.alloc((size_t)2 * h->dpart_cap * sizeof(double));
     h->d_derr.alloc((size_t)std::max(1, K) * sizeof(int));
+    sync(h);
+}
+
+// Nested factorisation: every local problem must be a box of fine cells (no lumps), whose A_i is
+// then hepta-banded in the box order p = z + bz (x + bx y) (Appendix A, Eq. A.1).  Per subdomain:
+// the slot of each band block of each cell, the cells, the owned cells, and G / G^{-1} / scratch.
+void upload_nf(asm_ctx* h, cudaStream_t st) {
+    const SysSym& S = *h->sym;
+    const Geom& g = S.g;
+    const int K = (int)S.subs.size();
+    struct Part {
+        int bx, by, bz, n, n_own;
+        size_t bands, cell, own;  // int offsets
+        long long g, gi, work;    // double offsets
+    };
+    std::vector<Part> parts(K);
+    std::vector<int> ints;
+    long long nval = 0;
+    h->nf_row_of_cell.assign(K, {});
+    h->nf_g_off.assign(K, 0);
+    for (int s = 0; s < K; s++) {
+        const SubSym& o = S.subs[s];
+        if (o.n != o.nf) {
+            h->last_error = "nested factorisation needs local problems without lumps (near_width 0, far mode none)";
+            throw CudaFail{ASM_ERR_INVALID_ARG};
+        }
+        int lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {-1, -1, -1};
+        std::vector<int> xyz(3 * (size_t)o.n);
+        for (int p = 0; p < o.n; p++) {
+            const int c = o.cells_of_row[o.cells_of_row_ptr[p]];
+            const int v[3] = {(c / g.nz) % g.nx, c / (g.nz * g.nx), c % g.nz};  // x, y, z
+            for (int d = 0; d < 3; d++) {
+                xyz[3 * p + d] = v[d];
+                lo[d] = std::min(lo[d], v[d]);
+                hi[d] = std::max(hi[d], v[d]);
+            }
+        }
+        Part& P = parts[s];
+        P.bx = hi[0] - lo[0] + 1;
+        P.by = hi[1] - lo[1] + 1;
+        P.bz = hi[2] - lo[2] + 1;
+        P.n = o.n;
+        if ((long long)P.bx * P.by * P.bz != o.n) {
+            h->last_error = "nested factorisation: a fine set is not a box";
+            throw CudaFail{ASM_ERR_INVALID_ARG};
+        }
+        const int S2 = P.bx * P.bz;
+        std::vector<int> nat(o.n), cell(o.n), bands(7 * (size_t)o.n, -1);
+        h->nf_row_of_cell[s].assign(o.n, 0);
+        for (int p = 0; p < o.n; p++) {
+            nat[p] = (xyz[3 * p + 2] - lo[2]) + P.bz * ((xyz[3 * p] - lo[0]) + P.bx * (xyz[3 * p + 1] - lo[1]));
+            cell[nat[p]] = o.cells_of_row[o.cells_of_row_ptr[p]];
+            h->nf_row_of_cell[s][nat[p]] = p;
+        }
+        for (int p = 0; p < o.n; p++) {
+            const int a = nat[p];
+            for (int t = o.prp[p]; t < o.prp[p + 1]; t++) {
+                const int b = nat[o.pci[t]], d = b - a;
+                int k = d == 0 ? 0 : d == -1 ? 1 : d == 1 ? 2 : d == -P.bz ? 3 : d == P.bz ? 4 : d == -S2 ? 5
+                      : d == S2 ? 6 : -1;
+                // a +-1 / +-bz offset that crosses into another line / plane is not a band entry
+                if ((k == 1 || k == 2) && b / P.bz != a / P.bz) k = -1;
+                if ((k == 3 || k == 4) && b / S2 != a / S2) k = -1;
+                if (k < 0 || bands[7 * (size_t)a + k] >= 0) {
+                    h->last_error = "nested factorisation: a local matrix is not hepta-banded on its box";
+                    throw CudaFail{ASM_ERR_PATTERN};
+                }
+                bands[7 * (size_t)a + k] = t;
+            }
+            if (bands[7 * (size_t)a] < 0) throw CudaFail{ASM_ERR_PATTERN};
+        }
+        std::vector<int> own(o.own_cell.size());
+        for (size_t i = 0; i < own.size(); i++) {
+            const int c = o.own_cell[i];
+            const int x = (c / g.nz) % g.nx - lo[0], y = c / (g.nz * g.nx) - lo[1], z = c % g.nz - lo[2];
+            own[i] = z + P.bz * (x + P.bx * y);
+            if (own[i] < 0 || own[i] >= o.n || cell[own[i]] != c) throw CudaFail{ASM_ERR_INVALID_ARG};
+        }
+        P.n_own = (int)own.size();
+        P.bands = ints.size();
+        ints.insert(ints.end(), bands.begin(), bands.end());
+        P.cell = ints.size();
+        ints.insert(ints.end(), cell.begin(), cell.end());
+        P.own = ints.size();
+        ints.insert(ints.end(), own.begin(), own.end());
+        P.g = nval;
+        P.gi = P.g + 9LL * o.n;
+        P.work = P.gi + 9LL * o.n;
+        nval = P.work + (long long)nf_work_doubles(P.bx, P.by, P.bz);
+        h->nf_g_off[s] = P.g;
+    }
+    h->d_nfint.upload(ints, st);
+    h->d_nfval.alloc((size_t)std::max<long long>(1, nval) * sizeof(double));
+    h->nf_desc.assign(K, NFDesc{});
+    const int* ib = h->d_nfint.as<int>();
+    double* vb = h->d_nfval.as<double>();
+    for (int s = 0; s < K; s++) {
+        const Part& P = parts[s];
+        NFDesc& d = h->nf_desc[s];
+        d.sys = 0;
+        d.sub = s;
+        d.bx = P.bx;
+        d.by = P.by;
+        d.bz = P.bz;
+        d.n = P.n;
+        d.colsum = h->opt.local_solver == ASM_LOCAL_NF_COLSUM ? 1 : 0;
+        d.n_own = P.n_own;
+        d.slot = h->d_slot.as<double>() + 9 * h->slot_base[s];
+        d.bands = ib + P.bands;
+        d.cell = ib + P.cell;
+        d.own = ib + P.own;
+        d.g = vb + P.g;
+        d.gi = vb + P.gi;
+        d.work = vb + P.work;
+    }
+    h->d_nfdesc1.upload(h->nf_desc, st);
     sync(h);
 }
 
@@ -466,6 +591,7 @@ void upload_symbolic(asm_ctx* h) {
         sync(h);
     }
     if (h->opt.local_solver == ASM_LOCAL_EXACT) upload_dense(h, st);
+    if (is_nf(h)) upload_nf(h, st);
     h->pk_nf = (long long)offf.size();
     h->pk_nc = (long long)offc.size();
     h->d_pk_off_f.upload(offf, st);
@@ -750,6 +876,8 @@ int factor_numeric(asm_ctx* h) {
         h->d_derr.zero(h->stream);
         ck(launch_gj_run(h->d_dmats.as<GJMat>(), K, h->dmax3, h->d_dpart.as<double>(), h->dpart_cap,
                          h->d_derr.as<int>(), h->device, h->stream));
+    } else if (is_nf(h)) {
+        launch_nf_factor(h->d_nfdesc1.as<NFDesc>(), (int)h->nf_desc.size(), h->d_err.as<FactErr>(), h->stream);
     } else {
         launch_factor(h->d_factdesc.as<FactDesc>(), (int)S.subs.size(), h->d_err.as<FactErr>(), nullptr, h->stream);
         launch_pack(h->d_pk_off_f.as<long long>(), h->d_pk_src_f.as<int>(), h->pk_nf, h->prec,
@@ -781,6 +909,9 @@ int factor_numeric(asm_ctx* h) {
     h->factor_ms = ms;
     h->prof.factor_ms += ms;
     h->prof.kernel_launches += 5;
+    if (fe.flag && is_nf(h) && fe.sub >= 0 && fe.sub < (int)h->nf_row_of_cell.size() && fe.row >= 0 &&
+        fe.row < (int)h->nf_row_of_cell[fe.sub].size())
+        fe.row = h->nf_row_of_cell[fe.sub][fe.row];  // box cell -> local row
     if (fe.flag) {
         h->err_sub = fe.sub;
         h->err_row = fe.row;
@@ -813,6 +944,9 @@ struct Batch {
     DBuf d_dense;           // exact local solves: (subdomain item, first owned row of 8)
     int ndense = 0;
     bool exact = false;     // every system of the batch has exact local solves
+    DBuf d_nf;              // nested factorisation: every system's subdomains
+    int nnf = 0;
+    bool nf = false;        // every system of the batch has nested-factorisation local solves
     DBuf d_cbox, d_cgrow;   // coarse-correction work items of the systems that have one
     int ncbox = 0, ncgrow = 0;
     bool two_stage = false;
@@ -843,6 +977,18 @@ void build_batch(Batch& B, cudaStream_t st) {
     }
     sd = longest_first(B.hs);
     B.exact = !B.hs.empty() && B.hs[0]->opt.local_solver == ASM_LOCAL_EXACT;
+    B.nf = !B.hs.empty() && is_nf(B.hs[0]);
+    if (B.nf) {
+        std::vector<NFDesc> nd;
+        for (int k = 0; k < (int)B.hs.size(); k++)
+            for (NFDesc d : B.hs[k]->nf_desc) {
+                d.sys = k;
+                nd.push_back(d);
+            }
+        std::stable_sort(nd.begin(), nd.end(), [](const NFDesc& a, const NFDesc& b) { return a.n > b.n; });
+        B.d_nf.upload(nd, st);
+        B.nnf = (int)nd.size();
+    }
     if (B.exact) {
         const std::vector<int2> di = dense_items(sd);
         B.d_dense.upload(di, st);
@@ -918,7 +1064,7 @@ struct StepEvents {
 // on the solve's own first steps.
 std::vector<ApplyConfig> apply_candidates(const Batch& B) {
     std::vector<ApplyConfig> c;
-    if (B.hs.empty() || B.exact) return c;
+    if (B.hs.empty() || B.exact || B.nf) return c;
     const asm_ctx* h = B.hs[0];
     if (h->apply_place != 0) return {B.apply};
     for (int force : {Y_SMEM + 1, Y_LUMPS + 1, Y_DEVICE + 1}) {
@@ -931,7 +1077,9 @@ std::vector<ApplyConfig> apply_candidates(const Batch& B) {
 
 // the local solves of one apply: fused ILU sweeps, or R_i r and the owned rows of A_i^{-1} R_i r
 void launch_local_solves(Batch& B, const SysTab* tab, cudaStream_t st) {
-    if (B.exact) {
+    if (B.nf) {
+        launch_nf_apply(tab, B.d_nf.as<NFDesc>(), B.nnf, st);
+    } else if (B.exact) {
         launch_dense_restrict(tab, B.d_sub.as<SubDesc>(), B.nsub, st);
         launch_dense_apply(tab, B.d_sub.as<SubDesc>(), B.d_dense.as<int2>(), B.ndense, st);
     } else {
@@ -1539,8 +1687,8 @@ int asm_create(asm_handle* out, const asm_options* opt, void* cuda_stream) {
     asm_default_options(&o);
     if (opt) o = *opt;
     if (o.precision < 0 || o.precision > 2 || o.krylov < 0 || o.krylov > 1 || o.restart < 1 || o.restart > 512 ||
-        o.local_solver < 0 || o.local_solver > 2 || o.flexible < -1 || o.flexible > 1 ||
-        (o.local_solver == ASM_LOCAL_EXACT && o.precision != ASM_PREC_FP64))
+        o.local_solver < 0 || o.local_solver > 4 || o.flexible < -1 || o.flexible > 1 ||
+        (o.local_solver >= ASM_LOCAL_EXACT && o.precision != ASM_PREC_FP64))
         return ASM_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
@@ -1713,7 +1861,9 @@ int asm_apply_precond(asm_handle h, const double* r, double* z, int on_device) {
         copy_in(h, in, r, bytes, on_device);
         set_ctl(h, VU, VZ, -1, -1, -1);
         launch_boxsum(h->d_tab1.as<SysTab>(), h->d_box1.as<BoxItem>(), (int)h->box_items.size(), h->stream);
-        if (h->opt.local_solver == ASM_LOCAL_EXACT) {
+        if (is_nf(h)) {
+            launch_nf_apply(h->d_tab1.as<SysTab>(), h->d_nfdesc1.as<NFDesc>(), (int)h->nf_desc.size(), h->stream);
+        } else if (h->opt.local_solver == ASM_LOCAL_EXACT) {
             launch_dense_restrict(h->d_tab1.as<SysTab>(), h->d_subdesc_single.as<SubDesc>(), (int)h->sub_desc.size(),
                                   h->stream);
             launch_dense_apply(h->d_tab1.as<SysTab>(), h->d_subdesc_single.as<SubDesc>(), h->d_ditems1.as<int2>(),
@@ -1783,7 +1933,8 @@ int asm_solve_batch(asm_handle* hs, int n, const double* const* b, double* const
         if (!h->factored) return ASM_ERR_STATE;
         if (h->device != v[0]->device || h->stream != v[0]->stream || h->prec != v[0]->prec ||
             h->opt.krylov != v[0]->opt.krylov ||
-            (h->opt.local_solver == ASM_LOCAL_EXACT) != (v[0]->opt.local_solver == ASM_LOCAL_EXACT))
+            (h->opt.local_solver == ASM_LOCAL_EXACT) != (v[0]->opt.local_solver == ASM_LOCAL_EXACT) ||
+            is_nf(h) != is_nf(v[0]))
             return ASM_ERR_INVALID_ARG;
     }
     for (int i = 0; i < n; i++)
@@ -1926,8 +2077,21 @@ int asm_get_local_matrix(asm_handle h, int s, int* row_ptr, int* col_idx, double
 int asm_get_local_factors(asm_handle h, int s, double* lu, double* dpiv) {
     if (!h || !h->sym_valid || s < 0 || s >= (int)h->sym->subs.size()) return ASM_ERR_INVALID_ARG;
     if (h->opt.local_solver == ASM_LOCAL_EXACT) return ASM_ERR_INVALID_ARG;  // no ILU factors
+    if (is_nf(h) && lu) return ASM_ERR_INVALID_ARG;                          // G blocks only
     if (!h->factored) return ASM_ERR_STATE;
     const SubSym& o = h->sym->subs[s];
+    if (is_nf(h)) {
+        if (!dpiv) return ASM_OK;
+        return guard(h, [&]() -> int {  // G of every box cell, by local row
+            std::vector<double> G(9 * (size_t)o.n);
+            ck(cudaMemcpyAsync(G.data(), h->d_nfval.as<double>() + h->nf_g_off[s], G.size() * sizeof(double),
+                               cudaMemcpyDeviceToHost, h->stream));
+            sync(h);
+            for (int c = 0; c < o.n; c++)
+                std::memcpy(dpiv + 9 * (size_t)h->nf_row_of_cell[s][c], G.data() + 9 * (size_t)c, 9 * sizeof(double));
+            return ASM_OK;
+        });
+    }
     return guard(h, [&]() -> int {
         if (lu)
             ck(cudaMemcpyAsync(lu, h->d_slot.as<double>() + h->slot_base[s] * 9, (size_t)o.nslot * 9 * sizeof(double),

@@ -197,6 +197,23 @@ struct FactErr {
     int flag, sub, row, pad_;
 };
 
+// One subdomain of the nested-factorisation local solver (Appendix A): a local problem without
+// lumps, i.e. the box of bx * by * bz fine cells, local cell p = z + bz (x + bx y).
+struct NFDesc {
+    int sys;
+    int sub;          // subdomain index (error location)
+    int bx, by, bz, n;
+    int colsum;       // Eq. A.7 (1) or Eq. A.6 alone (0)
+    int n_own;
+    const double* slot;  // the subdomain's assembled blocks of A_i (9 doubles each)
+    const int* bands;    // [7 n]: slot of D, L1, U1, L2, U2, L3, U3 in cell p's row, or -1
+    const int* cell;     // [n] grid cell of each local cell
+    const int* own;      // [n_own] local cells this subdomain owns
+    double* g;           // [9 n] the diagonal blocks G
+    double* gi;          // [9 n] their inverses
+    double* work;        // nf_work_doubles(bx, by, bz) doubles of scratch
+};
+
 // ---------------------------------------------------------------------------------------------
 // Kernel launchers (kernels.cu)
 // ---------------------------------------------------------------------------------------------
@@ -255,6 +272,11 @@ void launch_dense_scatter(const double* slot, const long long* off, const int* m
 // (items: (subdomain work item, first of 8 owned rows)) written to the apply output
 void launch_dense_restrict(const SysTab* tab, const SubDesc* subs, int nsub, cudaStream_t st);
 void launch_dense_apply(const SysTab* tab, const SubDesc* subs, const int2* items, int nitems, cudaStream_t st);
+// Nested factorisation: G and G^{-1} of every subdomain (one warp each; *err gets the first
+// singular G), and the apply z[owned] = (B_i^{-1} R_i r)[owned]
+size_t nf_work_doubles(int bx, int by, int bz);
+void launch_nf_factor(const NFDesc* descs, int ndesc, FactErr* err, cudaStream_t st);
+void launch_nf_apply(const SysTab* tab, const NFDesc* descs, int ndesc, cudaStream_t st);
 void launch_om(const SysTab* tab, const VecItem* items, int nitems, int l, cudaStream_t st);
 void launch_om_update(const SysTab* tab, const VecItem* items, int nitems, cudaStream_t st);
 // Coarse-grid correction: [A_C | I] from the box-pair blocks, then in-place Gauss-Jordan (one
