@@ -70,9 +70,13 @@ typedef enum {
     ASM_LOCAL_NF_COLSUM = 3,    /* nested factorisation with column-sum compensation (Appendix A,
                                    Eqs. A.2-A.4 and A.7): for local problems without lumps only
                                    (near_width 0 and ASM_FAR_NONE), whose A_i is hepta-banded on the
-                                   box of the fine set, ordered z fastest, then x, then y; FP64 only.
-                                   asm_factor returns ASM_ERR_INVALID_ARG when a local problem has lumps
-                                   and ASM_ERR_PATTERN when an A_i has a block off the seven bands */
+                                   box of the fine set, ordered z fastest, then x, then y.  G is always
+                                   computed in FP64; the apply runs in FP64 (ASM_PREC_FP64) or in FP32
+                                   (ASM_PREC_FP32; ASM_PREC_FP16S is refused at asm_create).  asm_factor
+                                   returns ASM_ERR_INVALID_ARG when a local problem has lumps or a line of
+                                   a fine box (its z extent) is too long for the apply's shared memory
+                                   (about 200 cells in FP64, 400 in FP32), and ASM_ERR_PATTERN when an
+                                   A_i has a block off the seven bands */
     ASM_LOCAL_NF = 4            /* nested factorisation without compensation: G = D - L1 G^{-1} U1
                                    (Eq. A.6); same conditions */
 } asm_local_solver;

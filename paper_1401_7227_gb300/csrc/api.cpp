@@ -123,7 +123,9 @@ struct asm_ctx {
     std::vector<std::vector<int>> drow_of_q;     // local row of each dense block row (error location)
     int n_dinit = 0, n_ditems1 = 0, dpart_cap = 0, dmax3 = 0;
     // nested factorisation (ASM_LOCAL_NF_COLSUM / ASM_LOCAL_NF): band tables, G, G^{-1}, scratch
-    DBuf d_nfint, d_nfval, d_nfdesc1;
+    DBuf d_nfint, d_nfval, d_nfdesc1, d_nfpack, d_nfy;
+    size_t nf_smem = 0;                            // shared memory of the apply launch
+    int nf_slots = 2, nf_bx_max = 0, nf_bz_max = 0;  // its ring depth; the largest line and plane
     std::vector<NFDesc> nf_desc;                   // sys = 0
     std::vector<std::vector<int>> nf_row_of_cell;  // local row of each box cell (error location)
     std::vector<long long> nf_g_off;               // offset of each subdomain's G in d_nfval
@@ -296,13 +298,16 @@ void upload_nf(asm_ctx* h, cudaStream_t st) {
     const Geom& g = S.g;
     const int K = (int)S.subs.size();
     struct Part {
-        int bx, by, bz, n, n_own;
-        size_t bands, cell, own;  // int offsets
-        long long g, gi, work;    // double offsets
+        int bx, by, bz, n, c0;
+        int lo[3], olo[3], ohi[3];
+        size_t bands;                         // int offset
+        long long g, gi, work, pack, yv;      // double / byte offsets
     };
     std::vector<Part> parts(K);
     std::vector<int> ints;
-    long long nval = 0;
+    long long nval = 0, npack = 0, ny = 0;
+    h->nf_smem = 0;
+    h->nf_bx_max = h->nf_bz_max = 0;
     h->nf_row_of_cell.assign(K, {});
     h->nf_g_off.assign(K, 0);
     for (int s = 0; s < K; s++) {
@@ -356,28 +361,52 @@ void upload_nf(asm_ctx* h, cudaStream_t st) {
             }
             if (bands[7 * (size_t)a] < 0) throw CudaFail{ASM_ERR_PATTERN};
         }
-        std::vector<int> own(o.own_cell.size());
-        for (size_t i = 0; i < own.size(); i++) {
-            const int c = o.own_cell[i];
-            const int x = (c / g.nz) % g.nx - lo[0], y = c / (g.nz * g.nx) - lo[1], z = c % g.nz - lo[2];
-            own[i] = z + P.bz * (x + P.bx * y);
-            if (own[i] < 0 || own[i] >= o.n || cell[own[i]] != c) throw CudaFail{ASM_ERR_INVALID_ARG};
+        // the owned cells form a box: its local bounds, checked against the owned-cell list
+        for (int d = 0; d < 3; d++) {
+            P.lo[d] = lo[d];
+            P.olo[d] = INT32_MAX;
+            P.ohi[d] = -1;
         }
-        P.n_own = (int)own.size();
+        for (const int c : o.own_cell) {
+            const int v[3] = {(c / g.nz) % g.nx - lo[0], c / (g.nz * g.nx) - lo[1], c % g.nz - lo[2]};
+            for (int d = 0; d < 3; d++) {
+                P.olo[d] = std::min(P.olo[d], v[d]);
+                P.ohi[d] = std::max(P.ohi[d], v[d] + 1);
+            }
+        }
+        if ((long long)(P.ohi[0] - P.olo[0]) * (P.ohi[1] - P.olo[1]) * (P.ohi[2] - P.olo[2]) != (long long)o.own_cell.size())
+            throw CudaFail{ASM_ERR_INVALID_ARG};
+        P.c0 = cell[0];
         P.bands = ints.size();
         ints.insert(ints.end(), bands.begin(), bands.end());
-        P.cell = ints.size();
-        ints.insert(ints.end(), cell.begin(), cell.end());
-        P.own = ints.size();
-        ints.insert(ints.end(), own.begin(), own.end());
         P.g = nval;
         P.gi = P.g + 9LL * o.n;
         P.work = P.gi + 9LL * o.n;
         nval = P.work + (long long)nf_work_doubles(P.bx, P.by, P.bz);
         h->nf_g_off[s] = P.g;
+        const size_t lb = nf_line_bytes(P.bz, h->prec);
+        P.pack = npack;
+        npack += (long long)(lb * (size_t)P.bx * P.by + 255) / 256 * 256;
+        P.yv = ny;
+        ny += (3LL * o.n * (h->prec == 0 ? 8 : 4) + 255) / 256 * 256;
+        h->nf_bx_max = std::max(h->nf_bx_max, P.bx);
+        h->nf_bz_max = std::max(h->nf_bz_max, P.bz);
+    }
+    int dev_smem = 0, sm_smem = 0, sms = 0;
+    ck(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    ck(cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device));
+    ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    h->nf_slots = nf_apply_slots(K, h->nf_bx_max, h->nf_bz_max, h->prec, sm_smem, sms, dev_smem);
+    h->nf_smem = nf_apply_smem(h->nf_bx_max, h->nf_bz_max, h->prec, h->nf_slots);
+    if (h->nf_smem > (size_t)dev_smem) {
+        h->last_error = "nested factorisation: a line of the fine boxes is too long for the apply's shared memory";
+        throw CudaFail{ASM_ERR_INVALID_ARG};
     }
     h->d_nfint.upload(ints, st);
     h->d_nfval.alloc((size_t)std::max<long long>(1, nval) * sizeof(double));
+    h->d_nfpack.alloc((size_t)std::max<long long>(256, npack));
+    h->d_nfpack.zero(st);
+    h->d_nfy.alloc((size_t)std::max<long long>(256, ny));
     h->nf_desc.assign(K, NFDesc{});
     const int* ib = h->d_nfint.as<int>();
     double* vb = h->d_nfval.as<double>();
@@ -391,14 +420,21 @@ void upload_nf(asm_ctx* h, cudaStream_t st) {
         d.bz = P.bz;
         d.n = P.n;
         d.colsum = h->opt.local_solver == ASM_LOCAL_NF_COLSUM ? 1 : 0;
-        d.n_own = P.n_own;
+        d.c0 = P.c0;
+        d.gnz = g.nz;
+        d.gnx = g.nx;
+        for (int k = 0; k < 3; k++) {
+            d.own_lo[k] = P.olo[k];
+            d.own_hi[k] = P.ohi[k];
+        }
+        d.line_bytes = (int)nf_line_bytes(P.bz, h->prec);
         d.slot = h->d_slot.as<double>() + 9 * h->slot_base[s];
         d.bands = ib + P.bands;
-        d.cell = ib + P.cell;
-        d.own = ib + P.own;
         d.g = vb + P.g;
         d.gi = vb + P.gi;
         d.work = vb + P.work;
+        d.pack = h->d_nfpack.as<unsigned char>() + P.pack;
+        d.yv = h->d_nfy.as<unsigned char>() + P.yv;
     }
     h->d_nfdesc1.upload(h->nf_desc, st);
     sync(h);
@@ -877,7 +913,10 @@ int factor_numeric(asm_ctx* h) {
         ck(launch_gj_run(h->d_dmats.as<GJMat>(), K, h->dmax3, h->d_dpart.as<double>(), h->dpart_cap,
                          h->d_derr.as<int>(), h->device, h->stream));
     } else if (is_nf(h)) {
-        launch_nf_factor(h->d_nfdesc1.as<NFDesc>(), (int)h->nf_desc.size(), h->d_err.as<FactErr>(), h->stream);
+        int nmax = 0;
+        for (const NFDesc& d : h->nf_desc) nmax = std::max(nmax, d.n);
+        launch_nf_factor(h->d_nfdesc1.as<NFDesc>(), (int)h->nf_desc.size(), nmax, h->prec, h->d_err.as<FactErr>(),
+                         h->stream);
     } else {
         launch_factor(h->d_factdesc.as<FactDesc>(), (int)S.subs.size(), h->d_err.as<FactErr>(), nullptr, h->stream);
         launch_pack(h->d_pk_off_f.as<long long>(), h->d_pk_src_f.as<int>(), h->pk_nf, h->prec,
@@ -946,6 +985,8 @@ struct Batch {
     bool exact = false;     // every system of the batch has exact local solves
     DBuf d_nf;              // nested factorisation: every system's subdomains
     int nnf = 0;
+    size_t nf_smem = 0;
+    int nf_slots = 2;
     bool nf = false;        // every system of the batch has nested-factorisation local solves
     DBuf d_cbox, d_cgrow;   // coarse-correction work items of the systems that have one
     int ncbox = 0, ncgrow = 0;
@@ -980,14 +1021,23 @@ void build_batch(Batch& B, cudaStream_t st) {
     B.nf = !B.hs.empty() && is_nf(B.hs[0]);
     if (B.nf) {
         std::vector<NFDesc> nd;
-        for (int k = 0; k < (int)B.hs.size(); k++)
+        int bxm = 0, bzm = 0;
+        for (int k = 0; k < (int)B.hs.size(); k++) {
+            bxm = std::max(bxm, B.hs[k]->nf_bx_max);
+            bzm = std::max(bzm, B.hs[k]->nf_bz_max);
             for (NFDesc d : B.hs[k]->nf_desc) {
                 d.sys = k;
                 nd.push_back(d);
             }
+        }
         std::stable_sort(nd.begin(), nd.end(), [](const NFDesc& a, const NFDesc& b) { return a.n > b.n; });
         B.d_nf.upload(nd, st);
         B.nnf = (int)nd.size();
+        asm_ctx* h0 = B.hs[0];
+        int dev_smem = 0;
+        ck(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h0->device));
+        B.nf_slots = nf_apply_slots(B.nnf, bxm, bzm, B.hs[0]->prec, h0->sm_smem, h0->n_sms, dev_smem);
+        B.nf_smem = nf_apply_smem(bxm, bzm, B.hs[0]->prec, B.nf_slots);
     }
     if (B.exact) {
         const std::vector<int2> di = dense_items(sd);
@@ -1078,7 +1128,7 @@ std::vector<ApplyConfig> apply_candidates(const Batch& B) {
 // the local solves of one apply: fused ILU sweeps, or R_i r and the owned rows of A_i^{-1} R_i r
 void launch_local_solves(Batch& B, const SysTab* tab, cudaStream_t st) {
     if (B.nf) {
-        launch_nf_apply(tab, B.d_nf.as<NFDesc>(), B.nnf, st);
+        launch_nf_apply(tab, B.d_nf.as<NFDesc>(), B.nnf, B.prec, B.nf_slots, B.nf_smem, st);
     } else if (B.exact) {
         launch_dense_restrict(tab, B.d_sub.as<SubDesc>(), B.nsub, st);
         launch_dense_apply(tab, B.d_sub.as<SubDesc>(), B.d_dense.as<int2>(), B.ndense, st);
@@ -1688,7 +1738,8 @@ int asm_create(asm_handle* out, const asm_options* opt, void* cuda_stream) {
     if (opt) o = *opt;
     if (o.precision < 0 || o.precision > 2 || o.krylov < 0 || o.krylov > 1 || o.restart < 1 || o.restart > 512 ||
         o.local_solver < 0 || o.local_solver > 4 || o.flexible < -1 || o.flexible > 1 ||
-        (o.local_solver >= ASM_LOCAL_EXACT && o.precision != ASM_PREC_FP64))
+        (o.local_solver == ASM_LOCAL_EXACT && o.precision != ASM_PREC_FP64) ||
+        (o.local_solver >= ASM_LOCAL_NF_COLSUM && o.precision == ASM_PREC_FP16S))
         return ASM_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
@@ -1862,7 +1913,8 @@ int asm_apply_precond(asm_handle h, const double* r, double* z, int on_device) {
         set_ctl(h, VU, VZ, -1, -1, -1);
         launch_boxsum(h->d_tab1.as<SysTab>(), h->d_box1.as<BoxItem>(), (int)h->box_items.size(), h->stream);
         if (is_nf(h)) {
-            launch_nf_apply(h->d_tab1.as<SysTab>(), h->d_nfdesc1.as<NFDesc>(), (int)h->nf_desc.size(), h->stream);
+            launch_nf_apply(h->d_tab1.as<SysTab>(), h->d_nfdesc1.as<NFDesc>(), (int)h->nf_desc.size(), h->prec,
+                            h->nf_slots, h->nf_smem, h->stream);
         } else if (h->opt.local_solver == ASM_LOCAL_EXACT) {
             launch_dense_restrict(h->d_tab1.as<SysTab>(), h->d_subdesc_single.as<SubDesc>(), (int)h->sub_desc.size(),
                                   h->stream);

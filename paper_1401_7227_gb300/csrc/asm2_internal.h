@@ -205,13 +205,16 @@ struct NFDesc {
     int bx, by, bz, n;
     int colsum;       // Eq. A.7 (1) or Eq. A.6 alone (0)
     int n_own;
+    int c0, gnz, gnx;    // grid cell of local (0, 0, 0); cell of (x, y, z) = c0 + z + gnz (x + gnx y)
+    int own_lo[3], own_hi[3];  // the owned box in local (x, y, z)
+    int line_bytes;      // one line packet of the apply (nf_line_bytes)
     const double* slot;  // the subdomain's assembled blocks of A_i (9 doubles each)
     const int* bands;    // [7 n]: slot of D, L1, U1, L2, U2, L3, U3 in cell p's row, or -1
-    const int* cell;     // [n] grid cell of each local cell
-    const int* own;      // [n_own] local cells this subdomain owns
     double* g;           // [9 n] the diagonal blocks G
     double* gi;          // [9 n] their inverses
-    double* work;        // nf_work_doubles(bx, by, bz) doubles of scratch
+    double* work;        // nf_work_doubles(bx, by, bz) doubles of scratch (factorisation)
+    void* pack;          // [by * bx] line packets (16-byte aligned), compute type
+    void* yv;            // [3 n] forward result of the apply, compute type
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -273,10 +276,17 @@ void launch_dense_scatter(const double* slot, const long long* off, const int* m
 void launch_dense_restrict(const SysTab* tab, const SubDesc* subs, int nsub, cudaStream_t st);
 void launch_dense_apply(const SysTab* tab, const SubDesc* subs, const int2* items, int nitems, cudaStream_t st);
 // Nested factorisation: G and G^{-1} of every subdomain (one warp each; *err gets the first
-// singular G), and the apply z[owned] = (B_i^{-1} R_i r)[owned]
+// singular G) and the line packets of the apply (nmax: largest n; prec 0 FP64, else FP32); the
+// apply z[owned] = (B_i^{-1} R_i r)[owned], one CTA of one warp per subdomain, smem = the largest
+// nf_apply_smem of the descriptors at that ring depth
 size_t nf_work_doubles(int bx, int by, int bz);
-void launch_nf_factor(const NFDesc* descs, int ndesc, FactErr* err, cudaStream_t st);
-void launch_nf_apply(const SysTab* tab, const NFDesc* descs, int ndesc, cudaStream_t st);
+size_t nf_line_bytes(int bz, int prec);
+size_t nf_apply_smem(int bx, int bz, int prec, int slots);
+// ring slots of the apply (2..4) for ndesc subdomains of at most bx_max x bz_max planes
+int nf_apply_slots(int ndesc, int bx_max, int bz_max, int prec, int sm_smem, int sms, int dev_smem);
+void launch_nf_factor(const NFDesc* descs, int ndesc, int nmax, int prec, FactErr* err, cudaStream_t st);
+void launch_nf_apply(const SysTab* tab, const NFDesc* descs, int ndesc, int prec, int slots, size_t smem,
+                     cudaStream_t st);
 void launch_om(const SysTab* tab, const VecItem* items, int nitems, int l, cudaStream_t st);
 void launch_om_update(const SysTab* tab, const VecItem* items, int nitems, cudaStream_t st);
 // Coarse-grid correction: [A_C | I] from the box-pair blocks, then in-place Gauss-Jordan (one

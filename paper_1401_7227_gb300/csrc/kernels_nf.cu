@@ -3,15 +3,23 @@
 // A = D + L1 + U1 + L2 + U2 + L3 + U3, and
 //   B = (P + L3)(I + P^{-1} U3),  P = (T + L2)(I + T^{-1} U2),  T = (G + L1)(I + G^{-1} U1)
 // with G block diagonal, G = D - L1 G^{-1} U1 (Eq. A.6), with colsum also minus the block column sums
-// of L2 T^{-1} U2 and L3 P^{-1} U3 (Eq. A.7).  The factorisation and the solve are sequential along
-// the cells of a subdomain (each line depends on the previous one, each plane on the previous
-// plane), so one warp takes one subdomain and its lanes share the 3x3 block algebra: nine lanes for
-// a block product (lane 3 r + c holds element (r, c)), three for a block times a 3-vector.
+// of L2 T^{-1} U2 and L3 P^{-1} U3 (Eq. A.7).
+//
+// Both the factorisation and the solve are sequential along the cells of a subdomain: every line
+// depends on the previous line of its plane, every plane on the previous plane.  So one warp takes
+// one subdomain.  In the factorisation its lanes share the 3x3 block algebra (lane 3 r + c holds
+// element (r, c) of a block).  The apply streams one packet per line -- G^{-1}, G^{-1} L1,
+// G^{-1} U1, L2, U2, L3, U3 of the line's cells, packed after the factorisation -- through a
+// two-slot shared-memory ring by bulk copies, one line ahead of the line being solved.  The
+// products that do not depend on the line recurrence run on all lanes; the two recurrences of T^{-1}
+// run from shared memory on one lane (FP32) or three (FP64, one row each: an FP64 instruction costs
+// the same for one lane as for 32).
 #include <cuda_runtime.h>
 
 #include <algorithm>
 
 #include "asm2_internal.h"
+#include "tma.h"
 
 namespace asm2 {
 namespace {
@@ -81,20 +89,6 @@ __device__ bool binv(double a, double& inv, int lane) {
     return ok != 0;
 }
 
-// ---- 3-vectors held one component per lane (lanes 0..2) --------------------------------------
-
-__device__ __forceinline__ double vload(const double* p, int lane) { return lane < 3 ? p[lane] : 0.0; }
-__device__ __forceinline__ void vstore(double* p, double v, int lane) {
-    if (lane < 3) p[lane] = v;
-}
-
-// (block at p) * x for x held per lane (nullptr: zero)
-__device__ __forceinline__ double bvmul(const double* p, double x, int lane) {
-    const double x0 = __shfl_sync(kFull, x, 0), x1 = __shfl_sync(kFull, x, 1), x2 = __shfl_sync(kFull, x, 2);
-    if (!p || lane >= 3) return 0.0;
-    return p[3 * lane] * x0 + p[3 * lane + 1] * x1 + p[3 * lane + 2] * x2;
-}
-
 struct NFView {
     const NFDesc& d;
     __device__ const double* band(int k, int p) const {  // k: 0 D, 1 L1, 2 U1, 3 L2, 4 U2, 5 L3, 6 U3
@@ -123,55 +117,6 @@ __device__ void line_row_solve(const NFView& v, int q0, const double* u, double*
         next = w;
     }
     __syncwarp();
-}
-
-// out = T^{-1} b on the line starting at q0 (3-vectors); b and out may not alias
-__device__ void line_solve(const NFView& v, int q0, const double* b, double* out, int lane) {
-    const int bz = v.d.bz;
-    double s = 0.0;
-    for (int q = 0; q < bz; q++) {  // (G + L1) s = b
-        double t = vload(b + 3 * q, lane);
-        if (q > 0) t -= bvmul(v.band(1, q0 + q), s, lane);
-        s = bvmul(v.gi(q0 + q), t, lane);
-        vstore(out + 3 * q, s, lane);
-    }
-    __syncwarp();
-    double o = 0.0;
-    for (int q = bz - 1; q >= 0; q--) {  // (I + G^{-1} U1) out = s
-        double t = vload(out + 3 * q, lane);
-        if (q < bz - 1) t -= bvmul(v.gi(q0 + q), bvmul(v.band(2, q0 + q), o, lane), lane);
-        vstore(out + 3 * q, t, lane);
-        o = t;
-    }
-    __syncwarp();
-}
-
-// out = P^{-1} b on the plane starting at c0; scratch: 3 bz + 3 bz doubles
-__device__ void plane_solve(const NFView& v, int c0, const double* b, double* out, double* t1, double* t2, int lane) {
-    const int bz = v.d.bz, bx = v.d.bx;
-    for (int l = 0; l < bx; l++) {  // (T + L2) z = b, z kept in out
-        for (int q = 0; q < bz; q++) {
-            const int c = l * bz + q;
-            double t = vload(b + 3 * c, lane);
-            if (l > 0) t -= bvmul(v.band(3, c0 + c), vload(out + 3 * (c - bz), lane), lane);
-            vstore(t1 + 3 * q, t, lane);
-        }
-        __syncwarp();
-        line_solve(v, c0 + l * bz, t1, out + 3 * l * bz, lane);
-    }
-    for (int l = bx - 2; l >= 0; l--) {  // (I + T^{-1} U2) out = z
-        for (int q = 0; q < bz; q++) {
-            const int c = l * bz + q;
-            vstore(t1 + 3 * q, bvmul(v.band(4, c0 + c), vload(out + 3 * (c + bz), lane), lane), lane);
-        }
-        __syncwarp();
-        line_solve(v, c0 + l * bz, t1, t2, lane);
-        for (int q = 0; q < bz; q++) {
-            const int c = l * bz + q;
-            vstore(out + 3 * c, vload(out + 3 * c, lane) - vload(t2 + 3 * q, lane), lane);
-        }
-        __syncwarp();
-    }
 }
 
 // W = u P^{-1} on the plane starting at c0 (rows of blocks); scratch: vb (9 S), x, y, vt (9 bz each)
@@ -267,70 +212,435 @@ __global__ void __launch_bounds__(128) k_nf_factor(const NFDesc* __restrict__ de
     }
 }
 
-// Apply: y = R_i r (the box's cells), x = B^{-1} y, z[owned cells] = x[owned]
-__global__ void __launch_bounds__(128) k_nf_apply(const SysTab* __restrict__ tab, const NFDesc* __restrict__ descs,
-                                                 int ndesc) {
-    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (w >= ndesc) return;
-    const NFDesc& d = descs[w];
+
+// ---- the apply ---------------------------------------------------------------------------------
+
+// fields of a line packet, each bz blocks, field after field
+enum { PK_GI = 0, PK_M, PK_N, PK_L2, PK_U2, PK_L3, PK_U3, PK_FIELDS };
+
+// Layout of the compute type: a 3x3 block is 3 rows of RS values (row r at r RS), a cell's
+// 3-vector takes VS values in shared memory.  FP32 pads both to 4, so that a row or a vector is one
+// 16-byte access; FP64 keeps them dense (its packets are twice as large already).
+template <typename T>
+struct Lay {
+    static constexpr int RS = 3, VS = 3;
+};
+template <>
+struct Lay<float> {
+    static constexpr int RS = 4, VS = 4;
+};
+
+__device__ __forceinline__ void ld3(const float* p, float& a, float& b, float& c) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    a = v.x;
+    b = v.y;
+    c = v.z;
+}
+__device__ __forceinline__ void ld3(const double* p, double& a, double& b, double& c) {
+    a = p[0];
+    b = p[1];
+    c = p[2];
+}
+__device__ __forceinline__ void st3(float* p, float a, float b, float c) {
+    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, 0.f);
+}
+__device__ __forceinline__ void st3(double* p, double a, double b, double c) {
+    p[0] = a;
+    p[1] = b;
+    p[2] = c;
+}
+
+// y -= a x for a 3x3 block a and 3-vectors, one fused chain per row
+template <typename T>
+__device__ __forceinline__ void sub_mv(const T* a, T x0, T x1, T x2, T& y0, T& y1, T& y2) {
+    constexpr int RS = Lay<T>::RS;
+    T a0, a1, a2;
+    ld3(a, a0, a1, a2);
+    y0 = fma(-a2, x2, fma(-a1, x1, fma(-a0, x0, y0)));
+    ld3(a + RS, a0, a1, a2);
+    y1 = fma(-a2, x2, fma(-a1, x1, fma(-a0, x0, y1)));
+    ld3(a + 2 * RS, a0, a1, a2);
+    y2 = fma(-a2, x2, fma(-a1, x1, fma(-a0, x0, y2)));
+}
+
+// packets of every line, one thread per cell: G^{-1}, M = G^{-1} L1 (the forward recurrence of
+// (G + L1) s = u is s_q = G_q^{-1} u_q - M_q s_{q-1}), N = G^{-1} U1 (the backward recurrence of
+// (I + G^{-1} U1) w = s is w_q = s_q - N_q w_{q+1}), and the blocks L2, U2, L3, U3 (zero where the
+// neighbour is missing); products in FP64, stored in the compute type (row padding stays zero)
+template <typename T>
+__global__ void __launch_bounds__(128) k_nf_pack(const NFDesc* __restrict__ descs) {
+    constexpr int RS = Lay<T>::RS, BS = 3 * RS;
+    const NFDesc& d = descs[blockIdx.y];
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= d.n) return;
+    const int bz = d.bz, line = p / bz, q = p - line * bz;
+    T* pk = reinterpret_cast<T*>(static_cast<unsigned char*>(d.pack) + (size_t)line * d.line_bytes);
+    const auto band = [&](int k) -> const double* {
+        const int s = d.bands[7 * p + k];
+        return s >= 0 ? d.slot + 9LL * s : nullptr;
+    };
+    const auto put = [&](int f, const double* b) {
+        T* o = pk + ((size_t)f * bz + q) * BS;
+        for (int r = 0; r < 3; r++)
+            for (int c = 0; c < 3; c++) o[r * RS + c] = b ? (T)b[3 * r + c] : T(0);
+    };
+    double gi[9], m[9];
+    for (int e = 0; e < 9; e++) gi[e] = d.gi[9LL * p + e];
+    put(PK_GI, gi);
+    for (int k = 1; k <= 2; k++) {
+        const double* b = band(k);
+        if (b)
+            for (int r = 0; r < 3; r++)
+                for (int c = 0; c < 3; c++)
+                    m[3 * r + c] = gi[3 * r] * b[c] + gi[3 * r + 1] * b[3 + c] + gi[3 * r + 2] * b[6 + c];
+        put(k == 1 ? PK_M : PK_N, b ? m : nullptr);
+    }
+    put(PK_L2, band(3));
+    put(PK_U2, band(4));
+    put(PK_L3, band(5));
+    put(PK_U3, band(6));
+}
+
+// The line solves of one apply, in order: forward planes j = 0 .. by-1, then backward planes
+// j = by-2 .. 0; in each plane the forward lines l = 0 .. bx-1 of (T + L2) z = t, then the
+// backward lines l = bx-2 .. 0 of (I + T^{-1} U2) o = z.
+struct LineStep {
+    int j, l;
+    bool fwd_plane, fwd_line, plane_done;
+};
+__device__ __forceinline__ LineStep line_step(int k, int bx, int by) {
+    const int per = 2 * bx - 1, P = k / per, i = k - P * per;
+    LineStep s;
+    s.fwd_plane = P < by;
+    s.j = s.fwd_plane ? P : 2 * by - 2 - P;
+    s.fwd_line = i < bx;
+    s.l = s.fwd_line ? i : 2 * bx - 2 - i;
+    s.plane_done = i == per - 1;
+    return s;
+}
+
+__host__ __device__ size_t nf_rline_bytes(int bz) { return ((size_t)24 * bz + 32 + 15) & ~(size_t)15; }
+
+// z[owned cells of plane j] = x_j (held in pv)
+template <typename T>
+__device__ __forceinline__ void write_owned(const NFDesc& d, int j, const T* pv, double* z, int lane) {
+    constexpr int VS = Lay<T>::VS;
+    if (j < d.own_lo[1] || j >= d.own_hi[1]) return;
+    const int wx = d.own_hi[0] - d.own_lo[0], wz = d.own_hi[2] - d.own_lo[2];
+    for (int e = lane; e < 3 * wx * wz; e += 32) {
+        const int t = e / 3, c = e - 3 * t;
+        const int x = d.own_lo[0] + t / wz, zz = d.own_lo[2] + t % wz;
+        const long long cell = d.c0 + zz + (long long)d.gnz * (x + (long long)d.gnx * j);
+        z[3 * cell + c] = (double)pv[VS * (x * d.bz + zz) + c];
+    }
+}
+
+// The two recurrences of one line solve on one lane (FP32): s_q = c_q - M_q s_{q-1} over
+// q = 0 .. bz-1 in cb, then w_q = s_q - N_q w_{q+1} over q = bz-1 .. 0, with o_q = w_q (forward
+// line) or o_q -= w_q (backward line).  Four steps at a time: the group's operands are loaded
+// first, so the loads overlap the chains.
+__device__ __forceinline__ void line_recurrences(const float* M, const float* N, float* cb, float* o, int bz,
+                                                 bool fwd_line) {
+    const float4* Mv = reinterpret_cast<const float4*>(M);
+    const float4* Nv = reinterpret_cast<const float4*>(N);
+    float4* cv = reinterpret_cast<float4*>(cb);
+    float4* ov = reinterpret_cast<float4*>(o);
+    const auto step = [](const float4* m, float4 c, float& x0, float& x1, float& x2) {
+        const float n0 = fmaf(-m[0].z, x2, fmaf(-m[0].y, x1, fmaf(-m[0].x, x0, c.x)));
+        const float n1 = fmaf(-m[1].z, x2, fmaf(-m[1].y, x1, fmaf(-m[1].x, x0, c.y)));
+        const float n2 = fmaf(-m[2].z, x2, fmaf(-m[2].y, x1, fmaf(-m[2].x, x0, c.z)));
+        x0 = n0;
+        x1 = n1;
+        x2 = n2;
+    };
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    int q = 0;
+    for (; q + 4 <= bz; q += 4) {
+        float4 m[12], c[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            m[3 * u] = Mv[3 * (q + u)];
+            m[3 * u + 1] = Mv[3 * (q + u) + 1];
+            m[3 * u + 2] = Mv[3 * (q + u) + 2];
+            c[u] = cv[q + u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            step(m + 3 * u, c[u], s0, s1, s2);
+            c[u] = make_float4(s0, s1, s2, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) cv[q + u] = c[u];
+    }
+    for (; q < bz; q++) {
+        const float4 m[3] = {Mv[3 * q], Mv[3 * q + 1], Mv[3 * q + 2]};
+        step(m, cv[q], s0, s1, s2);
+        cv[q] = make_float4(s0, s1, s2, 0.f);
+    }
+    float w0 = 0.f, w1 = 0.f, w2 = 0.f;
+    q = bz - 1;
+    for (; q >= 3; q -= 4) {
+        float4 m[12], c[4], a[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            m[3 * u] = Nv[3 * (q - u)];
+            m[3 * u + 1] = Nv[3 * (q - u) + 1];
+            m[3 * u + 2] = Nv[3 * (q - u) + 2];
+            c[u] = cv[q - u];
+            a[u] = fwd_line ? make_float4(0.f, 0.f, 0.f, 0.f) : ov[q - u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            step(m + 3 * u, c[u], w0, w1, w2);
+            a[u] = fwd_line ? make_float4(w0, w1, w2, 0.f) : make_float4(a[u].x - w0, a[u].y - w1, a[u].z - w2, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) ov[q - u] = a[u];
+    }
+    for (; q >= 0; q--) {
+        const float4 m[3] = {Nv[3 * q], Nv[3 * q + 1], Nv[3 * q + 2]};
+        step(m, cv[q], w0, w1, w2);
+        const float4 a = ov[q];
+        ov[q] = fwd_line ? make_float4(w0, w1, w2, 0.f) : make_float4(a.x - w0, a.y - w1, a.z - w2, 0.f);
+    }
+}
+
+// The same on three lanes (FP64: an FP64 instruction costs the same for one lane as for 32, so
+// lane r takes row r and the state is exchanged by shuffles)
+__device__ __forceinline__ void line_recurrences(const double* M, const double* N, double* cb, double* o, int bz,
+                                                 bool fwd_line, int lane) {
+    constexpr unsigned kRow = 0x7u;
+    const double* mr = M + 3 * lane;
+    double sv = 0, m0 = mr[0], m1 = mr[1], m2 = mr[2], c = cb[lane];
+    for (int q = 0; q < bz; q++) {
+        const int qn = q + 1 < bz ? q + 1 : q;
+        const double n0 = mr[9 * qn], n1 = mr[9 * qn + 1], n2 = mr[9 * qn + 2], cn = cb[3 * qn + lane];
+        const double s0 = __shfl_sync(kRow, sv, 0), s1 = __shfl_sync(kRow, sv, 1), s2 = __shfl_sync(kRow, sv, 2);
+        sv = fma(-m2, s2, fma(-m1, s1, fma(-m0, s0, c)));
+        cb[3 * q + lane] = sv;
+        m0 = n0;
+        m1 = n1;
+        m2 = n2;
+        c = cn;
+    }
+    const double* nr = N + 3 * lane;
+    const int ql = bz - 1;
+    double wv = 0;
+    m0 = nr[9 * ql];
+    m1 = nr[9 * ql + 1];
+    m2 = nr[9 * ql + 2];
+    c = cb[3 * ql + lane];
+    for (int q = ql; q >= 0; q--) {
+        const int qn = q > 0 ? q - 1 : q;
+        const double n0 = nr[9 * qn], n1 = nr[9 * qn + 1], n2 = nr[9 * qn + 2], cn = cb[3 * qn + lane];
+        const double on = o[3 * q + lane];
+        const double w0 = __shfl_sync(kRow, wv, 0), w1 = __shfl_sync(kRow, wv, 1), w2 = __shfl_sync(kRow, wv, 2);
+        wv = fma(-m2, w2, fma(-m1, w1, fma(-m0, w0, c)));
+        o[3 * q + lane] = fwd_line ? wv : on - wv;
+        m0 = n0;
+        m1 = n1;
+        m2 = n2;
+        c = cn;
+    }
+}
+
+// B_i^{-1} R_i r for one subdomain per CTA (one warp), owned cells written to the apply output.
+// Shared memory: SLOTS mbarriers (16 bytes each) | SLOTS packet slots | SLOTS slots for the line's
+// part of r (FP64) |
+// plane vector pv [VS S] | line vector cb [VS bz].  pv holds, in turn, y_{j-1} and z / o of plane
+// j during the forward planes, then x_{j+1} and z / o of plane j during the backward ones: every
+// line reads the previous plane's value of a line before it overwrites it.
+template <typename T, int SLOTS>
+__global__ void __launch_bounds__(32) k_nf_apply(const SysTab* __restrict__ tab, const NFDesc* __restrict__ descs) {
+    constexpr int BS = 3 * Lay<T>::RS, VS = Lay<T>::VS;
+    extern __shared__ __align__(16) unsigned char nf_smem[];
+    const NFDesc& d = descs[blockIdx.x];
     const SysTab& st = tab[d.sys];
     const int in = st.ctl[C_APPLY_IN];
     if (in < 0) return;
-    const double* r = st.ws + (long long)in * st.n3p;
-    double* z = st.ws + (long long)st.ctl[C_APPLY_OUT] * st.n3p;
-    const NFView v{d};
-    const int bz = d.bz, bx = d.bx, by = d.by, S = bz * bx, n = d.n;
-    // scratch: yv (3 n), xv (3 n), t (3 S), wv (3 S), t1, t2 (3 bz each)
-    double* yv = d.work;
-    double* xv = yv + 3 * n;
-    double* t = xv + 3 * n;
-    double* wv = t + 3 * S;
-    double* t1 = wv + 3 * S;
-    double* t2 = t1 + 3 * bz;
-    for (int j = 0; j < by; j++) {  // (P + L3) yv = R r
-        for (int c = 0; c < S; c++) {
-            const int p = j * S + c;
-            double e = vload(r + 3LL * d.cell[p], lane);
-            if (j > 0) e -= bvmul(v.band(5, p), vload(yv + 3 * (p - S), lane), lane);
-            vstore(t + 3 * c, e, lane);
+    const double* __restrict__ r = st.ws + (long long)in * st.n3p;
+    double* __restrict__ z = st.ws + (long long)st.ctl[C_APPLY_OUT] * st.n3p;
+    const int lane = threadIdx.x;
+    const int bx = d.bx, by = d.by, bz = d.bz, S = bx * bz;
+    const size_t LB = (size_t)d.line_bytes, RB = nf_rline_bytes(bz);
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(nf_smem);  // 2 words apart
+    unsigned char* const pk_base = nf_smem + 16 * SLOTS;
+    unsigned char* const r_base = pk_base + SLOTS * LB;
+    T* pv = reinterpret_cast<T*>(r_base + SLOTS * RB);
+    T* cb = pv + ((VS * (size_t)S * sizeof(T) + 15) / 16 * 16) / sizeof(T);
+    T* yv = static_cast<T*>(d.yv);
+    const int K = (2 * by - 1) * (2 * bx - 1);
+
+    // the grid cell of a line's first cell; the line's cells follow it (z is the fastest index)
+    const auto cell0_of = [&](const LineStep& s) {
+        return d.c0 + (long long)d.gnz * (s.l + (long long)d.gnx * s.j);
+    };
+    // packet of line solve k, plus the line's part of r for a forward line of a forward plane (the
+    // copy starts at the 16-byte boundary at or below it: one leading double when the cell is odd)
+    const auto issue = [&](int k) {
+        const LineStep s = line_step(k, bx, by);
+        const int b = k % SLOTS;
+        unsigned rbytes = 0;
+        const unsigned char* rsrc = nullptr;
+        if (s.fwd_plane && s.fwd_line) {
+            const long long c0 = cell0_of(s);
+            const long long a = (24 * c0) & ~15LL, e = (24 * (c0 + bz) + 15) & ~15LL;
+            rbytes = (unsigned)(e - a);
+            rsrc = reinterpret_cast<const unsigned char*>(r) + a;
+        }
+        tma::mbar_expect_tx(&bar[2 * b], (unsigned)LB + rbytes);
+        tma::bulk_load(pk_base + b * LB, static_cast<const unsigned char*>(d.pack) + (size_t)(s.j * bx + s.l) * LB,
+                       (unsigned)LB, &bar[2 * b]);
+        if (rbytes) tma::bulk_load(r_base + b * RB, rsrc, rbytes, &bar[2 * b]);
+    };
+
+    if (lane == 0) {
+        for (int b = 0; b < SLOTS; b++) tma::mbar_init(&bar[2 * b], 1);
+        tma::fence_mbar_init();
+        for (int k = 0; k < SLOTS - 1 && k < K; k++) issue(k);
+    }
+    __syncwarp();
+    for (int k = 0; k < K; k++) {
+        // line solve k + SLOTS - 1 goes into the slot that line solve k - 1 has finished with
+        if (lane == 0 && k + SLOTS - 1 < K) issue(k + SLOTS - 1);
+        const int b = k % SLOTS;
+        const bool ok = tma::mbar_wait(&bar[2 * b], (unsigned)(k / SLOTS) & 1u);
+        if (!__all_sync(kFull, ok)) {
+            // a copy did not land in time: report it, wait (bounded) for the copies in flight
+            if (lane == 0) {
+                atomicExch(st.dev_err, 7);
+                for (int k2 = k; k2 < K && k2 < k + SLOTS; k2++)
+                    tma::mbar_wait(&bar[2 * (k2 % SLOTS)], (unsigned)(k2 / SLOTS) & 1u);
+            }
+            return;
+        }
+        const LineStep s = line_step(k, bx, by);
+        const T* pk = reinterpret_cast<const T*>(pk_base + b * LB);
+        const auto blk = [&](int f, int q) { return pk + ((size_t)f * bz + q) * BS; };
+        T* pl = pv + (size_t)VS * s.l * bz;  // this line's part of the plane vector
+        // c = G^{-1} u, u the line's right-hand side:
+        //   forward line of a forward plane:   u = r - L3 y_{j-1} - L2 z_{l-1}
+        //   forward line of a backward plane:  u = U3 x_{j+1} - L2 z_{l-1}
+        //   backward line:                     u = U2 o_{l+1}
+        // (a product that is added goes through sub_mv with the vector negated, which is exact)
+        const double* rl = reinterpret_cast<const double*>(r_base + b * RB) + (cell0_of(s) & 1);
+        for (int q = lane; q < bz; q += 32) {
+            T u0 = 0, u1 = 0, u2 = 0, x0, x1, x2;
+            const T* cur = pl + VS * q;
+            if (s.fwd_line) {
+                if (s.fwd_plane) {
+                    u0 = (T)rl[3 * q];
+                    u1 = (T)rl[3 * q + 1];
+                    u2 = (T)rl[3 * q + 2];
+                    if (s.j > 0) {
+                        ld3(cur, x0, x1, x2);
+                        sub_mv(blk(PK_L3, q), x0, x1, x2, u0, u1, u2);
+                    }
+                } else {
+                    ld3(cur, x0, x1, x2);
+                    sub_mv(blk(PK_U3, q), -x0, -x1, -x2, u0, u1, u2);
+                }
+                if (s.l > 0) {
+                    ld3(cur - VS * bz, x0, x1, x2);
+                    sub_mv(blk(PK_L2, q), x0, x1, x2, u0, u1, u2);
+                }
+            } else {
+                ld3(cur + VS * bz, x0, x1, x2);
+                sub_mv(blk(PK_U2, q), -x0, -x1, -x2, u0, u1, u2);
+            }
+            T c0 = 0, c1 = 0, c2 = 0;
+            sub_mv(blk(PK_GI, q), -u0, -u1, -u2, c0, c1, c2);
+            st3(cb + VS * q, c0, c1, c2);
         }
         __syncwarp();
-        plane_solve(v, j * S, t, yv + 3 * j * S, t1, t2, lane);
-    }
-    for (int c = (by - 1) * S; c < by * S; c++) vstore(xv + 3 * c, vload(yv + 3 * c, lane), lane);
-    for (int j = by - 2; j >= 0; j--) {  // (I + P^{-1} U3) xv = yv
-        for (int c = 0; c < S; c++) {
-            const int p = j * S + c;
-            vstore(t + 3 * c, bvmul(v.band(6, p), vload(xv + 3 * (p + S), lane), lane), lane);
+        if constexpr (sizeof(T) == 4) {
+            if (lane == 0) line_recurrences(blk(PK_M, 0), blk(PK_N, 0), cb, pl, bz, s.fwd_line);
+        } else {
+            if (lane < 3) line_recurrences(blk(PK_M, 0), blk(PK_N, 0), cb, pl, bz, s.fwd_line, lane);
         }
         __syncwarp();
-        plane_solve(v, j * S, t, wv, t1, t2, lane);
-        for (int c = 0; c < S; c++) {
-            const int p = j * S + c;
-            vstore(xv + 3 * p, vload(yv + 3 * p, lane) - vload(wv + 3 * c, lane), lane);
+        if (s.plane_done) {  // pv = P_j^{-1} t
+            T* yj = yv + 3 * (size_t)s.j * S;
+            if (s.fwd_plane) {
+                if (s.j < by - 1)
+                    for (int e = lane; e < 3 * S; e += 32) yj[e] = pv[VS * (e / 3) + e % 3];  // y_j
+                else
+                    write_owned(d, s.j, pv, z, lane);  // x_{by-1} = y_{by-1}
+            } else {
+                for (int e = lane; e < 3 * S; e += 32) {  // x_j = y_j - pv
+                    T& x = pv[VS * (e / 3) + e % 3];
+                    x = yj[e] - x;
+                }
+                __syncwarp();
+                write_owned(d, s.j, pv, z, lane);
+            }
+            __syncwarp();
         }
-        __syncwarp();
     }
-    // owned cells take this subdomain's solution (P_i R_i^T)
-    for (int i = lane; i < 3 * d.n_own; i += 32) {
-        const int p = d.own[i / 3], c = i - 3 * (i / 3);
-        z[3LL * d.cell[p] + c] = xv[3 * p + c];
-    }
+}
+
+template <typename T, int SLOTS>
+void nf_apply_t(const SysTab* tab, const NFDesc* descs, int ndesc, size_t smem, cudaStream_t st) {
+    cudaFuncSetAttribute(k_nf_apply<T, SLOTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_nf_apply<T, SLOTS><<<ndesc, 32, smem, st>>>(tab, descs);
+}
+
+template <typename T>
+void nf_apply_s(const SysTab* tab, const NFDesc* descs, int ndesc, int slots, size_t smem, cudaStream_t st) {
+    if (slots >= 4)
+        nf_apply_t<T, 4>(tab, descs, ndesc, smem, st);
+    else if (slots == 3)
+        nf_apply_t<T, 3>(tab, descs, ndesc, smem, st);
+    else
+        nf_apply_t<T, 2>(tab, descs, ndesc, smem, st);
 }
 
 }  // namespace
 
+size_t nf_line_bytes(int bz, int prec) {
+    const size_t t = prec == 0 ? 8 : 4, bs = prec == 0 ? 9 : 12;
+    return (PK_FIELDS * bs * (size_t)bz * t + 15) & ~(size_t)15;
+}
+
+size_t nf_apply_smem(int bx, int bz, int prec, int slots) {
+    const size_t t = prec == 0 ? 8 : 4, vs = prec == 0 ? 3 : 4;
+    return slots * (16 + nf_line_bytes(bz, prec) + nf_rline_bytes(bz)) + ((vs * (size_t)bx * bz * t + 15) & ~(size_t)15) +
+           vs * (size_t)bz * t;
+}
+
 size_t nf_work_doubles(int bx, int by, int bz) {
-    const size_t S = (size_t)bx * bz, n = S * by;
-    return std::max<size_t>(36 * (S + (size_t)bz), 6 * (n + S + (size_t)bz));
+    (void)by;
+    return 36 * ((size_t)bx * bz + (size_t)bz);
 }
 
-void launch_nf_factor(const NFDesc* descs, int ndesc, FactErr* err, cudaStream_t st) {
-    if (ndesc > 0) k_nf_factor<<<(ndesc + 3) / 4, 128, 0, st>>>(descs, ndesc, err);
+void launch_nf_factor(const NFDesc* descs, int ndesc, int nmax, int prec, FactErr* err, cudaStream_t st) {
+    if (ndesc <= 0) return;
+    k_nf_factor<<<(ndesc + 3) / 4, 128, 0, st>>>(descs, ndesc, err);
+    const dim3 grid((unsigned)((nmax + 127) / 128), (unsigned)ndesc);
+    if (prec == 0)
+        k_nf_pack<double><<<grid, 128, 0, st>>>(descs);
+    else
+        k_nf_pack<float><<<grid, 128, 0, st>>>(descs);
 }
 
-void launch_nf_apply(const SysTab* tab, const NFDesc* descs, int ndesc, cudaStream_t st) {
-    if (ndesc > 0) k_nf_apply<<<(ndesc + 3) / 4, 128, 0, st>>>(tab, descs, ndesc);
+void launch_nf_apply(const SysTab* tab, const NFDesc* descs, int ndesc, int prec, int slots, size_t smem,
+                     cudaStream_t st) {
+    if (ndesc <= 0) return;
+    if (prec == 0)
+        nf_apply_s<double>(tab, descs, ndesc, slots, smem, st);
+    else
+        nf_apply_s<float>(tab, descs, ndesc, slots, smem, st);
+}
+
+int nf_apply_slots(int ndesc, int bx_max, int bz_max, int prec, int sm_smem, int sms, int dev_smem) {
+    // the deepest ring with which every CTA of the launch is resident at once; else the shallowest
+    // that fits a CTA at all
+    const long long per_sm = (ndesc + std::max(1, sms) - 1) / std::max(1, sms);
+    for (int s = 4; s >= 2; s--) {
+        const size_t b = nf_apply_smem(bx_max, bz_max, prec, s);
+        if (b <= (size_t)dev_smem && per_sm * (long long)(b + 1024) <= (long long)sm_smem) return s;
+    }
+    return 2;
 }
 
 }  // namespace asm2

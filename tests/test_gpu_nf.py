@@ -20,13 +20,14 @@ GEOMS = {  # geometries whose local problems are boxes without lumps
     "yz": (O.Geometry(5, 6, 4, 1, 2, 2, ov=1, near_width=0, far_mode=0), 22),
     "ragged": (O.Geometry(9, 7, 6, 3, 2, 2, ov=1, near_width=0, far_mode=0), 23),
     "tiles": (O.Geometry(24, 20, 16, 3, 2, 1, ov=2, near_width=0, far_mode=0), 24),
+    "long": (O.Geometry(4, 3, 150, 2, 1, 1, ov=1, near_width=0, far_mode=0), 25),  # lines of 150 cells
 }
 SOLVERS = {"nf_colsum": O.NF_COLSUM, "nf": O.NF}
 EPS = np.finfo(float).eps
 
 
-def nf_solver(g, s, local="nf_colsum", krylov="gmres", restart=30):
-    sol = asm2.Solver(precision="fp64", local_solver=local, krylov=krylov, restart=restart)
+def nf_solver(g, s, local="nf_colsum", krylov="gmres", restart=30, precision="fp64"):
+    sol = asm2.Solver(precision=precision, local_solver=local, krylov=krylov, restart=restart)
     sol.set_grid(g.nx, g.ny, g.nz)
     sol.set_matrix(s.row_ptr, s.col_idx, s.vals)
     sol.set_partition(g.px, g.py, g.pz, g.ov, g.near_width, g.cnear, g.far_mode)
@@ -174,6 +175,39 @@ def test_local_problems_with_lumps_are_rejected():
     assert e.value.status == 1
 
 
-def test_nf_needs_fp64():
+def test_nf_refuses_fp16_storage():
     with pytest.raises(asm2.ASMError):
-        asm2.Solver(precision="fp32", local_solver="nf")
+        asm2.Solver(precision="fp16s", local_solver="nf")
+
+
+@pytest.mark.parametrize("local", list(SOLVERS))
+@pytest.mark.parametrize("name", ["x2", "ragged", "tiles", "long"])
+def test_fp32_apply_close_to_oracle(name, local):
+    """FP32 apply (G from the FP64 factorisation, rounded): within 1e-5 of the FP64 oracle."""
+    g, seed = GEOMS[name]
+    s = synth.grid_jacobian(g.nx, g.ny, g.nz, seed)
+    pc = O.Precond(g, s.row_ptr, s.col_idx, s.vals, solver=SOLVERS[local])
+    r = synth.rhs(s.n_cells, 3)
+    assert rel(nf_solver(g, s, local, precision="fp32").apply(r), pc.apply(r)) <= 1e-5
+
+
+@pytest.mark.parametrize("name", ["ragged", "tiles"])
+def test_fp32_gmres_reaches_fp64_tolerance(name):
+    g, seed = GEOMS[name]
+    s = synth.grid_jacobian(g.nx, g.ny, g.nz, seed)
+    pc = O.Precond(g, s.row_ptr, s.col_idx, s.vals, solver=O.NF_COLSUM)
+    _, oi = O.gmres(s.row_ptr, s.col_idx, s.vals, s.b, pc, 30, 1e-8, 500)
+    x, info = nf_solver(g, s, precision="fp32").solve(s.b, rtol=1e-8, max_iter=500)
+    assert info["converged"] and info["iterations"] <= oi.iters + 2
+    assert rel(O.spmv(s.row_ptr, s.col_idx, s.vals, x), s.b) <= 1e-8
+
+
+def test_line_too_long_for_fp64_apply_is_rejected():
+    """An FP64 line packet of 300 cells does not fit the apply's two shared-memory slots; FP32 does."""
+    g = O.Geometry(2, 2, 300, 1, 1, 1, ov=0, near_width=0, far_mode=0)
+    s = synth.grid_jacobian(2, 2, 300, 26)
+    with pytest.raises(asm2.ASMError) as e:
+        nf_solver(g, s, precision="fp64")
+    assert e.value.status == 1
+    pc = O.Precond(g, s.row_ptr, s.col_idx, s.vals, solver=O.NF_COLSUM)
+    assert rel(nf_solver(g, s, precision="fp32").apply(s.b), pc.apply(s.b)) <= 1e-5
