@@ -388,7 +388,7 @@ void upload_nf(asm_ctx* h, cudaStream_t st) {
         P.pack = npack;
         npack += (long long)(lb * (size_t)P.bx * P.by + 255) / 256 * 256;
         P.yv = ny;
-        ny += (3LL * o.n * (h->prec == 0 ? 8 : 4) + 255) / 256 * 256;
+        ny += ((long long)nf_plane_bytes(P.bx * P.bz, h->prec) * P.by + 255) / 256 * 256;
         h->nf_bx_max = std::max(h->nf_bx_max, P.bx);
         h->nf_bz_max = std::max(h->nf_bz_max, P.bz);
     }

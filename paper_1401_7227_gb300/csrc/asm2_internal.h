@@ -214,7 +214,7 @@ struct NFDesc {
     double* gi;          // [9 n] their inverses
     double* work;        // nf_work_doubles(bx, by, bz) doubles of scratch (factorisation)
     void* pack;          // [by * bx] line packets (16-byte aligned), compute type
-    void* yv;            // [3 n] forward result of the apply, compute type
+    void* yv;            // [by] planes of the apply's forward result, nf_plane_bytes(bx bz) apart
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -281,6 +281,7 @@ void launch_dense_apply(const SysTab* tab, const SubDesc* subs, const int2* item
 // nf_apply_smem of the descriptors at that ring depth
 size_t nf_work_doubles(int bx, int by, int bz);
 size_t nf_line_bytes(int bz, int prec);
+size_t nf_plane_bytes(int S, int prec);  // one plane of the apply's y (stride of NFDesc::yv)
 size_t nf_apply_smem(int bx, int bz, int prec, int slots);
 // ring slots of the apply (2..4) for ndesc subdomains of at most bx_max x bz_max planes
 int nf_apply_slots(int ndesc, int bx_max, int bz_max, int prec, int sm_smem, int sms, int dev_smem);

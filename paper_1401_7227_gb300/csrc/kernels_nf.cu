@@ -215,8 +215,12 @@ __global__ void __launch_bounds__(128) k_nf_factor(const NFDesc* __restrict__ de
 
 // ---- the apply ---------------------------------------------------------------------------------
 
-// fields of a line packet, each bz blocks, field after field
-enum { PK_GI = 0, PK_M, PK_N, PK_L2, PK_U2, PK_L3, PK_U3, PK_FIELDS };
+// fields of a line packet, each bz blocks, field after field.  A line solve copies only the fields
+// it reads into a ring slot of SL_FIELDS fields: G^{-1}, M, N always (slot fields 0-2), then L2
+// and L3 on a forward line of a forward plane, L2 and U3 on a forward line of a backward plane,
+// U2 on a backward line (slot fields 3, 4).
+enum { PK_GI = 0, PK_M, PK_N, PK_L2, PK_L3, PK_U3, PK_U2, PK_FIELDS };
+enum { SL_X = 3, SL_Y = 4, SL_FIELDS = 5 };
 
 // Layout of the compute type: a 3x3 block is 3 rows of RS values (row r at r RS), a cell's
 // 3-vector takes VS values in shared memory.  FP32 pads both to 4, so that a row or a vector is one
@@ -267,6 +271,12 @@ __device__ __forceinline__ void sub_mv(const T* a, T x0, T x1, T x2, T& y0, T& y
 // (G + L1) s = u is s_q = G_q^{-1} u_q - M_q s_{q-1}), N = G^{-1} U1 (the backward recurrence of
 // (I + G^{-1} U1) w = s is w_q = s_q - N_q w_{q+1}), and the blocks L2, U2, L3, U3 (zero where the
 // neighbour is missing); products in FP64, stored in the compute type (row padding stays zero)
+// bytes of one field of a line packet: bz blocks, rounded up to 16 bytes (a bulk-copy unit)
+template <typename T>
+__host__ __device__ __forceinline__ size_t field_bytes(int bz) {
+    return ((size_t)9 * Lay<T>::RS / 3 * sizeof(T) * bz + 15) & ~(size_t)15;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128) k_nf_pack(const NFDesc* __restrict__ descs) {
     constexpr int RS = Lay<T>::RS, BS = 3 * RS;
@@ -280,7 +290,7 @@ __global__ void __launch_bounds__(128) k_nf_pack(const NFDesc* __restrict__ desc
         return s >= 0 ? d.slot + 9LL * s : nullptr;
     };
     const auto put = [&](int f, const double* b) {
-        T* o = pk + ((size_t)f * bz + q) * BS;
+        T* o = pk + (size_t)f * (field_bytes<T>(bz) / sizeof(T)) + (size_t)q * BS;
         for (int r = 0; r < 3; r++)
             for (int c = 0; c < 3; c++) o[r * RS + c] = b ? (T)b[3 * r + c] : T(0);
     };
@@ -303,23 +313,35 @@ __global__ void __launch_bounds__(128) k_nf_pack(const NFDesc* __restrict__ desc
 
 // The line solves of one apply, in order: forward planes j = 0 .. by-1, then backward planes
 // j = by-2 .. 0; in each plane the forward lines l = 0 .. bx-1 of (T + L2) z = t, then the
-// backward lines l = bx-2 .. 0 of (I + T^{-1} U2) o = z.
+// backward lines l = bx-2 .. 0 of (I + T^{-1} U2) o = z.  P counts the plane passes, i the line
+// solves of the pass; next() advances without divisions.
 struct LineStep {
-    int j, l;
-    bool fwd_plane, fwd_line, plane_done;
+    int P = 0, i = 0, j = 0, l = 0;
+    bool fwd_plane = true, fwd_line = true, plane_first = true, plane_done = false;
+    __device__ __forceinline__ void set(int bx, int by) {
+        fwd_plane = P < by;
+        j = fwd_plane ? P : 2 * by - 2 - P;
+        fwd_line = i < bx;
+        l = fwd_line ? i : 2 * bx - 2 - i;
+        plane_first = i == 0;
+        plane_done = i == 2 * bx - 2;
+    }
+    __device__ __forceinline__ void next(int bx, int by) {
+        if (++i == 2 * bx - 1) {
+            i = 0;
+            ++P;
+        }
+        set(bx, by);
+    }
 };
-__device__ __forceinline__ LineStep line_step(int k, int bx, int by) {
-    const int per = 2 * bx - 1, P = k / per, i = k - P * per;
-    LineStep s;
-    s.fwd_plane = P < by;
-    s.j = s.fwd_plane ? P : 2 * by - 2 - P;
-    s.fwd_line = i < bx;
-    s.l = s.fwd_line ? i : 2 * bx - 2 - i;
-    s.plane_done = i == per - 1;
-    return s;
-}
 
 __host__ __device__ size_t nf_rline_bytes(int bz) { return ((size_t)24 * bz + 32 + 15) & ~(size_t)15; }
+
+// bytes of a plane vector (VS values per cell, rounded up to 16)
+template <typename T>
+__host__ __device__ __forceinline__ size_t nf_plane_bytes(int S) {
+    return ((size_t)Lay<T>::VS * S * sizeof(T) + 15) & ~(size_t)15;
+}
 
 // z[owned cells of plane j] = x_j (held in pv)
 template <typename T>
@@ -327,11 +349,13 @@ __device__ __forceinline__ void write_owned(const NFDesc& d, int j, const T* pv,
     constexpr int VS = Lay<T>::VS;
     if (j < d.own_lo[1] || j >= d.own_hi[1]) return;
     const int wx = d.own_hi[0] - d.own_lo[0], wz = d.own_hi[2] - d.own_lo[2];
-    for (int e = lane; e < 3 * wx * wz; e += 32) {
-        const int t = e / 3, c = e - 3 * t;
+    for (int t = lane; t < wx * wz; t += 32) {
         const int x = d.own_lo[0] + t / wz, zz = d.own_lo[2] + t % wz;
         const long long cell = d.c0 + zz + (long long)d.gnz * (x + (long long)d.gnx * j);
-        z[3 * cell + c] = (double)pv[VS * (x * d.bz + zz) + c];
+        const T* v = pv + VS * (x * d.bz + zz);
+        z[3 * cell] = (double)v[0];
+        z[3 * cell + 1] = (double)v[1];
+        z[3 * cell + 2] = (double)v[2];
     }
 }
 
@@ -445,11 +469,13 @@ __device__ __forceinline__ void line_recurrences(const double* M, const double* 
 }
 
 // B_i^{-1} R_i r for one subdomain per CTA (one warp), owned cells written to the apply output.
-// Shared memory: SLOTS mbarriers (16 bytes each) | SLOTS packet slots | SLOTS slots for the line's
-// part of r (FP64) |
-// plane vector pv [VS S] | line vector cb [VS bz].  pv holds, in turn, y_{j-1} and z / o of plane
-// j during the forward planes, then x_{j+1} and z / o of plane j during the backward ones: every
-// line reads the previous plane's value of a line before it overwrites it.
+// Shared memory: SLOTS + 1 mbarriers (16 bytes each) | SLOTS packet slots | SLOTS slots for the
+// line's part of r (FP64) | plane vector pv [VS S] | y_j of a backward plane [VS S] | line vector
+// cb [VS bz].  pv holds, in turn, y_{j-1} and z / o of plane j during the forward planes, then
+// x_{j+1} and z / o of plane j during the backward ones: every line reads the previous plane's
+// value of a line before it overwrites it.  y_j goes to device memory (yv, one plane every
+// nf_plane_bytes) when its forward plane is done, and comes back by a bulk copy issued at the start
+// of its backward plane.
 template <typename T, int SLOTS>
 __global__ void __launch_bounds__(32) k_nf_apply(const SysTab* __restrict__ tab, const NFDesc* __restrict__ descs) {
     constexpr int BS = 3 * Lay<T>::RS, VS = Lay<T>::VS;
@@ -462,24 +488,28 @@ __global__ void __launch_bounds__(32) k_nf_apply(const SysTab* __restrict__ tab,
     double* __restrict__ z = st.ws + (long long)st.ctl[C_APPLY_OUT] * st.n3p;
     const int lane = threadIdx.x;
     const int bx = d.bx, by = d.by, bz = d.bz, S = bx * bz;
-    const size_t LB = (size_t)d.line_bytes, RB = nf_rline_bytes(bz);
+    const unsigned fb = (unsigned)field_bytes<T>(bz);
+    const size_t LB = (size_t)d.line_bytes, SB = (size_t)SL_FIELDS * fb, RB = nf_rline_bytes(bz),
+                 PB = nf_plane_bytes<T>(S);
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(nf_smem);  // 2 words apart
-    unsigned char* const pk_base = nf_smem + 16 * SLOTS;
-    unsigned char* const r_base = pk_base + SLOTS * LB;
+    unsigned long long* ybar = bar + 2 * SLOTS;
+    unsigned char* const pk_base = nf_smem + 16 * (SLOTS + 1);
+    unsigned char* const r_base = pk_base + SLOTS * SB;
     T* pv = reinterpret_cast<T*>(r_base + SLOTS * RB);
-    T* cb = pv + ((VS * (size_t)S * sizeof(T) + 15) / 16 * 16) / sizeof(T);
-    T* yv = static_cast<T*>(d.yv);
+    T* yb = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(pv) + PB);
+    T* cb = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(yb) + PB);
+    unsigned char* yv = static_cast<unsigned char*>(d.yv);
     const int K = (2 * by - 1) * (2 * bx - 1);
+    const size_t fe = fb / sizeof(T);
 
     // the grid cell of a line's first cell; the line's cells follow it (z is the fastest index)
     const auto cell0_of = [&](const LineStep& s) {
         return d.c0 + (long long)d.gnz * (s.l + (long long)d.gnx * s.j);
     };
-    // packet of line solve k, plus the line's part of r for a forward line of a forward plane (the
-    // copy starts at the 16-byte boundary at or below it: one leading double when the cell is odd)
-    const auto issue = [&](int k) {
-        const LineStep s = line_step(k, bx, by);
-        const int b = k % SLOTS;
+    // packet of a line solve into slot b, plus the line's part of r for a forward line of a forward
+    // plane (the copy starts at the 16-byte boundary at or below it: one leading double when the
+    // cell is odd); only the fields the line solve reads
+    const auto issue = [&](const LineStep& s, int b) {
         unsigned rbytes = 0;
         const unsigned char* rsrc = nullptr;
         if (s.fwd_plane && s.fwd_line) {
@@ -488,42 +518,81 @@ __global__ void __launch_bounds__(32) k_nf_apply(const SysTab* __restrict__ tab,
             rbytes = (unsigned)(e - a);
             rsrc = reinterpret_cast<const unsigned char*>(r) + a;
         }
-        tma::mbar_expect_tx(&bar[2 * b], (unsigned)LB + rbytes);
-        tma::bulk_load(pk_base + b * LB, static_cast<const unsigned char*>(d.pack) + (size_t)(s.j * bx + s.l) * LB,
-                       (unsigned)LB, &bar[2 * b]);
+        // (packet field, slot field, count) of each copy
+        int f[3][3] = {{PK_GI, 0, 3}, {0, 0, 0}, {0, 0, 0}};
+        if (!s.fwd_line) {
+            f[1][0] = PK_U2, f[1][1] = SL_X, f[1][2] = 1;
+        } else if (s.fwd_plane) {
+            f[1][0] = PK_L2, f[1][1] = SL_X, f[1][2] = 2;  // L2, L3
+        } else {
+            f[1][0] = PK_L2, f[1][1] = SL_X, f[1][2] = 1;
+            f[2][0] = PK_U3, f[2][1] = SL_Y, f[2][2] = 1;
+        }
+        unsigned tx = rbytes;
+        for (int i = 0; i < 3; i++) tx += (unsigned)f[i][2] * fb;
+        tma::mbar_expect_tx(&bar[2 * b], tx);
+        const unsigned char* src = static_cast<const unsigned char*>(d.pack) + (size_t)(s.j * bx + s.l) * LB;
+        for (int i = 0; i < 3; i++)
+            if (f[i][2] > 0)
+                tma::bulk_load(pk_base + b * SB + (size_t)f[i][1] * fb, src + (size_t)f[i][0] * fb,
+                               (unsigned)f[i][2] * fb, &bar[2 * b]);
         if (rbytes) tma::bulk_load(r_base + b * RB, rsrc, rbytes, &bar[2 * b]);
     };
 
+    LineStep nx, s;  // the next line solve to issue, the one in progress
+    nx.set(bx, by);
+    s.set(bx, by);
+    int ni = 0, bi = 0;  // line solves issued, slot of the next issue
     if (lane == 0) {
-        for (int b = 0; b < SLOTS; b++) tma::mbar_init(&bar[2 * b], 1);
+        for (int b = 0; b <= SLOTS; b++) tma::mbar_init(&bar[2 * b], 1);
         tma::fence_mbar_init();
-        for (int k = 0; k < SLOTS - 1 && k < K; k++) issue(k);
     }
     __syncwarp();
+    for (; ni < SLOTS - 1 && ni < K; ni++) {
+        if (lane == 0) issue(nx, bi);
+        nx.next(bx, by);
+        bi = bi + 1 == SLOTS ? 0 : bi + 1;
+    }
+    bool ypend = false;
+    // a wait that expired: report it, wait (bounded) for the copies still in flight, and leave
+    const auto fail = [&](int k) {
+        if (lane == 0) {
+            atomicExch(st.dev_err, 7);
+            for (int k2 = k; k2 < ni; k2++) tma::mbar_wait(&bar[2 * (k2 % SLOTS)], (unsigned)(k2 / SLOTS) & 1u);
+            if (ypend) tma::mbar_wait(ybar, (unsigned)(by - 2 - s.j) & 1u);
+        }
+    };
+    int bc = 0;
+    unsigned ph = 0;  // slot and barrier phase of the line solve in progress
     for (int k = 0; k < K; k++) {
         // line solve k + SLOTS - 1 goes into the slot that line solve k - 1 has finished with
-        if (lane == 0 && k + SLOTS - 1 < K) issue(k + SLOTS - 1);
-        const int b = k % SLOTS;
-        const bool ok = tma::mbar_wait(&bar[2 * b], (unsigned)(k / SLOTS) & 1u);
-        if (!__all_sync(kFull, ok)) {
-            // a copy did not land in time: report it, wait (bounded) for the copies in flight
+        if (ni < K) {
+            if (lane == 0) issue(nx, bi);
+            nx.next(bx, by);
+            bi = bi + 1 == SLOTS ? 0 : bi + 1;
+            ni++;
+        }
+        if (s.plane_first && !s.fwd_plane) {  // y_j of this backward plane, needed when it is done
             if (lane == 0) {
-                atomicExch(st.dev_err, 7);
-                for (int k2 = k; k2 < K && k2 < k + SLOTS; k2++)
-                    tma::mbar_wait(&bar[2 * (k2 % SLOTS)], (unsigned)(k2 / SLOTS) & 1u);
+                tma::mbar_expect_tx(ybar, (unsigned)PB);
+                tma::bulk_load(yb, yv + (size_t)s.j * PB, (unsigned)PB, ybar);
             }
+            ypend = true;
+        }
+        const bool ok = tma::mbar_wait(&bar[2 * bc], ph);
+        if (!__all_sync(kFull, ok)) {
+            fail(k);
             return;
         }
-        const LineStep s = line_step(k, bx, by);
-        const T* pk = reinterpret_cast<const T*>(pk_base + b * LB);
-        const auto blk = [&](int f, int q) { return pk + ((size_t)f * bz + q) * BS; };
+        const T* pk = reinterpret_cast<const T*>(pk_base + bc * SB);
+        const auto blk = [&](int f, int q) { return pk + f * fe + (size_t)q * BS; };
         T* pl = pv + (size_t)VS * s.l * bz;  // this line's part of the plane vector
         // c = G^{-1} u, u the line's right-hand side:
         //   forward line of a forward plane:   u = r - L3 y_{j-1} - L2 z_{l-1}
         //   forward line of a backward plane:  u = U3 x_{j+1} - L2 z_{l-1}
         //   backward line:                     u = U2 o_{l+1}
         // (a product that is added goes through sub_mv with the vector negated, which is exact)
-        const double* rl = reinterpret_cast<const double*>(r_base + b * RB) + (cell0_of(s) & 1);
+        const double* rl = reinterpret_cast<const double*>(r_base + bc * RB) + (cell0_of(s) & 1);
         for (int q = lane; q < bz; q += 32) {
             T u0 = 0, u1 = 0, u2 = 0, x0, x1, x2;
             const T* cur = pl + VS * q;
@@ -534,19 +603,19 @@ __global__ void __launch_bounds__(32) k_nf_apply(const SysTab* __restrict__ tab,
                     u2 = (T)rl[3 * q + 2];
                     if (s.j > 0) {
                         ld3(cur, x0, x1, x2);
-                        sub_mv(blk(PK_L3, q), x0, x1, x2, u0, u1, u2);
+                        sub_mv(blk(SL_Y, q), x0, x1, x2, u0, u1, u2);  // L3
                     }
                 } else {
                     ld3(cur, x0, x1, x2);
-                    sub_mv(blk(PK_U3, q), -x0, -x1, -x2, u0, u1, u2);
+                    sub_mv(blk(SL_Y, q), -x0, -x1, -x2, u0, u1, u2);  // U3
                 }
                 if (s.l > 0) {
                     ld3(cur - VS * bz, x0, x1, x2);
-                    sub_mv(blk(PK_L2, q), x0, x1, x2, u0, u1, u2);
+                    sub_mv(blk(SL_X, q), x0, x1, x2, u0, u1, u2);  // L2
                 }
             } else {
                 ld3(cur + VS * bz, x0, x1, x2);
-                sub_mv(blk(PK_U2, q), -x0, -x1, -x2, u0, u1, u2);
+                sub_mv(blk(SL_X, q), -x0, -x1, -x2, u0, u1, u2);  // U2
             }
             T c0 = 0, c1 = 0, c2 = 0;
             sub_mv(blk(PK_GI, q), -u0, -u1, -u2, c0, c1, c2);
@@ -560,21 +629,31 @@ __global__ void __launch_bounds__(32) k_nf_apply(const SysTab* __restrict__ tab,
         }
         __syncwarp();
         if (s.plane_done) {  // pv = P_j^{-1} t
-            T* yj = yv + 3 * (size_t)s.j * S;
             if (s.fwd_plane) {
-                if (s.j < by - 1)
-                    for (int e = lane; e < 3 * S; e += 32) yj[e] = pv[VS * (e / 3) + e % 3];  // y_j
-                else
+                if (s.j < by - 1) {  // y_j to device memory, ordered before its later bulk copy back
+                    T* yj = reinterpret_cast<T*>(yv + (size_t)s.j * PB);
+                    for (int e = lane; e < VS * S; e += 32) yj[e] = pv[e];
+                    asm volatile("fence.proxy.async;" ::: "memory");
+                } else {
                     write_owned(d, s.j, pv, z, lane);  // x_{by-1} = y_{by-1}
-            } else {
-                for (int e = lane; e < 3 * S; e += 32) {  // x_j = y_j - pv
-                    T& x = pv[VS * (e / 3) + e % 3];
-                    x = yj[e] - x;
                 }
+            } else {
+                const bool yok = tma::mbar_wait(ybar, (unsigned)(by - 2 - s.j) & 1u);
+                if (!__all_sync(kFull, yok)) {
+                    fail(k + 1);
+                    return;
+                }
+                ypend = false;
+                for (int e = lane; e < VS * S; e += 32) pv[e] = yb[e] - pv[e];  // x_j = y_j - pv
                 __syncwarp();
                 write_owned(d, s.j, pv, z, lane);
             }
             __syncwarp();
+        }
+        s.next(bx, by);
+        if (++bc == SLOTS) {
+            bc = 0;
+            ph ^= 1u;
         }
     }
 }
@@ -598,14 +677,16 @@ void nf_apply_s(const SysTab* tab, const NFDesc* descs, int ndesc, int slots, si
 }  // namespace
 
 size_t nf_line_bytes(int bz, int prec) {
-    const size_t t = prec == 0 ? 8 : 4, bs = prec == 0 ? 9 : 12;
-    return (PK_FIELDS * bs * (size_t)bz * t + 15) & ~(size_t)15;
+    return PK_FIELDS * (prec == 0 ? field_bytes<double>(bz) : field_bytes<float>(bz));
 }
+
+size_t nf_plane_bytes(int S, int prec) { return prec == 0 ? nf_plane_bytes<double>(S) : nf_plane_bytes<float>(S); }
 
 size_t nf_apply_smem(int bx, int bz, int prec, int slots) {
     const size_t t = prec == 0 ? 8 : 4, vs = prec == 0 ? 3 : 4;
-    return slots * (16 + nf_line_bytes(bz, prec) + nf_rline_bytes(bz)) + ((vs * (size_t)bx * bz * t + 15) & ~(size_t)15) +
-           vs * (size_t)bz * t;
+    const size_t fb = prec == 0 ? field_bytes<double>(bz) : field_bytes<float>(bz);
+    return 16 * (size_t)(slots + 1) + slots * (SL_FIELDS * fb + nf_rline_bytes(bz)) +
+           2 * nf_plane_bytes(bx * bz, prec) + vs * (size_t)bz * t;
 }
 
 size_t nf_work_doubles(int bx, int by, int bz) {
