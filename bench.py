@@ -274,6 +274,69 @@ def run_batch(args, stream):
             "all_converged": all(i["converged"] for i in infos), "worst_true_rel_residual": worst}
 
 
+def nf_apply_bytes(w, elem: int) -> int:
+    """Algorithmic bytes of one nested-factorisation apply on workload w: every line solve reads the
+    fields of its line's packet it needs (G^-1, M, N, then L2 + L3, L2 + U3 or U2: 9 values per cell
+    each), r comes in once (FP64), y_j goes out and back once per plane but the last, and the owned
+    cells go out once (FP64)."""
+    def spans(n, p, ov):
+        return [min(n, n * (t + 1) // p + ov) - max(0, n * t // p - ov) for t in range(p)]
+    tot = 24 * w.nx * w.ny * w.nz
+    for bx in spans(w.nx, w.px, w.overlap):
+        for by in spans(w.ny, w.py, w.overlap):
+            for bz in spans(w.nz, w.pz, w.overlap):
+                field = 9 * elem * bz
+                fwd = by * bx + (by - 1) * bx            # forward lines of the forward and backward planes
+                bwd = by * (bx - 1) + (by - 1) * (bx - 1)  # backward lines
+                tot += (5 * fwd + 4 * bwd) * field + 24 * bx * by * bz + 2 * 3 * elem * bx * bz * (by - 1)
+    return tot
+
+
+def run_nf(args, stream, w, w_system, vals_d, b_d):
+    """Nested factorisation with column-sum compensation (Appendix A) as the local solver, on the
+    same system, partition and overlap without lumps (near width 0, no far field); FP32 apply,
+    GMRES(restart) to 1e-8.  A step is the main line's: update values + re-factor + solve."""
+    import torch
+    from paper_1401_7227_gb300 import asm2
+    sol = asm2.Solver(precision="fp32", restart=w.restart, local_solver="nf_colsum", stream=stream.cuda_stream)
+    sol.set_grid(w.nx, w.ny, w.nz)
+    sol.set_matrix(w_system[0], w_system[1], vals_d)
+    sol.set_partition(w.px, w.py, w.pz, w.overlap, 0, (2, 2, 2), "none")
+    sol.factor()
+
+    def step():
+        sol.update_values(vals_d)
+        sol.factor()
+        return sol.solve(b_d, rtol=1e-8, max_iter=args.max_iter)
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    sol.reset_profile()
+    sol.set_profiling(True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        x, info = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    prof = sol.profile()
+    st = sol.stats()
+    sol.close()
+    apply_ms = prof["apply_ms"] / max(1, prof["apply_launches"])
+    alg = nf_apply_bytes(w, 4)
+    peak, peak_kind = peaks()
+    ach = alg / (apply_ms * 1e-3) / 1e9
+    return {"workload": f"{w.name} without lumps (near width 0, no far field), NF + colsum, FP32 apply",
+            "ms_per_step": ms, "iterations": info["iterations"], "converged": info["converged"],
+            "true_rel_residual": info["rel_residual"], "local_rows": st["local_rows"],
+            "breakdown_ms_per_step": {k: prof[k] / args.steps for k in ("apply_ms", "spmv_ms", "ortho_ms", "factor_ms")},
+            "apply": {"kernel": "k_nf_apply", "launch_ms": apply_ms, "alg_bytes_per_launch": alg, "achieved": ach,
+                      "peak": peak, "unit": "GB/s", "frac": ach / peak, "peak_kind": peak_kind,
+                      "bound": "latency (sequential line recurrences)"}}
+
+
 def run_profile_case(args):
     """Small case for ncu captures: 128 x 128 x 32 (16 x 16 x 1 subdomains, overlap 2), three
     preconditioner applies then one GMRES solve.  The apply runs with the local-vector placement the
@@ -296,6 +359,30 @@ def run_profile_case(args):
     torch.cuda.synchronize()
     x, info = sol.solve(b, 1e-8, 400)
     print(json.dumps({"profile_case": "grid128x128x32_k256", "info": info, "stats": sol.stats()}))
+    sol.close()
+    return 0
+
+
+def run_profile_nf(args):
+    """Case for ncu captures of the nested-factorisation apply: the 1M-cell workload's system
+    (128 x 128 x 64, 16 x 16 x 2 subdomains, overlap 2, no lumps), FP32 apply, three applies."""
+    import torch
+    from paper_1401_7227_gb300 import asm2
+    from paper_1401_7227_gb300 import build as lib_build
+    lib_build.build()
+    w = synth.WORKLOADS["grid128x128x64_k512"]
+    s = synth.make(w)
+    sol = asm2.Solver(precision="fp32", restart=w.restart, local_solver="nf_colsum")
+    sol.set_grid(w.nx, w.ny, w.nz)
+    sol.set_matrix(s.row_ptr, s.col_idx, s.vals)
+    sol.set_partition(w.px, w.py, w.pz, w.overlap, 0, (2, 2, 2), "none")
+    sol.factor()
+    b = torch.from_numpy(s.b).cuda()
+    for _ in range(3):
+        z = sol.apply(b)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": "nf_grid128x128x64_k512", "z_norm": float(torch.linalg.norm(z)),
+                      "alg_bytes_per_apply": nf_apply_bytes(w, 4), "stats": sol.stats()}))
     sol.close()
     return 0
 
@@ -491,6 +578,8 @@ def run_gpu(args):
                                 "detail": detail}
     for r_ in results.values():
         r_["solver"].close()
+    if not args.no_nf and rank == 0:
+        line["nf_local_solver"] = run_nf(args, stream, w, (system.row_ptr, system.col_idx), vals_d, b_d)
     if not args.no_batch and rank == 0:
         line["batch"] = run_batch(args, stream)
     if not args.no_serve and rank == 0:
@@ -515,8 +604,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-nf", action="store_true", help="skip the nested-factorisation leg")
     ap.add_argument("--batch-systems", type=int, default=256)
     ap.add_argument("--profile-case", action="store_true", help="small case for ncu captures")
+    ap.add_argument("--profile-nf", action="store_true", help="nested-factorisation apply case for ncu captures")
     ap.add_argument("--serve-requests", type=int, default=240)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-pool", type=int, default=12)
@@ -526,6 +617,8 @@ def main():
         return run_reference(args)
     if args.profile_case:
         return run_profile_case(args)
+    if args.profile_nf:
+        return run_profile_nf(args)
     return run_gpu(args)
 
 
