@@ -123,7 +123,7 @@ struct asm_ctx {
     std::vector<std::vector<int>> drow_of_q;     // local row of each dense block row (error location)
     int n_dinit = 0, n_ditems1 = 0, dpart_cap = 0, dmax3 = 0;
     // nested factorisation (ASM_LOCAL_NF_COLSUM / ASM_LOCAL_NF): band tables, G, G^{-1}, scratch
-    DBuf d_nfint, d_nfval, d_nfdesc1, d_nfpack, d_nfy;
+    DBuf d_nfint, d_nfval, d_nfdesc1, d_nfpack, d_nfy, d_nfband;
     size_t nf_smem = 0;                            // shared memory of the apply launch
     int nf_slots = 2, nf_bx_max = 0, nf_bz_max = 0;  // its ring depth; the largest line and plane
     std::vector<NFDesc> nf_desc;                   // sys = 0
@@ -301,11 +301,11 @@ void upload_nf(asm_ctx* h, cudaStream_t st) {
         int bx, by, bz, n, c0;
         int lo[3], olo[3], ohi[3];
         size_t bands;                         // int offset
-        long long g, gi, work, pack, yv;      // double / byte offsets
+        long long g, gi, work, pack, yv, band;  // double / byte offsets
     };
     std::vector<Part> parts(K);
     std::vector<int> ints;
-    long long nval = 0, npack = 0, ny = 0;
+    long long nval = 0, npack = 0, ny = 0, nband = 0;
     h->nf_smem = 0;
     h->nf_bx_max = h->nf_bz_max = 0;
     h->nf_row_of_cell.assign(K, {});
@@ -387,6 +387,8 @@ void upload_nf(asm_ctx* h, cudaStream_t st) {
         const size_t lb = nf_line_bytes(P.bz, h->prec);
         P.pack = npack;
         npack += (long long)(lb * (size_t)P.bx * P.by + 255) / 256 * 256;
+        P.band = nband;
+        nband += (63LL * o.n * (h->prec == 0 ? 8 : 4) + 255) / 256 * 256;
         P.yv = ny;
         ny += ((long long)nf_plane_bytes(P.bx * P.bz, h->prec) * P.by + 255) / 256 * 256;
         h->nf_bx_max = std::max(h->nf_bx_max, P.bx);
@@ -407,6 +409,7 @@ void upload_nf(asm_ctx* h, cudaStream_t st) {
     h->d_nfpack.alloc((size_t)std::max<long long>(256, npack));
     h->d_nfpack.zero(st);
     h->d_nfy.alloc((size_t)std::max<long long>(256, ny));
+    h->d_nfband.alloc((size_t)std::max<long long>(256, nband));
     h->nf_desc.assign(K, NFDesc{});
     const int* ib = h->d_nfint.as<int>();
     double* vb = h->d_nfval.as<double>();
@@ -435,6 +438,7 @@ void upload_nf(asm_ctx* h, cudaStream_t st) {
         d.work = vb + P.work;
         d.pack = h->d_nfpack.as<unsigned char>() + P.pack;
         d.yv = h->d_nfy.as<unsigned char>() + P.yv;
+        d.fband = h->d_nfband.as<unsigned char>() + P.band;
     }
     h->d_nfdesc1.upload(h->nf_desc, st);
     sync(h);

@@ -213,6 +213,7 @@ struct NFDesc {
     double* g;           // [9 n] the diagonal blocks G
     double* gi;          // [9 n] their inverses
     double* work;        // nf_work_doubles(bx, by, bz) doubles of scratch (factorisation)
+    void* fband;         // [7 n] the band blocks of each cell, compute type (factorisation)
     void* pack;          // [by * bx] line packets (16-byte aligned), compute type
     void* yv;            // [by] planes of the apply's forward result, nf_plane_bytes(bx bz) apart
 };

@@ -26,178 +26,200 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// ---- 3x3 blocks held one element per lane (lanes 0..8; other lanes carry zeros) --------------
+// ---- the factorisation: 3x3 blocks held one element per lane (lanes 0..8; others carry zeros) ----
 
-// element (r, c) of a block stored row-major at p (nullptr: a zero block)
-__device__ __forceinline__ double bload(const double* p, int lane) { return (p && lane < 9) ? p[lane] : 0.0; }
+// Each cell's seven band blocks D, L1, U1, L2, U2, L3, U3 (zero where the neighbour is missing),
+// gathered from the assembled slots into the compute type before the sequential factorisation,
+// so that its operand loads need no index and can be issued early.
+enum { BD_D = 0, BD_L1, BD_U1, BD_L2, BD_U2, BD_L3, BD_U3, BD_N };
+
+template <typename TC>
+__global__ void __launch_bounds__(128) k_nf_gather(const NFDesc* __restrict__ descs) {
+    const NFDesc& d = descs[blockIdx.y];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;  // (cell, band)
+    if (t >= BD_N * d.n) return;
+    const int sl = d.bands[t];
+    TC* o = static_cast<TC*>(d.fband) + 9LL * t;
+    for (int e = 0; e < 9; e++) o[e] = sl >= 0 ? (TC)d.slot[9LL * sl + e] : TC(0);
+}
 
 // a * b for blocks held per lane
-__device__ __forceinline__ double bmul(double a, double b, int lane) {
+template <typename TC>
+__device__ __forceinline__ TC bmul(TC a, TC b, int lane) {
     const int r = lane < 9 ? lane / 3 : 0, c = lane < 9 ? lane - 3 * (lane / 3) : 0;
-    const double a0 = __shfl_sync(kFull, a, 3 * r), a1 = __shfl_sync(kFull, a, 3 * r + 1),
-                 a2 = __shfl_sync(kFull, a, 3 * r + 2);
-    const double b0 = __shfl_sync(kFull, b, c), b1 = __shfl_sync(kFull, b, 3 + c), b2 = __shfl_sync(kFull, b, 6 + c);
-    return lane < 9 ? a0 * b0 + a1 * b1 + a2 * b2 : 0.0;
+    const TC a0 = __shfl_sync(kFull, a, 3 * r), a1 = __shfl_sync(kFull, a, 3 * r + 1), a2 = __shfl_sync(kFull, a, 3 * r + 2);
+    const TC b0 = __shfl_sync(kFull, b, c), b1 = __shfl_sync(kFull, b, 3 + c), b2 = __shfl_sync(kFull, b, 6 + c);
+    return lane < 9 ? a0 * b0 + a1 * b1 + a2 * b2 : TC(0);
 }
 
-// inverse of a block held per lane: lane 0 runs Gauss-Jordan with partial pivoting, the result is
-// spread back.  false (on every lane) for a zero pivot.
-__device__ bool binv(double a, double& inv, int lane) {
-    double m[3][6];
-#pragma unroll
-    for (int r = 0; r < 3; r++)
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            m[r][c] = __shfl_sync(kFull, a, 3 * r + c);
-            m[r][3 + c] = r == c ? 1.0 : 0.0;
-        }
-    int ok = 1;
-    if (lane == 0) {
-        for (int c = 0; c < 3 && ok; c++) {
-            int p = c;
-            for (int r = c + 1; r < 3; r++)
-                if (fabs(m[r][c]) > fabs(m[p][c])) p = r;
-            if (m[p][c] == 0.0) {
-                ok = 0;
-                break;
-            }
-            if (p != c)
-                for (int k = 0; k < 6; k++) {
-                    const double t = m[c][k];
-                    m[c][k] = m[p][k];
-                    m[p][k] = t;
-                }
-            const double id = 1.0 / m[c][c];
-            for (int k = 0; k < 6; k++) m[c][k] *= id;
-            for (int r = 0; r < 3; r++) {
-                if (r == c) continue;
-                const double f = m[r][c];
-                for (int k = 0; k < 6; k++) m[r][k] -= f * m[c][k];
-            }
-        }
-    }
-    ok = __shfl_sync(kFull, ok, 0);
-    double out = 0.0;
-#pragma unroll
-    for (int r = 0; r < 3; r++)
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            const double v = __shfl_sync(kFull, m[r][3 + c], 0);
-            if (lane == 3 * r + c) out = v;
-        }
-    inv = out;
-    return ok != 0;
+// Inverse of a block held per lane by cofactors: lane 3 r + c gets C_cr / det, with the cofactor
+// C_ij = a_{i+1,j+1} a_{i+2,j+2} - a_{i+1,j+2} a_{i+2,j+1} (indices mod 3) and det = sum_k a_0k C_0k.
+// Twelve dependent operations instead of the ~60 of an elimination on one lane (a dependent FP64
+// operation costs ~100 cycles here).  false (on every lane) when det = 0.
+template <typename TC>
+__device__ __forceinline__ bool binv(TC a, TC& inv, int lane) {
+    const int r = lane < 9 ? lane / 3 : 0, c = lane < 9 ? lane - 3 * (lane / 3) : 0;
+    const int i1 = c == 2 ? 0 : c + 1, i2 = c == 0 ? 2 : c - 1, j1 = r == 2 ? 0 : r + 1, j2 = r == 0 ? 2 : r - 1;
+    const TC p = __shfl_sync(kFull, a, 3 * i1 + j1), q = __shfl_sync(kFull, a, 3 * i2 + j2);
+    const TC u = __shfl_sync(kFull, a, 3 * i1 + j2), v = __shfl_sync(kFull, a, 3 * i2 + j1);
+    const TC cof = p * q - u * v;                       // C_cr
+    const TC term = __shfl_sync(kFull, a, r) * cof;     // lanes 3 r (c = 0): a_0r C_0r
+    const TC det = __shfl_sync(kFull, term, 0) + __shfl_sync(kFull, term, 3) + __shfl_sync(kFull, term, 6);
+    if (det == TC(0)) return false;
+    inv = lane < 9 ? cof / det : TC(0);
+    return true;
 }
 
+template <typename TC>
 struct NFView {
     const NFDesc& d;
-    __device__ const double* band(int k, int p) const {  // k: 0 D, 1 L1, 2 U1, 3 L2, 4 U2, 5 L3, 6 U3
-        const int s = d.bands[7 * p + k];
-        return s >= 0 ? d.slot + 9LL * s : nullptr;
-    }
+    __device__ const TC* band(int k, int p) const { return static_cast<const TC*>(d.fband) + 9LL * (BD_N * p + k); }
     __device__ const double* gi(int p) const { return d.gi + 9LL * p; }
 };
 
-// W = u T^{-1} on the line starting at cell q0: W (G + L1)(I + G^{-1} U1) = u (rows of blocks)
-__device__ void line_row_solve(const NFView& v, int q0, const double* u, double* vtmp, double* W, int lane) {
+// element `lane` of a block (lanes 9..31: zero)
+template <typename TC, typename TS>
+__device__ __forceinline__ TC ld(const TS* p, int lane) { return lane < 9 ? (TC)p[lane] : TC(0); }
+
+// W = u T^{-1} on the line starting at cell q0: W (G + L1)(I + G^{-1} U1) = u (rows of blocks).
+// Each loop loads the next step's operands before the current step's products.
+template <typename TC>
+__device__ void line_row_solve(const NFView<TC>& v, int q0, const TC* u, TC* vtmp, TC* W, int lane) {
     const int bz = v.d.bz;
-    double prev = 0.0;
+    TC prev = 0, nu = ld<TC>(u, lane), ngi = 0, nu1 = 0;
     for (int q = 0; q < bz; q++) {  // vtmp (I + G^{-1} U1) = u
-        double x = bload(u + 9 * q, lane);
-        if (q > 0) x -= bmul(bmul(prev, bload(v.gi(q0 + q - 1), lane), lane), bload(v.band(2, q0 + q - 1), lane), lane);
+        const TC cu = nu, cgi = ngi, cu1 = nu1;
+        if (q + 1 < bz) {
+            nu = ld<TC>(u + 9 * (q + 1), lane);
+            ngi = ld<TC>(v.gi(q0 + q), lane);
+            nu1 = ld<TC>(v.band(BD_U1, q0 + q), lane);
+        }
+        TC x = cu;
+        if (q > 0) x -= bmul(bmul(prev, cgi, lane), cu1, lane);
         if (lane < 9) vtmp[9 * q + lane] = x;
         prev = x;
     }
-    double next = 0.0;
+    __syncwarp();
+    TC next = 0, nv = ld<TC>(vtmp + 9 * (bz - 1), lane), nl1 = 0, ng = ld<TC>(v.gi(q0 + bz - 1), lane);
     for (int q = bz - 1; q >= 0; q--) {  // W (G + L1) = vtmp
-        double x = bload(vtmp + 9 * q, lane);
-        if (q < bz - 1) x -= bmul(next, bload(v.band(1, q0 + q + 1), lane), lane);
-        const double w = bmul(x, bload(v.gi(q0 + q), lane), lane);
+        const TC cv = nv, cl1 = nl1, cg = ng;
+        if (q > 0) {
+            nv = ld<TC>(vtmp + 9 * (q - 1), lane);
+            nl1 = ld<TC>(v.band(BD_L1, q0 + q), lane);
+            ng = ld<TC>(v.gi(q0 + q - 1), lane);
+        }
+        TC x = cv;
+        if (q < bz - 1) x -= bmul(next, cl1, lane);
+        const TC w = bmul(x, cg, lane);
         if (lane < 9) W[9 * q + lane] = w;
         next = w;
     }
     __syncwarp();
 }
 
-// W = u P^{-1} on the plane starting at c0 (rows of blocks); scratch: vb (9 S), x, y, vt (9 bz each)
-__device__ void plane_row_solve(const NFView& v, int c0, const double* u, double* vb, double* x, double* y, double* vt,
-                                double* W, int lane) {
-    const int bz = v.d.bz, bx = v.d.bx;
-    for (int l = 0; l < bx; l++) {  // vb (I + T^{-1} U2) = u
-        if (l > 0) line_row_solve(v, c0 + (l - 1) * bz, vb + 9 * (l - 1) * bz, vt, x, lane);
-        for (int q = 0; q < bz; q++) {
-            const int c = l * bz + q;
-            double e = bload(u + 9 * c, lane);
-            if (l > 0) e -= bmul(bload(x + 9 * q, lane), bload(v.band(4, c0 + c - bz), lane), lane);
-            if (lane < 9) vb[9 * c + lane] = e;
-        }
-        __syncwarp();
+// Independent block operations over n cells, one block element per lane and step (all 32 lanes):
+// dst_c = src_c - A_c B_c (SUB), dst_c = A_c B_c, or dst_c = src_c (no product); src, A, B give
+// each cell's block (src may be null: zero)
+template <bool SUB, typename TC, typename FS, typename FA, typename FB>
+__device__ __forceinline__ void blocks(TC* dst, int n, FS src, FA A, FB B, int lane) {
+    for (int t = lane; t < 9 * n; t += 32) {
+        const int c = t / 9, e = t - 9 * c, r = e / 3, k = e - 3 * r;
+        const TC* a = A(c);
+        const TC* b = B(c);
+        const TC* s0 = src(c);
+        TC v = 0;
+        if (a && b) v = a[3 * r] * b[k] + a[3 * r + 1] * b[3 + k] + a[3 * r + 2] * b[6 + k];
+        if (SUB) v = (s0 ? s0[e] : TC(0)) - v;
+        dst[9 * c + e] = v;
     }
-    for (int l = bx - 1; l >= 0; l--) {  // W (T + L2) = vb
-        for (int q = 0; q < bz; q++) {
-            const int c = l * bz + q;
-            double e = bload(vb + 9 * c, lane);
-            if (l < bx - 1) e -= bmul(bload(W + 9 * (c + bz), lane), bload(v.band(3, c0 + c + bz), lane), lane);
-            if (lane < 9) y[9 * q + lane] = e;
+    __syncwarp();
+}
+
+// W = u P^{-1} on the plane starting at c0 (rows of blocks); scratch: vb (9 S), x, y, vt (9 bz each)
+template <typename TC>
+__device__ void plane_row_solve(const NFView<TC>& v, int c0, const TC* u, TC* vb, TC* x, TC* y, TC* vt, TC* W,
+                                int lane) {
+    const int bz = v.d.bz, bx = v.d.bx;
+    const auto none = [](int) -> const TC* { return nullptr; };
+    for (int l = 0; l < bx; l++) {  // vb (I + T^{-1} U2) = u: vb_l = u_l - (vb_{l-1} T_{l-1}^{-1}) U2_{l-1}
+        const int cl = l * bz;
+        if (l > 0) {
+            line_row_solve(v, c0 + cl - bz, vb + 9 * (cl - bz), vt, x, lane);
+            blocks<true>(vb + 9 * cl, bz, [&](int q) { return u + 9 * (cl + q); }, [&](int q) { return x + 9 * q; },
+                         [&](int q) { return v.band(BD_U2, c0 + cl - bz + q); }, lane);
+        } else {
+            blocks<true>(vb, bz, [&](int q) { return u + 9 * q; }, none, none, lane);
         }
-        __syncwarp();
-        line_row_solve(v, c0 + l * bz, y, vt, W + 9 * l * bz, lane);
+    }
+    for (int l = bx - 1; l >= 0; l--) {  // W (T + L2) = vb: W_l = (vb_l - W_{l+1} L2_{l+1}) T_l^{-1}
+        const int cl = l * bz;
+        if (l < bx - 1)
+            blocks<true>(y, bz, [&](int q) { return vb + 9 * (cl + q); }, [&](int q) { return W + 9 * (cl + bz + q); },
+                         [&](int q) { return v.band(BD_L2, c0 + cl + bz + q); }, lane);
+        else
+            blocks<true>(y, bz, [&](int q) { return vb + 9 * (cl + q); }, none, none, lane);
+        line_row_solve(v, c0 + cl, y, vt, W + 9 * cl, lane);
     }
 }
 
-// Factorisation: G^{-1} of every cell, plane by plane, line by line, cell by cell
+// Factorisation in the compute type TC: G and G^{-1} (stored in FP64) of every cell, plane by
+// plane, line by line, cell by cell
+template <typename TC>
 __global__ void __launch_bounds__(128) k_nf_factor(const NFDesc* __restrict__ descs, int ndesc, FactErr* err) {
     const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (w >= ndesc) return;
     const NFDesc& d = descs[w];
-    const NFView v{d};
+    const NFView<TC> v{d};
     const int bz = d.bz, bx = d.bx, by = d.by, S = bz * bx;
     // scratch: cs3 (9 S), u (9 S), W (9 S), vb (9 S), x, y, vt, cs2 (9 bz each)
-    double* cs3 = d.work;
-    double* u = cs3 + 9 * S;
-    double* W = u + 9 * S;
-    double* vb = W + 9 * S;
-    double* x = vb + 9 * S;
-    double* y = x + 9 * bz;
-    double* vt = y + 9 * bz;
-    double* cs2 = vt + 9 * bz;
+    TC* cs3 = reinterpret_cast<TC*>(d.work);
+    TC* u = cs3 + 9 * S;
+    TC* W = u + 9 * S;
+    TC* vb = W + 9 * S;
+    TC* x = vb + 9 * S;
+    TC* y = x + 9 * bz;
+    TC* vt = y + 9 * bz;
+    TC* cs2 = vt + 9 * bz;
     for (int j = 0; j < by; j++) {
         const int c0 = j * S;
         const bool plane_term = d.colsum && j > 0;
+        const auto none = [](int) -> const TC* { return nullptr; };
         if (plane_term) {  // block column sums of L3 P_{j-1}^{-1} U3 on plane j
-            for (int c = 0; c < S; c++)
-                if (lane < 9) u[9 * c + lane] = bload(v.band(5, c0 + c), lane);
-            __syncwarp();
+            blocks<true>(u, S, [&](int c) { return v.band(BD_L3, c0 + c); }, none, none, lane);
             plane_row_solve(v, c0 - S, u, vb, x, y, vt, W, lane);
-            for (int c = 0; c < S; c++) {
-                const double e = bmul(bload(W + 9 * c, lane), bload(v.band(6, c0 - S + c), lane), lane);
-                if (lane < 9) cs3[9 * c + lane] = e;
-            }
-            __syncwarp();
+            blocks<false>(cs3, S, none, [&](int c) { return W + 9 * c; }, [&](int c) { return v.band(BD_U3, c0 - S + c); },
+                          lane);
         }
         for (int l = 0; l < bx; l++) {
             const int q0 = c0 + l * bz;
             const bool line_term = d.colsum && l > 0;
             if (line_term) {  // block column sums of L2 T_{l-1}^{-1} U2 on line l
-                for (int q = 0; q < bz; q++)
-                    if (lane < 9) u[9 * q + lane] = bload(v.band(3, q0 + q), lane);
-                __syncwarp();
+                blocks<true>(u, bz, [&](int q) { return v.band(BD_L2, q0 + q); }, none, none, lane);
                 line_row_solve(v, q0 - bz, u, vt, W, lane);
-                for (int q = 0; q < bz; q++) {
-                    const double e = bmul(bload(W + 9 * q, lane), bload(v.band(4, q0 - bz + q), lane), lane);
-                    if (lane < 9) cs2[9 * q + lane] = e;
-                }
-                __syncwarp();
+                blocks<false>(cs2, bz, none, [&](int q) { return W + 9 * q; },
+                              [&](int q) { return v.band(BD_U2, q0 - bz + q); }, lane);
             }
+            // G_p = D_p - L1_p G_{p-1}^{-1} U1_{p-1} - (line and plane column sums); the previous
+            // cell's G^{-1} stays in a register, the next cell's operands load early
+            TC gprev = 0;
+            TC nd = ld<TC>(v.band(BD_D, q0), lane), nl1 = 0, nu1 = 0;
+            TC nc2 = line_term ? ld<TC>(cs2, lane) : TC(0), nc3 = plane_term ? ld<TC>(cs3 + 9 * l * bz, lane) : TC(0);
             for (int q = 0; q < bz; q++) {
                 const int p = q0 + q;
-                double g = bload(v.band(0, p), lane);
-                if (q > 0) g -= bmul(bmul(bload(v.band(1, p), lane), bload(v.gi(p - 1), lane), lane),
-                                     bload(v.band(2, p - 1), lane), lane);
-                if (line_term) g -= bload(cs2 + 9 * q, lane);
-                if (plane_term) g -= bload(cs3 + 9 * (l * bz + q), lane);
-                if (lane < 9) d.g[9LL * p + lane] = g;
-                double gi;
+                const TC cd = nd, cl1 = nl1, cu1 = nu1, cc2 = nc2, cc3 = nc3;
+                if (q + 1 < bz) {
+                    nd = ld<TC>(v.band(BD_D, p + 1), lane);
+                    nl1 = ld<TC>(v.band(BD_L1, p + 1), lane);
+                    nu1 = ld<TC>(v.band(BD_U1, p), lane);
+                    if (line_term) nc2 = ld<TC>(cs2 + 9 * (q + 1), lane);
+                    if (plane_term) nc3 = ld<TC>(cs3 + 9 * (l * bz + q + 1), lane);
+                }
+                TC g = cd;
+                if (q > 0) g -= bmul(bmul(cl1, gprev, lane), cu1, lane);
+                g -= cc2;
+                g -= cc3;
+                if (lane < 9) d.g[9LL * p + lane] = (double)g;
+                TC gi;
                 if (!binv(g, gi, lane)) {
                     if (lane == 0 && atomicCAS(&err->flag, 0, 1) == 0) {
                         err->sub = d.sub;
@@ -205,13 +227,13 @@ __global__ void __launch_bounds__(128) k_nf_factor(const NFDesc* __restrict__ de
                     }
                     return;  // the whole warp leaves together (binv's result is warp-uniform)
                 }
-                if (lane < 9) d.gi[9LL * p + lane] = gi;
-                __syncwarp();
+                if (lane < 9) d.gi[9LL * p + lane] = (double)gi;
+                gprev = gi;
             }
+            __syncwarp();
         }
     }
 }
-
 
 // ---- the apply ---------------------------------------------------------------------------------
 
@@ -696,12 +718,17 @@ size_t nf_work_doubles(int bx, int by, int bz) {
 
 void launch_nf_factor(const NFDesc* descs, int ndesc, int nmax, int prec, FactErr* err, cudaStream_t st) {
     if (ndesc <= 0) return;
-    k_nf_factor<<<(ndesc + 3) / 4, 128, 0, st>>>(descs, ndesc, err);
+    const dim3 ggrid((unsigned)((BD_N * nmax + 127) / 128), (unsigned)ndesc);
     const dim3 grid((unsigned)((nmax + 127) / 128), (unsigned)ndesc);
-    if (prec == 0)
+    if (prec == 0) {
+        k_nf_gather<double><<<ggrid, 128, 0, st>>>(descs);
+        k_nf_factor<double><<<(ndesc + 3) / 4, 128, 0, st>>>(descs, ndesc, err);
         k_nf_pack<double><<<grid, 128, 0, st>>>(descs);
-    else
+    } else {
+        k_nf_gather<float><<<ggrid, 128, 0, st>>>(descs);
+        k_nf_factor<float><<<(ndesc + 3) / 4, 128, 0, st>>>(descs, ndesc, err);
         k_nf_pack<float><<<grid, 128, 0, st>>>(descs);
+    }
 }
 
 void launch_nf_apply(const SysTab* tab, const NFDesc* descs, int ndesc, int prec, int slots, size_t smem,
