@@ -340,7 +340,7 @@ def run_nf(args, stream, w, w_system, vals_d, b_d):
 def run_profile_case(args):
     """Small case for ncu captures: 128 x 128 x 32 (16 x 16 x 1 subdomains, overlap 2), three
     preconditioner applies then one GMRES solve.  The apply runs with the local-vector placement the
-    1M-cell workload gets (lump vector in shared memory, fine rows in device memory, 128-thread CTAs):
+    1M-cell workload gets (all local vectors in device memory, 128-thread CTAs, 24 KB ring slots):
     at half size the automatic choice would keep everything in shared memory."""
     import torch
     from paper_1401_7227_gb300 import asm2
@@ -352,7 +352,7 @@ def run_profile_case(args):
     sol.set_matrix(s.row_ptr, s.col_idx, s.vals)
     sol.set_partition(16, 16, 1, 2)
     sol.factor()
-    sol.set_tuning(apply_smem="lumps")
+    sol.set_tuning(apply_smem="device")
     b = torch.from_numpy(s.b).cuda()
     for _ in range(3):
         sol.apply(b)

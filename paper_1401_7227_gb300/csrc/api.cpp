@@ -91,6 +91,7 @@ struct asm_ctx {
     int apply_smem = 0;       // shared memory for all local vectors of the largest subdomain (0: none)
     int apply_lump_smem = 0;  // shared memory for its lump vector and the FP32 mirror
     int apply_slots = 3; // factor-stream ring slots of the apply
+    int chunk_cap = kStreamChunkMin;  // largest stream-chunk capacity of the subdomains (ring slot bytes)
     int sm_smem = 0, n_sms = 1;  // shared memory per SM and SM count of the device
     DBuf d_factdesc, d_subdesc_single;
     DBuf d_err;
@@ -564,6 +565,7 @@ void upload_symbolic(asm_ctx* h) {
     h->sub_cost.assign(K, 0.0);
     h->apply_smem = 0;
     h->apply_lump_smem = 0;
+    h->chunk_cap = kStreamChunkMin;
     h->tuned_ymode = -1;
     for (int s = 0; s < K; s++) {
         const SubSym& o = S.subs[s];
@@ -601,6 +603,8 @@ void upload_symbolic(asm_ctx* h) {
         sd.n_own = (int)o.own_pos.size();
         sd.n_long = (int)o.clong.size();
         sd.corr0 = corr_base;
+        sd.chunk_cap = o.chunk_cap;
+        h->chunk_cap = std::max(h->chunk_cap, o.chunk_cap);
         sd.stream = h->d_stream.as<unsigned char>() + h->stream_base[s];
         sd.y = h->d_y.as<double>() + h->y_base[s];
         {
@@ -669,11 +673,11 @@ void upload_symbolic(asm_ctx* h) {
     ck(cudaDeviceGetAttribute(&h->n_sms, cudaDevAttrMultiProcessorCount, h->device));
     h->apply_slots = 4;
     for (int sl = 4; sl >= 2; sl--)
-        if (2 * ((size_t)h->apply_smem + apply_ring_bytes(sl) + 1024) <= (size_t)sm_smem) {
+        if (2 * ((size_t)h->apply_smem + apply_ring_bytes(sl, h->chunk_cap) + 1024) <= (size_t)sm_smem) {
             h->apply_slots = sl;
             break;
         }
-    if ((size_t)h->apply_smem + apply_ring_bytes(h->apply_slots) > (size_t)dev_smem - 1024) {
+    if ((size_t)h->apply_smem + apply_ring_bytes(h->apply_slots, h->chunk_cap) > (size_t)dev_smem - 1024) {
         h->apply_smem = 0;
         h->apply_slots = 3;
     }
@@ -981,8 +985,8 @@ namespace {
 struct Batch {
     std::vector<asm_ctx*> hs;
     DBuf d_tab, d_vec, d_row, d_box, d_sub, d_gather;
-    int nvec = 0, nrow = 0, nbox = 0, nsub = 0, prec = 0, slots = 3;
-    ApplyConfig apply{Y_DEVICE, 0, 2};
+    int nvec = 0, nrow = 0, nbox = 0, nsub = 0, prec = 0, slots = 3, chunk = kStreamChunkMin;
+    ApplyConfig apply{Y_DEVICE, 0, 2, kStreamChunkMin};
     int all_bytes = 0, lump_bytes = 0;  // largest subdomain's shared-memory needs (placements)
     DBuf d_dense;           // exact local solves: (subdomain item, first owned row of 8)
     int ndense = 0;
@@ -1093,10 +1097,14 @@ void build_batch(Batch& B, cudaStream_t st) {
     B.all_bytes = all_bytes;
     B.lump_bytes = lump_bytes;
     B.slots = 4;
-    for (asm_ctx* h : B.hs) B.slots = std::min(B.slots, h->apply_slots);
+    B.chunk = kStreamChunkMin;
+    for (asm_ctx* h : B.hs) {
+        B.slots = std::min(B.slots, h->apply_slots);
+        B.chunk = std::max(B.chunk, h->chunk_cap);
+    }
     if (!B.hs.empty())
-        B.apply = apply_local_vectors(B.nsub, all_bytes, lump_bytes, B.slots, B.hs[0]->sm_smem, B.hs[0]->n_sms,
-                                      B.hs[0]->apply_place);
+        B.apply = apply_local_vectors(B.nsub, all_bytes, lump_bytes, B.slots, B.chunk, B.hs[0]->sm_smem,
+                                      B.hs[0]->n_sms, B.hs[0]->apply_place);
 }
 
 // events bracketing the launch groups of one step: [prep | apply | post | spmv | mgs+finish]
@@ -1123,7 +1131,7 @@ std::vector<ApplyConfig> apply_candidates(const Batch& B) {
     if (h->apply_place != 0) return {B.apply};
     for (int force : {Y_SMEM + 1, Y_LUMPS + 1, Y_DEVICE + 1}) {
         const ApplyConfig a =
-            apply_local_vectors(B.nsub, B.all_bytes, B.lump_bytes, B.slots, h->sm_smem, h->n_sms, force);
+            apply_local_vectors(B.nsub, B.all_bytes, B.lump_bytes, B.slots, B.chunk, h->sm_smem, h->n_sms, force);
         if (a.ymode == force - 1) c.push_back(a);
     }
     return c;
@@ -1927,8 +1935,8 @@ int asm_apply_precond(asm_handle h, const double* r, double* z, int on_device) {
         } else {
             const int nsub = (int)h->sub_desc.size();
             launch_apply(h->d_tab1.as<SysTab>(), h->d_subdesc_single.as<SubDesc>(), nsub, h->prec,
-                         apply_local_vectors(nsub, h->apply_smem, h->apply_lump_smem, h->apply_slots, h->sm_smem,
-                                             h->n_sms, h->apply_place),
+                         apply_local_vectors(nsub, h->apply_smem, h->apply_lump_smem, h->apply_slots, h->chunk_cap,
+                                             h->sm_smem, h->n_sms, h->apply_place),
                          h->stream);
         }
         if (h->tab.cmode != 0)

@@ -14,7 +14,9 @@ namespace asm2 {
 // (n3 = 3 * n_cells rounded up to VEC_CHUNK), addressed by slot number.
 // ---------------------------------------------------------------------------------------------
 constexpr int VEC_CHUNK = 4096;   // elements per vector work item (256 threads x 16)
-constexpr int kStreamChunk = 8192;   // bytes of one factor-stream chunk / shared-memory ring slot
+// bytes of one factor-stream chunk (= one shared-memory ring slot of the apply): chosen per subdomain
+// so that its largest fine level fits one chunk, within [kStreamChunkMin, kStreamChunkMax]
+constexpr int kStreamChunkMin = 8192, kStreamChunkMax = 24576;
 constexpr int kStreamSlots = 3;      // default ring slots of the apply (chunks in flight per CTA)
 constexpr int kLongLumpRow = 16;     // lump rows with more stored blocks are swept by a whole warp
 // The apply runs one CTA per subdomain.  With all its local vectors in shared memory a CTA has 256
@@ -28,6 +30,7 @@ struct ApplyConfig {
     int ymode;  // ApplyY
     int smem;   // dynamic shared memory of the vectors (bytes)
     int slots;  // factor-stream ring slots (2 for the 128-thread variants: deeper rings gain nothing)
+    int chunk;  // bytes of one ring slot: the largest chunk capacity of the launch's subdomains
 };
 // Chunk header word 6: bit 0 = last chunk of its wavefront level; bits 8..11 = log2 of the entry
 // slots S of the short lump rows (each such row takes 3 S lanes: 3 output components x S slots).
@@ -159,6 +162,7 @@ struct SubDesc {
     int n_own;
     int n_long;       // lump rows restricted by a whole warp
     int corr0;        // first correction sum of this subdomain in SysTab::corr
+    int chunk_cap;    // bytes of this subdomain's ring slots (its largest chunk fits one)
     const double* dinv;          // exact local solves: [A_i | A_i^{-1}] (3n x 6n), fine then lump order
     const int2* chunks;          // (byte offset, bytes) of every chunk, consumption order
     const unsigned char* stream; // 16-byte aligned
@@ -242,13 +246,14 @@ void launch_apply(const SysTab* st_tab, const SubDesc* subs, int nsub, int prec,
 size_t apply_smem_bytes(int nf, int nc, int prec);  // all local vectors of one subdomain
 size_t apply_lump_bytes(int nc, int prec);          // its lump vector and the FP32 mirror
 // Placement of one apply launch's local vectors.  all_bytes / lump_bytes: the largest subdomain's
-// needs (0: not available); smem_slots: ring slots of the all-shared-memory variant; force: 0
+// needs (0: not available); smem_slots: ring slots of the all-shared-memory variant; chunk: bytes of
+// one ring slot (the largest chunk capacity of the launch's subdomains); force: 0
 // automatic (all in shared memory while the launch's nsub CTAs run at once at that occupancy, else
 // lumps in shared memory when four CTAs fit, else device memory), Y_SMEM + 1 / Y_LUMPS + 1 /
 // Y_DEVICE + 1 to ask for one placement (taken when it fits).
-ApplyConfig apply_local_vectors(int nsub, int all_bytes, int lump_bytes, int smem_slots, int sm_smem, int sms,
-                                int force);
-size_t apply_ring_bytes(int slots);
+ApplyConfig apply_local_vectors(int nsub, int all_bytes, int lump_bytes, int smem_slots, int chunk, int sm_smem,
+                                int sms, int force);
+size_t apply_ring_bytes(int slots, int chunk);
 void launch_spmv(const SysTab* st_tab, const RowItem* items, int nitems, cudaStream_t st);
 
 void launch_init(const SysTab* tab, const VecItem* items, int nitems, cudaStream_t st);

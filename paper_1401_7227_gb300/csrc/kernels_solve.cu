@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(YM == Y_SMEM ? 256 : kApplyThreadsDev, YM == Y
     const double* __restrict__ r = st.ws + (long long)in * st.n3p;
     double* __restrict__ z = st.ws + (long long)out * st.n3p;
     unsigned char* ring = smem_raw;
-    constexpr int ring_bytes = SLOTS * kStreamChunk;
+    const int cap = sd.chunk_cap, ring_bytes = SLOTS * cap;  // this subdomain's ring slots
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + ring_bytes);
     // local vectors: lumps (FP64), fine rows (factor precision), FP32 mirror of the lumps; laid out
     // [yc | yf | ycf] in shared or device memory, or [yc | ycf] in shared memory with yf in device
@@ -483,7 +483,7 @@ __global__ void __launch_bounds__(YM == Y_SMEM ? 256 : kApplyThreadsDev, YM == Y
         for (int k = 0; k < SLOTS && k < sd.n_chunks; k++) {
             const int2 ch = sd.chunks[k];
             mbar_expect_tx(&bar[k], (unsigned)ch.y);
-            bulk_load(ring + (size_t)k * kStreamChunk, sd.stream + ch.x, (unsigned)ch.y, &bar[k]);
+            bulk_load(ring + (size_t)k * cap, sd.stream + ch.x, (unsigned)ch.y, &bar[k]);
         }
 
     // restriction R_i r (overlaps the first chunk copies)
@@ -502,7 +502,7 @@ __global__ void __launch_bounds__(YM == Y_SMEM ? 256 : kApplyThreadsDev, YM == Y
         const bool ok = mbar_wait(&bar[slot], (unsigned)(ci / SLOTS) & 1u);
         bool fine_chunk = false;
         if (ok) {
-            const unsigned char* chunk = ring + (size_t)slot * kStreamChunk;
+            const unsigned char* chunk = ring + (size_t)slot * cap;
             fine_chunk = reinterpret_cast<const int*>(chunk)[1] > 0;
             sweep_chunk<TF>(chunk, ci < sd.n_fwd, yf, yc, ycf);
         }
@@ -519,7 +519,7 @@ __global__ void __launch_bounds__(YM == Y_SMEM ? 256 : kApplyThreadsDev, YM == Y
         if (ci + SLOTS < sd.n_chunks) {
             if (fine_chunk ? issuer_fine : issuer_lump) {
                 mbar_expect_tx(&bar[slot], (unsigned)next_ch.y);
-                bulk_load(ring + (size_t)slot * kStreamChunk, sd.stream + next_ch.x, (unsigned)next_ch.y, &bar[slot]);
+                bulk_load(ring + (size_t)slot * cap, sd.stream + next_ch.x, (unsigned)next_ch.y, &bar[slot]);
             }
             if ((issuer_fine || issuer_lump) && ci + SLOTS + 1 < sd.n_chunks) next_ch = sd.chunks[ci + SLOTS + 1];
         }
@@ -1198,16 +1198,18 @@ size_t apply_smem_bytes(int nf, int nc, int prec) {
     return prec == 0 ? 24 * ((size_t)nc + nf) : 24 * (size_t)nc + 12 * ((size_t)nf + nc);
 }
 
-size_t apply_ring_bytes(int slots) { return (size_t)slots * kStreamChunk + kRingHeader; }
+size_t apply_ring_bytes(int slots, int chunk) { return (size_t)slots * chunk + kRingHeader; }
 
 size_t apply_lump_bytes(int nc, int prec) { return prec == 0 ? 24 * (size_t)nc : 36 * (size_t)nc; }
 
-ApplyConfig apply_local_vectors(int nsub, int all_bytes, int lump_bytes, int smem_slots, int sm_smem, int sms,
-                                int force) {
-    const long long ring_all = (long long)apply_ring_bytes(smem_slots) + 1024, ring2 = (long long)apply_ring_bytes(2) + 1024;
+ApplyConfig apply_local_vectors(int nsub, int all_bytes, int lump_bytes, int smem_slots, int chunk, int sm_smem,
+                                int sms, int force) {
+    const long long ring_all = (long long)apply_ring_bytes(smem_slots, chunk) + 1024,
+                    ring2 = (long long)apply_ring_bytes(2, chunk) + 1024;
     const long long fit_all = all_bytes > 0 ? std::min<long long>(2, sm_smem / (all_bytes + ring_all)) : 0;
     const bool lumps_fit = lump_bytes > 0 && 4 * (lump_bytes + ring2) <= sm_smem;
-    const ApplyConfig all{Y_SMEM, all_bytes, smem_slots}, lumps{Y_LUMPS, lump_bytes, 2}, dev{Y_DEVICE, 0, 2};
+    const ApplyConfig all{Y_SMEM, all_bytes, smem_slots, chunk}, lumps{Y_LUMPS, lump_bytes, 2, chunk},
+        dev{Y_DEVICE, 0, 2, chunk};
     if (force == Y_SMEM + 1) return fit_all >= 1 ? all : dev;
     if (force == Y_LUMPS + 1) return lumps_fit ? lumps : dev;
     if (force == Y_DEVICE + 1) return dev;
@@ -1236,7 +1238,7 @@ void launch_apply_s(const SysTab* tab, const SubDesc* subs, int nsub, int smem, 
 }
 template <typename TF>
 void launch_apply_p(const SysTab* tab, const SubDesc* subs, int nsub, ApplyConfig cfg, int slots, cudaStream_t st) {
-    const int ring = (int)apply_ring_bytes(slots);
+    const int ring = (int)apply_ring_bytes(slots, cfg.chunk);
     if (cfg.ymode == Y_SMEM)
         launch_apply_s<TF, Y_SMEM>(tab, subs, nsub, ring + cfg.smem, slots, st);
     else if (cfg.ymode == Y_LUMPS)

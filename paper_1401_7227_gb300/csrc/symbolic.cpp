@@ -25,7 +25,6 @@ inline int split_lo(int n, int p, int t) { return (int)((long long)n * t / p); }
 // lump rows whose restriction list is longer than this are summed by a whole warp
 constexpr int kLongList = 16;
 // largest factor-stream chunk (one shared-memory ring slot of the apply)
-constexpr int kChunkBytes = asm2::kStreamChunk;
 inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 struct Box {
@@ -438,7 +437,7 @@ std::string build_sub(const Ctx& X, int s, SubSym& o) {
     o.cells_of_row = rowcells;
     for (int J : far_box_of_row) o.cells_of_row.push_back(-1 - J);  // far rows: -1 - box
 
-    // Factor stream: self-contained chunks of at most kChunkBytes, each holding rows of one wavefront
+    // Factor stream: self-contained chunks of at most o.chunk_cap, each holding rows of one wavefront
     // level (fine rows at the factor precision, lump rows in FP64): all forward chunks in level
     // order, then all backward chunks in reverse level order -- the order the apply consumes them,
     // so the stream is read front to back.  Chunk layout (every array 16-byte aligned):
@@ -460,6 +459,22 @@ std::string build_sub(const Ctx& X, int s, SubSym& o) {
         if (!fwd) b += al16(fbb * nf_) + al16(72 * (size_t)nc_);
         return b;
     };
+    // chunk capacity: the largest fine level (forward or backward part) in one chunk, rounded up to
+    // 4 KB, within [kStreamChunkMin, kStreamChunkMax] (fewer chunks mean fewer barriers in the apply;
+    // larger ring slots mean fewer CTAs per SM, so small subdomains keep the smallest capacity)
+    {
+        size_t big = 0;
+        for (int l = 0; l < nlev; l++)
+            for (int pass = 0; pass < 2; pass++) {
+                int ef = 0;
+                for (int pos = o.lv_pos0[l]; pos < o.lv_pos0[l] + cntf[l]; pos++)
+                    ef += pass == 0 ? nl(o.row_of_pos[pos]) : nu(o.row_of_pos[pos]);
+                big = std::max(big, chunk_bytes(cntf[l], ef, 0, 0, pass == 0) + 256);
+            }
+        const size_t cap = (big + 4095) / 4096 * 4096;
+        o.chunk_cap = (int)std::min<size_t>(asm2::kStreamChunkMax, std::max<size_t>(asm2::kStreamChunkMin, cap));
+    }
+    const size_t kChunkBytes = (size_t)o.chunk_cap;
     for (int pass = 0; pass < 2; pass++) {
         const bool fwd = pass == 0;
         for (int li = 0; li < nlev; li++) {
@@ -472,7 +487,7 @@ std::string build_sub(const Ctx& X, int s, SubSym& o) {
                 while (pf < pf_end) {
                     const int p = o.row_of_pos[pf];
                     const int e = fwd ? nl(p) : nu(p);
-                    if (chunk_bytes(pc_.nf + 1, ef + e, 0, 0, fwd) > (size_t)kChunkBytes - 256) break;
+                    if (chunk_bytes(pc_.nf + 1, ef + e, 0, 0, fwd) > kChunkBytes - 256) break;
                     ef += e;
                     pc_.nf++;
                     pf++;
@@ -481,7 +496,7 @@ std::string build_sub(const Ctx& X, int s, SubSym& o) {
                     while (pc < pc_end) {
                         const int p = o.row_of_pos[pc];
                         const int e = fwd ? nl(p) : nu(p);
-                        if (chunk_bytes(pc_.nf, ef, pc_.nc + 1, ec + e, fwd) > (size_t)kChunkBytes) break;
+                        if (chunk_bytes(pc_.nf, ef, pc_.nc + 1, ec + e, fwd) > kChunkBytes) break;
                         ec += e;
                         pc_.nc++;
                         pc++;

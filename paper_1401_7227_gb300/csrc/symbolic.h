@@ -36,6 +36,7 @@ struct Pattern {
 
 struct SubSym {
     int n = 0, nf = 0, nn = 0, nfar = 0, nlev = 0, nslot = 0;
+    int chunk_cap = 0;    // capacity of this subdomain's stream chunks (kStreamChunkMin .. Max)
     // local pattern by local row, slot = CSR position
     std::vector<int> prp, pci, pdiag;
     // assembly: slot value = C[acs] (if >= 0) + sum of signed ELL blocks aloc[aptr[s] .. aptr[s+1])
