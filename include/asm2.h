@@ -75,7 +75,7 @@ typedef enum {
                                    (ASM_PREC_FP32; ASM_PREC_FP16S is refused at asm_create).  asm_factor
                                    returns ASM_ERR_INVALID_ARG when a local problem has lumps or a line of
                                    a fine box (its z extent) is too long for the apply's shared memory
-                                   (about 200 cells in FP64, 400 in FP32), and ASM_ERR_PATTERN when an
+                                   (about 180 cells in FP64, 280 in FP32), and ASM_ERR_PATTERN when an
                                    A_i has a block off the seven bands */
     ASM_LOCAL_NF = 4            /* nested factorisation without compensation: G = D - L1 G^{-1} U1
                                    (Eq. A.6); same conditions */

@@ -238,11 +238,11 @@ __global__ void __launch_bounds__(128) k_nf_factor(const NFDesc* __restrict__ de
 // ---- the apply ---------------------------------------------------------------------------------
 
 // fields of a line packet, each bz blocks, field after field.  A line solve copies only the fields
-// it reads into a ring slot of SL_FIELDS fields: G^{-1}, M, N always (slot fields 0-2), then L2
-// and L3 on a forward line of a forward plane, L2 and U3 on a forward line of a backward plane,
-// U2 on a backward line (slot fields 3, 4).
-enum { PK_GI = 0, PK_M, PK_N, PK_L2, PK_L3, PK_U3, PK_U2, PK_FIELDS };
-enum { SL_X = 3, SL_Y = 4, SL_FIELDS = 5 };
+// it reads into a ring slot of SL_FIELDS fields: G^{-1}, M, N, P, Q always (slot fields 0-4),
+// then L2 and L3 on a forward line of a forward plane, L2 and U3 on a forward line of a backward
+// plane, U2 on a backward line (slot fields 5, 6).
+enum { PK_GI = 0, PK_M, PK_N, PK_P, PK_Q, PK_L2, PK_L3, PK_U3, PK_U2, PK_FIELDS };
+enum { SL_X = 5, SL_Y = 6, SL_FIELDS = 7 };
 
 // Layout of the compute type: a 3x3 block is 3 rows of RS values (row r at r RS), a cell's
 // 3-vector takes VS values in shared memory.  FP32 pads both to 4, so that a row or a vector is one
@@ -291,8 +291,9 @@ __device__ __forceinline__ void sub_mv(const T* a, T x0, T x1, T x2, T& y0, T& y
 
 // packets of every line, one thread per cell: G^{-1}, M = G^{-1} L1 (the forward recurrence of
 // (G + L1) s = u is s_q = G_q^{-1} u_q - M_q s_{q-1}), N = G^{-1} U1 (the backward recurrence of
-// (I + G^{-1} U1) w = s is w_q = s_q - N_q w_{q+1}), and the blocks L2, U2, L3, U3 (zero where the
-// neighbour is missing); products in FP64, stored in the compute type (row padding stays zero)
+// (I + G^{-1} U1) w = s is w_q = s_q - N_q w_{q+1}), the two-step products P_q = M_q M_{q-1} and
+// Q_q = N_q N_{q+1}, and the blocks L2, U2, L3, U3 (zero where the neighbour is missing); products
+// in FP64, stored in the compute type (row padding stays zero)
 // bytes of one field of a line packet: bz blocks, rounded up to 16 bytes (a bulk-copy unit)
 template <typename T>
 __host__ __device__ __forceinline__ size_t field_bytes(int bz) {
@@ -316,17 +317,25 @@ __global__ void __launch_bounds__(128) k_nf_pack(const NFDesc* __restrict__ desc
         for (int r = 0; r < 3; r++)
             for (int c = 0; c < 3; c++) o[r * RS + c] = b ? (T)b[3 * r + c] : T(0);
     };
-    double gi[9], m[9];
-    for (int e = 0; e < 9; e++) gi[e] = d.gi[9LL * p + e];
-    put(PK_GI, gi);
-    for (int k = 1; k <= 2; k++) {
-        const double* b = band(k);
-        if (b)
-            for (int r = 0; r < 3; r++)
-                for (int c = 0; c < 3; c++)
-                    m[3 * r + c] = gi[3 * r] * b[c] + gi[3 * r + 1] * b[3 + c] + gi[3 * r + 2] * b[6 + c];
-        put(k == 1 ? PK_M : PK_N, b ? m : nullptr);
-    }
+    const auto mul = [](const double* a, const double* b, double* c) {
+        for (int r = 0; r < 3; r++)
+            for (int k = 0; k < 3; k++) c[3 * r + k] = a[3 * r] * b[k] + a[3 * r + 1] * b[3 + k] + a[3 * r + 2] * b[6 + k];
+    };
+    // G^{-1} L1 (k = 1) or G^{-1} U1 (k = 2) of cell pp; false where that band block is missing
+    const auto gib = [&](int pp, int k, double* out) {
+        const int sl = d.bands[7 * pp + k];
+        if (sl < 0) return false;
+        mul(d.gi + 9LL * pp, d.slot + 9LL * sl, out);
+        return true;
+    };
+    double m[9], m2[9], pq[9];
+    put(PK_GI, d.gi + 9LL * p);
+    const bool hm = gib(p, 1, m);
+    put(PK_M, hm ? m : nullptr);
+    put(PK_P, hm && q > 0 && gib(p - 1, 1, m2) ? (mul(m, m2, pq), pq) : nullptr);
+    const bool hn = gib(p, 2, m);
+    put(PK_N, hn ? m : nullptr);
+    put(PK_Q, hn && q + 1 < bz && gib(p + 1, 2, m2) ? (mul(m, m2, pq), pq) : nullptr);
     put(PK_L2, band(3));
     put(PK_U2, band(4));
     put(PK_L3, band(5));
@@ -381,112 +390,145 @@ __device__ __forceinline__ void write_owned(const NFDesc& d, int j, const T* pv,
     }
 }
 
-// The two recurrences of one line solve on one lane (FP32): s_q = c_q - M_q s_{q-1} over
-// q = 0 .. bz-1 in cb, then w_q = s_q - N_q w_{q+1} over q = bz-1 .. 0, with o_q = w_q (forward
-// line) or o_q -= w_q (backward line).  Four steps at a time: the group's operands are loaded
-// first, so the loads overlap the chains.
-__device__ __forceinline__ void line_recurrences(const float* M, const float* N, float* cb, float* o, int bz,
-                                                 bool fwd_line) {
-    const float4* Mv = reinterpret_cast<const float4*>(M);
-    const float4* Nv = reinterpret_cast<const float4*>(N);
+// One chain step x <- c + A x for a 3x3 block A (three float4 rows) and 3-vectors, one fused
+// chain per row
+__device__ __forceinline__ void chain_step(const float4* a, float4 c, float& x0, float& x1, float& x2) {
+    const float n0 = fmaf(a[0].z, x2, fmaf(a[0].y, x1, fmaf(a[0].x, x0, c.x)));
+    const float n1 = fmaf(a[1].z, x2, fmaf(a[1].y, x1, fmaf(a[1].x, x0, c.y)));
+    const float n2 = fmaf(a[2].z, x2, fmaf(a[2].y, x1, fmaf(a[2].x, x0, c.z)));
+    x0 = n0;
+    x1 = n1;
+    x2 = n2;
+}
+
+// x_q = c_q + A_q x_{q-d} for q = q0, q0 + d, ... (d = +-2; the x before q0 is zero), in place
+// in cb, on one lane (FP32).  Four steps make a group whose operands are loaded first.
+__device__ __forceinline__ void chain(const float* A, float* cb, int q0, int d, int count) {
+    const float4* Av = reinterpret_cast<const float4*>(A);
     float4* cv = reinterpret_cast<float4*>(cb);
-    float4* ov = reinterpret_cast<float4*>(o);
-    const auto step = [](const float4* m, float4 c, float& x0, float& x1, float& x2) {
-        const float n0 = fmaf(-m[0].z, x2, fmaf(-m[0].y, x1, fmaf(-m[0].x, x0, c.x)));
-        const float n1 = fmaf(-m[1].z, x2, fmaf(-m[1].y, x1, fmaf(-m[1].x, x0, c.y)));
-        const float n2 = fmaf(-m[2].z, x2, fmaf(-m[2].y, x1, fmaf(-m[2].x, x0, c.z)));
-        x0 = n0;
-        x1 = n1;
-        x2 = n2;
-    };
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-    int q = 0;
-    for (; q + 4 <= bz; q += 4) {
-        float4 m[12], c[4];
+    float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+    int i = 0;
+    for (; i + 4 <= count; i += 4) {
+        float4 a[12], c[4];
 #pragma unroll
         for (int u = 0; u < 4; u++) {
-            m[3 * u] = Mv[3 * (q + u)];
-            m[3 * u + 1] = Mv[3 * (q + u) + 1];
-            m[3 * u + 2] = Mv[3 * (q + u) + 2];
-            c[u] = cv[q + u];
+            const int q = q0 + d * (i + u);
+            a[3 * u] = Av[3 * q];
+            a[3 * u + 1] = Av[3 * q + 1];
+            a[3 * u + 2] = Av[3 * q + 2];
+            c[u] = cv[q];
         }
 #pragma unroll
         for (int u = 0; u < 4; u++) {
-            step(m + 3 * u, c[u], s0, s1, s2);
-            c[u] = make_float4(s0, s1, s2, 0.f);
+            chain_step(a + 3 * u, c[u], x0, x1, x2);
+            c[u] = make_float4(x0, x1, x2, 0.f);
         }
 #pragma unroll
-        for (int u = 0; u < 4; u++) cv[q + u] = c[u];
+        for (int u = 0; u < 4; u++) cv[q0 + d * (i + u)] = c[u];
     }
-    for (; q < bz; q++) {
-        const float4 m[3] = {Mv[3 * q], Mv[3 * q + 1], Mv[3 * q + 2]};
-        step(m, cv[q], s0, s1, s2);
-        cv[q] = make_float4(s0, s1, s2, 0.f);
-    }
-    float w0 = 0.f, w1 = 0.f, w2 = 0.f;
-    q = bz - 1;
-    for (; q >= 3; q -= 4) {
-        float4 m[12], c[4], a[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            m[3 * u] = Nv[3 * (q - u)];
-            m[3 * u + 1] = Nv[3 * (q - u) + 1];
-            m[3 * u + 2] = Nv[3 * (q - u) + 2];
-            c[u] = cv[q - u];
-            a[u] = fwd_line ? make_float4(0.f, 0.f, 0.f, 0.f) : ov[q - u];
-        }
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            step(m + 3 * u, c[u], w0, w1, w2);
-            a[u] = fwd_line ? make_float4(w0, w1, w2, 0.f) : make_float4(a[u].x - w0, a[u].y - w1, a[u].z - w2, 0.f);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; u++) ov[q - u] = a[u];
-    }
-    for (; q >= 0; q--) {
-        const float4 m[3] = {Nv[3 * q], Nv[3 * q + 1], Nv[3 * q + 2]};
-        step(m, cv[q], w0, w1, w2);
-        const float4 a = ov[q];
-        ov[q] = fwd_line ? make_float4(w0, w1, w2, 0.f) : make_float4(a.x - w0, a.y - w1, a.z - w2, 0.f);
+    for (; i < count; i++) {
+        const int q = q0 + d * i;
+        const float4 a[3] = {Av[3 * q], Av[3 * q + 1], Av[3 * q + 2]};
+        chain_step(a, cv[q], x0, x1, x2);
+        cv[q] = make_float4(x0, x1, x2, 0.f);
     }
 }
 
-// The same on three lanes (FP64: an FP64 instruction costs the same for one lane as for 32, so
-// lane r takes row r and the state is exchanged by shuffles)
-__device__ __forceinline__ void line_recurrences(const double* M, const double* N, double* cb, double* o, int bz,
-                                                 bool fwd_line, int lane) {
+// The same on three lanes (FP64: lane r takes row r, the state goes round by shuffles; an FP64
+// instruction costs the same for one lane as for 32)
+__device__ __forceinline__ void chain(const double* A, double* cb, int q0, int d, int count, int lane) {
     constexpr unsigned kRow = 0x7u;
-    const double* mr = M + 3 * lane;
-    double sv = 0, m0 = mr[0], m1 = mr[1], m2 = mr[2], c = cb[lane];
-    for (int q = 0; q < bz; q++) {
-        const int qn = q + 1 < bz ? q + 1 : q;
-        const double n0 = mr[9 * qn], n1 = mr[9 * qn + 1], n2 = mr[9 * qn + 2], cn = cb[3 * qn + lane];
-        const double s0 = __shfl_sync(kRow, sv, 0), s1 = __shfl_sync(kRow, sv, 1), s2 = __shfl_sync(kRow, sv, 2);
-        sv = fma(-m2, s2, fma(-m1, s1, fma(-m0, s0, c)));
-        cb[3 * q + lane] = sv;
-        m0 = n0;
-        m1 = n1;
-        m2 = n2;
-        c = cn;
+    double x = 0.0;
+    for (int i = 0; i < count; i++) {
+        const int q = q0 + d * i;
+        const double* a = A + 9 * q + 3 * lane;
+        const double a0 = a[0], a1 = a[1], a2 = a[2], c = cb[3 * q + lane];
+        const double x0 = __shfl_sync(kRow, x, 0), x1 = __shfl_sync(kRow, x, 1), x2 = __shfl_sync(kRow, x, 2);
+        x = fma(a2, x2, fma(a1, x1, fma(a0, x0, c)));
+        cb[3 * q + lane] = x;
     }
-    const double* nr = N + 3 * lane;
-    const int ql = bz - 1;
-    double wv = 0;
-    m0 = nr[9 * ql];
-    m1 = nr[9 * ql + 1];
-    m2 = nr[9 * ql + 2];
-    c = cb[3 * ql + lane];
-    for (int q = ql; q >= 0; q--) {
-        const int qn = q > 0 ? q - 1 : q;
-        const double n0 = nr[9 * qn], n1 = nr[9 * qn + 1], n2 = nr[9 * qn + 2], cn = cb[3 * qn + lane];
-        const double on = o[3 * q + lane];
-        const double w0 = __shfl_sync(kRow, wv, 0), w1 = __shfl_sync(kRow, wv, 1), w2 = __shfl_sync(kRow, wv, 2);
-        wv = fma(-m2, w2, fma(-m1, w1, fma(-m0, w0, c)));
-        o[3 * q + lane] = fwd_line ? wv : on - wv;
-        m0 = n0;
-        m1 = n1;
-        m2 = n2;
-        c = cn;
+}
+
+// T^{-1} of one line, c = G^{-1} u given in cb: s_q = c_q - M_q s_{q-1} (s_{-1} = 0), then
+// w_q = s_q - N_q w_{q+1} (w_bz = 0), with one level of recursive doubling: the sequential chains
+// visit every other cell,
+//   s_q = (c_q - M_q c_{q-1}) + P_q s_{q-2},  P_q = M_q M_{q-1}    (q odd)
+//   w_q = (s_q - N_q s_{q+1}) + Q_q w_{q+2},  Q_q = N_q N_{q+1}    (chain cells q = bz-2, bz-4, ...)
+// and the cells in between follow from their neighbours on all lanes, each lane finishing the
+// cells next to its own (three passes over the line besides the two chains).  On return o_q = w_q
+// (forward line) or o_q -= w_q (backward line).  Called by the whole warp.
+template <typename T>
+__device__ __forceinline__ void line_solve(const T* M, const T* N, const T* P, const T* Q, T* cb, T* o, int bz,
+                                           bool fwd_line, int lane) {
+    constexpr int BS = 3 * Lay<T>::RS, VS = Lay<T>::VS;
+    // y_q - B_q x_{q'} for cells of cb (a missing q' contributes nothing)
+    const auto sub = [&](const T* B, int q, int qx, T& y0, T& y1, T& y2) {
+        if (qx < 0 || qx >= bz) return;
+        T x0, x1, x2;
+        ld3(cb + VS * qx, x0, x1, x2);
+        sub_mv(B + BS * q, x0, x1, x2, y0, y1, y2);
+    };
+    // odd q: c_q - M_q c_{q-1}
+    for (int q = 1 + 2 * lane; q < bz; q += 64) {
+        T y0, y1, y2;
+        ld3(cb + VS * q, y0, y1, y2);
+        sub(M, q, q - 1, y0, y1, y2);
+        st3(cb + VS * q, y0, y1, y2);
+    }
+    __syncwarp();
+    if constexpr (sizeof(T) == 4) {
+        if (lane == 0) chain(P, cb, 1, 2, bz / 2);
+    } else {
+        if (lane < 3) chain(P, cb, 1, 2, bz / 2, lane);
+    }
+    __syncwarp();
+    // chain cells q = bz-2-2i: t_q = s_q - N_q s_{q+1}, the even one of q and q + 1 first finished
+    // as s_e = c_e - M_e s_{e-1} (it is this lane's: bz even, e = q; bz odd, e = q + 1)
+    for (int i = lane;; i += 32) {
+        const int q = bz - 2 - 2 * i;
+        if (q < 0) break;
+        T s0, s1, s2, n0, n1, n2;
+        ld3(cb + VS * q, s0, s1, s2);
+        ld3(cb + VS * (q + 1), n0, n1, n2);
+        if ((q & 1) == 0) {
+            sub(M, q, q - 1, s0, s1, s2);  // s_q
+        } else {
+            sub_mv(M + BS * (q + 1), s0, s1, s2, n0, n1, n2);  // s_{q+1} = c_{q+1} - M_{q+1} s_q
+            st3(cb + VS * (q + 1), n0, n1, n2);
+        }
+        sub_mv(N + BS * q, n0, n1, n2, s0, s1, s2);
+        st3(cb + VS * q, s0, s1, s2);
+    }
+    __syncwarp();
+    if constexpr (sizeof(T) == 4) {
+        if (lane == 0) chain(Q, cb, bz - 2, -2, bz / 2);
+    } else {
+        if (lane < 3) chain(Q, cb, bz - 2, -2, bz / 2, lane);
+    }
+    __syncwarp();
+    // the other cells q = bz-1-2i: w_q = s_q - N_q w_{q+1} (w_bz = 0); this lane then writes the
+    // output of q and of the chain cell q - 1 below it
+    const auto out = [&](int q, T w0, T w1, T w2) {
+        if (!fwd_line) {
+            T a0, a1, a2;
+            ld3(o + VS * q, a0, a1, a2);
+            w0 = a0 - w0;
+            w1 = a1 - w1;
+            w2 = a2 - w2;
+        }
+        st3(o + VS * q, w0, w1, w2);
+    };
+    for (int i = lane;; i += 32) {
+        const int q = bz - 1 - 2 * i;
+        if (q < 0) break;
+        T w0, w1, w2;
+        ld3(cb + VS * q, w0, w1, w2);
+        sub(N, q, q + 1, w0, w1, w2);
+        out(q, w0, w1, w2);
+        if (q > 0) {
+            ld3(cb + VS * (q - 1), w0, w1, w2);
+            out(q - 1, w0, w1, w2);
+        }
     }
 }
 
@@ -541,7 +583,7 @@ __global__ void __launch_bounds__(32) k_nf_apply(const SysTab* __restrict__ tab,
             rsrc = reinterpret_cast<const unsigned char*>(r) + a;
         }
         // (packet field, slot field, count) of each copy
-        int f[3][3] = {{PK_GI, 0, 3}, {0, 0, 0}, {0, 0, 0}};
+        int f[3][3] = {{PK_GI, 0, PK_Q + 1}, {0, 0, 0}, {0, 0, 0}};
         if (!s.fwd_line) {
             f[1][0] = PK_U2, f[1][1] = SL_X, f[1][2] = 1;
         } else if (s.fwd_plane) {
@@ -644,11 +686,7 @@ __global__ void __launch_bounds__(32) k_nf_apply(const SysTab* __restrict__ tab,
             st3(cb + VS * q, c0, c1, c2);
         }
         __syncwarp();
-        if constexpr (sizeof(T) == 4) {
-            if (lane == 0) line_recurrences(blk(PK_M, 0), blk(PK_N, 0), cb, pl, bz, s.fwd_line);
-        } else {
-            if (lane < 3) line_recurrences(blk(PK_M, 0), blk(PK_N, 0), cb, pl, bz, s.fwd_line, lane);
-        }
+        line_solve(blk(PK_M, 0), blk(PK_N, 0), blk(PK_P, 0), blk(PK_Q, 0), cb, pl, bz, s.fwd_line, lane);
         __syncwarp();
         if (s.plane_done) {  // pv = P_j^{-1} t
             if (s.fwd_plane) {

@@ -203,9 +203,9 @@ def test_fp32_gmres_reaches_fp64_tolerance(name):
 
 
 def test_line_too_long_for_fp64_apply_is_rejected():
-    """An FP64 line packet of 300 cells does not fit the apply's two shared-memory slots; FP32 does."""
-    g = O.Geometry(2, 2, 300, 1, 1, 1, ov=0, near_width=0, far_mode=0)
-    s = synth.grid_jacobian(2, 2, 300, 26)
+    """An FP64 line packet of 250 cells does not fit the apply's two shared-memory slots; FP32 does."""
+    g = O.Geometry(2, 2, 250, 1, 1, 1, ov=0, near_width=0, far_mode=0)
+    s = synth.grid_jacobian(2, 2, 250, 26)
     with pytest.raises(asm2.ASMError) as e:
         nf_solver(g, s, precision="fp64")
     assert e.value.status == 1

@@ -253,6 +253,26 @@ def test_batch_equals_alone_bitwise():
         assert info == ib
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_mixing_chunk_capacities_equals_alone(precision):
+    """Subdomains whose largest wavefront level needs larger stream chunks (a 40x40x24 grid in 2x2
+    boxes) share a batch with subdomains that keep the smallest chunks (10x10x5): every CTA uses its
+    own ring-slot size inside the launch's shared memory, and the bits do not change."""
+    cases = [GEOMS["cfg1"], (O.Geometry(40, 40, 24, 2, 2, 1, ov=1), 11)]
+    systems = [synth.grid_jacobian(g.nx, g.ny, g.nz, seed) for g, seed in cases]
+    alone = []
+    for (g, _), s in zip(cases, systems):
+        sol = gpu_solver(g, s, precision=precision)
+        sol.set_tuning(coop_ortho=False)
+        alone.append(sol.solve(s.b, 1e-8, 2000))
+    solvers = [gpu_solver(g, s, precision=precision) for (g, _), s in zip(cases, systems)]
+    xs, infos = asm2.solve_batch(solvers, [s.b for s in systems], 1e-8, 2000)
+    for (x, info), xb, ib in zip(alone, xs, infos):
+        assert ib["converged"]
+        np.testing.assert_array_equal(x, xb)
+        assert info == ib
+
+
 def test_configuration_64x64x16_k64():
     w = synth.WORKLOADS["grid64x64x16_k64"]
     s = synth.make(w)
