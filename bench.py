@@ -276,9 +276,9 @@ def run_batch(args, stream):
 
 def nf_apply_bytes(w, elem: int) -> int:
     """Algorithmic bytes of one nested-factorisation apply on workload w: every line solve reads the
-    fields of its line's packet it needs (G^-1, M, N, then L2 + L3, L2 + U3 or U2: 9 values per cell
-    each), r comes in once (FP64), y_j goes out and back once per plane but the last, and the owned
-    cells go out once (FP64)."""
+    fields of its line's packet it needs (G^-1, M, N, the two-step products P and Q, then L2 + L3,
+    L2 + U3 or U2: 9 values per cell each), r comes in once (FP64), y_j goes out and back once per
+    plane but the last, and the owned cells go out once (FP64)."""
     def spans(n, p, ov):
         return [min(n, n * (t + 1) // p + ov) - max(0, n * t // p - ov) for t in range(p)]
     tot = 24 * w.nx * w.ny * w.nz
@@ -288,7 +288,7 @@ def nf_apply_bytes(w, elem: int) -> int:
                 field = 9 * elem * bz
                 fwd = by * bx + (by - 1) * bx            # forward lines of the forward and backward planes
                 bwd = by * (bx - 1) + (by - 1) * (bx - 1)  # backward lines
-                tot += (5 * fwd + 4 * bwd) * field + 24 * bx * by * bz + 2 * 3 * elem * bx * bz * (by - 1)
+                tot += (7 * fwd + 6 * bwd) * field + 24 * bx * by * bz + 2 * 3 * elem * bx * bz * (by - 1)
     return tot
 
 
