@@ -774,17 +774,24 @@ static int nf_setup(const bsr_t* A, int bx, int by, int bz, nf_t* f) {
     f->Gi = (double*)calloc(9 * (size_t)f->n + 1, sizeof(double));
     if (!f->G || !f->Gi) return ORC_ERR_NOMEM;
     const int S = bz * bx;
-    for (int p = 0; p < f->n; p++)
+    /* the band of an entry follows from the two cells' box coordinates (z, x, y): neighbours in z
+     * are L1/U1, in x L2/U2, in y L3/U3 (an index offset alone is ambiguous when bz or bx is 1) */
+    for (int p = 0; p < f->n; p++) {
+        const int pz = p % bz, px = (p / bz) % bx, py = p / S;
         for (int e = A->rp[p]; e < A->rp[p + 1]; e++) {
-            const int d = A->ci[e] - p;
-            double* dst = d == 0 ? f->D : d == -1 ? f->L1 : d == 1 ? f->U1 : d == -bz ? f->L2 : d == bz ? f->U2
-                        : d == -S ? f->L3 : d == S ? f->U3 : NULL;
-            /* a -1/+1 or -bz/+bz offset that wraps to another line/plane is not a band entry */
-            if (dst && (d == -1 || d == 1) && (A->ci[e] / bz != p / bz)) dst = NULL;
-            if (dst && (d == -bz || d == bz) && (A->ci[e] / S != p / S)) dst = NULL;
+            const int q = A->ci[e];
+            const int dz = q % bz - pz, dx = (q / bz) % bx - px, dy = q / S - py;
+            double* dst = NULL;
+            if (dx == 0 && dy == 0 && (dz == 0 || dz == -1 || dz == 1))
+                dst = dz == 0 ? f->D : dz < 0 ? f->L1 : f->U1;
+            else if (dz == 0 && dy == 0 && (dx == -1 || dx == 1))
+                dst = dx < 0 ? f->L2 : f->U2;
+            else if (dz == 0 && dx == 0 && (dy == -1 || dy == 1))
+                dst = dy < 0 ? f->L3 : f->U3;
             if (!dst) return ORC_ERR_PATTERN;
             memcpy(dst + 9 * (size_t)p, A->v + 9 * (size_t)e, sizeof(double) * 9);
         }
+    }
     return ORC_OK;
 }
 

@@ -18,6 +18,8 @@ CASES = [  # geometries whose local problems are boxes without lumps
     O.Geometry(5, 4, 3, 1, 1, 1, ov=0, near_width=0, far_mode=0),
     O.Geometry(6, 5, 4, 2, 1, 1, ov=1, near_width=0, far_mode=0),
     O.Geometry(5, 6, 4, 1, 2, 2, ov=1, near_width=0, far_mode=0),
+    O.Geometry(5, 4, 1, 2, 1, 1, ov=1, near_width=0, far_mode=0),  # lines of one cell
+    O.Geometry(1, 5, 4, 1, 2, 1, ov=1, near_width=0, far_mode=0),  # planes of one line
 ]
 
 
