@@ -337,7 +337,6 @@ void upload_nf(asm_ctx* h, cudaStream_t st) {
             h->last_error = "nested factorisation: a fine set is not a box";
             throw CudaFail{ASM_ERR_INVALID_ARG};
         }
-        const int S2 = P.bx * P.bz;
         std::vector<int> nat(o.n), cell(o.n), bands(7 * (size_t)o.n, -1);
         h->nf_row_of_cell[s].assign(o.n, 0);
         for (int p = 0; p < o.n; p++) {
@@ -348,12 +347,18 @@ void upload_nf(asm_ctx* h, cudaStream_t st) {
         for (int p = 0; p < o.n; p++) {
             const int a = nat[p];
             for (int t = o.prp[p]; t < o.prp[p + 1]; t++) {
-                const int b = nat[o.pci[t]], d = b - a;
-                int k = d == 0 ? 0 : d == -1 ? 1 : d == 1 ? 2 : d == -P.bz ? 3 : d == P.bz ? 4 : d == -S2 ? 5
-                      : d == S2 ? 6 : -1;
-                // a +-1 / +-bz offset that crosses into another line / plane is not a band entry
-                if ((k == 1 || k == 2) && b / P.bz != a / P.bz) k = -1;
-                if ((k == 3 || k == 4) && b / S2 != a / S2) k = -1;
+                const int q = o.pci[t];
+                // the band follows from the box coordinates: neighbours in z are L1/U1, in x L2/U2,
+                // in y L3/U3 (an index offset alone is ambiguous when bz or bx is 1)
+                const int dx = xyz[3 * q] - xyz[3 * p], dy = xyz[3 * q + 1] - xyz[3 * p + 1],
+                          dz = xyz[3 * q + 2] - xyz[3 * p + 2];
+                int k = -1;
+                if (dx == 0 && dy == 0 && dz >= -1 && dz <= 1)
+                    k = dz == 0 ? 0 : dz < 0 ? 1 : 2;
+                else if (dz == 0 && dy == 0 && (dx == -1 || dx == 1))
+                    k = dx < 0 ? 3 : 4;
+                else if (dz == 0 && dx == 0 && (dy == -1 || dy == 1))
+                    k = dy < 0 ? 5 : 6;
                 if (k < 0 || bands[7 * (size_t)a + k] >= 0) {
                     h->last_error = "nested factorisation: a local matrix is not hepta-banded on its box";
                     throw CudaFail{ASM_ERR_PATTERN};

@@ -8,12 +8,13 @@
 // Both the factorisation and the solve are sequential along the cells of a subdomain: every line
 // depends on the previous line of its plane, every plane on the previous plane.  So one warp takes
 // one subdomain.  In the factorisation its lanes share the 3x3 block algebra (lane 3 r + c holds
-// element (r, c) of a block).  The apply streams one packet per line -- G^{-1}, G^{-1} L1,
-// G^{-1} U1, L2, U2, L3, U3 of the line's cells, packed after the factorisation -- through a
-// two-slot shared-memory ring by bulk copies, one line ahead of the line being solved.  The
-// products that do not depend on the line recurrence run on all lanes; the two recurrences of T^{-1}
-// run from shared memory on one lane (FP32) or three (FP64, one row each: an FP64 instruction costs
-// the same for one lane as for 32).
+// element (r, c) of a block) and the independent per-cell products.  The apply streams one packet
+// per line -- G^{-1}, G^{-1} L1, G^{-1} U1, their two-step products, L2, L3, U3, U2 of the line's
+// cells, packed after the factorisation -- through a shared-memory ring of 2-4 slots by bulk copies,
+// ahead of the line being solved.  The products that do not depend on the line recurrences run on
+// all lanes; the two recurrences of T^{-1}, with one level of recursive doubling, run from shared
+// memory on one lane (FP32) or three (FP64, one row each: an FP64 instruction costs the same for one
+// lane as for 32).
 #include <cuda_runtime.h>
 
 #include <algorithm>

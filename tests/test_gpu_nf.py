@@ -21,6 +21,8 @@ GEOMS = {  # geometries whose local problems are boxes without lumps
     "ragged": (O.Geometry(9, 7, 6, 3, 2, 2, ov=1, near_width=0, far_mode=0), 23),
     "tiles": (O.Geometry(24, 20, 16, 3, 2, 1, ov=2, near_width=0, far_mode=0), 24),
     "long": (O.Geometry(4, 3, 150, 2, 1, 1, ov=1, near_width=0, far_mode=0), 25),  # lines of 150 cells
+    "flat": (O.Geometry(7, 6, 1, 2, 2, 1, ov=1, near_width=0, far_mode=0), 27),   # lines of one cell
+    "thin": (O.Geometry(6, 5, 2, 2, 1, 1, ov=1, near_width=0, far_mode=0), 28),   # lines of two cells
 }
 SOLVERS = {"nf_colsum": O.NF_COLSUM, "nf": O.NF}
 EPS = np.finfo(float).eps
@@ -181,7 +183,7 @@ def test_nf_refuses_fp16_storage():
 
 
 @pytest.mark.parametrize("local", list(SOLVERS))
-@pytest.mark.parametrize("name", ["x2", "ragged", "tiles", "long"])
+@pytest.mark.parametrize("name", ["x2", "ragged", "tiles", "long", "flat", "thin"])
 def test_fp32_apply_close_to_oracle(name, local):
     """FP32 apply (G from the FP64 factorisation, rounded): within 1e-5 of the FP64 oracle."""
     g, seed = GEOMS[name]
