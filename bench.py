@@ -486,7 +486,8 @@ def run_gpu(args):
         return x, info
 
     results = {}
-    for prec in ([args.precision, "fp64"] if args.precision != "fp64" else ["fp64"]):
+    precs = [args.precision] + [p_ for p_ in ("fp64", "fp32", "fp16s") if p_ != args.precision and not args.no_precisions]
+    for prec in precs:
         sol = make_solver(prec)
         for _ in range(args.warmup):
             step(sol)
@@ -559,9 +560,11 @@ def run_gpu(args):
         "solves_per_s": 1e3 * ws / main["ms"],
         "iterations": main["info"]["iterations"], "restarts": main["info"]["restarts"],
         "true_rel_residual": main["info"]["rel_residual"], "host_check_rel_residual": main["host_check_relres"],
-        "fp64": {"ms_per_solve": results["fp64"]["ms"], "iterations": results["fp64"]["info"]["iterations"],
-                 "true_rel_residual": results["fp64"]["info"]["rel_residual"],
-                 "host_check_rel_residual": results["fp64"]["host_check_relres"]} if "fp64" in results else None,
+        "mean_local_rows": st["local_rows"] / st["n_sub"],
+        "precisions": {p_: {"ms_per_solve": r_["ms"], "iterations": r_["info"]["iterations"],
+                            "converged": bool(r_["info"]["converged"]), "true_rel_residual": r_["info"]["rel_residual"],
+                            "host_check_rel_residual": r_["host_check_relres"]}
+                       for p_, r_ in results.items() if p_ != args.precision},
         "breakdown_ms_per_solve": {k: prof[k] / args.steps for k in ("apply_ms", "spmv_ms", "ortho_ms", "factor_ms")},
         "roofline": {"bound": "hbm", "kernel": "precond apply (boxsum + fused local solves)", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": apply_traffic(alg_bytes),
@@ -605,6 +608,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-nf", action="store_true", help="skip the nested-factorisation leg")
+    ap.add_argument("--no-precisions", action="store_true", help="time the --precision path only")
     ap.add_argument("--batch-systems", type=int, default=256)
     ap.add_argument("--profile-case", action="store_true", help="small case for ncu captures")
     ap.add_argument("--profile-nf", action="store_true", help="nested-factorisation apply case for ncu captures")
