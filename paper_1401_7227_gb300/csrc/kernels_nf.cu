@@ -593,6 +593,10 @@ __global__ void __launch_bounds__(32) k_nf_apply(const SysTab* __restrict__ tab,
             f[1][0] = PK_L2, f[1][1] = SL_X, f[1][2] = 1;
             f[2][0] = PK_U3, f[2][1] = SL_Y, f[2][2] = 1;
         }
+        if (f[1][2] > 0 && f[1][0] == f[0][0] + f[0][2] && f[1][1] == f[0][1] + f[0][2]) {
+            f[0][2] += f[1][2];  // adjacent in the packet and in the slot: one copy
+            f[1][2] = 0;
+        }
         unsigned tx = rbytes;
         for (int i = 0; i < 3; i++) tx += (unsigned)f[i][2] * fb;
         tma::mbar_expect_tx(&bar[2 * b], tx);
