@@ -459,9 +459,10 @@ std::string build_sub(const Ctx& X, int s, SubSym& o) {
         if (!fwd) b += al16(fbb * nf_) + al16(72 * (size_t)nc_);
         return b;
     };
-    // chunk capacity: the largest fine level (forward or backward part) in one chunk, rounded up to
-    // 4 KB, within [kStreamChunkMin, kStreamChunkMax] (fewer chunks mean fewer barriers in the apply;
-    // larger ring slots mean fewer CTAs per SM, so small subdomains keep the smallest capacity)
+    // chunk capacity: the largest fine level (forward or backward part) and the longest single lump
+    // row in one chunk, rounded up to 4 KB, within [kStreamChunkMin, kStreamChunkMax] (fewer chunks
+    // mean fewer barriers in the apply; larger ring slots mean fewer CTAs per SM, so small
+    // subdomains keep the smallest capacity)
     {
         size_t big = 0;
         for (int l = 0; l < nlev; l++)
@@ -471,6 +472,9 @@ std::string build_sub(const Ctx& X, int s, SubSym& o) {
                     ef += pass == 0 ? nl(o.row_of_pos[pos]) : nu(o.row_of_pos[pos]);
                 big = std::max(big, chunk_bytes(cntf[l], ef, 0, 0, pass == 0) + 256);
             }
+        for (int p = o.nf; p < n; p++)
+            for (int pass = 0; pass < 2; pass++)
+                big = std::max(big, chunk_bytes(0, 0, 1, pass == 0 ? nl(p) : nu(p), pass == 0));
         const size_t cap = (big + 4095) / 4096 * 4096;
         o.chunk_cap = (int)std::min<size_t>(asm2::kStreamChunkMax, std::max<size_t>(asm2::kStreamChunkMin, cap));
     }

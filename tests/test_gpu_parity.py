@@ -273,6 +273,17 @@ def test_batch_mixing_chunk_capacities_equals_alone(precision):
         assert info == ib
 
 
+@pytest.mark.parametrize("precision, tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_lump_rows_longer_than_the_smallest_chunk(precision, tol):
+    """Far lumps that touch many near lumps (32x32x64 in 4x4 boxes): lump rows of ~130 blocks (~10 KB
+    in FP64) need stream chunks above the 8 KB minimum capacity; the apply matches the oracle."""
+    g = O.Geometry(32, 32, 64, 4, 4, 1, ov=1)
+    s = synth.grid_jacobian(32, 32, 64, 9)
+    pc = O.Precond(g, s.row_ptr, s.col_idx, s.vals)
+    r = synth.rhs(s.n_cells, 1)
+    assert rel(gpu_solver(g, s, precision=precision).apply(r), pc.apply(r)) <= tol
+
+
 def test_configuration_64x64x16_k64():
     w = synth.WORKLOADS["grid64x64x16_k64"]
     s = synth.make(w)
