@@ -269,20 +269,18 @@ std::string build_sub(const Ctx& X, int s, SubSym& o) {
         for (int t = o.prp[p]; t < o.prp[p + 1]; t++)
             if (slot(o.pci[t], p) < 0) return "local pattern not structurally symmetric";
 
-    // Wavefront levels of the DAG of L (the same sets, reversed, serve U).  Fine rows never depend
-    // on lump rows in L (lumps come last in the local order), so every lump row is placed after the
-    // last fine level: the forward sweep does all fine levels first and the backward sweep all
-    // lump levels first, and no fine level waits on a (slower, FP64) lump row.  Any level
-    // assignment that respects the DAG gives the same arithmetic.
+    // Wavefront levels of the DAG of L (the same sets, reversed, serve U), every row at the earliest
+    // level its dependencies allow: the lump rows (FP64) then run in the same levels as the fine
+    // rows they follow instead of after the last of them, which shortens the chain of levels (and
+    // of CTA barriers) by about a fifth at 1M cells.  Any level assignment that respects the DAG
+    // gives the same arithmetic.
     std::vector<int> level(n, 0);
     int nlev = 0;
-    int fine_levels = 0;
     for (int p = 0; p < n; p++) {
-        int l = p < o.nf ? 0 : fine_levels;
+        int l = 0;
         for (int t = o.prp[p]; t < o.pdiag[p]; t++) l = std::max(l, level[o.pci[t]] + 1);
         level[p] = l;
         nlev = std::max(nlev, l + 1);
-        if (p < o.nf) fine_levels = std::max(fine_levels, l + 1);
     }
     if (n == 0) nlev = 0;
     o.nlev = nlev;
