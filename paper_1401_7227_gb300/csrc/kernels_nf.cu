@@ -74,8 +74,11 @@ __device__ __forceinline__ bool binv(TC a, TC& inv, int lane) {
 template <typename TC>
 struct NFView {
     const NFDesc& d;
+    TC* nk;  // N_p = G_p^{-1} U1_p ([9 n]), then K_p = L1_{p+1} G_p^{-1} ([9 n])
     __device__ const TC* band(int k, int p) const { return static_cast<const TC*>(d.fband) + 9LL * (BD_N * p + k); }
     __device__ const double* gi(int p) const { return d.gi + 9LL * p; }
+    __device__ const TC* N(int p) const { return nk + 9LL * p; }
+    __device__ const TC* K(int p) const { return nk + 9LL * (d.n + p); }
 };
 
 // element `lane` of a block (lanes 9..31: zero)
@@ -83,37 +86,112 @@ template <typename TC, typename TS>
 __device__ __forceinline__ TC ld(const TS* p, int lane) { return lane < 9 ? (TC)p[lane] : TC(0); }
 
 // W = u T^{-1} on the line starting at cell q0: W (G + L1)(I + G^{-1} U1) = u (rows of blocks).
-// Each loop loads the next step's operands before the current step's products.
+// With N_q = G_q^{-1} U1_q and K_q = L1_{q+1} G_q^{-1} (formed once per line after its G), each
+// sequential step is one block product:
+//   forward   v_q = u_q - v_{q-1} N_{q-1}            (v (I + G^{-1} U1) = u)
+//   backward  W_q = v_q G_q^{-1} - W_{q+1} K_q       (W (G + L1) = v; v_q G_q^{-1} on all lanes first)
+// The operands come from device memory (L2) at ~400 cycles, against ~50 cycles of arithmetic per
+// step, so the chains take them kRowG steps at a time into one of two register buffers, the next
+// group's loads issued before the current group is computed.
 template <typename TC>
 __device__ void line_row_solve(const NFView<TC>& v, int q0, const TC* u, TC* vtmp, TC* W, int lane) {
+    constexpr int kRowG = 8;
     const int bz = v.d.bz;
-    TC prev = 0, nu = ld<TC>(u, lane), ngi = 0, nu1 = 0;
-    for (int q = 0; q < bz; q++) {  // vtmp (I + G^{-1} U1) = u
-        const TC cu = nu, cgi = ngi, cu1 = nu1;
-        if (q + 1 < bz) {
-            nu = ld<TC>(u + 9 * (q + 1), lane);
-            ngi = ld<TC>(v.gi(q0 + q), lane);
-            nu1 = ld<TC>(v.band(BD_U1, q0 + q), lane);
+    {
+        TC a[2][kRowG], b[2][kRowG];  // u_q, N_{q-1}
+        TC prev = 0;
+#define NF_LOAD_F(h, gs)                                                            \
+    _Pragma("unroll") for (int i = 0; i < kRowG; i++) {                             \
+        const int q = (gs) + i;                                                     \
+        a[h][i] = q < bz ? ld<TC>(u + 9 * q, lane) : TC(0);                         \
+        b[h][i] = q > 0 && q < bz ? ld<TC>(v.N(q0 + q - 1), lane) : TC(0);          \
+    }
+        NF_LOAD_F(0, 0)
+        for (int g0 = 0; g0 < bz; g0 += 2 * kRowG) {
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int gs = g0 + h * kRowG;
+                if (gs < bz) {
+                    if (gs + kRowG < bz) {
+                        if (h == 0) {
+                            NF_LOAD_F(1, gs + kRowG)
+                        } else {
+                            NF_LOAD_F(0, gs + kRowG)
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < kRowG; i++) {
+                        const int q = gs + i;
+                        if (q < bz) {
+                            TC x = a[h][i];
+                            if (q > 0) x -= bmul(prev, b[h][i], lane);
+                            if (lane < 9) vtmp[9 * q + lane] = x;
+                            prev = x;
+                        }
+                    }
+                }
+            }
         }
-        TC x = cu;
-        if (q > 0) x -= bmul(bmul(prev, cgi, lane), cu1, lane);
-        if (lane < 9) vtmp[9 * q + lane] = x;
-        prev = x;
+#undef NF_LOAD_F
     }
     __syncwarp();
-    TC next = 0, nv = ld<TC>(vtmp + 9 * (bz - 1), lane), nl1 = 0, ng = ld<TC>(v.gi(q0 + bz - 1), lane);
-    for (int q = bz - 1; q >= 0; q--) {  // W (G + L1) = vtmp
-        const TC cv = nv, cl1 = nl1, cg = ng;
-        if (q > 0) {
-            nv = ld<TC>(vtmp + 9 * (q - 1), lane);
-            nl1 = ld<TC>(v.band(BD_L1, q0 + q), lane);
-            ng = ld<TC>(v.gi(q0 + q - 1), lane);
+    // v_q G_q^{-1}, one block element per lane, kB elements' loads in flight per lane
+    constexpr int kB = 4;
+    for (int t0 = lane; t0 < 9 * bz; t0 += 32 * kB) {
+        TC av[kB][3], gv[kB][3];
+#pragma unroll
+        for (int j = 0; j < kB; j++) {
+            const int t = t0 + 32 * j, q = t / 9, e = t - 9 * q, r = e / 3, k = e - 3 * r;
+            const bool in = t < 9 * bz;
+            const TC* a = vtmp + 9 * (in ? q : 0);
+            const double* g = v.gi(q0 + (in ? q : 0));
+#pragma unroll
+            for (int m = 0; m < 3; m++) {
+                av[j][m] = a[3 * r + m];
+                gv[j][m] = (TC)g[3 * m + k];
+            }
         }
-        TC x = cv;
-        if (q < bz - 1) x -= bmul(next, cl1, lane);
-        const TC w = bmul(x, cg, lane);
-        if (lane < 9) W[9 * q + lane] = w;
-        next = w;
+#pragma unroll
+        for (int j = 0; j < kB; j++)
+            if (t0 + 32 * j < 9 * bz) W[t0 + 32 * j] = av[j][0] * gv[j][0] + av[j][1] * gv[j][1] + av[j][2] * gv[j][2];
+    }
+    __syncwarp();
+    {
+        TC a[2][kRowG], b[2][kRowG];  // (v G^{-1})_q, K_q, for q = bz - 1 - (step)
+        TC next = 0;
+#define NF_LOAD_B(h, gs)                                                            \
+    _Pragma("unroll") for (int i = 0; i < kRowG; i++) {                             \
+        const int q = bz - 1 - ((gs) + i);                                          \
+        a[h][i] = q >= 0 ? ld<TC>(W + 9 * q, lane) : TC(0);                         \
+        b[h][i] = q >= 0 && q < bz - 1 ? ld<TC>(v.K(q0 + q), lane) : TC(0);         \
+    }
+        NF_LOAD_B(0, 0)
+        for (int g0 = 0; g0 < bz; g0 += 2 * kRowG) {
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int gs = g0 + h * kRowG;
+                if (gs < bz) {
+                    if (gs + kRowG < bz) {
+                        if (h == 0) {
+                            NF_LOAD_B(1, gs + kRowG)
+                        } else {
+                            NF_LOAD_B(0, gs + kRowG)
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < kRowG; i++) {
+                        const int q = bz - 1 - (gs + i);
+                        if (q >= 0) {
+                            TC x = a[h][i];
+                            if (q < bz - 1) x -= bmul(next, b[h][i], lane);
+                            if (lane < 9) W[9 * q + lane] = x;
+                            next = x;
+                        }
+                    }
+                }
+            }
+        }
+#undef NF_LOAD_B
     }
     __syncwarp();
 }
@@ -169,11 +247,11 @@ template <typename TC>
 __global__ void __launch_bounds__(128) k_nf_factor(const NFDesc* __restrict__ descs, int ndesc, FactErr* err) {
     const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (w >= ndesc) return;
-    const NFDesc& d = descs[w];
-    const NFView<TC> v{d};
+    const NFDesc d = descs[w];  // by value: its fields stay in registers across the stores
     const int bz = d.bz, bx = d.bx, by = d.by, S = bz * bx;
-    // scratch: cs3 (9 S), u (9 S), W (9 S), vb (9 S), x, y, vt, cs2 (9 bz each)
+    // scratch: cs3 (9 S), u (9 S), W (9 S), vb (9 S), x, y, vt, cs2 (9 bz each), N and K (9 n each)
     TC* cs3 = reinterpret_cast<TC*>(d.work);
+    const NFView<TC> v{d, cs3 + 36 * S + 36 * bz};
     TC* u = cs3 + 9 * S;
     TC* W = u + 9 * S;
     TC* vb = W + 9 * S;
@@ -230,6 +308,22 @@ __global__ void __launch_bounds__(128) k_nf_factor(const NFDesc* __restrict__ de
                 }
                 if (lane < 9) d.gi[9LL * p + lane] = (double)gi;
                 gprev = gi;
+            }
+            __syncwarp();
+            // N_q = G_q^{-1} U1_q and K_q = L1_{q+1} G_q^{-1} of this line, for its row-vector solves
+            TC* nline = v.nk + 9LL * q0;
+            TC* kline = v.nk + 9LL * (d.n + q0);
+            for (int t = lane; t < 9 * bz; t += 32) {
+                const int q = t / 9, e = t - 9 * q, r = e / 3, k = e - 3 * r;
+                const double* g = v.gi(q0 + q);
+                const TC* u1 = v.band(BD_U1, q0 + q);
+                nline[t] = (TC)g[3 * r] * u1[k] + (TC)g[3 * r + 1] * u1[3 + k] + (TC)g[3 * r + 2] * u1[6 + k];
+                TC kv = 0;
+                if (q + 1 < bz) {
+                    const TC* l1 = v.band(BD_L1, q0 + q + 1);
+                    kv = l1[3 * r] * (TC)g[k] + l1[3 * r + 1] * (TC)g[3 + k] + l1[3 * r + 2] * (TC)g[6 + k];
+                }
+                kline[t] = kv;
             }
             __syncwarp();
         }
@@ -545,7 +639,7 @@ template <typename T, int SLOTS>
 __global__ void __launch_bounds__(32) k_nf_apply(const SysTab* __restrict__ tab, const NFDesc* __restrict__ descs) {
     constexpr int BS = 3 * Lay<T>::RS, VS = Lay<T>::VS;
     extern __shared__ __align__(16) unsigned char nf_smem[];
-    const NFDesc& d = descs[blockIdx.x];
+    const NFDesc d = descs[blockIdx.x];  // by value: its fields stay in registers across the stores
     const SysTab& st = tab[d.sys];
     const int in = st.ctl[C_APPLY_IN];
     if (in < 0) return;
@@ -755,8 +849,7 @@ size_t nf_apply_smem(int bx, int bz, int prec, int slots) {
 }
 
 size_t nf_work_doubles(int bx, int by, int bz) {
-    (void)by;
-    return 36 * ((size_t)bx * bz + (size_t)bz);
+    return 36 * ((size_t)bx * bz + (size_t)bz) + 18 * (size_t)bx * by * bz;
 }
 
 void launch_nf_factor(const NFDesc* descs, int ndesc, int nmax, int prec, FactErr* err, cudaStream_t st) {
