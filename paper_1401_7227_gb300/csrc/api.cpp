@@ -1440,12 +1440,18 @@ int handle_matrix_view(asm_ctx* h, MatrixView* out) {
 namespace {
 
 size_t ctx_device_bytes(const asm_ctx* h) {
-    const DBuf* bufs[] = {&h->d_ell_val, &h->d_ell_col, &h->d_ell_loc, &h->d_bsr_val, &h->d_bcell, &h->d_cptr, &h->d_cloc,
-                          &h->d_cval, &h->d_boxsum, &h->d_slot, &h->d_dpiv, &h->d_aptr, &h->d_aloc, &h->d_acs, &h->d_fp,
-                          &h->d_stream, &h->d_pk_off_f, &h->d_pk_src_f, &h->d_pk_off_c, &h->d_pk_src_c, &h->d_lv,
-                          &h->d_rlists, &h->d_y, &h->d_corr_cells, &h->d_corr, &h->d_dev_err, &h->d_factdesc,
-                          &h->d_subdesc_single, &h->d_err, &h->d_ws, &h->d_scal, &h->d_ctl, &h->d_partial, &h->d_tab1,
-                          &h->d_vec1, &h->d_row1, &h->d_box1};
+    const DBuf* bufs[] = {&h->d_ell_val, &h->d_ell_col, &h->d_ell_loc, &h->d_bsr_rp, &h->d_bsr_val, &h->d_bcell,
+                          &h->d_cptr, &h->d_cloc, &h->d_cval, &h->d_boxsum, &h->d_slot, &h->d_dpiv, &h->d_aptr,
+                          &h->d_aloc, &h->d_acs, &h->d_along, &h->d_fp, &h->d_stream, &h->d_pk_off_f, &h->d_pk_src_f,
+                          &h->d_pk_off_c, &h->d_pk_src_c, &h->d_lv, &h->d_rlists, &h->d_y, &h->d_corr_cells,
+                          &h->d_corr, &h->d_dev_err, &h->d_factdesc, &h->d_subdesc_single, &h->d_err, &h->d_ws,
+                          &h->d_scal, &h->d_ctl, &h->d_partial, &h->d_tab1, &h->d_vec1, &h->d_row1, &h->d_box1,
+                          // exact local solves, nested factorisation, classical coarse correction
+                          &h->d_daug, &h->d_dprow, &h->d_dfcol, &h->d_dmats, &h->d_dinit, &h->d_doff,
+                          &h->d_dmat_of_slot, &h->d_dpart, &h->d_derr, &h->d_ditems1, &h->d_nfint, &h->d_nfval,
+                          &h->d_nfdesc1, &h->d_nfpack, &h->d_nfy, &h->d_nfband, &h->d_cbox, &h->d_ccells, &h->d_ckptr,
+                          &h->d_ckloc, &h->d_ckeys, &h->d_cblk, &h->d_caug, &h->d_cprow, &h->d_cfcol, &h->d_cpart,
+                          &h->d_cerr, &h->d_crc, &h->d_cyc, &h->d_cw, &h->d_cbox_items1, &h->d_cgrow1, &h->d_cmat};
     size_t b = 0;
     for (const DBuf* d : bufs) b += d->bytes;
     return b;
