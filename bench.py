@@ -427,8 +427,7 @@ def run_reference(args):
     iters = args.ref_iters
     vals = []
     sample = ""
-    for _ in range(args.warmup if args.warmup < 1 else 0):
-        pass
+    # no warm-up: the oracle has no caches or lazy setup worth excluding, and each step is long
     for _ in range(args.steps):
         ms, sample, _ = oracle_estimate(w, system, iters, sample_subs=1, sample_iters=2)
         vals.append(ms)
