@@ -267,10 +267,11 @@ int asm_get_local_factors(asm_handle h, int s, double* lu, double* dpiv);
 /* ------------------------------------------------------------------------------------------
  * Serving loop (continuous batching).  Requests of any grid size are submitted as they arrive;
  * asm_server_progress admits them while the active-system limit and the device-memory budget
- * allow (a request whose matrix key is already resident reuses its factors; a new grid shape is
- * analysed once on a host worker thread and cached), and advances every active system by Krylov
- * steps in the same kernel launches; finished systems leave the batch between steps.  Each
- * system's arithmetic does not depend on the others in the batch.
+ * allow (a request whose matrix key is already resident reuses its factors; a new structure --
+ * grid, partition, precision and a 64-bit FNV-1a hash of the block pattern; the pattern itself is
+ * not compared -- is analysed once on a host worker thread and cached), and advances every active
+ * system by Krylov steps in the same kernel launches; finished systems leave the batch between
+ * steps.  Each system's arithmetic does not depend on the others in the batch.
  * ------------------------------------------------------------------------------------------ */
 typedef struct {
     int precision;        /* asm_precision of every served system (default FP32) */
