@@ -432,7 +432,8 @@ def run_reference(args):
         ms, sample, _ = oracle_estimate(w, system, iters, sample_subs=1, sample_iters=2)
         vals.append(ms)
     v = float(np.mean(vals))
-    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+    # n_gpus: the launch's world size, as in the GPU arm; the work itself ran on one host core
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": v, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": w.name, "grid": [w.nx, w.ny, w.nz], "partition": [w.px, w.py, w.pz],
