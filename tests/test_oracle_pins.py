@@ -467,3 +467,25 @@ def test_configuration_10x10x5_converges():
     assert info.converged and info.relres <= 1e-8
     xs = np.linalg.solve(s.dense(), s.b)
     assert np.linalg.norm(x - xs) <= 1e-4 * np.linalg.norm(xs)
+
+
+@pytest.mark.parametrize("nx,ny,nz,K,C", [(10, 10, 5, 2, 2), (10, 10, 5, 5, 2), (10, 10, 5, 5, 4), (12, 12, 4, 4, 3),
+                                          (16, 16, 4, 4, 4), (16, 16, 4, 8, 4)])
+def test_P8_near_and_far_together_need_no_more_iterations(nx, ny, nz, K, C):
+    """Section 5 (Figs. 5-8): with exact local solves and no overlap, the near field and the far
+    field together take no more GMRES iterations than either one alone.  K subdomains split in x;
+    near ring of 2x2x2 lumps, width 2; far lumps of C x C x min(C, nz) cells.  A qualitative check
+    of the lump construction, not an exact value."""
+    s = synth.grid_jacobian(nx, ny, nz, 1)
+    cb = (C, C, min(C, nz))
+
+    def iters(near_width, far_mode):
+        g = O.Geometry(nx, ny, nz, K, 1, 1, ov=0, near_width=near_width, cnear=(2, 2, 2), far_mode=far_mode,
+                       cfar=cb if far_mode == 2 else (0, 0, 0))
+        pc = O.Precond(g, s.row_ptr, s.col_idx, s.vals, solver=O.DENSE_LU)
+        _, info = O.gmres(s.row_ptr, s.col_idx, s.vals, s.b, pc, 30, 1e-8, 300)
+        assert info.converged
+        return info.iters
+
+    near, far, both = iters(2, 0), iters(0, 2), iters(2, 2)
+    assert both <= min(near, far), (near, far, both)
