@@ -302,7 +302,8 @@ typedef struct {
 
 void asm_server_default_options(asm_server_options* opt);
 typedef struct asm_server* asm_server_handle;
-/* cuda_stream: the stream all served work is issued on (NULL = legacy default stream). */
+/* cuda_stream: the stream all served work is issued on (NULL = legacy default stream).
+ * Errors: INVALID_ARG (bad option / device index), CUDA (no usable device), OOM. */
 int asm_server_create(asm_server_handle* s, const asm_server_options* opt, void* cuda_stream);
 /* Queue a request; *ticket identifies it.  Errors: INVALID_ARG (inconsistent sizes). */
 int asm_server_submit(asm_server_handle s, const asm_request* req, long long* ticket);

@@ -2199,9 +2199,15 @@ int asm_server_create(asm_server_handle* out, const asm_server_options* opt, voi
     if (o.precision < 0 || o.precision > 2 || o.restart < 1 || o.restart > 512 || o.max_active < 0 || o.max_cached < 0 ||
         o.hbm_budget < 0)
         return ASM_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {  // no driver or no device, as in asm_create
+        cudaGetLastError();
+        return ASM_ERR_CUDA;
+    }
+    if (o.device < 0 || o.device >= ndev) return ASM_ERR_INVALID_ARG;
     if (cudaSetDevice(o.device) != cudaSuccess) {
         cudaGetLastError();
-        return ASM_ERR_INVALID_ARG;
+        return ASM_ERR_CUDA;
     }
     asm_server* S = new (std::nothrow) asm_server();
     if (!S) return ASM_ERR_OOM;

@@ -58,3 +58,26 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
 def test_sources_compile_for_sm_103a_only():
     src = open(os.path.join(ROOT, "paper_1401_7227_gb300", "build.py")).read()
     assert "arch=compute_103a,code=sm_103a" in src
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """No fallback: without libasm2.so the binding raises instead of computing anything."""
+    monkeypatch.setattr(asm2, "_lib", None)
+    monkeypatch.setattr(lib_build, "LIB", os.path.join(ROOT, "no-such-dir", "libasm2.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        asm2.load()
+
+
+def test_no_device_is_a_cuda_error(lib):
+    """Without a usable GPU both constructors return ASM_ERR_CUDA (6); a bad device index where
+    devices exist would be ASM_ERR_INVALID_ARG.  Here, with no GPU, only the first case is reachable."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = C.c_void_p()
+    assert lib.asm_create(C.byref(h), None, None) == 6 and not h
+    s = C.c_void_p()
+    assert lib.asm_server_create(C.byref(s), None, None) == 6 and not s
+    with pytest.raises(asm2.ASMError) as e:
+        asm2.Solver(stream=0)
+    assert e.value.status == 6
