@@ -630,12 +630,14 @@ int Pattern::find(int r, int c) const {
 std::string build_pattern(int n, const int* rp, const int* ci, int nnzb, Pattern& P) {
     if (n < 1 || nnzb < n) return "bad sizes";
     if (rp[0] != 0 || rp[n] != nnzb) return "row_ptr does not span col_idx";
+    // all of row_ptr first: a row that ends past nnzb must not be read
+    for (int r = 0; r < n; r++)
+        if (rp[r + 1] < rp[r] || rp[r + 1] > nnzb) return "row_ptr not monotone";
     P.n = n;
     P.rp.assign(rp, rp + n + 1);
     P.ci.assign(ci, ci + nnzb);
     int w = 0;
     for (int r = 0; r < n; r++) {
-        if (rp[r + 1] < rp[r]) return "row_ptr not monotone";
         w = std::max(w, rp[r + 1] - rp[r]);
         bool diag = false;
         for (int e = rp[r]; e < rp[r + 1]; e++) {

@@ -69,6 +69,15 @@ void* hs_create(const int* geo, int n, int nnzb, const int* rp, const int* ci, i
 
 void hs_destroy(void* p) { delete static_cast<Handle*>(p); }
 
+// build_pattern alone: "" or its error message (for the input checks of asm_set_matrix_bsr)
+int hs_check_pattern(int n, int nnzb, const int* rp, const int* ci, char* err, int errlen) {
+    Pattern P;
+    const std::string e = build_pattern(n, rp, ci, nnzb, P);
+    std::strncpy(err, e.c_str(), (size_t)errlen - 1);
+    err[errlen - 1] = 0;
+    return e.empty() ? 0 : 1;
+}
+
 // copies the list `what` of subdomain s (s = -1: of the system) into out (if not NULL); returns
 // its length, or -1 for an unknown name.  int32 lists unless noted: chunk_off int64, stream bytes.
 long long hs_get(void* p, int s, const char* what, void* out) {
@@ -78,6 +87,9 @@ long long hs_get(void* p, int s, const char* what, void* out) {
         if (w == "n_sub") return put(std::vector<int>{(int)h.sym.subs.size()}, out);
         if (w == "cptr") return put(h.sym.cptr, out);
         if (w == "cloc") return put(to_bsr(h.pat, h.sym.cloc), out);
+        if (w == "ell_shape") return put(std::vector<int>{h.pat.ell_w, h.pat.rows_pad}, out);
+        if (w == "ell_loc") return put(h.pat.ell_loc, out);
+        if (w == "ell_col") return put(h.pat.ell_col, out);
         return -1;
     }
     const SubSym& o = h.sym.subs[s];

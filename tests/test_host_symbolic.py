@@ -63,6 +63,7 @@ def hs(tmp_path_factory):
     lib.hs_destroy.argtypes = [C.c_void_p]
     lib.hs_get.restype = C.c_longlong
     lib.hs_get.argtypes = [C.c_void_p, C.c_int, C.c_char_p, C.c_void_p]
+    lib.hs_check_pattern.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_char_p, C.c_int]
     return lib
 
 
@@ -295,3 +296,59 @@ def test_symbolic_errors_are_reported(hs):
     h = hs.hs_create(geo.ctypes.data, 4, 5, rp.ctypes.data, ci.ctypes.data, 0, 1, err, 256)
     assert not h
     assert b"symmetric" in err.value
+
+
+def check_pattern(hs, rp, ci):
+    rp = np.ascontiguousarray(rp, dtype=np.int32)
+    ci = np.ascontiguousarray(ci, dtype=np.int32)
+    err = C.create_string_buffer(256)
+    st = hs.hs_check_pattern(len(rp) - 1, len(ci), rp.ctypes.data, ci.ctypes.data, err, 256)
+    return st, err.value.decode()
+
+
+@pytest.mark.parametrize("rp,ci,msg", [
+    ([0, 2, 4], [0, 1, 0, 1], ""),                                  # a valid 2-cell pattern
+    ([0, 1, 2], [1, 0], "missing diagonal"),
+    ([0, 2, 4], [1, 0, 0, 1], "ascending"),
+    ([0, 2, 4], [0, 0, 0, 1], "ascending"),                         # a repeated column
+    ([0, 2, 4], [0, 2, 0, 1], "out of range"),
+    ([0, 2, 4], [0, -1, 0, 1], "out of range"),
+    ([0, 2, 3], [0, 1, 1], "symmetric"),
+    ([0, 2, 3], [0, 1, 0, 1], "span"),                              # row_ptr ends before col_idx
+    ([1, 2, 4], [0, 1, 0, 1], "span"),
+    ([0, 3, 1, 4], [0, 1, 2, 2], "monotone"),                       # a row ends past the next start
+    ([0, 9, 2, 4], [0, 1, 0, 1], "monotone"),                       # a row ends past nnzb
+])
+def test_pattern_input_checks(hs, rp, ci, msg):
+    """asm_set_matrix_bsr's checks of A's block pattern (Section 1: a structurally symmetric
+    7-point pattern with diagonal blocks).  row_ptr is checked in full before col_idx is read, so a
+    row that ends past nnzb is refused, not read."""
+    st, err = check_pattern(hs, rp, ci)
+    if not msg:
+        assert st == 0 and err == ""
+    else:
+        assert st == 1 and msg in err, err
+
+
+@pytest.mark.parametrize("name", ["cfg1", "ragged", "line"])
+def test_ell_layout_is_a_bijection_onto_bsr_blocks(hs, name):
+    """The ELL copy of A that the SpMV and the value fill use: block e of row r sits in slot
+    e - row_ptr[r] of row r, with its column; unused slots point at the row itself (their values
+    are zero)."""
+    g, seed = GEOMS[name]
+    s = synth.grid_jacobian(g.nx, g.ny, g.nz, seed)
+    sym = Sym(hs, g, s)
+    w, pad = sym.get(-1, "ell_shape")
+    loc, col = sym.get(-1, "ell_loc"), sym.get(-1, "ell_col")
+    n = s.n_cells
+    assert pad % 64 == 0 and n <= pad < n + 64
+    assert w == np.diff(s.row_ptr).max() and len(col) == w * pad
+    rows = np.repeat(np.arange(n), np.diff(s.row_ptr))
+    slot = np.arange(s.nnzb) - s.row_ptr[rows]
+    np.testing.assert_array_equal(loc, slot * pad + rows)
+    np.testing.assert_array_equal(col[loc], s.col_idx)
+    used = np.zeros(w * pad, dtype=bool)
+    used[loc] = True
+    free = np.nonzero(~used)[0]
+    r = free % pad
+    np.testing.assert_array_equal(col[free], np.where(r < n, r, 0))
