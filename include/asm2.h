@@ -305,7 +305,8 @@ typedef struct asm_server* asm_server_handle;
 /* cuda_stream: the stream all served work is issued on (NULL = legacy default stream).
  * Errors: INVALID_ARG (bad option / device index), CUDA (no usable device), OOM. */
 int asm_server_create(asm_server_handle* s, const asm_server_options* opt, void* cuda_stream);
-/* Queue a request; *ticket identifies it.  Errors: INVALID_ARG (inconsistent sizes). */
+/* Queue a request; *ticket identifies it.  Errors: INVALID_ARG (inconsistent sizes, or grid and
+ * partition arguments that asm_set_grid / asm_set_partition_boxes refuse). */
 int asm_server_submit(asm_server_handle s, const asm_request* req, long long* ticket);
 /* Admit what fits, then run up to max_steps Krylov steps of the active systems. */
 int asm_server_progress(asm_server_handle s, int max_steps, int* n_active, int* n_pending);

@@ -2231,6 +2231,14 @@ int asm_server_submit(asm_server_handle S, const asm_request* q, long long* tick
         !(q->rtol >= 0.0) || q->max_iter < 1 || q->px < 1 || q->py < 1 || q->pz < 1 || q->px > q->nx ||
         q->py > q->ny || q->pz > q->nz)
         return ASM_ERR_INVALID_ARG;
+    // what asm_set_grid and asm_set_partition_boxes refuse, refused before the analysis thread
+    // builds the structure from the request
+    if (q->n_cells > (1 << 27) || q->overlap < 0 || q->near_width < 0 || q->far_mode < ASM_FAR_NONE ||
+        q->far_mode > ASM_FAR_BOXES)
+        return ASM_ERR_INVALID_ARG;
+    for (int d = 0; d < 3; d++)
+        if ((q->near_width > 0 && q->c_near[d] < 1) || (q->far_mode == ASM_FAR_BOXES && q->c_far[d] < 1))
+            return ASM_ERR_INVALID_ARG;
     Req* r = new (std::nothrow) Req();
     if (!r) return ASM_ERR_OOM;
     r->ticket = S->next_ticket++;
