@@ -95,4 +95,12 @@ def test_bad_request_is_rejected():
     s = synth.grid_jacobian(4, 4, 2, 1)
     with pytest.raises(asm2.ASMError):
         srv.submit(s, s.b, partition=(5, 1, 1))
+    # partition arguments asm_set_partition_boxes refuses are refused at submission, before the
+    # analysis thread sees them
+    for kw in ({"c_near": (0, 2, 2)}, {"overlap": -1}, {"near_width": -1}, {"far_mode": 3},
+               {"far_mode": "boxes", "c_far": (2, 0, 2)}):
+        with pytest.raises(asm2.ASMError) as e:
+            srv.submit(s, s.b, partition=(2, 1, 1), **kw)
+        assert e.value.status == 1, kw
+    assert srv.stats()["submitted"] == 0
     srv.close()
