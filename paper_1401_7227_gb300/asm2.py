@@ -166,6 +166,28 @@ def _is_torch(x) -> bool:
     return type(x).__module__.startswith("torch")
 
 
+def _values(x, n: int, what: str):
+    """(x as contiguous float64 with exactly n values, on_device).  CUDA tensors stay on the device;
+    anything else becomes a host array.  The library reads exactly n values from the pointer, so a
+    shorter or narrower buffer is refused here instead of being read past its end."""
+    if _is_torch(x) and x.is_cuda:
+        import torch
+        xi = x.contiguous().to(torch.float64)
+        got = xi.numel()
+        dev = True
+    else:
+        xi = np.ascontiguousarray(x, dtype=np.float64)
+        got = xi.size
+        dev = False
+    if got != n:
+        raise ValueError(f"{what}: expected {n} values, got {got}")
+    return xi, dev
+
+
+def _ptr(a, on_device: bool):
+    return C.c_void_p(a.data_ptr()) if on_device else _host_ptr(a)
+
+
 def _current_stream(device: int):
     import torch
     return torch.cuda.current_stream(device).cuda_stream
@@ -196,6 +218,7 @@ class Solver:
         _check(L.asm_create(C.byref(h), C.byref(o), C.c_void_p(self.stream)), "create")
         self._h = h
         self.n_cells = 0
+        self.nnzb = None
 
     def close(self):
         if getattr(self, "_h", None):
@@ -217,24 +240,20 @@ class Solver:
         self.n_cells = nx * ny * nz
 
     def set_matrix(self, row_ptr, col_idx, vals):
-        rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
-        ci = np.ascontiguousarray(col_idx, dtype=np.int32)
-        if _is_torch(vals) and vals.is_cuda:
-            v = vals.contiguous()
-            _check(load().asm_set_matrix_bsr(self._h, rp.shape[0] - 1, ci.shape[0], _host_ptr(rp), _host_ptr(ci),
-                                             C.c_void_p(v.data_ptr()), 1), "set_matrix")
-        else:
-            v = np.ascontiguousarray(vals, dtype=np.float64)
-            _check(load().asm_set_matrix_bsr(self._h, rp.shape[0] - 1, ci.shape[0], _host_ptr(rp), _host_ptr(ci),
-                                             _host_ptr(v), 0), "set_matrix")
+        """row_ptr int32 [N+1], col_idx int32 [nnzb], vals [nnzb, 3, 3] float64 (host or CUDA)."""
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int32).ravel()
+        ci = np.ascontiguousarray(col_idx, dtype=np.int32).ravel()
+        v, dev = _values(vals, 9 * ci.shape[0], "set_matrix")
+        _check(load().asm_set_matrix_bsr(self._h, rp.shape[0] - 1, ci.shape[0], _host_ptr(rp), _host_ptr(ci),
+                                         _ptr(v, dev), int(dev)), "set_matrix")
+        self.nnzb = ci.shape[0]
 
     def update_values(self, vals):
-        if _is_torch(vals) and vals.is_cuda:
-            v = vals.contiguous()
-            _check(load().asm_update_values(self._h, C.c_void_p(v.data_ptr()), 1), "update_values")
-        else:
-            v = np.ascontiguousarray(vals, dtype=np.float64)
-            _check(load().asm_update_values(self._h, _host_ptr(v), 0), "update_values")
+        """New values on the pattern of set_matrix (vals [nnzb, 3, 3], host or CUDA)."""
+        if self.nnzb is None:  # no matrix yet: the library reports STATE without reading vals
+            _check(load().asm_update_values(self._h, _host_ptr(np.zeros(9)), 0), "update_values")
+        v, dev = _values(vals, 9 * self.nnzb, "update_values")
+        _check(load().asm_update_values(self._h, _ptr(v, dev), int(dev)), "update_values")
 
     def set_partition(self, px: int, py: int, pz: int, overlap: int = 1, near_width: int = 2,
                       c_near=(2, 2, 2), far_mode: str | int = "partition", c_far=None):
@@ -262,18 +281,13 @@ class Solver:
         _check(st, "factor")
 
     def _vec_call(self, fn, x, what):
-        n3 = 3 * self.n_cells
-        if _is_torch(x) and x.is_cuda:
+        xi, dev = _values(x, 3 * self.n_cells, what)
+        if dev:
             import torch
-            xi = x.contiguous().to(torch.float64)
             out = torch.empty_like(xi)
-            _check(fn(self._h, C.c_void_p(xi.data_ptr()), C.c_void_p(out.data_ptr()), 1), what)
-            return out
-        xi = np.ascontiguousarray(x, dtype=np.float64)
-        if xi.shape[0] != n3:
-            raise ValueError(f"{what}: expected {n3} values")
-        out = np.empty_like(xi)
-        _check(fn(self._h, _host_ptr(xi), _host_ptr(out), 0), what)
+        else:
+            out = np.empty_like(xi)
+        _check(fn(self._h, _ptr(xi, dev), _ptr(out, dev), int(dev)), what)
         return out
 
     def apply(self, r):
@@ -286,16 +300,13 @@ class Solver:
     def solve(self, b, rtol: float = 1e-8, max_iter: int = 1000, check: bool = False):
         """x with ||b - A x|| <= rtol ||b||; returns (x, info dict)."""
         info = SolveInfo()
-        if _is_torch(b) and b.is_cuda:
+        bi, dev = _values(b, 3 * self.n_cells, "solve")
+        if dev:
             import torch
-            bi = b.contiguous().to(torch.float64)
             x = torch.empty_like(bi)
-            st = load().asm_solve(self._h, C.c_void_p(bi.data_ptr()), C.c_void_p(x.data_ptr()), rtol, max_iter, 1,
-                                  C.byref(info))
         else:
-            bi = np.ascontiguousarray(b, dtype=np.float64)
             x = np.empty_like(bi)
-            st = load().asm_solve(self._h, _host_ptr(bi), _host_ptr(x), rtol, max_iter, 0, C.byref(info))
+        st = load().asm_solve(self._h, _ptr(bi, dev), _ptr(x, dev), rtol, max_iter, int(dev), C.byref(info))
         if st not in (ASM_OK, 4) or (check and st != ASM_OK):
             raise ASMError(st, "solve")
         return x, info.as_dict()
@@ -370,17 +381,20 @@ class Solver:
 
 def solve_batch(solvers, bs, rtol: float = 1e-8, max_iter: int = 1000):
     """Solve several factored systems in the same launches; returns ([x], [info])."""
-    import torch
     n = len(solvers)
+    if len(bs) != n:
+        raise ValueError("solve_batch: one right-hand side per solver")
     hs = (C.c_void_p * n)(*[s.handle for s in solvers])
     on_dev = all(_is_torch(b) and b.is_cuda for b in bs)
     if on_dev:
-        bi = [b.contiguous().to(torch.float64) for b in bs]
+        import torch
+        bi = [_values(b, 3 * s.n_cells, "solve_batch")[0] for s, b in zip(solvers, bs)]
         xs = [torch.empty_like(b) for b in bi]
         bp = (C.c_void_p * n)(*[b.data_ptr() for b in bi])
         xp = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
-    else:
-        bi = [np.ascontiguousarray(b, dtype=np.float64) for b in bs]
+    else:  # all on the host (CUDA tensors in a mixed list are copied to the host)
+        bi = [np.ascontiguousarray(b.cpu() if _is_torch(b) else b, dtype=np.float64) for b in bs]
+        bi = [_values(b, 3 * s.n_cells, "solve_batch")[0] for s, b in zip(solvers, bi)]
         xs = [np.empty_like(b) for b in bi]
         bp = (C.c_void_p * n)(*[b.ctypes.data for b in bi])
         xp = (C.c_void_p * n)(*[x.ctypes.data for x in xs])
@@ -441,13 +455,18 @@ class Server:
 
     def submit(self, system, b, partition=(1, 1, 1), overlap=1, near_width=2, c_near=(2, 2, 2), far_mode="partition",
                c_far=None, rtol=1e-8, max_iter=1000, matrix_key=-1) -> int:
-        rp = np.ascontiguousarray(system.row_ptr, dtype=np.int32)
-        ci = np.ascontiguousarray(system.col_idx, dtype=np.int32)
-        v = np.ascontiguousarray(system.vals, dtype=np.float64)
-        bb = np.ascontiguousarray(b, dtype=np.float64)
+        # host copies: the request borrows these pointers until its result is collected
+        host = lambda a: a.detach().cpu() if _is_torch(a) else a  # noqa: E731
+        n_cells = system.nx * system.ny * system.nz
+        rp = np.ascontiguousarray(host(system.row_ptr), dtype=np.int32).ravel()
+        ci = np.ascontiguousarray(host(system.col_idx), dtype=np.int32).ravel()
+        if rp.shape[0] != n_cells + 1:
+            raise ValueError(f"submit: row_ptr needs {n_cells + 1} entries, got {rp.shape[0]}")
+        v, _ = _values(host(system.vals), 9 * ci.shape[0], "submit")
+        bb, _ = _values(host(b), 3 * n_cells, "submit")
         q = Request()
         q.nx, q.ny, q.nz = system.nx, system.ny, system.nz
-        q.n_cells, q.nnzb = system.nx * system.ny * system.nz, ci.shape[0]
+        q.n_cells, q.nnzb = n_cells, ci.shape[0]
         q.row_ptr, q.col_idx, q.vals = rp.ctypes.data, ci.ctypes.data, v.ctypes.data
         q.px, q.py, q.pz = partition
         q.overlap, q.near_width = overlap, near_width

@@ -81,3 +81,58 @@ def test_no_device_is_a_cuda_error(lib):
     with pytest.raises(asm2.ASMError) as e:
         asm2.Solver(stream=0)
     assert e.value.status == 6
+
+
+class _FakeLib:
+    """Records the library calls the binding makes; every call returns ASM_OK."""
+
+    def __init__(self):
+        self.calls = []
+
+    def __getattr__(self, name):
+        def call(*args):
+            self.calls.append(name)
+            return 0
+        return call
+
+
+def test_binding_refuses_wrong_lengths_before_calling_the_library(monkeypatch):
+    """The library reads exactly 3N (vectors) or 9 nnzb (values) doubles from each pointer it gets,
+    so the binding checks those counts first: a wrong length raises ValueError with no call made."""
+    import numpy as np
+    from paper_1401_7227_gb300 import synth
+    fake = _FakeLib()
+    monkeypatch.setattr(asm2, "_lib", fake)
+    s = synth.grid_jacobian(2, 2, 1, 1)     # N = 4, nnzb = 12
+    sol = object.__new__(asm2.Solver)
+    sol._h, sol.n_cells, sol.nnzb, sol.device, sol.stream = C.c_void_p(1), s.n_cells, s.nnzb, 0, 0
+    srv = object.__new__(asm2.Server)
+    srv._h, srv._keep, srv._n, srv.stream = C.c_void_p(1), {}, {}, 0
+    try:
+        bad = [
+            lambda: sol.solve(np.zeros(3 * s.n_cells - 1)),
+            lambda: sol.apply(np.zeros(3 * s.n_cells + 1)),
+            lambda: sol.spmv(np.zeros((3, 3))),
+            lambda: sol.update_values(s.vals[:-1]),
+            lambda: sol.set_matrix(s.row_ptr, s.col_idx, s.vals[:-1]),
+            lambda: asm2.solve_batch([sol, sol], [s.b, s.b[:-1]]),
+            lambda: asm2.solve_batch([sol, sol], [s.b]),
+            lambda: srv.submit(s, s.b[:-3]),
+            lambda: srv.submit(synth.GridSystem(s.nx, s.ny, s.nz, s.row_ptr[:-1], s.col_idx, s.vals, s.b, 1, 1.0),
+                               s.b),
+        ]
+        for f in bad:
+            with pytest.raises(ValueError):
+                f()
+        assert fake.calls == []
+        # the right lengths reach the library
+        sol.solve(s.b)
+        sol.apply(s.b.reshape(-1, 3))
+        sol.update_values(s.vals)
+        asm2.solve_batch([sol, sol], [s.b, s.b])
+        srv.submit(s, s.b)
+        assert fake.calls == ["asm_solve", "asm_apply_precond", "asm_update_values", "asm_solve_batch",
+                              "asm_server_submit"]
+    finally:
+        sol._h = None   # never hand the fake handle to the real library
+        srv._h = None
