@@ -41,6 +41,18 @@ GEOMS = {
     "far_small": (O.Geometry(12, 12, 6, 3, 3, 1, ov=1, near_width=1, far_mode=2, cfar=(2, 2, 3)), 10),
     "ov_wide": (O.Geometry(10, 9, 8, 2, 3, 2, ov=3, near_width=2, cnear=(4, 4, 4)), 11),
     "line": (O.Geometry(1, 1, 30, 1, 1, 4, ov=1, near_width=2, cnear=(1, 1, 2)), 12),
+    # edge cases: one-cell-wide boxes, an overlap or a near ring that covers the grid, near boxes
+    # larger than the grid, one-cell and whole-grid far boxes, no near and no far field
+    "thin_x": (O.Geometry(6, 4, 3, 6, 1, 1, ov=1, near_width=2), 16),
+    "thin_all": (O.Geometry(3, 3, 3, 3, 3, 3, ov=0, near_width=1, cnear=(1, 1, 1)), 17),
+    "ov_covers": (O.Geometry(6, 5, 4, 2, 1, 1, ov=10, near_width=2), 18),
+    "ring_covers": (O.Geometry(6, 5, 4, 2, 2, 1, ov=0, near_width=20), 19),
+    "cnear_big": (O.Geometry(6, 5, 4, 2, 1, 1, ov=0, near_width=2, cnear=(50, 50, 50)), 20),
+    "cfar_one": (O.Geometry(6, 5, 4, 2, 1, 1, ov=0, near_width=1, far_mode=2, cfar=(1, 1, 1)), 21),
+    "cfar_big": (O.Geometry(6, 5, 4, 2, 2, 1, ov=0, near_width=1, far_mode=2, cfar=(40, 40, 40)), 22),
+    "cnear_odd": (O.Geometry(7, 9, 5, 2, 3, 1, ov=1, near_width=3, cnear=(3, 4, 5), far_mode=2, cfar=(5, 2, 3)), 23),
+    "z_split": (O.Geometry(4, 4, 12, 1, 1, 6, ov=1, near_width=2), 24),
+    "nothing": (O.Geometry(6, 6, 3, 3, 3, 1, ov=0, near_width=0, far_mode=0), 25),
 }
 # levels of several hundred fine rows: more than the largest chunk capacity, so levels are split
 WIDE = (O.Geometry(40, 40, 8, 1, 1, 1, ov=0, near_width=0, far_mode=0), 15)
