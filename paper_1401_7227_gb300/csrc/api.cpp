@@ -159,6 +159,8 @@ int guard(asm_ctx* h, const std::function<int()>& f) {
         return e.status;
     } catch (const std::bad_alloc&) {
         return ASM_ERR_OOM;
+    } catch (const std::exception&) {  // other host resources: vector growth, thread creation
+        return ASM_ERR_OOM;
     }
 }
 
@@ -1463,6 +1465,7 @@ struct SymEntry {
     std::shared_ptr<SysSym> sym;
     bool ready = false;
     std::string err;
+    int status = ASM_ERR_INVALID_ARG;  // the requests' status when err is set
 };
 
 struct Req {
@@ -1526,24 +1529,30 @@ void sym_worker(asm_server* S) {
         }
         SymEntry e;
         const asm_request& q = r->in;
-        e.err = build_pattern(q.n_cells, q.row_ptr, q.col_idx, q.nnzb, e.pat);
-        if (e.err.empty()) {
-            Geom g;
-            g.nx = q.nx;
-            g.ny = q.ny;
-            g.nz = q.nz;
-            g.px = q.px;
-            g.py = q.py;
-            g.pz = q.pz;
-            g.ov = q.overlap;
-            g.nw = q.near_width;
-            for (int d = 0; d < 3; d++) {
-                g.cn[d] = q.near_width > 0 ? q.c_near[d] : 1;
-                g.cf[d] = q.far_mode == ASM_FAR_BOXES ? q.c_far[d] : 1;
+        try {  // an exception must not leave the thread: host memory or threads ran out
+            e.err = build_pattern(q.n_cells, q.row_ptr, q.col_idx, q.nnzb, e.pat);
+            if (e.err.empty()) {
+                Geom g;
+                g.nx = q.nx;
+                g.ny = q.ny;
+                g.nz = q.nz;
+                g.px = q.px;
+                g.py = q.py;
+                g.pz = q.pz;
+                g.ov = q.overlap;
+                g.nw = q.near_width;
+                for (int d = 0; d < 3; d++) {
+                    g.cn[d] = q.near_width > 0 ? q.c_near[d] : 1;
+                    g.cf[d] = q.far_mode == ASM_FAR_BOXES ? q.c_far[d] : 1;
+                }
+                g.far_mode = q.far_mode;
+                e.sym = std::make_shared<SysSym>();
+                e.err = build_symbolic(g, e.pat, S->opt.precision, 1, *e.sym, 0);
             }
-            g.far_mode = q.far_mode;
-            e.sym = std::make_shared<SysSym>();
-            e.err = build_symbolic(g, e.pat, S->opt.precision, 1, *e.sym, 0);
+        } catch (const std::exception& ex) {
+            e.sym.reset();
+            e.err = std::string("host resources: ") + ex.what();
+            e.status = ASM_ERR_OOM;
         }
         e.ready = true;
         std::lock_guard<std::mutex> lk(S->mu);
@@ -1649,7 +1658,7 @@ void admit(asm_server* S) {
                 continue;
             }
             if (!e->err.empty()) {
-                r->info.status = ASM_ERR_INVALID_ARG;
+                r->info.status = e->status;
                 r->state = 2;
                 it = S->pending.erase(it);
                 continue;
@@ -2220,7 +2229,12 @@ int asm_server_create(asm_server_handle* out, const asm_server_options* opt, voi
         return ASM_ERR_CUDA;
     }
     S->budget = o.hbm_budget > 0 ? (size_t)o.hbm_budget : (size_t)(0.85 * (double)fr);
-    S->worker = std::thread(sym_worker, S);
+    try {
+        S->worker = std::thread(sym_worker, S);
+    } catch (const std::exception&) {
+        delete S;
+        return ASM_ERR_OOM;
+    }
     *out = S;
     return ASM_OK;
 }
@@ -2241,12 +2255,19 @@ int asm_server_submit(asm_server_handle S, const asm_request* q, long long* tick
             return ASM_ERR_INVALID_ARG;
     Req* r = new (std::nothrow) Req();
     if (!r) return ASM_ERR_OOM;
-    r->ticket = S->next_ticket++;
+    r->ticket = S->next_ticket;
     r->in = *q;
-    r->b.assign(q->b, q->b + 3 * (size_t)q->n_cells);
     r->in.b = nullptr;
-    S->pending.push_back(r);
-    S->by_ticket[r->ticket] = r;
+    try {  // host memory: on failure nothing of the request stays queued
+        r->b.assign(q->b, q->b + 3 * (size_t)q->n_cells);
+        S->by_ticket[r->ticket] = r;
+        S->pending.push_back(r);
+    } catch (const std::exception&) {
+        S->by_ticket.erase(r->ticket);
+        delete r;
+        return ASM_ERR_OOM;
+    }
+    S->next_ticket++;
     S->st.submitted++;
     *ticket = r->ticket;
     return ASM_OK;
@@ -2304,6 +2325,8 @@ int asm_server_progress(asm_server_handle S, int max_steps, int* n_active, int* 
     } catch (const CudaFail& e) {
         return e.status;
     } catch (const std::bad_alloc&) {
+        return ASM_ERR_OOM;
+    } catch (const std::exception&) {
         return ASM_ERR_OOM;
     }
     if (n_active) *n_active = (int)S->active.size();

@@ -738,7 +738,11 @@ std::string build_symbolic(const Geom& g, const Pattern& A, int prec, int colsum
         }
     };
     std::vector<std::thread> pool;
-    for (int t = 1; t < threads; t++) pool.emplace_back(worker);
+    try {
+        for (int t = 1; t < threads; t++) pool.emplace_back(worker);
+    } catch (const std::exception&) {
+        // no more threads to be had: the ones that started and this one share the subdomains
+    }
     worker();
     for (auto& t : pool) t.join();
     for (int s = 0; s < K; s++)
