@@ -2011,7 +2011,12 @@ int asm_solve(asm_handle h, const double* b, double* x, double rtol, int max_ite
 int asm_solve_batch(asm_handle* hs, int n, const double* const* b, double* const* x, double rtol, int max_iter,
                     int on_device, asm_solve_info* infos) {
     if (!hs || n < 1 || !b || !x || !(rtol >= 0.0) || max_iter < 1) return ASM_ERR_INVALID_ARG;
-    std::vector<asm_ctx*> v(hs, hs + n);
+    std::vector<asm_ctx*> v;
+    try {
+        v.assign(hs, hs + n);
+    } catch (const std::exception&) {
+        return ASM_ERR_OOM;
+    }
     for (asm_ctx* h : v) {
         if (!h) return ASM_ERR_INVALID_ARG;
         if (!h->factored) return ASM_ERR_STATE;
@@ -2125,9 +2130,13 @@ int asm_get_local_info(asm_handle h, int s, int* n, int* nnzb, int* counts, int*
 
 int asm_get_local_map(asm_handle h, int s, int* map) {
     if (!h || !map || !h->sym_valid || s < 0 || s >= (int)h->sym->subs.size()) return ASM_ERR_INVALID_ARG;
-    std::vector<int> m;
-    local_map(*h->sym, s, m);
-    std::memcpy(map, m.data(), m.size() * sizeof(int));
+    try {
+        std::vector<int> m;
+        local_map(*h->sym, s, m);
+        std::memcpy(map, m.data(), m.size() * sizeof(int));
+    } catch (const std::exception&) {
+        return ASM_ERR_OOM;
+    }
     return ASM_OK;
 }
 
