@@ -1,7 +1,11 @@
-"""The benchmark's algorithmic byte count of the nested-factorisation apply, checked against an
+"""Host logic of the benchmark line (no GPU).
+
+The algorithmic byte count of the nested-factorisation apply is checked against an
 enumeration of the apply's line solves (no GPU): forward planes j = 0 .. by-1, then backward planes
 j = by-2 .. 0; in each plane the forward lines l = 0 .. bx-1, then the backward lines l = bx-2 .. 0.
-A forward line reads G^-1, M, N, P, Q and two of L2, L3, U3; a backward line G^-1, M, N, P, Q and U2."""
+A forward line reads G^-1, M, N, P, Q and two of L2, L3, U3; a backward line G^-1, M, N, P, Q and U2.
+
+The clocks summary (median SM clock, maximum, throttle reasons) is checked against sample rows."""
 import bench
 from paper_1401_7227_gb300 import synth
 
@@ -35,3 +39,22 @@ def test_nf_apply_bytes_match_the_line_solve_schedule():
         w = synth.WORKLOADS[name]
         for elem in (4, 8):
             assert bench.nf_apply_bytes(w, elem) == enumerated_bytes(w, elem), (name, elem)
+
+
+def test_clock_summary_reads_throttle_reasons():
+    """The clocks object of the bench line: median SM clock under load, the maximum, and every
+    throttle reason seen Active in any sample (nvidia-smi csv rows, noheader, nounits)."""
+    cs = bench.ClockSampler(0)
+    cs.rows = [
+        ["0", "2070", "2070", "900.5", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"],
+        ["0", "1980", "2070", "1390.0", "0x4", "Not Active", "Not Active", "Not Active", "Active"],
+        ["0", "2032", "2070", "1200.0", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"],
+        ["garbage"],
+        ["0", "[N/A]", "2070"],
+    ]
+    s = cs.summary()
+    assert s["sm_mhz"] == 2032.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    cs.rows.append(["0", "1500", "2070", "800", "0x8", "Active", "Not Active", "Active", "Not Active"])
+    assert cs.summary()["reasons"] == ["hw_slowdown", "sw_power_cap", "sw_thermal_slowdown"]
+    assert bench.ClockSampler(0).summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
