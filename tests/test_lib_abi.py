@@ -1,5 +1,6 @@
-"""The C-ABI library builds for sm_103a, loads, and exports every symbol include/asm2.h declares
-(no GPU compute here)."""
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol include/asm2.h declares; a
+C program links against it; the host-side checks of the library and of the Python binding refuse
+bad input before any device work, and nothing falls back to the CPU (no GPU compute here)."""
 import ctypes as C
 import os
 import re
@@ -136,3 +137,46 @@ def test_binding_refuses_wrong_lengths_before_calling_the_library(monkeypatch):
     finally:
         sol._h = None   # never hand the fake handle to the real library
         srv._h = None
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <string.h>
+#include "asm2.h"
+int main(void) {
+    asm_options o;
+    asm_server_options so;
+    asm_handle h = 0;
+    asm_default_options(&o);
+    asm_server_default_options(&so);
+    printf("%d %d %d %d %d %d\n", o.precision, o.krylov, o.restart, o.local_solver, o.flexible, o.device);
+    printf("%d %d %d\n", so.precision, so.restart, so.max_cached);
+    printf("%s|%s\n", asm_error_string(ASM_ERR_ZERO_PIVOT), asm_error_string(99));
+    o.restart = 0;
+    printf("%d %d\n", asm_create(&h, &o, NULL), h == 0);
+    printf("%d %d\n", asm_set_grid(NULL, 1, 1, 1), asm_destroy(NULL));
+    return 0;
+}
+"""
+
+
+def test_c_program_links_against_the_library(lib, tmp_path):
+    """The boundary is a C ABI: a C99 program includes include/asm2.h, links libasm2.so and calls
+    the host-only entry points (no GPU needed)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("no gcc")
+    src, exe = tmp_path / "abi.c", tmp_path / "abi"
+    src.write_text(C_PROGRAM)
+    libdir = os.path.dirname(lib_build.LIB)
+    subprocess.run([cc, "-std=c99", "-Wall", "-Werror", f"-I{os.path.join(ROOT, 'include')}", str(src), "-o", str(exe),
+                    f"-L{libdir}", "-l:libasm2.so", f"-Wl,-rpath,{libdir}"], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines()
+    assert out[0] == "0 0 30 0 -1 0"
+    assert out[1].split()[1] == "30" and out[1].split()[2] == "16"
+    zp, unknown = out[2].split("|")
+    assert zp == lib.asm_error_string(3).decode() and unknown == "unknown status"
+    assert out[3] == "1 1"          # restart 0 is refused on the host, the handle stays NULL
+    assert out[4] == "1 0"
