@@ -1,6 +1,7 @@
-"""Thin ctypes binding of ``libasm2.so`` (include/asm2.h).  Argument marshalling only: every step of
-the solver runs in the library's CUDA kernels.  Device buffers are torch CUDA tensors, host
-buffers numpy arrays; the stream is torch's current CUDA stream unless one is given.
+"""Thin ctypes binding of ``libasm2.so`` (include/asm2.h): the boundary-conditioned additive
+Schwarz preconditioner (Section 4) with GMRES / ORTHOMIN (Section 2).  Argument marshalling only:
+every step of the solver runs in the library's CUDA kernels.  Device buffers are torch CUDA
+tensors, host buffers numpy arrays; the stream is torch's current CUDA stream unless one is given.
 
 There is no fallback: if the library is missing or no CUDA device is present the calls raise.
 """

@@ -1,6 +1,14 @@
 // C-ABI of libasm2 (include/asm2.h): handle state, device memory, factorisation and the batched
-// GMRES driver.  All arithmetic of the method runs in the CUDA kernels; the host only moves
-// data, builds the symbolic structure and sequences launches.
+// Krylov driver.  It covers:
+//   - the set-up of A and of the boundary-conditioned subdomains (Section 4, Eq. 4.1);
+//   - the local factorisations (Section 2, block ILU(0) with column sums; Section 5, exact;
+//     Appendix A, nested factorisation);
+//   - GMRES(m) and ORTHOMIN(k) right-preconditioned by the additive Schwarz apply (Section 2,
+//     Eqs. 4.2-4.5);
+//   - the classical coarse corrections (Section 3);
+//   - the continuous-batching server.
+// All arithmetic of the method runs in the CUDA kernels; the host only moves data, builds the
+// symbolic structure and sequences launches.
 #include <algorithm>
 #include <chrono>
 #include <cstdio>

@@ -1,4 +1,5 @@
-// asm_residual_noalloc: r = b - A x and ||r||_2 without allocating anything.
+// asm_residual_noalloc: r = b - A x and ||r||_2 without allocating anything (the true residual
+// that ends a Krylov solve, Section 2).
 //
 // Some callers cannot call cudaMalloc at the point where they need a residual: code running while
 // a caller-owned memory pool forbids further device allocations, code whose allocations must stay
