@@ -10,7 +10,6 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built libasm2.so")
-    config.addinivalue_line("markers", "slow: long-running CPU test")
 
 
 def pytest_collection_modifyitems(config, items):
