@@ -489,3 +489,21 @@ def test_P8_near_and_far_together_need_no_more_iterations(nx, ny, nz, K, C):
 
     near, far, both = iters(2, 0), iters(0, 2), iters(2, 2)
     assert both <= min(near, far), (near, far, both)
+
+
+@pytest.mark.parametrize("g", [
+    O.Geometry(4, 4, 2, 5, 1, 1),                                   # more boxes than cells in x
+    O.Geometry(4, 4, 2, 1, 1, 1, ov=-1),
+    O.Geometry(4, 4, 2, 1, 1, 1, near_width=2, cnear=(0, 2, 2)),
+    O.Geometry(4, 4, 2, 1, 1, 1, far_mode=2, cfar=(0, 1, 1)),
+    O.Geometry(4, 4, 2, 1, 1, 1, far_mode=3),
+    O.Geometry(0, 4, 2),
+])
+def test_invalid_geometry_is_refused(g):
+    """Section 4's geometry needs 1 <= p <= n per axis, ov >= 0, near and far boxes of >= 1 cell:
+    the oracle refuses anything else instead of building from it."""
+    s = synth.grid_jacobian(4, 4, 2, 1)
+    with pytest.raises(ValueError):
+        O.local_map(g, 0)
+    with pytest.raises(O.OracleError):
+        O.Precond(g, s.row_ptr, s.col_idx, s.vals)
