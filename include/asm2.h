@@ -247,6 +247,7 @@ int asm_set_tuning(asm_handle h, int key, int value);
 int asm_set_profiling(asm_handle h, int enable);
 /* Accumulated profile since the last reset (counters keep running when profiling is off). */
 int asm_get_profile(asm_handle h, asm_profile_info* p);
+/* Zero the accumulated profile and launch counters. */
 int asm_reset_profile(asm_handle h);
 
 /* After ZERO_PIVOT: the subdomain and local block row of the first singular pivot found. */
@@ -300,6 +301,8 @@ typedef struct {
     int active, pending;
 } asm_server_stats;
 
+/* Defaults: FP32 factors, GMRES(30), device 0, 64 active systems, 16 cached, budget 0 (85% of the
+ * free device memory at creation). */
 void asm_server_default_options(asm_server_options* opt);
 typedef struct asm_server* asm_server_handle;
 /* cuda_stream: the stream all served work is issued on (NULL = legacy default stream).
@@ -313,7 +316,9 @@ int asm_server_progress(asm_server_handle s, int max_steps, int* n_active, int* 
 /* STATE while the request is unfinished; else copies x (3N doubles, host) and its info, forgets
  * the ticket and returns OK (also when not converged: see info.status) or the request's error. */
 int asm_server_result(asm_server_handle s, long long ticket, double* x, asm_solve_info* info);
+/* Counters since creation, and the current resident bytes, budget, active and pending counts. */
 int asm_server_get_stats(asm_server_handle s, asm_server_stats* stats);
+/* Stops the analysis thread and frees every system, cached factor and uncollected request. */
 int asm_server_destroy(asm_server_handle s);
 
 /* No-allocation true residual: r = b - A x and *norm = ||r||_2 for the matrix held by h.
