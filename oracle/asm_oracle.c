@@ -1023,6 +1023,8 @@ int orc_pc_set_coarse(orc_pc* pc, const int* rp, const int* ci, const double* v,
                 for (int k = 0; k < g->nz; k++)
                     cc->box[k + g->nz * (i + g->nx * j)] = k / cbox[2] + nbz * (i / cbox[0] + nbx * (j / cbox[1]));
     }
+    for (int a = 0; a < N; a++) /* every cell in one of the nb boxes, before A_C is indexed by them */
+        if (cc->box[a] < 0 || cc->box[a] >= cc->nb) return ORC_ERR_ARG;
     const int n3 = 3 * cc->nb;
     if (dense_alloc(&cc->lu, n3)) return ORC_ERR_NOMEM;
     /* A_C(I, J) = sum of the blocks A(a, b) over cells a in box I and b in box J */
