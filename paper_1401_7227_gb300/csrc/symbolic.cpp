@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <climits>
 #include <cstring>
 #include <thread>
 #include <unordered_map>
@@ -652,6 +653,8 @@ std::string build_pattern(int n, const int* rp, const int* ci, int nnzb, Pattern
             if (P.find(ci[e], r) < 0) return "pattern: not structurally symmetric";
     P.ell_w = w;
     P.rows_pad = (n + 63) / 64 * 64;
+    // ELL locations w * rows_pad + r are int (the kernels index the values in 64 bits)
+    if ((long long)w * P.rows_pad > (long long)INT_MAX) return "too large: the longest row times the rows";
     P.ell_loc.assign(nnzb, 0);
     P.ell_col.assign((size_t)w * P.rows_pad, 0);
     for (int r = 0; r < P.rows_pad; r++)
