@@ -112,35 +112,134 @@ def max_over_ranks(x: float, ws: int) -> float:
 
 
 # ---------------------------------------------------------------------------------------------
-# CPU oracle, bounded sample
+# CPU oracle: measured in full on the small workloads, estimated from a bounded sample on the
+# 1M-cell one
 # ---------------------------------------------------------------------------------------------
-def oracle_estimate(w, system, iters: int, sample_subs=2, sample_iters=4):
-    """Estimated oracle ms per solve: sampled subdomain setup+factor and local solves scaled by K,
-    plus oracle GMRES iterations (SpMV + MGS) timed on the full grid, for `iters` iterations."""
+# GMRES(30) iterations to 1e-8 of each workload (FP64 path; the oracle takes the same count at the
+# two smaller sizes): the reference arm extrapolates its sample to this many iterations
+ITERS_MEASURED = {"grid10x10x5_k4": 26, "grid64x64x16_k64": 38, "grid128x128x64_k512": 87}
+
+# readings of the generator that differ from the workload text, stated in every line's config
+GENERATOR = {"diagonal": "accumulation minus the COLUMN sum of the off-diagonal blocks (conservative form)",
+             "eps_p": synth.EPS_P, "eps_s": synth.EPS_S,
+             "wells": f"{synth.WELL} x T_nominal x I3 on every layer of columns (0,0) and (nx-1,ny-1)",
+             "sigma": f"scales the layer term of ln k; the cell term is fixed at {synth.CELL_NOISE}"}
+
+
+def cpu_info():
+    """(CPU model, logical cores) of this host."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu model")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return model or "unknown", os.cpu_count()
+
+
+def cycles(iters: int, m: int):
+    """Lengths of the GMRES(m) cycles of a solve of `iters` iterations."""
+    out = [m] * (iters // m)
+    if iters % m:
+        out.append(iters % m)
+    return out or [0]
+
+
+def krylov_model(w, system, points=(1, 2, 6)):
+    """Oracle GMRES(m) time without a preconditioner, T(n) = c + a n + b n (n + 1) / 2 for n
+    iterations of one cycle (c: setup and true residual, a: SpMV and the rest of an iteration,
+    b: one Gram-Schmidt projection), fitted to runs of `points` iterations.  Returns (c, a, b)
+    and the seconds spent."""
     import oracle as O
-    K = w.px * w.py * w.pz
+    t0 = time.perf_counter()
+    T = []
+    for n in points:
+        t1 = time.perf_counter()
+        O.gmres(system.row_ptr, system.col_idx, system.vals, system.b, None, w.restart, 1e-30, n)
+        T.append(time.perf_counter() - t1)
+    M = np.array([[1.0, n, n * (n + 1) / 2] for n in points])
+    c, a, b = np.linalg.lstsq(M, np.array(T), rcond=None)[0]
+    return (float(c), float(a), max(0.0, float(b))), time.perf_counter() - t0
+
+
+def subdomain_sample(w, system, subs):
+    """Oracle setup (local problem + factorisation) and one apply of each subdomain in `subs`."""
+    import oracle as O
     g = O.Geometry(w.nx, w.ny, w.nz, w.px, w.py, w.pz, ov=w.overlap)
-    subs = sorted({0, K // 2, K - 1})[:sample_subs]
-    t_setup, t_apply = 0.0, 0.0
+    t_setup, t_apply = [], []
     for s in subs:
         t0 = time.perf_counter()
-        pc = O.Precond(g, system.row_ptr, system.col_idx, system.vals, only=s)
-        t_setup += time.perf_counter() - t0
-        z = np.zeros(3 * system.n_cells)
+        pc = O.Precond(g, system.row_ptr, system.col_idx, system.vals, only=int(s))
+        t_setup.append(time.perf_counter() - t0)
         t0 = time.perf_counter()
-        pc.apply(system.b, z)
-        t_apply += time.perf_counter() - t0
+        pc.apply(system.b)
+        t_apply.append(time.perf_counter() - t0)
         del pc
-    t_setup /= len(subs)
-    t_apply /= len(subs)
+    return float(np.mean(t_setup)), float(np.mean(t_apply))
+
+
+def estimate_ms(w, iters: int, t_setup: float, t_apply: float, kry):
+    """Oracle ms per solve: every subdomain set up once; one apply per iteration and one per cycle
+    (x += B^{-1} V y); the Krylov part of each cycle from the fitted model."""
+    K = w.px * w.py * w.pz
+    c, a, b = kry
+    cyc = cycles(iters, w.restart)
+    krylov = sum(c + a * L + b * L * (L + 1) / 2 for L in cyc)
+    return 1e3 * (K * t_setup + (iters + len(cyc)) * K * t_apply + krylov), {
+        "setup_s": K * t_setup, "apply_s": (iters + len(cyc)) * K * t_apply, "krylov_s": krylov}
+
+
+def sample_subs(K: int, n: int, seed: int = 0):
+    return sorted(int(x) for x in np.random.default_rng(1000 + K + seed).choice(K, size=min(n, K), replace=False))
+
+
+def oracle_estimate(w, system, iters: int, n_subs: int = 6):
+    """Estimated oracle ms per solve of workload w from a bounded sample (n_subs random
+    subdomains, three short unpreconditioned GMRES runs)."""
+    K = w.px * w.py * w.pz
+    subs = sample_subs(K, n_subs)
     t0 = time.perf_counter()
-    O.gmres(system.row_ptr, system.col_idx, system.vals, system.b, None, w.restart, 1e-30, sample_iters)
-    t_it = (time.perf_counter() - t0) / sample_iters
-    est = K * t_setup + iters * (t_it + K * t_apply)
-    sample = (f"oracle setup+factor and one apply timed on subdomains {subs} (x{K} subdomains); "
-              f"{sample_iters} unpreconditioned oracle GMRES({w.restart}) iterations on the full grid; "
-              f"combined for {iters} iterations")
-    return est * 1e3, sample, {"setup_per_sub_s": t_setup, "apply_per_sub_s": t_apply, "gmres_iter_s": t_it}
+    t_setup, t_apply = subdomain_sample(w, system, subs)
+    kry, _ = krylov_model(w, system)
+    ms, parts = estimate_ms(w, iters, t_setup, t_apply, kry)
+    sample = (f"oracle setup+factor and one apply of subdomains {subs} (of {K}), scaled to all {K}; "
+              f"unpreconditioned oracle GMRES({w.restart}) runs of 1, 2 and 6 iterations on the full grid, "
+              f"fitted per cycle; combined for {iters} iterations")
+    return ms, sample, {"per_subdomain_setup_s": t_setup, "per_subdomain_apply_s": t_apply,
+                        "parts_s": parts, "sample_wall_s": time.perf_counter() - t0}
+
+
+def oracle_measured(name: str):
+    """One full oracle solve of a named workload (setup + factorisation, then GMRES to 1e-8),
+    timed, with its solution; beside it the estimator's prediction from a bounded sample."""
+    import oracle as O
+    w = synth.WORKLOADS[name]
+    system = synth.make(w)
+    g = O.Geometry(w.nx, w.ny, w.nz, w.px, w.py, w.pz, ov=w.overlap)
+    t0 = time.perf_counter()
+    pc = O.Precond(g, system.row_ptr, system.col_idx, system.vals)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    x, info = O.gmres(system.row_ptr, system.col_idx, system.vals, system.b, pc, w.restart, 1e-8, 3000)
+    t_solve = time.perf_counter() - t0
+    del pc
+    est, _, _ = oracle_estimate(w, system, info.iters)
+    total = 1e3 * (t_setup + t_solve)
+    rec = {"setup_factor_ms": 1e3 * t_setup, "solve_ms": 1e3 * t_solve, "total_ms": total,
+           "iterations": info.iters, "true_rel_residual": info.relres, "estimator_ms": est,
+           "estimator_error": (est - total) / total}
+    return rec, system, x
 
 
 def serving_pool(n_pool: int, seed0: int = 5_000_000):
@@ -418,27 +517,50 @@ def apply_traffic(alg_bytes: int):
         return None
 
 
+def workload_config(w, system, precision: str):
+    """The `config` object of both arms' lines (the same dict, so that the two lines compare)."""
+    return {"workload": w.name, "grid": [w.nx, w.ny, w.nz], "cells": system.n_cells,
+            "partition": [w.px, w.py, w.pz], "overlap": w.overlap, "near_width": 2, "c_near": [2, 2, 2],
+            "far": "partition boxes", "krylov": f"GMRES({w.restart})", "precision": precision,
+            "tol": 1e-8, "l2": "inputs larger than L2 (A 0.56 GB, factors > 0.5 GB)",
+            "step": "update values + re-assemble + re-factor + GMRES to 1e-8", "generator": GENERATOR}
+
+
 def run_reference(args):
+    """The oracle as it stands, on the host cores, for the GPU arm's workload and metric.  A full
+    1M-cell oracle solve takes many minutes, so each step is a bounded sample of it: the setup and
+    one apply of one subdomain (a different random one each step) and three short
+    unpreconditioned GMRES runs on the full grid, extrapolated to the whole solve (ms per solve,
+    `value`).  `ms_per_step` is the time the sample itself took."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
     w = synth.WORKLOADS[args.workload]
     system = synth.make(w)
-    iters = args.ref_iters
-    vals = []
-    sample = ""
-    # no warm-up: the oracle has no caches or lazy setup worth excluding, and each step is long
-    for _ in range(args.steps):
-        ms, sample, _ = oracle_estimate(w, system, iters, sample_subs=1, sample_iters=2)
-        vals.append(ms)
-    v = float(np.mean(vals))
+    iters = args.ref_iters if args.ref_iters is not None else ITERS_MEASURED[w.name]
+    K = w.px * w.py * w.pz
+    order = sample_subs(K, K, seed=1)
+    est, wall = [], []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        t_setup, t_apply = subdomain_sample(w, system, [order[k % K]])
+        kry, _ = krylov_model(w, system)
+        ms, _ = estimate_ms(w, iters, t_setup, t_apply, kry)
+        if k >= args.warmup:
+            est.append(ms)
+            wall.append(1e3 * (time.perf_counter() - t0))
+    v = float(np.mean(est))
+    model, nproc = cpu_info()
+    sample = (f"per step: oracle setup+factor and one apply of one random subdomain (of {K}), scaled to all {K}, "
+              f"plus unpreconditioned oracle GMRES({w.restart}) runs of 1, 2 and 6 iterations on the full grid; "
+              f"extrapolated to {iters} iterations; value = mean of the steps' estimates")
     # n_gpus: the launch's world size, as in the GPU arm; the work itself ran on one host core
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": v, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "impl": "reference",
-            "config": {"workload": w.name, "grid": [w.nx, w.ny, w.nz], "partition": [w.px, w.py, w.pz],
-                       "overlap": w.overlap, "restart": w.restart, "iterations_assumed": iters},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "ms_per_step": float(np.mean(wall)), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference", "estimated": True,
+            "config": workload_config(w, system, args.precision), "iterations_assumed": iters,
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "cpu_model": model, "nproc": nproc, "estimated": True},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -447,6 +569,53 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------------------------
+def run_small(args, stream):
+    """The two smaller workloads end to end on both sides: one full oracle solve each (setup +
+    factorisation and GMRES timed separately, single-threaded) beside the GPU's solve in each factor
+    precision (a step as in the main line: update values, re-factor, solve), with each GPU
+    solution's error against the oracle's."""
+    import torch
+    from paper_1401_7227_gb300 import asm2
+    model, nproc = cpu_info()
+    out = {"kind": "oracle", "cores": 1, "cpu_model": model, "nproc": nproc, "workloads": {}}
+    for name in ("grid10x10x5_k4", "grid64x64x16_k64"):
+        w = synth.WORKLOADS[name]
+        rec, system, xo = oracle_measured(name)
+        vals_d = torch.from_numpy(system.vals.reshape(-1)).cuda()
+        b_d = torch.from_numpy(system.b).cuda()
+        gpu = {}
+        for prec in ("fp64", "fp32", "fp16s"):
+            sol = asm2.Solver(precision=prec, restart=w.restart, stream=stream.cuda_stream)
+            sol.set_grid(w.nx, w.ny, w.nz)
+            sol.set_matrix(system.row_ptr, system.col_idx, vals_d)
+            sol.set_partition(w.px, w.py, w.pz, w.overlap)
+            sol.factor()
+
+            def step():
+                sol.update_values(vals_d)
+                sol.factor()
+                return sol.solve(b_d, rtol=1e-8, max_iter=3000)
+
+            for _ in range(max(3, args.warmup)):
+                step()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                x, info = step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            xh = x.cpu().numpy()
+            gpu[prec] = {"ms_per_solve": e0.elapsed_time(e1) / args.steps, "iterations": info["iterations"],
+                         "true_rel_residual": info["rel_residual"],
+                         "err_vs_oracle": float(np.linalg.norm(xh - xo) / np.linalg.norm(xo))}
+            sol.close()
+        rec["gpu"] = gpu
+        rec["oracle_over_gpu_fp64"] = rec["total_ms"] / gpu["fp64"]["ms_per_solve"]
+        out["workloads"][name] = rec
+    return out
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -511,7 +680,8 @@ def run_gpu(args):
         import oracle as O
         r = system.b - O.spmv(system.row_ptr, system.col_idx, system.vals, xh)
         results[prec] = {"ms": ms, "info": infos[-1], "prof": prof, "stats": st, "clocks": clk.summary(),
-                         "host_check_relres": float(np.linalg.norm(r) / np.linalg.norm(system.b)), "solver": sol}
+                         "host_check_relres": float(np.linalg.norm(r) / np.linalg.norm(system.b)), "solver": sol,
+                         "x": xh}
 
     main = results[args.precision]
     sol = main["solver"]
@@ -540,6 +710,14 @@ def run_gpu(args):
     barrier()
     e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, ws)
 
+    def err_vs_fp64(x):
+        """relative distance to the FP64 GPU solution (itself checked against the oracle at the
+        smaller sizes and against the oracle's apply on sampled subdomains at this size)"""
+        if "fp64" not in results:
+            return None
+        x64 = results["fp64"]["x"]
+        return float(np.linalg.norm(x - x64) / np.linalg.norm(x64))
+
     prof = main["prof"]
     st = main["stats"]
     n_apply = max(1, prof["apply_launches"])
@@ -552,19 +730,17 @@ def run_gpu(args):
         "metric": METRIC, "value": main["ms"], "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": main["ms"], "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64 Krylov / f32 factors" if args.precision == "fp32" else args.precision, "data": "synthetic",
-        "config": {"workload": w.name, "grid": [w.nx, w.ny, w.nz], "cells": system.n_cells,
-                   "partition": [w.px, w.py, w.pz], "overlap": w.overlap, "near_width": 2, "c_near": [2, 2, 2],
-                   "far": "partition boxes", "krylov": f"GMRES({w.restart})", "precision": args.precision,
-                   "tol": 1e-8, "l2": "inputs larger than L2 (A 0.56 GB, factors > 0.5 GB)",
-                   "step": "update values + re-assemble + re-factor + GMRES to 1e-8"},
+        "config": workload_config(w, system, args.precision),
         "solves_per_s": 1e3 * ws / main["ms"],
         "iterations": main["info"]["iterations"], "restarts": main["info"]["restarts"],
         "true_rel_residual": main["info"]["rel_residual"], "host_check_rel_residual": main["host_check_relres"],
         "mean_local_rows": st["local_rows"] / st["n_sub"],
         "precisions": {p_: {"ms_per_solve": r_["ms"], "iterations": r_["info"]["iterations"],
                             "converged": bool(r_["info"]["converged"]), "true_rel_residual": r_["info"]["rel_residual"],
-                            "host_check_rel_residual": r_["host_check_relres"]}
+                            "host_check_rel_residual": r_["host_check_relres"],
+                            "err_vs_fp64": err_vs_fp64(r_["x"])}
                        for p_, r_ in results.items() if p_ != args.precision},
+        "err_vs_fp64": err_vs_fp64(main["x"]),
         "breakdown_ms_per_solve": {k: prof[k] / args.steps for k in ("apply_ms", "spmv_ms", "ortho_ms", "factor_ms")},
         "roofline": {"bound": "hbm", "kernel": "precond apply (boxsum + fused local solves)", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": apply_traffic(alg_bytes),
@@ -577,8 +753,10 @@ def run_gpu(args):
     }
     if rank == 0 and not args.no_cpu_baseline:
         cpu_ms, sample, detail = oracle_estimate(w, system, main["info"]["iterations"])
+        model, nproc = cpu_info()
         line["cpu_baseline"] = {"value": cpu_ms, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
-                                "detail": detail}
+                                "estimated": True, "cpu_model": model, "nproc": nproc, "detail": detail}
+        line["cpu_baseline_measured"] = run_small(args, stream)
     for r_ in results.values():
         r_["solver"].close()
     if not args.no_nf and rank == 0:
@@ -603,9 +781,8 @@ def main():
     ap.add_argument("--workload", default="grid128x128x64_k512", choices=list(synth.WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16s"])
     ap.add_argument("--max-iter", type=int, default=3000)
-    # GMRES(30) iterations to 1e-8 on the 1M-cell workload (87 in every precision): the reference
-    # arm's oracle estimate extrapolates its timed sample to this many iterations
-    ap.add_argument("--ref-iters", type=int, default=87)
+    ap.add_argument("--ref-iters", type=int, default=None,
+                    help="iterations the reference arm extrapolates to (default: the workload's measured count)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batch", action="store_true")

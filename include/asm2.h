@@ -238,8 +238,15 @@ typedef enum {
                               local vectors that fits (a warm-up round, then a timed round) and
                               keep the fastest; remembered per handle for single-system solves.
                               Placements give bitwise equal results.  0: the placement rule only. */
-    ASM_TUNE_GRAPHS = 3    /* 1 (default): batched solves replay each Krylov step as a captured
+    ASM_TUNE_GRAPHS = 3,   /* 1 (default): batched solves replay each Krylov step as a captured
                               CUDA graph (one per projection count); 0: plain launches */
+    ASM_TUNE_WAIT_LIMIT = 4 /* failure-detection hook (0..30, default 22): the apply kernels (ILU
+                              sweeps and nested factorisation) give up waiting for a factor-stream
+                              copy after 2^value polls, 0 polls for value 0, and the call returns
+                              ASM_ERR_TIMEOUT without a result.  Before it leaves, each CTA waits
+                              with the full bound for its own copies in flight, so the device stays
+                              usable.  Value 0 makes every wait expire at once, which tests the
+                              timeout path without a fault; restore 22 afterwards */
 } asm_tune_key;
 int asm_set_tuning(asm_handle h, int key, int value);
 
@@ -324,16 +331,19 @@ int asm_server_destroy(asm_server_handle s);
 /* No-allocation true residual: r = b - A x and *norm = ||r||_2 for the matrix held by h.
  * The paper has no counterpart: this entry point is for callers that cannot allocate device
  * memory when they need it -- code running under a memory pool that forbids further device
- * allocations, code that must keep its allocations fixed after start-up, or a driver about to
- * capture work into a graph.  b, x (3N doubles, read), r (3N doubles, written) and norm (one
+ * allocations, or code that must keep its allocations fixed after start-up (certified or
+ * real-time simulators).  b, x (3N doubles, read), r (3N doubles, written) and norm (one
  * double, written) are caller-owned DEVICE pointers; the call allocates nothing and calls no
  * allocating routine.  The partial sums of the norm go to a scratch array compiled into the
  * library (16384 doubles + a counter, 128 KB, held by every GPU that loads the library until the
- * process exits), so N is limited to 256 * 16384 = 4,194,304 cells (INVALID_ARG beyond).  The
- * first call on a device looks up the array's device address and clears its counter: make that
- * first call before any stream capture.  All calls share the array: calls that overlap on the
- * GPU race.  Work is issued on the handle's stream; the call returns when it is done.
- * Errors: INVALID_ARG (NULL pointer, N too large), STATE (no matrix), CUDA. */
+ * process exits), so N is limited to 256 * 16384 = 4,194,304 cells (INVALID_ARG beyond).  CUDA
+ * loads a library's kernels and device arrays lazily, and loading allocates device memory, so
+ * asm_create loads this entry point's kernel and array onto the handle's device: later calls,
+ * the first one included, allocate nothing.  All calls share the array and each leaves its
+ * counter at zero: calls that overlap on the GPU race.  r must not overlap x (INVALID_ARG); r may
+ * be b.  Work is issued on the handle's stream, and the call waits for that stream before it
+ * returns.
+ * Errors: INVALID_ARG (NULL pointer, N too large, r overlapping x), STATE (no matrix), CUDA. */
 int asm_residual_noalloc(asm_handle h, const double* b, const double* x, double* r, double* norm);
 
 #ifdef __cplusplus

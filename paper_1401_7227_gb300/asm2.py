@@ -318,11 +318,14 @@ class Solver:
         return s.as_dict()
 
     def set_tuning(self, apply_smem: bool | str | None = None, coop_ortho: bool | None = None,
-                   autotune: bool | None = None, graphs: bool | None = None):
+                   autotune: bool | None = None, graphs: bool | None = None, wait_limit_log2: int | None = None):
         """apply_smem: True / "auto" (default placement), False / "device", "lumps" (lump vector in
         shared memory), "shared" (all local vectors in shared memory); see ASM_TUNE_APPLY_SMEM.
         autotune: the online placement tuner (ASM_TUNE_AUTOTUNE); graphs: CUDA graphs for batched
-        solves (ASM_TUNE_GRAPHS)."""
+        solves (ASM_TUNE_GRAPHS); wait_limit_log2: the apply kernels' chunk waits give up after
+        2^value polls (0: at once; default 22), a failure-detection hook (ASM_TUNE_WAIT_LIMIT)."""
+        if wait_limit_log2 is not None:
+            _check(load().asm_set_tuning(self._h, 4, int(wait_limit_log2)), "set_tuning")
         if autotune is not None:
             _check(load().asm_set_tuning(self._h, 2, int(autotune)), "set_tuning")
         if graphs is not None:

@@ -124,6 +124,7 @@ struct asm_ctx {
     int apply_place = 0;  // 0 automatic, else ApplyY + 1 (asm_set_tuning ASM_TUNE_APPLY_SMEM)
     bool no_autotune = false;  // asm_set_tuning ASM_TUNE_AUTOTUNE = 0
     bool no_graphs = false;    // asm_set_tuning ASM_TUNE_GRAPHS = 0
+    long long wait_limit = 1LL << 22;  // asm_set_tuning ASM_TUNE_WAIT_LIMIT (polls per chunk wait)
     int tuned_ymode = -1;      // placement the online tuner chose for single-system solves (-1: none)
     asm_profile_info prof{};
     // exact local solves (local_solver = ASM_LOCAL_EXACT): [A_i | I] inverted in place per subdomain
@@ -752,6 +753,7 @@ void ensure_workspace(asm_ctx* h) {
         h->d_dev_err.zero(h->stream);
     }
     t.dev_err = h->d_dev_err.as<int>();
+    t.wait_limit = h->wait_limit;
     const bool coarse = h->coarse_mode != 0 && h->coarse_valid;
     t.cmode = coarse ? h->coarse_mode : 0;
     t.cnb = coarse ? h->cnb : 0;
@@ -1794,7 +1796,8 @@ int asm_create(asm_handle* out, const asm_options* opt, void* cuda_stream) {
     h->stream = static_cast<cudaStream_t>(cuda_stream);
     h->prec = o.precision;
     h->flexible = o.flexible >= 0 ? o.flexible : (o.precision == ASM_PREC_FP64 ? 0 : 1);
-    int st = guard(h, [&] { return ASM_OK; });
+    // loads the no-allocation residual's module and kernel now, so that its calls allocate nothing
+    int st = guard(h, [&] { return asm2::noalloc_prepare(h->device); });
     if (st) {
         delete h;
         return st;
@@ -2091,6 +2094,16 @@ int asm_set_tuning(asm_handle h, int key, int value) {
     } else if (key == ASM_TUNE_COOP_ORTHO) {
         if (value > 1) return ASM_ERR_INVALID_ARG;
         h->no_coop = value == 0;
+    } else if (key == ASM_TUNE_WAIT_LIMIT) {
+        if (value > 30) return ASM_ERR_INVALID_ARG;
+        h->wait_limit = value == 0 ? 0 : 1LL << value;
+        h->tab.wait_limit = h->wait_limit;
+        if (h->d_tab1.p)  // the single-system table already on the device
+            return guard(h, [&] {
+                ck(cudaMemcpyAsync(h->d_tab1.p, &h->tab, sizeof(SysTab), cudaMemcpyHostToDevice, h->stream));
+                sync(h);
+                return ASM_OK;
+            });
     } else {
         return ASM_ERR_INVALID_ARG;
     }

@@ -119,6 +119,7 @@ struct SysTab {
     double* boxsum;      // [n_boxes * 3] far-box sums of the apply input
     double* corr;        // [n_corr * 3] near-region sums subtracted from far-lump box sums
     int* dev_err;        // device status word: nonzero after a bounded wait expired
+    long long wait_limit;  // polls of the first wait on each factor-stream copy of the apply kernels
     // classical coarse-grid correction (0 none, 1 two-level, 2 two-stage; Eqs. 3.5-3.8)
     int cmode;
     int cnb;             // coarse boxes
@@ -317,6 +318,9 @@ struct MatrixView {
     int ell_w, rows_pad, n_cells, device;
     cudaStream_t stream;
 };
+// Loads the no-allocation residual's scratch array and kernel onto `device` (current) and keeps
+// the array's device address; called by asm_create, while the caller can still allocate.
+int noalloc_prepare(int device);
 
 }  // namespace asm2
 

@@ -742,7 +742,7 @@ __global__ void __launch_bounds__(32) k_nf_apply(const SysTab* __restrict__ tab,
             }
             ypend = true;
         }
-        const bool ok = tma::mbar_wait(&bar[2 * bc], ph);
+        const bool ok = tma::mbar_wait(&bar[2 * bc], ph, st.wait_limit);
         if (!__all_sync(kFull, ok)) {
             fail(k);
             return;
@@ -797,7 +797,7 @@ __global__ void __launch_bounds__(32) k_nf_apply(const SysTab* __restrict__ tab,
                     write_owned(d, s.j, pv, z, lane);  // x_{by-1} = y_{by-1}
                 }
             } else {
-                const bool yok = tma::mbar_wait(ybar, (unsigned)(by - 2 - s.j) & 1u);
+                const bool yok = tma::mbar_wait(ybar, (unsigned)(by - 2 - s.j) & 1u, st.wait_limit);
                 if (!__all_sync(kFull, yok)) {
                     fail(k + 1);
                     return;

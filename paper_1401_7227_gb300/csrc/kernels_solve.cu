@@ -9,6 +9,7 @@
 #include <cooperative_groups.h>
 
 #include "asm2_internal.h"
+#include "tma.h"
 
 namespace asm2 {
 
@@ -114,36 +115,12 @@ __device__ __forceinline__ void warp_sum3(double& a0, double& a1, double& a2) {
     }
 }
 
-// TMA bulk copies into a ring of shared-memory slots, completion tracked by mbarriers.
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait: false once the iteration limit expired (the caller reports ASM_ERR_TIMEOUT).
-constexpr long long kWaitLimit = 1LL << 22;
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-    for (long long i = 0; i < kWaitLimit; i++)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
+// TMA bulk copies into a ring of shared-memory slots, completion tracked by mbarriers, with
+// bounded waits (tma.h).
+using tma::bulk_load;
+using tma::mbar_expect_tx;
+using tma::mbar_init;
+using tma::mbar_wait;
 
 constexpr int kMaxSlots = 4;  // ring slots of the apply: a template argument, 2..kMaxSlots
 constexpr int kRingHeader = 64;  // mbarriers
@@ -499,7 +476,8 @@ __global__ void __launch_bounds__(YM == Y_SMEM ? 256 : kApplyThreadsDev, YM == Y
     if ((issuer_fine || issuer_lump) && SLOTS < sd.n_chunks) next_ch = sd.chunks[SLOTS];
     for (int ci = 0; ci < sd.n_chunks; ci++) {
         const int slot = ci % SLOTS;
-        const bool ok = mbar_wait(&bar[slot], (unsigned)(ci / SLOTS) & 1u);
+        // warp-uniform, so that the warp-collective code of the sweep runs on whole warps
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(&bar[slot], (unsigned)(ci / SLOTS) & 1u, st.wait_limit));
         bool fine_chunk = false;
         if (ok) {
             const unsigned char* chunk = ring + (size_t)slot * cap;

@@ -2,13 +2,14 @@
 // that ends a Krylov solve, Section 2).
 //
 // Some callers cannot call cudaMalloc at the point where they need a residual: code running while
-// a caller-owned memory pool forbids further device allocations, code whose allocations must stay
-// fixed after start-up (certified or real-time simulators), or a driver that is about to capture
-// its work.  This entry point gives them the true residual of an x they hold: it reads the matrix
-// already stored in the handle and writes only the caller's buffers, and the block partial sums
-// of the norm go to a fixed scratch array compiled into the library.
+// a caller-owned memory pool forbids further device allocations, or code whose allocations must
+// stay fixed after start-up (certified or real-time simulators).  This entry point gives them the
+// true residual of an x they hold: it reads the matrix already stored in the handle and writes
+// only the caller's buffers, and the block partial sums of the norm go to a fixed scratch array
+// compiled into the library.
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <mutex>
 
 #include "asm2.h"
@@ -23,7 +24,7 @@ constexpr long long kNoAllocMaxCells = 256LL * kNoAllocPartials;
 // File-scope scratch: [0, kNoAllocPartials) block partials of sum r^2, then one arrival counter
 // (as an unsigned int in the last 8-byte word).  Every GPU that loads the library holds it until
 // the process exits.  Every call shares it: calls that overlap on the GPU race.
-static __device__ __align__(256) double g_noalloc_scratch[kNoAllocPartials + 1];
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocPartials + 1] = {};
 
 namespace {
 
@@ -84,34 +85,40 @@ __global__ void __launch_bounds__(256) k_residual_noalloc(const double* __restri
     }
 }
 
-// Device address of the scratch array, looked up once per device (the array's name is only a
-// host-side stand-in in host code).
+// Device address of the scratch array and the kernel, loaded once per device by
+// noalloc_prepare() from asm_create.  The library's kernels are loaded lazily by CUDA (each .cu
+// file is its own module), and loading a module or a kernel allocates device memory, so it must
+// happen while the caller can still allocate: in asm_create, not in the first residual call.  In
+// host code the array's name is only a host-side stand-in, never a device address.
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 double* g_scratch_ptr[kMaxDevices] = {};
 
-int scratch_for(int device, cudaStream_t st, double** out) {
-    if (device < 0 || device >= kMaxDevices) return ASM_ERR_INVALID_ARG;
+double* scratch_of(int device) {
+    if (device < 0 || device >= kMaxDevices) return nullptr;
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_ptr[device]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
-            cudaGetLastError();
-            return ASM_ERR_CUDA;
-        }
-        // the arrival counter must start at zero
-        if (cudaMemsetAsync(static_cast<double*>(p) + kNoAllocPartials, 0, sizeof(double), st) != cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess) {
-            cudaGetLastError();
-            return ASM_ERR_CUDA;
-        }
-        g_scratch_ptr[device] = static_cast<double*>(p);
-    }
-    *out = g_scratch_ptr[device];
-    return ASM_OK;
+    return g_scratch_ptr[device];
 }
 
 }  // namespace
+
+// Called by asm_create with `device` current.  The array needs no clearing: it is
+// zero-initialised when its module loads, and every call leaves the counter at zero.
+int noalloc_prepare(int device) {
+    if (device < 0 || device >= kMaxDevices) return ASM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (g_scratch_ptr[device]) return ASM_OK;
+    void* p = nullptr;
+    cudaFuncAttributes attr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess ||
+        cudaFuncGetAttributes(&attr, k_residual_noalloc) != cudaSuccess) {
+        cudaGetLastError();
+        return ASM_ERR_CUDA;
+    }
+    g_scratch_ptr[device] = static_cast<double*>(p);
+    return ASM_OK;
+}
+
 }  // namespace asm2
 
 extern "C" int asm_residual_noalloc(asm_handle h, const double* b, const double* x, double* r, double* norm) {
@@ -121,13 +128,17 @@ extern "C" int asm_residual_noalloc(asm_handle h, const double* b, const double*
     int st = handle_matrix_view(h, &mv);
     if (st != ASM_OK) return st;
     if (mv.n_cells > kNoAllocMaxCells) return ASM_ERR_INVALID_ARG;  // beyond the scratch array
+    // r is written while other threads still read x at neighbouring rows: they must not overlap
+    // (r may be b: each row reads its b entries before writing the same r entries)
+    const size_t n3 = 3 * (size_t)mv.n_cells;
+    const uintptr_t xs = reinterpret_cast<uintptr_t>(x), rs = reinterpret_cast<uintptr_t>(r);
+    if (rs < xs + n3 * sizeof(double) && xs < rs + n3 * sizeof(double)) return ASM_ERR_INVALID_ARG;
+    double* scratch = scratch_of(mv.device);
+    if (!scratch) return ASM_ERR_STATE;  // asm_create did not prepare this device
     if (cudaSetDevice(mv.device) != cudaSuccess) {
         cudaGetLastError();
         return ASM_ERR_CUDA;
     }
-    double* scratch = nullptr;
-    st = scratch_for(mv.device, mv.stream, &scratch);
-    if (st != ASM_OK) return st;
     const int blocks = (mv.n_cells + 255) / 256;
     k_residual_noalloc<<<blocks, 256, 0, mv.stream>>>(mv.ell_val, mv.ell_col, mv.ell_w, mv.rows_pad, mv.n_cells, b, x,
                                                       r, norm, scratch);

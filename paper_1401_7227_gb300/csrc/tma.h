@@ -40,9 +40,9 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
 
 constexpr long long kWaitLimit = 1LL << 22;
 
-// false once the iteration limit expired
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-    for (long long i = 0; i < kWaitLimit; i++)
+// false once `limit` polls have failed (limit 0: gives up at once)
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long limit = kWaitLimit) {
+    for (long long i = 0; i < limit; i++)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }

@@ -66,7 +66,9 @@ def test_reference_arm_runs_on_rank_zero_only():
 
 def test_reference_arm_prints_one_contract_line():
     """Rank 0 of a one-process launch prints one JSON line with the contract's keys; its value, the
-    CPU baseline's and the end-to-end figure are the same oracle time (small workload)."""
+    CPU baseline's and the end-to-end figure are the same estimated oracle time per solve, the step
+    time is the sample's own time, the config is the GPU arm's, and the sample is extrapolated to
+    the workload's own iteration count (small workload)."""
     env = dict(os.environ)
     for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
         env.pop(k, None)
@@ -83,7 +85,13 @@ def test_reference_arm_prints_one_contract_line():
     assert d["impl"] == "reference" and d["n_gpus"] == 1 and d["steps"] == 2 and d["warmup"] == 0
     assert d["higher_is_better"] is False and d["vs_baseline"] is None and d["data"] == "synthetic"
     assert d["config"]["workload"] == "grid10x10x5_k4"
-    assert d["value"] > 0 and d["ms_per_step"] == d["value"]
+    assert d["value"] > 0 and d["ms_per_step"] > 0 and d["estimated"] is True
+    assert d["iterations_assumed"] == 26
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1401_7227_gb300 import synth
+    w = synth.WORKLOADS["grid10x10x5_k4"]
+    assert d["config"] == json.loads(json.dumps(bench.workload_config(w, synth.make(w), "fp32")))
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["unit"] == d["unit"] and cb["cores"] >= 1
     assert cb["sample"]

@@ -1,0 +1,128 @@
+"""The 1M-cell configuration the benchmark times (128 x 128 x 64 = 1,048,576 cells, sigma 2,
+512 subdomains 16 x 16 x 2, overlap 2, near width 2 with 2 x 2 x 2 near boxes, far lumps = the
+partition boxes), checked against the oracle at full size.
+
+This is where the largest local problems (~5,900 block rows, 72+ wavefront levels), the 24 KB
+factor chunks, pz = 2 with overlap 2 and the near/far lump mix (~500 near and 511 far lumps per
+subdomain) meet.  At this size the oracle builds one subdomain at a time (its apply then writes
+that subdomain's owned rows only, Eqs. 4.2-4.5), so the preconditioner apply is compared on the
+owned rows of sampled subdomains: two corners and two x-edge subdomains (in both z halves), two
+interior ones (the largest local problems), and one a step in from a corner.  Every local-vector
+placement the apply can run in at this size is checked, since the benchmark's online tuner picks
+among them.
+
+Tolerances (relative, per subdomain's owned rows):
+- FP64 factors: 1e-12, as at the smaller sizes (summation order and FMA contraction only).
+- FP32 factors: 1e-5 (unit roundoff 6e-8 times the local amplification, measured < 1e-6).
+- FP16 factors with a per-block power-of-two exponent: 1e-2 (unit roundoff 2^-11 = 4.9e-4 on
+  every stored factor value, times the same amplification).
+The GMRES solve in each precision must reach a true relative residual of 1e-8, recomputed on the
+host with the oracle's SpMV."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1401_7227_gb300 import asm2, synth
+
+pytestmark = pytest.mark.gpu
+
+W = synth.WORKLOADS["grid128x128x64_k512"]
+# s = tz + pz (tx + px ty): 0 and 511 corners, 255 and 256 x-edges, 272 and 273 interior (both z
+# halves), 34 one subdomain in from a corner
+SUBS = (0, 255, 256, 511, 272, 273, 34)
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp16s": 1e-2}
+
+
+def owned_cells(s):
+    tz = s % W.pz
+    tx = (s // W.pz) % W.px
+    ty = s // (W.pz * W.px)
+    xs = np.arange(W.nx * tx // W.px, W.nx * (tx + 1) // W.px)
+    ys = np.arange(W.ny * ty // W.py, W.ny * (ty + 1) // W.py)
+    zs = np.arange(W.nz * tz // W.pz, W.nz * (tz + 1) // W.pz)
+    j, i, k = np.meshgrid(ys, xs, zs, indexing="ij")
+    return (k + W.nz * (i + W.nx * j)).ravel()
+
+
+@pytest.fixture(scope="module")
+def system():
+    return synth.make(W)
+
+
+@pytest.fixture(scope="module")
+def rhs(system):
+    return [system.b, synth.rhs(system.n_cells, 777)]
+
+
+@pytest.fixture(scope="module")
+def oracle_rows(system, rhs):
+    """{s: (owned cells, [oracle z on them for each right-hand side])}"""
+    g = O.Geometry(W.nx, W.ny, W.nz, W.px, W.py, W.pz, ov=W.overlap)
+    out = {}
+    for s in SUBS:
+        pc = O.Precond(g, system.row_ptr, system.col_idx, system.vals, only=s)
+        cells = owned_cells(s)
+        idx = (3 * cells[:, None] + np.arange(3)).ravel()
+        out[s] = (idx, [pc.apply(r)[idx] for r in rhs])
+        del pc
+    return out
+
+
+_solvers = {}
+
+
+def solver(system, prec):
+    if prec not in _solvers:
+        sol = asm2.Solver(precision=prec, restart=W.restart)
+        sol.set_grid(W.nx, W.ny, W.nz)
+        sol.set_matrix(system.row_ptr, system.col_idx, system.vals)
+        sol.set_partition(W.px, W.py, W.pz, W.overlap)
+        sol.factor()
+        _solvers[prec] = sol
+    return _solvers[prec]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _close_solvers():
+    yield
+    for s in _solvers.values():
+        s.close()
+    _solvers.clear()
+
+
+@pytest.mark.parametrize("placement", ["auto", "device", "lumps", "shared"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16s"])
+def test_apply_matches_oracle_on_sampled_subdomains(system, rhs, oracle_rows, prec, placement):
+    sol = solver(system, prec)
+    sol.set_tuning(apply_smem=placement)
+    worst = 0.0
+    for k, r in enumerate(rhs):
+        z = sol.apply(torch.from_numpy(r).cuda()).cpu().numpy()
+        assert np.all(np.isfinite(z))
+        for s in SUBS:
+            idx, zo = oracle_rows[s]
+            err = np.linalg.norm(z[idx] - zo[k]) / np.linalg.norm(zo[k])
+            worst = max(worst, err)
+            assert err <= TOL[prec], (s, k, err)
+    sol.set_tuning(apply_smem="auto")
+    print(f"headline apply {prec} {placement}: worst relative error on sampled owned rows {worst:.3e}")
+
+
+_x64 = {}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16s"])
+def test_solve_reaches_fp64_tolerance(system, prec):
+    sol = solver(system, prec)
+    x, info = sol.solve(torch.from_numpy(system.b).cuda(), rtol=1e-8, max_iter=3000)
+    x = x.cpu().numpy()
+    r = system.b - O.spmv(system.row_ptr, system.col_idx, system.vals, x)
+    rel = np.linalg.norm(r) / np.linalg.norm(system.b)
+    assert info["converged"] and rel <= 1e-8 * (1 + 1e-6), (info, rel)
+    if prec == "fp64":
+        _x64["x"] = x
+    msg = f"headline solve {prec}: {info['iterations']} iterations, true residual {rel:.3e}"
+    if "x" in _x64 and prec != "fp64":
+        msg += f", error vs the FP64 GPU solution {np.linalg.norm(x - _x64['x']) / np.linalg.norm(_x64['x']):.3e}"
+    print(msg)
