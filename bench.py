@@ -446,7 +446,7 @@ def run_profile_case(args):
     from paper_1401_7227_gb300 import build as lib_build
     lib_build.build()
     s = synth.grid_jacobian(128, 128, 32, 3, 2.0)
-    sol = asm2.Solver(precision=args.precision, restart=30)
+    sol = asm2.Solver(precision=args.precision, restart=30, lumps=args.lumps)
     sol.set_grid(128, 128, 32)
     sol.set_matrix(s.row_ptr, s.col_idx, s.vals)
     sol.set_partition(16, 16, 1, 2)
@@ -636,7 +636,7 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
 
     def make_solver(prec):
-        s = asm2.Solver(precision=prec, restart=w.restart, device=local, stream=stream.cuda_stream)
+        s = asm2.Solver(precision=prec, restart=w.restart, device=local, stream=stream.cuda_stream, lumps=args.lumps)
         s.set_grid(w.nx, w.ny, w.nz)
         s.set_matrix(system.row_ptr, system.col_idx, vals_d)
         s.set_partition(w.px, w.py, w.pz, w.overlap)
@@ -780,6 +780,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="grid128x128x64_k512", choices=list(synth.WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16s"])
+    ap.add_argument("--lumps", default="fp64", choices=["fp64", "fp32"],
+                    help="lump rows' precision under FP32/FP16S fine rows (asm_options.lump_precision)")
     ap.add_argument("--max-iter", type=int, default=3000)
     ap.add_argument("--ref-iters", type=int, default=None,
                     help="iterations the reference arm extrapolates to (default: the workload's measured count)")

@@ -19,6 +19,7 @@ ASM_OK = 0
 STATUS = {0: "ok", 1: "invalid argument", 2: "pattern", 3: "zero pivot", 4: "not converged", 5: "out of memory",
           6: "cuda error", 7: "timeout", 8: "state"}
 PREC = {"fp64": 0, "fp32": 1, "fp16s": 2}
+LUMPS = {"fp64": 0, "fp32": 1}
 FAR = {"none": 0, "partition": 1, "boxes": 2}
 COARSE = {"none": 0, "two-level": 1, "two-stage": 2}
 
@@ -35,7 +36,7 @@ EXPORTS = [
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("krylov", C.c_int), ("restart", C.c_int), ("local_solver", C.c_int),
-                ("flexible", C.c_int), ("device", C.c_int)]
+                ("flexible", C.c_int), ("device", C.c_int), ("lump_precision", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -67,7 +68,7 @@ class Profile(C.Structure):
 
 class ServerOptions(C.Structure):
     _fields_ = [("precision", C.c_int), ("restart", C.c_int), ("device", C.c_int), ("max_active", C.c_int),
-                ("max_cached", C.c_int), ("hbm_budget", C.c_longlong)]
+                ("max_cached", C.c_int), ("hbm_budget", C.c_longlong), ("lump_precision", C.c_int)]
 
 
 class Request(C.Structure):
@@ -203,10 +204,14 @@ class Solver:
     """One system: grid, BSR 3x3 matrix, partition, factorisation and solves."""
 
     def __init__(self, precision: str = "fp64", restart: int = 30, local_solver: str = "colsum",
-                 flexible: int = -1, device: int = 0, stream: int | None = None, krylov: str = "gmres"):
+                 flexible: int = -1, device: int = 0, stream: int | None = None, krylov: str = "gmres",
+                 lumps: str = "fp64"):
+        """lumps: "fp64" or "fp32", the lump rows' precision under FP32/FP16S fine rows
+        (asm_options.lump_precision)."""
         L = load()
         o = Options()
         L.asm_default_options(C.byref(o))
+        o.lump_precision = LUMPS[lumps]
         o.precision = PREC[precision]
         o.restart = restart
         o.local_solver = LOCAL[local_solver]
@@ -433,12 +438,13 @@ class Server:
     arrive, call progress() to admit and advance them, collect results by ticket."""
 
     def __init__(self, precision: str = "fp32", restart: int = 30, device: int = 0, max_active: int = 64,
-                 max_cached: int = 16, hbm_budget: int = 0, stream: int | None = None):
+                 max_cached: int = 16, hbm_budget: int = 0, stream: int | None = None, lumps: str = "fp64"):
         L = load()
         o = ServerOptions()
         L.asm_server_default_options(C.byref(o))
         o.precision, o.restart, o.device = PREC[precision], restart, device
         o.max_active, o.max_cached, o.hbm_budget = max_active, max_cached, hbm_budget
+        o.lump_precision = LUMPS[lumps]
         self.stream = stream if stream is not None else _current_stream(device)
         h = C.c_void_p()
         _check(L.asm_server_create(C.byref(h), C.byref(o), C.c_void_p(self.stream)), "server_create")

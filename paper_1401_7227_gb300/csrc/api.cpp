@@ -77,6 +77,7 @@ struct asm_ctx {
     int device = 0;
     int prec = 0;
     int flexible = 0;
+    bool lump32 = false;  // lump rows of the ILU factors stored and applied in FP32 (FP32/FP16 fine rows)
     // grid / matrix
     int nx = 0, ny = 0, nz = 0, N = 0;
     bool has_grid = false, has_matrix = false, has_partition = false;
@@ -98,10 +99,12 @@ struct asm_ctx {
     DBuf d_lv, d_rlists, d_y, d_corr_cells, d_corr, d_dev_err;
     int apply_smem = 0;       // shared memory for all local vectors of the largest subdomain (0: none)
     int apply_lump_smem = 0;  // shared memory for its lump vector and the FP32 mirror
+    int win_rows = 0;         // fine-level window rows of the apply (FP32 lump rows; 0 = none)
     int apply_slots = 3; // factor-stream ring slots of the apply
     int chunk_cap = kStreamChunkMin;  // largest stream-chunk capacity of the subdomains (ring slot bytes)
     int sm_smem = 0, n_sms = 1;  // shared memory per SM and SM count of the device
-    DBuf d_factdesc, d_subdesc_single;
+    DBuf d_factdesc, d_subdesc_single, d_ritems1;
+    int n_ritems1 = 0;
     DBuf d_err;
     std::vector<FactDesc> fact_desc;
     std::vector<SubDesc> sub_desc;   // sys = 0
@@ -213,6 +216,14 @@ std::vector<int2> dense_items(const std::vector<SubDesc>& sd) {
     std::vector<int2> it;
     for (int i = 0; i < (int)sd.size(); i++)
         for (int q = 0; q < 3 * sd[i].n_own; q += 8) it.push_back(make_int2(i, q));
+    return it;
+}
+
+// Work items of the restriction: (subdomain, first local row) per 256 rows (fine rows, then lumps)
+std::vector<int2> restrict_items(const std::vector<SubDesc>& sd) {
+    std::vector<int2> it;
+    for (int i = 0; i < (int)sd.size(); i++)
+        for (int q = 0; q < sd[i].nf + sd[i].nc; q += 256) it.push_back(make_int2(i, q));
     return it;
 }
 
@@ -498,7 +509,7 @@ void upload_symbolic(asm_ctx* h) {
     h->y_base.assign(K + 1, 0);
     for (int s = 0; s < K; s++) {
         const SubSym& o = S.subs[s];
-        const long long bytes = std::max<long long>((long long)apply_smem_bytes(o.nf, o.n - o.nf, S.prec), 24LL * o.n);
+        const long long bytes = std::max<long long>((long long)apply_smem_bytes(o.nf, o.n - o.nf, S.prec, S.lump32), 24LL * o.n);
         h->y_base[s + 1] = h->y_base[s] + (bytes + 15) / 16 * 2;
     }
     h->d_y.alloc((size_t)h->y_base[K] * sizeof(double));
@@ -581,6 +592,7 @@ void upload_symbolic(asm_ctx* h) {
     h->sub_cost.assign(K, 0.0);
     h->apply_smem = 0;
     h->apply_lump_smem = 0;
+    h->win_rows = 0;
     h->chunk_cap = kStreamChunkMin;
     h->tuned_ymode = -1;
     for (int s = 0; s < K; s++) {
@@ -610,11 +622,21 @@ void upload_symbolic(asm_ctx* h) {
         sd.nc = o.n - o.nf;
         sd.n_chunks = (int)o.chunk_off.size();
         sd.n_fwd = o.n_fwd_chunks;
-        // a chunk costs about one barrier-bounded step; lump-only chunks (FP64 rows) about 2.3
-        for (size_t i = 0; i < o.chunk_off.size(); i++) {
-            int hdr_nf = 0;
-            std::memcpy(&hdr_nf, o.stream.data() + o.chunk_off[i] + 4, sizeof(int));
-            h->sub_cost[s] += hdr_nf == 0 ? 2.3 : 1.0;
+        // a chunk costs about one barrier-bounded step; lump-only chunks (FP64 rows) about 2.3.
+        // The widest fine level (rows summed over its chunks) sizes the apply's level window.
+        {
+            int level_rows = 0;
+            for (size_t i = 0; i < o.chunk_off.size(); i++) {
+                int hdr_nf = 0, hdr_flags = 0;
+                std::memcpy(&hdr_nf, o.stream.data() + o.chunk_off[i] + 4, sizeof(int));
+                std::memcpy(&hdr_flags, o.stream.data() + o.chunk_off[i] + 24, sizeof(int));
+                h->sub_cost[s] += hdr_nf == 0 ? 2.3 : 1.0;
+                level_rows += hdr_nf;
+                if (hdr_flags & 1) {
+                    if (S.lump32) h->win_rows = std::max(h->win_rows, std::min(level_rows, kWinMaxRows));
+                    level_rows = 0;
+                }
+            }
         }
         sd.n_own = (int)o.own_pos.size();
         sd.n_long = (int)o.clong.size();
@@ -623,6 +645,12 @@ void upload_symbolic(asm_ctx* h) {
         h->chunk_cap = std::max(h->chunk_cap, o.chunk_cap);
         sd.stream = h->d_stream.as<unsigned char>() + h->stream_base[s];
         sd.y = h->d_y.as<double>() + h->y_base[s];
+        {
+            const YLayout L = y_layout(o.nf, o.n - o.nf, S.prec, S.lump32);
+            sd.y_fine = (int)L.fine;
+            sd.y_mirror = (int)L.mirror;
+            sd.y_bytes = (int)L.total;
+        }
         {
             // the chunk table goes first: base is 8-byte aligned, so the int2 entries are too
             std::vector<int> ch;
@@ -640,8 +668,8 @@ void upload_symbolic(asm_ctx* h) {
         sd.clong = put(o.clong);
         sd.own_pos = put(o.own_pos);
         sd.own_cell = put(o.own_cell);
-        h->apply_smem = std::max<int>(h->apply_smem, (int)apply_smem_bytes(o.nf, o.n - o.nf, S.prec));
-        h->apply_lump_smem = std::max<int>(h->apply_lump_smem, (int)apply_lump_bytes(o.n - o.nf, S.prec));
+        h->apply_smem = std::max<int>(h->apply_smem, (int)apply_smem_bytes(o.nf, o.n - o.nf, S.prec, S.lump32));
+        h->apply_lump_smem = std::max<int>(h->apply_lump_smem, (int)apply_lump_bytes(o.n - o.nf, S.prec, S.lump32));
         for (size_t k = 0; k + 1 < o.corr_ptr.size(); k++)
             corr_items.push_back(BoxItem{0, corr_base + (int)k, (int)corr_cells.size() + o.corr_ptr[k],
                                          (int)corr_cells.size() + o.corr_ptr[k + 1], 1, 0, nullptr});
@@ -704,6 +732,9 @@ void upload_symbolic(asm_ctx* h) {
         const std::vector<int2> di = dense_items(ordered);
         h->d_ditems1.upload(di, st);
         h->n_ditems1 = (int)di.size();
+        const std::vector<int2> ri = restrict_items(ordered);
+        h->d_ritems1.upload(ri, st);
+        h->n_ritems1 = (int)ri.size();
     }
     h->d_err.alloc(sizeof(FactErr));
     sync(h);
@@ -946,7 +977,7 @@ int factor_numeric(asm_ctx* h) {
         launch_factor(h->d_factdesc.as<FactDesc>(), (int)S.subs.size(), h->d_err.as<FactErr>(), nullptr, h->stream);
         launch_pack(h->d_pk_off_f.as<long long>(), h->d_pk_src_f.as<int>(), h->pk_nf, h->prec,
                     h->d_stream.as<unsigned char>(), h->d_slot.as<double>(), h->stream);
-        launch_pack(h->d_pk_off_c.as<long long>(), h->d_pk_src_c.as<int>(), h->pk_nc, 0,
+        launch_pack(h->d_pk_off_c.as<long long>(), h->d_pk_src_c.as<int>(), h->pk_nc, h->lump32 ? 1 : 0,
                     h->d_stream.as<unsigned char>(), h->d_slot.as<double>(), h->stream);
     }
     ck(cudaGetLastError());
@@ -1001,9 +1032,12 @@ namespace {
 
 struct Batch {
     std::vector<asm_ctx*> hs;
-    DBuf d_tab, d_vec, d_row, d_box, d_sub, d_gather;
+    DBuf d_tab, d_vec, d_row, d_box, d_sub, d_gather, d_ritems;
+    int nritems = 0;
     int nvec = 0, nrow = 0, nbox = 0, nsub = 0, prec = 0, slots = 3, chunk = kStreamChunkMin;
-    ApplyConfig apply{Y_DEVICE, 0, 2, kStreamChunkMin};
+    bool lump32 = false;
+    ApplyConfig apply{Y_DEVICE, 0, 2, kStreamChunkMin, 0};
+    int win = 0;  // fine-level window rows (FP32 lump rows): the widest level of the batch, capped
     int all_bytes = 0, lump_bytes = 0;  // largest subdomain's shared-memory needs (placements)
     DBuf d_dense;           // exact local solves: (subdomain item, first owned row of 8)
     int ndense = 0;
@@ -1094,6 +1128,11 @@ void build_batch(Batch& B, cudaStream_t st) {
     B.d_row.upload(ri, st);
     B.d_box.upload(bi, st);
     B.d_sub.upload(sd, st);
+    {
+        const std::vector<int2> ri = restrict_items(sd);
+        B.d_ritems.upload(ri, st);
+        B.nritems = (int)ri.size();
+    }
     B.nvec = (int)vi.size();
     B.nrow = (int)ri.size();
     B.nbox = (int)bi.size();
@@ -1103,6 +1142,7 @@ void build_batch(Batch& B, cudaStream_t st) {
     ck(cudaMallocHost((void**)&B.pinned, sizeof(int) * C_NCTL * std::max<size_t>(1, B.hs.size())));
     // kernel variants shared by the whole batch
     B.prec = B.hs.empty() ? 0 : B.hs[0]->prec;
+    B.lump32 = !B.hs.empty() && B.hs[0]->lump32;
     int all_bytes = 0, lump_bytes = 0;
     bool all_ok = !B.hs.empty();
     for (asm_ctx* h : B.hs) {
@@ -1115,13 +1155,15 @@ void build_batch(Batch& B, cudaStream_t st) {
     B.lump_bytes = lump_bytes;
     B.slots = 4;
     B.chunk = kStreamChunkMin;
+    B.win = 0;
     for (asm_ctx* h : B.hs) {
         B.slots = std::min(B.slots, h->apply_slots);
         B.chunk = std::max(B.chunk, h->chunk_cap);
+        B.win = std::max(B.win, h->win_rows);
     }
     if (!B.hs.empty())
         B.apply = apply_local_vectors(B.nsub, all_bytes, lump_bytes, B.slots, B.chunk, B.hs[0]->sm_smem,
-                                      B.hs[0]->n_sms, B.hs[0]->apply_place);
+                                      B.hs[0]->n_sms, B.hs[0]->apply_place, B.win);
 }
 
 // events bracketing the launch groups of one step: [prep | apply | post | spmv | mgs+finish]
@@ -1148,13 +1190,17 @@ std::vector<ApplyConfig> apply_candidates(const Batch& B) {
     if (h->apply_place != 0) return {B.apply};
     for (int force : {Y_SMEM + 1, Y_LUMPS + 1, Y_DEVICE + 1}) {
         const ApplyConfig a =
-            apply_local_vectors(B.nsub, B.all_bytes, B.lump_bytes, B.slots, B.chunk, h->sm_smem, h->n_sms, force);
+            apply_local_vectors(B.nsub, B.all_bytes, B.lump_bytes, B.slots, B.chunk, h->sm_smem, h->n_sms, force, B.win);
         if (a.ymode == force - 1) c.push_back(a);
     }
     return c;
 }
 
-// the local solves of one apply: fused ILU sweeps, or R_i r and the owned rows of A_i^{-1} R_i r
+// kernels launched by launch_local_solves
+int local_solve_launches(const Batch& B) { return B.nf ? 1 : 2; }
+
+// the local solves of one apply: R_i r and the fused ILU sweeps, or R_i r and the owned rows of
+// A_i^{-1} R_i r, or the nested-factorisation sweeps
 void launch_local_solves(Batch& B, const SysTab* tab, cudaStream_t st) {
     if (B.nf) {
         launch_nf_apply(tab, B.d_nf.as<NFDesc>(), B.nnf, B.prec, B.nf_slots, B.nf_smem, st);
@@ -1162,7 +1208,8 @@ void launch_local_solves(Batch& B, const SysTab* tab, cudaStream_t st) {
         launch_dense_restrict(tab, B.d_sub.as<SubDesc>(), B.nsub, st);
         launch_dense_apply(tab, B.d_sub.as<SubDesc>(), B.d_dense.as<int2>(), B.ndense, st);
     } else {
-        launch_apply(tab, B.d_sub.as<SubDesc>(), B.nsub, B.prec, B.apply, st);
+        launch_restrict(tab, B.d_sub.as<SubDesc>(), B.d_ritems.as<int2>(), B.nritems, B.prec, B.lump32, st);
+        launch_apply(tab, B.d_sub.as<SubDesc>(), B.nsub, B.prec, B.lump32, B.apply, st);
     }
 }
 
@@ -1182,7 +1229,7 @@ void launch_step(Batch& B, int kmax, cudaStream_t st, StepEvents* ev) {
     if (ev) ck(cudaEventRecord(ev->e[3], st));
     launch_spmv(tab, B.d_row.as<RowItem>(), B.nrow, st);
     if (ev) ck(cudaEventRecord(ev->e[4], st));
-    long long n = 5;
+    long long n = 4 + local_solve_launches(B);
     if (B.coop_grid > 0) {
         ck(launch_ortho_coop(tab, B.hs[0]->d_partial.as<double>(), B.coop_grid, st));
         n += 1;
@@ -1218,7 +1265,7 @@ void launch_step_om(Batch& B, int kmax, cudaStream_t st, StepEvents* ev) {
     launch_om_update(tab, vi, B.nvec, st);
     if (ev) ck(cudaEventRecord(ev->e[5], st));
     ck(cudaGetLastError());
-    for (asm_ctx* h : B.hs) h->prof.kernel_launches += 4 + kmax + 1;
+    for (asm_ctx* h : B.hs) h->prof.kernel_launches += 3 + local_solve_launches(B) + kmax + 1;
 }
 
 float elapsed(cudaEvent_t a, cudaEvent_t b) {
@@ -1460,7 +1507,7 @@ size_t ctx_device_bytes(const asm_ctx* h) {
                           &h->d_scal, &h->d_ctl, &h->d_partial, &h->d_tab1, &h->d_vec1, &h->d_row1, &h->d_box1,
                           // exact local solves, nested factorisation, classical coarse correction
                           &h->d_daug, &h->d_dprow, &h->d_dfcol, &h->d_dmats, &h->d_dinit, &h->d_doff,
-                          &h->d_dmat_of_slot, &h->d_dpart, &h->d_derr, &h->d_ditems1, &h->d_nfint, &h->d_nfval,
+                          &h->d_dmat_of_slot, &h->d_dpart, &h->d_derr, &h->d_ditems1, &h->d_ritems1, &h->d_nfint, &h->d_nfval,
                           &h->d_nfdesc1, &h->d_nfpack, &h->d_nfy, &h->d_nfband, &h->d_cbox, &h->d_ccells, &h->d_ckptr,
                           &h->d_ckloc, &h->d_ckeys, &h->d_cblk, &h->d_caug, &h->d_cprow, &h->d_cfcol, &h->d_cpart,
                           &h->d_cerr, &h->d_crc, &h->d_cyc, &h->d_cw, &h->d_cbox_items1, &h->d_cgrow1, &h->d_cmat};
@@ -1557,7 +1604,7 @@ void sym_worker(asm_server* S) {
                 }
                 g.far_mode = q.far_mode;
                 e.sym = std::make_shared<SysSym>();
-                e.err = build_symbolic(g, e.pat, S->opt.precision, 1, *e.sym, 0);
+                e.err = build_symbolic(g, e.pat, S->opt.precision, S->opt.lump_precision == ASM_LUMP_FP32 ? 1 : 0, 1, *e.sym, 0);
             }
         } catch (const std::exception& ex) {
             e.sym.reset();
@@ -1600,6 +1647,7 @@ int build_ctx(asm_server* S, Req* r, const SymEntry& e, asm_ctx** out) {
     o.precision = S->opt.precision;
     o.restart = S->opt.restart;
     o.device = S->opt.device;
+    o.lump_precision = S->opt.lump_precision;
     asm_ctx* h = nullptr;
     int st = asm_create(&h, &o, S->stream);
     if (st) return st;
@@ -1755,6 +1803,7 @@ void asm_default_options(asm_options* opt) {
     opt->local_solver = ASM_LOCAL_BILU0_COLSUM;
     opt->flexible = -1;
     opt->device = 0;
+    opt->lump_precision = ASM_LUMP_FP64;
 }
 
 const char* asm_error_string(int s) {
@@ -1779,7 +1828,8 @@ int asm_create(asm_handle* out, const asm_options* opt, void* cuda_stream) {
     asm_default_options(&o);
     if (opt) o = *opt;
     if (o.precision < 0 || o.precision > 2 || o.krylov < 0 || o.krylov > 1 || o.restart < 1 || o.restart > 512 ||
-        o.local_solver < 0 || o.local_solver > 4 || o.flexible < -1 || o.flexible > 1 ||
+        o.local_solver < 0 || o.local_solver > 4 || o.flexible < -1 || o.flexible > 1 || o.lump_precision < 0 ||
+        o.lump_precision > 1 ||
         (o.local_solver == ASM_LOCAL_EXACT && o.precision != ASM_PREC_FP64) ||
         (o.local_solver >= ASM_LOCAL_NF_COLSUM && o.precision == ASM_PREC_FP16S))
         return ASM_ERR_INVALID_ARG;
@@ -1795,6 +1845,7 @@ int asm_create(asm_handle* out, const asm_options* opt, void* cuda_stream) {
     h->device = o.device;
     h->stream = static_cast<cudaStream_t>(cuda_stream);
     h->prec = o.precision;
+    h->lump32 = o.precision != ASM_PREC_FP64 && o.lump_precision == ASM_LUMP_FP32;
     h->flexible = o.flexible >= 0 ? o.flexible : (o.precision == ASM_PREC_FP64 ? 0 : 1);
     // loads the no-allocation residual's module and kernel now, so that its calls allocate nothing
     int st = guard(h, [&] { return asm2::noalloc_prepare(h->device); });
@@ -1927,7 +1978,8 @@ int asm_factor(asm_handle h) {
         if (!h->sym_valid) {
             auto t0 = std::chrono::steady_clock::now();
             h->sym = std::make_shared<SysSym>();
-            std::string e = build_symbolic(h->geom, h->pat, h->prec, h->opt.local_solver == ASM_LOCAL_BILU0_COLSUM ? 1 : 0,
+            std::string e = build_symbolic(h->geom, h->pat, h->prec, h->lump32 ? 1 : 0,
+                                           h->opt.local_solver == ASM_LOCAL_BILU0_COLSUM ? 1 : 0,
                                            *h->sym, 0);
             if (!e.empty()) {
                 h->last_error = e;
@@ -1965,9 +2017,11 @@ int asm_apply_precond(asm_handle h, const double* r, double* z, int on_device) {
                                h->n_ditems1, h->stream);
         } else {
             const int nsub = (int)h->sub_desc.size();
-            launch_apply(h->d_tab1.as<SysTab>(), h->d_subdesc_single.as<SubDesc>(), nsub, h->prec,
+            launch_restrict(h->d_tab1.as<SysTab>(), h->d_subdesc_single.as<SubDesc>(), h->d_ritems1.as<int2>(),
+                            h->n_ritems1, h->prec, h->lump32, h->stream);
+            launch_apply(h->d_tab1.as<SysTab>(), h->d_subdesc_single.as<SubDesc>(), nsub, h->prec, h->lump32,
                          apply_local_vectors(nsub, h->apply_smem, h->apply_lump_smem, h->apply_slots, h->chunk_cap,
-                                             h->sm_smem, h->n_sms, h->apply_place),
+                                             h->sm_smem, h->n_sms, h->apply_place, h->win_rows),
                          h->stream);
         }
         if (h->tab.cmode != 0)
@@ -1976,7 +2030,7 @@ int asm_apply_precond(asm_handle h, const double* r, double* z, int on_device) {
                                 (int)h->cgrow_items.size(), h->d_vec1.as<VecItem>(), h->n_vec1, h->tab.cmode == 2,
                                 h->stream);
         ck(cudaGetLastError());
-        h->prof.kernel_launches += 2;
+        h->prof.kernel_launches += is_nf(h) ? 2 : 3;
         copy_out(h, z, out, bytes, on_device);
         sync(h);
         return take_dev_err(h) ? ASM_ERR_TIMEOUT : ASM_OK;
@@ -2032,6 +2086,7 @@ int asm_solve_batch(asm_handle* hs, int n, const double* const* b, double* const
         if (!h) return ASM_ERR_INVALID_ARG;
         if (!h->factored) return ASM_ERR_STATE;
         if (h->device != v[0]->device || h->stream != v[0]->stream || h->prec != v[0]->prec ||
+            h->lump32 != v[0]->lump32 ||
             h->opt.krylov != v[0]->opt.krylov ||
             (h->opt.local_solver == ASM_LOCAL_EXACT) != (v[0]->opt.local_solver == ASM_LOCAL_EXACT) ||
             is_nf(h) != is_nf(v[0]))
@@ -2062,11 +2117,11 @@ int asm_get_stats(asm_handle h, asm_stats* st) {
         }
         st->factor_bytes = fb;
         st->apply_index_bytes = ib;
-        const long long wf = S.prec == 0 ? 8 : (S.prec == 1 ? 4 : 2);
+        const long long wf = S.prec == 0 ? 8 : (S.prec == 1 ? 4 : 2), wl = S.lump32 ? 4 : 8;
         long long ab = 48LL * h->N;
         for (const SubSym& o : S.subs)
             for (int p = 0; p < o.n; p++) {
-                const long long w = p < o.nf ? wf : 8;
+                const long long w = p < o.nf ? wf : wl;
                 const long long ne = o.prp[p + 1] - o.prp[p] - 1;
                 ab += ne * (9 * w + 4) + 9 * w;
             }
@@ -2227,6 +2282,7 @@ void asm_server_default_options(asm_server_options* o) {
     o->max_active = 64;
     o->max_cached = 16;
     o->hbm_budget = 0;
+    o->lump_precision = ASM_LUMP_FP64;
 }
 
 int asm_server_create(asm_server_handle* out, const asm_server_options* opt, void* cuda_stream) {
@@ -2236,7 +2292,7 @@ int asm_server_create(asm_server_handle* out, const asm_server_options* opt, voi
     asm_server_default_options(&o);
     if (opt) o = *opt;
     if (o.precision < 0 || o.precision > 2 || o.restart < 1 || o.restart > 512 || o.max_active < 0 || o.max_cached < 0 ||
-        o.hbm_budget < 0)
+        o.hbm_budget < 0 || o.lump_precision < 0 || o.lump_precision > 1)
         return ASM_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess) {  // no driver or no device, as in asm_create

@@ -24,16 +24,23 @@ constexpr int kLongLumpRow = 16;     // lump rows with more stored blocks are sw
 // threads and four fit, which wins once a launch has more subdomains than the shared-memory variant
 // runs at once.  The lump vector (FP64) and its FP32 mirror then stay in shared memory when four
 // CTAs' worth fit, else they go to device memory too.
-constexpr int kApplyThreadsDev = 128;
+constexpr int kApplyThreadsDev = 256;
 enum ApplyY { Y_SMEM = 0, Y_LUMPS = 1, Y_DEVICE = 2 };  // where the apply's local vectors live
 struct ApplyConfig {
     int ymode;  // ApplyY
     int smem;   // dynamic shared memory of the vectors (bytes)
     int slots;  // factor-stream ring slots (2 for the 128-thread variants: deeper rings gain nothing)
     int chunk;  // bytes of one ring slot: the largest chunk capacity of the launch's subdomains
+    int win;    // rows of each of the two shared-memory buffers that hold the last two fine wavefront
+                // levels (FP32 lump rows with local vectors in device memory or lumps in shared
+                // memory); 0 = none
 };
+// Largest window buffer (rows): wider levels read their rows beyond it from device memory.
+constexpr int kWinMaxRows = 512;
 // Chunk header word 6: bit 0 = last chunk of its wavefront level; bits 8..11 = log2 of the entry
-// slots S of the short lump rows (each such row takes 3 S lanes: 3 output components x S slots).
+// slots S of the short lump rows (each such row takes 3 S lanes: 3 output components x S slots);
+// kChunkLongLumps = the chunk holds a lump row of more than kLongLumpRow blocks.
+constexpr int kChunkLongLumps = 1 << 12;
 constexpr int VEC_THREADS = 256;
 enum VecSlot { VX = 0, VB = 1, VR = 2, VW = 3, VZ = 4, VU = 5, VV0 = 6 };  // V_k = VV0 + k; Z_k after V
 
@@ -167,7 +174,10 @@ struct SubDesc {
     const double* dinv;          // exact local solves: [A_i | A_i^{-1}] (3n x 6n), fine then lump order
     const int2* chunks;          // (byte offset, bytes) of every chunk, consumption order
     const unsigned char* stream; // 16-byte aligned
-    double* y;        // global scratch for the local vectors when they do not fit in shared memory
+    double* y;        // the local vectors in device memory (written by k_restrict, 16-byte aligned)
+    int y_fine;       // byte offsets within y: fine rows, and the FP32 mirror of FP64 lumps; lumps at 0
+    int y_mirror;
+    int y_bytes;      // bytes of all local vectors (the shared-memory copy of Y_SMEM)
     const int* fcell; // [nf] cell of each fine row
     const int* rptr;  // [nc + 1] cells summed into each near lump (far lumps: empty)
     const int* rsrc;
@@ -242,10 +252,31 @@ void launch_ell_fill(const double* bsr_vals, const int* row_ptr, int n, int ell_
 void launch_boxsum(const SysTab* st_tab, const BoxItem* items, int nitems, cudaStream_t st);
 // ysmem: shared memory for the local vectors (0 = they stay in the global scratch SubDesc.y);
 // the ring of factor-stream slots is added on top
-void launch_apply(const SysTab* st_tab, const SubDesc* subs, int nsub, int prec, ApplyConfig cfg, cudaStream_t st);
+void launch_apply(const SysTab* st_tab, const SubDesc* subs, int nsub, int prec, bool lump32, ApplyConfig cfg,
+                  cudaStream_t st);
+// R_i r of every subdomain into its device-memory local vectors (items: subdomain, first local row
+// of 256; fine rows first, then lump rows)
+void launch_restrict(const SysTab* tab, const SubDesc* subs, const int2* items, int nitems, int prec, bool lump32,
+                     cudaStream_t st);
 // shared memory the local vectors of a subdomain need (nf fine rows, nc lump rows), and the ring
-size_t apply_smem_bytes(int nf, int nc, int prec);  // all local vectors of one subdomain
-size_t apply_lump_bytes(int nc, int prec);          // its lump vector and the FP32 mirror
+// Layout of one subdomain's apply local vectors (the same in device and in shared memory): lumps at
+// byte 0 (FP64, or FP32 with lump32), fine rows at `fine` (FP64 with FP64 factors, else FP32), and
+// the FP32 mirror of FP64 lumps under FP32/FP16 fine rows at `mirror`; every part 16-byte aligned.
+// With FP32 lumps every row (fine or lump) is four floats, 16 bytes.
+// The lumps-in-shared-memory placement keeps lumps and mirror as [lumps | mirror] (mirror at `fine`).
+struct YLayout {
+    size_t fine, mirror, total, lump_part;
+};
+inline YLayout y_layout(int nf, int nc, int prec, bool lump32) {
+    const auto a16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    if (prec != 0 && lump32) return YLayout{16 * (size_t)nc, 16 * (size_t)(nc + nf), 16 * (size_t)(nc + nf), 16 * (size_t)nc};
+    const size_t tl = 8, tc = prec == 0 ? 8 : 4;
+    const size_t yc = a16(3 * tl * (size_t)nc), yf = a16(3 * tc * (size_t)nf);
+    const size_t ycf = prec != 0 && !lump32 ? a16(12 * (size_t)nc) : 0;
+    return YLayout{yc, yc + yf, yc + yf + ycf, yc + ycf};
+}
+size_t apply_smem_bytes(int nf, int nc, int prec, bool lump32);  // all local vectors of one subdomain
+size_t apply_lump_bytes(int nc, int prec, bool lump32);  // its lump vector (and FP32 mirror of FP64 lumps)
 // Placement of one apply launch's local vectors.  all_bytes / lump_bytes: the largest subdomain's
 // needs (0: not available); smem_slots: ring slots of the all-shared-memory variant; chunk: bytes of
 // one ring slot (the largest chunk capacity of the launch's subdomains); force: 0
@@ -253,7 +284,7 @@ size_t apply_lump_bytes(int nc, int prec);          // its lump vector and the F
 // lumps in shared memory when four CTAs fit, else device memory), Y_SMEM + 1 / Y_LUMPS + 1 /
 // Y_DEVICE + 1 to ask for one placement (taken when it fits).
 ApplyConfig apply_local_vectors(int nsub, int all_bytes, int lump_bytes, int smem_slots, int chunk, int sm_smem,
-                                int sms, int force);
+                                int sms, int force, int win);
 size_t apply_ring_bytes(int slots, int chunk);
 void launch_spmv(const SysTab* st_tab, const RowItem* items, int nitems, cudaStream_t st);
 

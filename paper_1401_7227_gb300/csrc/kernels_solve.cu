@@ -44,6 +44,40 @@ struct FineBlock<double> {
     static constexpr int bytes = 72;
 };
 
+// a -= V x for one stored 3x3 block V (row-major) and a 3-vector x, as negated fused multiply-adds.
+// FP32 blocks: 9 loads.  FP16 blocks (9 halves scaled by 2^-e, then e): 5 32-bit loads, the product
+// of the unscaled block, then one multiply-add by 2^e per component (a power of two: exact).
+template <typename TF>
+__device__ __forceinline__ void block_mv_sub(const unsigned char* p, float x0, float x1, float x2, float& a0, float& a1,
+                                             float& a2);
+template <>
+__device__ __forceinline__ void block_mv_sub<float>(const unsigned char* p, float x0, float x1, float x2, float& a0,
+                                                    float& a1, float& a2) {
+    const float* v = reinterpret_cast<const float*>(p);
+    a0 = fmaf(-v[0], x0, fmaf(-v[1], x1, fmaf(-v[2], x2, a0)));
+    a1 = fmaf(-v[3], x0, fmaf(-v[4], x1, fmaf(-v[5], x2, a1)));
+    a2 = fmaf(-v[6], x0, fmaf(-v[7], x1, fmaf(-v[8], x2, a2)));
+}
+template <>
+__device__ __forceinline__ void block_mv_sub<__half>(const unsigned char* p, float x0, float x1, float x2, float& a0,
+                                                     float& a1, float& a2) {
+    const unsigned* w = reinterpret_cast<const unsigned*>(p);
+    const unsigned w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3], w4 = w[4];
+    const float2 v01 = __half22float2(*reinterpret_cast<const __half2*>(&w0));
+    const float2 v23 = __half22float2(*reinterpret_cast<const __half2*>(&w1));
+    const float2 v45 = __half22float2(*reinterpret_cast<const __half2*>(&w2));
+    const float2 v67 = __half22float2(*reinterpret_cast<const __half2*>(&w3));
+    const float v8 = __half2float(__ushort_as_half((unsigned short)(w4 & 0xffffu)));
+    const int ex = (int)(short)(w4 >> 16);
+    const float sc = __int_as_float((127 + ex) << 23);  // 2^ex: |ex| is far below 126 for these factors
+    const float t0 = fmaf(v01.x, x0, fmaf(v01.y, x1, v23.x * x2));
+    const float t1 = fmaf(v23.y, x0, fmaf(v45.x, x1, v45.y * x2));
+    const float t2 = fmaf(v67.x, x0, fmaf(v67.y, x1, v8 * x2));
+    a0 = fmaf(-sc, t0, a0);
+    a1 = fmaf(-sc, t1, a1);
+    a2 = fmaf(-sc, t2, a2);
+}
+
 // ------------------------------------------------------------------------------------------
 // gather sums of the apply input: far-box sums (kind 0) and, per subdomain, the sums of the
 // near-region cells of each far box (kind 1); a far lump's restricted residual is their difference
@@ -125,15 +159,30 @@ using tma::mbar_wait;
 constexpr int kMaxSlots = 4;  // ring slots of the apply: a template argument, 2..kMaxSlots
 constexpr int kRingHeader = 64;  // mbarriers
 
-// One chunk of the forward (lower = true) or backward sweep, read from shared memory.
-template <typename TF>
+// The last two fine wavefront levels' results in shared memory, for sweeps whose local vectors live
+// in device memory: a fine row's fine neighbours sit in the level just before its own (hyperplanes
+// of the box), so they are read from here instead of from stores that may still be on their way
+// to L2.  prev holds rows [prev_lo, prev_hi) at prev[f - prev_lo], cur receives the current level's
+// rows at cur[f - cur_lo]; rows at or beyond cap positions, and every other row, use the device
+// copy (which is always written).  cur == nullptr: no window.
+struct Win {
+    float4* cur;
+    const float4* prev;
+    int cur_lo, prev_lo, prev_hi, cap;
+};
+
+// One chunk of the forward (lower = true) or backward sweep, read from shared memory.  TL is the
+// lump rows' storage and arithmetic type (double, or float with FP32/FP16 fine rows); ycf is the
+// FP32 mirror of FP64 lump values that FP32 fine rows read (nullptr otherwise).
+template <typename TF, typename TL>
 __device__ __forceinline__ void sweep_chunk(const unsigned char* base, bool lower, typename Compute<TF>::T* yf,
-                                            double* yc, typename Compute<TF>::T* ycf) {
+                                            TL* yc, typename Compute<TF>::T* ycf, const Win& w) {
     using TC = typename Compute<TF>::T;
     constexpr int FB = FineBlock<TF>::bytes;
-    const int* hdr = reinterpret_cast<const int*>(base);
-    const int f0 = hdr[0], nf = hdr[1], c0 = hdr[2], nc = hdr[3], ef = hdr[4], ec = hdr[5];
-    const int lump_lg = (hdr[6] >> 8) & 15;
+    const int4 h0 = reinterpret_cast<const int4*>(base)[0], h1 = reinterpret_cast<const int4*>(base)[1];
+    const int f0 = h0.x, nf = h0.y, c0 = h0.z, nc = h0.w, ef = h1.x, ec = h1.y;
+    const int lump_lg = (h1.z >> 8) & 15;
+    const bool has_long = (h1.z & kChunkLongLumps) != 0;
     const unsigned char* p = base + 32;
     const int* fptr = reinterpret_cast<const int*>(p);
     p += align16(4 * (size_t)(nf + 1));
@@ -147,10 +196,126 @@ __device__ __forceinline__ void sweep_chunk(const unsigned char* base, bool lowe
     p += align16(4 * (size_t)(nc + 1));
     const int* ccol = reinterpret_cast<const int*>(p);
     p += align16(4 * (size_t)ec);
-    const double* cval = reinterpret_cast<const double*>(p);
-    p += align16(72 * (size_t)ec);
-    const double* cdi = reinterpret_cast<const double*>(p);
+    const TL* cval = reinterpret_cast<const TL*>(p);
+    p += align16(9 * sizeof(TL) * (size_t)ec);
+    const TL* cdi = reinterpret_cast<const TL*>(p);
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
+    if constexpr (sizeof(TL) == 4) {
+        // FP32 lump rows (with FP32 or FP16-stored fine rows).  Both local vectors hold a row as
+        // four floats (16 bytes, the last unused), so each operand is one vector load.  Every row
+        // of the chunk, fine or lump, is one thread's, fine rows first.  A row's column indices
+        // and then the operands they point at are loaded four entries at a time before any
+        // arithmetic (a 7-point fine row has at most six entries).  Lump rows of more than
+        // kLongLumpRow entries are summed by a whole warp after the loop.
+        constexpr int kUnroll = 4;
+        float4* yf4 = reinterpret_cast<float4*>(yf);
+        float4* yc4 = reinterpret_cast<float4*>(yc);
+        const unsigned wn = w.cur != nullptr ? (unsigned)min(w.prev_hi - w.prev_lo, w.cap) : 0u;  // window rows
+        for (int q = tid; q < nf + nc; q += nt) {
+            const bool fine = q < nf;
+            const int i = fine ? q : q - nf;
+            const int* ptr = fine ? fptr : cptr;
+            const int e0 = ptr[i], e1 = ptr[i + 1];
+            if (!fine && e1 - e0 > kLongLumpRow) continue;
+            const int* col = fine ? fcol : ccol;
+            float4* yo = fine ? yf4 + f0 + i : yc4 + c0 + i;
+            // the row's own entry is subtracted from at the end, so its load overlaps the products
+            const float4 own = *yo;
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f;  // - sum of the row's products
+            // straight-line batches: a padded entry (past the row's end) reloads the row's last
+            // entry and contributes zero, so no branch separates the loads of a batch
+            const unsigned char* vbase =
+                fine ? fval : reinterpret_cast<const unsigned char*>(cval);  // FP32 lumps: 36-byte blocks
+            for (int eb = e0; eb < e1; eb += kUnroll) {
+                const int last = e1 - 1;
+                int cs[kUnroll];
+#pragma unroll
+                for (int u = 0; u < kUnroll; u++) cs[u] = col[min(eb + u, last)];
+                float4 xs[kUnroll];
+#pragma unroll
+                for (int u = 0; u < kUnroll; u++) {
+                    const int c = cs[u];
+                    const unsigned wp = (unsigned)(c - w.prev_lo);
+                    const float4 x = wp < wn ? w.prev[wp] : (c >= 0 ? yf4[c] : yc4[~c]);
+                    const bool live = eb + u <= last;
+                    xs[u] = make_float4(live ? x.x : 0.f, live ? x.y : 0.f, live ? x.z : 0.f, 0.f);
+                }
+                if (sizeof(TF) == 4 || fine) {
+#pragma unroll
+                    for (int u = 0; u < kUnroll; u++)
+                        block_mv_sub<TF>(vbase + (size_t)FB * min(eb + u, last), xs[u].x, xs[u].y, xs[u].z, a0, a1, a2);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < kUnroll; u++)
+                        block_mv_sub<float>(vbase + 36 * (size_t)min(eb + u, last), xs[u].x, xs[u].y, xs[u].z, a0, a1,
+                                            a2);
+                }
+            }
+            a0 += own.x;
+            a1 += own.y;
+            a2 += own.z;
+            if (!lower) {  // z = D^{-1} a, as 0 - D^{-1} (-a)
+                float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+                if (sizeof(TF) == 4 || fine)
+                    block_mv_sub<TF>(fine ? fdi + (size_t)FB * i : reinterpret_cast<const unsigned char*>(cdi + 9 * i),
+                                     -a0, -a1, -a2, b0, b1, b2);
+                else
+                    block_mv_sub<float>(reinterpret_cast<const unsigned char*>(cdi + 9 * i), -a0, -a1, -a2, b0, b1, b2);
+                a0 = b0;
+                a1 = b1;
+                a2 = b2;
+            }
+            const float4 res = make_float4(a0, a1, a2, 0.f);
+            *yo = res;
+            if (fine && w.cur != nullptr && f0 + i - w.cur_lo < w.cap) w.cur[f0 + i - w.cur_lo] = res;
+        }
+        if (!has_long) return;
+        // long lump rows: one warp each, lane = 8 k + s computing component k over the entries
+        // s, s + 8, ..., kUnroll of them loaded at a time, combined by three shuffle adds
+        const int k = lane >> 3, sl = lane & 7;
+        const bool lane_on = lane < 24;
+        for (int i = nwarp - 1 - warp; i < nc; i += nwarp) {
+            const int e0 = cptr[i], e1 = cptr[i + 1];
+            if (e1 - e0 <= kLongLumpRow) continue;
+            float acc = 0.f;
+            if (lane_on)
+                for (int eb = e0 + sl; eb < e1; eb += 8 * kUnroll) {
+                    float4 xs[kUnroll];
+#pragma unroll
+                    for (int u = 0; u < kUnroll; u++) {
+                        xs[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (eb + 8 * u < e1) {
+                            const int c = ccol[eb + 8 * u];
+                            const unsigned wp = (unsigned)(c - w.prev_lo);
+                            xs[u] = wp < wn ? w.prev[wp] : (c >= 0 ? yf4[c] : yc4[~c]);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kUnroll; u++)
+                        if (eb + 8 * u < e1) {
+                            const float* v = cval + 9LL * (eb + 8 * u) + 3 * k;
+                            acc = fmaf(v[0], xs[u].x, fmaf(v[1], xs[u].y, fmaf(v[2], xs[u].z, acc)));
+                        }
+                }
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            float* yr = reinterpret_cast<float*>(yc4 + c0 + i);
+            float b = 0.f;
+            if (lane_on && sl == 0) b = yr[k] - acc;
+            if (lower) {
+                if (lane_on && sl == 0) yr[k] = b;
+            } else {
+                const float b0 = __shfl_sync(0xffffffffu, b, 0);
+                const float b1 = __shfl_sync(0xffffffffu, b, 8);
+                const float b2 = __shfl_sync(0xffffffffu, b, 16);
+                if (lane_on && sl == 0) {
+                    const float* d = cdi + 9LL * i + 3 * k;
+                    yr[k] = fmaf(d[0], b0, fmaf(d[1], b1, d[2] * b2));
+                }
+            }
+        }
+        return;
+    }
     if constexpr (sizeof(TC) == 8) {
         // FP64 fine rows: three lanes per row (one per output component), ten rows per warp, so that
         // each FP64 instruction carries three times the work of a thread-per-row loop
@@ -242,9 +407,9 @@ __device__ __forceinline__ void sweep_chunk(const unsigned char* base, bool lowe
         }
     }
     }
-    // Lump rows are FP64, and an FP64 warp instruction keeps an SM sub-partition's FP64 unit busy
-    // for ~64 cycles whatever the number of active lanes, so lump work is packed into as few FP64
-    // instructions as the latency allows:
+    // Lump rows (TL = double: an FP64 warp instruction keeps an SM sub-partition's FP64 unit busy
+    // for ~64 cycles whatever the number of active lanes, so lump work is packed into as few
+    // instructions as the latency allows; the same packing serves TL = float):
     //  - short rows (<= kLongLumpRow blocks): 3 S lanes per row, lane = 3 s + k computing output
     //    component k over the entries s, s + S, ..., combined by log2(S) shuffle adds; 32 / (3 S)
     //    rows per warp.  S (1, 2, 4 or 8) is chosen per chunk by the host (header word 6);
@@ -257,16 +422,16 @@ __device__ __forceinline__ void sweep_chunk(const unsigned char* base, bool lowe
         const bool lane_on = lane < 24;
         for (int i = nwarp - 1 - warp; i < nc; i += nwarp) {
             if (cptr[i + 1] - cptr[i] <= kLongRow) continue;
-            double acc = 0.0;
+            TL acc = 0;
             if (lane_on)
                 for (int e = cptr[i] + sl; e < cptr[i + 1]; e += 8) {
-                    const double* v = cval + 9LL * e + 3 * k;
+                    const TL* v = cval + 9LL * e + 3 * k;
                     const int c = ccol[e];
-                    double x0, x1, x2;
+                    TL x0, x1, x2;
                     if (c >= 0) {
-                        x0 = yf[3 * c];
-                        x1 = yf[3 * c + 1];
-                        x2 = yf[3 * c + 2];
+                        x0 = (TL)yf[3 * c];
+                        x1 = (TL)yf[3 * c + 1];
+                        x2 = (TL)yf[3 * c + 2];
                     } else {
                         x0 = yc[3 * ~c];
                         x1 = yc[3 * ~c + 1];
@@ -277,17 +442,17 @@ __device__ __forceinline__ void sweep_chunk(const unsigned char* base, bool lowe
 #pragma unroll
             for (int o = 1; o < 8; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
             const int c = c0 + i;
-            double b = 0.0;
+            TL b = 0;
             if (lane_on && sl == 0) b = yc[3 * c + k] - acc;
             if (lower) {
                 if (lane_on && sl == 0) yc[3 * c + k] = b;
             } else {
-                const double b0 = __shfl_sync(0xffffffffu, b, 0);
-                const double b1 = __shfl_sync(0xffffffffu, b, 8);
-                const double b2 = __shfl_sync(0xffffffffu, b, 16);
+                const TL b0 = __shfl_sync(0xffffffffu, b, 0);
+                const TL b1 = __shfl_sync(0xffffffffu, b, 8);
+                const TL b2 = __shfl_sync(0xffffffffu, b, 16);
                 if (lane_on && sl == 0) {
-                    const double* d = cdi + 9LL * i + 3 * k;
-                    const double t = fma(d[0], b0, fma(d[1], b1, d[2] * b2));
+                    const TL* d = cdi + 9LL * i + 3 * k;
+                    const TL t = fma(d[0], b0, fma(d[1], b1, d[2] * b2));
                     yc[3 * c + k] = t;
                     if (ycf != nullptr) ycf[3 * c + k] = (TC)t;
                 }
@@ -301,16 +466,16 @@ __device__ __forceinline__ void sweep_chunk(const unsigned char* base, bool lowe
             const int i = base + r;
             const bool on = r < rpw && i < nc && cptr[i + 1] - cptr[i] <= kLongRow;
             if (!__any_sync(0xffffffffu, on)) continue;
-            double acc = 0.0;
+            TL acc = 0;
             if (on)
                 for (int e = cptr[i] + sl; e < cptr[i + 1]; e += S) {
-                    const double* v = cval + 9LL * e + 3 * k;
+                    const TL* v = cval + 9LL * e + 3 * k;
                     const int c = ccol[e];
-                    double x0, x1, x2;
+                    TL x0, x1, x2;
                     if (c >= 0) {
-                        x0 = yf[3 * c];
-                        x1 = yf[3 * c + 1];
-                        x2 = yf[3 * c + 2];
+                        x0 = (TL)yf[3 * c];
+                        x1 = (TL)yf[3 * c + 1];
+                        x2 = (TL)yf[3 * c + 2];
                     } else {
                         x0 = yc[3 * ~c];
                         x1 = yc[3 * ~c + 1];
@@ -322,17 +487,17 @@ __device__ __forceinline__ void sweep_chunk(const unsigned char* base, bool lowe
             for (int o = 3; o < lpr; o <<= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
             const bool head = on && sl == 0;
             const int c = c0 + i;
-            const double b = head ? yc[3 * c + k] - acc : 0.0;
+            const TL b = head ? yc[3 * c + k] - acc : (TL)0;
             if (lower) {
                 if (head) yc[3 * c + k] = b;
             } else {
                 const int l0 = r * lpr;
-                const double b0 = __shfl_sync(0xffffffffu, b, l0 < 32 ? l0 : 0);
-                const double b1 = __shfl_sync(0xffffffffu, b, l0 + 1 < 32 ? l0 + 1 : 0);
-                const double b2 = __shfl_sync(0xffffffffu, b, l0 + 2 < 32 ? l0 + 2 : 0);
+                const TL b0 = __shfl_sync(0xffffffffu, b, l0 < 32 ? l0 : 0);
+                const TL b1 = __shfl_sync(0xffffffffu, b, l0 + 1 < 32 ? l0 + 1 : 0);
+                const TL b2 = __shfl_sync(0xffffffffu, b, l0 + 2 < 32 ? l0 + 2 : 0);
                 if (head) {
-                    const double* d = cdi + 9LL * i + 3 * k;
-                    const double t = fma(d[0], b0, fma(d[1], b1, d[2] * b2));
+                    const TL* d = cdi + 9LL * i + 3 * k;
+                    const TL t = fma(d[0], b0, fma(d[1], b1, d[2] * b2));
                     yc[3 * c + k] = t;
                     if (ycf != nullptr) ycf[3 * c + k] = (TC)t;
                 }
@@ -343,10 +508,10 @@ __device__ __forceinline__ void sweep_chunk(const unsigned char* base, bool lowe
 
 // R_i r (Eqs. 4.1, B.2): fine entries copied from their cells (as TC), lump entries summed over
 // the lump's cells in FP64 -- far lumps as the far box's sum minus its near-region cells, long
-// lists by a whole warp.  The caller synchronises the CTA afterwards.
-template <typename TC>
+// lists by a whole warp -- and stored as TL.  The caller synchronises the CTA afterwards.
+template <typename TC, typename TL>
 __device__ __forceinline__ void restrict_local(const SysTab& st, const SubDesc& sd, const double* __restrict__ r,
-                                               TC* yf, double* yc) {
+                                               TC* yf, TL* yc) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
     // fine cells in batches of kB rows per thread: all cell indices, then all values, are in flight
@@ -397,9 +562,9 @@ __device__ __forceinline__ void restrict_local(const SysTab& st, const SubDesc& 
             a1 += rc[1];
             a2 += rc[2];
         }
-        yc[3 * c] = a0;
-        yc[3 * c + 1] = a1;
-        yc[3 * c + 2] = a2;
+        yc[3 * c] = (TL)a0;
+        yc[3 * c + 1] = (TL)a1;
+        yc[3 * c + 2] = (TL)a2;
     }
     for (int k = warp; k < sd.n_long; k += nwarp) {
         const int c = sd.clong[k];
@@ -412,10 +577,93 @@ __device__ __forceinline__ void restrict_local(const SysTab& st, const SubDesc& 
         }
         warp_sum3(a0, a1, a2);
         if (lane == 0) {
-            yc[3 * c] = a0;
-            yc[3 * c + 1] = a1;
-            yc[3 * c + 2] = a2;
+            yc[3 * c] = (TL)a0;
+            yc[3 * c + 1] = (TL)a1;
+            yc[3 * c + 2] = (TL)a2;
         }
+    }
+}
+
+// R_i r (Eqs. 4.1, B.2) of every subdomain into its device-memory local vectors, in the layout of
+// y_layout(): a fine row copies its cell's entries (rounded to the fine rows' compute type), a
+// lump row sums its cells in FP64 -- a far lump as the far box's sum minus its near-region cells
+// -- and is rounded to the lump type TL (with an FP32 mirror of FP64 lumps under FP32 fine rows;
+// with FP32 lumps every row is four floats, the last zero).
+// One thread per local row; items are (subdomain, first row of 256).
+template <typename TC, typename TL>
+__global__ void __launch_bounds__(256) k_restrict(const SysTab* __restrict__ tab, const SubDesc* __restrict__ subs,
+                                                  const int2* __restrict__ items) {
+    const int2 it = items[blockIdx.x];
+    const SubDesc& sd = subs[it.x];
+    const SysTab& st = tab[sd.sys];
+    const int in = st.ctl[C_APPLY_IN];
+    if (in < 0) return;
+    const double* __restrict__ r = st.ws + (long long)in * st.n3p;
+    unsigned char* y = reinterpret_cast<unsigned char*>(sd.y);
+    const int q = it.y + threadIdx.x;
+    constexpr bool kRow16 = sizeof(TL) == 4;  // FP32 lumps: rows of four floats (16 bytes)
+    if (q < sd.nf) {
+        const double* rc = r + 3LL * sd.fcell[q];
+        if constexpr (kRow16) {
+            reinterpret_cast<float4*>(y + sd.y_fine)[q] = make_float4((float)rc[0], (float)rc[1], (float)rc[2], 0.f);
+        } else {
+            TC* yf = reinterpret_cast<TC*>(y + sd.y_fine) + 3 * q;
+            yf[0] = (TC)rc[0];
+            yf[1] = (TC)rc[1];
+            yf[2] = (TC)rc[2];
+        }
+        return;
+    }
+    const int c = q - sd.nf;
+    if (c >= sd.nc) return;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    const int b = sd.rbox[c];
+    if (b >= 0) {
+        a0 = st.boxsum[3 * b];
+        a1 = st.boxsum[3 * b + 1];
+        a2 = st.boxsum[3 * b + 2];
+        const int k = sd.rcorr[c];
+        if (k >= 0) {
+            const double* qc = st.corr + 3LL * (sd.corr0 + k);
+            a0 -= qc[0];
+            a1 -= qc[1];
+            a2 -= qc[2];
+        }
+    }
+    const int i0 = sd.rptr[c], i1 = sd.rptr[c + 1];
+    for (int i = i0; i < i1; i += 4) {
+        int cell[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) cell[u] = i + u < i1 ? sd.rsrc[i + u] : -1;
+        double v[4][3];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const double* rc = r + 3LL * (cell[u] >= 0 ? cell[u] : 0);
+            v[u][0] = rc[0];
+            v[u][1] = rc[1];
+            v[u][2] = rc[2];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            if (cell[u] >= 0) {
+                a0 += v[u][0];
+                a1 += v[u][1];
+                a2 += v[u][2];
+            }
+    }
+    if constexpr (kRow16) {
+        reinterpret_cast<float4*>(y)[c] = make_float4((float)a0, (float)a1, (float)a2, 0.f);
+        return;
+    }
+    TL* yc = reinterpret_cast<TL*>(y) + 3 * c;
+    yc[0] = (TL)a0;
+    yc[1] = (TL)a1;
+    yc[2] = (TL)a2;
+    if constexpr (sizeof(TL) == 8 && sizeof(TC) == 4) {
+        TC* ycf = reinterpret_cast<TC*>(y + sd.y_mirror) + 3 * c;
+        ycf[0] = (TC)a0;
+        ycf[1] = (TC)a1;
+        ycf[2] = (TC)a2;
     }
 }
 
@@ -424,10 +672,11 @@ __device__ __forceinline__ void restrict_local(const SysTab& st, const SubDesc& 
 // (front to back) into a ring of shared-memory slots with TMA bulk copies; all threads compute
 // from shared memory, one chunk at a time, with a CTA barrier after each chunk (which also orders
 // the wavefront levels).  Fine rows and lump rows live in separate local vectors (fine rows at the
-// factor precision, lumps in FP64), in shared memory when they fit.
-template <typename TF, int YM, int SLOTS>
+// factor precision, lumps as TL: FP64, or FP32 with FP32/FP16 fine rows), in shared memory when
+// they fit.
+template <typename TF, typename TL, int YM, int SLOTS>
 __global__ void __launch_bounds__(YM == Y_SMEM ? 256 : kApplyThreadsDev, YM == Y_SMEM ? 2 : 4)
-    k_apply(const SysTab* __restrict__ tab, const SubDesc* __restrict__ subs) {
+    k_apply(const SysTab* __restrict__ tab, const SubDesc* __restrict__ subs, int win) {
     using TC = typename Compute<TF>::T;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const SubDesc sd = subs[blockIdx.x];
@@ -435,19 +684,25 @@ __global__ void __launch_bounds__(YM == Y_SMEM ? 256 : kApplyThreadsDev, YM == Y
     const int in = st.ctl[C_APPLY_IN];
     if (in < 0) return;
     const int out = st.ctl[C_APPLY_OUT];
-    const double* __restrict__ r = st.ws + (long long)in * st.n3p;
+    (void)in;
     double* __restrict__ z = st.ws + (long long)out * st.n3p;
     unsigned char* ring = smem_raw;
     const int cap = sd.chunk_cap, ring_bytes = SLOTS * cap;  // this subdomain's ring slots
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + ring_bytes);
-    // local vectors: lumps (FP64), fine rows (factor precision), FP32 mirror of the lumps; laid out
-    // [yc | yf | ycf] in shared or device memory, or [yc | ycf] in shared memory with yf in device
-    // memory (Y_LUMPS; the device slice keeps the same offsets)
-    double* ysm = reinterpret_cast<double*>(smem_raw + ring_bytes + kRingHeader);
-    double* yc = YM == Y_DEVICE ? sd.y : ysm;
-    TC* yf = YM == Y_LUMPS ? reinterpret_cast<TC*>(sd.y + 3 * sd.nc) : reinterpret_cast<TC*>(yc + 3 * sd.nc);
-    TC* ycf = sizeof(TC) == 8 ? nullptr
-                              : (YM == Y_LUMPS ? reinterpret_cast<TC*>(yc + 3 * sd.nc) : yf + 3 * sd.nf);
+    // local vectors (written by k_restrict in device memory): lumps (TL), fine rows (factor
+    // precision) and, for FP64 lumps under FP32 fine rows, an FP32 mirror of the lumps, in the
+    // layout of y_layout(); Y_SMEM copies all of them into shared memory, Y_LUMPS the lumps and the
+    // mirror (as [lumps | mirror]), Y_DEVICE none
+    constexpr bool kMirror = sizeof(TL) == 8 && sizeof(TC) == 4;
+    // the fine-level window (two buffers of win rows) sits between the ring and the vectors
+    constexpr bool kWin = sizeof(TL) == 4 && YM != Y_SMEM;
+    float4* wbuf = reinterpret_cast<float4*>(smem_raw + ring_bytes + kRingHeader);
+    unsigned char* ysm = smem_raw + ring_bytes + kRingHeader + (kWin ? 32 * win : 0);
+    unsigned char* ydev = reinterpret_cast<unsigned char*>(sd.y);
+    unsigned char* yc_raw = YM == Y_DEVICE ? ydev : ysm;
+    TL* yc = reinterpret_cast<TL*>(yc_raw);
+    TC* yf = reinterpret_cast<TC*>((YM == Y_LUMPS ? ydev : yc_raw) + sd.y_fine);
+    TC* ycf = !kMirror ? nullptr : reinterpret_cast<TC*>(yc_raw + (YM == Y_LUMPS ? sd.y_fine : sd.y_mirror));
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
 
@@ -463,17 +718,33 @@ __global__ void __launch_bounds__(YM == Y_SMEM ? 256 : kApplyThreadsDev, YM == Y
             bulk_load(ring + (size_t)k * cap, sd.stream + ch.x, (unsigned)ch.y, &bar[k]);
         }
 
-    // restriction R_i r (overlaps the first chunk copies)
-    restrict_local<TC>(st, sd, r, yf, yc);
+    // the local vectors k_restrict wrote (overlaps the first chunk copies)
+    if constexpr (YM != Y_DEVICE) {
+        const int4* src = reinterpret_cast<const int4*>(ydev);
+        int4* dst = reinterpret_cast<int4*>(ysm);
+        const int n16 = (YM == Y_SMEM ? sd.y_bytes : sd.y_fine) >> 4;
+        for (int i = tid; i < n16; i += nt) dst[i] = src[i];
+        if (YM == Y_LUMPS && kMirror) {
+            const int m16 = (sd.y_bytes - sd.y_mirror) >> 4;
+            const int4* msrc = reinterpret_cast<const int4*>(ydev + sd.y_mirror);
+            for (int i = tid; i < m16; i += nt) dst[n16 + i] = msrc[i];
+        }
+    }
     __syncthreads();
 
     // The copy that refills a slot is issued by lane 0 of a warp without rows in the chunk just
     // finished (fine rows fill warps from the first, lump rows from the last), so the next chunk's
     // rows are not held up behind it.  Both candidate issuers keep the next chunk's descriptor,
     // loaded one chunk ahead.
-    const bool issuer_fine = lane == 0 && warp == nwarp - 1, issuer_lump = tid == 0;
+    // (With FP32 lump rows every row is one thread's, fine rows from thread 0 up and lump rows
+    // after them, so the last warp issues every refill.)
+    const bool issuer_fine = lane == 0 && warp == nwarp - 1,
+               issuer_lump = sizeof(TL) == 4 ? issuer_fine : tid == 0;
     int2 next_ch = make_int2(0, 0);
     if ((issuer_fine || issuer_lump) && SLOTS < sd.n_chunks) next_ch = sd.chunks[SLOTS];
+    // fine wavefront levels seen so far: the current one [cur_lo, cur_hi) and the one before
+    int cur_lo = 0, cur_hi = 0, prev_lo = 0, prev_hi = 0, par = 0;
+    bool level_start = true;
     for (int ci = 0; ci < sd.n_chunks; ci++) {
         const int slot = ci % SLOTS;
         // warp-uniform, so that the warp-collective code of the sweep runs on whole warps
@@ -481,8 +752,20 @@ __global__ void __launch_bounds__(YM == Y_SMEM ? 256 : kApplyThreadsDev, YM == Y
         bool fine_chunk = false;
         if (ok) {
             const unsigned char* chunk = ring + (size_t)slot * cap;
-            fine_chunk = reinterpret_cast<const int*>(chunk)[1] > 0;
-            sweep_chunk<TF>(chunk, ci < sd.n_fwd, yf, yc, ycf);
+            const int* hdr = reinterpret_cast<const int*>(chunk);
+            const int hf0 = hdr[0], hnf = hdr[1], hflags = hdr[6];
+            fine_chunk = hnf > 0;
+            if (level_start && hnf > 0) {  // a new fine level: the current one becomes the previous
+                prev_lo = cur_lo;
+                prev_hi = cur_hi;
+                cur_lo = cur_hi = hf0;
+                par ^= 1;
+            }
+            if (hnf > 0) cur_hi = max(cur_hi, hf0 + hnf);
+            level_start = (hflags & 1) != 0;
+            const Win w{kWin && win > 0 ? wbuf + par * win : nullptr, wbuf + (par ^ 1) * win, cur_lo, prev_lo, prev_hi,
+                        win};
+            sweep_chunk<TF, TL>(chunk, ci < sd.n_fwd, yf, yc, ycf, w);
         }
         if (__syncthreads_or(!ok)) {
             // a copy did not land in time: report it, wait (bounded) for the copies still in
@@ -504,12 +787,13 @@ __global__ void __launch_bounds__(YM == Y_SMEM ? 256 : kApplyThreadsDev, YM == Y
     }
 
     // P_i R_i^T: owned cells take this subdomain's solution; the lumps are discarded
+    constexpr int RS = sizeof(TL) == 4 ? 4 : 3;  // floats per fine row (FP32 lumps: 16-byte rows)
     for (int t = tid; t < sd.n_own; t += nt) {
         const int f = sd.own_pos[t];
         const long long c = 3LL * sd.own_cell[t];
-        z[c] = yf[3 * f];
-        z[c + 1] = yf[3 * f + 1];
-        z[c + 2] = yf[3 * f + 2];
+        z[c] = yf[RS * f];
+        z[c + 1] = yf[RS * f + 1];
+        z[c + 2] = yf[RS * f + 2];
     }
 }
 
@@ -520,7 +804,7 @@ __global__ void __launch_bounds__(256) k_dense_restrict(const SysTab* __restrict
     const SysTab& st = tab[sd.sys];
     const int in = st.ctl[C_APPLY_IN];
     if (in < 0) return;
-    restrict_local<double>(st, sd, st.ws + (long long)in * st.n3p, sd.y, sd.y + 3 * sd.nf);
+    restrict_local<double, double>(st, sd, st.ws + (long long)in * st.n3p, sd.y, sd.y + 3 * sd.nf);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1172,22 +1456,20 @@ void launch_boxsum(const SysTab* tab, const BoxItem* items, int nitems, cudaStre
     if (nitems > 0) k_sums<<<nitems, 128, 0, st>>>(tab, items);
 }
 
-size_t apply_smem_bytes(int nf, int nc, int prec) {
-    return prec == 0 ? 24 * ((size_t)nc + nf) : 24 * (size_t)nc + 12 * ((size_t)nf + nc);
-}
+size_t apply_smem_bytes(int nf, int nc, int prec, bool lump32) { return y_layout(nf, nc, prec, lump32).total; }
 
 size_t apply_ring_bytes(int slots, int chunk) { return (size_t)slots * chunk + kRingHeader; }
 
-size_t apply_lump_bytes(int nc, int prec) { return prec == 0 ? 24 * (size_t)nc : 36 * (size_t)nc; }
+size_t apply_lump_bytes(int nc, int prec, bool lump32) { return y_layout(0, nc, prec, lump32).lump_part; }
 
 ApplyConfig apply_local_vectors(int nsub, int all_bytes, int lump_bytes, int smem_slots, int chunk, int sm_smem,
-                                int sms, int force) {
+                                int sms, int force, int win) {
     const long long ring_all = (long long)apply_ring_bytes(smem_slots, chunk) + 1024,
-                    ring2 = (long long)apply_ring_bytes(2, chunk) + 1024;
+                    ring2 = (long long)apply_ring_bytes(2, chunk) + 1024 + 32LL * win;
     const long long fit_all = all_bytes > 0 ? std::min<long long>(2, sm_smem / (all_bytes + ring_all)) : 0;
     const bool lumps_fit = lump_bytes > 0 && 4 * (lump_bytes + ring2) <= sm_smem;
-    const ApplyConfig all{Y_SMEM, all_bytes, smem_slots, chunk}, lumps{Y_LUMPS, lump_bytes, 2, chunk},
-        dev{Y_DEVICE, 0, 2, chunk};
+    const ApplyConfig all{Y_SMEM, all_bytes, smem_slots, chunk, 0}, lumps{Y_LUMPS, lump_bytes, 2, chunk, win},
+        dev{Y_DEVICE, 0, 2, chunk, win};
     if (force == Y_SMEM + 1) return fit_all >= 1 ? all : dev;
     if (force == Y_LUMPS + 1) return lumps_fit ? lumps : dev;
     if (force == Y_DEVICE + 1) return dev;
@@ -1196,45 +1478,63 @@ ApplyConfig apply_local_vectors(int nsub, int all_bytes, int lump_bytes, int sme
 }
 
 namespace {
-template <typename TF, int YM, int SLOTS>
-void launch_apply_t(const SysTab* tab, const SubDesc* subs, int nsub, int smem, cudaStream_t st) {
+template <typename TF, typename TL, int YM, int SLOTS>
+void launch_apply_t(const SysTab* tab, const SubDesc* subs, int nsub, int smem, int win, cudaStream_t st) {
     static int configured = -1;
     if (configured < smem) {
-        cudaFuncSetAttribute(k_apply<TF, YM, SLOTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_apply<TF, TL, YM, SLOTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         configured = smem;
     }
-    k_apply<TF, YM, SLOTS><<<nsub, YM == Y_SMEM ? 256 : kApplyThreadsDev, smem, st>>>(tab, subs);
+    k_apply<TF, TL, YM, SLOTS><<<nsub, YM == Y_SMEM ? 256 : kApplyThreadsDev, smem, st>>>(tab, subs, win);
 }
-template <typename TF, int YM>
-void launch_apply_s(const SysTab* tab, const SubDesc* subs, int nsub, int smem, int slots, cudaStream_t st) {
+template <typename TF, typename TL, int YM>
+void launch_apply_s(const SysTab* tab, const SubDesc* subs, int nsub, int smem, int slots, int win, cudaStream_t st) {
     if (slots == 2)
-        launch_apply_t<TF, YM, 2>(tab, subs, nsub, smem, st);
+        launch_apply_t<TF, TL, YM, 2>(tab, subs, nsub, smem, win, st);
     else if (slots == 3)
-        launch_apply_t<TF, YM, 3>(tab, subs, nsub, smem, st);
+        launch_apply_t<TF, TL, YM, 3>(tab, subs, nsub, smem, win, st);
     else
-        launch_apply_t<TF, YM, 4>(tab, subs, nsub, smem, st);
+        launch_apply_t<TF, TL, YM, 4>(tab, subs, nsub, smem, win, st);
 }
-template <typename TF>
+template <typename TF, typename TL>
 void launch_apply_p(const SysTab* tab, const SubDesc* subs, int nsub, ApplyConfig cfg, int slots, cudaStream_t st) {
     const int ring = (int)apply_ring_bytes(slots, cfg.chunk);
+    // the fine-level window of FP32-lump sweeps with local vectors outside shared memory
+    const int win = sizeof(TL) == 4 && cfg.ymode != Y_SMEM ? cfg.win : 0;
     if (cfg.ymode == Y_SMEM)
-        launch_apply_s<TF, Y_SMEM>(tab, subs, nsub, ring + cfg.smem, slots, st);
+        launch_apply_s<TF, TL, Y_SMEM>(tab, subs, nsub, ring + cfg.smem, slots, 0, st);
     else if (cfg.ymode == Y_LUMPS)
-        launch_apply_s<TF, Y_LUMPS>(tab, subs, nsub, ring + cfg.smem, slots, st);
+        launch_apply_s<TF, TL, Y_LUMPS>(tab, subs, nsub, ring + 32 * win + cfg.smem, slots, win, st);
     else
-        launch_apply_s<TF, Y_DEVICE>(tab, subs, nsub, ring, slots, st);
+        launch_apply_s<TF, TL, Y_DEVICE>(tab, subs, nsub, ring + 32 * win, slots, win, st);
 }
 }  // namespace
 
-void launch_apply(const SysTab* tab, const SubDesc* subs, int nsub, int prec, ApplyConfig cfg, cudaStream_t st) {
+void launch_apply(const SysTab* tab, const SubDesc* subs, int nsub, int prec, bool lump32, ApplyConfig cfg,
+                  cudaStream_t st) {
     if (nsub <= 0) return;
     const int slots = cfg.slots < 2 ? 2 : (cfg.slots > kMaxSlots ? kMaxSlots : cfg.slots);
     if (prec == 0)
-        launch_apply_p<double>(tab, subs, nsub, cfg, slots, st);
+        launch_apply_p<double, double>(tab, subs, nsub, cfg, slots, st);
+    else if (prec == 1 && lump32)
+        launch_apply_p<float, float>(tab, subs, nsub, cfg, slots, st);
     else if (prec == 1)
-        launch_apply_p<float>(tab, subs, nsub, cfg, slots, st);
+        launch_apply_p<float, double>(tab, subs, nsub, cfg, slots, st);
+    else if (lump32)
+        launch_apply_p<__half, float>(tab, subs, nsub, cfg, slots, st);
     else
-        launch_apply_p<__half>(tab, subs, nsub, cfg, slots, st);
+        launch_apply_p<__half, double>(tab, subs, nsub, cfg, slots, st);
+}
+
+void launch_restrict(const SysTab* tab, const SubDesc* subs, const int2* items, int nitems, int prec, bool lump32,
+                     cudaStream_t st) {
+    if (nitems <= 0) return;
+    if (prec == 0)
+        k_restrict<double, double><<<nitems, 256, 0, st>>>(tab, subs, items);
+    else if (lump32)
+        k_restrict<float, float><<<nitems, 256, 0, st>>>(tab, subs, items);
+    else
+        k_restrict<float, double><<<nitems, 256, 0, st>>>(tab, subs, items);
 }
 
 void launch_dense_restrict(const SysTab* tab, const SubDesc* subs, int nsub, cudaStream_t st) {

@@ -437,7 +437,7 @@ std::string build_sub(const Ctx& X, int s, SubSym& o) {
     for (int J : far_box_of_row) o.cells_of_row.push_back(-1 - J);  // far rows: -1 - box
 
     // Factor stream: self-contained chunks of at most o.chunk_cap, each holding rows of one wavefront
-    // level (fine rows at the factor precision, lump rows in FP64): all forward chunks in level
+    // level (fine rows at the factor precision, lump rows in FP64 or FP32): all forward chunks in level
     // order, then all backward chunks in reverse level order -- the order the apply consumes them,
     // so the stream is read front to back.  Chunk layout (every array 16-byte aligned):
     //   header int[8] = {f0, nf, c0, nc, nef, nec, flags, bytes}; flags: bit 0 = last chunk of
@@ -445,6 +445,7 @@ std::string build_sub(const Ctx& X, int s, SubSym& o) {
     //   fptr[nf+1] fcol[nef] fval[nef blocks] (fdinv[nf blocks]) cptr[nc+1] ccol[nec] cval[nec] (cdinv[nc])
     // Columns: fine index (>= 0) or ~lump index.
     const size_t fbb = X.prec == 0 ? 72 : (X.prec == 1 ? 36 : 20);  // FP64 / FP32 / FP16 + exponent
+    const size_t lbb = X.S.lump32 ? 36 : 72;                            // lump rows: FP32 / FP64
     struct Piece {
         int lv, pos_f, nf, pos_c, nc;
         bool fwd, last;
@@ -454,8 +455,8 @@ std::string build_sub(const Ctx& X, int s, SubSym& o) {
     auto nu = [&](int p) { return o.prp[p + 1] - o.pdiag[p] - 1; };
     auto chunk_bytes = [&](int nf_, int ef, int nc_, int ec, bool fwd) {
         size_t b = 32 + al16(4 * (size_t)(nf_ + 1)) + al16(4 * (size_t)ef) + al16(fbb * ef) + al16(4 * (size_t)(nc_ + 1)) +
-                   al16(4 * (size_t)ec) + al16(72 * (size_t)ec);
-        if (!fwd) b += al16(fbb * nf_) + al16(72 * (size_t)nc_);
+                   al16(4 * (size_t)ec) + al16(lbb * (size_t)ec);
+        if (!fwd) b += al16(fbb * nf_) + al16(lbb * (size_t)nc_);
         return b;
     };
     // chunk capacity: the largest fine level (forward or backward part) and the longest single lump
@@ -604,14 +605,19 @@ std::string build_sub(const Ctx& X, int s, SubSym& o) {
         int* hdr = reinterpret_cast<int*>(o.stream.data() + w);
         w += 32;
         const int ef = put_rows(w, pc_.pos_f, pc_.nf, pc_.fwd, fbb, !pc_.fwd, true);
-        const int ec = put_rows(w, pc_.pos_c, pc_.nc, pc_.fwd, 72, !pc_.fwd, false);
+        const int ec = put_rows(w, pc_.pos_c, pc_.nc, pc_.fwd, lbb, !pc_.fwd, false);
         hdr[0] = fidx_pos[pc_.pos_f];
         hdr[1] = pc_.nf;
         hdr[2] = cidx_pos[pc_.pos_c];
         hdr[3] = pc_.nc;
         hdr[4] = ef;
         hdr[5] = ec;
-        hdr[6] = (pc_.last ? 1 : 0) | (lump_slots_log2(pc_) << 8);
+        bool has_long = false;
+        for (int k = 0; k < pc_.nc; k++) {
+            const int p = o.row_of_pos[pc_.pos_c + k];
+            has_long = has_long || (pc_.fwd ? nl(p) : nu(p)) > asm2::kLongLumpRow;
+        }
+        hdr[6] = (pc_.last ? 1 : 0) | (lump_slots_log2(pc_) << 8) | (has_long ? asm2::kChunkLongLumps : 0);
         hdr[7] = o.chunk_bytes[i];
         if (w != (size_t)o.chunk_off[i] + (size_t)o.chunk_bytes[i]) return "stream chunk layout mismatch";
     }
@@ -668,12 +674,14 @@ std::string build_pattern(int n, const int* rp, const int* ci, int nnzb, Pattern
     return "";
 }
 
-std::string build_symbolic(const Geom& g, const Pattern& A, int prec, int colsum, SysSym& S, int threads) {
+std::string build_symbolic(const Geom& g, const Pattern& A, int prec, int lump32, int colsum, SysSym& S,
+                           int threads) {
     const int N = g.n_cells();
     if (A.n != N) return "matrix size does not match the grid";
     S = SysSym();
     S.g = g;
     S.prec = prec;
+    S.lump32 = prec != 0 && lump32 ? 1 : 0;
     S.colsum = colsum;
     const int K = g.n_sub();
     if (g.far_mode != 0) {

@@ -72,6 +72,7 @@ struct SubSym {
 struct SysSym {
     Geom g;
     int prec = 0;  // element size class of the fine-row values: 0 f64, 1 f32, 2 f16
+    int lump32 = 0;  // lump-row values stored in FP32 (else FP64)
     int colsum = 1;
     // far boxes
     int nboxes = 0;
@@ -86,8 +87,10 @@ struct SysSym {
 };
 
 // Builds the whole symbolic structure; returns "" or an error message.  prec: 0 f64, 1 f32,
-// 2 f16 element storage of fine-row factors; colsum: compensation on/off.  threads <= 0: auto.
-std::string build_symbolic(const Geom& g, const Pattern& A, int prec, int colsum, SysSym& out, int threads);
+// 2 f16 element storage of fine-row factors; lump32: lump-row factors stored in FP32 (else FP64);
+// colsum: compensation on/off.  threads <= 0: auto.
+std::string build_symbolic(const Geom& g, const Pattern& A, int prec, int lump32, int colsum, SysSym& out,
+                           int threads);
 
 // local row of every cell for subdomain s (-1 = outside), from the stored lists
 void local_map(const SysSym& S, int s, std::vector<int>& map);

@@ -39,10 +39,10 @@ std::vector<int> to_bsr(const Pattern& P, const std::vector<int>& locs) {
 
 extern "C" {
 
-// geo = {nx, ny, nz, px, py, pz, ov, near_width, cn[3], far_mode, cf[3]}; NULL on error (message
-// in err)
-void* hs_create(const int* geo, int n, int nnzb, const int* rp, const int* ci, int prec, int colsum, char* err,
-                int errlen) {
+// geo = {nx, ny, nz, px, py, pz, ov, near_width, cn[3], far_mode, cf[3]}; lump32: lump-row
+// factors in FP32 (FP32/FP16 fine rows only); NULL on error (message in err)
+void* hs_create(const int* geo, int n, int nnzb, const int* rp, const int* ci, int prec, int lump32, int colsum,
+                char* err, int errlen) {
     Geom g;
     g.nx = geo[0];
     g.ny = geo[1];
@@ -57,7 +57,7 @@ void* hs_create(const int* geo, int n, int nnzb, const int* rp, const int* ci, i
     for (int d = 0; d < 3; d++) g.cf[d] = geo[12 + d];
     Handle* h = new Handle();
     std::string e = build_pattern(n, rp, ci, nnzb, h->pat);
-    if (e.empty()) e = build_symbolic(g, h->pat, prec, colsum, h->sym, 0);
+    if (e.empty()) e = build_symbolic(g, h->pat, prec, lump32, colsum, h->sym, 0);
     if (!e.empty()) {
         std::strncpy(err, e.c_str(), (size_t)errlen - 1);
         err[errlen - 1] = 0;

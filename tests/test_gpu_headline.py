@@ -14,8 +14,9 @@ among them.
 Tolerances (relative, per subdomain's owned rows):
 - FP64 factors: 1e-12, as at the smaller sizes (summation order and FMA contraction only).
 - FP32 factors: 1e-5 (unit roundoff 6e-8 times the local amplification, measured < 1e-6).
-- FP16 factors with a per-block power-of-two exponent: 1e-2 (unit roundoff 2^-11 = 4.9e-4 on
-  every stored factor value, times the same amplification).
+- FP16 factors with a per-block power-of-two exponent: 5e-3 (unit roundoff 2^-11 = 4.9e-4 on
+  every stored factor value, times the same amplification; measured 1.0e-3).
+Lump rows in FP64 or FP32 (asm_options.lump_precision) share these tolerances.
 The GMRES solve in each precision must reach a true relative residual of 1e-8, recomputed on the
 host with the oracle's SpMV."""
 import numpy as np
@@ -31,7 +32,7 @@ W = synth.WORKLOADS["grid128x128x64_k512"]
 # s = tz + pz (tx + px ty): 0 and 511 corners, 255 and 256 x-edges, 272 and 273 interior (both z
 # halves), 34 one subdomain in from a corner
 SUBS = (0, 255, 256, 511, 272, 273, 34)
-TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp16s": 1e-2}
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp16s": 5e-3}
 
 
 def owned_cells(s):
@@ -72,15 +73,15 @@ def oracle_rows(system, rhs):
 _solvers = {}
 
 
-def solver(system, prec):
-    if prec not in _solvers:
-        sol = asm2.Solver(precision=prec, restart=W.restart)
+def solver(system, prec, lumps="fp64"):
+    if (prec, lumps) not in _solvers:
+        sol = asm2.Solver(precision=prec, restart=W.restart, lumps=lumps)
         sol.set_grid(W.nx, W.ny, W.nz)
         sol.set_matrix(system.row_ptr, system.col_idx, system.vals)
         sol.set_partition(W.px, W.py, W.pz, W.overlap)
         sol.factor()
-        _solvers[prec] = sol
-    return _solvers[prec]
+        _solvers[(prec, lumps)] = sol
+    return _solvers[(prec, lumps)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -91,10 +92,13 @@ def _close_solvers():
     _solvers.clear()
 
 
+CASES = [("fp64", "fp64"), ("fp32", "fp64"), ("fp16s", "fp64"), ("fp32", "fp32"), ("fp16s", "fp32")]
+
+
 @pytest.mark.parametrize("placement", ["auto", "device", "lumps", "shared"])
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16s"])
-def test_apply_matches_oracle_on_sampled_subdomains(system, rhs, oracle_rows, prec, placement):
-    sol = solver(system, prec)
+@pytest.mark.parametrize("prec, lumps", CASES)
+def test_apply_matches_oracle_on_sampled_subdomains(system, rhs, oracle_rows, prec, lumps, placement):
+    sol = solver(system, prec, lumps)
     sol.set_tuning(apply_smem=placement)
     worst = 0.0
     for k, r in enumerate(rhs):
@@ -106,15 +110,15 @@ def test_apply_matches_oracle_on_sampled_subdomains(system, rhs, oracle_rows, pr
             worst = max(worst, err)
             assert err <= TOL[prec], (s, k, err)
     sol.set_tuning(apply_smem="auto")
-    print(f"headline apply {prec} {placement}: worst relative error on sampled owned rows {worst:.3e}")
+    print(f"headline apply {prec} lumps {lumps} {placement}: worst relative error on sampled owned rows {worst:.3e}")
 
 
 _x64 = {}
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16s"])
-def test_solve_reaches_fp64_tolerance(system, prec):
-    sol = solver(system, prec)
+@pytest.mark.parametrize("prec, lumps", CASES)
+def test_solve_reaches_fp64_tolerance(system, prec, lumps):
+    sol = solver(system, prec, lumps)
     x, info = sol.solve(torch.from_numpy(system.b).cuda(), rtol=1e-8, max_iter=3000)
     x = x.cpu().numpy()
     r = system.b - O.spmv(system.row_ptr, system.col_idx, system.vals, x)
@@ -122,7 +126,7 @@ def test_solve_reaches_fp64_tolerance(system, prec):
     assert info["converged"] and rel <= 1e-8 * (1 + 1e-6), (info, rel)
     if prec == "fp64":
         _x64["x"] = x
-    msg = f"headline solve {prec}: {info['iterations']} iterations, true residual {rel:.3e}"
+    msg = f"headline solve {prec} lumps {lumps}: {info['iterations']} iterations, true residual {rel:.3e}"
     if "x" in _x64 and prec != "fp64":
         msg += f", error vs the FP64 GPU solution {np.linalg.norm(x - _x64['x']) / np.linalg.norm(_x64['x']):.3e}"
     print(msg)

@@ -2,7 +2,10 @@
 
 Tolerances (relative): local matrices and factors 1e-12 per block row; each preconditioner apply
 1e-12 (||dz|| / ||z||); GMRES solution 1e-8.  Integer structure (maps, patterns, level counts,
-iteration counts) must be identical.
+iteration counts) must be identical.  Mixed precision (factors computed in FP64, then stored):
+FP32 applies 1e-5 (unit roundoff 6e-8 times the local triangular solves' amplification); FP16S
+applies 5e-3 (unit roundoff 2^-11 = 4.9e-4 of the stored values, same amplification); lump rows
+in FP64 or FP32 alike.
 """
 import numpy as np
 import pytest
@@ -25,8 +28,11 @@ GEOMS = {
 }
 
 
-def gpu_solver(g, s, precision="fp64", local_solver="colsum", restart=30):
-    sol = asm2.Solver(precision=precision, restart=restart, local_solver=local_solver)
+MIXED_TOL = {"fp32": 1e-5, "fp16s": 5e-3}
+
+
+def gpu_solver(g, s, precision="fp64", local_solver="colsum", restart=30, lumps="fp64"):
+    sol = asm2.Solver(precision=precision, restart=restart, local_solver=local_solver, lumps=lumps)
     sol.set_grid(g.nx, g.ny, g.nz)
     sol.set_matrix(s.row_ptr, s.col_idx, s.vals)
     sol.set_partition(g.px, g.py, g.pz, g.ov, g.near_width, g.cnear, g.far_mode,
@@ -100,13 +106,15 @@ def test_apply(name, local_solver):
     np.testing.assert_array_equal(zd, sol.apply(s.b))
 
 
-def test_apply_mixed_precision_close_to_fp64():
-    g, seed = GEOMS["cfg1"]
+@pytest.mark.parametrize("lumps", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", ["cfg1", "ragged", "cfar", "k32", "tall"])
+def test_apply_mixed_precision_close_to_fp64(name, lumps):
+    g, seed = GEOMS[name]
     s = synth.grid_jacobian(g.nx, g.ny, g.nz, seed)
     pc = O.Precond(g, s.row_ptr, s.col_idx, s.vals)
     zo = pc.apply(s.b)
-    for prec, tol in (("fp32", 1e-5), ("fp16s", 1e-2)):
-        z = gpu_solver(g, s, precision=prec).apply(s.b)
+    for prec, tol in MIXED_TOL.items():
+        z = gpu_solver(g, s, precision=prec, lumps=lumps).apply(s.b)
         assert rel(z, zo) <= tol, prec
 
 
@@ -138,11 +146,12 @@ def test_gmres_restart_short_cycles():
     assert rel(x, xo) <= 1e-8
 
 
+@pytest.mark.parametrize("lumps", ["fp64", "fp32"])
 @pytest.mark.parametrize("prec", ["fp32", "fp16s"])
-def test_mixed_precision_reaches_fp64_tolerance(prec):
+def test_mixed_precision_reaches_fp64_tolerance(prec, lumps):
     g, seed = GEOMS["k32"]
     s = synth.grid_jacobian(g.nx, g.ny, g.nz, seed)
-    sol = gpu_solver(g, s, precision=prec)
+    sol = gpu_solver(g, s, precision=prec, lumps=lumps)
     x, info = sol.solve(s.b, rtol=1e-8, max_iter=3000)
     r = s.b - O.spmv(s.row_ptr, s.col_idx, s.vals, x)
     assert info["converged"]
@@ -273,15 +282,16 @@ def test_batch_mixing_chunk_capacities_equals_alone(precision):
         assert info == ib
 
 
-@pytest.mark.parametrize("precision, tol", [("fp64", 1e-12), ("fp32", 1e-5)])
-def test_lump_rows_longer_than_the_smallest_chunk(precision, tol):
+@pytest.mark.parametrize("precision, tol, lumps", [("fp64", 1e-12, "fp64"), ("fp32", 1e-5, "fp64"),
+                                                   ("fp32", 1e-5, "fp32"), ("fp16s", 5e-3, "fp32")])
+def test_lump_rows_longer_than_the_smallest_chunk(precision, tol, lumps):
     """Far lumps that touch many near lumps (32x32x64 in 4x4 boxes): lump rows of ~130 blocks (~10 KB
     in FP64) need stream chunks above the 8 KB minimum capacity; the apply matches the oracle."""
     g = O.Geometry(32, 32, 64, 4, 4, 1, ov=1)
     s = synth.grid_jacobian(32, 32, 64, 9)
     pc = O.Precond(g, s.row_ptr, s.col_idx, s.vals)
     r = synth.rhs(s.n_cells, 1)
-    assert rel(gpu_solver(g, s, precision=precision).apply(r), pc.apply(r)) <= tol
+    assert rel(gpu_solver(g, s, precision=precision, lumps=lumps).apply(r), pc.apply(r)) <= tol
 
 
 def test_configuration_64x64x16_k64():
@@ -301,13 +311,14 @@ def test_configuration_64x64x16_k64():
     assert i32["converged"] and np.linalg.norm(r) / np.linalg.norm(s.b) <= 1e-8
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16s"])
-def test_kernel_variants(prec):
+@pytest.mark.parametrize("prec, lumps", [("fp64", "fp64"), ("fp32", "fp64"), ("fp16s", "fp64"), ("fp32", "fp32"),
+                                         ("fp16s", "fp32")])
+def test_kernel_variants(prec, lumps):
     """Shared-memory vs device-memory local vectors give the same bits; the cooperative and the
     per-projection Gram-Schmidt paths differ only in the order of the reduction sums."""
     g, seed = GEOMS["k32"]
     s = synth.grid_jacobian(g.nx, g.ny, g.nz, seed)
-    sol = gpu_solver(g, s, precision=prec)
+    sol = gpu_solver(g, s, precision=prec, lumps=lumps)
     z1 = sol.apply(s.b)
     x1, i1 = sol.solve(s.b, 1e-8, 2000)
     sol.set_tuning(apply_smem=False)
@@ -320,36 +331,36 @@ def test_kernel_variants(prec):
     assert rel(x3, x1) <= 1e-10
 
 
+@pytest.mark.parametrize("lumps", ["fp64", "fp32"])
 @pytest.mark.parametrize("prec", ["fp32", "fp16s"])
-def test_device_memory_local_vectors_with_more_lumps_than_fine_rows(prec):
+def test_device_memory_local_vectors_with_more_lumps_than_fine_rows(prec, lumps):
     """Subdomains of 4 cells with ~60 far lumps each: the device-memory local vectors (lumps in
-    FP64, fine rows and the lump mirror at the factor precision) must not spill into the next
-    subdomain's; the result equals the shared-memory variant bit for bit."""
+    FP64 with an FP32 mirror, or in FP32; fine rows at the factor precision) must not spill into
+    the next subdomain's; the result equals the shared-memory variant bit for bit."""
     g = O.Geometry(8, 8, 4, 8, 8, 1, ov=0, near_width=2)
     s = synth.grid_jacobian(g.nx, g.ny, g.nz, 9)
     pc = O.Precond(g, s.row_ptr, s.col_idx, s.vals)
     assert max(pc.sub_n(k) - pc.sub_counts(k)[0] for k in range(g.n_sub)) > 4 * pc.sub_counts(0)[0]
-    sol = gpu_solver(g, s, precision=prec)
+    sol = gpu_solver(g, s, precision=prec, lumps=lumps)
     z1 = sol.apply(s.b)
     sol.set_tuning(apply_smem=False)
     np.testing.assert_array_equal(z1, sol.apply(s.b))
-    assert rel(z1, pc.apply(s.b)) <= (1e-5 if prec == "fp32" else 1e-2)
+    assert rel(z1, pc.apply(s.b)) <= MIXED_TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_local_vector_placements_agree(prec):
+@pytest.mark.parametrize("prec, lumps", [("fp64", "fp64"), ("fp32", "fp64"), ("fp32", "fp32"), ("fp16s", "fp32")])
+def test_local_vector_placements_agree(prec, lumps):
     """512 subdomains (more than one wave of the shared-memory variant, so the automatic choice is
     lumps in shared memory): every placement of the apply's local vectors gives the same bits, and
     the FP64 apply matches the oracle."""
     g = O.Geometry(32, 32, 4, 16, 16, 2, ov=1)
     s = synth.grid_jacobian(g.nx, g.ny, g.nz, 12)
-    sol = gpu_solver(g, s, precision=prec)
+    sol = gpu_solver(g, s, precision=prec, lumps=lumps)
     z = sol.apply(s.b)
     for place in ("device", "lumps", "shared", "auto"):
         sol.set_tuning(apply_smem=place)
         np.testing.assert_array_equal(z, sol.apply(s.b))
-    if prec == "fp64":
-        assert rel(z, O.Precond(g, s.row_ptr, s.col_idx, s.vals).apply(s.b)) <= 1e-12
+    assert rel(z, O.Precond(g, s.row_ptr, s.col_idx, s.vals).apply(s.b)) <= MIXED_TOL.get(prec, 1e-12)
     x1, i1 = sol.solve(s.b, 1e-8, 2000)
     sol.set_tuning(apply_smem="device")
     x2, i2 = sol.solve(s.b, 1e-8, 2000)
@@ -384,3 +395,16 @@ def test_graphs_and_online_tuner_leave_results_unchanged():
     x2, i2 = sol.solve(s.b, 1e-8, 2000)
     np.testing.assert_array_equal(x1, x2)
     assert i1 == i2
+
+
+def test_batch_refuses_mixed_lump_precisions():
+    """Every system of a batch runs in the same apply launch, so all must store lump rows alike."""
+    g, seed = GEOMS["cfg1"]
+    s = synth.grid_jacobian(g.nx, g.ny, g.nz, seed)
+    a = gpu_solver(g, s, precision="fp32", lumps="fp64")
+    b = gpu_solver(g, s, precision="fp32", lumps="fp32")
+    with pytest.raises(asm2.ASMError) as e:
+        asm2.solve_batch([a, b], [s.b, s.b], 1e-8, 100)
+    assert e.value.status == 1
+    xs, infos = asm2.solve_batch([b], [s.b], 1e-8, 2000)
+    assert infos[0]["converged"]

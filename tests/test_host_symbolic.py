@@ -70,7 +70,7 @@ def hs(tmp_path_factory):
                     os.path.join(ROOT, "tests", "host_symbolic_shim.cpp"), "-o", out, "-lpthread"], check=True)
     lib = C.CDLL(out)
     lib.hs_create.restype = C.c_void_p
-    lib.hs_create.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_char_p,
+    lib.hs_create.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_char_p,
                               C.c_int]
     lib.hs_destroy.argtypes = [C.c_void_p]
     lib.hs_get.restype = C.c_longlong
@@ -84,15 +84,15 @@ class Sym:
 
     DTYPES = {"chunk_off": np.int64, "pk_off_f": np.int64, "pk_off_c": np.int64, "stream": np.uint8}
 
-    def __init__(self, lib, g, s, prec=0, colsum=1):
+    def __init__(self, lib, g, s, prec=0, colsum=1, lump32=0):
         geo = np.array([g.nx, g.ny, g.nz, g.px, g.py, g.pz, g.ov, g.near_width, *g.cnear, g.far_mode,
                         *(g.cfar if g.far_mode == 2 else (1, 1, 1))], dtype=np.int32)
         rp = np.ascontiguousarray(s.row_ptr, dtype=np.int32)
         ci = np.ascontiguousarray(s.col_idx, dtype=np.int32)
         err = C.create_string_buffer(256)
         self.lib = lib
-        self.h = lib.hs_create(geo.ctypes.data, s.n_cells, s.nnzb, rp.ctypes.data, ci.ctypes.data, prec, colsum, err,
-                               256)
+        self.h = lib.hs_create(geo.ctypes.data, s.n_cells, s.nnzb, rp.ctypes.data, ci.ctypes.data, prec, lump32, colsum,
+                               err, 256)
         assert self.h, err.value.decode()
 
     def __del__(self):
@@ -194,7 +194,7 @@ def al16(x):
     return (x + 15) // 16 * 16
 
 
-def decode_chunks(sym, sd, prec):
+def decode_chunks(sym, sd, prec, lump32=0):
     """Chunks of subdomain sd's factor stream: (fwd, f0, nf, c0, nc, last, fine rows' columns, lump
     rows' columns, value offsets of the fine and lump blocks, bytes)."""
     stream, off, nbytes = sym.get(sd, "stream"), sym.get(sd, "chunk_off"), sym.get(sd, "chunk_bytes")
@@ -208,7 +208,7 @@ def decode_chunks(sym, sd, prec):
         assert b == nb
         w = o + 32
         groups = []
-        for cnt, ne, bb in ((nf, nef, fbb), (nc, nec, 72)):
+        for cnt, ne, bb in ((nf, nef, fbb), (nc, nec, 36 if lump32 and prec else 72)):
             ptr = stream[w:w + 4 * (cnt + 1)].view(np.int32)
             assert ptr[0] == 0 and ptr[-1] == ne
             w += al16(4 * (cnt + 1))
@@ -226,12 +226,12 @@ def decode_chunks(sym, sd, prec):
     return out
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec,lump32", [(0, 0), (1, 0), (2, 0), (1, 1), (2, 1)])
 @pytest.mark.parametrize("name", ["cfg1", "ragged", "cfar", "k32", "tall", "far_small", "ov_wide", "wide"])
-def test_factor_stream_is_a_valid_schedule(hs, name, prec):
+def test_factor_stream_is_a_valid_schedule(hs, name, prec, lump32):
     g, seed = WIDE if name == "wide" else GEOMS[name]
     s = synth.grid_jacobian(g.nx, g.ny, g.nz, seed)
-    sym = Sym(hs, g, s, prec=prec)
+    sym = Sym(hs, g, s, prec=prec, lump32=lump32)
     for sd in range(g.n_sub):
         inf = sym.info(sd)
         n, nf, cap = inf["n"], inf["nf"], inf["chunk_cap"]
@@ -243,7 +243,7 @@ def test_factor_stream_is_a_valid_schedule(hs, name, prec):
         assert off[0] == 0 and np.all(off % 16 == 0) and np.all(nbytes <= cap)
         np.testing.assert_array_equal(off[1:], off[:-1] + nbytes[:-1])
         assert off[-1] + nbytes[-1] == len(sym.get(sd, "stream"))
-        chunks = decode_chunks(sym, sd, prec)
+        chunks = decode_chunks(sym, sd, prec, lump32)
         level = levels_of(sym, sd)
         for fwd in (True, False):
             seen = np.zeros(n, dtype=np.int64)
@@ -305,7 +305,7 @@ def test_symbolic_errors_are_reported(hs):
     ci = np.array([0, 1, 1, 2, 3], dtype=np.int32)   # (0, 1) without (1, 0)
     geo = np.array([2, 1, 2, 1, 1, 1, 0, 0, 1, 1, 1, 0, 1, 1, 1], dtype=np.int32)
     err = C.create_string_buffer(256)
-    h = hs.hs_create(geo.ctypes.data, 4, 5, rp.ctypes.data, ci.ctypes.data, 0, 1, err, 256)
+    h = hs.hs_create(geo.ctypes.data, 4, 5, rp.ctypes.data, ci.ctypes.data, 0, 0, 1, err, 256)
     assert not h
     assert b"symmetric" in err.value
 
