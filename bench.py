@@ -517,11 +517,12 @@ def apply_traffic(alg_bytes: int):
         return None
 
 
-def workload_config(w, system, precision: str):
+def workload_config(w, system, precision: str, lumps: str = "fp32"):
     """The `config` object of both arms' lines (the same dict, so that the two lines compare)."""
     return {"workload": w.name, "grid": [w.nx, w.ny, w.nz], "cells": system.n_cells,
             "partition": [w.px, w.py, w.pz], "overlap": w.overlap, "near_width": 2, "c_near": [2, 2, 2],
             "far": "partition boxes", "krylov": f"GMRES({w.restart})", "precision": precision,
+            "lump_rows": "fp64" if precision == "fp64" else lumps,
             "tol": 1e-8, "l2": "inputs larger than L2 (A 0.56 GB, factors > 0.5 GB)",
             "step": "update values + re-assemble + re-factor + GMRES to 1e-8", "generator": GENERATOR}
 
@@ -558,7 +559,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": float(np.mean(wall)), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "impl": "reference", "estimated": True,
-            "config": workload_config(w, system, args.precision), "iterations_assumed": iters,
+            "config": workload_config(w, system, args.precision, args.lumps), "iterations_assumed": iters,
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
                              "cpu_model": model, "nproc": nproc, "estimated": True},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -635,8 +636,8 @@ def run_gpu(args):
     b_d = torch.from_numpy(system.b).cuda()
     stream = torch.cuda.current_stream()
 
-    def make_solver(prec):
-        s = asm2.Solver(precision=prec, restart=w.restart, device=local, stream=stream.cuda_stream, lumps=args.lumps)
+    def make_solver(prec, lumps):
+        s = asm2.Solver(precision=prec, restart=w.restart, device=local, stream=stream.cuda_stream, lumps=lumps)
         s.set_grid(w.nx, w.ny, w.nz)
         s.set_matrix(system.row_ptr, system.col_idx, vals_d)
         s.set_partition(w.px, w.py, w.pz, w.overlap)
@@ -655,9 +656,17 @@ def run_gpu(args):
         return x, info
 
     results = {}
-    precs = [args.precision] + [p_ for p_ in ("fp64", "fp32", "fp16s") if p_ != args.precision and not args.no_precisions]
-    for prec in precs:
-        sol = make_solver(prec)
+    def vkey(prec, lumps):  # "fp64", "fp32", "fp16s" (FP32 lump rows), or "fp32_lumps_fp64", ...
+        return prec if prec == "fp64" or lumps == "fp32" else f"{prec}_lumps_fp64"
+
+    main_key = vkey(args.precision, args.lumps)
+    variants = [(args.precision, args.lumps)]
+    if not args.no_precisions:
+        for pv in (("fp64", "fp64"), ("fp32", "fp32"), ("fp16s", "fp32"), ("fp32", "fp64")):
+            if vkey(*pv) != main_key:
+                variants.append(pv)
+    for prec, lumps in variants:
+        sol = make_solver(prec, lumps)
         for _ in range(args.warmup):
             step(sol)
         sol.reset_profile()
@@ -679,11 +688,11 @@ def run_gpu(args):
         xh = x.cpu().numpy()
         import oracle as O
         r = system.b - O.spmv(system.row_ptr, system.col_idx, system.vals, xh)
-        results[prec] = {"ms": ms, "info": infos[-1], "prof": prof, "stats": st, "clocks": clk.summary(),
+        results[vkey(prec, lumps)] = {"ms": ms, "info": infos[-1], "prof": prof, "stats": st, "clocks": clk.summary(),
                          "host_check_relres": float(np.linalg.norm(r) / np.linalg.norm(system.b)), "solver": sol,
                          "x": xh}
 
-    main = results[args.precision]
+    main = results[main_key]
     sol = main["solver"]
     # end to end through the public API with pinned host buffers (matrix values + b in, x out)
     vals_h = torch.from_numpy(system.vals.reshape(-1)).pin_memory()
@@ -730,7 +739,7 @@ def run_gpu(args):
         "metric": METRIC, "value": main["ms"], "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": main["ms"], "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64 Krylov / f32 factors" if args.precision == "fp32" else args.precision, "data": "synthetic",
-        "config": workload_config(w, system, args.precision),
+        "config": workload_config(w, system, args.precision, args.lumps),
         "solves_per_s": 1e3 * ws / main["ms"],
         "iterations": main["info"]["iterations"], "restarts": main["info"]["restarts"],
         "true_rel_residual": main["info"]["rel_residual"], "host_check_rel_residual": main["host_check_relres"],
@@ -739,7 +748,7 @@ def run_gpu(args):
                             "converged": bool(r_["info"]["converged"]), "true_rel_residual": r_["info"]["rel_residual"],
                             "host_check_rel_residual": r_["host_check_relres"],
                             "err_vs_fp64": err_vs_fp64(r_["x"])}
-                       for p_, r_ in results.items() if p_ != args.precision},
+                       for p_, r_ in results.items() if p_ != main_key},
         "err_vs_fp64": err_vs_fp64(main["x"]),
         "breakdown_ms_per_solve": {k: prof[k] / args.steps for k in ("apply_ms", "spmv_ms", "ortho_ms", "factor_ms")},
         "roofline": {"bound": "hbm", "kernel": "precond apply (boxsum + fused local solves)", "achieved": achieved,
@@ -780,7 +789,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="grid128x128x64_k512", choices=list(synth.WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16s"])
-    ap.add_argument("--lumps", default="fp64", choices=["fp64", "fp32"],
+    ap.add_argument("--lumps", default="fp32", choices=["fp64", "fp32"],
                     help="lump rows' precision under FP32/FP16S fine rows (asm_options.lump_precision)")
     ap.add_argument("--max-iter", type=int, default=3000)
     ap.add_argument("--ref-iters", type=int, default=None,

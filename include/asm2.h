@@ -63,9 +63,10 @@ typedef enum {
  * local ILU factors under FP32 or FP16S fine rows.  The factorisation itself always runs in FP64;
  * Gram-Schmidt, the true residual and the classical coarse-grid solve stay FP64 either way. */
 typedef enum {
-    ASM_LUMP_FP64 = 0,  /* lump rows stored and applied in FP64 (default) */
-    ASM_LUMP_FP32 = 1   /* lump rows stored and applied in FP32 like the fine rows: every ILU
-                           factor row of the mixed-precision path is FP32 (FP64 factors ignore it) */
+    ASM_LUMP_FP64 = 0,  /* lump rows stored and applied in FP64 */
+    ASM_LUMP_FP32 = 1   /* (default) lump rows stored and applied in FP32 like the fine rows: every
+                           ILU factor row of the mixed-precision path is FP32 (FP64 factors ignore
+                           it) */
 } asm_lump_precision;
 
 typedef enum { ASM_KRYLOV_GMRES = 0, ASM_KRYLOV_ORTHOMIN = 1 } asm_krylov;
@@ -106,7 +107,7 @@ typedef struct {
     int flexible;     /* GMRES update: 1 keeps Z_j = B^{-1} v_j and sets x += Z y; 0 sets
                          x += B^{-1}(V y); -1 = automatic (0 for FP64, 1 otherwise) */
     int device;       /* CUDA device ordinal */
-    int lump_precision; /* asm_lump_precision (default ASM_LUMP_FP64) */
+    int lump_precision; /* asm_lump_precision (default ASM_LUMP_FP32) */
 } asm_options;
 
 typedef struct {
@@ -300,7 +301,7 @@ typedef struct {
     int max_active;       /* systems advanced together, 0 = no limit (default 64) */
     int max_cached;       /* idle factored systems kept for matrix reuse, LRU (default 16) */
     long long hbm_budget; /* device bytes for resident systems; 0 = 85% of free memory */
-    int lump_precision;   /* asm_lump_precision of every served system (default ASM_LUMP_FP64) */
+    int lump_precision;   /* asm_lump_precision of every served system (default ASM_LUMP_FP32) */
 } asm_server_options;
 
 typedef struct {

@@ -205,8 +205,8 @@ class Solver:
 
     def __init__(self, precision: str = "fp64", restart: int = 30, local_solver: str = "colsum",
                  flexible: int = -1, device: int = 0, stream: int | None = None, krylov: str = "gmres",
-                 lumps: str = "fp64"):
-        """lumps: "fp64" or "fp32", the lump rows' precision under FP32/FP16S fine rows
+                 lumps: str = "fp32"):
+        """lumps: "fp32" (default) or "fp64", the lump rows' precision under FP32/FP16S fine rows
         (asm_options.lump_precision)."""
         L = load()
         o = Options()
@@ -438,7 +438,7 @@ class Server:
     arrive, call progress() to admit and advance them, collect results by ticket."""
 
     def __init__(self, precision: str = "fp32", restart: int = 30, device: int = 0, max_active: int = 64,
-                 max_cached: int = 16, hbm_budget: int = 0, stream: int | None = None, lumps: str = "fp64"):
+                 max_cached: int = 16, hbm_budget: int = 0, stream: int | None = None, lumps: str = "fp32"):
         L = load()
         o = ServerOptions()
         L.asm_server_default_options(C.byref(o))

@@ -99,7 +99,6 @@ struct asm_ctx {
     DBuf d_lv, d_rlists, d_y, d_corr_cells, d_corr, d_dev_err;
     int apply_smem = 0;       // shared memory for all local vectors of the largest subdomain (0: none)
     int apply_lump_smem = 0;  // shared memory for its lump vector and the FP32 mirror
-    int win_rows = 0;         // fine-level window rows of the apply (FP32 lump rows; 0 = none)
     int apply_slots = 3; // factor-stream ring slots of the apply
     int chunk_cap = kStreamChunkMin;  // largest stream-chunk capacity of the subdomains (ring slot bytes)
     int sm_smem = 0, n_sms = 1;  // shared memory per SM and SM count of the device
@@ -592,7 +591,6 @@ void upload_symbolic(asm_ctx* h) {
     h->sub_cost.assign(K, 0.0);
     h->apply_smem = 0;
     h->apply_lump_smem = 0;
-    h->win_rows = 0;
     h->chunk_cap = kStreamChunkMin;
     h->tuned_ymode = -1;
     for (int s = 0; s < K; s++) {
@@ -622,21 +620,11 @@ void upload_symbolic(asm_ctx* h) {
         sd.nc = o.n - o.nf;
         sd.n_chunks = (int)o.chunk_off.size();
         sd.n_fwd = o.n_fwd_chunks;
-        // a chunk costs about one barrier-bounded step; lump-only chunks (FP64 rows) about 2.3.
-        // The widest fine level (rows summed over its chunks) sizes the apply's level window.
-        {
-            int level_rows = 0;
-            for (size_t i = 0; i < o.chunk_off.size(); i++) {
-                int hdr_nf = 0, hdr_flags = 0;
-                std::memcpy(&hdr_nf, o.stream.data() + o.chunk_off[i] + 4, sizeof(int));
-                std::memcpy(&hdr_flags, o.stream.data() + o.chunk_off[i] + 24, sizeof(int));
-                h->sub_cost[s] += hdr_nf == 0 ? 2.3 : 1.0;
-                level_rows += hdr_nf;
-                if (hdr_flags & 1) {
-                    if (S.lump32) h->win_rows = std::max(h->win_rows, std::min(level_rows, kWinMaxRows));
-                    level_rows = 0;
-                }
-            }
+        // a chunk costs about one barrier-bounded step; lump-only chunks (FP64 rows) about 2.3
+        for (size_t i = 0; i < o.chunk_off.size(); i++) {
+            int hdr_nf = 0;
+            std::memcpy(&hdr_nf, o.stream.data() + o.chunk_off[i] + 4, sizeof(int));
+            h->sub_cost[s] += hdr_nf == 0 ? 2.3 : 1.0;
         }
         sd.n_own = (int)o.own_pos.size();
         sd.n_long = (int)o.clong.size();
@@ -1036,8 +1024,7 @@ struct Batch {
     int nritems = 0;
     int nvec = 0, nrow = 0, nbox = 0, nsub = 0, prec = 0, slots = 3, chunk = kStreamChunkMin;
     bool lump32 = false;
-    ApplyConfig apply{Y_DEVICE, 0, 2, kStreamChunkMin, 0};
-    int win = 0;  // fine-level window rows (FP32 lump rows): the widest level of the batch, capped
+    ApplyConfig apply{Y_DEVICE, 0, 2, kStreamChunkMin};
     int all_bytes = 0, lump_bytes = 0;  // largest subdomain's shared-memory needs (placements)
     DBuf d_dense;           // exact local solves: (subdomain item, first owned row of 8)
     int ndense = 0;
@@ -1155,15 +1142,13 @@ void build_batch(Batch& B, cudaStream_t st) {
     B.lump_bytes = lump_bytes;
     B.slots = 4;
     B.chunk = kStreamChunkMin;
-    B.win = 0;
     for (asm_ctx* h : B.hs) {
         B.slots = std::min(B.slots, h->apply_slots);
         B.chunk = std::max(B.chunk, h->chunk_cap);
-        B.win = std::max(B.win, h->win_rows);
     }
     if (!B.hs.empty())
         B.apply = apply_local_vectors(B.nsub, all_bytes, lump_bytes, B.slots, B.chunk, B.hs[0]->sm_smem,
-                                      B.hs[0]->n_sms, B.hs[0]->apply_place, B.win);
+                                      B.hs[0]->n_sms, B.hs[0]->apply_place);
 }
 
 // events bracketing the launch groups of one step: [prep | apply | post | spmv | mgs+finish]
@@ -1190,7 +1175,7 @@ std::vector<ApplyConfig> apply_candidates(const Batch& B) {
     if (h->apply_place != 0) return {B.apply};
     for (int force : {Y_SMEM + 1, Y_LUMPS + 1, Y_DEVICE + 1}) {
         const ApplyConfig a =
-            apply_local_vectors(B.nsub, B.all_bytes, B.lump_bytes, B.slots, B.chunk, h->sm_smem, h->n_sms, force, B.win);
+            apply_local_vectors(B.nsub, B.all_bytes, B.lump_bytes, B.slots, B.chunk, h->sm_smem, h->n_sms, force);
         if (a.ymode == force - 1) c.push_back(a);
     }
     return c;
@@ -1803,7 +1788,7 @@ void asm_default_options(asm_options* opt) {
     opt->local_solver = ASM_LOCAL_BILU0_COLSUM;
     opt->flexible = -1;
     opt->device = 0;
-    opt->lump_precision = ASM_LUMP_FP64;
+    opt->lump_precision = ASM_LUMP_FP32;
 }
 
 const char* asm_error_string(int s) {
@@ -2021,7 +2006,7 @@ int asm_apply_precond(asm_handle h, const double* r, double* z, int on_device) {
                             h->n_ritems1, h->prec, h->lump32, h->stream);
             launch_apply(h->d_tab1.as<SysTab>(), h->d_subdesc_single.as<SubDesc>(), nsub, h->prec, h->lump32,
                          apply_local_vectors(nsub, h->apply_smem, h->apply_lump_smem, h->apply_slots, h->chunk_cap,
-                                             h->sm_smem, h->n_sms, h->apply_place, h->win_rows),
+                                             h->sm_smem, h->n_sms, h->apply_place),
                          h->stream);
         }
         if (h->tab.cmode != 0)
@@ -2282,7 +2267,7 @@ void asm_server_default_options(asm_server_options* o) {
     o->max_active = 64;
     o->max_cached = 16;
     o->hbm_budget = 0;
-    o->lump_precision = ASM_LUMP_FP64;
+    o->lump_precision = ASM_LUMP_FP32;
 }
 
 int asm_server_create(asm_server_handle* out, const asm_server_options* opt, void* cuda_stream) {

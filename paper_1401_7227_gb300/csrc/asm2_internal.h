@@ -31,12 +31,7 @@ struct ApplyConfig {
     int smem;   // dynamic shared memory of the vectors (bytes)
     int slots;  // factor-stream ring slots (2 for the 128-thread variants: deeper rings gain nothing)
     int chunk;  // bytes of one ring slot: the largest chunk capacity of the launch's subdomains
-    int win;    // rows of each of the two shared-memory buffers that hold the last two fine wavefront
-                // levels (FP32 lump rows with local vectors in device memory or lumps in shared
-                // memory); 0 = none
 };
-// Largest window buffer (rows): wider levels read their rows beyond it from device memory.
-constexpr int kWinMaxRows = 512;
 // Chunk header word 6: bit 0 = last chunk of its wavefront level; bits 8..11 = log2 of the entry
 // slots S of the short lump rows (each such row takes 3 S lanes: 3 output components x S slots);
 // kChunkLongLumps = the chunk holds a lump row of more than kLongLumpRow blocks.
@@ -284,7 +279,7 @@ size_t apply_lump_bytes(int nc, int prec, bool lump32);  // its lump vector (and
 // lumps in shared memory when four CTAs fit, else device memory), Y_SMEM + 1 / Y_LUMPS + 1 /
 // Y_DEVICE + 1 to ask for one placement (taken when it fits).
 ApplyConfig apply_local_vectors(int nsub, int all_bytes, int lump_bytes, int smem_slots, int chunk, int sm_smem,
-                                int sms, int force, int win);
+                                int sms, int force);
 size_t apply_ring_bytes(int slots, int chunk);
 void launch_spmv(const SysTab* st_tab, const RowItem* items, int nitems, cudaStream_t st);
 

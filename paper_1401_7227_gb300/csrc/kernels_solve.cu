@@ -159,24 +159,12 @@ using tma::mbar_wait;
 constexpr int kMaxSlots = 4;  // ring slots of the apply: a template argument, 2..kMaxSlots
 constexpr int kRingHeader = 64;  // mbarriers
 
-// The last two fine wavefront levels' results in shared memory, for sweeps whose local vectors live
-// in device memory: a fine row's fine neighbours sit in the level just before its own (hyperplanes
-// of the box), so they are read from here instead of from stores that may still be on their way
-// to L2.  prev holds rows [prev_lo, prev_hi) at prev[f - prev_lo], cur receives the current level's
-// rows at cur[f - cur_lo]; rows at or beyond cap positions, and every other row, use the device
-// copy (which is always written).  cur == nullptr: no window.
-struct Win {
-    float4* cur;
-    const float4* prev;
-    int cur_lo, prev_lo, prev_hi, cap;
-};
-
 // One chunk of the forward (lower = true) or backward sweep, read from shared memory.  TL is the
 // lump rows' storage and arithmetic type (double, or float with FP32/FP16 fine rows); ycf is the
 // FP32 mirror of FP64 lump values that FP32 fine rows read (nullptr otherwise).
 template <typename TF, typename TL>
 __device__ __forceinline__ void sweep_chunk(const unsigned char* base, bool lower, typename Compute<TF>::T* yf,
-                                            TL* yc, typename Compute<TF>::T* ycf, const Win& w) {
+                                            TL* yc, typename Compute<TF>::T* ycf) {
     using TC = typename Compute<TF>::T;
     constexpr int FB = FineBlock<TF>::bytes;
     const int4 h0 = reinterpret_cast<const int4*>(base)[0], h1 = reinterpret_cast<const int4*>(base)[1];
@@ -207,10 +195,9 @@ __device__ __forceinline__ void sweep_chunk(const unsigned char* base, bool lowe
         // and then the operands they point at are loaded four entries at a time before any
         // arithmetic (a 7-point fine row has at most six entries).  Lump rows of more than
         // kLongLumpRow entries are summed by a whole warp after the loop.
-        constexpr int kUnroll = 4;
+        constexpr int kUnroll = 3;
         float4* yf4 = reinterpret_cast<float4*>(yf);
         float4* yc4 = reinterpret_cast<float4*>(yc);
-        const unsigned wn = w.cur != nullptr ? (unsigned)min(w.prev_hi - w.prev_lo, w.cap) : 0u;  // window rows
         for (int q = tid; q < nf + nc; q += nt) {
             const bool fine = q < nf;
             const int i = fine ? q : q - nf;
@@ -235,8 +222,7 @@ __device__ __forceinline__ void sweep_chunk(const unsigned char* base, bool lowe
 #pragma unroll
                 for (int u = 0; u < kUnroll; u++) {
                     const int c = cs[u];
-                    const unsigned wp = (unsigned)(c - w.prev_lo);
-                    const float4 x = wp < wn ? w.prev[wp] : (c >= 0 ? yf4[c] : yc4[~c]);
+                    const float4 x = c >= 0 ? yf4[c] : yc4[~c];
                     const bool live = eb + u <= last;
                     xs[u] = make_float4(live ? x.x : 0.f, live ? x.y : 0.f, live ? x.z : 0.f, 0.f);
                 }
@@ -265,9 +251,7 @@ __device__ __forceinline__ void sweep_chunk(const unsigned char* base, bool lowe
                 a1 = b1;
                 a2 = b2;
             }
-            const float4 res = make_float4(a0, a1, a2, 0.f);
-            *yo = res;
-            if (fine && w.cur != nullptr && f0 + i - w.cur_lo < w.cap) w.cur[f0 + i - w.cur_lo] = res;
+            *yo = make_float4(a0, a1, a2, 0.f);
         }
         if (!has_long) return;
         // long lump rows: one warp each, lane = 8 k + s computing component k over the entries
@@ -286,8 +270,7 @@ __device__ __forceinline__ void sweep_chunk(const unsigned char* base, bool lowe
                         xs[u] = make_float4(0.f, 0.f, 0.f, 0.f);
                         if (eb + 8 * u < e1) {
                             const int c = ccol[eb + 8 * u];
-                            const unsigned wp = (unsigned)(c - w.prev_lo);
-                            xs[u] = wp < wn ? w.prev[wp] : (c >= 0 ? yf4[c] : yc4[~c]);
+                            xs[u] = c >= 0 ? yf4[c] : yc4[~c];
                         }
                     }
 #pragma unroll
@@ -676,7 +659,7 @@ __global__ void __launch_bounds__(256) k_restrict(const SysTab* __restrict__ tab
 // they fit.
 template <typename TF, typename TL, int YM, int SLOTS>
 __global__ void __launch_bounds__(YM == Y_SMEM ? 256 : kApplyThreadsDev, YM == Y_SMEM ? 2 : 4)
-    k_apply(const SysTab* __restrict__ tab, const SubDesc* __restrict__ subs, int win) {
+    k_apply(const SysTab* __restrict__ tab, const SubDesc* __restrict__ subs) {
     using TC = typename Compute<TF>::T;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const SubDesc sd = subs[blockIdx.x];
@@ -694,10 +677,7 @@ __global__ void __launch_bounds__(YM == Y_SMEM ? 256 : kApplyThreadsDev, YM == Y
     // layout of y_layout(); Y_SMEM copies all of them into shared memory, Y_LUMPS the lumps and the
     // mirror (as [lumps | mirror]), Y_DEVICE none
     constexpr bool kMirror = sizeof(TL) == 8 && sizeof(TC) == 4;
-    // the fine-level window (two buffers of win rows) sits between the ring and the vectors
-    constexpr bool kWin = sizeof(TL) == 4 && YM != Y_SMEM;
-    float4* wbuf = reinterpret_cast<float4*>(smem_raw + ring_bytes + kRingHeader);
-    unsigned char* ysm = smem_raw + ring_bytes + kRingHeader + (kWin ? 32 * win : 0);
+    unsigned char* ysm = smem_raw + ring_bytes + kRingHeader;
     unsigned char* ydev = reinterpret_cast<unsigned char*>(sd.y);
     unsigned char* yc_raw = YM == Y_DEVICE ? ydev : ysm;
     TL* yc = reinterpret_cast<TL*>(yc_raw);
@@ -742,9 +722,6 @@ __global__ void __launch_bounds__(YM == Y_SMEM ? 256 : kApplyThreadsDev, YM == Y
                issuer_lump = sizeof(TL) == 4 ? issuer_fine : tid == 0;
     int2 next_ch = make_int2(0, 0);
     if ((issuer_fine || issuer_lump) && SLOTS < sd.n_chunks) next_ch = sd.chunks[SLOTS];
-    // fine wavefront levels seen so far: the current one [cur_lo, cur_hi) and the one before
-    int cur_lo = 0, cur_hi = 0, prev_lo = 0, prev_hi = 0, par = 0;
-    bool level_start = true;
     for (int ci = 0; ci < sd.n_chunks; ci++) {
         const int slot = ci % SLOTS;
         // warp-uniform, so that the warp-collective code of the sweep runs on whole warps
@@ -752,20 +729,8 @@ __global__ void __launch_bounds__(YM == Y_SMEM ? 256 : kApplyThreadsDev, YM == Y
         bool fine_chunk = false;
         if (ok) {
             const unsigned char* chunk = ring + (size_t)slot * cap;
-            const int* hdr = reinterpret_cast<const int*>(chunk);
-            const int hf0 = hdr[0], hnf = hdr[1], hflags = hdr[6];
-            fine_chunk = hnf > 0;
-            if (level_start && hnf > 0) {  // a new fine level: the current one becomes the previous
-                prev_lo = cur_lo;
-                prev_hi = cur_hi;
-                cur_lo = cur_hi = hf0;
-                par ^= 1;
-            }
-            if (hnf > 0) cur_hi = max(cur_hi, hf0 + hnf);
-            level_start = (hflags & 1) != 0;
-            const Win w{kWin && win > 0 ? wbuf + par * win : nullptr, wbuf + (par ^ 1) * win, cur_lo, prev_lo, prev_hi,
-                        win};
-            sweep_chunk<TF, TL>(chunk, ci < sd.n_fwd, yf, yc, ycf, w);
+            fine_chunk = reinterpret_cast<const int*>(chunk)[1] > 0;
+            sweep_chunk<TF, TL>(chunk, ci < sd.n_fwd, yf, yc, ycf);
         }
         if (__syncthreads_or(!ok)) {
             // a copy did not land in time: report it, wait (bounded) for the copies still in
@@ -1463,13 +1428,13 @@ size_t apply_ring_bytes(int slots, int chunk) { return (size_t)slots * chunk + k
 size_t apply_lump_bytes(int nc, int prec, bool lump32) { return y_layout(0, nc, prec, lump32).lump_part; }
 
 ApplyConfig apply_local_vectors(int nsub, int all_bytes, int lump_bytes, int smem_slots, int chunk, int sm_smem,
-                                int sms, int force, int win) {
+                                int sms, int force) {
     const long long ring_all = (long long)apply_ring_bytes(smem_slots, chunk) + 1024,
-                    ring2 = (long long)apply_ring_bytes(2, chunk) + 1024 + 32LL * win;
+                    ring2 = (long long)apply_ring_bytes(2, chunk) + 1024;
     const long long fit_all = all_bytes > 0 ? std::min<long long>(2, sm_smem / (all_bytes + ring_all)) : 0;
     const bool lumps_fit = lump_bytes > 0 && 4 * (lump_bytes + ring2) <= sm_smem;
-    const ApplyConfig all{Y_SMEM, all_bytes, smem_slots, chunk, 0}, lumps{Y_LUMPS, lump_bytes, 2, chunk, win},
-        dev{Y_DEVICE, 0, 2, chunk, win};
+    const ApplyConfig all{Y_SMEM, all_bytes, smem_slots, chunk}, lumps{Y_LUMPS, lump_bytes, 2, chunk},
+        dev{Y_DEVICE, 0, 2, chunk};
     if (force == Y_SMEM + 1) return fit_all >= 1 ? all : dev;
     if (force == Y_LUMPS + 1) return lumps_fit ? lumps : dev;
     if (force == Y_DEVICE + 1) return dev;
@@ -1479,34 +1444,32 @@ ApplyConfig apply_local_vectors(int nsub, int all_bytes, int lump_bytes, int sme
 
 namespace {
 template <typename TF, typename TL, int YM, int SLOTS>
-void launch_apply_t(const SysTab* tab, const SubDesc* subs, int nsub, int smem, int win, cudaStream_t st) {
+void launch_apply_t(const SysTab* tab, const SubDesc* subs, int nsub, int smem, cudaStream_t st) {
     static int configured = -1;
     if (configured < smem) {
         cudaFuncSetAttribute(k_apply<TF, TL, YM, SLOTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         configured = smem;
     }
-    k_apply<TF, TL, YM, SLOTS><<<nsub, YM == Y_SMEM ? 256 : kApplyThreadsDev, smem, st>>>(tab, subs, win);
+    k_apply<TF, TL, YM, SLOTS><<<nsub, YM == Y_SMEM ? 256 : kApplyThreadsDev, smem, st>>>(tab, subs);
 }
 template <typename TF, typename TL, int YM>
-void launch_apply_s(const SysTab* tab, const SubDesc* subs, int nsub, int smem, int slots, int win, cudaStream_t st) {
+void launch_apply_s(const SysTab* tab, const SubDesc* subs, int nsub, int smem, int slots, cudaStream_t st) {
     if (slots == 2)
-        launch_apply_t<TF, TL, YM, 2>(tab, subs, nsub, smem, win, st);
+        launch_apply_t<TF, TL, YM, 2>(tab, subs, nsub, smem, st);
     else if (slots == 3)
-        launch_apply_t<TF, TL, YM, 3>(tab, subs, nsub, smem, win, st);
+        launch_apply_t<TF, TL, YM, 3>(tab, subs, nsub, smem, st);
     else
-        launch_apply_t<TF, TL, YM, 4>(tab, subs, nsub, smem, win, st);
+        launch_apply_t<TF, TL, YM, 4>(tab, subs, nsub, smem, st);
 }
 template <typename TF, typename TL>
 void launch_apply_p(const SysTab* tab, const SubDesc* subs, int nsub, ApplyConfig cfg, int slots, cudaStream_t st) {
     const int ring = (int)apply_ring_bytes(slots, cfg.chunk);
-    // the fine-level window of FP32-lump sweeps with local vectors outside shared memory
-    const int win = sizeof(TL) == 4 && cfg.ymode != Y_SMEM ? cfg.win : 0;
     if (cfg.ymode == Y_SMEM)
-        launch_apply_s<TF, TL, Y_SMEM>(tab, subs, nsub, ring + cfg.smem, slots, 0, st);
+        launch_apply_s<TF, TL, Y_SMEM>(tab, subs, nsub, ring + cfg.smem, slots, st);
     else if (cfg.ymode == Y_LUMPS)
-        launch_apply_s<TF, TL, Y_LUMPS>(tab, subs, nsub, ring + 32 * win + cfg.smem, slots, win, st);
+        launch_apply_s<TF, TL, Y_LUMPS>(tab, subs, nsub, ring + cfg.smem, slots, st);
     else
-        launch_apply_s<TF, TL, Y_DEVICE>(tab, subs, nsub, ring + 32 * win, slots, win, st);
+        launch_apply_s<TF, TL, Y_DEVICE>(tab, subs, nsub, ring, slots, st);
 }
 }  // namespace
 
