@@ -306,10 +306,17 @@ def serve_stream(pool, n_req: int, rate: float, precision: str, max_active: int,
     srv.close()
     lat_ms = np.array(lat) * 1e3
     span = max(done_t) - arrivals[0]
+    wall_ms = 1e3 * (time.perf_counter() - t0)
     return {"requests": n_req, "offered_per_s": rate, "p50_ms": float(np.percentile(lat_ms, 50)),
             "p99_ms": float(np.percentile(lat_ms, 99)), "mean_ms": float(lat_ms.mean()),
             "solves_per_s": n_req / span, "reuse_hits": stats["reuse_hits"],
-            "structure_builds": stats["structure_builds"], "steps": stats["steps"]}
+            "structure_builds": stats["structure_builds"], "structure_reuses": stats["structure_reuses"],
+            "steps": stats["steps"], "progress_calls": stats["progress_calls"],
+            # host wall time by phase (the analysis runs on a worker thread, beside the rest)
+            "phases_ms": {"loop_wall": wall_ms, "analysis_worker": stats["analysis_ms"], "admit": stats["admit_ms"],
+                          "of_which_build": stats["build_ms"], "of_which_rekey": stats["rekey_ms"],
+                          "build_factorisation": stats["build_factor_ms"],
+                          "steps": stats["step_ms"], "retire": stats["retire_ms"]}}
 
 
 def run_serving(args, stream):

@@ -320,6 +320,14 @@ typedef struct {
     long long submitted, admitted, completed, steps, reuse_hits, structure_builds, evictions;
     long long resident_bytes, budget_bytes;
     int active, pending;
+    /* where the host time goes (wall clock, ms, cumulative): structure analysis on the worker
+     * thread; admission (every call of it), of which building new systems (allocation, structure
+     * upload, values, factorisation) and re-keying idle systems of the same structure (values and
+     * factorisation only); Krylov steps (control-word reads, batch tables, launches; admission and
+     * retiring excluded); retiring (result download) */
+    double analysis_ms, admit_ms, build_ms, rekey_ms, step_ms, retire_ms;
+    long long progress_calls, structure_reuses;
+    double build_factor_ms; /* of build_ms: the numeric factorisation (the rest: allocation, uploads) */
 } asm_server_stats;
 
 /* Defaults: FP32 factors, GMRES(30), device 0, 64 active systems, 16 cached, budget 0 (85% of the

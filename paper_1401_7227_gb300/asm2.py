@@ -83,7 +83,10 @@ class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_longlong), ("admitted", C.c_longlong), ("completed", C.c_longlong),
                 ("steps", C.c_longlong), ("reuse_hits", C.c_longlong), ("structure_builds", C.c_longlong),
                 ("evictions", C.c_longlong), ("resident_bytes", C.c_longlong), ("budget_bytes", C.c_longlong),
-                ("active", C.c_int), ("pending", C.c_int)]
+                ("active", C.c_int), ("pending", C.c_int), ("analysis_ms", C.c_double), ("admit_ms", C.c_double),
+                ("build_ms", C.c_double), ("rekey_ms", C.c_double), ("step_ms", C.c_double),
+                ("retire_ms", C.c_double), ("progress_calls", C.c_longlong), ("structure_reuses", C.c_longlong),
+                ("build_factor_ms", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -67,6 +67,14 @@ struct DBuf {
         alloc(v.size() * sizeof(T));
         if (!v.empty()) ck(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
     }
+    // as upload, but keeps the allocation when it is large enough (tables rebuilt often: no
+    // cudaFree, which would wait for the device, and no cudaMalloc)
+    template <class T>
+    void upload_reuse(const std::vector<T>& v, cudaStream_t st) {
+        const size_t need = std::max<size_t>(16, v.size() * sizeof(T));
+        if (!p || bytes < need) alloc(need + need / 2);
+        if (!v.empty()) ck(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    }
 };
 
 }  // namespace
@@ -78,6 +86,7 @@ struct asm_ctx {
     int prec = 0;
     int flexible = 0;
     bool lump32 = false;  // lump rows of the ILU factors stored and applied in FP32 (FP32/FP16 fine rows)
+    std::string server_skey;  // serving: structure key of the request this system was built for
     // grid / matrix
     int nx = 0, ny = 0, nz = 0, N = 0;
     bool has_grid = false, has_matrix = false, has_partition = false;
@@ -570,8 +579,9 @@ void upload_symbolic(asm_ctx* h) {
             if (buf.size() % 2) buf.push_back(0);
             fd.pair = reinterpret_cast<const int2*>(put(o.pair));
             fd.ls = reinterpret_cast<const int2*>(put(o.ls));
+            // a copy from pageable host memory returns once the source is staged: buf may be
+            // reused at once, and no stream sync per subdomain is needed
             ck(cudaMemcpyAsync(base, buf.data(), buf.size() * 4, cudaMemcpyHostToDevice, st));
-            sync(h);
         }
         h->d_factdesc.upload(h->fact_desc, st);
     }
@@ -664,7 +674,6 @@ void upload_symbolic(asm_ctx* h) {
         corr_cells.insert(corr_cells.end(), o.corr_cells.begin(), o.corr_cells.end());
         corr_base += (int)o.corr_ptr.size() - 1;
         if (!rl.empty()) ck(cudaMemcpyAsync(base, rl.data(), rl.size() * 4, cudaMemcpyHostToDevice, st));
-        sync(h);
     }
     if (h->opt.local_solver == ASM_LOCAL_EXACT) upload_dense(h, st);
     if (is_nf(h)) upload_nf(h, st);
@@ -1041,6 +1050,7 @@ struct Batch {
     bool has_init = false;  // a system may be in its initial phase (serving: systems join mid-flight)
     std::vector<int> host_ctl;
     int* pinned = nullptr;
+    size_t pinned_cap = 0;
     ~Batch() {
         if (pinned) cudaFreeHost(pinned);
     }
@@ -1077,7 +1087,7 @@ void build_batch(Batch& B, cudaStream_t st) {
             }
         }
         std::stable_sort(nd.begin(), nd.end(), [](const NFDesc& a, const NFDesc& b) { return a.n > b.n; });
-        B.d_nf.upload(nd, st);
+        B.d_nf.upload_reuse(nd, st);
         B.nnf = (int)nd.size();
         asm_ctx* h0 = B.hs[0];
         int dev_smem = 0;
@@ -1087,7 +1097,7 @@ void build_batch(Batch& B, cudaStream_t st) {
     }
     if (B.exact) {
         const std::vector<int2> di = dense_items(sd);
-        B.d_dense.upload(di, st);
+        B.d_dense.upload_reuse(di, st);
         B.ndense = (int)di.size();
     }
     std::vector<BoxItem> cb;
@@ -1106,27 +1116,32 @@ void build_batch(Batch& B, cudaStream_t st) {
         }
         B.two_stage = B.two_stage || h->coarse_mode == 2;
     }
-    B.d_cbox.upload(cb, st);
-    B.d_cgrow.upload(cg, st);
+    B.d_cbox.upload_reuse(cb, st);
+    B.d_cgrow.upload_reuse(cg, st);
     B.ncbox = (int)cb.size();
     B.ncgrow = (int)cg.size();
-    B.d_tab.upload(tabs, st);
-    B.d_vec.upload(vi, st);
-    B.d_row.upload(ri, st);
-    B.d_box.upload(bi, st);
-    B.d_sub.upload(sd, st);
+    B.d_tab.upload_reuse(tabs, st);
+    B.d_vec.upload_reuse(vi, st);
+    B.d_row.upload_reuse(ri, st);
+    B.d_box.upload_reuse(bi, st);
+    B.d_sub.upload_reuse(sd, st);
     {
         const std::vector<int2> ri = restrict_items(sd);
-        B.d_ritems.upload(ri, st);
+        B.d_ritems.upload_reuse(ri, st);
         B.nritems = (int)ri.size();
     }
     B.nvec = (int)vi.size();
     B.nrow = (int)ri.size();
     B.nbox = (int)bi.size();
     B.nsub = (int)sd.size();
-    if (B.pinned) cudaFreeHost(B.pinned);
-    B.pinned = nullptr;
-    ck(cudaMallocHost((void**)&B.pinned, sizeof(int) * C_NCTL * std::max<size_t>(1, B.hs.size())));
+    // pinned control words: grown, never shrunk (pinning host memory is slow)
+    const size_t npin = std::max<size_t>(1, B.hs.size());
+    if (!B.pinned || B.pinned_cap < npin) {
+        if (B.pinned) cudaFreeHost(B.pinned);
+        B.pinned = nullptr;
+        B.pinned_cap = npin + npin / 2;
+        ck(cudaMallocHost((void**)&B.pinned, sizeof(int) * C_NCTL * B.pinned_cap));
+    }
     // kernel variants shared by the whole batch
     B.prec = B.hs.empty() ? 0 : B.hs[0]->prec;
     B.lump32 = !B.hs.empty() && B.hs[0]->lump32;
@@ -1540,7 +1555,9 @@ struct asm_server {
     std::deque<Req*> pending;
     std::vector<Req*> active;
     std::unordered_map<long long, Req*> by_ticket;
-    std::map<long long, asm_ctx*> idle;  // factored systems kept for matrix reuse
+    std::map<long long, asm_ctx*> idle;  // factored systems kept for matrix reuse (keyless ones under
+                                         // negative keys: reusable by structure only)
+    long long next_keyless = -2;
     std::list<long long> lru;            // idle keys, least recently used first
     std::map<long long, bool> key_busy;
     Batch batch;
@@ -1557,6 +1574,10 @@ struct asm_server {
 
 namespace {
 
+double ms_since(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
 void sym_worker(asm_server* S) {
     for (;;) {
         std::string key;
@@ -1571,6 +1592,7 @@ void sym_worker(asm_server* S) {
         }
         SymEntry e;
         const asm_request& q = r->in;
+        const auto t0 = std::chrono::steady_clock::now();
         try {  // an exception must not leave the thread: host memory or threads ran out
             e.err = build_pattern(q.n_cells, q.row_ptr, q.col_idx, q.nnzb, e.pat);
             if (e.err.empty()) {
@@ -1598,6 +1620,7 @@ void sym_worker(asm_server* S) {
         }
         e.ready = true;
         std::lock_guard<std::mutex> lk(S->mu);
+        S->st.analysis_ms += ms_since(t0);
         S->syms[key] = std::move(e);
     }
 }
@@ -1655,7 +1678,10 @@ int build_ctx(asm_server* S, Req* r, const SymEntry& e, asm_ctx** out) {
         upload_symbolic(h);
         h->sym_valid = true;
         h->ws_m = -1;
-        return factor_numeric(h);
+        const auto tf = std::chrono::steady_clock::now();
+        const int fs = factor_numeric(h);
+        S->st.build_factor_ms += ms_since(tf);
+        return fs;
     });
     if (st) {
         asm_destroy(h);
@@ -1663,6 +1689,29 @@ int build_ctx(asm_server* S, Req* r, const SymEntry& e, asm_ctx** out) {
     }
     *out = h;
     return ASM_OK;
+}
+
+// An idle system whose structure key is skey (least recently used first), taken out of the idle
+// set; nullptr if there is none.
+asm_ctx* take_idle_structure(asm_server* S, const std::string& skey) {
+    for (auto it = S->lru.begin(); it != S->lru.end(); ++it) {
+        asm_ctx* h = S->idle[*it];
+        if (h->server_skey != skey) continue;
+        S->idle.erase(*it);
+        S->lru.erase(it);
+        return h;
+    }
+    return nullptr;
+}
+
+// A system already on the device takes a request's matrix: new values, re-assembly and
+// re-factorisation (Section 4: the coarsened matrices are rebuilt for new values, the structure
+// is not), without any allocation or structure upload.
+int rekey_ctx(asm_ctx* h, const Req* r) {
+    return guard(h, [&]() -> int {
+        fill_ell(h, r->in.vals, 0);
+        return factor_numeric(h);
+    });
 }
 
 void admit(asm_server* S) {
@@ -1676,13 +1725,27 @@ void admit(asm_server* S) {
             ++it;
             continue;
         }
+        if (!(key >= 0 && S->idle.count(key)) && r->skey.empty()) r->skey = structure_key(r->in, S->opt.precision);
         if (key >= 0 && S->idle.count(key)) {  // repeated matrix: factors already on the device
             h = S->idle[key];
             S->idle.erase(key);
             S->lru.remove(key);
             S->st.reuse_hits++;
+        } else if (!r->skey.empty() && (h = take_idle_structure(S, r->skey)) != nullptr) {
+            // a new matrix of a structure an idle system already holds on the device
+            const auto t0 = std::chrono::steady_clock::now();
+            const int st = rekey_ctx(h, r);
+            S->st.rekey_ms += ms_since(t0);
+            if (st) {
+                S->resident -= ctx_device_bytes(h);
+                asm_destroy(h);
+                r->info.status = st;
+                r->state = 2;
+                it = S->pending.erase(it);
+                continue;
+            }
+            S->st.structure_reuses++;
         } else {
-            if (r->skey.empty()) r->skey = structure_key(r->in, S->opt.precision);
             SymEntry* e = nullptr;
             {
                 std::lock_guard<std::mutex> lk(S->mu);
@@ -1712,7 +1775,9 @@ void admit(asm_server* S) {
                 ++it;  // no memory now: wait for systems to finish
                 continue;
             }
+            const auto t0 = std::chrono::steady_clock::now();
             const int st = build_ctx(S, r, *e, &h);
+            S->st.build_ms += ms_since(t0);
             if (st) {
                 r->info.status = st;
                 r->state = 2;
@@ -1720,6 +1785,7 @@ void admit(asm_server* S) {
                 continue;
             }
             fresh = true;
+            h->server_skey = r->skey;
         }
         const int st = guard(h, [&]() -> int {
             begin_solve(h, r->b.data(), 0, r->in.rtol, r->in.max_iter);
@@ -1744,6 +1810,7 @@ void admit(asm_server* S) {
 }
 
 void retire(asm_server* S, Req* r, const int* c) {
+    const auto t0 = std::chrono::steady_clock::now();
     asm_ctx* h = r->h;
     r->x.resize(3 * (size_t)h->N);
     guard(h, [&]() -> int {
@@ -1752,25 +1819,28 @@ void retire(asm_server* S, Req* r, const int* c) {
     });
     r->state = 2;
     r->h = nullptr;
-    const long long key = r->in.matrix_key;
-    if (key >= 0) {
-        S->key_busy[key] = false;
-        if (S->opt.max_cached > 0) {
-            S->idle[key] = h;
-            S->lru.push_back(key);
-            while ((int)S->idle.size() > S->opt.max_cached) {
-                const long long k0 = S->lru.front();
-                S->lru.pop_front();
-                S->resident -= ctx_device_bytes(S->idle[k0]);
-                asm_destroy(S->idle[k0]);
-                S->idle.erase(k0);
-                S->st.evictions++;
-            }
-            return;
+    long long key = r->in.matrix_key;
+    if (key >= 0) S->key_busy[key] = false;
+    if (S->opt.max_cached > 0) {
+        // kept on the device: a later request with the same matrix key reuses the factors, one with
+        // the same structure the allocations and the structure (keyless systems under negative
+        // keys, reusable by structure only)
+        if (key < 0) key = S->next_keyless--;
+        S->idle[key] = h;
+        S->lru.push_back(key);
+        while ((int)S->idle.size() > S->opt.max_cached) {
+            const long long k0 = S->lru.front();
+            S->lru.pop_front();
+            S->resident -= ctx_device_bytes(S->idle[k0]);
+            asm_destroy(S->idle[k0]);
+            S->idle.erase(k0);
+            S->st.evictions++;
         }
+    } else {
+        S->resident -= ctx_device_bytes(h);
+        asm_destroy(h);
     }
-    S->resident -= ctx_device_bytes(h);
-    asm_destroy(h);
+    S->st.retire_ms += ms_since(t0);
 }
 
 }  // namespace
@@ -2350,9 +2420,14 @@ int asm_server_progress(asm_server_handle S, int max_steps, int* n_active, int* 
         cudaGetLastError();
         return ASM_ERR_CUDA;
     }
+    S->st.progress_calls++;
     try {
+        const auto ta = std::chrono::steady_clock::now();
         admit(S);
+        S->st.admit_ms += ms_since(ta);
         for (int step = 0; step < max_steps && !S->active.empty(); step++) {
+            const auto ts = std::chrono::steady_clock::now();
+            const double retire0 = S->st.retire_ms, admit0 = S->st.admit_ms;
             if (S->dirty) {
                 S->batch.hs.clear();
                 for (Req* r : S->active) S->batch.hs.push_back(r->h);
@@ -2376,7 +2451,9 @@ int asm_server_progress(asm_server_handle S, int max_steps, int* n_active, int* 
             }
             if (S->dirty) {  // membership changed: retired systems leave, waiting ones join
                 S->active.swap(keep);
+                const auto ti = std::chrono::steady_clock::now();
                 admit(S);
+                S->st.admit_ms += ms_since(ti);
                 if (S->active.empty()) break;
                 S->batch.hs.clear();
                 for (Req* r : S->active) S->batch.hs.push_back(r->h);
@@ -2392,6 +2469,7 @@ int asm_server_progress(asm_server_handle S, int max_steps, int* n_active, int* 
             }
             launch_step(S->batch, kmax, S->stream, nullptr);
             S->st.steps++;
+            S->st.step_ms += ms_since(ts) - (S->st.retire_ms - retire0) - (S->st.admit_ms - admit0);
         }
     } catch (const CudaFail& e) {
         return e.status;
@@ -2422,6 +2500,7 @@ int asm_server_result(asm_server_handle S, long long ticket, double* x, asm_solv
 
 int asm_server_get_stats(asm_server_handle S, asm_server_stats* out) {
     if (!S || !out) return ASM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);  // the analysis thread adds to analysis_ms
     S->st.resident_bytes = (long long)S->resident;
     S->st.budget_bytes = (long long)S->budget;
     S->st.active = (int)S->active.size();

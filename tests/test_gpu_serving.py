@@ -104,3 +104,27 @@ def test_bad_request_is_rejected():
         assert e.value.status == 1, kw
     assert srv.stats()["submitted"] == 0
     srv.close()
+
+
+def test_new_values_on_a_resident_structure_equal_results_alone():
+    """A request whose matrix is new but whose structure an idle system already holds takes that
+    system over (new values, re-assembly and re-factorisation on the device, no allocation): its
+    result equals the new matrix solved alone, and so does a keyless request after it."""
+    (g, part, ov, sd) = CASES[1]
+    first = synth.grid_jacobian(*g, seed=sd)
+    second = synth.grid_jacobian(*g, seed=sd + 100)   # same grid and pattern, other values
+    third = synth.grid_jacobian(*g, seed=sd + 200)
+    srv = asm2.Server(precision="fp32", max_cached=4)
+    out = drain(srv, [srv.submit(first, first.b, partition=part, overlap=ov, matrix_key=10)])
+    out.update(drain(srv, [srv.submit(second, second.b, partition=part, overlap=ov, matrix_key=11)]))
+    t3 = srv.submit(third, third.b, partition=part, overlap=ov)   # keyless
+    out.update(drain(srv, [t3]))
+    st = srv.stats()
+    assert st["structure_builds"] == 1 and st["structure_reuses"] == 2
+    for (x, info), s in zip(out.values(), (first, second, third)):
+        xa, ia = alone(s, s.b, part, ov)
+        assert info["converged"] and info["iterations"] == ia["iterations"]
+        np.testing.assert_array_equal(x, xa)
+    # the phase timers add up to something and the structure was analysed once
+    assert st["analysis_ms"] > 0 and st["step_ms"] > 0 and st["progress_calls"] > 0
+    srv.close()
