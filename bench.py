@@ -500,6 +500,62 @@ def run_profile_nf(args):
     return 0
 
 
+def run_profile_kernels(args):
+    """Case for one ncu capture of every kernel family (time and DRAM bytes per launch): on
+    128 x 128 x 32 (524,288 cells, 16 x 16 x 1 subdomains, overlap 2; inputs larger than L2):
+    the ILU path with FP32 factors (set-up, applies, a few GMRES steps), ORTHOMIN, the two-level
+    coarse correction, nested factorisation; exact local solves on 32 x 32 x 16 (16 subdomains);
+    and two systems through the batched per-projection Gram-Schmidt path."""
+    import torch
+    from paper_1401_7227_gb300 import asm2
+    from paper_1401_7227_gb300 import build as lib_build
+    lib_build.build()
+    s = synth.grid_jacobian(128, 128, 32, 3, 2.0)
+    b = torch.from_numpy(s.b).cuda()
+
+    def make(local="colsum", prec="fp32", krylov="gmres", near_width=2, far="partition", sys=s, part=(16, 16, 1),
+             ov=2, coarse=None):
+        sol = asm2.Solver(precision=prec, restart=30, local_solver=local, krylov=krylov)
+        sol.set_grid(sys.nx, sys.ny, sys.nz)
+        sol.set_matrix(sys.row_ptr, sys.col_idx, sys.vals)
+        sol.set_partition(*part, ov, near_width, (2, 2, 2), far)
+        if coarse:
+            sol.set_coarse(coarse)
+        sol.factor()
+        return sol
+
+    out = {}
+    sol = make()
+    for _ in range(2):
+        sol.apply(b)
+    x, info = sol.solve(b, 1e-8, 6)
+    out["ilu_fp32"] = info
+    sol.close()
+    sol = make(krylov="orthomin")
+    out["orthomin"] = sol.solve(b, 1e-8, 4)[1]
+    sol.close()
+    sol = make(prec="fp64", near_width=0, far="none", coarse="two-level")
+    sol.apply(b)
+    out["two_level"] = sol.solve(b, 1e-8, 3)[1]
+    sol.close()
+    sol = make(local="nf_colsum", near_width=0, far="none")
+    sol.apply(b)
+    out["nf"] = sol.solve(b, 1e-8, 3)[1]
+    sol.close()
+    small = synth.grid_jacobian(32, 32, 16, 4)
+    sol = make(local="exact", prec="fp64", sys=small, part=(4, 4, 1), ov=1)
+    sol.apply(torch.from_numpy(small.b).cuda())
+    out["exact"] = sol.solve(torch.from_numpy(small.b).cuda(), 1e-8, 3)[1]
+    sol.close()
+    bs = [make(sys=small, part=(4, 4, 1), ov=1) for _ in range(2)]
+    out["batch"] = asm2.solve_batch(bs, [torch.from_numpy(small.b).cuda()] * 2, 1e-8, 3)[1]
+    for x_ in bs:
+        x_.close()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": "kernels_grid128x128x32_k256", "infos": out}, default=str))
+    return 0
+
+
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64 (no measured figure for it is given)
 
 
@@ -816,6 +872,7 @@ def main():
     ap.add_argument("--batch-systems", type=int, default=256)
     ap.add_argument("--profile-case", action="store_true", help="small case for ncu captures")
     ap.add_argument("--profile-nf", action="store_true", help="nested-factorisation apply case for ncu captures")
+    ap.add_argument("--profile-kernels", action="store_true", help="every kernel family, for one ncu capture")
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--serve-warm", type=int, default=300)
     ap.add_argument("--serve-rate", type=float, default=200.0)
@@ -828,6 +885,8 @@ def main():
         return run_profile_case(args)
     if args.profile_nf:
         return run_profile_nf(args)
+    if args.profile_kernels:
+        return run_profile_kernels(args)
     return run_gpu(args)
 
 
