@@ -366,6 +366,13 @@ def run_batch(args, stream):
         solvers.append(sol)
         bs.append(torch.from_numpy(s.b).cuda())
     infos = None
+    tiling = None
+    if not args.no_tune:
+        rep = asm2.tune_tiling_batch(solvers, bs, 1e-8, 3000)
+        tiling = {"rule_ms_per_batch": rep["rule_ms"], "chosen": rep["best"],
+                  "chosen_vs_rule": rep["best"]["apply_ms"] / rep["rule_ms"],
+                  "measured": [[r["chunk_kb"], r["chunk_max_kb"], r["placement"], r["slots"], r["ctas_per_sm"],
+                                round(r["apply_ms"], 3)] for r in rep["measured"]]}
     for _ in range(max(1, args.warmup)):
         xs, infos = asm2.solve_batch(solvers, bs, 1e-8, 3000)
     torch.cuda.synchronize()
@@ -379,12 +386,21 @@ def run_batch(args, stream):
     its = [i["iterations"] for i in infos]
     worst = max(i["rel_residual"] for i in infos)
     cells = sum(s.n_cells for s in systems)
+    st0 = solvers[0].stats()
+    caps = {}
+    for sol in solvers:
+        c = sol.stats()["chunk_max_kb"]
+        caps[c] = caps.get(c, 0) + 1
+    apply_tiling = {"systems_per_chunk_kb": {str(k): v for k, v in sorted(caps.items())},
+                    "ring_slot_kb": st0["last_solve_chunk_kb"], "placement": st0["last_solve_placement"],
+                    "slots": st0["last_solve_slots"]}
     for sol in solvers:
         sol.close()
     return {"workload": f"{n_sys} systems, 256-55,296 cells each (total {cells}), K 4-64, ov 1, FP32 factors, GMRES(20)",
             "ms_per_batch": ms, "solves_per_s": 1e3 * n_sys / ms, "cells": cells,
             "iterations_mean": float(np.mean(its)), "iterations_max": int(max(its)),
-            "all_converged": all(i["converged"] for i in infos), "worst_true_rel_residual": worst}
+            "all_converged": all(i["converged"] for i in infos), "worst_true_rel_residual": worst,
+            "tiling": tiling, "apply_tiling": apply_tiling}
 
 
 def nf_apply_bytes(w, elem: int) -> int:
@@ -453,8 +469,7 @@ def run_nf(args, stream, w, w_system, vals_d, b_d):
 def run_profile_case(args):
     """Small case for ncu captures: 128 x 128 x 32 (16 x 16 x 1 subdomains, overlap 2), three
     preconditioner applies then one GMRES solve.  The apply runs with the local-vector placement the
-    1M-cell workload gets (all local vectors in device memory, 128-thread CTAs, 24 KB ring slots):
-    at half size the automatic choice would keep everything in shared memory."""
+    1M-cell workload's online tuner picks (all local vectors in shared memory, four ring slots)."""
     import torch
     from paper_1401_7227_gb300 import asm2
     from paper_1401_7227_gb300 import build as lib_build
@@ -465,7 +480,7 @@ def run_profile_case(args):
     sol.set_matrix(s.row_ptr, s.col_idx, s.vals)
     sol.set_partition(16, 16, 1, 2)
     sol.factor()
-    sol.set_tuning(apply_smem="device")
+    sol.set_tuning(apply_smem="shared")
     b = torch.from_numpy(s.b).cuda()
     for _ in range(3):
         sol.apply(b)
@@ -571,6 +586,28 @@ def spmv_roofline(res, system, steps: int):
     return {"kernel": "k_spmv", "bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
             "frac": ach / FP64_NOMINAL_TFLOPS, "peak_kind": "nominal FP64", "launch_ms": ms,
             "hbm_frac": (76.0 * system.col_idx.size + 48.0 * system.n_cells) / (ms * 1e-3) / 1e9 / peaks()[0]}
+
+
+def ortho_roofline(res, system, steps: int, m: int):
+    """Modified Gram-Schmidt (k_ortho_coop, one cooperative launch per Arnoldi step; the timer also
+    holds the small per-step control kernels).  Step j of a cycle makes j + 2 fused passes over
+    the 3N-vector w, each 2 FP64 FMAs per element (w -= h v_prev; dot with the next v, or the
+    norm), and one scaling pass: 4 * 3N * (j + 2) + 3N flops.  It reads v_0..v_j, w once and writes
+    v_{j+1}: 8 * 3N * (j + 3) algorithmic bytes (w stays in L2 between passes).  Bound: the FP64
+    pipe, against the nominal 1.25 TFLOP/s."""
+    info = res["info"]
+    n3 = 3.0 * system.n_cells
+    flops = byt = 0.0
+    for L in cycles(info["iterations"], m):
+        for j in range(L):
+            flops += 4.0 * n3 * (j + 2) + n3
+            byt += 8.0 * n3 * (j + 3)
+    sec = res["prof"]["ortho_ms"] / steps * 1e-3
+    ach = flops / sec / 1e12
+    return {"kernel": "k_ortho_coop", "bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS,
+            "unit": "TFLOP/s", "frac": ach / FP64_NOMINAL_TFLOPS, "peak_kind": "nominal FP64",
+            "ms_per_solve": sec * 1e3, "launch_ms": sec * 1e3 / max(1, info["iterations"]),
+            "hbm_frac": byt / sec / 1e9 / peaks()[0]}
 
 
 def apply_traffic(alg_bytes: int):
@@ -735,8 +772,19 @@ def run_gpu(args):
         for pv in (("fp64", "fp64"), ("fp32", "fp32"), ("fp16s", "fp32"), ("fp32", "fp64")):
             if vkey(*pv) != main_key:
                 variants.append(pv)
+    def tiling_summary(rep):
+        """the tuner's choice against the default tiling, and every measured configuration as
+        [chunk KB asked (0: rule), largest chunk KB, placement, ring slots, CTAs per SM, ms]"""
+        if rep is None:
+            return None
+        b = rep["best"]
+        return {"rule_ms": rep["rule_ms"], "chosen": b, "chosen_vs_rule": b["apply_ms"] / rep["rule_ms"],
+                "measured": [[r["chunk_kb"], r["chunk_max_kb"], r["placement"], r["slots"], r["ctas_per_sm"],
+                              round(r["apply_ms"], 4)] for r in rep["measured"]]}
+
     for prec, lumps in variants:
         sol = make_solver(prec, lumps)
+        tiling = None if args.no_tune else tiling_summary(sol.tune_tiling(reps=7))
         for _ in range(args.warmup):
             step(sol)
         sol.reset_profile()
@@ -760,7 +808,7 @@ def run_gpu(args):
         r = system.b - O.spmv(system.row_ptr, system.col_idx, system.vals, xh)
         results[vkey(prec, lumps)] = {"ms": ms, "info": infos[-1], "prof": prof, "stats": st, "clocks": clk.summary(),
                          "host_check_relres": float(np.linalg.norm(r) / np.linalg.norm(system.b)), "solver": sol,
-                         "x": xh}
+                         "x": xh, "tiling": tiling}
 
     main = results[main_key]
     sol = main["solver"]
@@ -817,14 +865,18 @@ def run_gpu(args):
         "precisions": {p_: {"ms_per_solve": r_["ms"], "iterations": r_["info"]["iterations"],
                             "converged": bool(r_["info"]["converged"]), "true_rel_residual": r_["info"]["rel_residual"],
                             "host_check_rel_residual": r_["host_check_relres"],
-                            "err_vs_fp64": err_vs_fp64(r_["x"])}
+                            "err_vs_fp64": err_vs_fp64(r_["x"]),
+                            "tiling": None if r_["tiling"] is None else
+                            {k: r_["tiling"][k] for k in ("rule_ms", "chosen", "chosen_vs_rule")}}
                        for p_, r_ in results.items() if p_ != main_key},
         "err_vs_fp64": err_vs_fp64(main["x"]),
+        "tiling": main["tiling"],
+        "apply_tiling": {k: st[k] for k in ("chunk_max_kb", "stream_chunks", "apply_placement", "apply_slots")},
         "breakdown_ms_per_solve": {k: prof[k] / args.steps for k in ("apply_ms", "spmv_ms", "ortho_ms", "factor_ms")},
         "roofline": {"bound": "hbm", "kernel": "precond apply (boxsum + fused local solves)", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": apply_traffic(alg_bytes),
                      "alg_bytes_per_launch": alg_bytes, "launch_ms": apply_ms, "peak_kind": peak_kind},
-        "rooflines_other": [spmv_roofline(main, system, args.steps)],
+        "rooflines_other": [spmv_roofline(main, system, args.steps), ortho_roofline(main, system, args.steps, w.restart)],
         "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(system.vals.nbytes + system.b.nbytes),
                 "d2h_bytes_per_step": int(system.b.nbytes)},
         "gpu_launches": int(launches),
@@ -873,6 +925,7 @@ def main():
     ap.add_argument("--profile-case", action="store_true", help="small case for ncu captures")
     ap.add_argument("--profile-nf", action="store_true", help="nested-factorisation apply case for ncu captures")
     ap.add_argument("--profile-kernels", action="store_true", help="every kernel family, for one ncu capture")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default tiling (no asm_tune_tiling)")
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--serve-warm", type=int, default=300)
     ap.add_argument("--serve-rate", type=float, default=200.0)

@@ -133,6 +133,16 @@ typedef struct {
                                     storage precision, plus r read and z written (48 N) */
     double setup_ms;             /* host symbolic analysis time of the last asm_factor */
     double factor_ms;            /* device assembly + factorisation time of the last asm_factor */
+    /* the ILU apply's tiling (0 for other local solvers): */
+    int chunk_max_kb;            /* largest stream-chunk capacity of the subdomains (a ring slot) */
+    long long stream_chunks;     /* stream chunks of all subdomains, both sweeps */
+    int apply_placement;         /* placement a single-system apply runs with now: 3 all in shared
+                                    memory, 2 lumps, 0 device (the online tuner's choice once made) */
+    int apply_slots;             /* its ring slots */
+    int last_solve_placement;    /* placement the last asm_solve / asm_solve_batch with this handle
+                                    ran its applies in (a batch shares one; -1: no solve yet) */
+    int last_solve_slots;        /* its ring slots */
+    int last_solve_chunk_kb;     /* its ring slot size: the largest chunk capacity of the batch */
 } asm_stats;
 
 /* Device time of each part of the solver, accumulated while profiling is on (CUDA events on the
@@ -233,14 +243,15 @@ int asm_solve_batch(asm_handle* hs, int n, const double* const* b, double* const
 /* Sizes and timings of the current factorisation. */
 int asm_get_stats(asm_handle h, asm_stats* st);
 
-/* Tuning switches of the kernels (none changes the arithmetic; results are bitwise the same):
+/* Tuning switches of the kernels (none changes the arithmetic of a fine row; results are bitwise
+ * the same, except where ASM_TUNE_CHUNK_KB says otherwise):
  *   ASM_TUNE_APPLY_SMEM  where the apply keeps each subdomain's local vectors.  1 (default):
- *                        all in shared memory (256-thread CTAs, two per SM) when every subdomain CTA
- *                        of the launch then runs at once; else the lump vector in shared memory and
- *                        the fine-row vector in device memory (128-thread CTAs, four per SM) when
- *                        that fits; else all in device memory (128-thread CTAs).  0: all in device
- *                        memory; 2: lumps in shared memory; 3: all in shared memory (2 and 3 fall
- *                        back to device memory when they do not fit);
+ *                        all in shared memory (256-thread CTAs) when every subdomain CTA of the
+ *                        launch then runs at once; else the lump vector in shared memory and the
+ *                        fine-row vector in device memory when that fits; else all in device memory
+ *                        (256-thread CTAs).  0: all in device memory; 2: lumps in shared memory;
+ *                        3: all in shared memory (2 and 3 fall back to device memory when they do
+ *                        not fit);
  *   ASM_TUNE_COOP_ORTHO  1 (default) runs the Gram-Schmidt step of a single-system solve in one
  *                        cooperative launch, 0 in one launch per projection.
  * Errors: INVALID_ARG for an unknown key or value. */
@@ -253,15 +264,67 @@ typedef enum {
                               Placements give bitwise equal results.  0: the placement rule only. */
     ASM_TUNE_GRAPHS = 3,   /* 1 (default): batched solves replay each Krylov step as a captured
                               CUDA graph (one per projection count); 0: plain launches */
-    ASM_TUNE_WAIT_LIMIT = 4 /* failure-detection hook (0..30, default 22): the apply kernels (ILU
+    ASM_TUNE_WAIT_LIMIT = 4, /* failure-detection hook (0..30, default 22): the apply kernels (ILU
                               sweeps and nested factorisation) give up waiting for a factor-stream
                               copy after 2^value polls, 0 polls for value 0, and the call returns
                               ASM_ERR_TIMEOUT without a result.  Before it leaves, each CTA waits
                               with the full bound for its own copies in flight, so the device stays
                               usable.  Value 0 makes every wait expire at once, which tests the
                               timeout path without a fault; restore 22 afterwards */
+    ASM_TUNE_CHUNK_KB = 5,   /* stream-chunk capacity of the ILU factor stream (the wavefront
+                              levels' rows are cut into chunks of at most this size; one ring slot
+                              of the apply holds one chunk).  0 (default): each subdomain's own
+                              rule (its largest fine level, 8..24 KB); 8, 12, 16, 20 or 24: that
+                              capacity in KB for every subdomain, raised where one row needs more.
+                              Takes effect at the next asm_factor, which then rebuilds the
+                              symbolic structure.  Fine rows compute the same bits under every
+                              capacity; FP64 lump rows may round differently (their entry slots
+                              are chosen per chunk) */
+    ASM_TUNE_APPLY_SLOTS = 6 /* ring slots of the apply with all local vectors in shared memory:
+                              0 (default) as many as keep two CTAs per SM, else 4; 2, 3 or 4 */
 } asm_tune_key;
 int asm_set_tuning(asm_handle h, int key, int value);
+
+/* The tiling tuner (no counterpart in the paper, which leaves the blocking of the local solves to
+ * the implementation).  For a factored handle with ILU(0) local solves it measures the
+ * preconditioner apply under every stream-chunk capacity (ASM_TUNE_CHUNK_KB: the rule, 8, 12, 16,
+ * 20, 24 KB; capacities that give every subdomain the same chunks as an earlier one are skipped)
+ * crossed with every placement of the local vectors that fits (all in shared memory with 2, 3 or
+ * 4 ring slots, lumps in shared memory, all in device memory), each as the median of `reps` timed
+ * applies after two untimed ones.  It then leaves the fastest in place (ASM_TUNE_CHUNK_KB,
+ * ASM_TUNE_APPLY_SLOTS and ASM_TUNE_APPLY_SMEM set, the online placement tuner off) with the
+ * handle factored again, and reports every measurement.  Each capacity costs one symbolic rebuild
+ * and factorisation, so this is a set-up step to run once per structure.  The handle's values are
+ * factored again as they are; the Krylov workspace is reused.
+ * Errors: STATE if not factored; INVALID_ARG for another local solver, reps < 1 or out == NULL. */
+#define ASM_TILING_MAX 48
+typedef struct {
+    int chunk_kb;      /* ASM_TUNE_CHUNK_KB value (0: the per-subdomain rule) */
+    int chunk_max_kb;  /* the largest capacity the subdomains got (a ring slot's size) */
+    long long chunks;  /* stream chunks of all subdomains, both sweeps */
+    int placement;     /* ASM_TUNE_APPLY_SMEM value: 3 all in shared memory, 2 lumps, 0 device */
+    int slots;         /* ring slots */
+    int ctas_per_sm;   /* apply CTAs resident per SM */
+    double apply_ms;   /* median time of one preconditioner apply (all its kernels) */
+} asm_tiling_entry;
+typedef struct {
+    int n;               /* entries measured */
+    int best;            /* index of the entry left in place */
+    double rule_ms;      /* the default (rule capacity, automatic placement), measured first */
+    asm_tiling_entry e[ASM_TILING_MAX];
+} asm_tiling_report;
+int asm_tune_tiling(asm_handle h, int reps, asm_tiling_report* out);
+
+/* The same search for a batch (asm_solve_batch's arguments): every handle gets each stream-chunk
+ * capacity in turn (one symbolic rebuild and factorisation each), and the batch is solved twice
+ * per capacity, the first solve untimed (its first steps run the online placement tuner), the
+ * second timed.  Each entry's apply_ms holds that timed batched solve's time, and its placement
+ * and slots are what the online tuner chose for the batch; rule_ms is the rule's entry.  The
+ * fastest capacity is left in place (handles factored again); placements stay with the online
+ * tuner.  x receives the last solve's iterates.  Errors as asm_solve_batch, plus STATE if a
+ * handle is not factored and INVALID_ARG for another local solver or out == NULL. */
+int asm_tune_tiling_batch(asm_handle* hs, int n, const double* const* b, double* const* x, double rtol, int max_iter,
+                          int on_device, asm_tiling_report* out);
 
 /* Profiling switch (0/1): when on, launch groups are bracketed by CUDA events. */
 int asm_set_profiling(asm_handle h, int enable);

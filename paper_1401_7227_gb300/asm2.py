@@ -22,13 +22,16 @@ PREC = {"fp64": 0, "fp32": 1, "fp16s": 2}
 LUMPS = {"fp64": 0, "fp32": 1}
 FAR = {"none": 0, "partition": 1, "boxes": 2}
 COARSE = {"none": 0, "two-level": 1, "two-stage": 2}
+#: placements of the apply's local vectors (ASM_TUNE_APPLY_SMEM values)
+PLACEMENT_NAMES = {0: "device", 2: "lumps", 3: "shared", -1: None}
 
 #: every symbol include/asm2.h declares
 EXPORTS = [
     "asm_default_options", "asm_error_string", "asm_create", "asm_destroy", "asm_set_grid", "asm_set_matrix_bsr",
     "asm_update_values", "asm_set_partition_boxes", "asm_set_coarse_correction", "asm_factor", "asm_apply_precond", "asm_spmv", "asm_solve",
     "asm_solve_batch", "asm_get_stats", "asm_get_error_location", "asm_get_local_info", "asm_get_local_map",
-    "asm_get_local_matrix", "asm_get_local_factors", "asm_set_profiling", "asm_get_profile", "asm_reset_profile", "asm_set_tuning", "asm_residual_noalloc",
+    "asm_get_local_matrix", "asm_get_local_factors", "asm_set_profiling", "asm_get_profile", "asm_reset_profile", "asm_set_tuning", "asm_tune_tiling", "asm_tune_tiling_batch",
+    "asm_residual_noalloc",
     "asm_server_default_options", "asm_server_create", "asm_server_submit", "asm_server_progress",
     "asm_server_result", "asm_server_get_stats", "asm_server_destroy",
 ]
@@ -52,10 +55,15 @@ class Stats(C.Structure):
                 ("max_levels", C.c_int), ("local_blocks", C.c_longlong), ("factor_bytes", C.c_longlong),
                 ("apply_index_bytes", C.c_longlong), ("matrix_bytes", C.c_longlong), ("alg_apply_bytes", C.c_longlong),
                 ("setup_ms", C.c_double),
-                ("factor_ms", C.c_double)]
+                ("factor_ms", C.c_double), ("chunk_max_kb", C.c_int), ("stream_chunks", C.c_longlong),
+                ("apply_placement", C.c_int), ("apply_slots", C.c_int), ("last_solve_placement", C.c_int),
+                ("last_solve_slots", C.c_int), ("last_solve_chunk_kb", C.c_int)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        for k in ("apply_placement", "last_solve_placement"):
+            d[k] = PLACEMENT_NAMES.get(d[k], d[k])
+        return d
 
 
 class Profile(C.Structure):
@@ -64,6 +72,24 @@ class Profile(C.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class TilingEntry(C.Structure):
+    _fields_ = [("chunk_kb", C.c_int), ("chunk_max_kb", C.c_int), ("chunks", C.c_longlong), ("placement", C.c_int),
+                ("slots", C.c_int), ("ctas_per_sm", C.c_int), ("apply_ms", C.c_double)]
+
+
+TILING_MAX = 48
+
+
+class TilingReport(C.Structure):
+    _fields_ = [("n", C.c_int), ("best", C.c_int), ("rule_ms", C.c_double), ("e", TilingEntry * TILING_MAX)]
+
+    def as_dict(self):
+        rows = [{"chunk_kb": e.chunk_kb, "chunk_max_kb": e.chunk_max_kb, "chunks": e.chunks,
+                 "placement": PLACEMENT_NAMES.get(e.placement, e.placement), "slots": e.slots,
+                 "ctas_per_sm": e.ctas_per_sm, "apply_ms": e.apply_ms} for e in self.e[:self.n]]
+        return {"rule_ms": self.rule_ms, "best": rows[self.best] if rows else None, "measured": rows}
 
 
 class ServerOptions(C.Structure):
@@ -142,6 +168,8 @@ def load(build_if_missing: bool = False):
     L.asm_get_profile.argtypes = [P, C.POINTER(Profile)]
     L.asm_reset_profile.argtypes = [P]
     L.asm_set_tuning.argtypes = [P, I, I]
+    L.asm_tune_tiling.argtypes = [P, I, C.POINTER(TilingReport)]
+    L.asm_tune_tiling_batch.argtypes = [P, I, P, P, D, I, I, C.POINTER(TilingReport)]
     L.asm_residual_noalloc.argtypes = [P, P, P, P, P]
     L.asm_server_default_options.argtypes = [C.POINTER(ServerOptions)]
     L.asm_server_default_options.restype = None
@@ -326,12 +354,20 @@ class Solver:
         return s.as_dict()
 
     def set_tuning(self, apply_smem: bool | str | None = None, coop_ortho: bool | None = None,
-                   autotune: bool | None = None, graphs: bool | None = None, wait_limit_log2: int | None = None):
+                   autotune: bool | None = None, graphs: bool | None = None, wait_limit_log2: int | None = None,
+                   chunk_kb: int | None = None, apply_slots: int | None = None):
         """apply_smem: True / "auto" (default placement), False / "device", "lumps" (lump vector in
         shared memory), "shared" (all local vectors in shared memory); see ASM_TUNE_APPLY_SMEM.
         autotune: the online placement tuner (ASM_TUNE_AUTOTUNE); graphs: CUDA graphs for batched
         solves (ASM_TUNE_GRAPHS); wait_limit_log2: the apply kernels' chunk waits give up after
-        2^value polls (0: at once; default 22), a failure-detection hook (ASM_TUNE_WAIT_LIMIT)."""
+        2^value polls (0: at once; default 22), a failure-detection hook (ASM_TUNE_WAIT_LIMIT).
+        chunk_kb: stream-chunk capacity (0 rule, 8..24 KB; ASM_TUNE_CHUNK_KB, applied by the next
+        factor()); apply_slots: ring slots with all local vectors in shared memory (0 rule, 2..4;
+        ASM_TUNE_APPLY_SLOTS)."""
+        if chunk_kb is not None:
+            _check(load().asm_set_tuning(self._h, 5, int(chunk_kb)), "set_tuning")
+        if apply_slots is not None:
+            _check(load().asm_set_tuning(self._h, 6, int(apply_slots)), "set_tuning")
         if wait_limit_log2 is not None:
             _check(load().asm_set_tuning(self._h, 4, int(wait_limit_log2)), "set_tuning")
         if autotune is not None:
@@ -344,6 +380,13 @@ class Solver:
             _check(load().asm_set_tuning(self._h, 0, v), "set_tuning")
         if coop_ortho is not None:
             _check(load().asm_set_tuning(self._h, 1, int(coop_ortho)), "set_tuning")
+
+    def tune_tiling(self, reps: int = 9) -> dict:
+        """asm_tune_tiling: measure the apply under every stream-chunk capacity and placement, leave
+        the fastest in place (the handle stays factored) and return the measurements."""
+        rep = TilingReport()
+        _check(load().asm_tune_tiling(self._h, int(reps), C.byref(rep)), "tune_tiling")
+        return rep.as_dict()
 
     def set_profiling(self, on: bool = True):
         _check(load().asm_set_profiling(self._h, 1 if on else 0), "set_profiling")
@@ -391,30 +434,49 @@ class Solver:
         return lu, dp
 
 
-def solve_batch(solvers, bs, rtol: float = 1e-8, max_iter: int = 1000):
-    """Solve several factored systems in the same launches; returns ([x], [info])."""
+def _batch_args(solvers, bs, what):
+    """handle array, b and x pointer arrays, the x arrays (allocated here), on-device flag, and the
+    arrays the pointers refer to (kept alive by the caller)"""
     n = len(solvers)
     if len(bs) != n:
-        raise ValueError("solve_batch: one right-hand side per solver")
+        raise ValueError(f"{what}: one right-hand side per solver")
     hs = (C.c_void_p * n)(*[s.handle for s in solvers])
     on_dev = all(_is_torch(b) and b.is_cuda for b in bs)
     if on_dev:
         import torch
-        bi = [_values(b, 3 * s.n_cells, "solve_batch")[0] for s, b in zip(solvers, bs)]
+        bi = [_values(b, 3 * s.n_cells, what)[0] for s, b in zip(solvers, bs)]
         xs = [torch.empty_like(b) for b in bi]
         bp = (C.c_void_p * n)(*[b.data_ptr() for b in bi])
         xp = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
     else:  # all on the host (CUDA tensors in a mixed list are copied to the host)
         bi = [np.ascontiguousarray(b.cpu() if _is_torch(b) else b, dtype=np.float64) for b in bs]
-        bi = [_values(b, 3 * s.n_cells, "solve_batch")[0] for s, b in zip(solvers, bi)]
+        bi = [_values(b, 3 * s.n_cells, what)[0] for s, b in zip(solvers, bi)]
         xs = [np.empty_like(b) for b in bi]
         bp = (C.c_void_p * n)(*[b.ctypes.data for b in bi])
         xp = (C.c_void_p * n)(*[x.ctypes.data for x in xs])
+    return hs, bp, xp, xs, on_dev, bi
+
+
+def solve_batch(solvers, bs, rtol: float = 1e-8, max_iter: int = 1000):
+    """Solve several factored systems in the same launches; returns ([x], [info])."""
+    n = len(solvers)
+    hs, bp, xp, xs, on_dev, _keep = _batch_args(solvers, bs, "solve_batch")
     infos = (SolveInfo * n)()
     st = load().asm_solve_batch(hs, n, bp, xp, rtol, max_iter, 1 if on_dev else 0, infos)
     if st not in (ASM_OK, 4):
         raise ASMError(st, "solve_batch")
     return xs, [i.as_dict() for i in infos]
+
+
+def tune_tiling_batch(solvers, bs, rtol: float = 1e-8, max_iter: int = 1000) -> dict:
+    """asm_tune_tiling_batch: time a batched solve under every stream-chunk capacity, leave the
+    fastest in place and return the measurements (apply_ms: the batched solve's time)."""
+    n = len(solvers)
+    hs, bp, xp, _xs, on_dev, _keep = _batch_args(solvers, bs, "tune_tiling_batch")
+    rep = TilingReport()
+    _check(load().asm_tune_tiling_batch(hs, n, bp, xp, rtol, max_iter, 1 if on_dev else 0, C.byref(rep)),
+           "tune_tiling_batch")
+    return rep.as_dict()
 
 
 @dataclass

@@ -25,7 +25,7 @@ NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["kernels_setup.cu", "kernels_solve.cu", "kernels_coarse.cu", "kernels_dense.cu", "kernels_nf.cu", "noalloc.cu"]
 CPP_SOURCES = ["api.cpp", "symbolic.cpp"]
-HEADERS = ["asm2_internal.h", "symbolic.h", "tma.h"]
+HEADERS = ["asm2_internal.h", "symbolic.h", "tma.h", "f64cvt.h"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", *ARCH, f"-I{INCLUDE}", f"-I{CSRC}"]
 CXX_FLAGS = ["-std=c++17", "-O2", "-fPIC", "-Wall", f"-I{INCLUDE}", f"-I{CSRC}",
              f"-I{os.path.join(CUDA_HOME, 'include')}"]

@@ -107,10 +107,13 @@ struct asm_ctx {
     DBuf d_stream, d_pk_off_f, d_pk_src_f, d_pk_off_c, d_pk_src_c;
     DBuf d_lv, d_rlists, d_y, d_corr_cells, d_corr, d_dev_err;
     int apply_smem = 0;       // shared memory for all local vectors of the largest subdomain (0: none)
+    int apply_smem_need = 0;  // the same before the fit test of choose_ring()
     int apply_lump_smem = 0;  // shared memory for its lump vector and the FP32 mirror
     int apply_slots = 3; // factor-stream ring slots of the apply
     int chunk_cap = kStreamChunkMin;  // largest stream-chunk capacity of the subdomains (ring slot bytes)
-    int sm_smem = 0, n_sms = 1;  // shared memory per SM and SM count of the device
+    int sm_smem = 0, n_sms = 1, dev_smem = 0;  // shared memory per SM / per CTA (opt-in), SM count
+    int chunk_force = 0;  // stream-chunk capacity asked for (bytes; 0: per-subdomain rule)
+    int slots_force = 0;  // ring slots asked for with all local vectors in shared memory (0: rule)
     DBuf d_factdesc, d_subdesc_single, d_ritems1;
     int n_ritems1 = 0;
     DBuf d_err;
@@ -137,6 +140,7 @@ struct asm_ctx {
     bool no_graphs = false;    // asm_set_tuning ASM_TUNE_GRAPHS = 0
     long long wait_limit = 1LL << 22;  // asm_set_tuning ASM_TUNE_WAIT_LIMIT (polls per chunk wait)
     int tuned_ymode = -1;      // placement the online tuner chose for single-system solves (-1: none)
+    ApplyConfig last_solve_apply{-1, 0, 0, 0};  // apply configuration of the last solve this handle was in
     asm_profile_info prof{};
     // exact local solves (local_solver = ASM_LOCAL_EXACT): [A_i | I] inverted in place per subdomain
     DBuf d_daug, d_dprow, d_dfcol, d_dmats, d_dinit, d_doff, d_dmat_of_slot, d_dpart, d_derr, d_ditems1;
@@ -480,6 +484,28 @@ void upload_nf(asm_ctx* h, cudaStream_t st) {
     sync(h);
 }
 
+// Ring slots of the apply with all local vectors in shared memory: the number asked for
+// (asm_set_tuning ASM_TUNE_APPLY_SLOTS), else as many as keep two CTAs per SM (shared memory per
+// SM minus 1 KB per CTA), else 4 with one CTA per SM.  That placement is off (apply_smem = 0)
+// when the local vectors and the ring do not fit one CTA's shared memory.
+void choose_ring(asm_ctx* h) {
+    h->apply_smem = h->apply_smem_need;
+    h->apply_slots = 4;
+    if (h->slots_force > 0) {
+        h->apply_slots = h->slots_force;
+    } else {
+        for (int sl = 4; sl >= 2; sl--)
+            if (2 * ((size_t)h->apply_smem + apply_ring_bytes(sl, h->chunk_cap) + 1024) <= (size_t)h->sm_smem) {
+                h->apply_slots = sl;
+                break;
+            }
+    }
+    if ((size_t)h->apply_smem + apply_ring_bytes(h->apply_slots, h->chunk_cap) > (size_t)h->dev_smem - 1024) {
+        h->apply_smem = 0;
+        h->apply_slots = h->slots_force > 0 ? h->slots_force : 3;
+    }
+}
+
 void upload_symbolic(asm_ctx* h) {
     SysSym& S = *h->sym;
     cudaStream_t st = h->stream;
@@ -600,6 +626,7 @@ void upload_symbolic(asm_ctx* h) {
     h->sub_desc.assign(K, SubDesc{});
     h->sub_cost.assign(K, 0.0);
     h->apply_smem = 0;
+    h->apply_smem_need = 0;
     h->apply_lump_smem = 0;
     h->chunk_cap = kStreamChunkMin;
     h->tuned_ymode = -1;
@@ -666,7 +693,7 @@ void upload_symbolic(asm_ctx* h) {
         sd.clong = put(o.clong);
         sd.own_pos = put(o.own_pos);
         sd.own_cell = put(o.own_cell);
-        h->apply_smem = std::max<int>(h->apply_smem, (int)apply_smem_bytes(o.nf, o.n - o.nf, S.prec, S.lump32));
+        h->apply_smem_need = std::max<int>(h->apply_smem_need, (int)apply_smem_bytes(o.nf, o.n - o.nf, S.prec, S.lump32));
         h->apply_lump_smem = std::max<int>(h->apply_lump_smem, (int)apply_lump_bytes(o.n - o.nf, S.prec, S.lump32));
         for (size_t k = 0; k + 1 < o.corr_ptr.size(); k++)
             corr_items.push_back(BoxItem{0, corr_base + (int)k, (int)corr_cells.size() + o.corr_ptr[k],
@@ -703,25 +730,10 @@ void upload_symbolic(asm_ctx* h) {
         it.cells = h->d_corr_cells.as<int>();
         h->box_items.push_back(it);
     }
-    // local vectors in shared memory when they fit next to the kernel's static needs
-    int dev_smem = 0;
-    ck(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-    // ring slots: as many as keep two CTAs per SM (shared memory per SM minus 1 KB per CTA),
-    // else 4 with one CTA per SM; local vectors in device memory when they cannot fit at all
-    int sm_smem = 0;
-    ck(cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device));
-    h->sm_smem = sm_smem;
+    ck(cudaDeviceGetAttribute(&h->dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    ck(cudaDeviceGetAttribute(&h->sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device));
     ck(cudaDeviceGetAttribute(&h->n_sms, cudaDevAttrMultiProcessorCount, h->device));
-    h->apply_slots = 4;
-    for (int sl = 4; sl >= 2; sl--)
-        if (2 * ((size_t)h->apply_smem + apply_ring_bytes(sl, h->chunk_cap) + 1024) <= (size_t)sm_smem) {
-            h->apply_slots = sl;
-            break;
-        }
-    if ((size_t)h->apply_smem + apply_ring_bytes(h->apply_slots, h->chunk_cap) > (size_t)dev_smem - 1024) {
-        h->apply_smem = 0;
-        h->apply_slots = 3;
-    }
+    choose_ring(h);
     // most expensive subdomains first: the CTAs of the last wave are then the short ones
     {
         const std::vector<SubDesc> ordered = longest_first({h});
@@ -1357,6 +1369,7 @@ int run_krylov(std::vector<asm_ctx*>& hs, const double* const* b, double* const*
             }
     std::vector<float> tune_ms(cand.size(), 0.0f);
     int tune_next = 0, tune_at = -1;
+    for (asm_ctx* h : hs) h->last_solve_apply = B.apply;
     StepEvents ev;
     if (prof || tune_total > 0) ev.create();
     // CUDA graphs for batches: the launch sequence of a step depends only on the number of
@@ -1393,6 +1406,7 @@ int run_krylov(std::vector<asm_ctx*>& hs, const double* const* b, double* const*
                     if (tune_ms[k] < tune_ms[best]) best = (int)k;
                 B.apply = cand[best];
                 if (hs.size() == 1) hs[0]->tuned_ymode = B.apply.ymode;
+                for (asm_ctx* h : hs) h->last_solve_apply = B.apply;
             }
         }
         int kmax = -1;
@@ -2035,7 +2049,7 @@ int asm_factor(asm_handle h) {
             h->sym = std::make_shared<SysSym>();
             std::string e = build_symbolic(h->geom, h->pat, h->prec, h->lump32 ? 1 : 0,
                                            h->opt.local_solver == ASM_LOCAL_BILU0_COLSUM ? 1 : 0,
-                                           *h->sym, 0);
+                                           *h->sym, 0, h->chunk_force);
             if (!e.empty()) {
                 h->last_error = e;
                 h->sym.reset();
@@ -2049,6 +2063,20 @@ int asm_factor(asm_handle h) {
         }
         return factor_numeric(h);
     });
+}
+
+// the placement of a single-system apply: `place` as ASM_TUNE_APPLY_SMEM stores it (0 automatic)
+ApplyConfig single_apply_config(const asm_ctx* h, int place) {
+    return apply_local_vectors((int)h->sub_desc.size(), h->apply_smem, h->apply_lump_smem, h->apply_slots,
+                               h->chunk_cap, h->sm_smem, h->n_sms, place);
+}
+
+// R_i r and the fused ILU sweeps of every subdomain (after k_sums), single-system tables
+void launch_ilu_local_solves(asm_ctx* h, const ApplyConfig& cfg) {
+    launch_restrict(h->d_tab1.as<SysTab>(), h->d_subdesc_single.as<SubDesc>(), h->d_ritems1.as<int2>(), h->n_ritems1,
+                    h->prec, h->lump32, h->stream);
+    launch_apply(h->d_tab1.as<SysTab>(), h->d_subdesc_single.as<SubDesc>(), (int)h->sub_desc.size(), h->prec,
+                 h->lump32, cfg, h->stream);
 }
 
 int asm_apply_precond(asm_handle h, const double* r, double* z, int on_device) {
@@ -2071,13 +2099,7 @@ int asm_apply_precond(asm_handle h, const double* r, double* z, int on_device) {
             launch_dense_apply(h->d_tab1.as<SysTab>(), h->d_subdesc_single.as<SubDesc>(), h->d_ditems1.as<int2>(),
                                h->n_ditems1, h->stream);
         } else {
-            const int nsub = (int)h->sub_desc.size();
-            launch_restrict(h->d_tab1.as<SysTab>(), h->d_subdesc_single.as<SubDesc>(), h->d_ritems1.as<int2>(),
-                            h->n_ritems1, h->prec, h->lump32, h->stream);
-            launch_apply(h->d_tab1.as<SysTab>(), h->d_subdesc_single.as<SubDesc>(), nsub, h->prec, h->lump32,
-                         apply_local_vectors(nsub, h->apply_smem, h->apply_lump_smem, h->apply_slots, h->chunk_cap,
-                                             h->sm_smem, h->n_sms, h->apply_place),
-                         h->stream);
+            launch_ilu_local_solves(h, single_apply_config(h, h->apply_place));
         }
         if (h->tab.cmode != 0)
             launch_coarse_apply(h->d_tab1.as<SysTab>(), h->d_row1.as<RowItem>(), h->n_row1,
@@ -2089,6 +2111,113 @@ int asm_apply_precond(asm_handle h, const double* r, double* z, int on_device) {
         copy_out(h, z, out, bytes, on_device);
         sync(h);
         return take_dev_err(h) ? ASM_ERR_TIMEOUT : ASM_OK;
+    });
+}
+
+int asm_tune_tiling(asm_handle h, int reps, asm_tiling_report* out) {
+    if (!h || !out || reps < 1) return ASM_ERR_INVALID_ARG;
+    if (!h->factored) return ASM_ERR_STATE;
+    if (is_nf(h) || h->opt.local_solver == ASM_LOCAL_EXACT) return ASM_ERR_INVALID_ARG;
+    *out = asm_tiling_report{};
+    return guard(h, [&]() -> int {
+        struct Ev {
+            cudaEvent_t e = nullptr;
+            ~Ev() {
+                if (e) cudaEventDestroy(e);
+            }
+        } ev0, ev1;
+        ck(cudaEventCreate(&ev0.e));
+        ck(cudaEventCreate(&ev1.e));
+        cudaEvent_t e0 = ev0.e, e1 = ev1.e;
+        // median time of one apply (box sums, restriction, sweeps) in placement `place`
+        auto time_apply = [&](int place) -> double {
+            ensure_workspace(h);
+            set_ctl(h, VU, VZ, -1, -1, -1);
+            const ApplyConfig cfg = single_apply_config(h, place);
+            std::vector<float> t;
+            for (int k = 0; k < reps + 2; k++) {
+                ck(cudaEventRecord(e0, h->stream));
+                launch_boxsum(h->d_tab1.as<SysTab>(), h->d_box1.as<BoxItem>(), (int)h->box_items.size(), h->stream);
+                launch_ilu_local_solves(h, cfg);
+                ck(cudaEventRecord(e1, h->stream));
+                ck(cudaEventSynchronize(e1));
+                float ms = 0.0f;
+                ck(cudaEventElapsedTime(&ms, e0, e1));
+                if (k >= 2) t.push_back(ms);
+            }
+            ck(cudaGetLastError());
+            std::sort(t.begin(), t.end());
+            return t[t.size() / 2];
+        };
+        auto rebuild = [&](int chunk_bytes) -> int {
+            if (h->chunk_force == chunk_bytes && h->sym_valid) return ASM_OK;
+            h->chunk_force = chunk_bytes;
+            h->sym_valid = false;
+            h->factored = false;
+            return asm_factor(h);
+        };
+        const int place0 = h->apply_place, slots0 = h->slots_force, chunk0 = h->chunk_force;
+        const bool autotune0 = h->no_autotune;
+        // the default configuration first
+        h->slots_force = 0;
+        int stt = rebuild(0);
+        if (stt != ASM_OK) return stt;
+        out->rule_ms = time_apply(0);
+        std::vector<std::vector<int>> seen;
+        for (int kb : {0, 8, 12, 16, 20, 24}) {
+            h->slots_force = 0;
+            stt = rebuild(kb * 1024);
+            if (stt != ASM_OK) return stt;
+            std::vector<int> caps;
+            long long chunks = 0;
+            for (const SubSym& o : h->sym->subs) {
+                caps.push_back(o.chunk_cap);
+                chunks += (long long)o.chunk_off.size();
+            }
+            if (std::find(seen.begin(), seen.end(), caps) != seen.end()) continue;
+            seen.push_back(caps);
+            struct Cand {
+                int place, slots;
+            };
+            std::vector<Cand> cands;
+            for (int sl = 2; sl <= 4; sl++) cands.push_back({Y_SMEM + 1, sl});
+            cands.push_back({Y_LUMPS + 1, 0});
+            cands.push_back({Y_DEVICE + 1, 0});
+            for (const Cand& c : cands) {
+                if (out->n >= ASM_TILING_MAX) break;
+                h->slots_force = c.place == Y_SMEM + 1 ? c.slots : 0;
+                choose_ring(h);
+                const ApplyConfig cfg = single_apply_config(h, c.place);
+                if (cfg.ymode != c.place - 1) continue;  // does not fit
+                asm_tiling_entry& e = out->e[out->n];
+                e.chunk_kb = kb;
+                e.chunk_max_kb = h->chunk_cap / 1024;
+                e.chunks = chunks;
+                e.placement = cfg.ymode == Y_SMEM ? 3 : (cfg.ymode == Y_LUMPS ? 2 : 0);
+                e.slots = cfg.slots;
+                e.ctas_per_sm = apply_ctas_per_sm(h->prec, h->lump32, cfg);
+                e.apply_ms = time_apply(c.place);
+                out->n++;
+            }
+        }
+        if (out->n == 0) {
+            h->apply_place = place0;
+            h->slots_force = slots0;
+            h->no_autotune = autotune0;
+            stt = rebuild(chunk0);
+            return stt != ASM_OK ? stt : ASM_ERR_INVALID_ARG;
+        }
+        for (int k = 1; k < out->n; k++)
+            if (out->e[k].apply_ms < out->e[out->best].apply_ms) out->best = k;
+        const asm_tiling_entry& b = out->e[out->best];
+        h->slots_force = b.placement == 3 ? b.slots : 0;
+        stt = rebuild(b.chunk_kb * 1024);
+        if (stt != ASM_OK) return stt;
+        choose_ring(h);
+        h->apply_place = b.placement == 3 ? Y_SMEM + 1 : (b.placement == 2 ? Y_LUMPS + 1 : Y_DEVICE + 1);
+        h->no_autotune = true;
+        h->tuned_ymode = -1;
+        return ASM_OK;
     });
 }
 
@@ -2153,6 +2282,86 @@ int asm_solve_batch(asm_handle* hs, int n, const double* const* b, double* const
     return guard(v[0], [&]() -> int { return run_krylov(v, b, x, rtol, max_iter, on_device, infos); });
 }
 
+int asm_tune_tiling_batch(asm_handle* hs, int n, const double* const* b, double* const* x, double rtol, int max_iter,
+                          int on_device, asm_tiling_report* out) {
+    if (!hs || n < 1 || !b || !x || !out || !(rtol >= 0.0) || max_iter < 1) return ASM_ERR_INVALID_ARG;
+    for (int i = 0; i < n; i++) {
+        if (!hs[i]) return ASM_ERR_INVALID_ARG;
+        if (!hs[i]->factored) return ASM_ERR_STATE;
+        if (is_nf(hs[i]) || hs[i]->opt.local_solver == ASM_LOCAL_EXACT) return ASM_ERR_INVALID_ARG;
+    }
+    *out = asm_tiling_report{};
+    asm_ctx* h0 = hs[0];
+    return guard(h0, [&]() -> int {
+        struct Ev {
+            cudaEvent_t e = nullptr;
+            ~Ev() {
+                if (e) cudaEventDestroy(e);
+            }
+        } ev0, ev1;
+        ck(cudaEventCreate(&ev0.e));
+        ck(cudaEventCreate(&ev1.e));
+        auto set_all = [&](int chunk_bytes) -> int {
+            for (int i = 0; i < n; i++) {
+                asm_ctx* h = hs[i];
+                if (h->chunk_force == chunk_bytes && h->sym_valid && h->factored) continue;
+                h->chunk_force = chunk_bytes;
+                h->sym_valid = false;
+                h->factored = false;
+                const int stt = asm_factor(h);
+                if (stt != ASM_OK) return stt;
+            }
+            return ASM_OK;
+        };
+        // one warm batched solve (its first steps run the online placement tuner), one timed
+        auto time_solve = [&]() -> double {
+            int stt = asm_solve_batch(hs, n, b, x, rtol, max_iter, on_device, nullptr);
+            if (stt != ASM_OK && stt != ASM_ERR_NOT_CONVERGED) throw CudaFail{stt};
+            ck(cudaEventRecord(ev0.e, h0->stream));
+            stt = asm_solve_batch(hs, n, b, x, rtol, max_iter, on_device, nullptr);
+            if (stt != ASM_OK && stt != ASM_ERR_NOT_CONVERGED) throw CudaFail{stt};
+            ck(cudaEventRecord(ev1.e, h0->stream));
+            ck(cudaEventSynchronize(ev1.e));
+            float ms = 0.0f;
+            ck(cudaEventElapsedTime(&ms, ev0.e, ev1.e));
+            return ms;
+        };
+        std::vector<std::vector<int>> seen;
+        for (int kb : {0, 8, 12, 16, 20, 24}) {
+            int stt = set_all(kb * 1024);
+            if (stt != ASM_OK) return stt;
+            std::vector<int> caps;
+            long long chunks = 0;
+            int cmax = 0;
+            for (int i = 0; i < n; i++) {
+                for (const SubSym& o : hs[i]->sym->subs) {
+                    caps.push_back(o.chunk_cap);
+                    chunks += (long long)o.chunk_off.size();
+                }
+                cmax = std::max(cmax, hs[i]->chunk_cap);
+            }
+            if (std::find(seen.begin(), seen.end(), caps) != seen.end()) continue;
+            seen.push_back(caps);
+            if (out->n >= ASM_TILING_MAX) break;
+            const double ms = time_solve();
+            if (kb == 0) out->rule_ms = ms;
+            asm_tiling_entry& e = out->e[out->n];
+            const ApplyConfig& a = h0->last_solve_apply;
+            e.chunk_kb = kb;
+            e.chunk_max_kb = cmax / 1024;
+            e.chunks = chunks;
+            e.placement = a.ymode == Y_SMEM ? 3 : (a.ymode == Y_LUMPS ? 2 : 0);
+            e.slots = a.slots;
+            e.ctas_per_sm = apply_ctas_per_sm(h0->prec, h0->lump32, a);
+            e.apply_ms = ms;
+            out->n++;
+        }
+        for (int k = 1; k < out->n; k++)
+            if (out->e[k].apply_ms < out->e[out->best].apply_ms) out->best = k;
+        return set_all(out->e[out->best].chunk_kb * 1024);
+    });
+}
+
 int asm_get_stats(asm_handle h, asm_stats* st) {
     if (!h || !st) return ASM_ERR_INVALID_ARG;
     std::memset(st, 0, sizeof(*st));
@@ -2184,6 +2393,18 @@ int asm_get_stats(asm_handle h, asm_stats* st) {
     }
     st->setup_ms = h->setup_ms;
     st->factor_ms = h->factor_ms;
+    if (h->sym && h->sym_valid && !is_nf(h) && h->opt.local_solver != ASM_LOCAL_EXACT) {
+        st->chunk_max_kb = h->chunk_cap / 1024;
+        for (const SubSym& o : h->sym->subs) st->stream_chunks += (long long)o.chunk_off.size();
+        const int place = h->apply_place != 0 ? h->apply_place : (h->tuned_ymode >= 0 ? h->tuned_ymode + 1 : 0);
+        const ApplyConfig cfg = single_apply_config(h, place);
+        st->apply_placement = cfg.ymode == Y_SMEM ? 3 : (cfg.ymode == Y_LUMPS ? 2 : 0);
+        st->apply_slots = cfg.slots;
+        const ApplyConfig& l = h->last_solve_apply;
+        st->last_solve_placement = l.ymode < 0 ? -1 : (l.ymode == Y_SMEM ? 3 : (l.ymode == Y_LUMPS ? 2 : 0));
+        st->last_solve_slots = l.ymode < 0 ? 0 : l.slots;
+        st->last_solve_chunk_kb = l.ymode < 0 ? 0 : l.chunk / 1024;
+    }
     return ASM_OK;
 }
 
@@ -2204,6 +2425,19 @@ int asm_set_tuning(asm_handle h, int key, int value) {
     } else if (key == ASM_TUNE_COOP_ORTHO) {
         if (value > 1) return ASM_ERR_INVALID_ARG;
         h->no_coop = value == 0;
+    } else if (key == ASM_TUNE_CHUNK_KB) {
+        if (value != 0 && (value % 4 != 0 || value * 1024 < kStreamChunkMin || value * 1024 > kStreamChunkMax))
+            return ASM_ERR_INVALID_ARG;
+        if (h->chunk_force != value * 1024) {
+            h->chunk_force = value * 1024;
+            h->sym_valid = false;
+            h->factored = false;
+        }
+    } else if (key == ASM_TUNE_APPLY_SLOTS) {
+        if (value != 0 && (value < 2 || value > 4)) return ASM_ERR_INVALID_ARG;
+        h->slots_force = value;
+        h->tuned_ymode = -1;
+        if (h->sym_valid && h->sm_smem > 0) choose_ring(h);
     } else if (key == ASM_TUNE_WAIT_LIMIT) {
         if (value > 30) return ASM_ERR_INVALID_ARG;
         h->wait_limit = value == 0 ? 0 : 1LL << value;

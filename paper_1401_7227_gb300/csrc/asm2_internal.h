@@ -249,6 +249,8 @@ void launch_boxsum(const SysTab* st_tab, const BoxItem* items, int nitems, cudaS
 // the ring of factor-stream slots is added on top
 void launch_apply(const SysTab* st_tab, const SubDesc* subs, int nsub, int prec, bool lump32, ApplyConfig cfg,
                   cudaStream_t st);
+// CTAs of that apply launch resident per SM (0 when it cannot launch)
+int apply_ctas_per_sm(int prec, bool lump32, ApplyConfig cfg);
 // R_i r of every subdomain into its device-memory local vectors (items: subdomain, first local row
 // of 256; fine rows first, then lump rows)
 void launch_restrict(const SysTab* tab, const SubDesc* subs, const int2* items, int nitems, int prec, bool lump32,

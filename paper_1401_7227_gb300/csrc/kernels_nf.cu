@@ -91,11 +91,14 @@ __device__ __forceinline__ TC ld(const TS* p, int lane) { return lane < 9 ? (TC)
 //   forward   v_q = u_q - v_{q-1} N_{q-1}            (v (I + G^{-1} U1) = u)
 //   backward  W_q = v_q G_q^{-1} - W_{q+1} K_q       (W (G + L1) = v; v_q G_q^{-1} on all lanes first)
 // The operands come from device memory (L2) at ~400 cycles, against ~50 cycles of arithmetic per
-// step, so the chains take them kRowG steps at a time into one of two register buffers, the next
-// group's loads issued before the current group is computed.
+// FP32 step, so the chains take them kRowG steps at a time into one of two register buffers, the
+// next group's loads issued before the current group is computed.  An FP64 step takes ~300 cycles,
+// so four steps cover the load latency, and the smaller buffers keep k_nf_factor<double> free of
+// register spills (eight: 255 registers and 92 bytes spilled; four: 233 registers, none, and the
+// FP64 re-factor 12% faster at 1M cells).
 template <typename TC>
 __device__ void line_row_solve(const NFView<TC>& v, int q0, const TC* u, TC* vtmp, TC* W, int lane) {
-    constexpr int kRowG = 8;
+    constexpr int kRowG = sizeof(TC) == 8 ? 4 : 8;
     const int bz = v.d.bz;
     {
         TC a[2][kRowG], b[2][kRowG];  // u_q, N_{q-1}

@@ -9,11 +9,22 @@
 #include <cooperative_groups.h>
 
 #include "asm2_internal.h"
+#include "f64cvt.h"
 #include "tma.h"
 
 namespace asm2 {
 
 namespace {
+
+// residual values into a local vector's type; FP32 on the integer pipes (f64cvt.h)
+template <typename T>
+__device__ __forceinline__ T narrow(double v) {
+    return (T)v;
+}
+template <>
+__device__ __forceinline__ float narrow<float>(double v) {
+    return f64_to_f32(v);
+}
 
 __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
@@ -516,9 +527,9 @@ __device__ __forceinline__ void restrict_local(const SysTab& st, const SubDesc& 
         for (int u = 0; u < kB; u++)
             if (cell[u] >= 0) {
                 const int f = f0 + u * nt;
-                yf[3 * f] = (TC)v[u][0];
-                yf[3 * f + 1] = (TC)v[u][1];
-                yf[3 * f + 2] = (TC)v[u][2];
+                yf[3 * f] = narrow<TC>(v[u][0]);
+                yf[3 * f + 1] = narrow<TC>(v[u][1]);
+                yf[3 * f + 2] = narrow<TC>(v[u][2]);
             }
     }
     for (int c = tid; c < sd.nc; c += nt) {
@@ -545,9 +556,9 @@ __device__ __forceinline__ void restrict_local(const SysTab& st, const SubDesc& 
             a1 += rc[1];
             a2 += rc[2];
         }
-        yc[3 * c] = (TL)a0;
-        yc[3 * c + 1] = (TL)a1;
-        yc[3 * c + 2] = (TL)a2;
+        yc[3 * c] = narrow<TL>(a0);
+        yc[3 * c + 1] = narrow<TL>(a1);
+        yc[3 * c + 2] = narrow<TL>(a2);
     }
     for (int k = warp; k < sd.n_long; k += nwarp) {
         const int c = sd.clong[k];
@@ -560,9 +571,9 @@ __device__ __forceinline__ void restrict_local(const SysTab& st, const SubDesc& 
         }
         warp_sum3(a0, a1, a2);
         if (lane == 0) {
-            yc[3 * c] = (TL)a0;
-            yc[3 * c + 1] = (TL)a1;
-            yc[3 * c + 2] = (TL)a2;
+            yc[3 * c] = narrow<TL>(a0);
+            yc[3 * c + 1] = narrow<TL>(a1);
+            yc[3 * c + 2] = narrow<TL>(a2);
         }
     }
 }
@@ -588,12 +599,13 @@ __global__ void __launch_bounds__(256) k_restrict(const SysTab* __restrict__ tab
     if (q < sd.nf) {
         const double* rc = r + 3LL * sd.fcell[q];
         if constexpr (kRow16) {
-            reinterpret_cast<float4*>(y + sd.y_fine)[q] = make_float4((float)rc[0], (float)rc[1], (float)rc[2], 0.f);
+            reinterpret_cast<float4*>(y + sd.y_fine)[q] =
+                make_float4(f64_to_f32(rc[0]), f64_to_f32(rc[1]), f64_to_f32(rc[2]), 0.f);
         } else {
             TC* yf = reinterpret_cast<TC*>(y + sd.y_fine) + 3 * q;
-            yf[0] = (TC)rc[0];
-            yf[1] = (TC)rc[1];
-            yf[2] = (TC)rc[2];
+            yf[0] = narrow<TC>(rc[0]);
+            yf[1] = narrow<TC>(rc[1]);
+            yf[2] = narrow<TC>(rc[2]);
         }
         return;
     }
@@ -635,18 +647,18 @@ __global__ void __launch_bounds__(256) k_restrict(const SysTab* __restrict__ tab
             }
     }
     if constexpr (kRow16) {
-        reinterpret_cast<float4*>(y)[c] = make_float4((float)a0, (float)a1, (float)a2, 0.f);
+        reinterpret_cast<float4*>(y)[c] = make_float4(f64_to_f32(a0), f64_to_f32(a1), f64_to_f32(a2), 0.f);
         return;
     }
     TL* yc = reinterpret_cast<TL*>(y) + 3 * c;
-    yc[0] = (TL)a0;
-    yc[1] = (TL)a1;
-    yc[2] = (TL)a2;
+    yc[0] = narrow<TL>(a0);
+    yc[1] = narrow<TL>(a1);
+    yc[2] = narrow<TL>(a2);
     if constexpr (sizeof(TL) == 8 && sizeof(TC) == 4) {
         TC* ycf = reinterpret_cast<TC*>(y + sd.y_mirror) + 3 * c;
-        ycf[0] = (TC)a0;
-        ycf[1] = (TC)a1;
-        ycf[2] = (TC)a2;
+        ycf[0] = narrow<TC>(a0);
+        ycf[1] = narrow<TC>(a1);
+        ycf[2] = narrow<TC>(a2);
     }
 }
 
@@ -1291,7 +1303,7 @@ __device__ __forceinline__ void grid_total(const double* part, int G, double& s0
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(VEC_THREADS) k_ortho_coop(const SysTab* __restrict__ tab, double* __restrict__ part2) {
+__global__ void __launch_bounds__(VEC_THREADS, 2) k_ortho_coop(const SysTab* __restrict__ tab, double* __restrict__ part2) {
     constexpr int kU = 4;
     namespace cg = cooperative_groups;
     cg::grid_group grid = cg::this_grid();
@@ -1308,50 +1320,72 @@ __global__ void __launch_bounds__(VEC_THREADS) k_ortho_coop(const SysTab* __rest
     if (ph == PH_ARNOLDI) {
         const int j = st.ctl[C_J];
         double hprev = 0.0, w0 = 0.0, hn = 0.0;
+        // Operands of the current group of kU elements; the next group's loads are issued before
+        // the current group is computed.  The first group of pass k + 1 needs nothing from the
+        // barrier that ends pass k (its w is this thread's own result), so its loads are issued
+        // before that barrier.
+        double A[kU], B[kU], C[kU];
+        {
+            const double* v0 = vec(st, VV0);
+#pragma unroll
+            for (int u = 0; u < kU; u++) {
+                const long long e = e_begin + u * stride;
+                A[u] = e < n ? w[e] : 0.0;
+                B[u] = 0.0;
+                C[u] = e < n ? v0[e] : 0.0;
+            }
+        }
         for (int k = 0; k <= j + 1; k++) {
             double* part = part2 + (size_t)(k & 1) * 2 * G;
             double s0 = 0.0, s1 = 0.0;
-            // kU elements per thread per iteration, loaded before any arithmetic, with kU partial
-            // sums: keeps enough loads in flight per warp to cover the memory latency
+            // kU partial sums per thread, combined in a fixed order
             double p0[kU], p1[kU];
 #pragma unroll
             for (int u = 0; u < kU; u++) p0[u] = p1[u] = 0.0;
-            if (k == 0) {
-                const double* vk = vec(st, VV0);
-                for (long long e0 = e_begin; e0 < n; e0 += kU * stride) {
-                    double a[kU], b[kU];
+            const double* vp = k > 0 ? vec(st, VV0 + k - 1) : nullptr;
+            const double* vk = k <= j ? vec(st, VV0 + k) : nullptr;
+            for (long long e0 = e_begin; e0 < n; e0 += kU * stride) {
+                const long long e1 = e0 + kU * stride;
+                double An[kU], Bn[kU], Cn[kU];
+#pragma unroll
+                for (int u = 0; u < kU; u++) {
+                    const long long e = e1 + u * stride;
+                    const bool in = e < n;
+                    An[u] = in ? w[e] : 0.0;
+                    Bn[u] = in && vp ? vp[e] : 0.0;
+                    Cn[u] = in && vk ? vk[e] : 0.0;
+                }
+                if (k == 0) {  // (w, v_0) and (w, w)
+#pragma unroll
+                    for (int u = 0; u < kU; u++) {
+                        p0[u] = fma(A[u], C[u], p0[u]);
+                        p1[u] = fma(A[u], A[u], p1[u]);
+                    }
+                } else {  // w -= h_{k-1} v_{k-1}, then (w, v_k), or (w, w) after the last projection
 #pragma unroll
                     for (int u = 0; u < kU; u++) {
                         const long long e = e0 + u * stride;
-                        a[u] = e < n ? w[e] : 0.0;
-                        b[u] = e < n ? vk[e] : 0.0;
-                    }
-#pragma unroll
-                    for (int u = 0; u < kU; u++) {
-                        p0[u] = fma(a[u], b[u], p0[u]);
-                        p1[u] = fma(a[u], a[u], p1[u]);
+                        const double x = fma(-hprev, B[u], A[u]);
+                        if (e < n) w[e] = x;
+                        p0[u] = fma(x, vk ? C[u] : x, p0[u]);
                     }
                 }
-            } else {
-                const double* vp = vec(st, VV0 + k - 1);
-                const double* vk = k <= j ? vec(st, VV0 + k) : nullptr;
-                for (long long e0 = e_begin; e0 < n; e0 += kU * stride) {
-                    double a[kU], b[kU], c[kU];
 #pragma unroll
-                    for (int u = 0; u < kU; u++) {
-                        const long long e = e0 + u * stride;
-                        const bool in = e < n;
-                        a[u] = in ? w[e] : 0.0;
-                        b[u] = in ? vp[e] : 0.0;
-                        c[u] = in && vk ? vk[e] : 0.0;
-                    }
+                for (int u = 0; u < kU; u++) {
+                    A[u] = An[u];
+                    B[u] = Bn[u];
+                    C[u] = Cn[u];
+                }
+            }
+            if (k <= j) {  // the first group of pass k + 1
+                const double* vn = k + 1 <= j ? vec(st, VV0 + k + 1) : nullptr;
 #pragma unroll
-                    for (int u = 0; u < kU; u++) {
-                        const long long e = e0 + u * stride;
-                        const double x = fma(-hprev, b[u], a[u]);
-                        if (e < n) w[e] = x;
-                        p0[u] = fma(x, vk ? c[u] : x, p0[u]);
-                    }
+                for (int u = 0; u < kU; u++) {
+                    const long long e = e_begin + u * stride;
+                    const bool in = e < n;
+                    A[u] = in ? w[e] : 0.0;
+                    B[u] = in ? vk[e] : 0.0;
+                    C[u] = in && vn ? vn[e] : 0.0;
                 }
             }
             s0 = (p0[0] + p0[1]) + (p0[2] + p0[3]);
@@ -1444,49 +1478,66 @@ ApplyConfig apply_local_vectors(int nsub, int all_bytes, int lump_bytes, int sme
 
 namespace {
 template <typename TF, typename TL, int YM, int SLOTS>
-void launch_apply_t(const SysTab* tab, const SubDesc* subs, int nsub, int smem, cudaStream_t st) {
+void launch_apply_t(const SysTab* tab, const SubDesc* subs, int nsub, int smem, cudaStream_t st, int* occ) {
     static int configured = -1;
     if (configured < smem) {
         cudaFuncSetAttribute(k_apply<TF, TL, YM, SLOTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         configured = smem;
     }
-    k_apply<TF, TL, YM, SLOTS><<<nsub, YM == Y_SMEM ? 256 : kApplyThreadsDev, smem, st>>>(tab, subs);
+    const int threads = YM == Y_SMEM ? 256 : kApplyThreadsDev;
+    if (occ != nullptr) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_apply<TF, TL, YM, SLOTS>, threads, smem) != cudaSuccess)
+            *occ = 0;
+        return;
+    }
+    k_apply<TF, TL, YM, SLOTS><<<nsub, threads, smem, st>>>(tab, subs);
 }
 template <typename TF, typename TL, int YM>
-void launch_apply_s(const SysTab* tab, const SubDesc* subs, int nsub, int smem, int slots, cudaStream_t st) {
+void launch_apply_s(const SysTab* tab, const SubDesc* subs, int nsub, int smem, int slots, cudaStream_t st, int* occ) {
     if (slots == 2)
-        launch_apply_t<TF, TL, YM, 2>(tab, subs, nsub, smem, st);
+        launch_apply_t<TF, TL, YM, 2>(tab, subs, nsub, smem, st, occ);
     else if (slots == 3)
-        launch_apply_t<TF, TL, YM, 3>(tab, subs, nsub, smem, st);
+        launch_apply_t<TF, TL, YM, 3>(tab, subs, nsub, smem, st, occ);
     else
-        launch_apply_t<TF, TL, YM, 4>(tab, subs, nsub, smem, st);
+        launch_apply_t<TF, TL, YM, 4>(tab, subs, nsub, smem, st, occ);
 }
 template <typename TF, typename TL>
-void launch_apply_p(const SysTab* tab, const SubDesc* subs, int nsub, ApplyConfig cfg, int slots, cudaStream_t st) {
+void launch_apply_p(const SysTab* tab, const SubDesc* subs, int nsub, ApplyConfig cfg, int slots, cudaStream_t st,
+                    int* occ) {
     const int ring = (int)apply_ring_bytes(slots, cfg.chunk);
     if (cfg.ymode == Y_SMEM)
-        launch_apply_s<TF, TL, Y_SMEM>(tab, subs, nsub, ring + cfg.smem, slots, st);
+        launch_apply_s<TF, TL, Y_SMEM>(tab, subs, nsub, ring + cfg.smem, slots, st, occ);
     else if (cfg.ymode == Y_LUMPS)
-        launch_apply_s<TF, TL, Y_LUMPS>(tab, subs, nsub, ring + cfg.smem, slots, st);
+        launch_apply_s<TF, TL, Y_LUMPS>(tab, subs, nsub, ring + cfg.smem, slots, st, occ);
     else
-        launch_apply_s<TF, TL, Y_DEVICE>(tab, subs, nsub, ring, slots, st);
+        launch_apply_s<TF, TL, Y_DEVICE>(tab, subs, nsub, ring, slots, st, occ);
+}
+// the k_apply instance of (prec, lump32, cfg): launched, or (occ != nullptr) its resident CTAs per SM
+void apply_dispatch(const SysTab* tab, const SubDesc* subs, int nsub, int prec, bool lump32, ApplyConfig cfg,
+                    cudaStream_t st, int* occ) {
+    const int slots = cfg.slots < 2 ? 2 : (cfg.slots > kMaxSlots ? kMaxSlots : cfg.slots);
+    if (prec == 0)
+        launch_apply_p<double, double>(tab, subs, nsub, cfg, slots, st, occ);
+    else if (prec == 1 && lump32)
+        launch_apply_p<float, float>(tab, subs, nsub, cfg, slots, st, occ);
+    else if (prec == 1)
+        launch_apply_p<float, double>(tab, subs, nsub, cfg, slots, st, occ);
+    else if (lump32)
+        launch_apply_p<__half, float>(tab, subs, nsub, cfg, slots, st, occ);
+    else
+        launch_apply_p<__half, double>(tab, subs, nsub, cfg, slots, st, occ);
 }
 }  // namespace
 
 void launch_apply(const SysTab* tab, const SubDesc* subs, int nsub, int prec, bool lump32, ApplyConfig cfg,
                   cudaStream_t st) {
-    if (nsub <= 0) return;
-    const int slots = cfg.slots < 2 ? 2 : (cfg.slots > kMaxSlots ? kMaxSlots : cfg.slots);
-    if (prec == 0)
-        launch_apply_p<double, double>(tab, subs, nsub, cfg, slots, st);
-    else if (prec == 1 && lump32)
-        launch_apply_p<float, float>(tab, subs, nsub, cfg, slots, st);
-    else if (prec == 1)
-        launch_apply_p<float, double>(tab, subs, nsub, cfg, slots, st);
-    else if (lump32)
-        launch_apply_p<__half, float>(tab, subs, nsub, cfg, slots, st);
-    else
-        launch_apply_p<__half, double>(tab, subs, nsub, cfg, slots, st);
+    if (nsub > 0) apply_dispatch(tab, subs, nsub, prec, lump32, cfg, st, nullptr);
+}
+
+int apply_ctas_per_sm(int prec, bool lump32, ApplyConfig cfg) {
+    int occ = 0;
+    apply_dispatch(nullptr, nullptr, 0, prec, lump32, cfg, nullptr, &occ);
+    return occ;
 }
 
 void launch_restrict(const SysTab* tab, const SubDesc* subs, const int2* items, int nitems, int prec, bool lump32,

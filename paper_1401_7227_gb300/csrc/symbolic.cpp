@@ -462,19 +462,27 @@ std::string build_sub(const Ctx& X, int s, SubSym& o) {
     // chunk capacity: the largest fine level (forward or backward part) and the longest single lump
     // row in one chunk, rounded up to 4 KB, within [kStreamChunkMin, kStreamChunkMax] (fewer chunks
     // mean fewer barriers in the apply; larger ring slots mean fewer CTAs per SM, so small
-    // subdomains keep the smallest capacity)
+    // subdomains keep the smallest capacity).  A capacity asked for (the tiling tuner's) replaces
+    // the level term; every single row must still fit.
     {
-        size_t big = 0;
+        size_t big = 0, one = 0;
         for (int l = 0; l < nlev; l++)
             for (int pass = 0; pass < 2; pass++) {
                 int ef = 0;
-                for (int pos = o.lv_pos0[l]; pos < o.lv_pos0[l] + cntf[l]; pos++)
-                    ef += pass == 0 ? nl(o.row_of_pos[pos]) : nu(o.row_of_pos[pos]);
+                for (int pos = o.lv_pos0[l]; pos < o.lv_pos0[l] + cntf[l]; pos++) {
+                    const int e = pass == 0 ? nl(o.row_of_pos[pos]) : nu(o.row_of_pos[pos]);
+                    ef += e;
+                    one = std::max(one, chunk_bytes(1, e, 0, 0, pass == 0) + 256);
+                }
                 big = std::max(big, chunk_bytes(cntf[l], ef, 0, 0, pass == 0) + 256);
             }
         for (int p = o.nf; p < n; p++)
-            for (int pass = 0; pass < 2; pass++)
-                big = std::max(big, chunk_bytes(0, 0, 1, pass == 0 ? nl(p) : nu(p), pass == 0));
+            for (int pass = 0; pass < 2; pass++) {
+                const size_t b = chunk_bytes(0, 0, 1, pass == 0 ? nl(p) : nu(p), pass == 0);
+                big = std::max(big, b);
+                one = std::max(one, b);
+            }
+        if (X.S.chunk_force > 0) big = std::max(one, (size_t)X.S.chunk_force);
         const size_t cap = (big + 4095) / 4096 * 4096;
         o.chunk_cap = (int)std::min<size_t>(asm2::kStreamChunkMax, std::max<size_t>(asm2::kStreamChunkMin, cap));
     }
@@ -675,14 +683,18 @@ std::string build_pattern(int n, const int* rp, const int* ci, int nnzb, Pattern
 }
 
 std::string build_symbolic(const Geom& g, const Pattern& A, int prec, int lump32, int colsum, SysSym& S,
-                           int threads) {
+                           int threads, int chunk_force) {
     const int N = g.n_cells();
     if (A.n != N) return "matrix size does not match the grid";
+    if (chunk_force != 0 &&
+        (chunk_force % 4096 != 0 || chunk_force < asm2::kStreamChunkMin || chunk_force > asm2::kStreamChunkMax))
+        return "stream chunk capacity out of range";
     S = SysSym();
     S.g = g;
     S.prec = prec;
     S.lump32 = prec != 0 && lump32 ? 1 : 0;
     S.colsum = colsum;
+    S.chunk_force = chunk_force;
     const int K = g.n_sub();
     if (g.far_mode != 0) {
         S.farbox.assign(N, 0);

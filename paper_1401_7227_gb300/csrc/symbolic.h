@@ -74,6 +74,7 @@ struct SysSym {
     int prec = 0;  // element size class of the fine-row values: 0 f64, 1 f32, 2 f16
     int lump32 = 0;  // lump-row values stored in FP32 (else FP64)
     int colsum = 1;
+    int chunk_force = 0;  // stream-chunk capacity asked for (bytes; 0: each subdomain's own rule)
     // far boxes
     int nboxes = 0;
     std::vector<int> farbox;     // [N]
@@ -88,9 +89,11 @@ struct SysSym {
 
 // Builds the whole symbolic structure; returns "" or an error message.  prec: 0 f64, 1 f32,
 // 2 f16 element storage of fine-row factors; lump32: lump-row factors stored in FP32 (else FP64);
-// colsum: compensation on/off.  threads <= 0: auto.
+// colsum: compensation on/off.  threads <= 0: auto.  chunk_force: 0, or the stream-chunk capacity
+// in bytes (a multiple of 4096 in [kStreamChunkMin, kStreamChunkMax]) for every subdomain, raised
+// where one row needs more.
 std::string build_symbolic(const Geom& g, const Pattern& A, int prec, int lump32, int colsum, SysSym& out,
-                           int threads);
+                           int threads, int chunk_force = 0);
 
 // local row of every cell for subdomain s (-1 = outside), from the stored lists
 void local_map(const SysSym& S, int s, std::vector<int>& map);

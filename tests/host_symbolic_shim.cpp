@@ -40,9 +40,10 @@ std::vector<int> to_bsr(const Pattern& P, const std::vector<int>& locs) {
 extern "C" {
 
 // geo = {nx, ny, nz, px, py, pz, ov, near_width, cn[3], far_mode, cf[3]}; lump32: lump-row
-// factors in FP32 (FP32/FP16 fine rows only); NULL on error (message in err)
+// factors in FP32 (FP32/FP16 fine rows only); chunk_force: stream-chunk capacity in bytes (0: the
+// per-subdomain rule); NULL on error (message in err)
 void* hs_create(const int* geo, int n, int nnzb, const int* rp, const int* ci, int prec, int lump32, int colsum,
-                char* err, int errlen) {
+                char* err, int errlen, int chunk_force) {
     Geom g;
     g.nx = geo[0];
     g.ny = geo[1];
@@ -57,7 +58,7 @@ void* hs_create(const int* geo, int n, int nnzb, const int* rp, const int* ci, i
     for (int d = 0; d < 3; d++) g.cf[d] = geo[12 + d];
     Handle* h = new Handle();
     std::string e = build_pattern(n, rp, ci, nnzb, h->pat);
-    if (e.empty()) e = build_symbolic(g, h->pat, prec, lump32, colsum, h->sym, 0);
+    if (e.empty()) e = build_symbolic(g, h->pat, prec, lump32, colsum, h->sym, 0, chunk_force);
     if (!e.empty()) {
         std::strncpy(err, e.c_str(), (size_t)errlen - 1);
         err[errlen - 1] = 0;

@@ -71,7 +71,7 @@ def hs(tmp_path_factory):
     lib = C.CDLL(out)
     lib.hs_create.restype = C.c_void_p
     lib.hs_create.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_char_p,
-                              C.c_int]
+                              C.c_int, C.c_int]
     lib.hs_destroy.argtypes = [C.c_void_p]
     lib.hs_get.restype = C.c_longlong
     lib.hs_get.argtypes = [C.c_void_p, C.c_int, C.c_char_p, C.c_void_p]
@@ -84,7 +84,7 @@ class Sym:
 
     DTYPES = {"chunk_off": np.int64, "pk_off_f": np.int64, "pk_off_c": np.int64, "stream": np.uint8}
 
-    def __init__(self, lib, g, s, prec=0, colsum=1, lump32=0):
+    def __init__(self, lib, g, s, prec=0, colsum=1, lump32=0, chunk_force=0):
         geo = np.array([g.nx, g.ny, g.nz, g.px, g.py, g.pz, g.ov, g.near_width, *g.cnear, g.far_mode,
                         *(g.cfar if g.far_mode == 2 else (1, 1, 1))], dtype=np.int32)
         rp = np.ascontiguousarray(s.row_ptr, dtype=np.int32)
@@ -92,7 +92,7 @@ class Sym:
         err = C.create_string_buffer(256)
         self.lib = lib
         self.h = lib.hs_create(geo.ctypes.data, s.n_cells, s.nnzb, rp.ctypes.data, ci.ctypes.data, prec, lump32, colsum,
-                               err, 256)
+                               err, 256, chunk_force)
         assert self.h, err.value.decode()
 
     def __del__(self):
@@ -231,7 +231,35 @@ def decode_chunks(sym, sd, prec, lump32=0):
 def test_factor_stream_is_a_valid_schedule(hs, name, prec, lump32):
     g, seed = WIDE if name == "wide" else GEOMS[name]
     s = synth.grid_jacobian(g.nx, g.ny, g.nz, seed)
-    sym = Sym(hs, g, s, prec=prec, lump32=lump32)
+    check_stream(Sym(hs, g, s, prec=prec, lump32=lump32), g, prec, lump32)
+
+
+@pytest.mark.parametrize("prec,lump32", [(0, 0), (1, 1)])
+@pytest.mark.parametrize("chunk_kb", [8, 12, 24])
+@pytest.mark.parametrize("name", ["cfg1", "k32", "wide"])
+def test_forced_chunk_capacity_gives_a_valid_schedule(hs, name, chunk_kb, prec, lump32):
+    """The tiling tuner's capacities (ASM_TUNE_CHUNK_KB): every subdomain gets exactly the capacity
+    asked for (no row of these geometries needs more), chunks stay within it, and the stream is
+    still a valid schedule with the same rows as under the rule."""
+    g, seed = WIDE if name == "wide" else GEOMS[name]
+    s = synth.grid_jacobian(g.nx, g.ny, g.nz, seed)
+    sym = Sym(hs, g, s, prec=prec, lump32=lump32, chunk_force=chunk_kb * 1024)
+    rule = Sym(hs, g, s, prec=prec, lump32=lump32)
+    for sd in range(g.n_sub):
+        assert sym.info(sd)["chunk_cap"] == chunk_kb * 1024
+        np.testing.assert_array_equal(sym.get(sd, "row_of_pos"), rule.get(sd, "row_of_pos"))
+    check_stream(sym, g, prec, lump32)
+
+
+def test_forced_chunk_capacity_out_of_range_is_refused(hs):
+    g, seed = GEOMS["cfg1"]
+    s = synth.grid_jacobian(g.nx, g.ny, g.nz, seed)
+    for bad in (4096, 10000, 28672):
+        with pytest.raises(AssertionError, match="capacity out of range"):
+            Sym(hs, g, s, chunk_force=bad)
+
+
+def check_stream(sym, g, prec, lump32):
     for sd in range(g.n_sub):
         inf = sym.info(sd)
         n, nf, cap = inf["n"], inf["nf"], inf["chunk_cap"]
@@ -305,7 +333,7 @@ def test_symbolic_errors_are_reported(hs):
     ci = np.array([0, 1, 1, 2, 3], dtype=np.int32)   # (0, 1) without (1, 0)
     geo = np.array([2, 1, 2, 1, 1, 1, 0, 0, 1, 1, 1, 0, 1, 1, 1], dtype=np.int32)
     err = C.create_string_buffer(256)
-    h = hs.hs_create(geo.ctypes.data, 4, 5, rp.ctypes.data, ci.ctypes.data, 0, 0, 1, err, 256)
+    h = hs.hs_create(geo.ctypes.data, 4, 5, rp.ctypes.data, ci.ctypes.data, 0, 0, 1, err, 256, 0)
     assert not h
     assert b"symmetric" in err.value
 
