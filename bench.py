@@ -469,7 +469,8 @@ def run_nf(args, stream, w, w_system, vals_d, b_d):
 def run_profile_case(args):
     """Small case for ncu captures: 128 x 128 x 32 (16 x 16 x 1 subdomains, overlap 2), three
     preconditioner applies then one GMRES solve.  The apply runs with the local-vector placement the
-    1M-cell workload's online tuner picks (all local vectors in shared memory, four ring slots)."""
+    1M-cell workload runs with (the placement rule and the tiling tuner both give all local vectors
+    in device memory, 256-thread CTAs, four per SM, two ring slots)."""
     import torch
     from paper_1401_7227_gb300 import asm2
     from paper_1401_7227_gb300 import build as lib_build
@@ -480,7 +481,7 @@ def run_profile_case(args):
     sol.set_matrix(s.row_ptr, s.col_idx, s.vals)
     sol.set_partition(16, 16, 1, 2)
     sol.factor()
-    sol.set_tuning(apply_smem="shared")
+    sol.set_tuning(apply_smem="device", autotune=False)
     b = torch.from_numpy(s.b).cuda()
     for _ in range(3):
         sol.apply(b)
@@ -748,7 +749,11 @@ def run_gpu(args):
         s.set_grid(w.nx, w.ny, w.nz)
         s.set_matrix(system.row_ptr, system.col_idx, vals_d)
         s.set_partition(w.px, w.py, w.pz, w.overlap)
+        if args.chunk_kb is not None:
+            s.set_tuning(chunk_kb=args.chunk_kb)
         s.factor()
+        if args.placement is not None:  # a fixed placement: no online tuning
+            s.set_tuning(apply_smem=args.placement, autotune=False)
         return s
 
     def barrier():
@@ -926,6 +931,9 @@ def main():
     ap.add_argument("--profile-nf", action="store_true", help="nested-factorisation apply case for ncu captures")
     ap.add_argument("--profile-kernels", action="store_true", help="every kernel family, for one ncu capture")
     ap.add_argument("--no-tune", action="store_true", help="keep the default tiling (no asm_tune_tiling)")
+    ap.add_argument("--placement", choices=["auto", "device", "lumps", "shared"], default=None,
+                    help="with --no-tune: fix the apply's placement (for profiling runs)")
+    ap.add_argument("--chunk-kb", type=int, default=None, help="with --no-tune: fix the stream-chunk capacity")
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--serve-warm", type=int, default=300)
     ap.add_argument("--serve-rate", type=float, default=200.0)
@@ -940,6 +948,8 @@ def main():
         return run_profile_nf(args)
     if args.profile_kernels:
         return run_profile_kernels(args)
+    if args.placement is not None or args.chunk_kb is not None:
+        args.no_tune = True
     return run_gpu(args)
 
 
