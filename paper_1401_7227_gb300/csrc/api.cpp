@@ -105,7 +105,8 @@ struct asm_ctx {
     int n_along = 0;  // slots whose assembly lists are summed by a warp each
     DBuf d_fp;  // factor program arrays (one allocation, see upload_factor_program)
     DBuf d_stream, d_pk_off_f, d_pk_src_f, d_pk_off_c, d_pk_src_c;
-    DBuf d_lv, d_rlists, d_y, d_corr_cells, d_corr, d_dev_err;
+    DBuf d_lv, d_rlists, d_y, d_corr_cells, d_corr, d_dev_err, d_gsum;
+    int n_group_items = 0;  // box_items[0 .. n_group_items): the cell-group sums (kind 2)
     int apply_smem = 0;       // shared memory for all local vectors of the largest subdomain (0: none)
     int apply_smem_need = 0;  // the same before the fit test of choose_ring()
     int apply_lump_smem = 0;  // shared memory for its lump vector and the FP32 mirror
@@ -710,16 +711,28 @@ void upload_symbolic(asm_ctx* h) {
     h->d_pk_src_f.upload(srcf, st);
     h->d_pk_off_c.upload(offc, st);
     h->d_pk_src_c.upload(srcc, st);
-    // far boxes, their near-region corrections, and the coarse matrix
+    // cell-group sums (when any sum list may use them), far boxes, their near-region corrections,
+    // and the coarse matrix
     h->box_items.clear();
+    h->n_group_items = 0;
+    bool sum_lists = S.g.far_mode != 0;
+    for (const SubSym& o : S.subs) sum_lists = sum_lists || !o.rsrc.empty();
+    if (sum_lists) {
+        const int ng = n_groups(S.g);
+        h->d_gsum.alloc((size_t)ng * 3 * sizeof(double));
+        for (int g0 = 0; g0 < ng; g0 += 256) h->box_items.push_back(BoxItem{0, 0, g0, std::min(ng, g0 + 256), 2, 0, nullptr});
+        h->n_group_items = (int)h->box_items.size();
+    } else {
+        h->d_gsum.alloc(16);
+    }
     if (S.g.far_mode != 0) {
-        h->d_bcell.upload(S.bcell, st);
+        h->d_bcell.upload(S.bsum, st);
         h->d_cptr.upload(S.cptr, st);
         h->d_cloc.upload(bsr_of_locs(h->pat, S.cloc), st);
         h->d_cval.alloc((size_t)std::max(1, S.nC) * 9 * sizeof(double));
         h->d_boxsum.alloc((size_t)std::max(1, S.nboxes) * 3 * sizeof(double));
         for (int b = 0; b < S.nboxes; b++)
-            h->box_items.push_back(BoxItem{0, b, S.bptr[b], S.bptr[b + 1], 0, 0, h->d_bcell.as<int>()});
+            h->box_items.push_back(BoxItem{0, b, S.bsum_ptr[b], S.bsum_ptr[b + 1], 0, 0, h->d_bcell.as<int>()});
     } else {
         h->d_cval.alloc(16);
         h->d_boxsum.alloc(16);
@@ -788,6 +801,10 @@ void ensure_workspace(asm_ctx* h) {
     t.rows_pad = h->pat.rows_pad;
     t.boxsum = h->d_boxsum.as<double>();
     t.corr = h->d_corr.p ? h->d_corr.as<double>() : h->d_boxsum.as<double>();
+    t.gsum = h->d_gsum.p ? h->d_gsum.as<double>() : h->d_boxsum.as<double>();
+    t.gnx = h->geom.nx;
+    t.gny = h->geom.ny;
+    t.gnz = h->geom.nz;
     if (!h->d_dev_err.p) {
         h->d_dev_err.alloc(16);
         h->d_dev_err.zero(h->stream);
@@ -1044,6 +1061,7 @@ struct Batch {
     DBuf d_tab, d_vec, d_row, d_box, d_sub, d_gather, d_ritems;
     int nritems = 0;
     int nvec = 0, nrow = 0, nbox = 0, nsub = 0, prec = 0, slots = 3, chunk = kStreamChunkMin;
+    int ngroup = 0;  // d_box[0 .. ngroup): every system's cell-group sum items
     bool lump32 = false;
     ApplyConfig apply{Y_DEVICE, 0, 2, kStreamChunkMin};
     int all_bytes = 0, lump_bytes = 0;  // largest subdomain's shared-memory needs (placements)
@@ -1079,7 +1097,17 @@ void build_batch(Batch& B, cudaStream_t st) {
         tabs.push_back(h->tab);
         for (int c = 0; c < h->nchunk; c++) vi.push_back(VecItem{k, c});
         for (int r = 0; r < h->N; r += 256) ri.push_back(RowItem{k, r});
-        for (BoxItem b : h->box_items) {
+        for (int j = 0; j < h->n_group_items; j++) {
+            BoxItem b = h->box_items[j];
+            b.sys = k;
+            bi.push_back(b);
+        }
+    }
+    B.ngroup = (int)bi.size();
+    for (int k = 0; k < (int)B.hs.size(); k++) {
+        const asm_ctx* h = B.hs[k];
+        for (size_t j = h->n_group_items; j < h->box_items.size(); j++) {
+            BoxItem b = h->box_items[j];
             b.sys = k;
             bi.push_back(b);
         }
@@ -1232,7 +1260,7 @@ void launch_step(Batch& B, int kmax, cudaStream_t st, StepEvents* ev) {
     if (B.has_init) launch_init(tab, vi, B.nvec, st);
     launch_prep(tab, vi, B.nvec, st);
     if (ev) ck(cudaEventRecord(ev->e[1], st));
-    launch_boxsum(tab, B.d_box.as<BoxItem>(), B.nbox, st);
+    launch_boxsum(tab, B.d_box.as<BoxItem>(), B.nbox, B.ngroup, st);
     launch_local_solves(B, tab, st);
     launch_coarse_apply(tab, B.d_row.as<RowItem>(), B.nrow, B.d_cbox.as<BoxItem>(), B.ncbox, B.d_cgrow.as<RowItem>(),
                         B.ncgrow, vi, B.nvec, B.two_stage, st);
@@ -1263,7 +1291,7 @@ void launch_step_om(Batch& B, int kmax, cudaStream_t st, StepEvents* ev) {
     if (ev) ck(cudaEventRecord(ev->e[0], st));
     if (B.has_init) launch_init(tab, vi, B.nvec, st);
     if (ev) ck(cudaEventRecord(ev->e[1], st));
-    launch_boxsum(tab, B.d_box.as<BoxItem>(), B.nbox, st);
+    launch_boxsum(tab, B.d_box.as<BoxItem>(), B.nbox, B.ngroup, st);
     launch_local_solves(B, tab, st);
     launch_coarse_apply(tab, B.d_row.as<RowItem>(), B.nrow, B.d_cbox.as<BoxItem>(), B.ncbox, B.d_cgrow.as<RowItem>(),
                         B.ncgrow, vi, B.nvec, B.two_stage, st);
@@ -2089,7 +2117,8 @@ int asm_apply_precond(asm_handle h, const double* r, double* z, int on_device) {
         double* out = h->d_ws.as<double>() + (long long)VZ * h->n3p;
         copy_in(h, in, r, bytes, on_device);
         set_ctl(h, VU, VZ, -1, -1, -1);
-        launch_boxsum(h->d_tab1.as<SysTab>(), h->d_box1.as<BoxItem>(), (int)h->box_items.size(), h->stream);
+        launch_boxsum(h->d_tab1.as<SysTab>(), h->d_box1.as<BoxItem>(), (int)h->box_items.size(), h->n_group_items,
+                      h->stream);
         if (is_nf(h)) {
             launch_nf_apply(h->d_tab1.as<SysTab>(), h->d_nfdesc1.as<NFDesc>(), (int)h->nf_desc.size(), h->prec,
                             h->nf_slots, h->nf_smem, h->stream);
@@ -2137,7 +2166,8 @@ int asm_tune_tiling(asm_handle h, int reps, asm_tiling_report* out) {
             std::vector<float> t;
             for (int k = 0; k < reps + 2; k++) {
                 ck(cudaEventRecord(e0, h->stream));
-                launch_boxsum(h->d_tab1.as<SysTab>(), h->d_box1.as<BoxItem>(), (int)h->box_items.size(), h->stream);
+                launch_boxsum(h->d_tab1.as<SysTab>(), h->d_box1.as<BoxItem>(), (int)h->box_items.size(), h->n_group_items,
+                      h->stream);
                 launch_ilu_local_solves(h, cfg);
                 ck(cudaEventRecord(e1, h->stream));
                 ck(cudaEventSynchronize(e1));
@@ -2228,6 +2258,7 @@ int asm_spmv(asm_handle h, const double* x, double* y, int on_device) {
         if (!h->sym_valid) {
             // SpMV needs only A; give it a workspace without a preconditioner
             h->box_items.clear();
+            h->n_group_items = 0;
             if (!h->d_boxsum.p) h->d_boxsum.alloc(16);
         }
         ensure_workspace(h);

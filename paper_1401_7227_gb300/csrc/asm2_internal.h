@@ -120,6 +120,8 @@ struct SysTab {
     // preconditioner
     double* boxsum;      // [n_boxes * 3] far-box sums of the apply input
     double* corr;        // [n_corr * 3] near-region sums subtracted from far-lump box sums
+    double* gsum;        // [n_groups * 3] sums of the apply input over aligned 2x2x2 cell groups
+    int gnx, gny, gnz;   // grid size (for the cells of a group)
     int* dev_err;        // device status word: nonzero after a bounded wait expired
     long long wait_limit;  // polls of the first wait on each factor-stream copy of the apply kernels
     // classical coarse-grid correction (0 none, 1 two-level, 2 two-stage; Eqs. 3.5-3.8)
@@ -139,7 +141,10 @@ struct VecItem {   // VEC_CHUNK elements [e0, e0 + VEC_CHUNK) of system sys; chu
 struct RowItem {   // rows [r0, r0 + 256) of system sys
     int sys, r0;
 };
-struct BoxItem {   // sum over cells[b0 .. b1) of the apply input into boxsum[out] (kind 0) or corr[out] (kind 1)
+// kind 0 / 1: sum over the sum list cells[b0 .. b1) (cells >= 0 and cell groups ~g) of the apply
+// input into boxsum[out] / corr[out]; kind 2: the group sums gsum of groups b0 .. b1 - 1 (these
+// items come first and run in their own launch, before the lists that read them)
+struct BoxItem {
     int sys, out, b0, b1;
     int kind, pad_;
     const int* cells;
@@ -244,7 +249,8 @@ void launch_pack(const long long* off, const int* src, long long n, int prec, un
 void launch_ell_fill(const double* bsr_vals, const int* row_ptr, int n, int ell_w, double* ell_val, int rows_pad,
                      cudaStream_t st);
 
-void launch_boxsum(const SysTab* st_tab, const BoxItem* items, int nitems, cudaStream_t st);
+// items[0 .. ngroup): group-sum items (kind 2), then the box and correction sums
+void launch_boxsum(const SysTab* st_tab, const BoxItem* items, int nitems, int ngroup, cudaStream_t st);
 // ysmem: shared memory for the local vectors (0 = they stay in the global scratch SubDesc.y);
 // the ring of factor-stream slots is added on top
 void launch_apply(const SysTab* st_tab, const SubDesc* subs, int nsub, int prec, bool lump32, ApplyConfig cfg,

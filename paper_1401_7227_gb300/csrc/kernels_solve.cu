@@ -93,6 +93,40 @@ __device__ __forceinline__ void block_mv_sub<__half>(const unsigned char* p, flo
 // gather sums of the apply input: far-box sums (kind 0) and, per subdomain, the sums of the
 // near-region cells of each far box (kind 1); a far lump's restricted residual is their difference
 // ------------------------------------------------------------------------------------------
+// the 3-vector of one sum-list entry: a cell's entries of r, or a cell group's sum
+__device__ __forceinline__ const double* sum_entry(const SysTab& st, const double* r, int e) {
+    return e >= 0 ? r + 3LL * e : st.gsum + 3LL * ~e;
+}
+
+// Sums of the apply input over aligned 2x2x2 cell groups, thread per group, the group's cells in a
+// fixed order (y, then x, then z): every list sum that covers whole groups reads these instead
+__global__ void __launch_bounds__(256) k_groups(const SysTab* __restrict__ tab, const BoxItem* __restrict__ items) {
+    const BoxItem it = items[blockIdx.x];
+    const SysTab& st = tab[it.sys];
+    const int in = st.ctl[C_APPLY_IN];
+    if (in < 0) return;
+    const int G = it.b0 + threadIdx.x;
+    if (G >= it.b1) return;
+    const double* r = st.ws + (long long)in * st.n3p;
+    const int ngz = (st.gnz + 1) >> 1, ngx = (st.gnx + 1) >> 1;
+    const int gz = G % ngz, t = G / ngz, gx = t % ngx, gy = t / ngx;
+    const int z0 = 2 * gz, x0 = 2 * gx, y0 = 2 * gy;
+    const int z1 = min(z0 + 2, st.gnz), x1 = min(x0 + 2, st.gnx), y1 = min(y0 + 2, st.gny);
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int y = y0; y < y1; y++)
+        for (int x = x0; x < x1; x++)
+            for (int z = z0; z < z1; z++) {
+                const double* rc = r + 3LL * (z + (long long)st.gnz * (x + (long long)st.gnx * y));
+                a0 += rc[0];
+                a1 += rc[1];
+                a2 += rc[2];
+            }
+    double* o = st.gsum + 3LL * G;
+    o[0] = a0;
+    o[1] = a1;
+    o[2] = a2;
+}
+
 __global__ void __launch_bounds__(128) k_sums(const SysTab* __restrict__ tab, const BoxItem* __restrict__ items) {
     const BoxItem it = items[blockIdx.x];
     const SysTab& st = tab[it.sys];
@@ -102,10 +136,10 @@ __global__ void __launch_bounds__(128) k_sums(const SysTab* __restrict__ tab, co
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
 #pragma unroll 4
     for (int i = it.b0 + threadIdx.x; i < it.b1; i += blockDim.x) {
-        const long long c = (long long)it.cells[i] * 3;
-        a0 += r[c];
-        a1 += r[c + 1];
-        a2 += r[c + 2];
+        const double* v = sum_entry(st, r, it.cells[i]);
+        a0 += v[0];
+        a1 += v[1];
+        a2 += v[2];
     }
     __shared__ double red[3][128];
     red[0][threadIdx.x] = a0;
@@ -551,7 +585,7 @@ __device__ __forceinline__ void restrict_local(const SysTab& st, const SubDesc& 
         }
 #pragma unroll 8
         for (int i = i0; i < i1; i++) {
-            const double* rc = r + 3LL * sd.rsrc[i];
+            const double* rc = sum_entry(st, r, sd.rsrc[i]);
             a0 += rc[0];
             a1 += rc[1];
             a2 += rc[2];
@@ -564,7 +598,7 @@ __device__ __forceinline__ void restrict_local(const SysTab& st, const SubDesc& 
         const int c = sd.clong[k];
         double a0 = 0.0, a1 = 0.0, a2 = 0.0;
         for (int i = sd.rptr[c] + lane; i < sd.rptr[c + 1]; i += 32) {
-            const double* rc = r + 3LL * sd.rsrc[i];
+            const double* rc = sum_entry(st, r, sd.rsrc[i]);
             a0 += rc[0];
             a1 += rc[1];
             a2 += rc[2];
@@ -627,20 +661,20 @@ __global__ void __launch_bounds__(256) k_restrict(const SysTab* __restrict__ tab
     }
     const int i0 = sd.rptr[c], i1 = sd.rptr[c + 1];
     for (int i = i0; i < i1; i += 4) {
-        int cell[4];
+        const double* src[4];
 #pragma unroll
-        for (int u = 0; u < 4; u++) cell[u] = i + u < i1 ? sd.rsrc[i + u] : -1;
+        for (int u = 0; u < 4; u++) src[u] = i + u < i1 ? sum_entry(st, r, sd.rsrc[i + u]) : nullptr;
         double v[4][3];
 #pragma unroll
         for (int u = 0; u < 4; u++) {
-            const double* rc = r + 3LL * (cell[u] >= 0 ? cell[u] : 0);
+            const double* rc = src[u] != nullptr ? src[u] : r;
             v[u][0] = rc[0];
             v[u][1] = rc[1];
             v[u][2] = rc[2];
         }
 #pragma unroll
         for (int u = 0; u < 4; u++)
-            if (cell[u] >= 0) {
+            if (src[u] != nullptr) {
                 a0 += v[u][0];
                 a1 += v[u][1];
                 a2 += v[u][2];
@@ -1451,8 +1485,9 @@ __global__ void __launch_bounds__(VEC_THREADS, 2) k_ortho_coop(const SysTab* __r
 
 }  // namespace
 
-void launch_boxsum(const SysTab* tab, const BoxItem* items, int nitems, cudaStream_t st) {
-    if (nitems > 0) k_sums<<<nitems, 128, 0, st>>>(tab, items);
+void launch_boxsum(const SysTab* tab, const BoxItem* items, int nitems, int ngroup, cudaStream_t st) {
+    if (ngroup > 0) k_groups<<<ngroup, 256, 0, st>>>(tab, items);
+    if (nitems > ngroup) k_sums<<<nitems - ngroup, 128, 0, st>>>(tab, items + ngroup);
 }
 
 size_t apply_smem_bytes(int nf, int nc, int prec, bool lump32) { return y_layout(nf, nc, prec, lump32).total; }

@@ -74,6 +74,34 @@ bool inside(const Box& a, const Box& b) {  // a within b (a non-empty)
 
 inline int cell_of(const Geom& g, int x, int y, int z) { return z + g.nz * (x + g.nx * y); }
 
+// cells of group G inside the grid
+int group_size(const Geom& g, int G) {
+    const int gz = G % group_dims(g.nz), t = G / group_dims(g.nz), gx = t % group_dims(g.nx), gy = t / group_dims(g.nx);
+    return std::min(2, g.nx - 2 * gx) * std::min(2, g.ny - 2 * gy) * std::min(2, g.nz - 2 * gz);
+}
+
+// Appends the sum list of a set of distinct cells to out: every group whose cells in the grid all
+// belong to the set becomes one entry ~G, at the place of its first cell in `cells`; the other
+// cells stay, in their order.  cnt / done: scratch of n_groups(g) entries, zero on entry and exit.
+void append_sum_list(const Geom& g, const int* cells, int n, std::vector<int>& out, std::vector<int>& cnt,
+                     std::vector<char>& done) {
+    for (int i = 0; i < n; i++) cnt[cell_group(g, cells[i])]++;
+    for (int i = 0; i < n; i++) {
+        const int G = cell_group(g, cells[i]);
+        if (cnt[G] == group_size(g, G)) {
+            if (!done[G]) out.push_back(~G);
+            done[G] = 1;
+        } else {
+            out.push_back(cells[i]);
+        }
+    }
+    for (int i = 0; i < n; i++) {
+        const int G = cell_group(g, cells[i]);
+        cnt[G] = 0;
+        done[G] = 0;
+    }
+}
+
 struct Tup {
     int p, q, v;  // kind: 0 plus (v = ELL loc), 1 minus (v = ELL loc), 2 coarse (v = C slot)
     int kind;
@@ -405,16 +433,21 @@ std::string build_sub(const Ctx& X, int s, SubSym& o) {
     o.clong.clear();
     o.corr_ptr.assign(1, 0);
     o.corr_cells.clear();
+    static thread_local std::vector<int> gcnt;
+    static thread_local std::vector<char> gdone;
+    gcnt.assign(n_groups(g), 0);
+    gdone.assign(n_groups(g), 0);
     for (int c = 0; c < nc; c++) {
         const int p = row_of_c[c];
         if (p < nN) {
-            for (int t = rowcells_ptr[p]; t < rowcells_ptr[p + 1]; t++) o.rsrc.push_back(rowcells[t]);
+            append_sum_list(g, rowcells.data() + rowcells_ptr[p], rowcells_ptr[p + 1] - rowcells_ptr[p], o.rsrc, gcnt,
+                            gdone);
         } else {
             const int J = far_box_of_row[p - nN];
             o.rbox[c] = J;
             if (!corr[J].empty()) {
                 o.rcorr[c] = (int)o.corr_ptr.size() - 1;
-                o.corr_cells.insert(o.corr_cells.end(), corr[J].begin(), corr[J].end());
+                append_sum_list(g, corr[J].data(), (int)corr[J].size(), o.corr_cells, gcnt, gdone);
                 o.corr_ptr.push_back((int)o.corr_cells.size());
             }
         }
@@ -726,6 +759,16 @@ std::string build_symbolic(const Geom& g, const Pattern& A, int prec, int lump32
         {
             std::vector<int> fill(S.bptr.begin(), S.bptr.end() - 1);
             for (int c = 0; c < N; c++) S.bcell[fill[S.farbox[c]]++] = c;
+        }
+        {
+            std::vector<int> cnt(n_groups(g), 0);
+            std::vector<char> done(n_groups(g), 0);
+            S.bsum_ptr.assign(1, 0);
+            S.bsum.clear();
+            for (int b = 0; b < S.nboxes; b++) {
+                append_sum_list(g, S.bcell.data() + S.bptr[b], S.bptr[b + 1] - S.bptr[b], S.bsum, cnt, done);
+                S.bsum_ptr.push_back((int)S.bsum.size());
+            }
         }
     }
     Ctx X{g, A, S, prec, colsum, {}};

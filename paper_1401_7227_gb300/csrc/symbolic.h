@@ -52,6 +52,9 @@ struct SubSym {
     // restriction: fcell by fine index; lump rows by lump index (rptr/rsrc/rbox), clong = lump
     // rows with long lists; owned-cell scatter (own_pos = fine index)
     std::vector<int> fcell, rptr, rsrc, rbox, clong, own_pos, own_cell;
+    // Sum lists (rsrc, corr_cells, and SysSym::bsum) hold cells (>= 0) and cell groups (~g < 0):
+    // an aligned 2 x 2 x 2 group whose cells inside the grid all belong to the list stands for
+    // them; its sum is formed once per apply (cell_group()).
     // far lumps: rcorr = index of the lump's correction list (or -1); corr_ptr/corr_cells = the
     // near-region cells of each far box, summed by a gather pass and subtracted from the box sum
     std::vector<int> rcorr, corr_ptr, corr_cells;
@@ -79,6 +82,7 @@ struct SysSym {
     int nboxes = 0;
     std::vector<int> farbox;     // [N]
     std::vector<int> bptr, bcell;
+    std::vector<int> bsum_ptr, bsum;  // each far box's cells as a sum list (cells and cell groups)
     // coarse (far-box) coupling matrix C: blocks summed over box pairs
     int nC = 0;
     std::vector<int> cptr, cloc;
@@ -94,6 +98,15 @@ struct SysSym {
 // where one row needs more.
 std::string build_symbolic(const Geom& g, const Pattern& A, int prec, int lump32, int colsum, SysSym& out,
                            int threads, int chunk_force = 0);
+
+// Aligned 2 x 2 x 2 cell groups: group of a cell, group count, and a group's cells in the grid
+// (x, y, z each in {2 g, 2 g + 1} within the grid; z fastest, as cells are numbered)
+inline int group_dims(int n) { return (n + 1) / 2; }
+inline int cell_group(const Geom& g, int c) {
+    const int z = c % g.nz, t = c / g.nz, x = t % g.nx, y = t / g.nx;
+    return (z >> 1) + group_dims(g.nz) * ((x >> 1) + group_dims(g.nx) * (y >> 1));
+}
+inline int n_groups(const Geom& g) { return group_dims(g.nx) * group_dims(g.ny) * group_dims(g.nz); }
 
 // local row of every cell for subdomain s (-1 = outside), from the stored lists
 void local_map(const SysSym& S, int s, std::vector<int>& map);

@@ -91,6 +91,8 @@ long long hs_get(void* p, int s, const char* what, void* out) {
         if (w == "ell_shape") return put(std::vector<int>{h.pat.ell_w, h.pat.rows_pad}, out);
         if (w == "ell_loc") return put(h.pat.ell_loc, out);
         if (w == "ell_col") return put(h.pat.ell_col, out);
+        if (w == "bsum_ptr") return put(h.sym.bsum_ptr, out);
+        if (w == "bsum") return put(h.sym.bsum, out);
         return -1;
     }
     const SubSym& o = h.sym.subs[s];
@@ -117,6 +119,12 @@ long long hs_get(void* p, int s, const char* what, void* out) {
     if (w == "pk_src_f") return put(o.pk_src_f, out);
     if (w == "pk_off_c") return put(o.pk_off_c, out);
     if (w == "pk_src_c") return put(o.pk_src_c, out);
+    if (w == "rptr") return put(o.rptr, out);
+    if (w == "rsrc") return put(o.rsrc, out);
+    if (w == "rbox") return put(o.rbox, out);
+    if (w == "rcorr") return put(o.rcorr, out);
+    if (w == "corr_ptr") return put(o.corr_ptr, out);
+    if (w == "corr_cells") return put(o.corr_cells, out);
     return -1;
 }
 

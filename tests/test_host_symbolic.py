@@ -392,3 +392,57 @@ def test_ell_layout_is_a_bijection_onto_bsr_blocks(hs, name):
     free = np.nonzero(~used)[0]
     r = free % pad
     np.testing.assert_array_equal(col[free], np.where(r < n, r, 0))
+
+
+def expand_sum_list(g, entries):
+    """cells of a sum list: cells (>= 0) and aligned 2x2x2 cell groups (~group), as a sorted array"""
+    ngz, ngx = (g.nz + 1) // 2, (g.nx + 1) // 2
+    out = []
+    for e in entries:
+        if e >= 0:
+            out.append(int(e))
+            continue
+        G = ~int(e)
+        gz, t = G % ngz, G // ngz
+        gx, gy = t % ngx, t // ngx
+        for y in range(2 * gy, min(2 * gy + 2, g.ny)):
+            for x in range(2 * gx, min(2 * gx + 2, g.nx)):
+                for z in range(2 * gz, min(2 * gz + 2, g.nz)):
+                    out.append(z + g.nz * (x + g.nx * y))
+    return np.sort(np.array(out, dtype=np.int64))
+
+
+@pytest.mark.parametrize("name", list(GEOMS) + ["aligned"])
+def test_restriction_sum_lists_cover_the_lump_cells(hs, name):
+    """The lump rows' restriction (Eqs. 4.1, B.2) through the sum lists the apply reads: a near lump
+    sums its list, a far lump its far box's list minus its near-region correction list, where a
+    cell group stands for its cells in the grid.  Every lump must sum exactly the cells the oracle's
+    local map assigns to it, each once."""
+    g, seed = (O.Geometry(16, 16, 8, 2, 2, 1, ov=2), 26) if name == "aligned" else GEOMS[name]
+    s = synth.grid_jacobian(g.nx, g.ny, g.nz, seed)
+    sym = Sym(hs, g, s)
+    pc = O.Precond(g, s.row_ptr, s.col_idx, s.vals)
+    bptr, bsum = sym.get(-1, "bsum_ptr"), sym.get(-1, "bsum")
+    groups_used = 0
+    for sd in range(g.n_sub):
+        inf = sym.info(sd)
+        omap = pc.sub_map(sd)
+        cid = sym.get(sd, "cidx_of_row")
+        rptr, rsrc, rbox, rcorr = (sym.get(sd, k) for k in ("rptr", "rsrc", "rbox", "rcorr"))
+        cptr, ccells = sym.get(sd, "corr_ptr"), sym.get(sd, "corr_cells")
+        groups_used += int(np.sum(rsrc < 0) + np.sum(ccells < 0))
+        for p in range(inf["nf"], inf["n"]):
+            c = cid[p]
+            want = np.sort(np.nonzero(omap == p)[0])
+            if rbox[c] < 0:
+                got = expand_sum_list(g, rsrc[rptr[c]:rptr[c + 1]])
+            else:
+                J = rbox[c]
+                box = expand_sum_list(g, bsum[bptr[J]:bptr[J + 1]])
+                assert len(np.unique(box)) == len(box)
+                cut = expand_sum_list(g, ccells[cptr[rcorr[c]]:cptr[rcorr[c] + 1]]) if rcorr[c] >= 0 else []
+                assert np.all(np.isin(cut, box)) and len(np.unique(cut)) == len(cut)
+                got = np.setdiff1d(box, cut)
+            np.testing.assert_array_equal(got, want)
+    if name == "aligned":
+        assert groups_used > 0 and np.sum(bsum < 0) > 0
