@@ -103,25 +103,34 @@ __global__ void __launch_bounds__(256) k_gj_batched(const GJMat* __restrict__ ma
             }
         }
         grid.sync();
-        // (C) row k <- scaled pivot row; row p <- old row k minus its multiple; others in place
+        // (C) row k <- scaled pivot row; row p <- old row k minus its multiple; others in place.
+        // One warp per row: a row whose multiplier is zero keeps every entry (its pivot-column
+        // entry is already zero), so the warp skips it whole.
         if (go) {
-            const long long total = (long long)n * W;
-            for (long long t = gtid; t < total; t += gstride) {
-                const long long i = t / W, j = t - i * W;
+            const int wpc = blockDim.x >> 5, lane = threadIdx.x & 31;
+            const long long gw = (long long)rank * wpc + (threadIdx.x >> 5), nw = (long long)per * wpc;
+            for (long long i = gw; i < n; i += nw) {
                 if (i == p && p != k) continue;  // handled together with row k
-                const double pj = M.prow[j];
                 if (i == k) {
-                    if (p != k) {
-                        const double old_k = M.aug[(long long)k * W + j];
-                        M.aug[(long long)p * W + j] = (j == k) ? 0.0 : old_k - M.fcol[p] * pj;
+                    double* rk = M.aug + (long long)k * W;
+                    double* rp = M.aug + (long long)p * W;
+                    const double fp = M.fcol[p];
+                    for (long long j = lane; j < W; j += 32) {
+                        const double pj = M.prow[j];
+                        if (p != k) rp[j] = (j == k) ? 0.0 : rk[j] - fp * pj;
+                        rk[j] = pj;
                     }
-                    M.aug[(long long)k * W + j] = pj;
-                } else {
-                    const double f = M.fcol[i];
+                    continue;
+                }
+                const double f = M.fcol[i];
+                if (f == 0.0) continue;
+                double* ri = M.aug + i * W;
+                for (long long j = lane; j < W; j += 32) {
+                    const double pj = M.prow[j];
                     if (j == k)
-                        M.aug[i * W + j] = 0.0;
-                    else if (f != 0.0 && pj != 0.0)
-                        M.aug[i * W + j] -= f * pj;
+                        ri[j] = 0.0;
+                    else if (pj != 0.0)
+                        ri[j] -= f * pj;
                 }
             }
         }
