@@ -520,8 +520,9 @@ def run_profile_kernels(args):
     """Case for one ncu capture of every kernel family (time and DRAM bytes per launch): on
     128 x 128 x 32 (524,288 cells, 16 x 16 x 1 subdomains, overlap 2; inputs larger than L2):
     the ILU path with FP32 factors (set-up, applies, a few GMRES steps), ORTHOMIN, the two-level
-    coarse correction, nested factorisation; exact local solves on 32 x 32 x 16 (16 subdomains);
-    and two systems through the batched per-projection Gram-Schmidt path."""
+    coarse correction, nested factorisation; exact local solves on 16 x 16 x 8 (4 subdomains of
+    ~2,200 unknowns: their dense inverses stay within a few hundred MB); and two systems of
+    32 x 32 x 16 through the batched per-projection Gram-Schmidt path."""
     import torch
     from paper_1401_7227_gb300 import asm2
     from paper_1401_7227_gb300 import build as lib_build
@@ -559,9 +560,10 @@ def run_profile_kernels(args):
     out["nf"] = sol.solve(b, 1e-8, 3)[1]
     sol.close()
     small = synth.grid_jacobian(32, 32, 16, 4)
-    sol = make(local="exact", prec="fp64", sys=small, part=(4, 4, 1), ov=1)
-    sol.apply(torch.from_numpy(small.b).cuda())
-    out["exact"] = sol.solve(torch.from_numpy(small.b).cuda(), 1e-8, 3)[1]
+    tiny = synth.grid_jacobian(16, 16, 8, 4)
+    sol = make(local="exact", prec="fp64", sys=tiny, part=(2, 2, 1), ov=1)
+    sol.apply(torch.from_numpy(tiny.b).cuda())
+    out["exact"] = sol.solve(torch.from_numpy(tiny.b).cuda(), 1e-8, 3)[1]
     sol.close()
     bs = [make(sys=small, part=(4, 4, 1), ov=1) for _ in range(2)]
     out["batch"] = asm2.solve_batch(bs, [torch.from_numpy(small.b).cuda()] * 2, 1e-8, 3)[1]
@@ -744,8 +746,9 @@ def run_gpu(args):
     b_d = torch.from_numpy(system.b).cuda()
     stream = torch.cuda.current_stream()
 
-    def make_solver(prec, lumps):
-        s = asm2.Solver(precision=prec, restart=w.restart, device=local, stream=stream.cuda_stream, lumps=lumps)
+    def make_solver(prec, lumps, ortho="mgs"):
+        s = asm2.Solver(precision=prec, restart=w.restart, device=local, stream=stream.cuda_stream, lumps=lumps,
+                        ortho=ortho)
         s.set_grid(w.nx, w.ny, w.nz)
         s.set_matrix(system.row_ptr, system.col_idx, vals_d)
         s.set_partition(w.px, w.py, w.pz, w.overlap)
@@ -768,13 +771,15 @@ def run_gpu(args):
         return x, info
 
     results = {}
-    def vkey(prec, lumps):  # "fp64", "fp32", "fp16s" (FP32 lump rows), or "fp32_lumps_fp64", ...
-        return prec if prec == "fp64" or lumps == "fp32" else f"{prec}_lumps_fp64"
+    def vkey(prec, lumps, ortho="mgs"):  # "fp64", "fp32", "fp16s" (FP32 lumps), "fp32_lumps_fp64", "fp32_cgs"
+        k = prec if prec == "fp64" or lumps == "fp32" else f"{prec}_lumps_fp64"
+        return k if ortho == "mgs" else f"{k}_cgs"
 
     main_key = vkey(args.precision, args.lumps)
-    variants = [(args.precision, args.lumps)]
+    variants = [(args.precision, args.lumps, "mgs")]
     if not args.no_precisions:
-        for pv in (("fp64", "fp64"), ("fp32", "fp32"), ("fp16s", "fp32"), ("fp32", "fp64")):
+        for pv in (("fp64", "fp64", "mgs"), ("fp32", "fp32", "mgs"), ("fp16s", "fp32", "mgs"), ("fp32", "fp64", "mgs"),
+                   ("fp32", "fp32", "cgs")):
             if vkey(*pv) != main_key:
                 variants.append(pv)
     def tiling_summary(rep):
@@ -787,8 +792,8 @@ def run_gpu(args):
                 "measured": [[r["chunk_kb"], r["chunk_max_kb"], r["placement"], r["slots"], r["ctas_per_sm"],
                               round(r["apply_ms"], 4)] for r in rep["measured"]]}
 
-    for prec, lumps in variants:
-        sol = make_solver(prec, lumps)
+    for prec, lumps, ortho in variants:
+        sol = make_solver(prec, lumps, ortho)
         tiling = None if args.no_tune else tiling_summary(sol.tune_tiling(reps=7))
         for _ in range(args.warmup):
             step(sol)
@@ -811,7 +816,7 @@ def run_gpu(args):
         xh = x.cpu().numpy()
         import oracle as O
         r = system.b - O.spmv(system.row_ptr, system.col_idx, system.vals, xh)
-        results[vkey(prec, lumps)] = {"ms": ms, "info": infos[-1], "prof": prof, "stats": st, "clocks": clk.summary(),
+        results[vkey(prec, lumps, ortho)] = {"ms": ms, "info": infos[-1], "prof": prof, "stats": st, "clocks": clk.summary(),
                          "host_check_relres": float(np.linalg.norm(r) / np.linalg.norm(system.b)), "solver": sol,
                          "x": xh, "tiling": tiling}
 
@@ -871,6 +876,7 @@ def run_gpu(args):
                             "converged": bool(r_["info"]["converged"]), "true_rel_residual": r_["info"]["rel_residual"],
                             "host_check_rel_residual": r_["host_check_relres"],
                             "err_vs_fp64": err_vs_fp64(r_["x"]),
+                            "ortho_ms_per_solve": r_["prof"]["ortho_ms"] / args.steps,
                             "tiling": None if r_["tiling"] is None else
                             {k: r_["tiling"][k] for k in ("rule_ms", "chosen", "chosen_vs_rule")}}
                        for p_, r_ in results.items() if p_ != main_key},

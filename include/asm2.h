@@ -93,6 +93,19 @@ typedef enum {
                                    (Eq. A.6); same conditions */
 } asm_local_solver;
 
+/* Orthogonalisation of the GMRES Arnoldi step (Section 2 uses modified Gram-Schmidt).  The
+ * paper has no classical option; it is offered because on this GPU every projection of MGS is a
+ * global reduction (a grid-wide barrier per projection), while classical Gram-Schmidt takes the
+ * same FP64 work with two global reductions per step.  It rounds differently and keeps the basis
+ * less orthogonal (loss ~ cond^2 eps instead of cond eps), so iteration counts may differ from
+ * MGS and from the oracle; tests hold it to the solution tolerance.  It applies to single-system
+ * GMRES solves with the cooperative Gram-Schmidt (ASM_TUNE_COOP_ORTHO = 1) and restart <= 62;
+ * batched solves use MGS. */
+typedef enum {
+    ASM_ORTHO_MGS = 0, /* modified Gram-Schmidt (default; the oracle's arithmetic order) */
+    ASM_ORTHO_CGS = 1  /* classical Gram-Schmidt: all projections, then the norm, from two reductions */
+} asm_ortho;
+
 typedef enum {
     ASM_FAR_NONE = 0,      /* no far field: cells outside fine set + near lumps are left out */
     ASM_FAR_PARTITION = 1, /* far lumps = the partition boxes */
@@ -108,6 +121,7 @@ typedef struct {
                          x += B^{-1}(V y); -1 = automatic (0 for FP64, 1 otherwise) */
     int device;       /* CUDA device ordinal */
     int lump_precision; /* asm_lump_precision (default ASM_LUMP_FP32) */
+    int ortho;          /* asm_ortho (default ASM_ORTHO_MGS) */
 } asm_options;
 
 typedef struct {
@@ -280,8 +294,9 @@ typedef enum {
                               symbolic structure.  Fine rows compute the same bits under every
                               capacity; FP64 lump rows may round differently (their entry slots
                               are chosen per chunk) */
-    ASM_TUNE_APPLY_SLOTS = 6 /* ring slots of the apply with all local vectors in shared memory:
-                              0 (default) as many as keep two CTAs per SM, else 4; 2, 3 or 4 */
+    ASM_TUNE_APPLY_SLOTS = 6 /* ring slots of the apply: 0 (default) with all local vectors in
+                              shared memory as many as keep two CTAs per SM, else 4, and 2 with the
+                              other placements; 2, 3 or 4 for every placement */
 } asm_tune_key;
 int asm_set_tuning(asm_handle h, int key, int value);
 
@@ -289,15 +304,15 @@ int asm_set_tuning(asm_handle h, int key, int value);
  * the implementation).  For a factored handle with ILU(0) local solves it measures the
  * preconditioner apply under every stream-chunk capacity (ASM_TUNE_CHUNK_KB: the rule, 8, 12, 16,
  * 20, 24 KB; capacities that give every subdomain the same chunks as an earlier one are skipped)
- * crossed with every placement of the local vectors that fits (all in shared memory with 2, 3 or
- * 4 ring slots, lumps in shared memory, all in device memory), each as the median of `reps` timed
+ * crossed with every placement of the local vectors that fits (all in shared memory, lumps in
+ * shared memory, all in device memory) and 2, 3 or 4 ring slots, each as the median of `reps` timed
  * applies after two untimed ones.  It then leaves the fastest in place (ASM_TUNE_CHUNK_KB,
  * ASM_TUNE_APPLY_SLOTS and ASM_TUNE_APPLY_SMEM set, the online placement tuner off) with the
  * handle factored again, and reports every measurement.  Each capacity costs one symbolic rebuild
  * and factorisation, so this is a set-up step to run once per structure.  The handle's values are
  * factored again as they are; the Krylov workspace is reused.
  * Errors: STATE if not factored; INVALID_ARG for another local solver, reps < 1 or out == NULL. */
-#define ASM_TILING_MAX 48
+#define ASM_TILING_MAX 64
 typedef struct {
     int chunk_kb;      /* ASM_TUNE_CHUNK_KB value (0: the per-subdomain rule) */
     int chunk_max_kb;  /* the largest capacity the subdomains got (a ring slot's size) */

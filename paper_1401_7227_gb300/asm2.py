@@ -39,7 +39,7 @@ EXPORTS = [
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("krylov", C.c_int), ("restart", C.c_int), ("local_solver", C.c_int),
-                ("flexible", C.c_int), ("device", C.c_int), ("lump_precision", C.c_int)]
+                ("flexible", C.c_int), ("device", C.c_int), ("lump_precision", C.c_int), ("ortho", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -79,7 +79,7 @@ class TilingEntry(C.Structure):
                 ("slots", C.c_int), ("ctas_per_sm", C.c_int), ("apply_ms", C.c_double)]
 
 
-TILING_MAX = 48
+TILING_MAX = 64
 
 
 class TilingReport(C.Structure):
@@ -236,9 +236,10 @@ class Solver:
 
     def __init__(self, precision: str = "fp64", restart: int = 30, local_solver: str = "colsum",
                  flexible: int = -1, device: int = 0, stream: int | None = None, krylov: str = "gmres",
-                 lumps: str = "fp32"):
+                 lumps: str = "fp32", ortho: str = "mgs"):
         """lumps: "fp32" (default) or "fp64", the lump rows' precision under FP32/FP16S fine rows
-        (asm_options.lump_precision)."""
+        (asm_options.lump_precision).  ortho: "mgs" (default) or "cgs", the Arnoldi step's
+        Gram-Schmidt (asm_options.ortho)."""
         L = load()
         o = Options()
         L.asm_default_options(C.byref(o))
@@ -249,6 +250,7 @@ class Solver:
         o.flexible = flexible
         o.device = device
         o.krylov = {"gmres": 0, "orthomin": 1}[krylov]
+        o.ortho = {"mgs": 0, "cgs": 1}[ortho]
         self.device = device
         self.stream = stream if stream is not None else _current_stream(device)
         h = C.c_void_p()
@@ -362,8 +364,7 @@ class Solver:
         solves (ASM_TUNE_GRAPHS); wait_limit_log2: the apply kernels' chunk waits give up after
         2^value polls (0: at once; default 22), a failure-detection hook (ASM_TUNE_WAIT_LIMIT).
         chunk_kb: stream-chunk capacity (0 rule, 8..24 KB; ASM_TUNE_CHUNK_KB, applied by the next
-        factor()); apply_slots: ring slots with all local vectors in shared memory (0 rule, 2..4;
-        ASM_TUNE_APPLY_SLOTS)."""
+        factor()); apply_slots: the apply's ring slots (0 rule, 2..4; ASM_TUNE_APPLY_SLOTS)."""
         if chunk_kb is not None:
             _check(load().asm_set_tuning(self._h, 5, int(chunk_kb)), "set_tuning")
         if apply_slots is not None:

@@ -23,7 +23,7 @@ LIB = os.path.join(BUILD, "libasm2.so")
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["kernels_setup.cu", "kernels_solve.cu", "kernels_coarse.cu", "kernels_dense.cu", "kernels_nf.cu", "noalloc.cu"]
+CU_SOURCES = ["kernels_setup.cu", "kernels_solve.cu", "kernels_krylov.cu", "kernels_coarse.cu", "kernels_dense.cu", "kernels_nf.cu", "noalloc.cu"]
 CPP_SOURCES = ["api.cpp", "symbolic.cpp"]
 HEADERS = ["asm2_internal.h", "symbolic.h", "tma.h", "f64cvt.h"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", *ARCH, f"-I{INCLUDE}", f"-I{CSRC}"]

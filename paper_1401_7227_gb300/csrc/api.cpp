@@ -485,6 +485,10 @@ void upload_nf(asm_ctx* h, cudaStream_t st) {
     sync(h);
 }
 
+// Ring slots of the apply with the lump vector or no local vector in shared memory: the number
+// asked for (asm_set_tuning ASM_TUNE_APPLY_SLOTS), else 2.
+int other_slots(const asm_ctx* h) { return h->slots_force > 0 ? h->slots_force : 2; }
+
 // Ring slots of the apply with all local vectors in shared memory: the number asked for
 // (asm_set_tuning ASM_TUNE_APPLY_SLOTS), else as many as keep two CTAs per SM (shared memory per
 // SM minus 1 KB per CTA), else 4 with one CTA per SM.  That placement is off (apply_smem = 0)
@@ -780,7 +784,10 @@ void ensure_workspace(asm_ctx* h) {
     h->d_scal.zero(h->stream);
     h->d_ctl.alloc(C_NCTL * sizeof(int));
     h->d_ctl.zero(h->stream);
-    h->d_partial.alloc((size_t)4 * std::max(h->nchunk, 4096) * sizeof(double));
+    // chunk partials; the cooperative Gram-Schmidt's per-CTA partials (classical: kCgsMax values per
+    // CTA, at most two CTAs per SM)
+    h->d_partial.alloc(std::max<size_t>((size_t)4 * std::max(h->nchunk, 4096), (size_t)kCgsMax * 2 * 1024) *
+                       sizeof(double));
     h->ws_m = m;
     h->ws_flex = flex;
     SysTab& t = h->tab;
@@ -791,6 +798,7 @@ void ensure_workspace(asm_ctx* h) {
     t.m = m;
     t.flexible = om ? 0 : flex;
     t.krylov = om ? 1 : 0;
+    t.ortho = om ? 0 : h->opt.ortho;
     t.nchunk = h->nchunk;
     t.scal = h->d_scal.as<double>();
     t.ctl = h->d_ctl.as<int>();
@@ -1203,7 +1211,7 @@ void build_batch(Batch& B, cudaStream_t st) {
     }
     if (!B.hs.empty())
         B.apply = apply_local_vectors(B.nsub, all_bytes, lump_bytes, B.slots, B.chunk, B.hs[0]->sm_smem,
-                                      B.hs[0]->n_sms, B.hs[0]->apply_place);
+                                      B.hs[0]->n_sms, B.hs[0]->apply_place, other_slots(B.hs[0]));
 }
 
 // events bracketing the launch groups of one step: [prep | apply | post | spmv | mgs+finish]
@@ -1230,7 +1238,8 @@ std::vector<ApplyConfig> apply_candidates(const Batch& B) {
     if (h->apply_place != 0) return {B.apply};
     for (int force : {Y_SMEM + 1, Y_LUMPS + 1, Y_DEVICE + 1}) {
         const ApplyConfig a =
-            apply_local_vectors(B.nsub, B.all_bytes, B.lump_bytes, B.slots, B.chunk, h->sm_smem, h->n_sms, force);
+            apply_local_vectors(B.nsub, B.all_bytes, B.lump_bytes, B.slots, B.chunk, h->sm_smem, h->n_sms, force,
+                                other_slots(h));
         if (a.ymode == force - 1) c.push_back(a);
     }
     return c;
@@ -1901,6 +1910,7 @@ void asm_default_options(asm_options* opt) {
     opt->flexible = -1;
     opt->device = 0;
     opt->lump_precision = ASM_LUMP_FP32;
+    opt->ortho = ASM_ORTHO_MGS;
 }
 
 const char* asm_error_string(int s) {
@@ -1926,7 +1936,8 @@ int asm_create(asm_handle* out, const asm_options* opt, void* cuda_stream) {
     if (opt) o = *opt;
     if (o.precision < 0 || o.precision > 2 || o.krylov < 0 || o.krylov > 1 || o.restart < 1 || o.restart > 512 ||
         o.local_solver < 0 || o.local_solver > 4 || o.flexible < -1 || o.flexible > 1 || o.lump_precision < 0 ||
-        o.lump_precision > 1 ||
+        o.lump_precision > 1 || o.ortho < 0 || o.ortho > 1 ||
+        (o.ortho == ASM_ORTHO_CGS && o.restart > kCgsMax - 2) ||
         (o.local_solver == ASM_LOCAL_EXACT && o.precision != ASM_PREC_FP64) ||
         (o.local_solver >= ASM_LOCAL_NF_COLSUM && o.precision == ASM_PREC_FP16S))
         return ASM_ERR_INVALID_ARG;
@@ -2096,7 +2107,7 @@ int asm_factor(asm_handle h) {
 // the placement of a single-system apply: `place` as ASM_TUNE_APPLY_SMEM stores it (0 automatic)
 ApplyConfig single_apply_config(const asm_ctx* h, int place) {
     return apply_local_vectors((int)h->sub_desc.size(), h->apply_smem, h->apply_lump_smem, h->apply_slots,
-                               h->chunk_cap, h->sm_smem, h->n_sms, place);
+                               h->chunk_cap, h->sm_smem, h->n_sms, place, other_slots(h));
 }
 
 // R_i r and the fused ILU sweeps of every subdomain (after k_sums), single-system tables
@@ -2210,12 +2221,11 @@ int asm_tune_tiling(asm_handle h, int reps, asm_tiling_report* out) {
                 int place, slots;
             };
             std::vector<Cand> cands;
-            for (int sl = 2; sl <= 4; sl++) cands.push_back({Y_SMEM + 1, sl});
-            cands.push_back({Y_LUMPS + 1, 0});
-            cands.push_back({Y_DEVICE + 1, 0});
+            for (int place : {Y_SMEM + 1, Y_LUMPS + 1, Y_DEVICE + 1})
+                for (int sl = 2; sl <= 4; sl++) cands.push_back({place, sl});
             for (const Cand& c : cands) {
                 if (out->n >= ASM_TILING_MAX) break;
-                h->slots_force = c.place == Y_SMEM + 1 ? c.slots : 0;
+                h->slots_force = c.slots;
                 choose_ring(h);
                 const ApplyConfig cfg = single_apply_config(h, c.place);
                 if (cfg.ymode != c.place - 1) continue;  // does not fit
@@ -2240,7 +2250,7 @@ int asm_tune_tiling(asm_handle h, int reps, asm_tiling_report* out) {
         for (int k = 1; k < out->n; k++)
             if (out->e[k].apply_ms < out->e[out->best].apply_ms) out->best = k;
         const asm_tiling_entry& b = out->e[out->best];
-        h->slots_force = b.placement == 3 ? b.slots : 0;
+        h->slots_force = b.slots;
         stt = rebuild(b.chunk_kb * 1024);
         if (stt != ASM_OK) return stt;
         choose_ring(h);

@@ -37,6 +37,7 @@ struct ApplyConfig {
 // kChunkLongLumps = the chunk holds a lump row of more than kLongLumpRow blocks.
 constexpr int kChunkLongLumps = 1 << 12;
 constexpr int VEC_THREADS = 256;
+constexpr int kCgsMax = 64;  // classical Gram-Schmidt: at most kCgsMax - 2 basis vectors (restart)
 enum VecSlot { VX = 0, VB = 1, VR = 2, VW = 3, VZ = 4, VU = 5, VV0 = 6 };  // V_k = VV0 + k; Z_k after V
 
 // GMRES phases of one system
@@ -108,6 +109,7 @@ struct SysTab {
     int m;               // GMRES restart length, or ORTHOMIN direction count k
     int flexible;        // keep Z_k = B^{-1} V_k (slots after V)
     int krylov;          // asm_krylov: 0 GMRES (slots V_k, Z_k), 1 ORTHOMIN (slots P_s, then Q_s)
+    int ortho;           // asm_ortho: 0 modified, 1 classical Gram-Schmidt (single-system GMRES)
     int nchunk;          // vector work items of this system
     double* scal;        // scalars (ScalLayout)
     int* ctl;            // control words (Ctl)
@@ -285,9 +287,10 @@ size_t apply_lump_bytes(int nc, int prec, bool lump32);  // its lump vector (and
 // one ring slot (the largest chunk capacity of the launch's subdomains); force: 0
 // automatic (all in shared memory while the launch's nsub CTAs run at once at that occupancy, else
 // lumps in shared memory when four CTAs fit, else device memory), Y_SMEM + 1 / Y_LUMPS + 1 /
-// Y_DEVICE + 1 to ask for one placement (taken when it fits).
+// Y_DEVICE + 1 to ask for one placement (taken when it fits).  smem_slots: ring slots with all
+// local vectors in shared memory; other_slots: with the other placements.
 ApplyConfig apply_local_vectors(int nsub, int all_bytes, int lump_bytes, int smem_slots, int chunk, int sm_smem,
-                                int sms, int force);
+                                int sms, int force, int other_slots = 2);
 size_t apply_ring_bytes(int slots, int chunk);
 void launch_spmv(const SysTab* st_tab, const RowItem* items, int nitems, cudaStream_t st);
 

@@ -36,11 +36,15 @@ ASM2_HD bool f64_to_f32_bits(unsigned hi, unsigned lo, unsigned& out) {
 }
 
 #if defined(__CUDACC__)
+// the conversion instruction, out of line: a call is a branch, so lanes that take the integer
+// path do not execute it (inlined, the compiler may predicate it on every lane)
+__device__ __noinline__ float f64_to_f32_instruction(double d) { return __double2float_rn(d); }
+
 __device__ __forceinline__ float f64_to_f32(double d) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(d);
     unsigned f;
     if (f64_to_f32_bits((unsigned)(b >> 32), (unsigned)b, f)) return __uint_as_float(f);
-    return __double2float_rn(d);
+    return f64_to_f32_instruction(d);
 }
 #endif
 

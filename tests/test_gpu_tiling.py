@@ -69,18 +69,19 @@ def test_chunk_capacity_keeps_the_bits_of_fp32_rows(system, kb):
     sol.close()
 
 
+@pytest.mark.parametrize("place", ["shared", "device", "lumps"])
 @pytest.mark.parametrize("slots", [2, 3, 4])
-def test_ring_slots_keep_the_bits(system, slots):
+def test_ring_slots_keep_the_bits(system, slots, place):
     """With 8 KB chunks all local vectors (186 KB per subdomain here) and 2-4 ring slots fit one
-    CTA's shared memory, which 24 KB slots do not allow."""
+    CTA's shared memory, which 24 KB slots do not allow; the other placements take 2-4 slots too."""
     sol = solver(system)
     b = torch.from_numpy(system.b).cuda()
     z0 = sol.apply(b).clone()
     sol.set_tuning(chunk_kb=8)
     sol.factor()
-    sol.set_tuning(apply_smem="shared", apply_slots=slots)
+    sol.set_tuning(apply_smem=place, apply_slots=slots)
     st = sol.stats()
-    assert st["apply_placement"] == "shared" and st["apply_slots"] == slots
+    assert st["apply_placement"] == place and st["apply_slots"] == slots
     assert torch.equal(sol.apply(b), z0)
     sol.close()
 

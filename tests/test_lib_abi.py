@@ -42,6 +42,7 @@ def test_error_strings_and_defaults(lib):
     o = asm2.Options()
     lib.asm_default_options(C.byref(o))
     assert (o.precision, o.krylov, o.restart, o.local_solver, o.flexible, o.device) == (0, 0, 30, 0, -1, 0)
+    assert (o.lump_precision, o.ortho) == (1, 0)
 
 
 def test_invalid_arguments_are_rejected_on_the_host(lib):
@@ -49,6 +50,12 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     o = asm2.Options()
     lib.asm_default_options(C.byref(o))
     o.restart = 0
+    assert lib.asm_create(C.byref(h), C.byref(o), None) == 1
+    lib.asm_default_options(C.byref(o))
+    o.ortho = 2
+    assert lib.asm_create(C.byref(h), C.byref(o), None) == 1
+    o.ortho = 1
+    o.restart = 63  # classical Gram-Schmidt keeps at most 62 basis vectors
     assert lib.asm_create(C.byref(h), C.byref(o), None) == 1
     assert lib.asm_create(None, None, None) == 1
     assert lib.asm_set_grid(None, 1, 1, 1) == 1
