@@ -31,9 +31,11 @@ __global__ void __launch_bounds__(256) k_spmv(const SysTab* __restrict__ tab, co
         const int c = st.ell_col[(long long)w * rp + row];
         const double x0 = x[3LL * c], x1 = x[3LL * c + 1], x2 = x[3LL * c + 2];
         const double* v = st.ell_val + (long long)w * 9 * rp + row;
-        a0 += v[0] * x0 + v[rp] * x1 + v[2 * rp] * x2;
-        a1 += v[3 * rp] * x0 + v[4 * rp] * x1 + v[5 * rp] * x2;
-        a2 += v[6 * rp] * x0 + v[7 * rp] * x1 + v[8 * rp] * x2;
+        // one FMA per product into the running sums: an FP64 instruction costs a warp ~64 cycles
+        // here, and a separate product-then-add form would take four per three products
+        a0 = fma(v[2 * rp], x2, fma(v[rp], x1, fma(v[0], x0, a0)));
+        a1 = fma(v[5 * rp], x2, fma(v[4 * rp], x1, fma(v[3 * rp], x0, a1)));
+        a2 = fma(v[8 * rp], x2, fma(v[7 * rp], x1, fma(v[6 * rp], x0, a2)));
     }
     if (bs >= 0) {
         const double* b = st.ws + (long long)bs * st.n3p;

@@ -203,7 +203,8 @@ __global__ void __launch_bounds__(256, 4) k_factor(const FactDesc* __restrict__ 
                 }
 #pragma unroll
                 for (int u = 0; u < kP; u++)
-                    if (pr[u].x >= 0) acc -= l[u][0] * uu[u][0] + l[u][1] * uu[u][1] + l[u][2] * uu[u][2];
+                    if (pr[u].x >= 0)  // three FMAs into the running value (not product, sum, subtract)
+                        acc = fma(-l[u][2], uu[u][2], fma(-l[u][1], uu[u][1], fma(-l[u][0], uu[u][0], acc)));
             }
             s[e9] = acc;
         }
