@@ -310,7 +310,7 @@ int asm_set_tuning(asm_handle h, int key, int value);
  * ASM_TUNE_APPLY_SLOTS and ASM_TUNE_APPLY_SMEM set, the online placement tuner off) with the
  * handle factored again, and reports every measurement.  Each capacity costs one symbolic rebuild
  * and factorisation, so this is a set-up step to run once per structure.  The handle's values are
- * factored again as they are; the Krylov workspace is reused.
+ * factored again as they are.
  * Errors: STATE if not factored; INVALID_ARG for another local solver, reps < 1 or out == NULL. */
 #define ASM_TILING_MAX 64
 typedef struct {

@@ -17,19 +17,18 @@ constexpr int VEC_CHUNK = 4096;   // elements per vector work item (256 threads 
 // bytes of one factor-stream chunk (= one shared-memory ring slot of the apply): chosen per subdomain
 // so that its largest fine level fits one chunk, within [kStreamChunkMin, kStreamChunkMax]
 constexpr int kStreamChunkMin = 8192, kStreamChunkMax = 24576;
-constexpr int kStreamSlots = 3;      // default ring slots of the apply (chunks in flight per CTA)
 constexpr int kLongLumpRow = 16;     // lump rows with more stored blocks are swept by a whole warp
-// The apply runs one CTA per subdomain.  With all its local vectors in shared memory a CTA has 256
-// threads and two fit on an SM; with the fine-row vector in device memory (L1/L2) a CTA has 128
-// threads and four fit, which wins once a launch has more subdomains than the shared-memory variant
-// runs at once.  The lump vector (FP64) and its FP32 mirror then stay in shared memory when four
-// CTAs' worth fit, else they go to device memory too.
+// The apply runs one 256-thread CTA per subdomain.  With all its local vectors in shared memory
+// one or two CTAs fit on an SM; with the fine-row vector in device memory (L1/L2) four fit, which
+// wins once a launch has more subdomains than the shared-memory variant runs at once.  The lump
+// vector (and, for FP64 lump rows, its FP32 mirror) then stays in shared memory when four CTAs'
+// worth fit, else it goes to device memory too.
 constexpr int kApplyThreadsDev = 256;
 enum ApplyY { Y_SMEM = 0, Y_LUMPS = 1, Y_DEVICE = 2 };  // where the apply's local vectors live
 struct ApplyConfig {
     int ymode;  // ApplyY
     int smem;   // dynamic shared memory of the vectors (bytes)
-    int slots;  // factor-stream ring slots (2 for the 128-thread variants: deeper rings gain nothing)
+    int slots;  // factor-stream ring slots (2..4; the tiling tuner measured deeper rings slower)
     int chunk;  // bytes of one ring slot: the largest chunk capacity of the launch's subdomains
 };
 // Chunk header word 6: bit 0 = last chunk of its wavefront level; bits 8..11 = log2 of the entry

@@ -299,7 +299,7 @@ std::string build_sub(const Ctx& X, int s, SubSym& o) {
             if (slot(o.pci[t], p) < 0) return "local pattern not structurally symmetric";
 
     // Wavefront levels of the DAG of L (the same sets, reversed, serve U), every row at the earliest
-    // level its dependencies allow: the lump rows (FP64) then run in the same levels as the fine
+    // level its dependencies allow: the lump rows then run in the same levels as the fine
     // rows they follow instead of after the last of them, which shortens the chain of levels (and
     // of CTA barriers) by about a fifth at 1M cells.  Any level assignment that respects the DAG
     // gives the same arithmetic.
