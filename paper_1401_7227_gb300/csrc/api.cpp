@@ -105,7 +105,7 @@ struct asm_ctx {
     int n_along = 0;  // slots whose assembly lists are summed by a warp each
     DBuf d_fp;  // factor program arrays (one allocation, see upload_factor_program)
     DBuf d_stream, d_pk_off_f, d_pk_src_f, d_pk_off_c, d_pk_src_c;
-    DBuf d_lv, d_rlists, d_y, d_corr_cells, d_corr, d_dev_err, d_gsum;
+    DBuf d_lv, d_rlists, d_y, d_corr_cells, d_corr, d_dev_err, d_gsum, d_r32;
     int n_group_items = 0;  // box_items[0 .. n_group_items): the cell-group sums (kind 2)
     int apply_smem = 0;       // shared memory for all local vectors of the largest subdomain (0: none)
     int apply_smem_need = 0;  // the same before the fit test of choose_ring()
@@ -724,6 +724,8 @@ void upload_symbolic(asm_ctx* h) {
     if (sum_lists) {
         const int ng = n_groups(S.g);
         h->d_gsum.alloc((size_t)ng * 3 * sizeof(double));
+        // FP32 local vectors: k_groups also rounds every cell's entries once, for the fine rows
+        if (h->lump32) h->d_r32.alloc((size_t)h->N * 4 * sizeof(float));
         for (int g0 = 0; g0 < ng; g0 += 256) h->box_items.push_back(BoxItem{0, 0, g0, std::min(ng, g0 + 256), 2, 0, nullptr});
         h->n_group_items = (int)h->box_items.size();
     } else {
@@ -810,6 +812,7 @@ void ensure_workspace(asm_ctx* h) {
     t.boxsum = h->d_boxsum.as<double>();
     t.corr = h->d_corr.p ? h->d_corr.as<double>() : h->d_boxsum.as<double>();
     t.gsum = h->d_gsum.p ? h->d_gsum.as<double>() : h->d_boxsum.as<double>();
+    t.r32 = h->n_group_items > 0 && h->lump32 && h->d_r32.p ? h->d_r32.as<float4>() : nullptr;
     t.gnx = h->geom.nx;
     t.gny = h->geom.ny;
     t.gnz = h->geom.nz;
@@ -1554,7 +1557,8 @@ size_t ctx_device_bytes(const asm_ctx* h) {
                           &h->d_cptr, &h->d_cloc, &h->d_cval, &h->d_boxsum, &h->d_slot, &h->d_dpiv, &h->d_aptr,
                           &h->d_aloc, &h->d_acs, &h->d_along, &h->d_fp, &h->d_stream, &h->d_pk_off_f, &h->d_pk_src_f,
                           &h->d_pk_off_c, &h->d_pk_src_c, &h->d_lv, &h->d_rlists, &h->d_y, &h->d_corr_cells,
-                          &h->d_corr, &h->d_dev_err, &h->d_factdesc, &h->d_subdesc_single, &h->d_err, &h->d_ws,
+                          &h->d_corr, &h->d_dev_err, &h->d_gsum, &h->d_r32, &h->d_factdesc, &h->d_subdesc_single,
+                          &h->d_err, &h->d_ws,
                           &h->d_scal, &h->d_ctl, &h->d_partial, &h->d_tab1, &h->d_vec1, &h->d_row1, &h->d_box1,
                           // exact local solves, nested factorisation, classical coarse correction
                           &h->d_daug, &h->d_dprow, &h->d_dfcol, &h->d_dmats, &h->d_dinit, &h->d_doff,

@@ -122,6 +122,7 @@ struct SysTab {
     double* boxsum;      // [n_boxes * 3] far-box sums of the apply input
     double* corr;        // [n_corr * 3] near-region sums subtracted from far-lump box sums
     double* gsum;        // [n_groups * 3] sums of the apply input over aligned 2x2x2 cell groups
+    float4* r32;         // [n_cells] the apply input rounded to FP32 (written with gsum), or null
     int gnx, gny, gnz;   // grid size (for the cells of a group)
     int* dev_err;        // device status word: nonzero after a bounded wait expired
     long long wait_limit;  // polls of the first wait on each factor-stream copy of the apply kernels

@@ -12,9 +12,10 @@ namespace asm2 {
 namespace {
 
 // ------------------------------------------------------------------------------------------
-// SpMV y = A x or y = b - A x (ELL, one thread per block row, 3x3 blocks)
+// SpMV y = A x or y = b - A x (ELL, one thread per block row, 3x3 blocks); four CTAs per SM
+// (64 registers) hide the gathers of x better than three at 80 registers
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_spmv(const SysTab* __restrict__ tab, const RowItem* __restrict__ items) {
+__global__ void __launch_bounds__(256, 4) k_spmv(const SysTab* __restrict__ tab, const RowItem* __restrict__ items) {
     const RowItem it = items[blockIdx.x];
     const SysTab& st = tab[it.sys];
     const int in = st.ctl[C_SPMV_IN];

@@ -98,7 +98,9 @@ __device__ __forceinline__ const double* sum_entry(const SysTab& st, const doubl
 }
 
 // Sums of the apply input over aligned 2x2x2 cell groups, thread per group, the group's cells in a
-// fixed order (y, then x, then z): every list sum that covers whole groups reads these instead
+// fixed order (y, then x, then z): every list sum that covers whole groups reads these instead.
+// With FP32 local vectors it also writes each cell's entries rounded to FP32 (r32, 16 bytes per
+// cell), once per cell, for the restriction's fine rows to copy.
 __global__ void __launch_bounds__(256) k_groups(const SysTab* __restrict__ tab, const BoxItem* __restrict__ items) {
     const BoxItem it = items[blockIdx.x];
     const SysTab& st = tab[it.sys];
@@ -115,10 +117,13 @@ __global__ void __launch_bounds__(256) k_groups(const SysTab* __restrict__ tab, 
     for (int y = y0; y < y1; y++)
         for (int x = x0; x < x1; x++)
             for (int z = z0; z < z1; z++) {
-                const double* rc = r + 3LL * (z + (long long)st.gnz * (x + (long long)st.gnx * y));
-                a0 += rc[0];
-                a1 += rc[1];
-                a2 += rc[2];
+                const long long cell = z + (long long)st.gnz * (x + (long long)st.gnx * y);
+                const double* rc = r + 3LL * cell;
+                const double v0 = rc[0], v1 = rc[1], v2 = rc[2];
+                a0 += v0;
+                a1 += v1;
+                a2 += v2;
+                if (st.r32 != nullptr) st.r32[cell] = make_float4(f64_to_f32(v0), f64_to_f32(v1), f64_to_f32(v2), 0.f);
             }
     double* o = st.gsum + 3LL * G;
     o[0] = a0;
@@ -367,7 +372,7 @@ __device__ __forceinline__ void sweep_chunk(const unsigned char* base, bool lowe
                         x1 = yc[3 * ~c + 1];
                         x2 = yc[3 * ~c + 2];
                     }
-                    acc -= fma(v[0], x0, fma(v[1], x1, v[2] * x2));
+                    acc = fma(-v[2], x2, fma(-v[1], x1, fma(-v[0], x0, acc)));  // one FMA per product
                 }
             }
             if (lower) {
@@ -630,11 +635,16 @@ __global__ void __launch_bounds__(256) k_restrict(const SysTab* __restrict__ tab
     const int q = it.y + threadIdx.x;
     constexpr bool kRow16 = sizeof(TL) == 4;  // FP32 lumps: rows of four floats (16 bytes)
     if (q < sd.nf) {
-        const double* rc = r + 3LL * sd.fcell[q];
         if constexpr (kRow16) {
-            reinterpret_cast<float4*>(y + sd.y_fine)[q] =
-                make_float4(f64_to_f32(rc[0]), f64_to_f32(rc[1]), f64_to_f32(rc[2]), 0.f);
+            float4* yf4 = reinterpret_cast<float4*>(y + sd.y_fine) + q;
+            if (st.r32 != nullptr) {  // rounded once per cell by k_groups
+                *yf4 = st.r32[sd.fcell[q]];
+            } else {
+                const double* rc = r + 3LL * sd.fcell[q];
+                *yf4 = make_float4(f64_to_f32(rc[0]), f64_to_f32(rc[1]), f64_to_f32(rc[2]), 0.f);
+            }
         } else {
+            const double* rc = r + 3LL * sd.fcell[q];
             TC* yf = reinterpret_cast<TC*>(y + sd.y_fine) + 3 * q;
             yf[0] = narrow<TC>(rc[0]);
             yf[1] = narrow<TC>(rc[1]);
