@@ -58,3 +58,24 @@ def test_clock_summary_reads_throttle_reasons():
     cs.rows.append(["0", "1500", "2070", "800", "0x8", "Active", "Not Active", "Active", "Not Active"])
     assert cs.summary()["reasons"] == ["hw_slowdown", "sw_power_cap", "sw_thermal_slowdown"]
     assert bench.ClockSampler(0).summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def test_ortho_roofline_counts_the_mgs_passes():
+    """The Gram-Schmidt roofline's flops: every Arnoldi step j of a GMRES(m) cycle makes j + 2
+    passes of 2 FMAs per element (the first pass: (w, v_0) and (w, w); then w -= h v and the next
+    dot; the last: w -= h v_j and (w, w)) and one scaling pass, enumerated here pass by pass."""
+    class Sys:
+        n_cells = 1000
+
+    for iters, m in ((87, 30), (30, 30), (5, 30), (61, 20)):
+        n3 = 3.0 * Sys.n_cells
+        flops = 0.0
+        done = 0
+        while done < iters:
+            for j in range(min(m, iters - done)):
+                passes = [2] + [2] * j + [2]  # FMAs per element of each pass
+                flops += sum(2 * f for f in passes) * n3 + n3  # 2 flops per FMA; the scaling: 1 per element
+                done += 1
+        res = {"info": {"iterations": iters, "restarts": 0}, "prof": {"ortho_ms": 1000.0}}
+        line = bench.ortho_roofline(res, Sys, 1, m)
+        assert abs(line["achieved"] * 1e12 * 1.0 - flops) <= 1e-9 * flops, (iters, m)
