@@ -586,19 +586,34 @@ __device__ void cgs_project(const SysTab& st, double* part2, cooperative_groups:
         double p[kD][2];
 #pragma unroll
         for (int d = 0; d < kD; d++) p[d][0] = p[d][1] = 0.0;
+        double a[2], b[kD][2];
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+            const long long e = e_begin + u * stride;
+            a[u] = e < n ? w[e] : 0.0;
+#pragma unroll
+            for (int d = 0; d < kD; d++) b[d][u] = e < n && vs[d] ? vs[d][e] : 0.0;
+        }
         for (long long e0 = e_begin; e0 < n; e0 += 2 * stride) {
-            double a[2], b[kD][2];
+            double an[2], bn[kD][2];
 #pragma unroll
             for (int u = 0; u < 2; u++) {
-                const long long e = e0 + u * stride;
-                a[u] = e < n ? w[e] : 0.0;
+                const long long e = e0 + (2 + u) * stride;
+                an[u] = e < n ? w[e] : 0.0;
 #pragma unroll
-                for (int d = 0; d < kD; d++) b[d][u] = e < n && vs[d] ? vs[d][e] : 0.0;
+                for (int d = 0; d < kD; d++) bn[d][u] = e < n && vs[d] ? vs[d][e] : 0.0;
             }
 #pragma unroll
             for (int d = 0; d < kD; d++)
+                if (vs[d] != nullptr)
 #pragma unroll
-                for (int u = 0; u < 2; u++) p[d][u] = fma(a[u], b[d][u], p[d][u]);
+                    for (int u = 0; u < 2; u++) p[d][u] = fma(a[u], b[d][u], p[d][u]);
+#pragma unroll
+            for (int u = 0; u < 2; u++) {
+                a[u] = an[u];
+#pragma unroll
+                for (int d = 0; d < kD; d++) b[d][u] = bn[d][u];
+            }
         }
         // the kD block sums: warp d adds column d (eight entries per lane, then five shuffles)
 #pragma unroll
@@ -620,8 +635,18 @@ __device__ void cgs_project(const SysTab& st, double* part2, cooperative_groups:
     for (int base = 0; base < nv; base += 32) {
         const int i = base + (int)(threadIdx.x >> 3), q = threadIdx.x & 7;
         double a = 0.0;
-        if (i < nv)
-            for (int c = q; c < G; c += 8) a += __ldcg(&part2[(size_t)i * G + c]);
+        if (i < nv) {
+            const double* pi = part2 + (size_t)i * G;
+            int c = q;
+            for (; c + 24 < G; c += 32) {
+                const double l0 = __ldcg(&pi[c]), l1 = __ldcg(&pi[c + 8]), l2 = __ldcg(&pi[c + 16]), l3 = __ldcg(&pi[c + 24]);
+                a += l0;
+                a += l1;
+                a += l2;
+                a += l3;
+            }
+            for (; c < G; c += 8) a += __ldcg(&pi[c]);
+        }
         a += __shfl_xor_sync(0xffffffffu, a, 4);
         a += __shfl_xor_sync(0xffffffffu, a, 2);
         a += __shfl_xor_sync(0xffffffffu, a, 1);
@@ -636,7 +661,26 @@ __device__ void cgs_project(const SysTab& st, double* part2, cooperative_groups:
         double x[kU];
 #pragma unroll
         for (int u = 0; u < kU; u++) x[u] = e0 + u * stride < n ? w[e0 + u * stride] : 0.0;
-        for (int i = 0; i <= j; i++) {
+        // kV basis vectors at a time: all their loads are issued before their multiply-adds (which
+        // keep the order i = 0..j), so that enough loads are in flight to stream V from memory
+        constexpr int kV = 4;
+        int i = 0;
+        for (; i + kV <= j + 1; i += kV) {
+            double b[kV][kU];
+#pragma unroll
+            for (int d = 0; d < kV; d++) {
+                const double* vi = vec(st, VV0 + i + d);
+#pragma unroll
+                for (int u = 0; u < kU; u++) b[d][u] = e0 + u * stride < n ? vi[e0 + u * stride] : 0.0;
+            }
+#pragma unroll
+            for (int d = 0; d < kV; d++) {
+                const double h = htot[i + d];
+#pragma unroll
+                for (int u = 0; u < kU; u++) x[u] = fma(-h, b[d][u], x[u]);
+            }
+        }
+        for (; i <= j; i++) {
             const double h = htot[i];
             const double* vi = vec(st, VV0 + i);
             double b[kU];
